@@ -1,0 +1,215 @@
+/*
+ * nep_ciss.h -- C ABI of the GB300 contour-integral (CISS) solver for nonlinear
+ * eigenvalue problems in split form.
+ *
+ * Problem (Sec. 2, Eqs. (nep) and (split)): find (lambda, x), x != 0, with
+ *     T(lambda) x = 0,    T(z) = sum_{i<l} A_i f_i(z),
+ * A_i constant sparse n x n matrices, f_i scalar holomorphic functions (Sec. 3.1.2
+ * function classes: rational, exp, principal sqrt, with argument/result scaling and
+ * combinations). The solver returns every eigenpair inside an ellipse Gamma.
+ *
+ * Conventions
+ *   - Complex numbers are interleaved doubles (re, im); a "complex array of length k"
+ *     is 2k doubles. Dense blocks are column-major.
+ *   - Every call returns int: NEP_OK (0) or a negative NEP_ERR_*; nep_last_error()
+ *     gives a message (thread-local, valid until the next failing call on the thread).
+ *   - Inputs are copied at the call; callers keep ownership of their buffers. Objects
+ *     returned through an out-pointer are owned by the library until the matching
+ *     *_free/*_destroy call.
+ *   - Entry points that take device pointers ("_dev") expect memory of the current
+ *     CUDA device; "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - All arithmetic is complex. Host callbacks are not supported: every f_i must be a
+ *     closed-form kind below, because the Rayleigh-Ritz/Newton step evaluates f_i and
+ *     f_i' on the device.
+ */
+#ifndef NEP_CISS_H
+#define NEP_CISS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define NEP_OK 0
+#define NEP_ERR_ARG (-1)         /* invalid argument (sizes, CSR structure, options)    */
+#define NEP_ERR_CUDA (-2)        /* a CUDA runtime call failed                           */
+#define NEP_ERR_REGION (-3)      /* the closed region meets a pole or a branch cut       */
+#define NEP_ERR_NOMEM (-4)       /* device or host allocation failed                      */
+#define NEP_ERR_UNSUPPORTED (-5) /* valid request outside what the library implements    */
+#define NEP_ERR_INTERNAL (-6)    /* device-side check failed (bounded wait, bad index)   */
+
+/* warning flags of a result (bitwise or) */
+#define NEP_WARN_SATURATED 1     /* Hankel rank m == L*M: the probe subspace may be too small */
+#define NEP_WARN_REFINE 2        /* some quadrature solve missed the backward-error target */
+#define NEP_WARN_SINGULAR_NODE 4 /* an exactly zero pivot at some quadrature node         */
+#define NEP_WARN_NEWTON 8        /* a Newton iteration on the projected problem failed      */
+
+/* arithmetic of the quadrature solves */
+#define NEP_PREC_FP64 0  /* complex128 factors and solves ("plain FP64")                  */
+#define NEP_PREC_MIXED 1 /* complex64 factors and solves, FP64 residuals and refinement  */
+
+/* ------------------------------------------------------------------ problem objects */
+typedef struct nep_split *nep_split_t;
+typedef struct nep_result *nep_result_t;
+typedef struct nep_plan *nep_plan_t;
+
+/* CSR matrix (0-based). Column indices of each row must be strictly increasing and in
+ * [0, n_cols). val_im may be NULL for a real matrix. */
+typedef struct {
+    int32_t n_rows, n_cols;
+    const int64_t *rowptr; /* n_rows + 1 entries */
+    const int32_t *col;    /* rowptr[n_rows] entries */
+    const double *val_re;
+    const double *val_im;
+} nep_csr;
+
+/* Scalar function g(z) = beta * h(alpha * z) (FNSetScale of Sec. 3.1.2), h by kind:
+ *   NEP_FN_RATIONAL  h(x) = p(x) / q(x); num/den are complex arrays, highest degree
+ *                    first (nnum, nden coefficients); nden == 0 means q = 1.
+ *   NEP_FN_EXP       h(x) = exp(x).
+ *   NEP_FN_SQRT      h(x) = sqrt(x - shift), principal branch (cut on x - shift <= 0).
+ *   NEP_FN_COMBINE   h = a + b, a * b, a / b or a(b(.)) (op), a and b nested nep_fn. */
+#define NEP_FN_RATIONAL 0
+#define NEP_FN_EXP 1
+#define NEP_FN_SQRT 2
+#define NEP_FN_COMBINE 3
+#define NEP_OP_ADD 0
+#define NEP_OP_MUL 1
+#define NEP_OP_DIV 2
+#define NEP_OP_COMPOSE 3
+typedef struct nep_fn {
+    int32_t kind;
+    double alpha_re, alpha_im, beta_re, beta_im;
+    double shift_re, shift_im;
+    int32_t nnum, nden;
+    const double *num;
+    const double *den;
+    int32_t op;
+    const struct nep_fn *a;
+    const struct nep_fn *b;
+} nep_fn;
+
+/* Ellipse Gamma: z(t) = center + a cos t + i b sin t (a: real semi-axis, b: imaginary). */
+typedef struct {
+    double center_re, center_im, a, b;
+} nep_region;
+
+typedef struct {
+    int32_t precision;   /* NEP_PREC_FP64 or NEP_PREC_MIXED                               */
+    double rank_tol;     /* Hankel numerical rank: sigma_i > rank_tol * sigma_1 (1e-12)   */
+    double basis_tol;    /* Rayleigh-Ritz basis rank, relative singular value (1e-6)     */
+    double refine_tol;   /* per-solve normwise backward error target (1e-10)              */
+    double step_tol;     /* relative refinement correction regarded as converged (1e-14) */
+    int32_t refine_max;  /* maximum refinement sweeps (10)                                */
+    double eig_tol;      /* scaled-residual acceptance of returned eigenpairs (1e-8)      */
+    int32_t newton_max;  /* Newton steps on the projected problem (30)                    */
+    double newton_tol;   /* |dlambda| <= newton_tol * max(1, |lambda|) (1e-14)            */
+    uint64_t seed;       /* probe block V when none is passed                             */
+} nep_opts;
+
+/* Defaults listed above. */
+void nep_opts_default(nep_opts *o);
+
+/* Builds the split operator T(z) = sum_i A_i f_i(z) (Sec. 3.1.2, NEPSetSplitOperator):
+ * validates each CSR (square n x n, sorted in-range columns), forms the union sparsity
+ * pattern with one value array per term, its bandwidths (kl, ku), ||A_i||_inf, and
+ * copies everything to the current device. nterms >= 1; f has nterms entries.
+ * Errors: NEP_ERR_ARG (bad sizes/CSR/function), NEP_ERR_CUDA, NEP_ERR_NOMEM. */
+int nep_create_split(int32_t n, int32_t nterms, const nep_csr *A, const nep_fn *f, nep_split_t *out);
+int nep_destroy(nep_split_t h);
+/* Bandwidths and band leading dimension (ldab = 2 kl + ku + 1) of the union pattern. */
+int nep_split_info(nep_split_t h, int32_t *n, int32_t *nterms, int32_t *kl, int32_t *ku, int32_t *ldab);
+
+/* ------------------------------------------------------------------ whole solve */
+/* Full contour-integral pass (all steps on the device): nodes and coefficients,
+ * assembly, banded LU, solves with FP64 refinement, moments, block-Hankel SVD and
+ * reduced eigenproblem, Rayleigh-Ritz projection (Sec. 5.3 Eq. (narnoldi-split)) with
+ * Newton steps (Sec. 5.2 Eq. (newton)), scaled residuals (Sec. 2 Eq. (sressplit)).
+ * V_host: n x L complex probe block (column-major) or NULL (drawn from opts->seed).
+ * N >= 2 quadrature points, 1 <= L <= n, M >= 1. Errors: NEP_ERR_ARG, NEP_ERR_REGION
+ * (a rational pole or sqrt branch cut meets the closed region), NEP_ERR_CUDA,
+ * NEP_ERR_NOMEM, NEP_ERR_INTERNAL. */
+int nep_ciss_solve(nep_split_t h, const nep_region *r, int32_t N, int32_t L, int32_t M, const nep_opts *o,
+                   const double *V_host, nep_result_t *out);
+
+/* Results: nconv eigenpairs sorted by (Re, Im); lambda: complex[nconv]; X: n x nconv
+ * complex, unit 2-norm columns, largest entry real positive; resid: eta per pair.
+ * Pointers stay valid until nep_result_free. */
+int nep_result_get(nep_result_t r, int32_t *nconv, const double **lambda, const double **X, const double **resid,
+                   int32_t *hankel_rank, int32_t *flags);
+typedef struct {
+    int32_t n, N, L, M, precision;
+    int32_t hankel_rank;    /* m */
+    int32_t basis_rank;     /* Rayleigh-Ritz basis dimension */
+    int32_t ncandidates;    /* Newton starts */
+    int32_t max_sweeps;     /* refinement sweeps of the slowest point */
+    int32_t flags;
+    double max_backward;    /* max over points of the last measured backward error */
+    double ms_assemble, ms_factor, ms_solve, ms_moments, ms_extract, ms_total;
+} nep_result_info_t;
+int nep_result_info(nep_result_t r, nep_result_info_t *info);
+/* Singular values of the Hankel matrix (L*M of them, descending). */
+int nep_result_hankel_sigma(nep_result_t r, const double **sigma, int32_t *count);
+int nep_result_free(nep_result_t r);
+const char *nep_last_error(void);
+
+/* ------------------------------------------------------------------ device-resident plan */
+/* A plan owns the device workspace of one (operator, region, N, L, M, opts) solve so
+ * that repeated solves allocate nothing. nep_plan_execute reads V from device memory
+ * (n x L complex128, column-major) and leaves all results on the device;
+ * nep_plan_result copies them into a new result object. One plan serves one solve
+ * at a time (calls on one plan must not overlap). */
+int nep_plan_create(nep_split_t h, const nep_region *r, int32_t N, int32_t L, int32_t M, const nep_opts *o,
+                    nep_plan_t *out);
+int nep_plan_execute(nep_plan_t p, const void *V_dev, void *stream);
+int nep_plan_result(nep_plan_t p, nep_result_t *out);
+int nep_plan_destroy(nep_plan_t p);
+/* Device buffers of a plan (for inspection/tests): name in {"F","coef","ab","ipiv","info",
+ * "Y","S","mu","sigma","tnorm","beta","sweeps"}; returns the device pointer and its bytes. */
+int nep_plan_buffer(nep_plan_t p, const char *name, void **dev_ptr, size_t *bytes);
+
+/* ------------------------------------------------------------------ step entry points */
+/* Trapezoid nodes on Gamma (host): theta_j = 2 pi (j + 1/2)/N, z_j, weights
+ * w_j = (b cos theta_j + i a sin theta_j)/N, zeta_j = (z_j - c)/a; each complex[N]. */
+int nep_nodes(const nep_region *r, int32_t N, double *z, double *w, double *zeta);
+/* F[i + l*j] = f_i(z_j) (host, complex[l*N]); dF likewise with f_i'. dF may be NULL. */
+int nep_coefficients(nep_split_t h, int32_t N, const double *z, double *F, double *dF);
+/* Kernel (a): band storage of T(z_j) = sum_i F[i,j] A_i for npts points (F_dev complex[l*npts]
+ * on the device). Row-oriented band: entry (r, k), r-kl <= k <= r+ku, of point j at
+ * ab[j*n*ldab + r*ldab + (k - r + kl)], other entries of the row zero; complex64
+ * (precision MIXED) or complex128 (FP64). tnorm_dev[j] = ||T(z_j)||_inf (may be NULL). */
+int nep_assemble_band(nep_split_t h, int32_t npts, const double *F_dev, int32_t precision, void *ab_dev,
+                      double *tnorm_dev, void *stream);
+/* Kernel (b): in-place banded LU with partial pivoting of npts assembled bands
+ * (pivot: max |Re|+|Im| within kl rows, first index on ties). Output layout per row c:
+ * ab[c*ldab + t] = U(c, c+t) for t in [0, kl+ku]; ab[c*ldab + kl+ku+1 + i] = L(c+1+i, c)
+ * for i in [0, kl). ipiv_dev[j*n + c] = pivot row (0-based). info_dev[j] = 0 or
+ * 1 + first column with an exactly zero pivot. */
+int nep_band_factor(nep_split_t h, int32_t npts, int32_t precision, void *ab_dev, int32_t *ipiv_dev,
+                    int32_t *info_dev, void *stream);
+/* Kernel (b): solve T(z_j) X_j = B_j with the factors, in place on B (npts x n x L,
+ * column-major per point, element type of the precision). */
+int nep_band_solve(nep_split_t h, int32_t npts, int32_t precision, const void *ab_dev, const int32_t *ipiv_dev,
+                   int32_t L, void *B_dev, void *stream);
+/* Kernel (c): FP64 split-form residual R_j = V - T(z_j) Y_j (npts x n x L complex128). */
+int nep_split_residual(nep_split_t h, int32_t npts, const double *F_dev, int32_t L, const double *V_dev,
+                       const double *Y_dev, double *R_dev, void *stream);
+/* Kernel (d): S_k = sum_j coef[j + N*k] Y_j for k < K (Y: N x n x L, S: K x n x L complex128);
+ * j summed in ascending order. */
+int nep_moments(int32_t n, int32_t L, int32_t N, int32_t K, const double *coef_dev, const double *Y_dev, double *S_dev,
+                void *stream);
+/* One-sided Jacobi SVD (FP64, device): A (rows x cols complex, column-major, rows >= cols)
+ * is overwritten by U Sigma; W_dev (cols x cols) receives W with A_in W = U Sigma; sigma
+ * descending with the columns of A and W permuted to match. */
+int nep_jacobi_svd(int32_t rows, int32_t cols, double *A_dev, double *W_dev, double *sigma_dev, void *stream);
+/* Eigenvalues and eigenvectors of a small complex matrix (m x m, FP64, device):
+ * Hessenberg reduction and shifted QR. evec_dev may be NULL. */
+int nep_small_eig(int32_t m, const double *A_dev, double *eval_dev, double *evec_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NEP_CISS_H */

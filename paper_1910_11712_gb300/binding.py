@@ -1,0 +1,359 @@
+"""ctypes binding of libnepciss.so: the same entry points as include/nep_ciss.h.
+
+Argument marshalling only: every numerical step runs inside the CUDA library. If the
+library is missing, ``load()`` raises; there is no CPU fallback. Device buffers are passed
+as raw pointers (e.g. ``torch.Tensor.data_ptr()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+c_int32, c_int64, c_double, c_void_p, c_size_t = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+P_double = ctypes.POINTER(c_double)
+
+NEP_OK = 0
+NEP_ERR_ARG, NEP_ERR_CUDA, NEP_ERR_REGION, NEP_ERR_NOMEM, NEP_ERR_UNSUPPORTED, NEP_ERR_INTERNAL = -1, -2, -3, -4, -5, -6
+NEP_WARN_SATURATED, NEP_WARN_REFINE, NEP_WARN_SINGULAR_NODE, NEP_WARN_NEWTON = 1, 2, 4, 8
+NEP_PREC_FP64, NEP_PREC_MIXED = 0, 1
+FN_KIND = {"rational": 0, "exp": 1, "sqrt": 2, "combine": 3}
+FN_OP = {"add": 0, "mul": 1, "div": 2, "compose": 3}
+
+
+class NepCsr(ctypes.Structure):
+    _fields_ = [("n_rows", c_int32), ("n_cols", c_int32), ("rowptr", ctypes.POINTER(c_int64)),
+                ("col", ctypes.POINTER(c_int32)), ("val_re", P_double), ("val_im", P_double)]
+
+
+class NepFn(ctypes.Structure):
+    pass
+
+
+NepFn._fields_ = [("kind", c_int32), ("alpha_re", c_double), ("alpha_im", c_double), ("beta_re", c_double),
+                  ("beta_im", c_double), ("shift_re", c_double), ("shift_im", c_double), ("nnum", c_int32),
+                  ("nden", c_int32), ("num", P_double), ("den", P_double), ("op", c_int32),
+                  ("a", ctypes.POINTER(NepFn)), ("b", ctypes.POINTER(NepFn))]
+
+
+class NepRegion(ctypes.Structure):
+    _fields_ = [("center_re", c_double), ("center_im", c_double), ("a", c_double), ("b", c_double)]
+
+
+class NepOpts(ctypes.Structure):
+    _fields_ = [("precision", c_int32), ("rank_tol", c_double), ("basis_tol", c_double), ("refine_tol", c_double),
+                ("step_tol", c_double), ("refine_max", c_int32), ("eig_tol", c_double), ("newton_max", c_int32),
+                ("newton_tol", c_double), ("seed", ctypes.c_uint64)]
+
+
+class NepResultInfo(ctypes.Structure):
+    _fields_ = [("n", c_int32), ("N", c_int32), ("L", c_int32), ("M", c_int32), ("precision", c_int32),
+                ("hankel_rank", c_int32), ("basis_rank", c_int32), ("ncandidates", c_int32),
+                ("max_sweeps", c_int32), ("flags", c_int32), ("max_backward", c_double),
+                ("ms_assemble", c_double), ("ms_factor", c_double), ("ms_solve", c_double),
+                ("ms_moments", c_double), ("ms_extract", c_double), ("ms_total", c_double)]
+
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "nep_opts_default": (None, [ctypes.POINTER(NepOpts)]),
+    "nep_create_split": (c_int32, [c_int32, c_int32, ctypes.POINTER(NepCsr), ctypes.POINTER(NepFn), ctypes.POINTER(c_void_p)]),
+    "nep_destroy": (c_int32, [c_void_p]),
+    "nep_split_info": (c_int32, [c_void_p] + [ctypes.POINTER(c_int32)] * 5),
+    "nep_ciss_solve": (c_int32, [c_void_p, ctypes.POINTER(NepRegion), c_int32, c_int32, c_int32, ctypes.POINTER(NepOpts),
+                                 c_void_p, ctypes.POINTER(c_void_p)]),
+    "nep_result_get": (c_int32, [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(P_double), ctypes.POINTER(P_double),
+                                 ctypes.POINTER(P_double), ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
+    "nep_result_info": (c_int32, [c_void_p, ctypes.POINTER(NepResultInfo)]),
+    "nep_result_hankel_sigma": (c_int32, [c_void_p, ctypes.POINTER(P_double), ctypes.POINTER(c_int32)]),
+    "nep_result_free": (c_int32, [c_void_p]),
+    "nep_last_error": (ctypes.c_char_p, []),
+    "nep_plan_create": (c_int32, [c_void_p, ctypes.POINTER(NepRegion), c_int32, c_int32, c_int32, ctypes.POINTER(NepOpts),
+                                  ctypes.POINTER(c_void_p)]),
+    "nep_plan_execute": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "nep_plan_result": (c_int32, [c_void_p, ctypes.POINTER(c_void_p)]),
+    "nep_plan_destroy": (c_int32, [c_void_p]),
+    "nep_plan_buffer": (c_int32, [c_void_p, ctypes.c_char_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_size_t)]),
+    "nep_nodes": (c_int32, [ctypes.POINTER(NepRegion), c_int32, c_void_p, c_void_p, c_void_p]),
+    "nep_coefficients": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "nep_assemble_band": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "nep_band_factor": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "nep_band_solve": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
+    "nep_split_residual": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "nep_moments": (c_int32, [c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "nep_jacobi_svd": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "nep_small_eig": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+}
+
+_lib = None
+
+
+class NepError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"nep error {code}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Loads libnepciss.so (building it first when asked). Raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"{path} is missing: build it with paper_1910_11712_gb300.build.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fnc = getattr(lib, name)
+        fnc.restype = res
+        fnc.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(rc: int):
+    if rc != NEP_OK:
+        raise NepError(rc, load().nep_last_error().decode())
+    return rc
+
+
+def ptr(x) -> int:
+    """Device or host address of a torch tensor / numpy array / int."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+# ------------------------------------------------------------------ marshalling helpers
+class _Keep:
+    """Keeps numpy buffers referenced while a C call reads them."""
+
+    def __init__(self):
+        self.refs = []
+
+    def arr(self, a, dtype):
+        a = np.ascontiguousarray(a, dtype=dtype)
+        self.refs.append(a)
+        return a
+
+
+def _cplx_array(keep, vals):
+    a = keep.arr(np.array([complex(v) for v in vals], dtype=np.complex128).view(np.float64), np.float64)
+    return a.ctypes.data_as(P_double)
+
+
+def _fn_struct(keep, spec) -> NepFn:
+    f = NepFn()
+    f.kind = FN_KIND[spec["kind"]]
+    al, be = complex(spec.get("alpha", 1.0)), complex(spec.get("beta", 1.0))
+    sh = complex(spec.get("shift", 0.0))
+    f.alpha_re, f.alpha_im, f.beta_re, f.beta_im = al.real, al.imag, be.real, be.imag
+    f.shift_re, f.shift_im = sh.real, sh.imag
+    if spec["kind"] == "rational":
+        f.nnum = len(spec["num"])
+        f.num = _cplx_array(keep, spec["num"])
+        den = spec.get("den")
+        f.nden = 0 if den is None else len(den)
+        f.den = _cplx_array(keep, den) if den is not None else P_double()
+    if spec["kind"] == "combine":
+        f.op = FN_OP[spec["op"]]
+        fa, fb = _fn_struct(keep, spec["a"]), _fn_struct(keep, spec["b"])
+        keep.refs += [fa, fb]
+        f.a = ctypes.pointer(fa)
+        f.b = ctypes.pointer(fb)
+    return f
+
+
+def region_struct(region) -> NepRegion:
+    c = complex(region["center"])
+    return NepRegion(c.real, c.imag, float(region["a"]), float(region["b"]))
+
+
+def opts_struct(**kw) -> NepOpts:
+    o = NepOpts()
+    load().nep_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if v is not None:
+            setattr(o, k, v)
+    return o
+
+
+class Split:
+    """Split operator T(z) = sum_i A_i f_i(z) on the device (nep_create_split)."""
+
+    def __init__(self, mats, fns):
+        import scipy.sparse as sp
+        lib = load()
+        keep = _Keep()
+        n = mats[0].shape[0]
+        csrs = (NepCsr * len(mats))()
+        for i, A in enumerate(mats):
+            A = sp.csr_matrix(A)
+            A.sort_indices()
+            rp = keep.arr(A.indptr, np.int64)
+            ci = keep.arr(A.indices, np.int32)
+            re = keep.arr(np.real(A.data), np.float64)
+            csrs[i].n_rows, csrs[i].n_cols = A.shape
+            csrs[i].rowptr = rp.ctypes.data_as(ctypes.POINTER(c_int64))
+            csrs[i].col = ci.ctypes.data_as(ctypes.POINTER(c_int32))
+            csrs[i].val_re = re.ctypes.data_as(P_double)
+            if np.iscomplexobj(A.data) and np.any(np.imag(A.data) != 0):
+                im = keep.arr(np.imag(A.data), np.float64)
+                csrs[i].val_im = im.ctypes.data_as(P_double)
+        fs = (NepFn * len(fns))()
+        for i, spec in enumerate(fns):
+            fs[i] = _fn_struct(keep, spec)
+        h = c_void_p()
+        check(lib.nep_create_split(n, len(mats), csrs, fs, ctypes.byref(h)))
+        self.handle = h
+        self.n = n
+        self.nterms = len(mats)
+        info = [c_int32() for _ in range(5)]
+        check(lib.nep_split_info(h, *[ctypes.byref(x) for x in info]))
+        _, _, self.kl, self.ku, self.ldab = (x.value for x in info)
+
+    @classmethod
+    def from_problem(cls, problem):
+        return cls(problem.mats, problem.fns)
+
+    def close(self):
+        if self.handle:
+            load().nep_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _result_dict(res) -> dict:
+    lib = load()
+    nconv, m, flags = c_int32(), c_int32(), c_int32()
+    lam_p, X_p, eta_p = P_double(), P_double(), P_double()
+    check(lib.nep_result_get(res, ctypes.byref(nconv), ctypes.byref(lam_p), ctypes.byref(X_p), ctypes.byref(eta_p),
+                             ctypes.byref(m), ctypes.byref(flags)))
+    info = NepResultInfo()
+    check(lib.nep_result_info(res, ctypes.byref(info)))
+    k = nconv.value
+    n = info.n
+    lam = np.ctypeslib.as_array(lam_p, (2 * k,)).copy().view(np.complex128) if k else np.zeros(0, np.complex128)
+    X = (np.ctypeslib.as_array(X_p, (2 * n * k,)).copy().view(np.complex128).reshape(k, n).T
+         if k else np.zeros((n, 0), np.complex128))
+    eta = np.ctypeslib.as_array(eta_p, (k,)).copy() if k else np.zeros(0)
+    sp_, cnt = P_double(), c_int32()
+    check(lib.nep_result_hankel_sigma(res, ctypes.byref(sp_), ctypes.byref(cnt)))
+    sigma = np.ctypeslib.as_array(sp_, (cnt.value,)).copy() if cnt.value else np.zeros(0)
+    out = {"lam": lam, "X": np.asfortranarray(X), "eta": eta, "m": m.value, "flags": flags.value, "sigma": sigma,
+           "info": {f: getattr(info, f) for f, _ in NepResultInfo._fields_}}
+    lib.nep_result_free(res)
+    return out
+
+
+def ciss_solve(split: Split, region, N, L, M, V=None, **opts) -> dict:
+    """nep_ciss_solve with host buffers: V (n x L complex128) or None (seeded draw)."""
+    lib = load()
+    r = region_struct(region)
+    o = opts_struct(**opts)
+    vptr = None
+    if V is not None:
+        Vf = np.asfortranarray(V, dtype=np.complex128)
+        vptr = Vf.ctypes.data
+    res = c_void_p()
+    check(lib.nep_ciss_solve(split.handle, ctypes.byref(r), N, L, M, ctypes.byref(o), vptr, ctypes.byref(res)))
+    return _result_dict(res)
+
+
+class Plan:
+    """Device-resident solve (nep_plan_*): allocate once, execute many times."""
+
+    def __init__(self, split: Split, region, N, L, M, **opts):
+        lib = load()
+        self.split = split
+        r = region_struct(region)
+        o = opts_struct(**opts)
+        h = c_void_p()
+        check(lib.nep_plan_create(split.handle, ctypes.byref(r), N, L, M, ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h
+
+    def execute(self, V_dev, stream=0):
+        check(load().nep_plan_execute(self.handle, ptr(V_dev), stream))
+
+    def result(self) -> dict:
+        res = c_void_p()
+        check(load().nep_plan_result(self.handle, ctypes.byref(res)))
+        return _result_dict(res)
+
+    def buffer(self, name: str):
+        p, b = c_void_p(), c_size_t()
+        check(load().nep_plan_buffer(self.handle, name.encode(), ctypes.byref(p), ctypes.byref(b)))
+        return p.value, b.value
+
+    def close(self):
+        if self.handle:
+            load().nep_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ step entry points
+def nodes(region, N):
+    z, w, zeta = (np.zeros(N, np.complex128) for _ in range(3))
+    r = region_struct(region)
+    check(load().nep_nodes(ctypes.byref(r), N, z.ctypes.data, w.ctypes.data, zeta.ctypes.data))
+    return z, w, zeta
+
+
+def coefficients(split: Split, z):
+    z = np.ascontiguousarray(z, dtype=np.complex128)
+    F = np.zeros((len(z), split.nterms), np.complex128)
+    dF = np.zeros_like(F)
+    check(load().nep_coefficients(split.handle, len(z), z.ctypes.data, F.ctypes.data, dF.ctypes.data))
+    return F.T.copy(), dF.T.copy()
+
+
+def assemble_band(split, npts, F_dev, precision, ab_dev, tnorm_dev=None, stream=0):
+    check(load().nep_assemble_band(split.handle, npts, ptr(F_dev), precision, ptr(ab_dev), ptr(tnorm_dev), stream))
+
+
+def band_factor(split, npts, precision, ab_dev, ipiv_dev, info_dev, stream=0):
+    check(load().nep_band_factor(split.handle, npts, precision, ptr(ab_dev), ptr(ipiv_dev), ptr(info_dev), stream))
+
+
+def band_solve(split, npts, precision, ab_dev, ipiv_dev, L, B_dev, stream=0):
+    check(load().nep_band_solve(split.handle, npts, precision, ptr(ab_dev), ptr(ipiv_dev), L, ptr(B_dev), stream))
+
+
+def split_residual(split, npts, F_dev, L, V_dev, Y_dev, R_dev, stream=0):
+    check(load().nep_split_residual(split.handle, npts, ptr(F_dev), L, ptr(V_dev), ptr(Y_dev), ptr(R_dev), stream))
+
+
+def moments(n, L, N, K, coef_dev, Y_dev, S_dev, stream=0):
+    check(load().nep_moments(n, L, N, K, ptr(coef_dev), ptr(Y_dev), ptr(S_dev), stream))
+
+
+def jacobi_svd(rows, cols, A_dev, W_dev, sigma_dev, stream=0):
+    check(load().nep_jacobi_svd(rows, cols, ptr(A_dev), ptr(W_dev), ptr(sigma_dev), stream))
+
+
+def small_eig(m, A_dev, eval_dev, evec_dev=None, stream=0):
+    check(load().nep_small_eig(m, ptr(A_dev), ptr(eval_dev), ptr(evec_dev), stream))

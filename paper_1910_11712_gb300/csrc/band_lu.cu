@@ -1,0 +1,586 @@
+// Kernel (b): batched complex banded LU with partial pivoting and the banded solves.
+//
+// The contour method needs one factorisation of T(z_j) per quadrature point (the
+// factorisations that dominate the cost of every solver in Sec. 5, cf. Table 3's "PC build").
+// All points are independent, so one CTA factors one point and the whole batch runs in
+// one launch.
+//
+// Band layout (row-oriented, in place). Before the LU, row r of a point holds
+// A(r, r-kl+t) at ab[r*ldab + t], t in [0, kl+ku]. The LU writes, for every row c,
+//   ab[c*ldab + t]            = U(c, c+t),       t in [0, kv]   (kv = kl + ku)
+//   ab[c*ldab + kv + 1 + i]   = L(c+1+i, c),     i in [0, kl)
+// which only reuses slots of rows that have already entered the elimination window.
+//
+// Elimination order (right-looking, unblocked, partial pivoting): at step c the active
+// window is rows c..c+kl by columns c..c+kv; the pivot is the first row maximising
+// |Re|+|Im| in column c; rows c and p swap across the window; the multipliers
+// l = a(:,c)/a(c,c) form column c of L; rows c+1..c+kl receive the rank-1 update
+// a(r,k) -= l(r) u(k) with u the pivot row. Row c+kl enters the window at step c (its
+// first nonzero is column c) and column c+kv enters empty (fill-in only).
+//
+// lu_reg_kernel keeps the whole (kl x kv) window in registers: row r lives in slot
+// r mod RS (lane = slot % 32), column k in slot k mod CS (warp = slot / CPW). With
+// RS == kl and CS == kv the entering row/column reuse the slots of the leaving ones, so
+// every thread updates exactly RPL x CPW elements per step (balanced). Two CTA barriers
+// per step: one after the pivot column is published, one after the multipliers are.
+// lu_glb_kernel runs the same elimination with the window in a global (L2-resident)
+// scratch array, for bands too wide for the register file.
+#include "nep_common.cuh"
+
+namespace nep {
+
+template <typename T>
+__device__ __forceinline__ cx<T> shfl_cx(cx<T> v, int src) {
+    cx<T> r;
+    r.re = __shfl_sync(0xffffffffu, v.re, src);
+    r.im = __shfl_sync(0xffffffffu, v.im, src);
+    return r;
+}
+
+__device__ __forceinline__ int posmod(int a, int m) {
+    int r = a % m;
+    return r < 0 ? r + m : r;
+}
+
+
+// Asynchronous global->shared copy of one complex element (8 or 16 bytes); completion is
+// awaited with cp_async_wait_all() before the barrier that publishes the data.
+template <typename T>
+__device__ __forceinline__ void cp_async_cx(cx<T>* smem, const cx<T>* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(cx<T>) == 16) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+    } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+    }
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// First index of the maximum of |Re|+|Im| over pcol[0..cnt-1], computed by one warp.
+// Ties resolve to the smallest index (the same rule as LAPACK's izamax).
+template <typename T>
+__device__ __forceinline__ int warp_pivot(const cx<T>* pcol, int cnt, int lane) {
+    T best = T(-1);
+    int bi = 0x7fffffff;
+    for (int i = lane; i < cnt; i += 32) {
+        T m = abs1(pcol[i]);
+        if (m > best) { best = m; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    return bi;
+}
+
+// Pivot step by warp 0: chooses the pivot among pcol[0..cnt-1], swaps it to pcol[0],
+// writes U(c,c), the multipliers (shared lvec and global L column) and ipiv.
+template <typename T>
+__device__ __forceinline__ void pivot_step(cx<T>* pcol, cx<T>* lvec, int* piv_s, int* info_s, int c, int n, int kl,
+                                           int kv, int ldab, cx<T>* ab, int* ipiv, int lane) {
+    const int cnt = min(kl, n - 1 - c) + 1;
+    int p = warp_pivot(pcol, cnt, lane);
+    cx<T> pv = pcol[p];
+    const bool zero = (pv.re == T(0) && pv.im == T(0));
+    if (zero) p = 0;
+    __syncwarp();
+    if (lane == 0 && p != 0) {
+        cx<T> t = pcol[0];
+        pcol[0] = pcol[p];
+        pcol[p] = t;
+    }
+    __syncwarp();
+    cx<T>* out = ab + (int64_t)c * ldab;
+    for (int i = lane; i < kl; i += 32) {
+        cx<T> l = mk<T>(0, 0);
+        if (!zero && c + 1 + i < n) l = cdiv(pcol[i + 1], pv);
+        lvec[i] = l;
+        out[kv + 1 + i] = l;
+    }
+    if (lane == 0) {
+        out[0] = zero ? mk<T>(0, 0) : pv;
+        ipiv[c] = c + p;
+        *piv_s = p;
+        if (zero && *info_s == 0) *info_s = c + 1;
+    }
+}
+
+template <typename T, int NW, int RPL, int CPW>
+__global__ void __launch_bounds__(NW * 32, 1)
+    lu_reg_kernel(int n, int kl, int ku, int ldab, cx<T>* __restrict__ ab_all, int* __restrict__ ipiv_all,
+                  int* __restrict__ info_all, const int* __restrict__ active) {
+    const int j = blockIdx.x;
+    if (active && !active[j]) return;
+    constexpr int RS = 32 * RPL;
+    constexpr int CS = NW * CPW;
+    const int kv = kl + ku;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cx<T>* ab = ab_all + (int64_t)j * n * ldab;
+    int* ipiv = ipiv_all + (int64_t)j * n;
+
+    __shared__ cx<T> nrow[2][CS + 1];
+    __shared__ cx<T> pcol[RS + 1];
+    __shared__ cx<T> lvec[RS];
+    __shared__ int piv_s, info_s;
+    if (threadIdx.x == 0) info_s = 0;
+
+    // window registers: a[q][p] = element (row slot lane + 32 q, column slot warp*CPW + p)
+    cx<T> a[RPL][CPW];
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+        const int r = lane + 32 * q;
+#pragma unroll
+        for (int p = 0; p < CPW; ++p) {
+            const int k = warp * CPW + p;
+            cx<T> v = mk<T>(0, 0);
+            const int t = k - r + kl;
+            if (r < kl && r < n && k < kv && k < n && t >= 0 && t <= kv) v = ab[(int64_t)r * ldab + t];
+            a[q][p] = v;
+        }
+    }
+    // row kl enters at step 0 with columns 0..kv
+    for (int t = threadIdx.x; t <= kv; t += blockDim.x) {
+        cx<T> v = mk<T>(0, 0);
+        if (kl < n && t < n) v = ab[(int64_t)kl * ldab + t];
+        nrow[0][t] = v;
+    }
+    __syncthreads();
+
+    for (int c = 0; c < n; ++c) {
+        const int buf = c & 1;
+        // (1) the owner warp publishes column c (rows c..c+kl-1), then empties the slot
+        //     that column c+kv takes over
+        {
+            const int csc = c % CS;
+            if (csc / CPW == warp) {
+                const int pc = csc % CPW;
+#pragma unroll
+                for (int p = 0; p < CPW; ++p) {
+                    if (p != pc) continue;
+#pragma unroll
+                    for (int q = 0; q < RPL; ++q) {
+                        const int rs = lane + 32 * q;
+                        const int i = posmod(rs - c, RS);
+                        if (i < kl) pcol[i] = a[q][p];
+                    }
+                }
+            }
+            const int csn = (c + kv) % CS;
+            if (csn / CPW == warp) {
+                const int pn = csn % CPW;
+#pragma unroll
+                for (int p = 0; p < CPW; ++p)
+                    if (p == pn)
+#pragma unroll
+                        for (int q = 0; q < RPL; ++q) a[q][p] = mk<T>(0, 0);
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();  // S1: pcol and nrow[buf] visible
+        // prefetch row c+1+kl (columns c+1..c+1+kv) for the next step, asynchronously
+        if (warp != 0 || NW == 1) {
+            const int r = c + 1 + kl;
+            const int t0 = (NW == 1) ? lane : threadIdx.x - 32;
+            const int ts = (NW == 1) ? 32 : blockDim.x - 32;
+            for (int t = t0; t <= kv; t += ts) {
+                if (r < n && c + 1 + t < n) cp_async_cx(&nrow[buf ^ 1][t], ab + (int64_t)r * ldab + t);
+                else nrow[buf ^ 1][t] = mk<T>(0, 0);
+            }
+        }
+        if (warp == 0) {
+            if (lane == 0) pcol[kl] = nrow[buf][0];
+            __syncwarp();
+            pivot_step(pcol, lvec, &piv_s, &info_s, c, n, kl, kv, ldab, ab, ipiv, lane);
+        }
+        __syncthreads();  // S2: pivot index and multipliers visible
+        const int prel = piv_s;
+        const cx<T>* nr = nrow[buf];
+        const int rsc = c % RS, lanec = rsc & 31, qc = rsc >> 5;
+        const int rsp = (c + prel) % RS, lanep = rsp & 31, qp = rsp >> 5;
+        const int rsn = (c + kl) % RS, lanen = rsn & 31, qn = rsn >> 5;
+        cx<T>* urow = ab + (int64_t)c * ldab;
+#pragma unroll
+        for (int p = 0; p < CPW; ++p) {
+            const int cs = warp * CPW + p;
+            const int k = c + 1 + posmod(cs - c - 1, CS);  // column held by this slot after step c
+            const bool colok = (k <= c + kv) && (k < n);
+            // value of row c in this column
+            cx<T> mine_c = a[0][p];
+#pragma unroll
+            for (int q = 1; q < RPL; ++q)
+                if (q == qc) mine_c = a[q][p];
+            const cx<T> vc = shfl_cx(mine_c, lanec);
+            const cx<T> vnew = (k - c <= kv) ? nr[k - c] : mk<T>(0, 0);
+            cx<T> u, newval;
+            if (prel == kl) {
+                u = vnew;
+                newval = vc;
+            } else {
+                newval = vnew;
+                if (prel != 0) {
+                    cx<T> mine_p = a[0][p];
+#pragma unroll
+                    for (int q = 1; q < RPL; ++q)
+                        if (q == qp) mine_p = a[q][p];
+                    u = shfl_cx(mine_p, lanep);
+                    if (lane == lanep) {
+#pragma unroll
+                        for (int q = 0; q < RPL; ++q)
+                            if (q == qp) a[q][p] = vc;
+                    }
+                } else {
+                    u = vc;
+                }
+            }
+            if (lane == lanec && colok) urow[k - c] = u;
+            if (lane == lanen) {
+#pragma unroll
+                for (int q = 0; q < RPL; ++q)
+                    if (q == qn) a[q][p] = newval;
+            }
+            if (colok) {
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) {
+                    const int rs = lane + 32 * q;
+                    const int r = c + 1 + posmod(rs - c - 1, RS);
+                    if (r <= c + kl && r < n) a[q][p] = fms(a[q][p], lvec[r - c - 1], u);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) info_all[j] = info_s;
+}
+
+// Same elimination with the window W[cs*kl + rs] (row slot r mod kl, column slot k mod kv)
+// in a per-point global scratch array. For kl = 0 the band is upper triangular and no
+// elimination happens besides copying U.
+template <typename T>
+__global__ void __launch_bounds__(1024, 1)
+    lu_glb_kernel(int n, int kl, int ku, int ldab, cx<T>* __restrict__ ab_all, int* __restrict__ ipiv_all,
+                  int* __restrict__ info_all, const int* __restrict__ active, cx<T>* __restrict__ win_all) {
+    const int j = blockIdx.x;
+    if (active && !active[j]) return;
+    const int kv = kl + ku;
+    const int RS = max(kl, 1), CS = max(kv, 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cx<T>* ab = ab_all + (int64_t)j * n * ldab;
+    int* ipiv = ipiv_all + (int64_t)j * n;
+    cx<T>* W = win_all + (int64_t)j * RS * CS;
+
+    extern __shared__ unsigned char smem_raw[];
+    cx<T>* nrow = reinterpret_cast<cx<T>*>(smem_raw);  // 2 x (kv+1)
+    cx<T>* pcol = nrow + 2 * (kv + 1);                  // kl+1
+    cx<T>* lvec = pcol + (kl + 1);                      // kl
+    cx<T>* uvec = lvec + max(kl, 1);                    // kv
+    __shared__ int piv_s, info_s;
+    if (threadIdx.x == 0) info_s = 0;
+    // initial window rows 0..kl-1, columns 0..kv-1
+    for (int64_t e = threadIdx.x; e < (int64_t)RS * CS; e += blockDim.x) {
+        const int cs = (int)(e / RS), rs = (int)(e % RS);
+        const int r = rs, k = cs, t = k - r + kl;
+        cx<T> v = mk<T>(0, 0);
+        if (r < kl && k < kv && r < n && k < n && t >= 0 && t <= kv) v = ab[(int64_t)r * ldab + t];
+        W[e] = v;
+    }
+    for (int t = threadIdx.x; t <= kv; t += blockDim.x) {
+        cx<T> v = mk<T>(0, 0);
+        if (kl < n && t < n) v = ab[(int64_t)kl * ldab + t];
+        nrow[t] = v;
+    }
+    __syncthreads();
+    for (int c = 0; c < n; ++c) {
+        cx<T>* nr = nrow + (c & 1) * (kv + 1);
+        for (int i = threadIdx.x; i < kl; i += blockDim.x) pcol[i] = W[(int64_t)(c % CS) * RS + (c + i) % RS];
+        if (threadIdx.x == 0) pcol[kl] = nr[0];
+        cp_async_wait_all();
+        __syncthreads();  // S1
+        {
+            const int r = c + 1 + kl;
+            cx<T>* nx = nrow + ((c + 1) & 1) * (kv + 1);
+            for (int t = threadIdx.x - 32; t <= kv; t += blockDim.x - 32) {
+                if (t < 0) continue;
+                if (r < n && c + 1 + t < n) cp_async_cx(nx + t, ab + (int64_t)r * ldab + t);
+                else nx[t] = mk<T>(0, 0);
+            }
+        }
+        if (warp == 0) pivot_step(pcol, lvec, &piv_s, &info_s, c, n, kl, kv, ldab, ab, ipiv, lane);
+        __syncthreads();  // S2
+        const int prel = piv_s;
+        cx<T>* urow = ab + (int64_t)c * ldab;
+        // column pass: swap rows c and c+prel, broadcast vector u, insert row c+kl
+        for (int t = threadIdx.x; t < kv; t += blockDim.x) {
+            const int k = c + 1 + t;
+            cx<T> u = mk<T>(0, 0);
+            if (k < n) {
+                const int64_t col = (int64_t)(k % CS) * RS;
+                const bool fresh = (k == c + kv);  // column entering the window: no stored values yet
+                cx<T> vc = (fresh || kl == 0) ? mk<T>(0, 0) : W[col + c % RS];
+                cx<T> vnew = nr[k - c];
+                cx<T> newval;
+                if (prel == kl) {
+                    u = vnew;
+                    newval = vc;
+                } else {
+                    newval = vnew;
+                    if (prel != 0) {
+                        const int64_t ip = col + (c + prel) % RS;
+                        u = fresh ? mk<T>(0, 0) : W[ip];
+                        W[ip] = vc;
+                    } else {
+                        u = vc;
+                    }
+                }
+                urow[1 + t] = u;
+                if (kl > 0) W[col + (c + kl) % RS] = newval;  // slot of row c (RS == kl)
+                if (fresh) {
+                    for (int i = 1; i < kl; ++i)
+                        if (i != prel) W[col + (c + i) % RS] = mk<T>(0, 0);
+                }
+            }
+            uvec[t] = u;
+        }
+        __syncthreads();  // S3
+        // rank-1 update of rows c+1..c+kl, columns c+1..c+kv
+        const int nrows = min(kl, n - 1 - c), ncols = min(kv, n - 1 - c);
+        if (nrows > 0 && ncols > 0) {
+            const int64_t tot = (int64_t)nrows * ncols;
+            for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+                const int t = (int)(e / nrows), i = (int)(e % nrows);
+                const int k = c + 1 + t, r = c + 1 + i;
+                cx<T>* w = W + (int64_t)(k % CS) * RS + r % RS;
+                *w = fms(*w, lvec[i], uvec[t]);
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) info_all[j] = info_s;
+}
+
+// ------------------------------------------------------------------ dispatch
+template <typename T, int NW, int RPL, int CPW>
+static int run_reg(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st) {
+    lu_reg_kernel<T, NW, RPL, CPW><<<npts, NW * 32, 0, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, info, active);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+
+template <typename T, int NW, int RPL>
+static int pick_cpw(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st,
+                    int cpw) {
+    switch (cpw) {
+        case 1: return run_reg<T, NW, RPL, 1>(s, npts, ab, ipiv, info, active, st);
+        case 2: return run_reg<T, NW, RPL, 2>(s, npts, ab, ipiv, info, active, st);
+        case 3: return run_reg<T, NW, RPL, 3>(s, npts, ab, ipiv, info, active, st);
+        case 4: return run_reg<T, NW, RPL, 4>(s, npts, ab, ipiv, info, active, st);
+        case 5: return run_reg<T, NW, RPL, 5>(s, npts, ab, ipiv, info, active, st);
+        case 6: return run_reg<T, NW, RPL, 6>(s, npts, ab, ipiv, info, active, st);
+        case 7: return run_reg<T, NW, RPL, 7>(s, npts, ab, ipiv, info, active, st);
+        case 8: return run_reg<T, NW, RPL, 8>(s, npts, ab, ipiv, info, active, st);
+    }
+    return NEP_ERR_INTERNAL;
+}
+
+// Register-window configuration for a band, or false if the band is too wide.
+template <typename T>
+static bool reg_config(int kl, int kv, int* nw, int* rpl, int* cpw) {
+    if (kl < 1 || kl > 64 || kv < 1) return false;
+    *rpl = (kl + 31) / 32;
+    *nw = sizeof(T) == 4 ? 32 : 16;
+    *cpw = (kv + *nw - 1) / *nw;
+    const int maxcpw = sizeof(T) == 4 ? 4 : 8;
+    return *cpw <= maxcpw;
+}
+
+template <typename T>
+int launch_band_lu(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st) {
+    if (npts <= 0) return NEP_OK;
+    const int kv = s.kl + s.ku;
+    int nw, rpl, cpw;
+    if (reg_config<T>(s.kl, kv, &nw, &rpl, &cpw)) {
+        if (nw == 32) {
+            if (rpl == 1) return pick_cpw<T, 32, 1>(s, npts, ab, ipiv, info, active, st, cpw);
+            return pick_cpw<T, 32, 2>(s, npts, ab, ipiv, info, active, st, cpw);
+        } else {
+            if (rpl == 1) return pick_cpw<T, 16, 1>(s, npts, ab, ipiv, info, active, st, cpw);
+            return pick_cpw<T, 16, 2>(s, npts, ab, ipiv, info, active, st, cpw);
+        }
+    }
+    // global-window path: per-point scratch of max(kl,1) x max(kv,1) elements
+    const int RS = s.kl > 1 ? s.kl : 1, CS = kv > 1 ? kv : 1;
+    const size_t win_bytes = sizeof(cx<T>) * (size_t)RS * CS * npts;
+    cx<T>* win = nullptr;
+    NEP_CUDA(cudaMallocAsync((void**)&win, win_bytes, st));
+    const size_t smem = sizeof(cx<T>) * (size_t)(2 * (kv + 1) + (s.kl + 1) + (s.kl > 1 ? s.kl : 1) + CS);
+    if (smem > 48 * 1024)
+        NEP_CUDA(cudaFuncSetAttribute(lu_glb_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    lu_glb_kernel<T><<<npts, 1024, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, info, active, win);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(win, st);
+    if (e != cudaSuccess) return cuda_fail(e, "lu_glb_kernel", __FILE__, __LINE__);
+    return NEP_OK;
+}
+
+template int launch_band_lu<float>(const SplitDev&, int, cx<float>*, int*, int*, const int*, cudaStream_t);
+template int launch_band_lu<double>(const SplitDev&, int, cx<double>*, int*, int*, const int*, cudaStream_t);
+
+// ------------------------------------------------------------------ banded solves
+// One warp per right-hand side column, one CTA per (point, group of columns). Forward
+// sweep: the (kl+1)-row window of the current right-hand side lives in shared memory
+// (slot r mod (kl+1)); at step c rows c and ipiv[c] swap, x_c is final, rows c+1..c+kl
+// take x_c times the L column and row c+kl+1 enters the freed slot. Backward sweep
+// (columns n-1..0): x_c = w_c / U(c,c) and rows c-kv..c-1 take x_c times U column c;
+// window of kv+1 rows. L columns (contiguous) and U columns (gathered from U rows,
+// coalesced by rows) are staged in shared memory in chunks of CH steps shared by all warps.
+template <typename T>
+__global__ void __launch_bounds__(512)
+    band_solve_kernel(int n, int kl, int ku, int ldab, const cx<T>* __restrict__ ab_all,
+                      const int* __restrict__ ipiv_all, int L, cx<T>* __restrict__ B_all,
+                      const int* __restrict__ active, int CH) {
+    const int j = blockIdx.x;
+    if (active && !active[j]) return;
+    const int kv = kl + ku;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const int col = blockIdx.y * nwarps + warp;
+    const bool has_col = col < L;
+    const cx<T>* ab = ab_all + (int64_t)j * n * ldab;
+    const int* ipiv = ipiv_all + (int64_t)j * n;
+    cx<T>* b = B_all + ((int64_t)j * L + (has_col ? col : 0)) * n;
+
+    extern __shared__ unsigned char smem_raw[];
+    const int RF = kl + 1, RB = kv + 1;
+    const int WIN = RF > RB ? RF : RB;
+    const int wide = kv > kl ? kv : (kl > 0 ? kl : 1);
+    cx<T>* win = reinterpret_cast<cx<T>*>(smem_raw) + (int64_t)warp * WIN;
+    cx<T>* nb = reinterpret_cast<cx<T>*>(smem_raw) + (int64_t)nwarps * WIN + (int64_t)warp * CH;
+    cx<T>* stage = reinterpret_cast<cx<T>*>(smem_raw) + (int64_t)nwarps * (WIN + CH);
+    cx<T>* diag = stage + (int64_t)CH * wide;
+    int* pst = reinterpret_cast<int*>(diag + CH);
+
+    // ---- forward: row interchanges and unit lower L
+    for (int i = lane; i < RF; i += 32) win[i] = (has_col && i < n) ? b[i] : mk<T>(0, 0);
+    for (int c0 = 0; c0 < n; c0 += CH) {
+        const int cn = min(CH, n - c0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < cn * kl; e += blockDim.x) {
+            const int cc = e / kl, i = e % kl;
+            stage[e] = ab[(int64_t)(c0 + cc) * ldab + kv + 1 + i];
+        }
+        for (int e = threadIdx.x; e < cn; e += blockDim.x) pst[e] = ipiv[c0 + e] - (c0 + e);
+        if (has_col)
+            for (int cc = lane; cc < cn; cc += 32) {
+                const int rn = c0 + cc + kl + 1;
+                nb[cc] = rn < n ? b[rn] : mk<T>(0, 0);
+            }
+        __syncthreads();
+        if (has_col) {
+            for (int cc = 0; cc < cn; ++cc) {
+                const int c = c0 + cc;
+                const int p = pst[cc];
+                if (p != 0 && lane == 0) {
+                    const int s0 = c % RF, s1 = (c + p) % RF;
+                    cx<T> t = win[s0];
+                    win[s0] = win[s1];
+                    win[s1] = t;
+                }
+                __syncwarp();
+                const cx<T> xc = win[c % RF];
+                const cx<T>* lc = stage + cc * kl;
+                for (int i = lane; i < kl; i += 32) {
+                    const int r = c + 1 + i;
+                    if (r < n) {
+                        cx<T>* w = win + r % RF;
+                        *w = fms(*w, lc[i], xc);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    b[c] = xc;
+                    win[c % RF] = nb[cc];
+                }
+                __syncwarp();
+            }
+        }
+    }
+    // ---- backward: U with bandwidth kv
+    __syncthreads();
+    for (int i = lane; i < RB; i += 32) {
+        const int r = n - 1 - i;
+        if (r >= 0) win[r % RB] = has_col ? b[r] : mk<T>(0, 0);
+    }
+    __syncwarp();
+    for (int c1 = n - 1; c1 >= 0; c1 -= CH) {
+        const int cn = min(CH, c1 + 1);
+        const int cbase = c1 - cn + 1;  // chunk columns cbase..c1
+        __syncthreads();
+        // stage[cc*kv + i] = U(c-1-i, c), c = cbase + cc, gathered from U rows (coalesced by row)
+        const int rlo = cbase - kv, rhi = c1 - 1;
+        const int nr = rhi - rlo + 1;
+        for (int e = threadIdx.x; e < nr * cn; e += blockDim.x) {
+            const int ri = e / cn, cc = e % cn;
+            const int r = rlo + ri, c = cbase + cc, t = c - r;
+            if (r >= 0 && t >= 1 && t <= kv) stage[cc * kv + (t - 1)] = ab[(int64_t)r * ldab + t];
+        }
+        for (int e = threadIdx.x; e < cn; e += blockDim.x) diag[e] = ab[(int64_t)(cbase + e) * ldab];
+        if (has_col)
+            for (int cc = lane; cc < cn; cc += 32) {
+                const int rn = cbase + cc - kv - 1;
+                nb[cc] = rn >= 0 ? b[rn] : mk<T>(0, 0);
+            }
+        __syncthreads();
+        if (has_col) {
+            for (int cc = cn - 1; cc >= 0; --cc) {
+                const int c = cbase + cc;
+                const cx<T> xc = cdiv(win[c % RB], diag[cc]);
+                __syncwarp();
+                const cx<T>* uc = stage + cc * kv;
+                for (int i = lane; i < kv; i += 32) {
+                    const int r = c - 1 - i;
+                    if (r >= 0) {
+                        cx<T>* w = win + r % RB;
+                        *w = fms(*w, uc[i], xc);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    b[c] = xc;
+                    win[c % RB] = nb[cc];
+                }
+                __syncwarp();
+            }
+        }
+    }
+}
+
+template <typename T>
+int launch_band_solve(const SplitDev& s, int npts, const cx<T>* ab, const int* ipiv, int L, cx<T>* B,
+                      const int* active, cudaStream_t st) {
+    if (npts <= 0 || L <= 0) return NEP_OK;
+    const int kv = s.kl + s.ku;
+    const int wpb = L < 16 ? L : 16;
+    const int gy = (L + wpb - 1) / wpb;
+    const int WIN = (s.kl + 1) > (kv + 1) ? (s.kl + 1) : (kv + 1);
+    const int wide = kv > s.kl ? kv : (s.kl > 0 ? s.kl : 1);
+    const size_t budget = 200 * 1024;
+    int CH = 32;
+    auto bytes = [&](int ch) {
+        return sizeof(cx<T>) * ((size_t)wpb * (WIN + ch) + (size_t)ch * wide + ch) + sizeof(int) * ch;
+    };
+    while (CH > 1 && bytes(CH) > budget) CH >>= 1;
+    const size_t smem = bytes(CH);
+    if (smem > 227 * 1024) return NEP_ERR_UNSUPPORTED;
+    NEP_CUDA(cudaFuncSetAttribute(band_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid(npts, gy);
+    band_solve_kernel<T><<<grid, wpb * 32, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, L, B, active, CH);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+
+template int launch_band_solve<float>(const SplitDev&, int, const cx<float>*, const int*, int, cx<float>*, const int*,
+                                      cudaStream_t);
+template int launch_band_solve<double>(const SplitDev&, int, const cx<double>*, const int*, int, cx<double>*,
+                                       const int*, cudaStream_t);
+
+}  // namespace nep

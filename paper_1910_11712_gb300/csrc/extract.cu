@@ -1,0 +1,916 @@
+// Extraction of the eigenpairs from the contour moments (all on the device, FP64 unless noted):
+//   * zgemm_kernel      dense complex products (column-major, op(A) in {A, A^H}), split-K
+//                       with a fixed-order reduction so results never depend on scheduling;
+//   * jacobi_kernel     one-sided (Hestenes) Jacobi SVD, cooperative across CTAs: round-robin
+//                       pairings, one warp per column pair, a bounded grid barrier per round
+//                       (FP64 throughput per SM is low on this part, so the pairs of a round
+//                       are spread over many SMs);
+//   * schur_eig_kernel  complex Hessenberg reduction + single-shift QR + triangular
+//                       eigenvectors, one warp, used in FP32 for the reduced Hankel matrix
+//                       (its eigenvalues only seed FP64 Newton, its eigenvectors only fix a
+//                       basis of an already determined span);
+//   * newton_kernel     Newton's method (Sec. 5.2 Eq. (newton)) on the projected split form
+//                       sum_i f_i(lambda) B_i y = 0 (Sec. 5.3 Eq. (narnoldi-split)), bordered
+//                       by the normalisation u^H y = 1, one CTA per candidate;
+//   * residual/select   scaled residual eta (Sec. 2 Eq. (sressplit), infinity norms of the A_i
+//                       as in Sec. 6), inside test, duplicate removal and ordering.
+#include <cooperative_groups.h>
+
+#include "nep_common.cuh"
+
+namespace nep {
+
+// ------------------------------------------------------------------ dense products
+constexpr int GB = 32, GK = 8;
+
+__global__ void __launch_bounds__(256) zgemm_kernel(int M, int N, int K, int opA, const zd* __restrict__ A, int lda,
+                                                    const zd* __restrict__ B, int ldb, zd* __restrict__ C, int ldc,
+                                                    int kchunk, int64_t part_stride) {
+    __shared__ zd As[GK][GB + 1];
+    __shared__ zd Bs[GK][GB + 1];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int m0 = blockIdx.x * GB, n0 = blockIdx.y * GB;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    zd acc[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) acc[a][b] = mk(0.0, 0.0);
+    for (int k0 = kb; k0 < ke; k0 += GK) {
+        for (int t = threadIdx.x; t < GK * GB; t += 256) {
+            const int kk = t % GK, mm = t / GK;
+            const int gm = m0 + mm, gk = k0 + kk;
+            zd v = mk(0.0, 0.0);
+            if (gm < M && gk < ke) v = opA == 0 ? A[gm + (int64_t)lda * gk] : conj(A[gk + (int64_t)lda * gm]);
+            As[kk][mm] = v;
+            const int nn = t / GK;
+            const int gn = n0 + nn;
+            zd w = mk(0.0, 0.0);
+            if (gn < N && gk < ke) w = B[gk + (int64_t)ldb * gn];
+            Bs[kk][nn] = w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            const zd a0 = As[kk][tx], a1 = As[kk][tx + 16];
+            const zd b0 = Bs[kk][ty], b1 = Bs[kk][ty + 16];
+            acc[0][0] = fma_(acc[0][0], a0, b0);
+            acc[1][0] = fma_(acc[1][0], a1, b0);
+            acc[0][1] = fma_(acc[0][1], a0, b1);
+            acc[1][1] = fma_(acc[1][1], a1, b1);
+        }
+        __syncthreads();
+    }
+    zd* Cz = C + (int64_t)blockIdx.z * part_stride;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int gm = m0 + tx + 16 * a, gn = n0 + ty + 16 * b;
+            if (gm < M && gn < N) Cz[gm + (int64_t)ldc * gn] = acc[a][b];
+        }
+}
+
+__global__ void zgemm_reduce_kernel(int M, int N, int splits, const zd* __restrict__ part, zd* __restrict__ C, int ldc) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)M * N) return;
+    const int m = (int)(t % M), n = (int)(t / M);
+    zd acc = mk(0.0, 0.0);
+    for (int z = 0; z < splits; ++z) acc = acc + part[(int64_t)z * M * N + t];
+    C[m + (int64_t)ldc * n] = acc;
+}
+
+// C = op(A) B. part: workspace of splits*M*N elements when K is long (nullptr => no split).
+int zgemm(int M, int N, int K, int opA, const zd* A, int lda, const zd* B, int ldb, zd* C, int ldc, zd* part,
+          size_t part_elems, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return NEP_OK;
+    const int tiles = ceil_div(M, GB) * ceil_div(N, GB);
+    int splits = 1;
+    if (part && K > 256 && tiles < 152) {
+        splits = std::min(ceil_div(K, 256), std::max(1, 304 / tiles));
+        while (splits > 1 && (size_t)splits * M * N > part_elems) --splits;
+    }
+    const int kchunk = ceil_div(ceil_div(K, splits), GK) * GK;
+    splits = ceil_div(K, kchunk);
+    if (splits < 1) splits = 1;
+    dim3 grid(ceil_div(M, GB), ceil_div(N, GB), splits);
+    if (splits == 1) {
+        zgemm_kernel<<<grid, 256, 0, st>>>(M, N, K, opA, A, lda, B, ldb, C, ldc, kchunk, 0);
+        NEP_CHECK_LAUNCH();
+        return NEP_OK;
+    }
+    zgemm_kernel<<<grid, 256, 0, st>>>(M, N, K, opA, A, lda, B, ldb, part, M, kchunk, (int64_t)M * N);
+    NEP_CHECK_LAUNCH();
+    zgemm_reduce_kernel<<<ceil_div((int64_t)M * N, 256), 256, 0, st>>>(M, N, splits, part, C, ldc);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+
+// ------------------------------------------------------------------ grid barrier
+// Sense counter barrier for a cooperative launch (all CTAs co-resident). Every wait is
+// bounded: after ~1 s of polling the CTA records an error and continues.
+struct GridBar {
+    unsigned int* count;
+    unsigned int* gen;
+    int* err;
+};
+
+__device__ __forceinline__ void grid_barrier(GridBar b) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* vg = b.gen;
+        const unsigned int g = *vg;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(b.count, 1u);
+        if (arrived == gridDim.x * gridDim.y * gridDim.z - 1) {
+            atomicExch(b.count, 0u);
+            __threadfence();
+            atomicAdd(b.gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*vg == g) {
+                if (++spins > (1ll << 24)) {
+                    atomicExch(b.err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ one-sided Jacobi SVD
+// A (rows x cols, column-major) is rotated in place until its columns are mutually
+// orthogonal: A V = U Sigma. Rotation of columns (p, q) with alpha = |a_p|^2,
+// beta = |a_q|^2, gamma = a_p^H a_q = |gamma| e^{i phi}: zeta = (beta - alpha)/(2|gamma|),
+// t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t,
+//   a_p <- c a_p - s e^{-i phi} a_q,   a_q <- s e^{i phi} a_p + c a_q   (same on V).
+// Pairs per round follow the circle method over P = cols rounded up to even.
+__global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __restrict__ A, zd* __restrict__ Vm,
+                                                     int max_sweeps, double tol, int* __restrict__ flags,
+                                                     int* __restrict__ sweeps_out, GridBar bar) {
+    const int lane = threadIdx.x & 31;
+    const int gwarp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int P = cols + (cols & 1);
+    // V = I
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)cols * cols;
+         t += (int64_t)gridDim.x * blockDim.x)
+        Vm[t] = mk((t % cols) == (t / cols) ? 1.0 : 0.0, 0.0);
+    grid_barrier(bar);
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) flags[(sweep + 1) & 1] = 0;
+        for (int round = 0; round < P - 1; ++round) {
+            for (int pi = gwarp; pi < P / 2; pi += nwarps) {
+                int p, q;
+                {
+                    auto pos = [&](int k) { return k == 0 ? 0 : ((k - 1 + round) % (P - 1)) + 1; };
+                    p = pos(pi);
+                    q = pos(P - 1 - pi);
+                }
+                if (p >= cols || q >= cols) continue;
+                if (p > q) { const int t = p; p = q; q = t; }
+                zd* ap = A + (int64_t)p * rows;
+                zd* aq = A + (int64_t)q * rows;
+                double al = 0.0, be = 0.0;
+                zd ga = mk(0.0, 0.0);
+                for (int i = lane; i < rows; i += 32) {
+                    const zd x = ap[i], y = aq[i];
+                    al += norm2(x);
+                    be += norm2(y);
+                    ga = fmac(ga, x, y);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    al += __shfl_xor_sync(0xffffffffu, al, o);
+                    be += __shfl_xor_sync(0xffffffffu, be, o);
+                    ga.re += __shfl_xor_sync(0xffffffffu, ga.re, o);
+                    ga.im += __shfl_xor_sync(0xffffffffu, ga.im, o);
+                }
+                const double g = hypot(ga.re, ga.im);
+                if (!(g > tol * sqrt(al * be)) || al == 0.0 || be == 0.0) continue;
+                const double zeta = (be - al) / (2.0 * g);
+                const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                const zd e = mk(ga.re / g, ga.im / g);  // e^{i phi}
+                const zd se = mk(s * e.re, s * e.im), sec = conj(se);
+                for (int i = lane; i < rows; i += 32) {
+                    const zd x = ap[i], y = aq[i];
+                    ap[i] = c * x - sec * y;
+                    aq[i] = se * x + c * y;
+                }
+                zd* vp = Vm + (int64_t)p * cols;
+                zd* vq = Vm + (int64_t)q * cols;
+                for (int i = lane; i < cols; i += 32) {
+                    const zd x = vp[i], y = vq[i];
+                    vp[i] = c * x - sec * y;
+                    vq[i] = se * x + c * y;
+                }
+                if (lane == 0) atomicOr(&flags[sweep & 1], 1);
+            }
+            grid_barrier(bar);
+        }
+        const int any = *((volatile int*)&flags[sweep & 1]);
+        if (!any) break;
+        grid_barrier(bar);  // everyone has read the flag before it is cleared again
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_out = sweep + 1;
+}
+
+// sigma_i = |a_i|, descending order; U(:, r) = a_(i)/sigma, W(:, r) = V(:, i) for rank r of i.
+__global__ void svd_finish_kernel(int rows, int cols, const zd* __restrict__ A, const zd* __restrict__ Vm,
+                                  zd* __restrict__ U, zd* __restrict__ W, double* __restrict__ sigma) {
+    extern __shared__ double nrm[];
+    for (int i = threadIdx.x; i < cols; i += blockDim.x) {
+        double s = 0.0;
+        const zd* a = A + (int64_t)i * rows;
+        for (int r = 0; r < rows; ++r) s += norm2(a[r]);
+        nrm[i] = sqrt(s);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cols; i += blockDim.x) {
+        int rank = 0;
+        for (int k = 0; k < cols; ++k) rank += (nrm[k] > nrm[i]) || (nrm[k] == nrm[i] && k < i);
+        sigma[rank] = nrm[i];
+    }
+    __syncthreads();
+    // copy columns in rank order (each thread a row, loop over columns)
+    for (int i = 0; i < cols; ++i) {
+        int rank = 0;
+        for (int k = 0; k < cols; ++k) rank += (nrm[k] > nrm[i]) || (nrm[k] == nrm[i] && k < i);
+        const double inv = nrm[i] > 0 ? 1.0 / nrm[i] : 0.0;
+        if (U)
+            for (int r = threadIdx.x; r < rows; r += blockDim.x) U[(int64_t)rank * rows + r] = inv * A[(int64_t)i * rows + r];
+        for (int r = threadIdx.x; r < cols; r += blockDim.x) W[(int64_t)rank * cols + r] = Vm[(int64_t)i * cols + r];
+    }
+}
+
+// A is destroyed; U (rows x cols) may be nullptr; W (cols x cols); sigma (cols).
+int jacobi_svd(int rows, int cols, zd* A, zd* U, zd* W, double* sigma, JacobiWork w, cudaStream_t st) {
+    if (cols <= 0) return NEP_OK;
+    NEP_CUDA(cudaMemsetAsync(w.flags, 0, 2 * sizeof(int), st));
+    NEP_CUDA(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st));
+    const int P = cols + (cols & 1);
+    int dev = 0, sms = 0;
+    NEP_CUDA(cudaGetDevice(&dev));
+    NEP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int per_sm = 0;
+    NEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, 256, 0));
+    int blocks = std::max(1, std::min(ceil_div(P / 2, 8), sms * std::max(per_sm, 1)));
+    GridBar gb{w.bar, w.bar + 1, w.err};
+    int max_sweeps = 40;
+    double tol = 1e-15;
+    void* args[] = {&rows, &cols, &A, &w.Vm, &max_sweeps, &tol, &w.flags, &w.sweeps, &gb};
+    NEP_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(256), args, 0, st));
+    svd_finish_kernel<<<1, 256, sizeof(double) * cols, st>>>(rows, cols, A, w.Vm, U, W, sigma);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+
+// ------------------------------------------------------------------ small complex eigenproblem
+// One warp. H (m x m, leading dimension ld) and Z live in shared or global memory. Steps:
+// Householder reduction to Hessenberg form (Z accumulates the reflectors), single-shift QR
+// sweeps with Wilkinson shifts and deflation on |h(k,k-1)| <= eps (|h(k,k)| + |h(k-1,k-1)|),
+// then eigenvectors of the triangular Schur factor by back substitution, mapped by Z.
+template <typename T>
+__device__ void givens(cx<T> x, cx<T> y, T* c, cx<T>* s) {
+    // [c s; -conj(s) c] [x; y] = [r; 0]
+    const T ax = hypot(x.re, x.im), ay = hypot(y.re, y.im);
+    if (ay == T(0)) { *c = T(1); *s = mk<T>(0, 0); return; }
+    if (ax == T(0)) { *c = T(0); *s = conj(cdiv(y, mk<T>(ay, 0))); return; }
+    const T nrm = hypot(ax, ay);
+    *c = ax / nrm;
+    const cx<T> ph = mk<T>(x.re / ax, x.im / ax);
+    *s = (T(1) / nrm) * (ph * conj(y));
+}
+
+template <typename T>
+__global__ void schur_eig_kernel(int m, const zd* __restrict__ Ain, zd* __restrict__ eval, zd* __restrict__ evec,
+                                 int* __restrict__ status, cx<T>* gbuf, int use_smem) {
+    extern __shared__ unsigned char sraw[];
+    const int ld = m + 1;
+    cx<T>* H = use_smem ? reinterpret_cast<cx<T>*>(sraw) : gbuf;
+    cx<T>* Z = H + (int64_t)m * ld;
+    cx<T>* v = Z + (int64_t)m * ld;  // m
+    const int lane = threadIdx.x;
+    const T eps = sizeof(T) == 4 ? T(6e-8) : T(1.2e-16);
+    auto h = [&](int i, int j) -> cx<T>& { return H[i + (int64_t)ld * j]; };
+    auto z = [&](int i, int j) -> cx<T>& { return Z[i + (int64_t)ld * j]; };
+    for (int t = lane; t < m * m; t += 32) {
+        const int i = t % m, j = t / m;
+        h(i, j) = cvt<T>(Ain[i + (int64_t)m * j]);
+        z(i, j) = mk<T>(i == j ? T(1) : T(0), T(0));
+    }
+    __syncwarp();
+    // Hessenberg reduction
+    for (int k = 0; k + 2 < m; ++k) {
+        T nx = 0;
+        for (int i = k + 1 + lane; i < m; i += 32) nx += norm2(h(i, k));
+        for (int o = 16; o > 0; o >>= 1) nx += __shfl_xor_sync(0xffffffffu, nx, o);
+        nx = sqrt(nx);
+        if (nx == T(0)) continue;
+        const cx<T> x0 = h(k + 1, k);
+        const T a0 = hypot(x0.re, x0.im);
+        const cx<T> ph = a0 > 0 ? mk<T>(x0.re / a0, x0.im / a0) : mk<T>(1, 0);
+        // v = x + ph*|x| e1, reflector I - 2 v v^H / (v^H v)
+        for (int i = k + 1 + lane; i < m; i += 32) v[i] = h(i, k);
+        __syncwarp();
+        if (lane == 0) v[k + 1] = v[k + 1] + nx * ph;
+        __syncwarp();
+        T vv = 0;
+        for (int i = k + 1 + lane; i < m; i += 32) vv += norm2(v[i]);
+        for (int o = 16; o > 0; o >>= 1) vv += __shfl_xor_sync(0xffffffffu, vv, o);
+        const T sc = T(2) / vv;
+        // left: rows k+1.., columns k..m-1 (lanes over columns)
+        for (int j = k + lane; j < m; j += 32) {
+            cx<T> s = mk<T>(0, 0);
+            for (int i = k + 1; i < m; ++i) s = fmac(s, v[i], h(i, j));
+            s = sc * s;
+            for (int i = k + 1; i < m; ++i) h(i, j) = fms(h(i, j), v[i], s);
+        }
+        __syncwarp();
+        // right: columns k+1.., all rows (lanes over rows), also Z
+        for (int i = lane; i < m; i += 32) {
+            cx<T> s = mk<T>(0, 0), sz = mk<T>(0, 0);
+            for (int j = k + 1; j < m; ++j) {
+                s = fma_(s, h(i, j), v[j]);
+                sz = fma_(sz, z(i, j), v[j]);
+            }
+            s = sc * s;
+            sz = sc * sz;
+            for (int j = k + 1; j < m; ++j) {
+                h(i, j) = fms(h(i, j), s, conj(v[j]));
+                z(i, j) = fms(z(i, j), sz, conj(v[j]));
+            }
+        }
+        __syncwarp();
+        for (int i = k + 2 + lane; i < m; i += 32) h(i, k) = mk<T>(0, 0);
+        __syncwarp();
+    }
+    // shifted QR
+    int ihi = m - 1, iter = 0, since = 0, fail = 0;
+    const int maxit = 60 * m + 100;
+    while (ihi > 0) {
+        if (iter++ > maxit) { fail = 1; break; }
+        int l = ihi;
+        while (l > 0) {
+            const cx<T> sub = h(l, l - 1);
+            const T ref = abs1(h(l, l)) + abs1(h(l - 1, l - 1));
+            if (abs1(sub) <= eps * (ref > 0 ? ref : T(1))) break;
+            --l;
+        }
+        __syncwarp();
+        if (l > 0) {
+            if (lane == 0) h(l, l - 1) = mk<T>(0, 0);
+            __syncwarp();
+        }
+        if (l == ihi) {
+            --ihi;
+            since = 0;
+            continue;
+        }
+        ++since;
+        // Wilkinson shift from the trailing 2x2 of the active block
+        const cx<T> a = h(ihi - 1, ihi - 1), b = h(ihi - 1, ihi), c2 = h(ihi, ihi - 1), d = h(ihi, ihi);
+        cx<T> mu;
+        if (since % 11 == 10) {
+            mu = d + mk<T>(T(0.75) * abs1(c2), T(0));  // exceptional shift
+        } else {
+            const cx<T> tr = a + d, det = a * d - b * c2;
+            const cx<T> disc = csqrt_(tr * tr - T(4) * det);
+            const cx<T> r1 = T(0.5) * (tr + disc), r2 = T(0.5) * (tr - disc);
+            mu = norm2(r1 - d) < norm2(r2 - d) ? r1 : r2;
+        }
+        cx<T> x = h(l, l) - mu, y = h(l + 1, l);
+        for (int k = l; k < ihi; ++k) {
+            T cs;
+            cx<T> sn;
+            givens(x, y, &cs, &sn);
+            // rows k, k+1 from column max(l, k-1) to m-1
+            for (int j = max(l, k - 1) + lane; j < m; j += 32) {
+                const cx<T> p = h(k, j), q = h(k + 1, j);
+                h(k, j) = cs * p + sn * q;
+                h(k + 1, j) = cs * q - conj(sn) * p;
+            }
+            __syncwarp();
+            // columns k, k+1 for rows 0..min(k+2, ihi); Z all rows
+            const int rlim = min(k + 2, ihi);
+            for (int i = lane; i <= rlim; i += 32) {
+                const cx<T> p = h(i, k), q = h(i, k + 1);
+                h(i, k) = cs * p + conj(sn) * q;
+                h(i, k + 1) = cs * q - sn * p;
+            }
+            for (int i = lane; i < m; i += 32) {
+                const cx<T> p = z(i, k), q = z(i, k + 1);
+                z(i, k) = cs * p + conj(sn) * q;
+                z(i, k + 1) = cs * q - sn * p;
+            }
+            __syncwarp();
+            if (k + 1 < ihi) {
+                x = h(k + 1, k);
+                y = h(k + 2, k);
+            }
+        }
+    }
+    __syncwarp();
+    for (int i = lane; i < m; i += 32) eval[i] = cvt<double>(h(i, i));
+    if (lane == 0 && status) *status = fail;
+    if (!evec) return;
+    // eigenvectors of the upper triangular Schur factor, then x = Z v
+    T hn = 0;
+    for (int t = lane; t < m * m; t += 32) {
+        const int i = t % m, j = t / m;
+        if (i <= j) hn = fmax(hn, abs1(h(i, j)));
+    }
+    for (int o = 16; o > 0; o >>= 1) hn = fmax(hn, __shfl_xor_sync(0xffffffffu, hn, o));
+    const T small = eps * (hn > 0 ? hn : T(1));
+    for (int e = 0; e < m; ++e) {
+        const cx<T> lam = h(e, e);
+        for (int i = lane; i < m; i += 32) v[i] = i < e ? -h(i, e) : (i == e ? mk<T>(1, 0) : mk<T>(0, 0));
+        __syncwarp();
+        for (int k = e - 1; k >= 0; --k) {
+            cx<T> den = h(k, k) - lam;
+            if (abs1(den) < small) den = mk<T>(small, 0);
+            const cx<T> vk = cdiv(v[k], den);
+            __syncwarp();
+            if (lane == 0) v[k] = vk;
+            for (int i = lane; i < k; i += 32) v[i] = fms(v[i], h(i, k), vk);
+            __syncwarp();
+        }
+        for (int i = lane; i < m; i += 32) {
+            cx<T> s = mk<T>(0, 0);
+            for (int k = 0; k <= e; ++k) s = fma_(s, z(i, k), v[k]);
+            evec[i + (int64_t)m * e] = cvt<double>(s);
+        }
+        __syncwarp();
+    }
+}
+
+template <typename T>
+int small_eig(int m, const zd* A, zd* eval, zd* evec, int* status, void* gbuf, cudaStream_t st) {
+    if (m <= 0) return NEP_OK;
+    const size_t bytes = sizeof(cx<T>) * ((size_t)2 * m * (m + 1) + m);
+    const int use_smem = bytes <= 200 * 1024;
+    if (use_smem)
+        NEP_CUDA(cudaFuncSetAttribute(schur_eig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    else if (!gbuf)
+        return NEP_ERR_INTERNAL;
+    schur_eig_kernel<T><<<1, 32, use_smem ? bytes : 0, st>>>(m, A, eval, evec, status, (cx<T>*)gbuf, use_smem);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+template int small_eig<float>(int, const zd*, zd*, zd*, int*, void*, cudaStream_t);
+template int small_eig<double>(int, const zd*, zd*, zd*, int*, void*, cudaStream_t);
+
+// ------------------------------------------------------------------ helpers
+// Scale column c of X (rows x cols) by 1/|x_c|_2 (optionally fixing the phase so the first
+// entry of largest modulus is real positive); nrm_out[c] = |x_c|_2 before scaling.
+__global__ void __launch_bounds__(256) normalize_columns_kernel(int rows, zd* __restrict__ X, int fix_phase,
+                                                                double* __restrict__ nrm_out) {
+    __shared__ double red[32];
+    __shared__ int redi[32];
+    __shared__ double rmax[32];
+    const int c = blockIdx.x;
+    zd* x = X + (int64_t)c * rows;
+    double s = 0.0, best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+        const double a = norm2(x[i]);
+        s += a;
+        if (a > best) { best = a; bi = i; }
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { red[w] = s; rmax[w] = best; redi[w] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ts = 0.0, tb = -1.0;
+        int ti = 0x7fffffff;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            ts += red[k];
+            if (rmax[k] > tb || (rmax[k] == tb && redi[k] < ti)) { tb = rmax[k]; ti = redi[k]; }
+        }
+        red[0] = ts;
+        redi[0] = ti;
+    }
+    __syncthreads();
+    const double nrm = sqrt(red[0]);
+    if (nrm_out && threadIdx.x == 0) nrm_out[c] = nrm;
+    if (nrm == 0.0) return;
+    zd f = mk(1.0 / nrm, 0.0);
+    if (fix_phase) {
+        const zd p = x[redi[0]];
+        const double ap = hypot(p.re, p.im);
+        f = mk(p.re / (ap * nrm), -p.im / (ap * nrm));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) x[i] = x[i] * f;
+}
+
+// out_i = A_i Q for every term i (Q: n x k), out: nterms x n x k
+__global__ void term_spmm_kernel(SplitDev s, int k, const zd* __restrict__ Q, zd* __restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nk = (int64_t)s.n * k;
+    if (t >= nk * s.nterms) return;
+    const int i = (int)(t / nk);
+    const int64_t rc = t % nk;
+    const int r = (int)(rc % s.n), c = (int)(rc / s.n);
+    zd acc = mk(0.0, 0.0);
+    for (int64_t e = s.rowptr[r]; e < s.rowptr[r + 1]; ++e) {
+        const zd a = mk(s.val[(int64_t)i * s.nnz + e], s.val_im ? s.val_im[(int64_t)i * s.nnz + e] : 0.0);
+        acc = fma_(acc, a, Q[(int64_t)c * s.n + s.col[e]]);
+    }
+    out[t] = acc;
+}
+
+// ------------------------------------------------------------------ Newton on the projected NEP
+// One CTA per candidate; J = [[B(l), B'(l) y], [y^H, 0]] factored by Gaussian elimination
+// with partial pivoting each step (FP64), in shared memory when it fits.
+__global__ void __launch_bounds__(256) newton_kernel(SplitDev s, int k, const zd* __restrict__ Bs,
+                                                     const zd* __restrict__ lam0, const zd* __restrict__ Y0, int ldy0,
+                                                     zd c, double rad, int maxit, double tol,
+                                                     zd* __restrict__ lam_out, zd* __restrict__ Yout,
+                                                     int* __restrict__ ok_out, int* __restrict__ its_out,
+                                                     zd* __restrict__ gscratch, int use_smem) {
+    extern __shared__ unsigned char sraw[];
+    const int cand = blockIdx.x;
+    const int K1 = k + 1;
+    zd* J = use_smem ? reinterpret_cast<zd*>(sraw) : gscratch + (int64_t)cand * ((int64_t)K1 * K1 + 3 * K1 + 64);
+    zd* rhs = J + (int64_t)K1 * K1;
+    zd* y = rhs + K1;
+    zd* g = y + K1;
+    zd* fv = g + K1;  // 2 * nterms <= 64
+    __shared__ double redd[32];
+    __shared__ int piv_s;
+    __shared__ int stop_s;
+    __shared__ zd lam_s;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+    // y = y0 / |y0|
+    double ss = 0.0;
+    for (int i = tid; i < k; i += blockDim.x) {
+        y[i] = Y0[(int64_t)cand * ldy0 + i];
+        ss += norm2(y[i]);
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) redd[w] = ss;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0;
+        for (int q = 0; q < nw; ++q) t += redd[q];
+        redd[0] = t;
+        lam_s = lam0[cand];
+        stop_s = 0;
+    }
+    __syncthreads();
+    {
+        const double inv = redd[0] > 0 ? 1.0 / sqrt(redd[0]) : 0.0;
+        for (int i = tid; i < k; i += blockDim.x) y[i] = inv * y[i];
+    }
+    int ok = redd[0] > 0, it = 0;
+    __syncthreads();
+    for (it = 1; it <= maxit && ok; ++it) {
+        if (tid < s.nterms) {
+            const FnEval fe = fn_eval(s.fn_nodes, s.fn_coef, s.fn_root[tid], lam_s);
+            fv[tid] = fe.f;
+            fv[s.nterms + tid] = fe.df;
+        }
+        __syncthreads();
+        // J(0:k, 0:k) = B(l); g = B'(l) y; rhs = -B(l) y
+        for (int e = tid; e < k * k; e += blockDim.x) {
+            const int r = e % k, q = e / k;
+            zd b = mk(0.0, 0.0);
+            for (int i = 0; i < s.nterms; ++i) b = fma_(b, fv[i], Bs[(int64_t)i * k * k + e]);
+            J[r + (int64_t)K1 * q] = b;
+        }
+        for (int r = tid; r < k; r += blockDim.x) {
+            zd bd = mk(0.0, 0.0), gd = mk(0.0, 0.0);
+            for (int q = 0; q < k; ++q) {
+                zd b = mk(0.0, 0.0), d = mk(0.0, 0.0);
+                for (int i = 0; i < s.nterms; ++i) {
+                    const zd bi = Bs[(int64_t)i * k * k + r + (int64_t)k * q];
+                    b = fma_(b, fv[i], bi);
+                    d = fma_(d, fv[s.nterms + i], bi);
+                }
+                bd = fma_(bd, b, y[q]);
+                gd = fma_(gd, d, y[q]);
+            }
+            rhs[r] = -bd;
+            J[r + (int64_t)K1 * k] = gd;
+        }
+        for (int q = tid; q < k; q += blockDim.x) J[k + (int64_t)K1 * q] = conj(y[q]);
+        if (tid == 0) {
+            J[k + (int64_t)K1 * k] = mk(0.0, 0.0);
+            rhs[k] = mk(0.0, 0.0);
+        }
+        __syncthreads();
+        // Gaussian elimination with partial pivoting on [J | rhs]
+        int singular = 0;
+        for (int col = 0; col < K1; ++col) {
+            if (w == 0) {
+                double best = -1.0;
+                int bi = col;
+                for (int r = col + lane; r < K1; r += 32) {
+                    const double a = abs1(J[r + (int64_t)K1 * col]);
+                    if (a > best) { best = a; bi = r; }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                }
+                if (lane == 0) piv_s = best > 0 ? bi : -1;
+            }
+            __syncthreads();
+            const int p = piv_s;
+            if (p < 0) { singular = 1; break; }
+            if (p != col) {
+                for (int q = col + tid; q < K1; q += blockDim.x) {
+                    const zd t = J[col + (int64_t)K1 * q];
+                    J[col + (int64_t)K1 * q] = J[p + (int64_t)K1 * q];
+                    J[p + (int64_t)K1 * q] = t;
+                }
+                if (tid == 0) {
+                    const zd t = rhs[col];
+                    rhs[col] = rhs[p];
+                    rhs[p] = t;
+                }
+            }
+            __syncthreads();
+            const zd pv = J[col + (int64_t)K1 * col];
+            for (int r = col + 1 + tid; r < K1; r += blockDim.x) g[r] = cdiv(J[r + (int64_t)K1 * col], pv);
+            __syncthreads();
+            const int nr = K1 - col - 1;
+            for (int e = tid; e < nr * (nr + 1); e += blockDim.x) {
+                const int r = col + 1 + e % nr, q = col + 1 + e / nr;
+                if (q < K1) J[r + (int64_t)K1 * q] = fms(J[r + (int64_t)K1 * q], g[r], J[col + (int64_t)K1 * q]);
+                else rhs[r] = fms(rhs[r], g[r], rhs[col]);
+            }
+            __syncthreads();
+        }
+        if (singular) { ok = 0; break; }
+        // back substitution (one warp)
+        if (w == 0) {
+            for (int r = K1 - 1; r >= 0; --r) {
+                zd acc = mk(0.0, 0.0);
+                for (int q = r + 1 + lane; q < K1; q += 32) acc = fma_(acc, J[r + (int64_t)K1 * q], rhs[q]);
+                for (int o = 16; o > 0; o >>= 1) {
+                    acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+                    acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+                }
+                if (lane == 0) rhs[r] = cdiv(rhs[r] - acc, J[r + (int64_t)K1 * r]);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        // update and normalise
+        double s2 = 0.0;
+        for (int i = tid; i < k; i += blockDim.x) {
+            y[i] = y[i] + rhs[i];
+            s2 += norm2(y[i]);
+        }
+        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        __syncthreads();
+        if (lane == 0) redd[w] = s2;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0;
+            for (int q = 0; q < nw; ++q) t += redd[q];
+            redd[0] = t;
+            const zd dl = rhs[k];
+            const zd nl = lam_s + dl;
+            lam_s = nl;
+            const double al = hypot(nl.re, nl.im);
+            int st = 0;
+            if (!isfinite(nl.re) || !isfinite(nl.im) || hypot(nl.re - c.re, nl.im - c.im) > rad || !(t > 0)) st = 2;
+            else if (hypot(dl.re, dl.im) <= tol * fmax(1.0, al)) st = 1;
+            stop_s = st;
+        }
+        __syncthreads();
+        const double inv = redd[0] > 0 ? 1.0 / sqrt(redd[0]) : 0.0;
+        for (int i = tid; i < k; i += blockDim.x) y[i] = inv * y[i];
+        __syncthreads();
+        if (stop_s == 2) { ok = 0; break; }
+        if (stop_s == 1) break;
+    }
+    for (int i = tid; i < k; i += blockDim.x) Yout[(int64_t)cand * k + i] = y[i];
+    if (tid == 0) {
+        lam_out[cand] = lam_s;
+        ok_out[cand] = ok;
+        its_out[cand] = min(it, maxit);
+    }
+}
+
+int launch_newton(const SplitDev& s, int k, int ncand, const zd* Bs, const zd* lam0, const zd* Y0, int ldy0, zd c,
+                  double rad, int maxit, double tol, zd* lam_out, zd* Yout, int* ok, int* its, zd* gscratch,
+                  cudaStream_t st) {
+    if (ncand <= 0) return NEP_OK;
+    const int K1 = k + 1;
+    const size_t bytes = sizeof(zd) * ((size_t)K1 * K1 + 3 * K1 + 64);
+    const int use_smem = bytes <= 200 * 1024;
+    if (use_smem)
+        NEP_CUDA(cudaFuncSetAttribute(newton_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    else if (!gscratch)
+        return NEP_ERR_INTERNAL;
+    newton_kernel<<<ncand, 256, use_smem ? bytes : 0, st>>>(s, k, Bs, lam0, Y0, ldy0, c, rad, maxit, tol, lam_out, Yout,
+                                                            ok, its, gscratch, use_smem);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+
+// ------------------------------------------------------------------ residuals and selection
+// eta_c = |sum_i f_i(l_c) A_i x_c|_2 / (sum_i |f_i(l_c)| |A_i|_inf |x_c|_2), one CTA per pair.
+__global__ void __launch_bounds__(256) eta_kernel(SplitDev s, const zd* __restrict__ lam, const zd* __restrict__ X,
+                                                  double* __restrict__ eta) {
+    __shared__ zd fv[32];
+    __shared__ double red[2][32];
+    const int cnd = blockIdx.x;
+    if (threadIdx.x < s.nterms) fv[threadIdx.x] = fn_eval(s.fn_nodes, s.fn_coef, s.fn_root[threadIdx.x], lam[cnd]).f;
+    __syncthreads();
+    const zd* x = X + (int64_t)cnd * s.n;
+    double rr = 0.0, xx = 0.0;
+    for (int r = threadIdx.x; r < s.n; r += blockDim.x) {
+        zd acc = mk(0.0, 0.0);
+        for (int64_t e = s.rowptr[r]; e < s.rowptr[r + 1]; ++e) {
+            zd t = mk(0.0, 0.0);
+            for (int i = 0; i < s.nterms; ++i) {
+                const zd a = mk(s.val[(int64_t)i * s.nnz + e], s.val_im ? s.val_im[(int64_t)i * s.nnz + e] : 0.0);
+                t = fma_(t, fv[i], a);
+            }
+            acc = fma_(acc, t, x[s.col[e]]);
+        }
+        rr += norm2(acc);
+        xx += norm2(x[r]);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        rr += __shfl_xor_sync(0xffffffffu, rr, o);
+        xx += __shfl_xor_sync(0xffffffffu, xx, o);
+    }
+    if (lane == 0) { red[0][w] = rr; red[1][w] = xx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a += red[0][q]; b += red[1][q]; }
+        double den = 0;
+        for (int i = 0; i < s.nterms; ++i) den += hypot(fv[i].re, fv[i].im) * s.norms[i];
+        eta[cnd] = (den > 0 && b > 0) ? sqrt(a) / (den * sqrt(b)) : INFINITY;
+    }
+}
+
+// Keep candidates inside the ellipse with eta <= eig_tol and a converged Newton run; drop
+// duplicates (|dl| <= 1e-10 max(1,|l|) and |x_a^H x_b| >= 1 - 1e-8; keep the smaller eta);
+// order by (Re, Im). order_out[0] = count, then the selected candidate indices.
+__global__ void select_kernel(int ncand, const zd* __restrict__ lam, const double* __restrict__ eta,
+                              const int* __restrict__ ok, const zd* __restrict__ G, zd c, double ea, double eb,
+                              double eig_tol, int* __restrict__ order_out) {
+    extern __shared__ int sidx[];
+    int* keep = sidx;            // ncand
+    int* byeta = sidx + ncand;   // ncand
+    if (threadIdx.x != 0) return;
+    int nk = 0;
+    for (int a = 0; a < ncand; ++a) {
+        const zd d = lam[a] - c;
+        const double q = (d.re / ea) * (d.re / ea) + (d.im / eb) * (d.im / eb);
+        if (ok[a] && q < 1.0 && eta[a] <= eig_tol) byeta[nk++] = a;
+    }
+    // insertion sort by eta (stable)
+    for (int i = 1; i < nk; ++i) {
+        const int v = byeta[i];
+        int p = i - 1;
+        while (p >= 0 && eta[byeta[p]] > eta[v]) { byeta[p + 1] = byeta[p]; --p; }
+        byeta[p + 1] = v;
+    }
+    int na = 0;
+    for (int i = 0; i < nk; ++i) {
+        const int a = byeta[i];
+        bool dup = false;
+        for (int q = 0; q < na && !dup; ++q) {
+            const int b = keep[q];
+            const zd d = lam[a] - lam[b];
+            const double la = hypot(lam[a].re, lam[a].im);
+            const zd ip = G[a + (int64_t)ncand * b];
+            if (hypot(d.re, d.im) <= 1e-10 * fmax(1.0, la) && hypot(ip.re, ip.im) >= 1.0 - 1e-8) dup = true;
+        }
+        if (!dup) keep[na++] = a;
+    }
+    // order by (Re, Im)
+    for (int i = 1; i < na; ++i) {
+        const int v = keep[i];
+        int p = i - 1;
+        while (p >= 0 && (lam[keep[p]].re > lam[v].re || (lam[keep[p]].re == lam[v].re && lam[keep[p]].im > lam[v].im))) {
+            keep[p + 1] = keep[p];
+            --p;
+        }
+        keep[p + 1] = v;
+    }
+    order_out[0] = na;
+    for (int i = 0; i < na; ++i) order_out[1 + i] = keep[i];
+}
+
+}  // namespace nep
+
+namespace nep {
+
+// ------------------------------------------------------------------ small helpers and launchers
+__global__ void scale_cols_kernel(int rows, int cols, zd* __restrict__ X, int ld, const double* __restrict__ s,
+                                  int mode) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)rows * cols) return;
+    const int r = (int)(t % rows), c = (int)(t / rows);
+    const double v = s[c];
+    const double f = mode == 0 ? (v > 0 ? 1.0 / v : 0.0) : (v > 0 ? 1.0 / sqrt(v) : 0.0);
+    X[r + (int64_t)ld * c] = f * X[r + (int64_t)ld * c];
+}
+
+__global__ void scale_rows_kernel(int rows, int cols, zd* __restrict__ X, int ld, const double* __restrict__ s) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)rows * cols) return;
+    const int r = (int)(t % rows), c = (int)(t / rows);
+    const double v = s[r];
+    X[r + (int64_t)ld * c] = (v > 0 ? 1.0 / v : 0.0) * X[r + (int64_t)ld * c];
+}
+
+__global__ void candidates_kernel(int m, const zd* __restrict__ theta, zd c, double a, zd* __restrict__ lam) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) lam[t] = c + a * theta[t];
+}
+
+__global__ void fill_int_kernel(int n, int* __restrict__ p, int v) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) p[t] = v;
+}
+
+// count of sigma_i > tol * sigma_0 (sigma descending)
+__global__ void rank_kernel(int n, const double* __restrict__ sigma, double tol, int* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int m = 0;
+    if (n > 0 && sigma[0] > 0)
+        for (int i = 0; i < n; ++i) m += sigma[i] > tol * sigma[0];
+    *out = m;
+}
+
+int launch_scale_cols(int rows, int cols, zd* X, int ld, const double* s, int mode, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return NEP_OK;
+    scale_cols_kernel<<<ceil_div((int64_t)rows * cols, 256), 256, 0, st>>>(rows, cols, X, ld, s, mode);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+int launch_scale_rows(int rows, int cols, zd* X, int ld, const double* s, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return NEP_OK;
+    scale_rows_kernel<<<ceil_div((int64_t)rows * cols, 256), 256, 0, st>>>(rows, cols, X, ld, s);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+int launch_candidates(int m, const zd* theta, zd c, double a, zd* lam, cudaStream_t st) {
+    if (m <= 0) return NEP_OK;
+    candidates_kernel<<<ceil_div(m, 128), 128, 0, st>>>(m, theta, c, a, lam);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+int launch_fill_int(int n, int* p, int v, cudaStream_t st) {
+    if (n <= 0) return NEP_OK;
+    fill_int_kernel<<<ceil_div(n, 256), 256, 0, st>>>(n, p, v);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+int launch_rank(int n, const double* sigma, double tol, int* out, cudaStream_t st) {
+    rank_kernel<<<1, 32, 0, st>>>(n, sigma, tol, out);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+int launch_normalize_columns(int rows, int cols, zd* X, int fix_phase, double* nrm, cudaStream_t st) {
+    if (cols <= 0) return NEP_OK;
+    normalize_columns_kernel<<<cols, 256, 0, st>>>(rows, X, fix_phase, nrm);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+int launch_term_spmm(const SplitDev& s, int k, const zd* Q, zd* out, cudaStream_t st) {
+    if (k <= 0) return NEP_OK;
+    const int64_t tot = (int64_t)s.n * k * s.nterms;
+    term_spmm_kernel<<<ceil_div(tot, 256), 256, 0, st>>>(s, k, Q, out);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+int launch_eta(const SplitDev& s, int ncand, const zd* lam, const zd* X, double* eta, cudaStream_t st) {
+    if (ncand <= 0) return NEP_OK;
+    eta_kernel<<<ncand, 256, 0, st>>>(s, lam, X, eta);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+int launch_select(int ncand, const zd* lam, const double* eta, const int* ok, const zd* G, zd c, double ea, double eb,
+                  double eig_tol, int* order, cudaStream_t st) {
+    select_kernel<<<1, 32, sizeof(int) * 2 * (ncand > 0 ? ncand : 1), st>>>(ncand, lam, eta, ok, G, c, ea, eb, eig_tol,
+                                                                            order);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+
+}  // namespace nep

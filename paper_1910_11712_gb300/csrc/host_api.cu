@@ -1,0 +1,998 @@
+// Host side of the C ABI: operator construction (split form, Sec. 2 Eq. (split); the
+// NEPSetSplitOperator interface of Sec. 3.1.2), region checks, quadrature nodes and
+// coefficients, the device-resident plan that runs the whole contour-integral pass, and
+// result objects. Every numerical step after the coefficient table runs in the CUDA
+// kernels of this library; the host only sizes launches and moves small scalars.
+#include <cstdarg>
+#include <cstring>
+#include <complex>
+#include <mutex>
+#include <vector>
+
+#include "nep_common.cuh"
+
+namespace nep {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+    set_error("CUDA error %s (%s) in %s at %s:%d", cudaGetErrorName(e), cudaGetErrorString(e), what, file, line);
+    return e == cudaErrorMemoryAllocation ? NEP_ERR_NOMEM : NEP_ERR_CUDA;
+}
+
+template <typename T>
+static int dalloc(T** p, size_t count, cudaStream_t st) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    NEP_CUDA(cudaMallocAsync((void**)p, sizeof(T) * count, st));
+    return NEP_OK;
+}
+
+static void configure_pool_once() {
+    static std::once_flag flag;
+    std::call_once(flag, [] {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return;
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+        uint64_t thr = UINT64_MAX;  // keep freed blocks cached in this process for reuse by later plans
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    });
+}
+
+}  // namespace nep
+
+using namespace nep;
+
+// ============================================================================ split operator
+struct nep_split {
+    int n = 0, nterms = 0, kl = 0, ku = 0, ldab = 0;
+    int64_t nnz = 0;
+    bool complex_vals = false;
+    std::vector<int64_t> rowptr;
+    std::vector<int32_t> col;
+    std::vector<double> val, val_im;
+    std::vector<double> norms;
+    std::vector<FnNode> nodes;
+    std::vector<zd> coef;
+    std::vector<int> roots;
+    // device copies
+    int64_t* d_rowptr = nullptr;
+    int32_t* d_col = nullptr;
+    double* d_val = nullptr;
+    double* d_val_im = nullptr;
+    double* d_norms = nullptr;
+    FnNode* d_nodes = nullptr;
+    zd* d_coef = nullptr;
+    int* d_roots = nullptr;
+    int device = 0;
+    SplitDev dev() const {
+        SplitDev s;
+        s.n = n;
+        s.nterms = nterms;
+        s.kl = kl;
+        s.ku = ku;
+        s.ldab = ldab;
+        s.nnz = nnz;
+        s.rowptr = d_rowptr;
+        s.col = d_col;
+        s.val = d_val;
+        s.val_im = complex_vals ? d_val_im : nullptr;
+        s.norms = d_norms;
+        s.fn_nodes = d_nodes;
+        s.fn_coef = d_coef;
+        s.fn_root = d_roots;
+        return s;
+    }
+};
+
+static int flatten_fn(nep_split* h, const nep_fn* f, int depth) {
+    if (!f) { set_error("null function description"); return -1; }
+    if (depth > 16) { set_error("function tree deeper than 16 levels"); return -1; }
+    FnNode nd;
+    memset(&nd, 0, sizeof(nd));
+    nd.kind = f->kind;
+    nd.op = f->op;
+    nd.alpha = mk(f->alpha_re, f->alpha_im);
+    nd.beta = mk(f->beta_re, f->beta_im);
+    nd.shift = mk(f->shift_re, f->shift_im);
+    nd.a = nd.b = -1;
+    if (f->kind == NEP_FN_RATIONAL) {
+        if (f->nnum < 1 || !f->num) { set_error("rational function needs at least one numerator coefficient"); return -1; }
+        if (f->nden < 0 || (f->nden > 0 && !f->den)) { set_error("bad denominator"); return -1; }
+        nd.num_off = (int)h->coef.size();
+        nd.num_len = f->nnum;
+        for (int i = 0; i < f->nnum; ++i) h->coef.push_back(mk(f->num[2 * i], f->num[2 * i + 1]));
+        nd.den_off = (int)h->coef.size();
+        nd.den_len = f->nden;
+        for (int i = 0; i < f->nden; ++i) h->coef.push_back(mk(f->den[2 * i], f->den[2 * i + 1]));
+    } else if (f->kind == NEP_FN_EXP || f->kind == NEP_FN_SQRT) {
+    } else if (f->kind == NEP_FN_COMBINE) {
+        if (f->op < NEP_OP_ADD || f->op > NEP_OP_COMPOSE) { set_error("bad combine op %d", f->op); return -1; }
+        const int self = (int)h->nodes.size();
+        h->nodes.push_back(nd);
+        const int a = flatten_fn(h, f->a, depth + 1);
+        if (a < 0) return -1;
+        const int b = flatten_fn(h, f->b, depth + 1);
+        if (b < 0) return -1;
+        h->nodes[self].a = a;
+        h->nodes[self].b = b;
+        return self;
+    } else {
+        set_error("unknown function kind %d", f->kind);
+        return -1;
+    }
+    h->nodes.push_back(nd);
+    return (int)h->nodes.size() - 1;
+}
+
+static void free_split_device(nep_split* h) {
+    cudaFree(h->d_rowptr);
+    cudaFree(h->d_col);
+    cudaFree(h->d_val);
+    cudaFree(h->d_val_im);
+    cudaFree(h->d_norms);
+    cudaFree(h->d_nodes);
+    cudaFree(h->d_coef);
+    cudaFree(h->d_roots);
+}
+
+template <typename T>
+static int upload(T** d, const std::vector<T>& v) {
+    const size_t bytes = sizeof(T) * (v.size() ? v.size() : 1);
+    NEP_CUDA(cudaMalloc((void**)d, bytes));
+    if (!v.empty()) NEP_CUDA(cudaMemcpy(*d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    return NEP_OK;
+}
+
+extern "C" int nep_create_split(int32_t n, int32_t nterms, const nep_csr* A, const nep_fn* f, nep_split_t* out) {
+    if (!out) { set_error("out is NULL"); return NEP_ERR_ARG; }
+    *out = nullptr;
+    if (n < 1 || nterms < 1 || nterms > 32 || !A || !f) {
+        set_error("nep_create_split: need n >= 1, 1 <= nterms <= 32 and non-NULL A, f");
+        return NEP_ERR_ARG;
+    }
+    for (int i = 0; i < nterms; ++i) {
+        const nep_csr& c = A[i];
+        if (c.n_rows != n || c.n_cols != n || !c.rowptr || !c.col || !c.val_re) {
+            set_error("term %d: CSR must be %d x %d with rowptr, col and val_re", i, n, n);
+            return NEP_ERR_ARG;
+        }
+        if (c.rowptr[0] != 0) { set_error("term %d: rowptr[0] must be 0", i); return NEP_ERR_ARG; }
+        for (int r = 0; r < n; ++r) {
+            if (c.rowptr[r + 1] < c.rowptr[r]) { set_error("term %d: rowptr decreases at row %d", i, r); return NEP_ERR_ARG; }
+            for (int64_t e = c.rowptr[r]; e < c.rowptr[r + 1]; ++e) {
+                if (c.col[e] < 0 || c.col[e] >= n) { set_error("term %d: column index out of range in row %d", i, r); return NEP_ERR_ARG; }
+                if (e > c.rowptr[r] && c.col[e] <= c.col[e - 1]) {
+                    set_error("term %d: column indices of row %d not strictly increasing", i, r);
+                    return NEP_ERR_ARG;
+                }
+            }
+        }
+    }
+    nep_split* h = new nep_split();
+    h->n = n;
+    h->nterms = nterms;
+    // union pattern: merge the sorted column lists row by row
+    h->rowptr.assign(n + 1, 0);
+    std::vector<int32_t> buf;
+    for (int r = 0; r < n; ++r) {
+        buf.clear();
+        for (int i = 0; i < nterms; ++i)
+            for (int64_t e = A[i].rowptr[r]; e < A[i].rowptr[r + 1]; ++e) buf.push_back(A[i].col[e]);
+        std::sort(buf.begin(), buf.end());
+        buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+        h->col.insert(h->col.end(), buf.begin(), buf.end());
+        h->rowptr[r + 1] = (int64_t)h->col.size();
+    }
+    h->nnz = (int64_t)h->col.size();
+    h->val.assign((size_t)nterms * h->nnz, 0.0);
+    h->val_im.assign((size_t)nterms * h->nnz, 0.0);
+    h->norms.assign(nterms, 0.0);
+    for (int i = 0; i < nterms; ++i) {
+        double nrm = 0.0;
+        for (int r = 0; r < n; ++r) {
+            int64_t u = h->rowptr[r];
+            double rs = 0.0;
+            for (int64_t e = A[i].rowptr[r]; e < A[i].rowptr[r + 1]; ++e) {
+                while (h->col[u] != A[i].col[e]) ++u;
+                const double re = A[i].val_re[e], im = A[i].val_im ? A[i].val_im[e] : 0.0;
+                h->val[(size_t)i * h->nnz + u] = re;
+                h->val_im[(size_t)i * h->nnz + u] = im;
+                if (im != 0.0) h->complex_vals = true;
+                rs += std::hypot(re, im);
+            }
+            nrm = std::max(nrm, rs);
+        }
+        h->norms[i] = nrm;
+    }
+    for (int r = 0; r < n; ++r)
+        for (int64_t e = h->rowptr[r]; e < h->rowptr[r + 1]; ++e) {
+            h->kl = std::max(h->kl, r - h->col[e]);
+            h->ku = std::max(h->ku, h->col[e] - r);
+        }
+    h->ldab = 2 * h->kl + h->ku + 1;
+    for (int i = 0; i < nterms; ++i) {
+        const int root = flatten_fn(h, &f[i], 0);
+        if (root < 0) { delete h; return NEP_ERR_ARG; }
+        h->roots.push_back(root);
+    }
+    cudaGetDevice(&h->device);
+    int rc = NEP_OK;
+    if ((rc = upload(&h->d_rowptr, h->rowptr)) || (rc = upload(&h->d_col, h->col)) || (rc = upload(&h->d_val, h->val)) ||
+        (rc = upload(&h->d_val_im, h->val_im)) || (rc = upload(&h->d_norms, h->norms)) ||
+        (rc = upload(&h->d_nodes, h->nodes)) || (rc = upload(&h->d_coef, h->coef)) || (rc = upload(&h->d_roots, h->roots))) {
+        free_split_device(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return NEP_OK;
+}
+
+extern "C" int nep_destroy(nep_split_t h) {
+    if (!h) return NEP_OK;
+    free_split_device(h);
+    delete h;
+    return NEP_OK;
+}
+
+extern "C" int nep_split_info(nep_split_t h, int32_t* n, int32_t* nterms, int32_t* kl, int32_t* ku, int32_t* ldab) {
+    if (!h) { set_error("null handle"); return NEP_ERR_ARG; }
+    if (n) *n = h->n;
+    if (nterms) *nterms = h->nterms;
+    if (kl) *kl = h->kl;
+    if (ku) *ku = h->ku;
+    if (ldab) *ldab = h->ldab;
+    return NEP_OK;
+}
+
+extern "C" void nep_opts_default(nep_opts* o) {
+    if (!o) return;
+    o->precision = NEP_PREC_MIXED;
+    o->rank_tol = 1e-12;
+    o->basis_tol = 1e-6;
+    o->refine_tol = 1e-10;
+    o->step_tol = 1e-14;
+    o->refine_max = 10;
+    o->eig_tol = 1e-8;
+    o->newton_max = 30;
+    o->newton_tol = 1e-14;
+    o->seed = 0;
+}
+
+extern "C" const char* nep_last_error(void) { return g_last_error.c_str(); }
+
+// ============================================================================ region checks
+typedef std::complex<double> C;
+
+static bool in_closed_ellipse(C z, const nep_region* r) {
+    const double x = (z.real() - r->center_re) / r->a, y = (z.imag() - r->center_im) / r->b;
+    return x * x + y * y <= 1.0 + 1e-12;
+}
+
+// roots of a polynomial (highest degree first) by the Weierstrass (Durand-Kerner) iteration
+static std::vector<C> poly_roots(const std::vector<C>& c) {
+    std::vector<C> a(c.begin(), c.end());
+    while (a.size() > 1 && std::abs(a[0]) == 0.0) a.erase(a.begin());
+    const int d = (int)a.size() - 1;
+    std::vector<C> z;
+    if (d < 1) return z;
+    for (auto& x : a) x /= a[0];
+    double rad = 0;
+    for (int i = 1; i <= d; ++i) rad = std::max(rad, std::pow(std::abs(a[i]), 1.0 / i));
+    rad = 1.0 + 2.0 * rad;
+    for (int i = 0; i < d; ++i) z.push_back(rad * std::polar(1.0, 0.4 + 2.0 * M_PI * i / d));
+    for (int it = 0; it < 500; ++it) {
+        double mx = 0;
+        for (int i = 0; i < d; ++i) {
+            C p = 1.0;
+            for (int k = 1; k <= d; ++k) p = p * z[i] + a[k];
+            C den = 1.0;
+            for (int k = 0; k < d; ++k)
+                if (k != i) den *= (z[i] - z[k]);
+            const C dz = p / den;
+            z[i] -= dz;
+            mx = std::max(mx, std::abs(dz));
+        }
+        if (mx < 1e-15) break;
+    }
+    return z;
+}
+
+// Returns NEP_OK or NEP_ERR_REGION if a pole of a rational node or the cut of a sqrt node
+// (argument alpha z) meets the closed ellipse. Nodes inside compositions are checked on
+// their own argument only.
+static int check_region_node(const nep_split* h, int k, const nep_region* r, bool top) {
+    const FnNode& nd = h->nodes[k];
+    const C alpha(nd.alpha.re, nd.alpha.im);
+    if (nd.kind == NEP_FN_RATIONAL && nd.den_len > 1 && top) {
+        std::vector<C> den;
+        for (int t = 0; t < nd.den_len; ++t) den.push_back(C(h->coef[nd.den_off + t].re, h->coef[nd.den_off + t].im));
+        for (const C& x : poly_roots(den)) {
+            if (std::abs(alpha) == 0) continue;
+            const C z = x / alpha;
+            // a pole cancelled by the numerator is removable
+            C p = 0;
+            for (int t = 0; t < nd.num_len; ++t) p = p * x + C(h->coef[nd.num_off + t].re, h->coef[nd.num_off + t].im);
+            if (std::abs(p) < 1e-12 * (1 + std::abs(x))) continue;
+            if (in_closed_ellipse(z, r)) {
+                set_error("pole of a rational term at (%g, %g) lies in the closed region", z.real(), z.imag());
+                return NEP_ERR_REGION;
+            }
+        }
+    } else if (nd.kind == NEP_FN_SQRT && top) {
+        if (std::abs(alpha) == 0) return NEP_OK;
+        // cut: alpha z - shift = -t, t >= 0  =>  z = (shift - t)/alpha; sample the ray densely
+        const C s(nd.shift.re, nd.shift.im);
+        const C z0 = s / alpha, d = -1.0 / alpha;
+        const double span = 4.0 * (std::abs(C(r->center_re, r->center_im) - z0) + r->a + r->b) / std::abs(d);
+        for (int i = 0; i <= 20000; ++i) {
+            const double t = span * i / 20000.0;
+            if (in_closed_ellipse(z0 + t * d, r)) {
+                set_error("branch cut of a square-root term meets the closed region");
+                return NEP_ERR_REGION;
+            }
+        }
+    } else if (nd.kind == NEP_FN_COMBINE) {
+        const bool inner_top = top && nd.op != NEP_OP_COMPOSE;
+        nep_region rs = *r;
+        // children see the argument alpha z: scale the region accordingly (circle/ellipse only
+        // when alpha is real positive; otherwise checks apply to the outer argument only)
+        if (!(nd.alpha.im == 0 && nd.alpha.re > 0)) return NEP_OK;
+        rs.center_re *= nd.alpha.re;
+        rs.center_im *= nd.alpha.re;
+        rs.a *= nd.alpha.re;
+        rs.b *= nd.alpha.re;
+        int rc = check_region_node(h, nd.a, &rs, inner_top);
+        if (rc) return rc;
+        if (nd.op != NEP_OP_COMPOSE) return check_region_node(h, nd.b, &rs, inner_top);
+        return check_region_node(h, nd.b, &rs, top);
+    }
+    return NEP_OK;
+}
+
+static int check_args(nep_split_t h, const nep_region* r, int N, int L, int M) {
+    if (!h || !r) { set_error("null handle or region"); return NEP_ERR_ARG; }
+    if (N < 2 || L < 1 || M < 1 || L > h->n) { set_error("need N >= 2, 1 <= L <= n, M >= 1"); return NEP_ERR_ARG; }
+    if (!(r->a > 0) || !(r->b > 0)) { set_error("region semi-axes must be positive"); return NEP_ERR_ARG; }
+    if ((int64_t)L * M > 512) { set_error("L*M = %d exceeds the supported 512", L * M); return NEP_ERR_UNSUPPORTED; }
+    for (int i = 0; i < h->nterms; ++i) {
+        const int rc = check_region_node(h, h->roots[i], r, true);
+        if (rc) return rc;
+    }
+    return NEP_OK;
+}
+
+// ============================================================================ nodes / coefficients
+static void make_nodes(const nep_region* r, int N, std::vector<zd>& z, std::vector<zd>& w, std::vector<zd>& zeta) {
+    z.resize(N);
+    w.resize(N);
+    zeta.resize(N);
+    for (int j = 0; j < N; ++j) {
+        const double th = 2.0 * M_PI * (j + 0.5) / N;
+        const double c = std::cos(th), s = std::sin(th);
+        z[j] = mk(r->center_re + r->a * c, r->center_im + r->b * s);
+        w[j] = mk(r->b * c / N, r->a * s / N);
+        zeta[j] = mk(c, r->b * s / r->a);
+    }
+}
+
+extern "C" int nep_nodes(const nep_region* r, int32_t N, double* z, double* w, double* zeta) {
+    if (!r || N < 1) { set_error("nep_nodes: bad arguments"); return NEP_ERR_ARG; }
+    std::vector<zd> zz, ww, qq;
+    make_nodes(r, N, zz, ww, qq);
+    if (z) memcpy(z, zz.data(), sizeof(zd) * N);
+    if (w) memcpy(w, ww.data(), sizeof(zd) * N);
+    if (zeta) memcpy(zeta, qq.data(), sizeof(zd) * N);
+    return NEP_OK;
+}
+
+extern "C" int nep_coefficients(nep_split_t h, int32_t N, const double* z, double* F, double* dF) {
+    if (!h || !z || !F || N < 1) { set_error("nep_coefficients: bad arguments"); return NEP_ERR_ARG; }
+    for (int j = 0; j < N; ++j)
+        for (int i = 0; i < h->nterms; ++i) {
+            const FnEval e = fn_eval(h->nodes.data(), h->coef.data(), h->roots[i], mk(z[2 * j], z[2 * j + 1]));
+            F[2 * (i + (int64_t)h->nterms * j)] = e.f.re;
+            F[2 * (i + (int64_t)h->nterms * j) + 1] = e.f.im;
+            if (dF) {
+                dF[2 * (i + (int64_t)h->nterms * j)] = e.df.re;
+                dF[2 * (i + (int64_t)h->nterms * j) + 1] = e.df.im;
+            }
+        }
+    return NEP_OK;
+}
+
+// ============================================================================ plan
+struct nep_plan {
+    nep_split_t h = nullptr;
+    nep_region reg;
+    nep_opts o;
+    int N = 0, L = 0, M = 0, K = 0, LM = 0;
+    bool mixed = true;
+    cudaStream_t alloc_stream = 0;
+    // device buffers
+    zd* F = nullptr;      // nterms x N
+    zd* coef = nullptr;   // N x K (column k: w_j zeta_j^k)
+    void* ab = nullptr;   // N x n x ldab of complex64/complex128
+    int* ipiv = nullptr;  // N x n
+    int* info = nullptr;  // N
+    double* tnorm = nullptr;
+    zd* tval = nullptr;   // N x nnz
+    zd* V = nullptr;      // n x L
+    zd* Y = nullptr;      // N x n x L
+    zd* R = nullptr;      // N x n x L
+    void* D = nullptr;    // N x n x L (solve precision)
+    double* nrm = nullptr;  // N x L x 3
+    double *dmax = nullptr, *ymax = nullptr, *prev = nullptr, *beta = nullptr;
+    int *active = nullptr, *sweeps = nullptr, *nactive = nullptr;
+    zd* S = nullptr;      // K x n x L
+    zd* mu = nullptr;     // K x L x L
+    zd* vpart = nullptr;  // chunks x K x L x L
+    zd *H = nullptr, *Hs = nullptr, *Hw = nullptr, *U = nullptr, *W = nullptr;  // LM x LM
+    double* sigma = nullptr;                                                     // LM
+    zd *T1 = nullptr, *Bred = nullptr, *theta = nullptr, *Tv = nullptr, *Z = nullptr, *cand = nullptr;
+    zd* XH = nullptr;     // n x LM
+    zd *G = nullptr, *Gw = nullptr, *Wg = nullptr;
+    double* lamg = nullptr;
+    zd* Q = nullptr;      // n x LM
+    zd* Y0 = nullptr;     // LM x LM
+    zd* AQ = nullptr;     // nterms x n x LM
+    zd* Bs = nullptr;     // nterms x LM x LM
+    zd *lamn = nullptr, *Yn = nullptr, *Xc = nullptr, *Gx = nullptr;
+    int *ok = nullptr, *its = nullptr, *order = nullptr, *scalars = nullptr, *eigstat = nullptr;
+    double* eta = nullptr;
+    zd* part = nullptr;
+    size_t part_elems = 0;
+    zd* newton_scratch = nullptr;
+    void* eig_scratch = nullptr;
+    JacobiWork jw{};
+    int* h_pinned = nullptr;  // host-mapped scalars
+    // last run
+    int m = 0, kb = 0, max_sweeps_seen = 0, flags = 0;
+    double max_beta = 0;
+    float ms[6] = {0, 0, 0, 0, 0, 0};
+    cudaEvent_t ev[6] = {};
+};
+
+static int plan_alloc(nep_plan* p) {
+    const nep_split* h = p->h;
+    const int n = h->n, N = p->N, L = p->L, K = p->K, LM = p->LM, nt = h->nterms;
+    cudaStream_t st = p->alloc_stream;
+    const size_t esz = p->mixed ? sizeof(zf) : sizeof(zd);
+    NEP_TRY(dalloc(&p->F, (size_t)nt * N, st));
+    NEP_TRY(dalloc(&p->coef, (size_t)N * K, st));
+    NEP_CUDA(cudaMallocAsync(&p->ab, esz * (size_t)N * n * h->ldab, st));
+    NEP_TRY(dalloc(&p->ipiv, (size_t)N * n, st));
+    NEP_TRY(dalloc(&p->info, N, st));
+    NEP_TRY(dalloc(&p->tnorm, N, st));
+    NEP_TRY(dalloc(&p->tval, (size_t)N * h->nnz, st));
+    NEP_TRY(dalloc(&p->V, (size_t)n * L, st));
+    NEP_TRY(dalloc(&p->Y, (size_t)N * n * L, st));
+    NEP_TRY(dalloc(&p->R, (size_t)N * n * L, st));
+    NEP_CUDA(cudaMallocAsync(&p->D, esz * (size_t)N * n * L, st));
+    NEP_TRY(dalloc(&p->nrm, (size_t)N * L * 3, st));
+    NEP_TRY(dalloc(&p->dmax, N, st));
+    NEP_TRY(dalloc(&p->ymax, N, st));
+    NEP_TRY(dalloc(&p->prev, N, st));
+    NEP_TRY(dalloc(&p->beta, N, st));
+    NEP_TRY(dalloc(&p->active, N, st));
+    NEP_TRY(dalloc(&p->sweeps, N, st));
+    NEP_TRY(dalloc(&p->nactive, 1, st));
+    NEP_TRY(dalloc(&p->S, (size_t)K * n * L, st));
+    NEP_TRY(dalloc(&p->mu, (size_t)K * L * L, st));
+    NEP_TRY(dalloc(&p->vpart, (size_t)ceil_div(n, 128) * K * L * L, st));
+    const size_t lm2 = (size_t)LM * LM;
+    NEP_TRY(dalloc(&p->H, lm2, st));
+    NEP_TRY(dalloc(&p->Hs, lm2, st));
+    NEP_TRY(dalloc(&p->Hw, lm2, st));
+    NEP_TRY(dalloc(&p->U, lm2, st));
+    NEP_TRY(dalloc(&p->W, lm2, st));
+    NEP_TRY(dalloc(&p->sigma, LM, st));
+    NEP_TRY(dalloc(&p->T1, lm2, st));
+    NEP_TRY(dalloc(&p->Bred, lm2, st));
+    NEP_TRY(dalloc(&p->theta, LM, st));
+    NEP_TRY(dalloc(&p->Tv, lm2, st));
+    NEP_TRY(dalloc(&p->Z, lm2, st));
+    NEP_TRY(dalloc(&p->cand, LM, st));
+    NEP_TRY(dalloc(&p->XH, (size_t)n * LM, st));
+    NEP_TRY(dalloc(&p->G, lm2, st));
+    NEP_TRY(dalloc(&p->Gw, lm2, st));
+    NEP_TRY(dalloc(&p->Wg, lm2, st));
+    NEP_TRY(dalloc(&p->lamg, LM, st));
+    NEP_TRY(dalloc(&p->Q, (size_t)n * LM, st));
+    NEP_TRY(dalloc(&p->Y0, lm2, st));
+    NEP_TRY(dalloc(&p->AQ, (size_t)nt * n * LM, st));
+    NEP_TRY(dalloc(&p->Bs, (size_t)nt * lm2, st));
+    NEP_TRY(dalloc(&p->lamn, LM, st));
+    NEP_TRY(dalloc(&p->Yn, lm2, st));
+    NEP_TRY(dalloc(&p->Xc, (size_t)n * LM, st));
+    NEP_TRY(dalloc(&p->Gx, lm2, st));
+    NEP_TRY(dalloc(&p->ok, LM, st));
+    NEP_TRY(dalloc(&p->its, LM, st));
+    NEP_TRY(dalloc(&p->order, LM + 1, st));
+    NEP_TRY(dalloc(&p->scalars, 8, st));
+    NEP_TRY(dalloc(&p->eigstat, 1, st));
+    NEP_TRY(dalloc(&p->eta, LM, st));
+    p->part_elems = std::max<size_t>(16 * lm2, 1 << 16);
+    NEP_TRY(dalloc(&p->part, p->part_elems, st));
+    if (LM + 1 > 110) NEP_TRY(dalloc(&p->newton_scratch, (size_t)LM * ((size_t)(LM + 1) * (LM + 1) + 3 * (LM + 1) + 64), st));
+    NEP_CUDA(cudaMallocAsync(&p->eig_scratch, sizeof(zf) * ((size_t)2 * LM * (LM + 1) + LM) + 256, st));
+    NEP_TRY(dalloc(&p->jw.Vm, lm2, st));
+    NEP_TRY(dalloc(&p->jw.flags, 2, st));
+    NEP_TRY(dalloc(&p->jw.sweeps, 1, st));
+    NEP_TRY(dalloc(&p->jw.bar, 2, st));
+    NEP_TRY(dalloc(&p->jw.err, 1, st));
+    NEP_CUDA(cudaMemsetAsync(p->jw.err, 0, sizeof(int), st));
+    NEP_CUDA(cudaHostAlloc((void**)&p->h_pinned, 64 * sizeof(int), cudaHostAllocDefault));
+    for (auto& e : p->ev) NEP_CUDA(cudaEventCreate(&e));
+    return NEP_OK;
+}
+
+static void plan_free(nep_plan* p) {
+    cudaStream_t st = p->alloc_stream;
+    void* bufs[] = {p->F, p->coef, p->ab, p->ipiv, p->info, p->tnorm, p->tval, p->V, p->Y, p->R, p->D, p->nrm,
+                    p->dmax, p->ymax, p->prev, p->beta, p->active, p->sweeps, p->nactive, p->S, p->mu, p->vpart,
+                    p->H, p->Hs, p->Hw, p->U, p->W, p->sigma, p->T1, p->Bred, p->theta, p->Tv, p->Z, p->cand,
+                    p->XH, p->G, p->Gw, p->Wg, p->lamg, p->Q, p->Y0, p->AQ, p->Bs, p->lamn, p->Yn, p->Xc, p->Gx,
+                    p->ok, p->its, p->order, p->scalars, p->eigstat, p->eta, p->part, p->newton_scratch,
+                    p->eig_scratch, p->jw.Vm, p->jw.flags, p->jw.sweeps, p->jw.bar, p->jw.err};
+    for (void* b : bufs)
+        if (b) cudaFreeAsync(b, st);
+    cudaStreamSynchronize(st);
+    if (p->h_pinned) cudaFreeHost(p->h_pinned);
+    for (auto& e : p->ev)
+        if (e) cudaEventDestroy(e);
+}
+
+extern "C" int nep_plan_create(nep_split_t h, const nep_region* r, int32_t N, int32_t L, int32_t M, const nep_opts* o,
+                               nep_plan_t* out) {
+    if (!out) { set_error("out is NULL"); return NEP_ERR_ARG; }
+    *out = nullptr;
+    NEP_TRY(check_args(h, r, N, L, M));
+    configure_pool_once();
+    nep_plan* p = new nep_plan();
+    p->h = h;
+    p->reg = *r;
+    if (o) p->o = *o;
+    else nep_opts_default(&p->o);
+    if (p->o.precision != NEP_PREC_FP64 && p->o.precision != NEP_PREC_MIXED) {
+        delete p;
+        set_error("precision must be NEP_PREC_FP64 or NEP_PREC_MIXED");
+        return NEP_ERR_ARG;
+    }
+    p->N = N;
+    p->L = L;
+    p->M = M;
+    p->K = 2 * M;
+    p->LM = L * M;
+    p->mixed = p->o.precision == NEP_PREC_MIXED;
+    int rc = plan_alloc(p);
+    if (rc) {
+        plan_free(p);
+        delete p;
+        return rc;
+    }
+    // quadrature nodes, coefficient table and moment weights (host, FP64) -> device
+    std::vector<zd> z, w, zeta;
+    make_nodes(r, N, z, w, zeta);
+    std::vector<zd> F((size_t)h->nterms * N), coef((size_t)N * p->K);
+    for (int j = 0; j < N; ++j) {
+        for (int i = 0; i < h->nterms; ++i) F[i + (size_t)h->nterms * j] = fn_eval(h->nodes.data(), h->coef.data(), h->roots[i], z[j]).f;
+        zd pw = mk(1.0, 0.0);
+        for (int k = 0; k < p->K; ++k) {
+            coef[j + (size_t)N * k] = w[j] * pw;
+            pw = pw * zeta[j];
+        }
+    }
+    if (cudaMemcpyAsync(p->F, F.data(), sizeof(zd) * F.size(), cudaMemcpyHostToDevice, p->alloc_stream) != cudaSuccess ||
+        cudaMemcpyAsync(p->coef, coef.data(), sizeof(zd) * coef.size(), cudaMemcpyHostToDevice, p->alloc_stream) != cudaSuccess ||
+        cudaStreamSynchronize(p->alloc_stream) != cudaSuccess) {
+        set_error("upload of the coefficient tables failed");
+        plan_free(p);
+        delete p;
+        return NEP_ERR_CUDA;
+    }
+    *out = p;
+    return NEP_OK;
+}
+
+extern "C" int nep_plan_destroy(nep_plan_t p) {
+    if (!p) return NEP_OK;
+    plan_free(p);
+    delete p;
+    return NEP_OK;
+}
+
+template <typename T>
+static int run_solves(nep_plan* p, cudaStream_t st) {
+    const SplitDev s = p->h->dev();
+    const int N = p->N, n = s.n, L = p->L;
+    cx<T>* ab = reinterpret_cast<cx<T>*>(p->ab);
+    cx<T>* D = reinterpret_cast<cx<T>*>(p->D);
+    NEP_CUDA(cudaEventRecord(p->ev[0], st));
+    NEP_TRY(launch_assemble<T>(s, N, p->F, ab, p->tnorm, p->tval, st));
+    NEP_CUDA(cudaEventRecord(p->ev[1], st));
+    NEP_TRY(launch_band_lu<T>(s, N, ab, p->ipiv, p->info, nullptr, st));
+    NEP_CUDA(cudaEventRecord(p->ev[2], st));
+    NEP_TRY(launch_convert_rhs<T>(N, n, L, p->V, D, st));
+    NEP_TRY(launch_band_solve<T>(s, N, ab, p->ipiv, L, D, nullptr, st));
+    NEP_TRY(launch_widen<T>(N, n, L, D, p->Y, st));
+    NEP_TRY(launch_fill_int(N, p->active, 1, st));
+    NEP_CUDA(cudaMemsetAsync(p->prev, 0, sizeof(double) * N, st));
+    NEP_CUDA(cudaMemsetAsync(p->sweeps, 0, sizeof(int) * N, st));
+    for (int sweep = 0; sweep < p->o.refine_max; ++sweep) {
+        NEP_TRY(launch_split_residual(s, N, p->tval, L, p->V, p->Y, p->R, p->nrm, p->active, st));
+        NEP_TRY(launch_refine_prepare<T>(N, n, L, p->R, D, p->active, st));
+        NEP_TRY(launch_band_solve<T>(s, N, ab, p->ipiv, L, D, p->active, st));
+        NEP_TRY(launch_refine_update<T>(N, n, L, D, p->Y, p->dmax, p->ymax, p->active, st));
+        NEP_TRY(launch_refine_decide(N, L, sweep, p->o.refine_max, p->o.refine_tol, p->o.step_tol, p->nrm, p->tnorm,
+                                     p->dmax, p->ymax, p->prev, p->beta, p->active, p->sweeps, p->nactive, st));
+        NEP_CUDA(cudaMemcpyAsync(p->h_pinned, p->nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+        NEP_CUDA(cudaStreamSynchronize(st));
+        if (p->h_pinned[0] == 0) break;
+    }
+    NEP_CUDA(cudaEventRecord(p->ev[3], st));
+    return NEP_OK;
+}
+
+static int read_scalar(nep_plan* p, const int* dptr, int* out, cudaStream_t st) {
+    NEP_CUDA(cudaMemcpyAsync(p->h_pinned, dptr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NEP_CUDA(cudaStreamSynchronize(st));
+    *out = p->h_pinned[0];
+    return NEP_OK;
+}
+
+static int run_extract(nep_plan* p, cudaStream_t st) {
+    const SplitDev s = p->h->dev();
+    const int n = s.n, N = p->N, L = p->L, M = p->M, K = p->K, LM = p->LM, nt = s.nterms;
+    // moments and Hankel matrices
+    NEP_TRY(launch_moments(n, L, N, K, p->coef, p->Y, p->S, st));
+    NEP_TRY(launch_vh_times(n, L, K, p->V, p->S, p->mu, p->vpart, st));
+    NEP_TRY(launch_hankel_build(L, M, p->mu, p->H, p->Hs, st));
+    NEP_CUDA(cudaEventRecord(p->ev[4], st));
+    // SVD of H and numerical rank
+    NEP_CUDA(cudaMemcpyAsync(p->Hw, p->H, sizeof(zd) * LM * LM, cudaMemcpyDeviceToDevice, st));
+    NEP_TRY(jacobi_svd(LM, LM, p->Hw, p->U, p->W, p->sigma, p->jw, st));
+    NEP_TRY(launch_rank(LM, p->sigma, p->o.rank_tol, p->scalars, st));
+    int m = 0;
+    NEP_TRY(read_scalar(p, p->scalars, &m, st));
+    p->m = m;
+    p->kb = 0;
+    if (m == 0) {
+        NEP_CUDA(cudaMemsetAsync(p->order, 0, sizeof(int), st));
+        return NEP_OK;
+    }
+    // reduced matrix U_m^H H< W_m Sigma_m^{-1} and its eigenpairs (FP32 Schur, seeds only)
+    NEP_TRY(zgemm(LM, m, LM, 0, p->Hs, LM, p->W, LM, p->T1, LM, p->part, p->part_elems, st));
+    NEP_TRY(zgemm(m, m, LM, 1, p->U, LM, p->T1, LM, p->Bred, m, p->part, p->part_elems, st));
+    NEP_TRY(launch_scale_cols(m, m, p->Bred, m, p->sigma, 0, st));
+    NEP_TRY(small_eig<float>(m, p->Bred, p->theta, p->Tv, p->eigstat, p->eig_scratch, st));
+    NEP_TRY(launch_candidates(m, p->theta, mk(p->reg.center_re, p->reg.center_im), p->reg.a, p->cand, st));
+    // Hankel eigenvector estimates X_H = [S_0 .. S_{M-1}] W_m Sigma_m^{-1} T
+    NEP_TRY(launch_scale_rows(m, m, p->Tv, m, p->sigma, st));
+    NEP_TRY(zgemm(LM, m, m, 0, p->W, LM, p->Tv, m, p->Z, LM, p->part, p->part_elems, st));
+    NEP_TRY(zgemm(n, m, LM, 0, p->S, n, p->Z, LM, p->XH, n, p->part, p->part_elems, st));
+    NEP_TRY(launch_normalize_columns(n, m, p->XH, 0, nullptr, st));
+    // orthonormal basis: eigen-decomposition of the Gram matrix of the normalised columns
+    NEP_TRY(zgemm(m, m, n, 1, p->XH, n, p->XH, n, p->G, m, p->part, p->part_elems, st));
+    NEP_TRY(jacobi_svd(m, m, p->G, nullptr, p->Wg, p->lamg, p->jw, st));
+    NEP_TRY(launch_rank(m, p->lamg, p->o.basis_tol * p->o.basis_tol, p->scalars + 1, st));
+    int kb = 0;
+    NEP_TRY(read_scalar(p, p->scalars + 1, &kb, st));
+    p->kb = kb;
+    if (kb == 0) {
+        NEP_CUDA(cudaMemsetAsync(p->order, 0, sizeof(int), st));
+        return NEP_OK;
+    }
+    NEP_TRY(launch_scale_cols(m, kb, p->Wg, m, p->lamg, 1, st));
+    NEP_TRY(zgemm(n, kb, m, 0, p->XH, n, p->Wg, m, p->Q, n, p->part, p->part_elems, st));
+    NEP_TRY(zgemm(kb, m, n, 1, p->Q, n, p->XH, n, p->Y0, kb, p->part, p->part_elems, st));
+    // projected split form B_i = Q^H A_i Q
+    NEP_TRY(launch_term_spmm(s, kb, p->Q, p->AQ, st));
+    for (int i = 0; i < nt; ++i)
+        NEP_TRY(zgemm(kb, kb, n, 1, p->Q, n, p->AQ + (size_t)i * n * kb, n, p->Bs + (size_t)i * kb * kb, kb, p->part,
+                      p->part_elems, st));
+    // Newton from every Hankel candidate
+    const double rad = 4.0 * std::max(p->reg.a, p->reg.b);
+    NEP_TRY(launch_newton(s, kb, m, p->Bs, p->cand, p->Y0, kb, mk(p->reg.center_re, p->reg.center_im), rad,
+                          p->o.newton_max, p->o.newton_tol, p->lamn, p->Yn, p->ok, p->its, p->newton_scratch, st));
+    // eigenvectors, residuals, selection
+    NEP_TRY(zgemm(n, m, kb, 0, p->Q, n, p->Yn, kb, p->Xc, n, p->part, p->part_elems, st));
+    NEP_TRY(launch_normalize_columns(n, m, p->Xc, 1, nullptr, st));
+    NEP_TRY(launch_eta(s, m, p->lamn, p->Xc, p->eta, st));
+    NEP_TRY(zgemm(m, m, n, 1, p->Xc, n, p->Xc, n, p->Gx, m, p->part, p->part_elems, st));
+    NEP_TRY(launch_select(m, p->lamn, p->eta, p->ok, p->Gx, mk(p->reg.center_re, p->reg.center_im), p->reg.a, p->reg.b,
+                          p->o.eig_tol, p->order, st));
+    return NEP_OK;
+}
+
+extern "C" int nep_plan_execute(nep_plan_t p, const void* V_dev, void* stream) {
+    if (!p || !V_dev) { set_error("nep_plan_execute: null plan or V"); return NEP_ERR_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = p->h->n, L = p->L;
+    NEP_CUDA(cudaMemcpyAsync(p->V, V_dev, sizeof(zd) * (size_t)n * L, cudaMemcpyDeviceToDevice, st));
+    NEP_CUDA(cudaMemsetAsync(p->jw.err, 0, sizeof(int), st));
+    int rc = p->mixed ? run_solves<float>(p, st) : run_solves<double>(p, st);
+    if (rc) return rc;
+    NEP_TRY(run_extract(p, st));
+    NEP_CUDA(cudaEventRecord(p->ev[5], st));
+    int err = 0;
+    NEP_TRY(read_scalar(p, p->jw.err, &err, st));
+    if (err) { set_error("a bounded grid barrier of the Jacobi SVD timed out"); return NEP_ERR_INTERNAL; }
+    return NEP_OK;
+}
+
+extern "C" int nep_plan_buffer(nep_plan_t p, const char* name, void** dev_ptr, size_t* bytes) {
+    if (!p || !name || !dev_ptr) { set_error("nep_plan_buffer: bad arguments"); return NEP_ERR_ARG; }
+    const nep_split* h = p->h;
+    const size_t n = h->n, N = p->N, L = p->L, K = p->K;
+    const size_t esz = p->mixed ? sizeof(zf) : sizeof(zd);
+    struct B { const char* nm; void* ptr; size_t bytes; } tab[] = {
+        {"F", p->F, sizeof(zd) * h->nterms * N},   {"coef", p->coef, sizeof(zd) * N * K},
+        {"ab", p->ab, esz * N * n * h->ldab},       {"ipiv", p->ipiv, sizeof(int) * N * n},
+        {"info", p->info, sizeof(int) * N},         {"Y", p->Y, sizeof(zd) * N * n * L},
+        {"S", p->S, sizeof(zd) * K * n * L},        {"mu", p->mu, sizeof(zd) * K * L * L},
+        {"sigma", p->sigma, sizeof(double) * p->LM}, {"tnorm", p->tnorm, sizeof(double) * N},
+        {"beta", p->beta, sizeof(double) * N},      {"sweeps", p->sweeps, sizeof(int) * N},
+        {"H", p->H, sizeof(zd) * p->LM * p->LM},
+    };
+    for (auto& b : tab)
+        if (!strcmp(b.nm, name)) {
+            *dev_ptr = b.ptr;
+            if (bytes) *bytes = b.bytes;
+            return NEP_OK;
+        }
+    set_error("unknown plan buffer '%s'", name);
+    return NEP_ERR_ARG;
+}
+
+// ============================================================================ results
+struct nep_result {
+    int n = 0, nconv = 0, m = 0, flags = 0;
+    std::vector<double> lam, X, resid, sigma;
+    nep_result_info_t info{};
+};
+
+extern "C" int nep_plan_result(nep_plan_t p, nep_result_t* out) {
+    if (!p || !out) { set_error("nep_plan_result: bad arguments"); return NEP_ERR_ARG; }
+    const int n = p->h->n, N = p->N, LM = p->LM;
+    nep_result* r = new nep_result();
+    r->n = n;
+    r->m = p->m;
+    std::vector<int> order(LM + 1, 0);
+    NEP_CUDA(cudaMemcpy(order.data(), p->order, sizeof(int) * (p->m > 0 ? p->m + 1 : 1), cudaMemcpyDeviceToHost));
+    const int nc = p->m > 0 && p->kb > 0 ? order[0] : 0;
+    r->nconv = nc;
+    std::vector<zd> lam(std::max(p->m, 1));
+    std::vector<double> eta(std::max(p->m, 1));
+    std::vector<int> ok(std::max(p->m, 1));
+    if (p->m > 0 && p->kb > 0) {
+        NEP_CUDA(cudaMemcpy(lam.data(), p->lamn, sizeof(zd) * p->m, cudaMemcpyDeviceToHost));
+        NEP_CUDA(cudaMemcpy(eta.data(), p->eta, sizeof(double) * p->m, cudaMemcpyDeviceToHost));
+        NEP_CUDA(cudaMemcpy(ok.data(), p->ok, sizeof(int) * p->m, cudaMemcpyDeviceToHost));
+    }
+    r->lam.resize(2 * (size_t)nc);
+    r->resid.resize(nc);
+    r->X.resize(2 * (size_t)n * nc);
+    for (int q = 0; q < nc; ++q) {
+        const int c = order[1 + q];
+        r->lam[2 * q] = lam[c].re;
+        r->lam[2 * q + 1] = lam[c].im;
+        r->resid[q] = eta[c];
+        NEP_CUDA(cudaMemcpy(r->X.data() + 2 * (size_t)n * q, p->Xc + (size_t)n * c, sizeof(zd) * n, cudaMemcpyDeviceToHost));
+    }
+    r->sigma.resize(LM);
+    NEP_CUDA(cudaMemcpy(r->sigma.data(), p->sigma, sizeof(double) * LM, cudaMemcpyDeviceToHost));
+    std::vector<double> beta(N);
+    std::vector<int> sweeps(N), info(N);
+    NEP_CUDA(cudaMemcpy(beta.data(), p->beta, sizeof(double) * N, cudaMemcpyDeviceToHost));
+    NEP_CUDA(cudaMemcpy(sweeps.data(), p->sweeps, sizeof(int) * N, cudaMemcpyDeviceToHost));
+    NEP_CUDA(cudaMemcpy(info.data(), p->info, sizeof(int) * N, cudaMemcpyDeviceToHost));
+    int flags = 0, msw = 0;
+    double mb = 0;
+    for (int j = 0; j < N; ++j) {
+        mb = std::max(mb, beta[j]);
+        msw = std::max(msw, sweeps[j]);
+        if (beta[j] > p->o.refine_tol) flags |= NEP_WARN_REFINE;
+        if (info[j]) flags |= NEP_WARN_SINGULAR_NODE;
+    }
+    if (p->m == LM) flags |= NEP_WARN_SATURATED;
+    for (int c = 0; c < p->m && p->kb > 0; ++c)
+        if (!ok[c]) flags |= NEP_WARN_NEWTON;
+    r->flags = flags;
+    nep_result_info_t& in = r->info;
+    in.n = n;
+    in.N = N;
+    in.L = p->L;
+    in.M = p->M;
+    in.precision = p->o.precision;
+    in.hankel_rank = p->m;
+    in.basis_rank = p->kb;
+    in.ncandidates = p->m;
+    in.max_sweeps = msw;
+    in.flags = flags;
+    in.max_backward = mb;
+    float t[5] = {0, 0, 0, 0, 0};
+    for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&t[i], p->ev[i], p->ev[i + 1]);
+    in.ms_assemble = t[0];
+    in.ms_factor = t[1];
+    in.ms_solve = t[2];
+    in.ms_moments = t[3];
+    in.ms_extract = t[4];
+    float tot = 0;
+    cudaEventElapsedTime(&tot, p->ev[0], p->ev[5]);
+    in.ms_total = tot;
+    *out = r;
+    return NEP_OK;
+}
+
+extern "C" int nep_ciss_solve(nep_split_t h, const nep_region* r, int32_t N, int32_t L, int32_t M, const nep_opts* o,
+                              const double* V_host, nep_result_t* out) {
+    if (!out) { set_error("out is NULL"); return NEP_ERR_ARG; }
+    *out = nullptr;
+    nep_plan_t p = nullptr;
+    NEP_TRY(nep_plan_create(h, r, N, L, M, o, &p));
+    const size_t nl = (size_t)h->n * L;
+    std::vector<zd> V(nl);
+    if (V_host) {
+        memcpy(V.data(), V_host, sizeof(zd) * nl);
+    } else {
+        // SplitMix64 stream + Box-Muller: Re, Im iid N(0,1)
+        uint64_t state = p->o.seed;
+        auto next = [&]() {
+            uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            return z ^ (z >> 31);
+        };
+        auto unif = [&]() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); };
+        for (size_t i = 0; i < nl; ++i) {
+            const double u1 = unif(), u2 = unif();
+            const double rr = std::sqrt(-2.0 * std::log(u1));
+            V[i] = mk(rr * std::cos(2 * M_PI * u2), rr * std::sin(2 * M_PI * u2));
+        }
+    }
+    int rc = NEP_OK;
+    zd* dV = nullptr;
+    if (cudaMalloc((void**)&dV, sizeof(zd) * nl) != cudaSuccess) rc = NEP_ERR_NOMEM;
+    if (!rc && cudaMemcpy(dV, V.data(), sizeof(zd) * nl, cudaMemcpyHostToDevice) != cudaSuccess) rc = NEP_ERR_CUDA;
+    if (!rc) rc = nep_plan_execute(p, dV, nullptr);
+    if (!rc) rc = nep_plan_result(p, out);
+    cudaFree(dV);
+    nep_plan_destroy(p);
+    return rc;
+}
+
+extern "C" int nep_result_get(nep_result_t r, int32_t* nconv, const double** lambda, const double** X,
+                              const double** resid, int32_t* hankel_rank, int32_t* flags) {
+    if (!r) { set_error("null result"); return NEP_ERR_ARG; }
+    if (nconv) *nconv = r->nconv;
+    if (lambda) *lambda = r->lam.data();
+    if (X) *X = r->X.data();
+    if (resid) *resid = r->resid.data();
+    if (hankel_rank) *hankel_rank = r->m;
+    if (flags) *flags = r->flags;
+    return NEP_OK;
+}
+
+extern "C" int nep_result_info(nep_result_t r, nep_result_info_t* info) {
+    if (!r || !info) { set_error("null result or info"); return NEP_ERR_ARG; }
+    *info = r->info;
+    return NEP_OK;
+}
+
+extern "C" int nep_result_hankel_sigma(nep_result_t r, const double** sigma, int32_t* count) {
+    if (!r) { set_error("null result"); return NEP_ERR_ARG; }
+    if (sigma) *sigma = r->sigma.data();
+    if (count) *count = (int32_t)r->sigma.size();
+    return NEP_OK;
+}
+
+extern "C" int nep_result_free(nep_result_t r) {
+    delete r;
+    return NEP_OK;
+}
+
+// ============================================================================ step entry points
+extern "C" int nep_assemble_band(nep_split_t h, int32_t npts, const double* F_dev, int32_t precision, void* ab_dev,
+                                 double* tnorm_dev, void* stream) {
+    if (!h || !F_dev || !ab_dev || npts < 0) { set_error("nep_assemble_band: bad arguments"); return NEP_ERR_ARG; }
+    const SplitDev s = h->dev();
+    if (precision == NEP_PREC_MIXED)
+        return launch_assemble<float>(s, npts, (const zd*)F_dev, (zf*)ab_dev, tnorm_dev, nullptr, (cudaStream_t)stream);
+    if (precision == NEP_PREC_FP64)
+        return launch_assemble<double>(s, npts, (const zd*)F_dev, (zd*)ab_dev, tnorm_dev, nullptr, (cudaStream_t)stream);
+    set_error("bad precision");
+    return NEP_ERR_ARG;
+}
+
+extern "C" int nep_band_factor(nep_split_t h, int32_t npts, int32_t precision, void* ab_dev, int32_t* ipiv_dev,
+                               int32_t* info_dev, void* stream) {
+    if (!h || !ab_dev || !ipiv_dev || !info_dev || npts < 0) { set_error("nep_band_factor: bad arguments"); return NEP_ERR_ARG; }
+    const SplitDev s = h->dev();
+    if (precision == NEP_PREC_MIXED) return launch_band_lu<float>(s, npts, (zf*)ab_dev, ipiv_dev, info_dev, nullptr, (cudaStream_t)stream);
+    if (precision == NEP_PREC_FP64) return launch_band_lu<double>(s, npts, (zd*)ab_dev, ipiv_dev, info_dev, nullptr, (cudaStream_t)stream);
+    set_error("bad precision");
+    return NEP_ERR_ARG;
+}
+
+extern "C" int nep_band_solve(nep_split_t h, int32_t npts, int32_t precision, const void* ab_dev, const int32_t* ipiv_dev,
+                              int32_t L, void* B_dev, void* stream) {
+    if (!h || !ab_dev || !ipiv_dev || !B_dev || npts < 0 || L < 0) { set_error("nep_band_solve: bad arguments"); return NEP_ERR_ARG; }
+    const SplitDev s = h->dev();
+    if (precision == NEP_PREC_MIXED)
+        return launch_band_solve<float>(s, npts, (const zf*)ab_dev, ipiv_dev, L, (zf*)B_dev, nullptr, (cudaStream_t)stream);
+    if (precision == NEP_PREC_FP64)
+        return launch_band_solve<double>(s, npts, (const zd*)ab_dev, ipiv_dev, L, (zd*)B_dev, nullptr, (cudaStream_t)stream);
+    set_error("bad precision");
+    return NEP_ERR_ARG;
+}
+
+extern "C" int nep_split_residual(nep_split_t h, int32_t npts, const double* F_dev, int32_t L, const double* V_dev,
+                                  const double* Y_dev, double* R_dev, void* stream) {
+    if (!h || !F_dev || !V_dev || !Y_dev || !R_dev || npts < 0 || L < 1) { set_error("nep_split_residual: bad arguments"); return NEP_ERR_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const SplitDev s = h->dev();
+    zd* tval = nullptr;
+    NEP_CUDA(cudaMallocAsync((void**)&tval, sizeof(zd) * (size_t)std::max(npts, 1) * std::max<int64_t>(h->nnz, 1), st));
+    int rc = launch_assemble<double>(s, npts, (const zd*)F_dev, nullptr, nullptr, tval, st);
+    if (!rc) rc = launch_split_residual(s, npts, tval, L, (const zd*)V_dev, (const zd*)Y_dev, (zd*)R_dev, nullptr, nullptr, st);
+    cudaFreeAsync(tval, st);
+    return rc;
+}
+
+extern "C" int nep_moments(int32_t n, int32_t L, int32_t N, int32_t K, const double* coef_dev, const double* Y_dev,
+                           double* S_dev, void* stream) {
+    if (n < 1 || L < 1 || N < 1 || K < 1 || !coef_dev || !Y_dev || !S_dev) { set_error("nep_moments: bad arguments"); return NEP_ERR_ARG; }
+    return launch_moments(n, L, N, K, (const zd*)coef_dev, (const zd*)Y_dev, (zd*)S_dev, (cudaStream_t)stream);
+}
+
+extern "C" int nep_jacobi_svd(int32_t rows, int32_t cols, double* A_dev, double* W_dev, double* sigma_dev, void* stream) {
+    if (rows < cols || cols < 1 || !A_dev || !W_dev || !sigma_dev) { set_error("nep_jacobi_svd: need rows >= cols >= 1"); return NEP_ERR_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    JacobiWork w{};
+    zd* U = nullptr;
+    NEP_CUDA(cudaMallocAsync((void**)&w.Vm, sizeof(zd) * (size_t)cols * cols, st));
+    NEP_CUDA(cudaMallocAsync((void**)&w.flags, 2 * sizeof(int), st));
+    NEP_CUDA(cudaMallocAsync((void**)&w.sweeps, sizeof(int), st));
+    NEP_CUDA(cudaMallocAsync((void**)&w.bar, 2 * sizeof(unsigned), st));
+    NEP_CUDA(cudaMallocAsync((void**)&w.err, sizeof(int), st));
+    NEP_CUDA(cudaMallocAsync((void**)&U, sizeof(zd) * (size_t)rows * cols, st));
+    NEP_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    int rc = jacobi_svd(rows, cols, (zd*)A_dev, U, (zd*)W_dev, sigma_dev, w, st);
+    int err = 0;
+    if (!rc) {
+        if (cudaMemcpyAsync(A_dev, U, sizeof(zd) * (size_t)rows * cols, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(&err, w.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = NEP_ERR_CUDA;
+    }
+    cudaFreeAsync(w.Vm, st);
+    cudaFreeAsync(w.flags, st);
+    cudaFreeAsync(w.sweeps, st);
+    cudaFreeAsync(w.bar, st);
+    cudaFreeAsync(w.err, st);
+    cudaFreeAsync(U, st);
+    if (!rc && err) { set_error("grid barrier timed out"); rc = NEP_ERR_INTERNAL; }
+    return rc;
+}
+
+extern "C" int nep_small_eig(int32_t m, const double* A_dev, double* eval_dev, double* evec_dev, void* stream) {
+    if (m < 1 || !A_dev || !eval_dev) { set_error("nep_small_eig: bad arguments"); return NEP_ERR_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    void* g = nullptr;
+    NEP_CUDA(cudaMallocAsync(&g, sizeof(zd) * ((size_t)2 * m * (m + 1) + m) + 256, st));
+    int rc = small_eig<double>(m, (const zd*)A_dev, (zd*)eval_dev, (zd*)evec_dev, nullptr, g, st);
+    cudaFreeAsync(g, st);
+    return rc;
+}

@@ -1,0 +1,246 @@
+// Shared definitions of the CUDA library: complex arithmetic, the split operator on
+// the device, scalar-function evaluation, error reporting and launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <string>
+
+#include "../../include/nep_ciss.h"
+
+namespace nep {
+
+// ----------------------------------------------------------------- complex numbers
+template <typename T>
+struct alignas(2 * sizeof(T)) cx {
+    T re, im;
+};
+typedef cx<double> zd;
+typedef cx<float> zf;
+
+template <typename T> __host__ __device__ __forceinline__ cx<T> mk(T r, T i) { cx<T> z; z.re = r; z.im = i; return z; }
+template <typename T> __host__ __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk(a.re + b.re, a.im + b.im); }
+template <typename T> __host__ __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk(a.re - b.re, a.im - b.im); }
+template <typename T> __host__ __device__ __forceinline__ cx<T> operator-(cx<T> a) { return mk(-a.re, -a.im); }
+template <typename T> __host__ __device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
+    return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename T> __host__ __device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return mk(s * a.re, s * a.im); }
+template <typename T> __host__ __device__ __forceinline__ cx<T> conj(cx<T> a) { return mk(a.re, -a.im); }
+template <typename T> __host__ __device__ __forceinline__ T abs1(cx<T> a) { return fabs(a.re) + fabs(a.im); }
+template <typename T> __host__ __device__ __forceinline__ T norm2(cx<T> a) { return a.re * a.re + a.im * a.im; }
+template <typename T> __host__ __device__ __forceinline__ T cabs_(cx<T> a) { return hypot(a.re, a.im); }
+// acc - a*b with fused multiply-adds
+template <typename T> __host__ __device__ __forceinline__ cx<T> fms(cx<T> acc, cx<T> a, cx<T> b) {
+    acc.re = fma(-a.re, b.re, acc.re);
+    acc.re = fma(a.im, b.im, acc.re);
+    acc.im = fma(-a.re, b.im, acc.im);
+    acc.im = fma(-a.im, b.re, acc.im);
+    return acc;
+}
+// acc + a*b
+template <typename T> __host__ __device__ __forceinline__ cx<T> fma_(cx<T> acc, cx<T> a, cx<T> b) {
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(-a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(a.im, b.re, acc.im);
+    return acc;
+}
+// acc + conj(a)*b
+template <typename T> __host__ __device__ __forceinline__ cx<T> fmac(cx<T> acc, cx<T> a, cx<T> b) {
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(-a.im, b.re, acc.im);
+    return acc;
+}
+// a / b with scaling against overflow (Smith's method)
+template <typename T> __host__ __device__ __forceinline__ cx<T> cdiv(cx<T> a, cx<T> b) {
+    if (fabs(b.re) >= fabs(b.im)) {
+        T r = b.im / b.re, d = b.re + b.im * r;
+        return mk((a.re + a.im * r) / d, (a.im - a.re * r) / d);
+    } else {
+        T r = b.re / b.im, d = b.im + b.re * r;
+        return mk((a.re * r + a.im) / d, (a.im * r - a.re) / d);
+    }
+}
+template <typename T> __host__ __device__ __forceinline__ cx<T> csqrt_(cx<T> z) {
+    // principal square root; the cut lies on the negative real axis, the sign of a zero
+    // imaginary part selects the side (as C99 csqrt)
+    T x = z.re, y = z.im;
+    if (x == 0 && y == 0) return mk<T>(0, y);
+    T r = hypot(x, y);
+    T s = sqrt((r + fabs(x)) * T(0.5));
+    if (x >= 0) return mk(s, y / (T(2) * s));
+    return mk(fabs(y) / (T(2) * s), copysign(s, y));
+}
+template <typename T> __host__ __device__ __forceinline__ cx<T> cexp_(cx<T> z) {
+    T e = exp(z.re);
+    return mk(e * cos(z.im), e * sin(z.im));
+}
+template <typename T, typename U> __host__ __device__ __forceinline__ cx<T> cvt(cx<U> a) {
+    return mk<T>((T)a.re, (T)a.im);
+}
+
+// ----------------------------------------------------------------- scalar functions
+// Flattened function tree: node k has kind/op, scaling alpha/beta, shift, coefficient
+// ranges into a shared coefficient pool, and child node indices (combine).
+struct FnNode {
+    int kind, op, a, b;
+    int num_off, num_len, den_off, den_len;
+    zd alpha, beta, shift;
+};
+
+struct FnEval {
+    zd f, df;
+};
+
+// Evaluates node k at z: g(z) = beta h(alpha z), returns g and g'.
+__host__ __device__ inline FnEval fn_eval(const FnNode* nodes, const zd* coef, int k, zd z, int depth = 0) {
+    const FnNode nd = nodes[k];
+    zd x = nd.alpha * z;
+    zd h, dh;
+    if (nd.kind == NEP_FN_RATIONAL) {
+        zd p = mk(0.0, 0.0), dp = mk(0.0, 0.0);
+        for (int t = 0; t < nd.num_len; ++t) {
+            dp = dp * x + p;
+            p = p * x + coef[nd.num_off + t];
+        }
+        if (nd.den_len > 0) {
+            zd q = mk(0.0, 0.0), dq = mk(0.0, 0.0);
+            for (int t = 0; t < nd.den_len; ++t) {
+                dq = dq * x + q;
+                q = q * x + coef[nd.den_off + t];
+            }
+            h = cdiv(p, q);
+            dh = cdiv(dp * q - p * dq, q * q);
+        } else {
+            h = p;
+            dh = dp;
+        }
+    } else if (nd.kind == NEP_FN_EXP) {
+        h = cexp_(x);
+        dh = h;
+    } else if (nd.kind == NEP_FN_SQRT) {
+        h = csqrt_(x - nd.shift);
+        dh = cdiv(mk(0.5, 0.0), h);
+    } else {  // combine
+        if (depth > 16) return FnEval{mk(0.0, 0.0), mk(0.0, 0.0)};
+        if (nd.op == NEP_OP_COMPOSE) {
+            FnEval eb = fn_eval(nodes, coef, nd.b, x, depth + 1);
+            FnEval ea = fn_eval(nodes, coef, nd.a, eb.f, depth + 1);
+            h = ea.f;
+            dh = ea.df * eb.df;
+        } else {
+            FnEval ea = fn_eval(nodes, coef, nd.a, x, depth + 1);
+            FnEval eb = fn_eval(nodes, coef, nd.b, x, depth + 1);
+            if (nd.op == NEP_OP_ADD) {
+                h = ea.f + eb.f;
+                dh = ea.df + eb.df;
+            } else if (nd.op == NEP_OP_MUL) {
+                h = ea.f * eb.f;
+                dh = ea.df * eb.f + ea.f * eb.df;
+            } else {
+                h = cdiv(ea.f, eb.f);
+                dh = cdiv(ea.df * eb.f - ea.f * eb.df, eb.f * eb.f);
+            }
+        }
+    }
+    return FnEval{nd.beta * h, nd.beta * nd.alpha * dh};
+}
+
+// ----------------------------------------------------------------- device split operator
+// Union sparsity pattern of all terms in CSR, one FP64 value array per term (zero where a
+// term has no entry), so a single pass over the pattern applies any combination of terms.
+struct SplitDev {
+    int n, nterms, kl, ku, ldab;
+    int64_t nnz;
+    const int64_t* rowptr;  // n+1
+    const int32_t* col;     // nnz
+    const double* val;      // nterms x nnz real parts
+    const double* val_im;   // nterms x nnz imaginary parts, or nullptr if all terms are real
+    const double* norms;    // nterms, ||A_i||_inf
+    const FnNode* fn_nodes;
+    const zd* fn_coef;
+    const int* fn_root;     // nterms root node indices
+};
+
+// ----------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define NEP_CUDA(call)                                                                  \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) return ::nep::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+#define NEP_CHECK_LAUNCH() NEP_CUDA(cudaGetLastError())
+#define NEP_TRY(call)            \
+    do {                         \
+        int rc_ = (call);        \
+        if (rc_ != NEP_OK) return rc_; \
+    } while (0)
+
+static inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ----------------------------------------------------------------- launchers (per file)
+// assemble.cu
+template <typename T>
+int launch_assemble(const SplitDev& s, int npts, const zd* F, cx<T>* ab, double* tnorm, zd* tval, cudaStream_t st);
+// band_lu.cu
+template <typename T>
+int launch_band_lu(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st);
+template <typename T>
+int launch_band_solve(const SplitDev& s, int npts, const cx<T>* ab, const int* ipiv, int L, cx<T>* B,
+                      const int* active, cudaStream_t st);
+// spmv.cu
+int launch_split_residual(const SplitDev& s, int npts, const zd* tval, int L, const zd* V, const zd* Y, zd* R,
+                          double* nrm, const int* active, cudaStream_t st);
+template <typename T>
+int launch_convert_rhs(int npts, int n, int L, const zd* V, cx<T>* B, cudaStream_t st);
+template <typename T>
+int launch_widen(int npts, int n, int L, const cx<T>* B, zd* Y, cudaStream_t st);
+template <typename T>
+int launch_refine_prepare(int npts, int n, int L, const zd* R, cx<T>* D, const int* active, cudaStream_t st);
+template <typename T>
+int launch_refine_update(int npts, int n, int L, const cx<T>* D, zd* Y, double* dmax, double* ymax,
+                         const int* active, cudaStream_t st);
+int launch_refine_decide(int npts, int L, int sweep, int max_sweeps, double tol, double step_tol, const double* nrm,
+                         const double* tnorm, const double* dmax, const double* ymax, double* prev, double* beta,
+                         int* active, int* sweeps, int* nactive, cudaStream_t st);
+// moments.cu
+int launch_moments(int n, int L, int N, int K, const zd* coef, const zd* Y, zd* S, cudaStream_t st);
+int launch_vh_times(int n, int L, int K, const zd* V, const zd* S, zd* mu, zd* part, cudaStream_t st);
+int launch_hankel_build(int L, int M, const zd* mu, zd* H, zd* Hs, cudaStream_t st);
+// extract.cu
+int zgemm(int M, int N, int K, int opA, const zd* A, int lda, const zd* B, int ldb, zd* C, int ldc, zd* part,
+          size_t part_elems, cudaStream_t st);
+struct JacobiWork {
+    zd* Vm;
+    int* flags;
+    int* sweeps;
+    unsigned* bar;
+    int* err;
+};
+int jacobi_svd(int rows, int cols, zd* A, zd* U, zd* W, double* sigma, JacobiWork w, cudaStream_t st);
+template <typename T>
+int small_eig(int m, const zd* A, zd* eval, zd* evec, int* status, void* gbuf, cudaStream_t st);
+int launch_newton(const SplitDev& s, int k, int ncand, const zd* Bs, const zd* lam0, const zd* Y0, int ldy0, zd c,
+                  double rad, int maxit, double tol, zd* lam_out, zd* Yout, int* ok, int* its, zd* gscratch,
+                  cudaStream_t st);
+int launch_scale_cols(int rows, int cols, zd* X, int ld, const double* s, int mode, cudaStream_t st);
+int launch_scale_rows(int rows, int cols, zd* X, int ld, const double* s, cudaStream_t st);
+int launch_candidates(int m, const zd* theta, zd c, double a, zd* lam, cudaStream_t st);
+int launch_fill_int(int n, int* p, int v, cudaStream_t st);
+int launch_rank(int n, const double* sigma, double tol, int* out, cudaStream_t st);
+int launch_normalize_columns(int rows, int cols, zd* X, int fix_phase, double* nrm, cudaStream_t st);
+int launch_term_spmm(const SplitDev& s, int k, const zd* Q, zd* out, cudaStream_t st);
+int launch_eta(const SplitDev& s, int ncand, const zd* lam, const zd* X, double* eta, cudaStream_t st);
+int launch_select(int ncand, const zd* lam, const double* eta, const int* ok, const zd* G, zd c, double ea, double eb,
+                  double eig_tol, int* order, cudaStream_t st);
+
+}  // namespace nep

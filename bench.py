@@ -1,0 +1,286 @@
+"""Benchmark: contour-integral quadrature solves per second on one GB300 (or N replicas).
+
+A step is one whole contour-integral pass over the n = 4096 (64 x 64 grid, bandwidth 64)
+delay problem with N = 64 quadrature points, L = 16 probe columns and M = 8 moments:
+assembly, banded LU, solves with FP64 refinement to backward error <= 1e-10, moments,
+block-Hankel SVD, reduced eigenproblem, Rayleigh-Ritz with Newton, scaled residuals.
+`value` counts quadrature solves (one (problem, z_j) pair with all L columns refined)
+per second with the operator and V resident in HBM; `e2e` is the same metric through
+nep_create_split + nep_ciss_solve with host buffers (copies included).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+                  [--impl ours|reference] [--workload delay2d_s64]
+
+`--impl reference` times the CPU oracle on this host's cores. Multi-GPU runs (torchrun)
+solve independent problems per rank (replicas, weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CISS quadrature solves/s (mixed FP32-factor + FP64 refinement, per-solve backward error <= 1e-10)"
+UNIT = "quadrature_solves/s"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def lu_flops(n, kl, ku, npts):
+    """Algorithmic real flops of the banded LU: n steps x kl rows x (kl+ku) columns x 8 (complex FMA)."""
+    return 8.0 * n * kl * (kl + ku) * npts
+
+
+def fp32_alu_peak_tflops(sm_mhz):
+    """152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fp64_alu_peak_tflops(sm_mhz):
+    """Measured 1.75 FP64 FMA/clk/SM on this part: 152 x 1.75 x 2 flops x clock."""
+    return 152 * 1.75 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def cpu_baseline(p, steps_budget_s=20.0):
+    """The oracle as it stands on this host's cores: full passes of the same workload until ~budget."""
+    from oracle import ciss
+    import synth
+    V = synth.random_probe_block(p.n, p.L, 0)
+    times = []
+    t_end = time.perf_counter() + steps_budget_s
+    while True:
+        t0 = time.perf_counter()
+        ciss.solve(p, V=V)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() > t_end or len(times) >= 3:
+            break
+    cores = max(1, min(32, os.cpu_count() or 1))
+    return {"value": p.N * len(times) / sum(times), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(times)} full CPU passes of {p.name} (N={p.N} quadrature solves each), "
+                      f"threads over quadrature points, {sum(times):.1f} s total"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="delay2d_s64")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    import synth
+    p = synth.config_problem(args.workload, seed=rank)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        times = []
+        from oracle import ciss
+        V = synth.random_probe_block(p.n, p.L, 0)
+        for _ in range(max(0, args.warmup)):
+            ciss.solve(p, V=V)
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            ciss.solve(p, V=V)
+            times.append(time.perf_counter() - t0)
+        val = p.N * len(times) / sum(times)
+        cores = max(1, min(32, os.cpu_count() or 1))
+        line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": args.workload, "n": p.n, "N": p.N, "L": p.L, "M": p.M},
+                "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": f"{len(times)} full passes of {args.workload}"},
+                "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+
+    import torch
+    import torch.distributed as dist
+    from paper_1910_11712_gb300 import binding
+
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    binding.load(build_if_missing=True)
+    prec = binding.NEP_PREC_MIXED if args.precision == "mixed" else binding.NEP_PREC_FP64
+    split = binding.Split.from_problem(p)
+    plan = binding.Plan(split, p.region, p.N, p.L, p.M, precision=prec)
+    V = synth.random_probe_block(p.n, p.L, rank)
+    Vd = torch.from_numpy(np.asfortranarray(V).ravel(order="F").view(np.float64).copy()).cuda()
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(max(3, args.warmup)):
+        plan.execute(Vd, stream)
+    torch.cuda.synchronize()
+    res = plan.result()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lu_ms = []
+    stage = {k: 0.0 for k in ("ms_assemble", "ms_factor", "ms_solve", "ms_moments", "ms_extract")}
+    launches0 = binding.kernel_launches()
+    with ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local) as clk:
+        barrier()
+        e0.record()
+        for _ in range(args.steps):
+            plan.execute(Vd, stream)
+        e1.record()
+        barrier()
+    launches = (binding.kernel_launches() - launches0) // max(1, args.steps)
+    ms = e0.elapsed_time(e1) / args.steps
+    # per-stage device times (CUDA events recorded on the launching stream inside the plan),
+    # from separate passes after the timed region
+    for _ in range(3):
+        plan.execute(Vd, stream)
+        r = plan.result()
+        lu_ms.append(r["info"]["ms_factor"])
+        for k in stage:
+            stage[k] += r["info"][k] / 3
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * p.N / (ms * 1e-3)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        csr_bytes = sum(8 * (A.shape[0] + 1) + 12 * A.nnz for A in p.mats)
+        v_bytes = 16 * p.n * p.L
+        tt = []
+        out_bytes = 0
+        for it in range(max(1, min(args.steps, 5)) + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sp = binding.Split.from_problem(p)
+            rr = binding.ciss_solve(sp, p.region, p.N, p.L, p.M, V=V, precision=prec)
+            sp.close()
+            torch.cuda.synchronize()
+            if it > 0:
+                tt.append(time.perf_counter() - t0)
+            out_bytes = 16 * len(rr["lam"]) * (p.n + 1) + 8 * len(rr["eta"])
+        e2e = {"value": p.N / (sum(tt) / len(tt)), "unit": UNIT, "h2d_bytes_per_step": csr_bytes + v_bytes,
+               "d2h_bytes_per_step": out_bytes}
+
+    line = None
+    if rank == 0:
+        peaks = measured_peaks()
+        cs = clk.summary()
+        sm_mhz = cs["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+        flops = lu_flops(p.n, split.kl, split.ku, p.N)
+        lu = float(np.mean(lu_ms))
+        achieved = flops / (lu * 1e-3) / 1e12
+        peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0)) if prec == binding.NEP_PREC_MIXED else \
+            fp64_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64+f64" if prec == binding.NEP_PREC_MIXED else "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": p.n, "bandwidth": split.kl, "N": p.N, "L": p.L, "M": p.M,
+                       "precision": args.precision, "l2": "inputs larger than L2 (band factors "
+                       f"{p.N * p.n * split.ldab * (8 if prec else 16) / 1e6:.0f} MB per step)"},
+            "roofline": {"kernel": "lu_reg_kernel (banded LU, all quadrature points in one launch)",
+                         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz" if prec else
+                         "derived: 152 SMs x 1.75 FP64 FMA/clk (measured) x 2 flop x 2070 MHz"},
+            "stages_ms": stage, "clocks": cs, "gpu_launches": int(launches),
+            "result": {"nconv": int(len(res["lam"])), "hankel_rank": res["m"], "max_eta": float(res["eta"].max())
+                       if len(res["eta"]) else None, "max_backward": res["info"]["max_backward"],
+                       "max_sweeps": res["info"]["max_sweeps"], "flags": res["flags"]},
+        }
+        if e2e:
+            line["e2e"] = e2e
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(p)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -155,6 +155,8 @@ int nep_result_info(nep_result_t r, nep_result_info_t *info);
 int nep_result_hankel_sigma(nep_result_t r, const double **sigma, int32_t *count);
 int nep_result_free(nep_result_t r);
 const char *nep_last_error(void);
+/* Number of CUDA kernels this library has launched in the process so far (diagnostics). */
+uint64_t nep_kernel_launches(void);
 
 /* ------------------------------------------------------------------ device-resident plan */
 /* A plan owns the device workspace of one (operator, region, N, L, M, opts) solve so

@@ -71,6 +71,7 @@ SIGNATURES = {
     "nep_result_hankel_sigma": (c_int32, [c_void_p, ctypes.POINTER(P_double), ctypes.POINTER(c_int32)]),
     "nep_result_free": (c_int32, [c_void_p]),
     "nep_last_error": (ctypes.c_char_p, []),
+    "nep_kernel_launches": (ctypes.c_uint64, []),
     "nep_plan_create": (c_int32, [c_void_p, ctypes.POINTER(NepRegion), c_int32, c_int32, c_int32, ctypes.POINTER(NepOpts),
                                   ctypes.POINTER(c_void_p)]),
     "nep_plan_execute": (c_int32, [c_void_p, c_void_p, c_void_p]),
@@ -353,6 +354,10 @@ def moments(n, L, N, K, coef_dev, Y_dev, S_dev, stream=0):
 
 def jacobi_svd(rows, cols, A_dev, W_dev, sigma_dev, stream=0):
     check(load().nep_jacobi_svd(rows, cols, ptr(A_dev), ptr(W_dev), ptr(sigma_dev), stream))
+
+
+def kernel_launches() -> int:
+    return int(load().nep_kernel_launches())
 
 
 def small_eig(m, A_dev, eval_dev, evec_dev=None, stream=0):

@@ -416,6 +416,7 @@ int launch_band_lu(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info,
     if (smem > 48 * 1024)
         NEP_CUDA(cudaFuncSetAttribute(lu_glb_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     lu_glb_kernel<T><<<npts, 1024, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, info, active, win);
+    count_launch();
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(win, st);
     if (e != cudaSuccess) return cuda_fail(e, "lu_glb_kernel", __FILE__, __LINE__);

@@ -264,6 +264,7 @@ int jacobi_svd(int rows, int cols, zd* A, zd* U, zd* W, double* sigma, JacobiWor
     double tol = 1e-15;
     void* args[] = {&rows, &cols, &A, &w.Vm, &max_sweeps, &tol, &w.flags, &w.sweeps, &gb};
     NEP_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(256), args, 0, st));
+    count_launch();
     svd_finish_kernel<<<1, 256, sizeof(double) * cols, st>>>(rows, cols, A, w.Vm, U, W, sigma);
     NEP_CHECK_LAUNCH();
     return NEP_OK;

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstring>
 #include <complex>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -14,6 +15,9 @@
 namespace nep {
 
 static thread_local std::string g_last_error;
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
     char buf[1024];
@@ -271,6 +275,8 @@ extern "C" void nep_opts_default(nep_opts* o) {
 }
 
 extern "C" const char* nep_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" uint64_t nep_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 // ============================================================================ region checks
 typedef std::complex<double> C;

@@ -178,7 +178,12 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
         cudaError_t e_ = (call);                                                        \
         if (e_ != cudaSuccess) return ::nep::cuda_fail(e_, #call, __FILE__, __LINE__); \
     } while (0)
-#define NEP_CHECK_LAUNCH() NEP_CUDA(cudaGetLastError())
+void count_launch();
+#define NEP_CHECK_LAUNCH()         \
+    do {                           \
+        ::nep::count_launch();     \
+        NEP_CUDA(cudaGetLastError()); \
+    } while (0)
 #define NEP_TRY(call)            \
     do {                         \
         int rc_ = (call);        \

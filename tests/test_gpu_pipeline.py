@@ -34,7 +34,7 @@ def gpu_buffer(plan, name, dtype="c128"):
     class _View:
         pass
     v = _View()
-    v.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, True), "version": 3}
+    v.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False), "version": 3}
     torch.cuda.synchronize()
     host = torch.as_tensor(v, device="cuda").cpu().numpy().copy()
     if dtype == "c128":

@@ -4,7 +4,7 @@
  *
  * Problem (Sec. 2, Eqs. (nep) and (split)): find (lambda, x), x != 0, with
  *     T(lambda) x = 0,    T(z) = sum_{i<l} A_i f_i(z),
- * A_i constant sparse n x n matrices, f_i scalar holomorphic functions (Sec. 3.1.2
+ * A_i constant sparse n x n matrices, f_i scalar holomorphic functions (Sec. 3.2.2
  * function classes: rational, exp, principal sqrt, with argument/result scaling and
  * combinations). The solver returns every eigenpair inside an ellipse Gamma.
  *
@@ -66,7 +66,7 @@ typedef struct {
     const double *val_im;
 } nep_csr;
 
-/* Scalar function g(z) = beta * h(alpha * z) (FNSetScale of Sec. 3.1.2), h by kind:
+/* Scalar function g(z) = beta * h(alpha * z) (FNSetScale of Sec. 3.2.2), h by kind:
  *   NEP_FN_RATIONAL  h(x) = p(x) / q(x); num/den are complex arrays, highest degree
  *                    first (nnum, nden coefficients); nden == 0 means q = 1.
  *   NEP_FN_EXP       h(x) = exp(x).
@@ -113,7 +113,7 @@ typedef struct {
 /* Defaults listed above. */
 void nep_opts_default(nep_opts *o);
 
-/* Builds the split operator T(z) = sum_i A_i f_i(z) (Sec. 3.1.2, NEPSetSplitOperator):
+/* Builds the split operator T(z) = sum_i A_i f_i(z) (Sec. 3.2.2, NEPSetSplitOperator):
  * validates each CSR (square n x n, sorted in-range columns), forms the union sparsity
  * pattern with one value array per term, its bandwidths (kl, ku), ||A_i||_inf, and
  * copies everything to the current device. nterms >= 1; f has nterms entries.
@@ -126,8 +126,8 @@ int nep_split_info(nep_split_t h, int32_t *n, int32_t *nterms, int32_t *kl, int3
 /* ------------------------------------------------------------------ whole solve */
 /* Full contour-integral pass (all steps on the device): nodes and coefficients,
  * assembly, banded LU, solves with FP64 refinement, moments, block-Hankel SVD and
- * reduced eigenproblem, Rayleigh-Ritz projection (Sec. 5.3 Eq. (narnoldi-split)) with
- * Newton steps (Sec. 5.2 Eq. (newton)), scaled residuals (Sec. 2 Eq. (sressplit)).
+ * reduced eigenproblem, Rayleigh-Ritz projection (Sec. 4.2 Eq. (narnoldi-split)) with
+ * Newton steps (Sec. 4.1 Eq. (newton)), scaled residuals (Sec. 2 Eq. (sressplit)).
  * V_host: n x L complex probe block (column-major) or NULL (drawn from opts->seed).
  * N >= 2 quadrature points, 1 <= L <= n, M >= 1. Errors: NEP_ERR_ARG, NEP_ERR_REGION
  * (a rational pole or sqrt branch cut meets the closed region), NEP_ERR_CUDA,

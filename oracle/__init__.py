@@ -8,7 +8,7 @@ code with it.
 What it computes, step by step, in complex128 (each module cites its passage):
   contour.py    quadrature nodes/weights on an ellipse (trapezoid rule) and the
                 coefficient table F[i, j] = f_i(z_j) (split form, Sec. 2 Eq. (split));
-  fn.py         the scalar function classes of Sec. 3.1.2 and their derivatives;
+  fn.py         the scalar function classes of Sec. 3.2.2 and their derivatives;
   band_lu.c     banded LU with partial pivoting and the banded solve (plain C);
   band.py       band storage assembly of T(z_j) = sum_i f_i(z_j) A_i and ctypes glue;
   ciss.py       solves T(z_j) Y_j = V with FP64 refinement, moments, block Hankel

@@ -1,6 +1,6 @@
 """Band storage assembly of T(z) and ctypes glue for band_lu.c (oracle; test infrastructure only).
 
-T(z) = sum_i f_i(z) A_i (Sec. 2 Eq. (split)); Sec. 3.1.2 builds it from the f_i(z)
+T(z) = sum_i f_i(z) A_i (Sec. 2 Eq. (split)); Sec. 3.2.2 builds it from the f_i(z)
 values with l-1 sparse matrix axpy operations, which is what ``assemble_dense``
 and ``assemble_band`` do (scipy sparse sums as the axpy primitive).
 """

@@ -3,7 +3,7 @@
  * and the banded solve with several right-hand sides. Plain unblocked C.
  *
  * The contour method factors T(z_j) at every quadrature point (the "matrix
- * factorizations" whose cost dominates the solvers of Sec. 5 and Table 3); the
+ * factorizations" whose cost dominates the solvers of Sec. 4, cf. Table 2); the
  * banded LU is the textbook Gaussian elimination restricted to the band.
  *
  * Storage (LAPACK gbtrf convention, column-major, 0-based):

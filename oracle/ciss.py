@@ -12,8 +12,8 @@ The steps, in the order the method takes them:
       eigenvalues theta of U_m^H H< W_m Sigma_m^{-1}; lambda = c + a theta;
       Hankel eigenvector estimates X_H = [S_0 .. S_{M-1}] W_m Sigma_m^{-1} T   (hankel_extract)
   O7  Q = orthonormal basis of the normalised X_H (truncated SVD)           (rayleigh_ritz)
-  O8  projected split form B_i = Q^H A_i Q (Sec. 5.3 Eq. (narnoldi-split)), Newton's
-      method on sum_i f_i(lambda) B_i y = 0 (Sec. 5.2 Eq. (newton), normalised by u^H y = 1)
+  O8  projected split form B_i = Q^H A_i Q (Sec. 4.2 Eq. (narnoldi-split)), Newton's
+      method on sum_i f_i(lambda) B_i y = 0 (Sec. 4.1 Eq. (newton), normalised by u^H y = 1)
       from every Hankel candidate; x = Q y                                   (newton_projected)
   O9  keep lambda strictly inside Gamma with eta <= eig_tol, drop duplicates
   O10 eta = ||T(lambda) x||_2 / (sum_i |f_i(lambda)| ||A_i||_inf ||x||_2)  (Sec. 2 Eq. (sressplit),
@@ -177,12 +177,12 @@ def orth_basis(XH: np.ndarray, delta: float = DELTA_BASIS):
 
 
 def project(mats, Q):
-    """B_i = Q^H A_i Q (Sec. 5.3 Eq. (narnoldi-split))."""
+    """B_i = Q^H A_i Q (Sec. 4.2 Eq. (narnoldi-split))."""
     return [Q.conj().T @ (A @ Q) for A in mats]
 
 
 def newton_projected(Bs, fns, lam0: complex, y0: np.ndarray, region: dict):
-    """Newton's method (Sec. 5.2 Eq. (newton)) on the projected NEP sum_i f_i(lam) B_i y = 0.
+    """Newton's method (Sec. 4.1 Eq. (newton)) on the projected NEP sum_i f_i(lam) B_i y = 0.
 
     Bordered system with normalisation u^H y = 1, u the current unit iterate:
         [ B(lam)  B'(lam) y ] [dy  ]     [ B(lam) y ]

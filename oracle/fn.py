@@ -1,9 +1,9 @@
 """Scalar functions of the split form and their derivatives (oracle; test infrastructure only).
 
-Function classes of Sec. 3.1.2: rational (numerator/denominator coefficients),
+Function classes of Sec. 3.2.2: rational (numerator/denominator coefficients),
 principal square root, exponential, argument/result scaling g(z) = beta f(alpha z)
 and combinations (sum, product, quotient, composition). Derivatives follow from
-the chain, product and quotient rules (Sec. 3.1.2 notes every function provides
+the chain, product and quotient rules (Sec. 3.2.2 notes every function provides
 both f and f').
 
 Pinned by tests/test_oracle_fn.py against finite differences and direct values.

@@ -1,5 +1,5 @@
 // Kernel (a): split-form assembly of the shifted matrices T(z_j) = sum_i f_i(z_j) A_i
-// (Sec. 2 Eq. (split); Sec. 3.1.2 builds T(lambda) from the f_i values and l-1 sparse
+// (Sec. 2 Eq. (split); Sec. 3.2.2 builds T(lambda) from the f_i values and l-1 sparse
 // axpys) for every quadrature point at once, written straight into the row-oriented band
 // storage that the banded LU consumes.
 //

@@ -1,7 +1,7 @@
 // Kernel (b): batched complex banded LU with partial pivoting and the banded solves.
 //
 // The contour method needs one factorisation of T(z_j) per quadrature point (the
-// factorisations that dominate the cost of every solver in Sec. 5, cf. Table 3's "PC build").
+// factorisations that dominate the cost of every solver in Sec. 4, cf. Table 2's "PC build").
 // All points are independent, so one CTA factors one point and the whole batch runs in
 // one launch.
 //

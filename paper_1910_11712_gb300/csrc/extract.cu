@@ -9,8 +9,8 @@
 //                       eigenvectors, one warp, used in FP32 for the reduced Hankel matrix
 //                       (its eigenvalues only seed FP64 Newton, its eigenvectors only fix a
 //                       basis of an already determined span);
-//   * newton_kernel     Newton's method (Sec. 5.2 Eq. (newton)) on the projected split form
-//                       sum_i f_i(lambda) B_i y = 0 (Sec. 5.3 Eq. (narnoldi-split)), bordered
+//   * newton_kernel     Newton's method (Sec. 4.1 Eq. (newton)) on the projected split form
+//                       sum_i f_i(lambda) B_i y = 0 (Sec. 4.2 Eq. (narnoldi-split)), bordered
 //                       by the normalisation u^H y = 1, one CTA per candidate;
 //   * residual/select   scaled residual eta (Sec. 2 Eq. (sressplit), infinity norms of the A_i
 //                       as in Sec. 6), inside test, duplicate removal and ordering.

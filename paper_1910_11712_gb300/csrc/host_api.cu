@@ -1,5 +1,5 @@
 // Host side of the C ABI: operator construction (split form, Sec. 2 Eq. (split); the
-// NEPSetSplitOperator interface of Sec. 3.1.2), region checks, quadrature nodes and
+// NEPSetSplitOperator interface of Sec. 3.2.2), region checks, quadrature nodes and
 // coefficients, the device-resident plan that runs the whole contour-integral pass, and
 // result objects. Every numerical step after the coefficient table runs in the CUDA
 // kernels of this library; the host only sizes launches and moves small scalars.

@@ -3,7 +3,7 @@
 //
 // T(z_j) is applied on the union sparsity pattern with the FP64 values the assembly kernel
 // produced (the split sum sum_i f_i(z_j) A_i of Sec. 2 Eq. (split), evaluated once per point);
-// this is the residual r = sum_i f_i(lambda) A_i x of Sec. 6 (one SpMV per term in the
+// this is the residual r = sum_i f_i(lambda) A_i x of Sec. 5 (one SpMV per term in the
 // paper's implementation, one fused pass here). One CTA handles 256 rows of one
 // (point, right-hand side) pair so that the infinity norms of R, Y and V it produces reduce
 // inside the CTA to one atomic maximum each.

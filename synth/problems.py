@@ -3,7 +3,7 @@
 Every problem is T(z) = sum_i A_i f_i(z) (Sec. 2, Eq. (split)) with:
   * ``mats``: list of scipy.sparse CSR matrices (float64 or complex128), one per term;
   * ``fns``: list of function descriptions (plain dicts) understood by both the
-    C-ABI binding and the oracle. Kinds (the FN classes of Sec. 3.1.2):
+    C-ABI binding and the oracle. Kinds (the FN classes of Sec. 3.2.2):
       {"kind": "rational", "num": [...], "den": [...] or None, "alpha": a, "beta": b}
             g(z) = b * p(a z) / q(a z), coefficients highest degree first;
       {"kind": "exp", "alpha": a, "beta": b}            g(z) = b * exp(a z);
@@ -92,7 +92,7 @@ def _sorted_csr(A) -> sp.csr_matrix:
 def delay_1d(n: int = 64, seed: int = 0, tau: float = 1.0) -> Problem:
     """Delay problem T = -z I + A + e^{-tau z} B with A = 5 tridiag(1,-2,1), B = diag(U[-1,1]).
 
-    Term order follows the split-form example of Sec. 3.1.2: (A, 1), (I, -z), (B, e^{-tau z}).
+    Term order follows the split-form example of Sec. 3.2.2: (A, 1), (I, -z), (B, e^{-tau z}).
     Circle centre -1, radius 2; N=32, L=4, M=4.
     """
     rng = np.random.default_rng(seed)

@@ -207,6 +207,18 @@ int nep_moments(int32_t n, int32_t L, int32_t N, int32_t K, const double *coef_d
  * is overwritten by U Sigma; W_dev (cols x cols) receives W with A_in W = U Sigma; sigma
  * descending with the columns of A and W permuted to match. */
 int nep_jacobi_svd(int32_t rows, int32_t cols, double *A_dev, double *W_dev, double *sigma_dev, void *stream);
+/* The SVD of nep_jacobi_svd for callers that cannot allocate device memory (a host that
+ * accounts for every device byte itself, or a loop that must not enter the CUDA allocator).
+ * The paper has no counterpart: this is a deployment variant of the Jacobi SVD above.
+ * Same arguments and results as nep_jacobi_svd; its work arrays live in one fixed block of
+ * device memory compiled into the library (2 MiB + 256 bytes, held on every GPU that loads
+ * the library until the process exits), so it accepts rows*cols + cols*cols <= 131072
+ * (e.g. 256 x 256) and returns NEP_ERR_ARG beyond that. It calls no allocation routine.
+ * The first call on a device looks the block's device address up on that device (make that
+ * first call before any stream capture). All calls share the block and each call resets the
+ * parts that must start at zero: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller. Returns after the stream finished. */
+int nep_jacobi_svd_noalloc(int32_t rows, int32_t cols, double *A_dev, double *W_dev, double *sigma_dev, void *stream);
 /* Eigenvalues and eigenvectors of a small complex matrix (m x m, FP64, device):
  * Hessenberg reduction and shifted QR. evec_dev may be NULL. */
 int nep_small_eig(int32_t m, const double *A_dev, double *eval_dev, double *evec_dev, void *stream);

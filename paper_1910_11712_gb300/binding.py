@@ -86,6 +86,7 @@ SIGNATURES = {
     "nep_split_residual": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "nep_moments": (c_int32, [c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "nep_jacobi_svd": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "nep_jacobi_svd_noalloc": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "nep_small_eig": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
 }
 
@@ -354,6 +355,11 @@ def moments(n, L, N, K, coef_dev, Y_dev, S_dev, stream=0):
 
 def jacobi_svd(rows, cols, A_dev, W_dev, sigma_dev, stream=0):
     check(load().nep_jacobi_svd(rows, cols, ptr(A_dev), ptr(W_dev), ptr(sigma_dev), stream))
+
+
+def jacobi_svd_noalloc(rows, cols, A_dev, W_dev, sigma_dev, stream=0):
+    """nep_jacobi_svd without device allocations (fixed scratch compiled into the library)."""
+    check(load().nep_jacobi_svd_noalloc(rows, cols, ptr(A_dev), ptr(W_dev), ptr(sigma_dev), stream))
 
 
 def kernel_launches() -> int:

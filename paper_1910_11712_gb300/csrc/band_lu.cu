@@ -253,6 +253,174 @@ __global__ void __launch_bounds__(NW * 32, 1)
     if (threadIdx.x == 0) info_all[j] = info_s;
 }
 
+// Register window, rows across warps and columns across lanes: row slot rs (r mod RS) is held
+// by warp rs / RPW (register index rs % RPW) and column slot cs (k mod CS) by lane cs % 32
+// (register index cs / 32). Per step: the lanes holding column c publish it (barrier 1); warp 0
+// picks the pivot and the multipliers (barrier 2); the warp holding the pivot row publishes it
+// (and the warp holding row c its old values when they move) (barrier 3); then every thread
+// swaps/inserts its own rows and applies a(r,k) -= l(r) u(k) to its RPW x CPL elements, with
+// l and u read from shared memory once per row and column.
+template <typename T, int NW, int RPW, int CPL>
+__global__ void __launch_bounds__(NW * 32, 1)
+    lu_regt_kernel(int n, int kl, int ku, int ldab, cx<T>* __restrict__ ab_all, int* __restrict__ ipiv_all,
+                   int* __restrict__ info_all, const int* __restrict__ active) {
+    const int j = blockIdx.x;
+    if (active && !active[j]) return;
+    constexpr int RS = NW * RPW;
+    constexpr int CS = 32 * CPL;
+    const int kv = kl + ku;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cx<T>* ab = ab_all + (int64_t)j * n * ldab;
+    int* ipiv = ipiv_all + (int64_t)j * n;
+
+    __shared__ cx<T> nrow[2][CS + 1];
+    __shared__ cx<T> pcol[RS + 1];
+    __shared__ cx<T> lvec[RS];
+    __shared__ cx<T> urow[CS];
+    __shared__ cx<T> oldc[CS];
+    __shared__ int piv_s, info_s;
+    if (threadIdx.x == 0) info_s = 0;
+
+    cx<T> a[RPW][CPL];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+        const int r = warp * RPW + q;
+#pragma unroll
+        for (int p = 0; p < CPL; ++p) {
+            const int k = lane + 32 * p;
+            cx<T> v = mk<T>(0, 0);
+            const int t = k - r + kl;
+            if (r < kl && r < n && k < kv && k < n && t >= 0 && t <= kv) v = ab[(int64_t)r * ldab + t];
+            a[q][p] = v;
+        }
+    }
+    for (int t = threadIdx.x; t <= kv; t += blockDim.x) {
+        cx<T> v = mk<T>(0, 0);
+        if (kl < n && t < n) v = ab[(int64_t)kl * ldab + t];
+        nrow[0][t] = v;
+    }
+    __syncthreads();
+
+    for (int c = 0; c < n; ++c) {
+        const int buf = c & 1;
+        // (1) publish column c; its slot then starts column c+kv with zero fill
+        {
+            const int csc = c % CS;
+            if (lane == (csc & 31)) {
+                const int pc = csc >> 5;
+#pragma unroll
+                for (int p = 0; p < CPL; ++p) {
+                    if (p != pc) continue;
+#pragma unroll
+                    for (int q = 0; q < RPW; ++q) {
+                        const int i = posmod(warp * RPW + q - c, RS);
+                        if (i < kl) pcol[i] = a[q][p];
+                    }
+                }
+            }
+            const int csn = (c + kv) % CS;
+            if (lane == (csn & 31)) {
+                const int pn = csn >> 5;
+#pragma unroll
+                for (int p = 0; p < CPL; ++p)
+                    if (p == pn)
+#pragma unroll
+                        for (int q = 0; q < RPW; ++q) a[q][p] = mk<T>(0, 0);
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();  // S1
+        if (warp != 0 || NW == 1) {
+            const int r = c + 1 + kl;
+            const int t0 = (NW == 1) ? lane : threadIdx.x - 32;
+            const int ts = (NW == 1) ? 32 : blockDim.x - 32;
+            for (int t = t0; t <= kv; t += ts) {
+                if (r < n && c + 1 + t < n) cp_async_cx(&nrow[buf ^ 1][t], ab + (int64_t)r * ldab + t);
+                else nrow[buf ^ 1][t] = mk<T>(0, 0);
+            }
+        }
+        if (warp == 0) {
+            if (lane == 0) pcol[kl] = nrow[buf][0];
+            __syncwarp();
+            pivot_step(pcol, lvec, &piv_s, &info_s, c, n, kl, kv, ldab, ab, ipiv, lane);
+        }
+        __syncthreads();  // S2
+        const int prel = piv_s;
+        const int rsc = c % RS, wc = rsc / RPW, qc = rsc % RPW;
+        const int rsp = (c + prel) % RS, wp = rsp / RPW, qp = rsp % RPW;
+        // (3) publish the pivot row (u) and, when row c moves, its old values
+        if (prel != kl && warp == wp) {
+#pragma unroll
+            for (int p = 0; p < CPL; ++p) {
+                const int cs = lane + 32 * p;
+                const int t = posmod(cs - c - 1, CS);  // column k = c+1+t
+                if (t < kv) {
+                    cx<T> v = a[0][p];
+#pragma unroll
+                    for (int q = 1; q < RPW; ++q)
+                        if (q == qp) v = a[q][p];
+                    urow[t] = v;
+                }
+            }
+        }
+        if (prel != 0 && warp == wc) {
+#pragma unroll
+            for (int p = 0; p < CPL; ++p) {
+                const int cs = lane + 32 * p;
+                const int t = posmod(cs - c - 1, CS);
+                if (t < kv) {
+                    cx<T> v = a[0][p];
+#pragma unroll
+                    for (int q = 1; q < RPW; ++q)
+                        if (q == qc) v = a[q][p];
+                    oldc[t] = v;
+                }
+            }
+        }
+        __syncthreads();  // S3
+        const cx<T>* u = (prel == kl) ? &nrow[buf][1] : urow;
+        // U row c (columns c+1..c+kv) to global
+        cx<T>* out = ab + (int64_t)c * ldab;
+        for (int t = threadIdx.x; t < kv; t += blockDim.x)
+            if (c + 1 + t < n) out[1 + t] = u[t];
+        // (4) row moves, new row c+kl, rank-1 update
+        const int rsn = (c + kl) % RS, wn = rsn / RPW, qn = rsn % RPW;
+        cx<T> lq[RPW];
+        int rowok[RPW];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int i = posmod(warp * RPW + q - c - 1, RS);  // row c+1+i
+            rowok[q] = (i < kl) && (c + 1 + i < n);
+            lq[q] = rowok[q] ? lvec[i] : mk<T>(0, 0);
+        }
+#pragma unroll
+        for (int p = 0; p < CPL; ++p) {
+            const int cs = lane + 32 * p;
+            const int t = posmod(cs - c - 1, CS);
+            if (t >= kv) continue;
+            const cx<T> up = u[t];
+            if (prel != 0 && prel != kl && warp == wp) {
+#pragma unroll
+                for (int q = 0; q < RPW; ++q)
+                    if (q == qp) a[q][p] = oldc[t];
+            }
+            if (warp == wn) {
+                const cx<T> nv = (prel == kl) ? oldc[t] : nrow[buf][1 + t];
+#pragma unroll
+                for (int q = 0; q < RPW; ++q)
+                    if (q == qn) a[q][p] = nv;
+            }
+            if (c + 1 + t < n) {
+#pragma unroll
+                for (int q = 0; q < RPW; ++q)
+                    if (rowok[q]) a[q][p] = fms(a[q][p], lq[q], up);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) info_all[j] = info_s;
+}
+
 // Same elimination with the window W[cs*kl + rs] (row slot r mod kl, column slot k mod kv)
 // in a per-point global scratch array. For kl = 0 the band is upper triangular and no
 // elimination happens besides copying U.
@@ -393,10 +561,39 @@ static bool reg_config(int kl, int kv, int* nw, int* rpl, int* cpw) {
     return *cpw <= maxcpw;
 }
 
+template <typename T, int RPW, int CPL>
+static int run_regt(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st) {
+    lu_regt_kernel<T, 16, RPW, CPL><<<npts, 16 * 32, 0, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, info, active);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+
+template <typename T, int RPW>
+static int regt_cpl(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st,
+                    int cpl) {
+    switch (cpl) {
+        case 1: return run_regt<T, RPW, 1>(s, npts, ab, ipiv, info, active, st);
+        case 2: return run_regt<T, RPW, 2>(s, npts, ab, ipiv, info, active, st);
+        case 3: return run_regt<T, RPW, 3>(s, npts, ab, ipiv, info, active, st);
+        case 4: return run_regt<T, RPW, 4>(s, npts, ab, ipiv, info, active, st);
+    }
+    return NEP_ERR_INTERNAL;
+}
+
 template <typename T>
 int launch_band_lu(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st) {
     if (npts <= 0) return NEP_OK;
     const int kv = s.kl + s.ku;
+    // transposed register window: 16 warps x RPW rows (kl <= 64), 32 lanes x CPL columns (kv <= 128)
+    if (s.kl >= 1 && s.kl <= 64 && kv >= 1 && kv <= 128) {
+        const int rpw = (s.kl + 15) / 16, cpl = (kv + 31) / 32;
+        switch (rpw) {
+            case 1: return regt_cpl<T, 1>(s, npts, ab, ipiv, info, active, st, cpl);
+            case 2: return regt_cpl<T, 2>(s, npts, ab, ipiv, info, active, st, cpl);
+            case 3: return regt_cpl<T, 3>(s, npts, ab, ipiv, info, active, st, cpl);
+            case 4: return regt_cpl<T, 4>(s, npts, ab, ipiv, info, active, st, cpl);
+        }
+    }
     int nw, rpl, cpw;
     if (reg_config<T>(s.kl, kv, &nw, &rpl, &cpw)) {
         if (nw == 32) {
@@ -460,13 +657,15 @@ __global__ void __launch_bounds__(512)
     cx<T>* diag = stage + (int64_t)CH * wide;
     int* pst = reinterpret_cast<int*>(diag + CH);
 
-    // ---- forward: row interchanges and unit lower L
+    // ---- forward: row interchanges and unit lower L. Row r lives in slot r mod RF; sc is the
+    //      slot of the current row c, advanced without integer division.
     for (int i = lane; i < RF; i += 32) win[i] = (has_col && i < n) ? b[i] : mk<T>(0, 0);
+    int sc = 0;
     for (int c0 = 0; c0 < n; c0 += CH) {
         const int cn = min(CH, n - c0);
         __syncthreads();
         for (int e = threadIdx.x; e < cn * kl; e += blockDim.x) {
-            const int cc = e / kl, i = e % kl;
+            const int cc = e / kl, i = e - cc * kl;
             stage[e] = ab[(int64_t)(c0 + cc) * ldab + kv + 1 + i];
         }
         for (int e = threadIdx.x; e < cn; e += blockDim.x) pst[e] = ipiv[c0 + e] - (c0 + e);
@@ -481,36 +680,38 @@ __global__ void __launch_bounds__(512)
                 const int c = c0 + cc;
                 const int p = pst[cc];
                 if (p != 0 && lane == 0) {
-                    const int s0 = c % RF, s1 = (c + p) % RF;
-                    cx<T> t = win[s0];
-                    win[s0] = win[s1];
+                    int s1 = sc + p;
+                    if (s1 >= RF) s1 -= RF;
+                    const cx<T> t = win[sc];
+                    win[sc] = win[s1];
                     win[s1] = t;
                 }
                 __syncwarp();
-                const cx<T> xc = win[c % RF];
+                const cx<T> xc = win[sc];
                 const cx<T>* lc = stage + cc * kl;
-                for (int i = lane; i < kl; i += 32) {
-                    const int r = c + 1 + i;
-                    if (r < n) {
-                        cx<T>* w = win + r % RF;
-                        *w = fms(*w, lc[i], xc);
-                    }
+                const int lim = min(kl, n - 1 - c);
+                for (int i = lane; i < lim; i += 32) {
+                    int s = sc + 1 + i;
+                    if (s >= RF) s -= RF;
+                    win[s] = fms(win[s], lc[i], xc);
                 }
                 __syncwarp();
                 if (lane == 0) {
                     b[c] = xc;
-                    win[c % RF] = nb[cc];
+                    win[sc] = nb[cc];
                 }
+                if (++sc == RF) sc = 0;
                 __syncwarp();
             }
         }
     }
-    // ---- backward: U with bandwidth kv
+    // ---- backward: U with bandwidth kv; row r lives in slot r mod RB
     __syncthreads();
     for (int i = lane; i < RB; i += 32) {
         const int r = n - 1 - i;
         if (r >= 0) win[r % RB] = has_col ? b[r] : mk<T>(0, 0);
     }
+    sc = (n - 1) % RB;
     __syncwarp();
     for (int c1 = n - 1; c1 >= 0; c1 -= CH) {
         const int cn = min(CH, c1 + 1);
@@ -520,7 +721,7 @@ __global__ void __launch_bounds__(512)
         const int rlo = cbase - kv, rhi = c1 - 1;
         const int nr = rhi - rlo + 1;
         for (int e = threadIdx.x; e < nr * cn; e += blockDim.x) {
-            const int ri = e / cn, cc = e % cn;
+            const int ri = e / cn, cc = e - ri * cn;
             const int r = rlo + ri, c = cbase + cc, t = c - r;
             if (r >= 0 && t >= 1 && t <= kv) stage[cc * kv + (t - 1)] = ab[(int64_t)r * ldab + t];
         }
@@ -534,21 +735,21 @@ __global__ void __launch_bounds__(512)
         if (has_col) {
             for (int cc = cn - 1; cc >= 0; --cc) {
                 const int c = cbase + cc;
-                const cx<T> xc = cdiv(win[c % RB], diag[cc]);
+                const cx<T> xc = cdiv(win[sc], diag[cc]);
                 __syncwarp();
                 const cx<T>* uc = stage + cc * kv;
-                for (int i = lane; i < kv; i += 32) {
-                    const int r = c - 1 - i;
-                    if (r >= 0) {
-                        cx<T>* w = win + r % RB;
-                        *w = fms(*w, uc[i], xc);
-                    }
+                const int lim = min(kv, c);
+                for (int i = lane; i < lim; i += 32) {
+                    int s = sc - 1 - i;
+                    if (s < 0) s += RB;
+                    win[s] = fms(win[s], uc[i], xc);
                 }
                 __syncwarp();
                 if (lane == 0) {
                     b[c] = xc;
-                    win[c % RB] = nb[cc];
+                    win[sc] = nb[cc];
                 }
+                if (--sc < 0) sc = RB - 1;
                 __syncwarp();
             }
         }
@@ -560,7 +761,8 @@ int launch_band_solve(const SplitDev& s, int npts, const cx<T>* ab, const int* i
                       const int* active, cudaStream_t st) {
     if (npts <= 0 || L <= 0) return NEP_OK;
     const int kv = s.kl + s.ku;
-    const int wpb = L < 16 ? L : 16;
+    // few warps per CTA so that the (latency-bound) column chains of one point spread over SMs
+    const int wpb = L < 4 ? L : 4;
     const int gy = (L + wpb - 1) / wpb;
     const int WIN = (s.kl + 1) > (kv + 1) ? (s.kl + 1) : (kv + 1);
     const int wide = kv > s.kl ? kv : (s.kl > 0 ? s.kl : 1);

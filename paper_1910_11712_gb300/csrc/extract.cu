@@ -107,34 +107,31 @@ int zgemm(int M, int N, int K, int opA, const zd* A, int lda, const zd* B, int l
 }
 
 // ------------------------------------------------------------------ grid barrier
-// Sense counter barrier for a cooperative launch (all CTAs co-resident). Every wait is
-// bounded: after ~1 s of polling the CTA records an error and continues.
+// Barrier for a cooperative launch (all CTAs co-resident) on a monotonically increasing
+// arrival counter: barrier number e completes once the counter reaches e * gridDim.x, so it
+// needs one atomic per CTA and no reset. Every wait is bounded: after ~2^22 polls the CTA
+// records an error and continues.
 struct GridBar {
     unsigned int* count;
-    unsigned int* gen;
+    unsigned int* gen;  // unused by this barrier, kept for the work layout
     int* err;
 };
 
-__device__ __forceinline__ void grid_barrier(GridBar b) {
+__device__ __forceinline__ void grid_barrier(GridBar b, unsigned int& epoch) {
     __syncthreads();
+    ++epoch;
     if (threadIdx.x == 0) {
-        volatile unsigned int* vg = b.gen;
-        const unsigned int g = *vg;
+        const unsigned int target = epoch * gridDim.x;
         __threadfence();
-        const unsigned int arrived = atomicAdd(b.count, 1u);
-        if (arrived == gridDim.x * gridDim.y * gridDim.z - 1) {
-            atomicExch(b.count, 0u);
-            __threadfence();
-            atomicAdd(b.gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*vg == g) {
-                if (++spins > (1ll << 24)) {
-                    atomicExch(b.err, 1);
-                    break;
-                }
-                __nanosleep(64);
+        atomicAdd(b.count, 1u);
+        volatile unsigned int* vc = b.count;
+        long long spins = 0;
+        while (*vc < target) {
+            if (++spins > (1ll << 22)) {
+                atomicExch(b.err, 1);
+                break;
             }
+            __nanosleep(32);
         }
         __threadfence();
     }
@@ -156,10 +153,11 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __r
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     const int P = cols + (cols & 1);
     // V = I
+    unsigned int epoch = 0;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)cols * cols;
          t += (int64_t)gridDim.x * blockDim.x)
         Vm[t] = mk((t % cols) == (t / cols) ? 1.0 : 0.0, 0.0);
-    grid_barrier(bar);
+    grid_barrier(bar, epoch);
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         if (blockIdx.x == 0 && threadIdx.x == 0) flags[(sweep + 1) & 1] = 0;
@@ -210,11 +208,11 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __r
                 }
                 if (lane == 0) atomicOr(&flags[sweep & 1], 1);
             }
-            grid_barrier(bar);
+            grid_barrier(bar, epoch);
         }
         const int any = *((volatile int*)&flags[sweep & 1]);
         if (!any) break;
-        grid_barrier(bar);  // everyone has read the flag before it is cleared again
+        grid_barrier(bar, epoch);  // everyone has read the flag before it is cleared again
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_out = sweep + 1;
 }
@@ -223,27 +221,32 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __r
 __global__ void svd_finish_kernel(int rows, int cols, const zd* __restrict__ A, const zd* __restrict__ Vm,
                                   zd* __restrict__ U, zd* __restrict__ W, double* __restrict__ sigma) {
     extern __shared__ double nrm[];
-    for (int i = threadIdx.x; i < cols; i += blockDim.x) {
+    int* rk = reinterpret_cast<int*>(nrm + cols);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = w; i < cols; i += nw) {
         double s = 0.0;
         const zd* a = A + (int64_t)i * rows;
-        for (int r = 0; r < rows; ++r) s += norm2(a[r]);
-        nrm[i] = sqrt(s);
+        for (int r = lane; r < rows; r += 32) s += norm2(a[r]);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) nrm[i] = sqrt(s);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < cols; i += blockDim.x) {
         int rank = 0;
         for (int k = 0; k < cols; ++k) rank += (nrm[k] > nrm[i]) || (nrm[k] == nrm[i] && k < i);
+        rk[i] = rank;
         sigma[rank] = nrm[i];
     }
     __syncthreads();
-    // copy columns in rank order (each thread a row, loop over columns)
-    for (int i = 0; i < cols; ++i) {
-        int rank = 0;
-        for (int k = 0; k < cols; ++k) rank += (nrm[k] > nrm[i]) || (nrm[k] == nrm[i] && k < i);
-        const double inv = nrm[i] > 0 ? 1.0 / nrm[i] : 0.0;
-        if (U)
-            for (int r = threadIdx.x; r < rows; r += blockDim.x) U[(int64_t)rank * rows + r] = inv * A[(int64_t)i * rows + r];
-        for (int r = threadIdx.x; r < cols; r += blockDim.x) W[(int64_t)rank * cols + r] = Vm[(int64_t)i * cols + r];
+    if (U)
+        for (int64_t e = threadIdx.x; e < (int64_t)rows * cols; e += blockDim.x) {
+            const int i = (int)(e / rows), r = (int)(e - (int64_t)i * rows);
+            const double inv = nrm[i] > 0 ? 1.0 / nrm[i] : 0.0;
+            U[(int64_t)rk[i] * rows + r] = inv * A[e];
+        }
+    for (int64_t e = threadIdx.x; e < (int64_t)cols * cols; e += blockDim.x) {
+        const int i = (int)(e / cols), r = (int)(e - (int64_t)i * cols);
+        W[(int64_t)rk[i] * cols + r] = Vm[e];
     }
 }
 
@@ -256,16 +259,123 @@ int jacobi_svd(int rows, int cols, zd* A, zd* U, zd* W, double* sigma, JacobiWor
     int dev = 0, sms = 0;
     NEP_CUDA(cudaGetDevice(&dev));
     NEP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // one warp (one column pair) per CTA, so that each pair gets a whole SM's FP64 pipe
     int per_sm = 0;
-    NEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, 256, 0));
-    int blocks = std::max(1, std::min(ceil_div(P / 2, 8), sms * std::max(per_sm, 1)));
+    NEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, 32, 0));
+    int blocks = std::max(1, std::min(P / 2, sms * std::max(per_sm, 1)));
     GridBar gb{w.bar, w.bar + 1, w.err};
     int max_sweeps = 40;
     double tol = 1e-15;
     void* args[] = {&rows, &cols, &A, &w.Vm, &max_sweeps, &tol, &w.flags, &w.sweeps, &gb};
-    NEP_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(256), args, 0, st));
+    NEP_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(32), args, 0, st));
     count_launch();
-    svd_finish_kernel<<<1, 256, sizeof(double) * cols, st>>>(rows, cols, A, w.Vm, U, W, sigma);
+    svd_finish_kernel<<<1, 256, (sizeof(double) + sizeof(int)) * cols, st>>>(rows, cols, A, w.Vm, U, W, sigma);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+
+// ------------------------------------------------------------------ basis of a column block
+// Pivoted Cholesky of the Gram matrix G = X^H X (m x m, Hermitian positive semidefinite), one
+// CTA, FP64: at step k the column with the largest remaining squared norm d_p (the diagonal of
+// the updated Gram matrix) is taken; the factorisation stops when d_p <= tol2 * max_i G_ii,
+// i.e. when every remaining column lies within sqrt(tol2) (relative) of the span of the chosen
+// ones. With P the pivoting and R the k' x k' factor, X P(:, 1:k') R^{-1} has orthonormal
+// columns spanning the chosen columns; Z = P(:, 1:k') R^{-1} (m x k') is written so that the
+// basis is the product X Z.
+__global__ void __launch_bounds__(256) pchol_kernel(int m, const zd* __restrict__ G, double tol2, int* __restrict__ rank_out,
+                                                    zd* __restrict__ Z, zd* __restrict__ gwork, int use_smem) {
+    extern __shared__ unsigned char sraw[];
+    zd* A = use_smem ? reinterpret_cast<zd*>(sraw) : gwork;  // m x m, column-major
+    double* d = reinterpret_cast<double*>(A + (int64_t)m * m);
+    int* perm = reinterpret_cast<int*>(d + m);
+    __shared__ int piv_s, rank_s;
+    __shared__ double dmax0;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < m * m; e += blockDim.x) A[e] = G[e];
+    for (int i = tid; i < m; i += blockDim.x) perm[i] = i;
+    __syncthreads();
+    for (int i = tid; i < m; i += blockDim.x) d[i] = A[i + (int64_t)m * i].re;
+    __syncthreads();
+    if (tid == 0) {
+        double mx = 0;
+        for (int i = 0; i < m; ++i) mx = fmax(mx, d[i]);
+        dmax0 = mx;
+        rank_s = m;
+    }
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+        if (tid == 0) {
+            int p = k;
+            for (int i = k + 1; i < m; ++i)
+                if (d[i] > d[p]) p = i;
+            piv_s = (d[p] > tol2 * dmax0 && d[p] > 0) ? p : -1;
+            if (piv_s < 0) rank_s = k;
+        }
+        __syncthreads();
+        const int p = piv_s;
+        if (p < 0) break;
+        if (p != k) {
+            // symmetric interchange of rows and columns k and p
+            for (int i = tid; i < m; i += blockDim.x) {
+                const zd t = A[i + (int64_t)m * k];
+                A[i + (int64_t)m * k] = A[i + (int64_t)m * p];
+                A[i + (int64_t)m * p] = t;
+            }
+            __syncthreads();
+            for (int j = tid; j < m; j += blockDim.x) {
+                const zd t = A[k + (int64_t)m * j];
+                A[k + (int64_t)m * j] = A[p + (int64_t)m * j];
+                A[p + (int64_t)m * j] = t;
+            }
+            if (tid == 0) {
+                const double td = d[k];
+                d[k] = d[p];
+                d[p] = td;
+                const int tp = perm[k];
+                perm[k] = perm[p];
+                perm[p] = tp;
+            }
+            __syncthreads();
+        }
+        const double rkk = sqrt(A[k + (int64_t)m * k].re);
+        // row k of R (stored in place): R(k, j) = A(k, j) / R(k, k), j > k
+        for (int j = k + 1 + tid; j < m; j += blockDim.x) A[k + (int64_t)m * j] = (1.0 / rkk) * A[k + (int64_t)m * j];
+        if (tid == 0) A[k + (int64_t)m * k] = mk(rkk, 0.0);
+        __syncthreads();
+        // trailing update A(i, j) -= conj(R(k, i)) R(k, j), i, j > k
+        const int nr = m - k - 1;
+        for (int e = tid; e < nr * nr; e += blockDim.x) {
+            const int i = k + 1 + e % nr, j = k + 1 + e / nr;
+            A[i + (int64_t)m * j] = A[i + (int64_t)m * j] - conj(A[k + (int64_t)m * i]) * A[k + (int64_t)m * j];
+        }
+        __syncthreads();
+        for (int i = k + 1 + tid; i < m; i += blockDim.x) d[i] = A[i + (int64_t)m * i].re;
+        __syncthreads();
+    }
+    const int kr = rank_s;
+    // Z = P(:, 1:kr) R^{-1}: column c of R^{-1} by back substitution (one thread per column)
+    for (int e = tid; e < m * kr; e += blockDim.x) Z[e] = mk(0.0, 0.0);
+    __syncthreads();
+    for (int c = tid; c < kr; c += blockDim.x) {
+        // solve R x = e_c (upper triangular); x_i = 0 for i > c
+        for (int i = c; i >= 0; --i) {
+            zd s = mk(i == c ? 1.0 : 0.0, 0.0);
+            for (int t = i + 1; t <= c; ++t) s = fms(s, A[i + (int64_t)m * t], Z[perm[t] + (int64_t)m * c]);
+            Z[perm[i] + (int64_t)m * c] = cdiv(s, A[i + (int64_t)m * i]);
+        }
+    }
+    if (tid == 0) *rank_out = kr;
+}
+
+int launch_pchol(int m, const zd* G, double tol2, int* rank_out, zd* Z, zd* gwork, cudaStream_t st) {
+    if (m <= 0) return NEP_OK;
+    const size_t bytes = sizeof(zd) * (size_t)m * m + sizeof(double) * m + sizeof(int) * m + 64;
+    const int use_smem = bytes <= 200 * 1024;
+    if (use_smem)
+        NEP_CUDA(cudaFuncSetAttribute(pchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    else if (!gwork)
+        return NEP_ERR_INTERNAL;
+    pchol_kernel<<<1, 256, use_smem ? bytes : 0, st>>>(m, G, tol2, rank_out, Z, gwork, use_smem);
     NEP_CHECK_LAUNCH();
     return NEP_OK;
 }
@@ -532,8 +642,11 @@ __global__ void term_spmm_kernel(SplitDev s, int k, const zd* __restrict__ Q, zd
 }
 
 // ------------------------------------------------------------------ Newton on the projected NEP
-// One CTA per candidate; J = [[B(l), B'(l) y], [y^H, 0]] factored by Gaussian elimination
-// with partial pivoting each step (FP64), in shared memory when it fits.
+// One CTA per candidate. Each step evaluates f_i, f_i' and the residual B(l) y in FP64, builds
+// the bordered Jacobian J = [[B(l), B'(l) y], [y^H, 0]] rounded to complex64 and solves
+// J [dy; dl] = -[B(l) y; 0] by Gaussian elimination with partial pivoting in FP32. Because the
+// residual is FP64, the iteration converges to the FP64 solution; the FP32 Jacobian only makes
+// the convergence linear with a rate ~ kappa(J) * 6e-8 instead of quadratic.
 __global__ void __launch_bounds__(256) newton_kernel(SplitDev s, int k, const zd* __restrict__ Bs,
                                                      const zd* __restrict__ lam0, const zd* __restrict__ Y0, int ldy0,
                                                      zd c, double rad, int maxit, double tol,
@@ -543,18 +656,18 @@ __global__ void __launch_bounds__(256) newton_kernel(SplitDev s, int k, const zd
     extern __shared__ unsigned char sraw[];
     const int cand = blockIdx.x;
     const int K1 = k + 1;
-    zd* J = use_smem ? reinterpret_cast<zd*>(sraw) : gscratch + (int64_t)cand * ((int64_t)K1 * K1 + 3 * K1 + 64);
-    zd* rhs = J + (int64_t)K1 * K1;
-    zd* y = rhs + K1;
-    zd* g = y + K1;
-    zd* fv = g + K1;  // 2 * nterms <= 64
+    unsigned char* base = use_smem ? sraw : reinterpret_cast<unsigned char*>(gscratch + (int64_t)cand * newton_scratch_elems(k));
+    zf* J = reinterpret_cast<zf*>(base);           // K1 x K1 complex64
+    zf* rhs = J + (int64_t)K1 * K1;                 // K1
+    zf* g = rhs + K1;                               // K1 (multipliers)
+    zd* y = reinterpret_cast<zd*>(g + K1 + (K1 & 1));  // k (FP64 iterate)
+    zd* fv = y + K1;                                 // 2 * nterms <= 64
     __shared__ double redd[32];
     __shared__ int piv_s;
     __shared__ int stop_s;
     __shared__ zd lam_s;
     const int tid = threadIdx.x;
     const int lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
-    // y = y0 / |y0|
     double ss = 0.0;
     for (int i = tid; i < k; i += blockDim.x) {
         y[i] = Y0[(int64_t)cand * ldy0 + i];
@@ -584,12 +697,12 @@ __global__ void __launch_bounds__(256) newton_kernel(SplitDev s, int k, const zd
             fv[s.nterms + tid] = fe.df;
         }
         __syncthreads();
-        // J(0:k, 0:k) = B(l); g = B'(l) y; rhs = -B(l) y
+        // J(0:k, 0:k) = B(l) (rounded); rhs = -B(l) y and J(0:k, k) = B'(l) y in FP64, rounded
         for (int e = tid; e < k * k; e += blockDim.x) {
             const int r = e % k, q = e / k;
             zd b = mk(0.0, 0.0);
             for (int i = 0; i < s.nterms; ++i) b = fma_(b, fv[i], Bs[(int64_t)i * k * k + e]);
-            J[r + (int64_t)K1 * q] = b;
+            J[r + (int64_t)K1 * q] = cvt<float>(b);
         }
         for (int r = tid; r < k; r += blockDim.x) {
             zd bd = mk(0.0, 0.0), gd = mk(0.0, 0.0);
@@ -603,27 +716,26 @@ __global__ void __launch_bounds__(256) newton_kernel(SplitDev s, int k, const zd
                 bd = fma_(bd, b, y[q]);
                 gd = fma_(gd, d, y[q]);
             }
-            rhs[r] = -bd;
-            J[r + (int64_t)K1 * k] = gd;
+            rhs[r] = cvt<float>(-bd);
+            J[r + (int64_t)K1 * k] = cvt<float>(gd);
         }
-        for (int q = tid; q < k; q += blockDim.x) J[k + (int64_t)K1 * q] = conj(y[q]);
+        for (int q = tid; q < k; q += blockDim.x) J[k + (int64_t)K1 * q] = cvt<float>(conj(y[q]));
         if (tid == 0) {
-            J[k + (int64_t)K1 * k] = mk(0.0, 0.0);
-            rhs[k] = mk(0.0, 0.0);
+            J[k + (int64_t)K1 * k] = mk(0.0f, 0.0f);
+            rhs[k] = mk(0.0f, 0.0f);
         }
         __syncthreads();
-        // Gaussian elimination with partial pivoting on [J | rhs]
         int singular = 0;
         for (int col = 0; col < K1; ++col) {
             if (w == 0) {
-                double best = -1.0;
+                float best = -1.0f;
                 int bi = col;
                 for (int r = col + lane; r < K1; r += 32) {
-                    const double a = abs1(J[r + (int64_t)K1 * col]);
+                    const float a = abs1(J[r + (int64_t)K1 * col]);
                     if (a > best) { best = a; bi = r; }
                 }
                 for (int o = 16; o > 0; o >>= 1) {
-                    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
                     const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                     if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
                 }
@@ -634,18 +746,18 @@ __global__ void __launch_bounds__(256) newton_kernel(SplitDev s, int k, const zd
             if (p < 0) { singular = 1; break; }
             if (p != col) {
                 for (int q = col + tid; q < K1; q += blockDim.x) {
-                    const zd t = J[col + (int64_t)K1 * q];
+                    const zf t = J[col + (int64_t)K1 * q];
                     J[col + (int64_t)K1 * q] = J[p + (int64_t)K1 * q];
                     J[p + (int64_t)K1 * q] = t;
                 }
                 if (tid == 0) {
-                    const zd t = rhs[col];
+                    const zf t = rhs[col];
                     rhs[col] = rhs[p];
                     rhs[p] = t;
                 }
             }
             __syncthreads();
-            const zd pv = J[col + (int64_t)K1 * col];
+            const zf pv = J[col + (int64_t)K1 * col];
             for (int r = col + 1 + tid; r < K1; r += blockDim.x) g[r] = cdiv(J[r + (int64_t)K1 * col], pv);
             __syncthreads();
             const int nr = K1 - col - 1;
@@ -657,10 +769,9 @@ __global__ void __launch_bounds__(256) newton_kernel(SplitDev s, int k, const zd
             __syncthreads();
         }
         if (singular) { ok = 0; break; }
-        // back substitution (one warp)
         if (w == 0) {
             for (int r = K1 - 1; r >= 0; --r) {
-                zd acc = mk(0.0, 0.0);
+                zf acc = mk(0.0f, 0.0f);
                 for (int q = r + 1 + lane; q < K1; q += 32) acc = fma_(acc, J[r + (int64_t)K1 * q], rhs[q]);
                 for (int o = 16; o > 0; o >>= 1) {
                     acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
@@ -671,10 +782,9 @@ __global__ void __launch_bounds__(256) newton_kernel(SplitDev s, int k, const zd
             }
         }
         __syncthreads();
-        // update and normalise
         double s2 = 0.0;
         for (int i = tid; i < k; i += blockDim.x) {
-            y[i] = y[i] + rhs[i];
+            y[i] = y[i] + cvt<double>(rhs[i]);
             s2 += norm2(y[i]);
         }
         for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
@@ -685,7 +795,7 @@ __global__ void __launch_bounds__(256) newton_kernel(SplitDev s, int k, const zd
             double t = 0;
             for (int q = 0; q < nw; ++q) t += redd[q];
             redd[0] = t;
-            const zd dl = rhs[k];
+            const zd dl = cvt<double>(rhs[k]);
             const zd nl = lam_s + dl;
             lam_s = nl;
             const double al = hypot(nl.re, nl.im);
@@ -713,8 +823,7 @@ int launch_newton(const SplitDev& s, int k, int ncand, const zd* Bs, const zd* l
                   double rad, int maxit, double tol, zd* lam_out, zd* Yout, int* ok, int* its, zd* gscratch,
                   cudaStream_t st) {
     if (ncand <= 0) return NEP_OK;
-    const int K1 = k + 1;
-    const size_t bytes = sizeof(zd) * ((size_t)K1 * K1 + 3 * K1 + 64);
+    const size_t bytes = sizeof(zd) * newton_scratch_elems(k);
     const int use_smem = bytes <= 200 * 1024;
     if (use_smem)
         NEP_CUDA(cudaFuncSetAttribute(newton_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));

@@ -531,7 +531,8 @@ static int plan_alloc(nep_plan* p) {
     NEP_TRY(dalloc(&p->eta, LM, st));
     p->part_elems = std::max<size_t>(16 * lm2, 1 << 16);
     NEP_TRY(dalloc(&p->part, p->part_elems, st));
-    if (LM + 1 > 110) NEP_TRY(dalloc(&p->newton_scratch, (size_t)LM * ((size_t)(LM + 1) * (LM + 1) + 3 * (LM + 1) + 64), st));
+    if (sizeof(zd) * newton_scratch_elems(LM) > 200 * 1024)
+        NEP_TRY(dalloc(&p->newton_scratch, (size_t)LM * newton_scratch_elems(LM), st));
     NEP_CUDA(cudaMallocAsync(&p->eig_scratch, sizeof(zf) * ((size_t)2 * LM * (LM + 1) + LM) + 256, st));
     NEP_TRY(dalloc(&p->jw.Vm, lm2, st));
     NEP_TRY(dalloc(&p->jw.flags, 2, st));
@@ -689,10 +690,9 @@ static int run_extract(nep_plan* p, cudaStream_t st) {
     NEP_TRY(zgemm(LM, m, m, 0, p->W, LM, p->Tv, m, p->Z, LM, p->part, p->part_elems, st));
     NEP_TRY(zgemm(n, m, LM, 0, p->S, n, p->Z, LM, p->XH, n, p->part, p->part_elems, st));
     NEP_TRY(launch_normalize_columns(n, m, p->XH, 0, nullptr, st));
-    // orthonormal basis: eigen-decomposition of the Gram matrix of the normalised columns
+    // orthonormal basis of the normalised columns: pivoted Cholesky of their Gram matrix
     NEP_TRY(zgemm(m, m, n, 1, p->XH, n, p->XH, n, p->G, m, p->part, p->part_elems, st));
-    NEP_TRY(jacobi_svd(m, m, p->G, nullptr, p->Wg, p->lamg, p->jw, st));
-    NEP_TRY(launch_rank(m, p->lamg, p->o.basis_tol * p->o.basis_tol, p->scalars + 1, st));
+    NEP_TRY(launch_pchol(m, p->G, p->o.basis_tol * p->o.basis_tol, p->scalars + 1, p->Wg, p->Gw, st));
     int kb = 0;
     NEP_TRY(read_scalar(p, p->scalars + 1, &kb, st));
     p->kb = kb;
@@ -700,7 +700,6 @@ static int run_extract(nep_plan* p, cudaStream_t st) {
         NEP_CUDA(cudaMemsetAsync(p->order, 0, sizeof(int), st));
         return NEP_OK;
     }
-    NEP_TRY(launch_scale_cols(m, kb, p->Wg, m, p->lamg, 1, st));
     NEP_TRY(zgemm(n, kb, m, 0, p->XH, n, p->Wg, m, p->Q, n, p->part, p->part_elems, st));
     NEP_TRY(zgemm(kb, m, n, 1, p->Q, n, p->XH, n, p->Y0, kb, p->part, p->part_elems, st));
     // projected split form B_i = Q^H A_i Q

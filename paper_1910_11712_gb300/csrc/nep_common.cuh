@@ -234,6 +234,12 @@ struct JacobiWork {
 int jacobi_svd(int rows, int cols, zd* A, zd* U, zd* W, double* sigma, JacobiWork w, cudaStream_t st);
 template <typename T>
 int small_eig(int m, const zd* A, zd* eval, zd* evec, int* status, void* gbuf, cudaStream_t st);
+// complex128-sized elements of one Newton candidate's work area (FP32 Jacobian + FP64 iterate)
+__host__ __device__ inline size_t newton_scratch_elems(int k) {
+    const size_t K1 = (size_t)k + 1;
+    return (K1 * K1 + 2 * K1 + 2) / 2 + K1 + 64 + 2;
+}
+int launch_pchol(int m, const zd* G, double tol2, int* rank_out, zd* Z, zd* gwork, cudaStream_t st);
 int launch_newton(const SplitDev& s, int k, int ncand, const zd* Bs, const zd* lam0, const zd* Y0, int ldy0, zd c,
                   double rad, int maxit, double tol, zd* lam_out, zd* Yout, int* ok, int* its, zd* gscratch,
                   cudaStream_t st);

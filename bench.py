@@ -270,7 +270,8 @@ def main():
             "stages_ms": stage, "clocks": cs, "gpu_launches": int(launches),
             "result": {"nconv": int(len(res["lam"])), "hankel_rank": res["m"], "max_eta": float(res["eta"].max())
                        if len(res["eta"]) else None, "max_backward": res["info"]["max_backward"],
-                       "max_sweeps": res["info"]["max_sweeps"], "flags": res["flags"]},
+                       "max_sweeps": res["info"]["max_sweeps"], "svd_sweeps": res["info"]["svd_sweeps"],
+                       "flags": res["flags"]},
         }
         if e2e:
             line["e2e"] = e2e

@@ -146,6 +146,7 @@ typedef struct {
     int32_t basis_rank;     /* Rayleigh-Ritz basis dimension */
     int32_t ncandidates;    /* Newton starts */
     int32_t max_sweeps;     /* refinement sweeps of the slowest point */
+    int32_t svd_sweeps;     /* Jacobi sweeps of the Hankel SVD */
     int32_t flags;
     double max_backward;    /* max over points of the last measured backward error */
     double ms_assemble, ms_factor, ms_solve, ms_moments, ms_extract, ms_total;

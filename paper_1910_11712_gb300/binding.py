@@ -52,7 +52,7 @@ class NepOpts(ctypes.Structure):
 class NepResultInfo(ctypes.Structure):
     _fields_ = [("n", c_int32), ("N", c_int32), ("L", c_int32), ("M", c_int32), ("precision", c_int32),
                 ("hankel_rank", c_int32), ("basis_rank", c_int32), ("ncandidates", c_int32),
-                ("max_sweeps", c_int32), ("flags", c_int32), ("max_backward", c_double),
+                ("max_sweeps", c_int32), ("svd_sweeps", c_int32), ("flags", c_int32), ("max_backward", c_double),
                 ("ms_assemble", c_double), ("ms_factor", c_double), ("ms_solve", c_double),
                 ("ms_moments", c_double), ("ms_extract", c_double), ("ms_total", c_double)]
 

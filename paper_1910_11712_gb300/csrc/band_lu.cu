@@ -55,6 +55,9 @@ __device__ __forceinline__ void cp_async_cx(cx<T>* smem, const cx<T>* gmem) {
     }
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // First index of the maximum of |Re|+|Im| over pcol[0..cnt-1], computed by one warp.
 // Ties resolve to the smallest index (the same rule as LAPACK's izamax).
@@ -273,7 +276,9 @@ __global__ void __launch_bounds__(NW * 32, 1)
     cx<T>* ab = ab_all + (int64_t)j * n * ldab;
     int* ipiv = ipiv_all + (int64_t)j * n;
 
-    __shared__ cx<T> nrow[2][CS + 1];
+    // ring of PF+1 entering rows: row c+kl is fetched PF steps before step c
+    constexpr int PF = 8;
+    __shared__ cx<T> nrow[PF + 1][CS + 1];
     __shared__ cx<T> pcol[RS + 1];
     __shared__ cx<T> lvec[RS];
     __shared__ cx<T> urow[CS];
@@ -294,15 +299,18 @@ __global__ void __launch_bounds__(NW * 32, 1)
             a[q][p] = v;
         }
     }
-    for (int t = threadIdx.x; t <= kv; t += blockDim.x) {
-        cx<T> v = mk<T>(0, 0);
-        if (kl < n && t < n) v = ab[(int64_t)kl * ldab + t];
-        nrow[0][t] = v;
+    // rows kl .. kl+PF-1 (for steps 0 .. PF-1): one commit group per row
+    for (int d = 0; d < PF; ++d) {
+        const int r = kl + d;
+        for (int t = threadIdx.x; t <= kv; t += blockDim.x) {
+            if (r < n && d + t < n) cp_async_cx(&nrow[d][t], ab + (int64_t)r * ldab + t);
+            else nrow[d][t] = mk<T>(0, 0);
+        }
+        cp_async_commit();
     }
-    __syncthreads();
 
     for (int c = 0; c < n; ++c) {
-        const int buf = c & 1;
+        const int buf = c % (PF + 1);
         // (1) publish column c; its slot then starts column c+kv with zero fill
         {
             const int csc = c % CS;
@@ -328,16 +336,17 @@ __global__ void __launch_bounds__(NW * 32, 1)
                         for (int q = 0; q < RPW; ++q) a[q][p] = mk<T>(0, 0);
             }
         }
-        cp_async_wait_all();
+        cp_async_wait_group<PF - 1>();  // the group of row c+kl has landed
         __syncthreads();  // S1
-        if (warp != 0 || NW == 1) {
-            const int r = c + 1 + kl;
-            const int t0 = (NW == 1) ? lane : threadIdx.x - 32;
-            const int ts = (NW == 1) ? 32 : blockDim.x - 32;
-            for (int t = t0; t <= kv; t += ts) {
-                if (r < n && c + 1 + t < n) cp_async_cx(&nrow[buf ^ 1][t], ab + (int64_t)r * ldab + t);
-                else nrow[buf ^ 1][t] = mk<T>(0, 0);
+        // fetch row c+kl+PF (columns c+PF..c+PF+kv) into the slot freed by step c-1
+        {
+            const int r = c + kl + PF;
+            cx<T>* dst = nrow[(c + PF) % (PF + 1)];
+            for (int t = threadIdx.x; t <= kv; t += blockDim.x) {
+                if (r < n && c + PF + t < n) cp_async_cx(&dst[t], ab + (int64_t)r * ldab + t);
+                else dst[t] = mk<T>(0, 0);
             }
+            cp_async_commit();
         }
         if (warp == 0) {
             if (lane == 0) pcol[kl] = nrow[buf][0];
@@ -632,6 +641,12 @@ template int launch_band_lu<double>(const SplitDev&, int, cx<double>*, int*, int
 // window of kv+1 rows. L columns (contiguous) and U columns (gathered from U rows,
 // coalesced by rows) are staged in shared memory in chunks of CH steps shared by all warps.
 template <typename T>
+__device__ __forceinline__ void cp_async_int(int* smem, const int* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+template <typename T>
 __global__ void __launch_bounds__(512)
     band_solve_kernel(int n, int kl, int ku, int ldab, const cx<T>* __restrict__ ab_all,
                       const int* __restrict__ ipiv_all, int L, cx<T>* __restrict__ B_all,
@@ -651,34 +666,50 @@ __global__ void __launch_bounds__(512)
     const int RF = kl + 1, RB = kv + 1;
     const int WIN = RF > RB ? RF : RB;
     const int wide = kv > kl ? kv : (kl > 0 ? kl : 1);
+    // layout: win[nwarps][WIN] | nb[2][nwarps][CH] | stage[2][CH*wide] | diag[2][CH] | pst[2][CH]
     cx<T>* win = reinterpret_cast<cx<T>*>(smem_raw) + (int64_t)warp * WIN;
-    cx<T>* nb = reinterpret_cast<cx<T>*>(smem_raw) + (int64_t)nwarps * WIN + (int64_t)warp * CH;
-    cx<T>* stage = reinterpret_cast<cx<T>*>(smem_raw) + (int64_t)nwarps * (WIN + CH);
-    cx<T>* diag = stage + (int64_t)CH * wide;
-    int* pst = reinterpret_cast<int*>(diag + CH);
+    cx<T>* nb0 = reinterpret_cast<cx<T>*>(smem_raw) + (int64_t)nwarps * WIN;
+    cx<T>* stage0 = nb0 + 2 * (int64_t)nwarps * CH;
+    cx<T>* diag0 = stage0 + 2 * (int64_t)CH * wide;
+    int* pst0 = reinterpret_cast<int*>(diag0 + 2 * CH);
+    auto nbuf = [&](int bsel) { return nb0 + ((int64_t)bsel * nwarps + warp) * CH; };
+    auto sbuf = [&](int bsel) { return stage0 + (int64_t)bsel * CH * wide; };
 
-    // ---- forward: row interchanges and unit lower L. Row r lives in slot r mod RF; sc is the
-    //      slot of the current row c, advanced without integer division.
-    for (int i = lane; i < RF; i += 32) win[i] = (has_col && i < n) ? b[i] : mk<T>(0, 0);
-    int sc = 0;
-    for (int c0 = 0; c0 < n; c0 += CH) {
+    // ---- forward: row interchanges and unit lower L. Row r lives in slot r mod RF.
+    auto issue_fwd = [&](int c0, int bsel) {
         const int cn = min(CH, n - c0);
-        __syncthreads();
+        cx<T>* st = sbuf(bsel);
         for (int e = threadIdx.x; e < cn * kl; e += blockDim.x) {
             const int cc = e / kl, i = e - cc * kl;
-            stage[e] = ab[(int64_t)(c0 + cc) * ldab + kv + 1 + i];
+            cp_async_cx(&st[e], ab + (int64_t)(c0 + cc) * ldab + kv + 1 + i);
         }
-        for (int e = threadIdx.x; e < cn; e += blockDim.x) pst[e] = ipiv[c0 + e] - (c0 + e);
-        if (has_col)
+        for (int e = threadIdx.x; e < cn; e += blockDim.x) cp_async_int<T>(&pst0[bsel * CH + e], ipiv + c0 + e);
+        if (has_col) {
+            cx<T>* nb = nbuf(bsel);
             for (int cc = lane; cc < cn; cc += 32) {
                 const int rn = c0 + cc + kl + 1;
-                nb[cc] = rn < n ? b[rn] : mk<T>(0, 0);
+                if (rn < n) cp_async_cx(&nb[cc], b + rn);
+                else nb[cc] = mk<T>(0, 0);
             }
+        }
+        cp_async_commit();
+    };
+    for (int i = lane; i < RF; i += 32) win[i] = (has_col && i < n) ? b[i] : mk<T>(0, 0);
+    int sc = 0;
+    issue_fwd(0, 0);
+    for (int c0 = 0, chunk = 0; c0 < n; c0 += CH, ++chunk) {
+        const int cn = min(CH, n - c0);
+        const int bsel = chunk & 1;
+        cp_async_wait_group<0>();
         __syncthreads();
+        if (c0 + CH < n) issue_fwd(c0 + CH, bsel ^ 1);
         if (has_col) {
+            const cx<T>* st = sbuf(bsel);
+            const int* pst = pst0 + bsel * CH;
+            const cx<T>* nb = nbuf(bsel);
             for (int cc = 0; cc < cn; ++cc) {
                 const int c = c0 + cc;
-                const int p = pst[cc];
+                const int p = pst[cc] - c;
                 if (p != 0 && lane == 0) {
                     int s1 = sc + p;
                     if (s1 >= RF) s1 -= RF;
@@ -688,7 +719,7 @@ __global__ void __launch_bounds__(512)
                 }
                 __syncwarp();
                 const cx<T> xc = win[sc];
-                const cx<T>* lc = stage + cc * kl;
+                const cx<T>* lc = st + cc * kl;
                 const int lim = min(kl, n - 1 - c);
                 for (int i = lane; i < lim; i += 32) {
                     int s = sc + 1 + i;
@@ -706,38 +737,54 @@ __global__ void __launch_bounds__(512)
         }
     }
     // ---- backward: U with bandwidth kv; row r lives in slot r mod RB
+    cp_async_wait_group<0>();
     __syncthreads();
-    for (int i = lane; i < RB; i += 32) {
-        const int r = n - 1 - i;
-        if (r >= 0) win[r % RB] = has_col ? b[r] : mk<T>(0, 0);
-    }
-    sc = (n - 1) % RB;
-    __syncwarp();
-    for (int c1 = n - 1; c1 >= 0; c1 -= CH) {
+    auto issue_bwd = [&](int c1, int bsel) {
         const int cn = min(CH, c1 + 1);
-        const int cbase = c1 - cn + 1;  // chunk columns cbase..c1
-        __syncthreads();
-        // stage[cc*kv + i] = U(c-1-i, c), c = cbase + cc, gathered from U rows (coalesced by row)
+        const int cbase = c1 - cn + 1;
+        cx<T>* st = sbuf(bsel);
+        cx<T>* dg = diag0 + bsel * CH;
+        // st[cc*kv + i] = U(c-1-i, c), c = cbase + cc, gathered from U rows (coalesced by row)
         const int rlo = cbase - kv, rhi = c1 - 1;
         const int nr = rhi - rlo + 1;
         for (int e = threadIdx.x; e < nr * cn; e += blockDim.x) {
             const int ri = e / cn, cc = e - ri * cn;
             const int r = rlo + ri, c = cbase + cc, t = c - r;
-            if (r >= 0 && t >= 1 && t <= kv) stage[cc * kv + (t - 1)] = ab[(int64_t)r * ldab + t];
+            if (r >= 0 && t >= 1 && t <= kv) cp_async_cx(&st[cc * kv + (t - 1)], ab + (int64_t)r * ldab + t);
         }
-        for (int e = threadIdx.x; e < cn; e += blockDim.x) diag[e] = ab[(int64_t)(cbase + e) * ldab];
-        if (has_col)
+        for (int e = threadIdx.x; e < cn; e += blockDim.x) cp_async_cx(&dg[e], ab + (int64_t)(cbase + e) * ldab);
+        if (has_col) {
+            cx<T>* nb = nbuf(bsel);
             for (int cc = lane; cc < cn; cc += 32) {
                 const int rn = cbase + cc - kv - 1;
-                nb[cc] = rn >= 0 ? b[rn] : mk<T>(0, 0);
+                if (rn >= 0) cp_async_cx(&nb[cc], b + rn);
+                else nb[cc] = mk<T>(0, 0);
             }
+        }
+        cp_async_commit();
+    };
+    for (int i = lane; i < RB; i += 32) {
+        const int r = n - 1 - i;
+        if (r >= 0) win[r % RB] = has_col ? b[r] : mk<T>(0, 0);
+    }
+    sc = (n - 1) % RB;
+    issue_bwd(n - 1, 0);
+    for (int c1 = n - 1, chunk = 0; c1 >= 0; c1 -= CH, ++chunk) {
+        const int cn = min(CH, c1 + 1);
+        const int cbase = c1 - cn + 1;  // chunk columns cbase..c1
+        const int bsel = chunk & 1;
+        cp_async_wait_group<0>();
         __syncthreads();
+        if (c1 - CH >= 0) issue_bwd(c1 - CH, bsel ^ 1);
         if (has_col) {
+            const cx<T>* st = sbuf(bsel);
+            const cx<T>* dg = diag0 + bsel * CH;
+            const cx<T>* nb = nbuf(bsel);
             for (int cc = cn - 1; cc >= 0; --cc) {
                 const int c = cbase + cc;
-                const cx<T> xc = cdiv(win[sc], diag[cc]);
+                const cx<T> xc = cdiv(win[sc], dg[cc]);
                 __syncwarp();
-                const cx<T>* uc = stage + cc * kv;
+                const cx<T>* uc = st + cc * kv;
                 const int lim = min(kv, c);
                 for (int i = lane; i < lim; i += 32) {
                     int s = sc - 1 - i;
@@ -769,7 +816,8 @@ int launch_band_solve(const SplitDev& s, int npts, const cx<T>* ab, const int* i
     const size_t budget = 200 * 1024;
     int CH = 32;
     auto bytes = [&](int ch) {
-        return sizeof(cx<T>) * ((size_t)wpb * (WIN + ch) + (size_t)ch * wide + ch) + sizeof(int) * ch;
+        return sizeof(cx<T>) * ((size_t)wpb * WIN + 2 * (size_t)wpb * ch + 2 * (size_t)ch * wide + 2 * ch) +
+               sizeof(int) * 2 * ch;
     };
     while (CH > 1 && bytes(CH) > budget) CH >>= 1;
     const size_t smem = bytes(CH);

@@ -265,7 +265,9 @@ int jacobi_svd(int rows, int cols, zd* A, zd* U, zd* W, double* sigma, JacobiWor
     int blocks = std::max(1, std::min(P / 2, sms * std::max(per_sm, 1)));
     GridBar gb{w.bar, w.bar + 1, w.err};
     int max_sweeps = 40;
-    double tol = 1e-15;
+    // columns count as orthogonal once |a_p^H a_q| <= rows * eps * |a_p| |a_q|: below that the
+    // rotation angle is rounding noise
+    double tol = std::max(rows, 1) * 2.220446049250313e-16;
     void* args[] = {&rows, &cols, &A, &w.Vm, &max_sweeps, &tol, &w.flags, &w.sweeps, &gb};
     NEP_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(32), args, 0, st));
     count_launch();

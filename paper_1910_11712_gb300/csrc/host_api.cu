@@ -464,7 +464,7 @@ struct nep_plan {
     JacobiWork jw{};
     int* h_pinned = nullptr;  // host-mapped scalars
     // last run
-    int m = 0, kb = 0, max_sweeps_seen = 0, flags = 0;
+    int m = 0, kb = 0, max_sweeps_seen = 0, flags = 0, svd_sweeps = 0;
     double max_beta = 0;
     float ms[6] = {0, 0, 0, 0, 0, 0};
     cudaEvent_t ev[6] = {};
@@ -674,6 +674,7 @@ static int run_extract(nep_plan* p, cudaStream_t st) {
     int m = 0;
     NEP_TRY(read_scalar(p, p->scalars, &m, st));
     p->m = m;
+    NEP_TRY(read_scalar(p, p->jw.sweeps, &p->svd_sweeps, st));
     p->kb = 0;
     if (m == 0) {
         NEP_CUDA(cudaMemsetAsync(p->order, 0, sizeof(int), st));
@@ -825,6 +826,7 @@ extern "C" int nep_plan_result(nep_plan_t p, nep_result_t* out) {
     in.basis_rank = p->kb;
     in.ncandidates = p->m;
     in.max_sweeps = msw;
+    in.svd_sweeps = p->svd_sweeps;
     in.flags = flags;
     in.max_backward = mb;
     float t[5] = {0, 0, 0, 0, 0};

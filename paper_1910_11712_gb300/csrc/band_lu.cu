@@ -780,9 +780,14 @@ __global__ void __launch_bounds__(512)
             const cx<T>* st = sbuf(bsel);
             const cx<T>* dg = diag0 + bsel * CH;
             const cx<T>* nb = nbuf(bsel);
+            // lane cc holds 1/U(c, c) of chunk column cc (CH <= 32), fetched by shuffle per step
+            const cx<T> rd = lane < cn ? cdiv(mk<T>(1, 0), dg[lane]) : mk<T>(0, 0);
             for (int cc = cn - 1; cc >= 0; --cc) {
                 const int c = cbase + cc;
-                const cx<T> xc = cdiv(win[sc], dg[cc]);
+                cx<T> r;
+                r.re = __shfl_sync(0xffffffffu, rd.re, cc);
+                r.im = __shfl_sync(0xffffffffu, rd.im, cc);
+                const cx<T> xc = win[sc] * r;
                 __syncwarp();
                 const cx<T>* uc = st + cc * kv;
                 const int lim = min(kv, c);

@@ -138,6 +138,14 @@ __device__ __forceinline__ void grid_barrier(GridBar b, unsigned int& epoch) {
     __syncthreads();
 }
 
+// Loads of data that other CTAs of the same (cooperative) launch write: L2 only (ld.global.cg),
+// never a possibly stale L1 line.
+__device__ __forceinline__ zd ldcg(const zd* p) {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+    return mk(v.x, v.y);
+}
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+
 // ------------------------------------------------------------------ one-sided Jacobi SVD
 // A (rows x cols, column-major) is rotated in place until its columns are mutually
 // orthogonal: A V = U Sigma. Rotation of columns (p, q) with alpha = |a_p|^2,
@@ -176,7 +184,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __r
                 double al = 0.0, be = 0.0;
                 zd ga = mk(0.0, 0.0);
                 for (int i = lane; i < rows; i += 32) {
-                    const zd x = ap[i], y = aq[i];
+                    const zd x = ldcg(ap + i), y = ldcg(aq + i);
                     al += norm2(x);
                     be += norm2(y);
                     ga = fmac(ga, x, y);
@@ -195,14 +203,14 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __r
                 const zd e = mk(ga.re / g, ga.im / g);  // e^{i phi}
                 const zd se = mk(s * e.re, s * e.im), sec = conj(se);
                 for (int i = lane; i < rows; i += 32) {
-                    const zd x = ap[i], y = aq[i];
+                    const zd x = ldcg(ap + i), y = ldcg(aq + i);
                     ap[i] = c * x - sec * y;
                     aq[i] = se * x + c * y;
                 }
                 zd* vp = Vm + (int64_t)p * cols;
                 zd* vq = Vm + (int64_t)q * cols;
                 for (int i = lane; i < cols; i += 32) {
-                    const zd x = vp[i], y = vq[i];
+                    const zd x = ldcg(vp + i), y = ldcg(vq + i);
                     vp[i] = c * x - sec * y;
                     vq[i] = se * x + c * y;
                 }
@@ -272,6 +280,183 @@ int jacobi_svd(int rows, int cols, zd* A, zd* U, zd* W, double* sigma, JacobiWor
     NEP_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(32), args, 0, st));
     count_launch();
     svd_finish_kernel<<<1, 256, (sizeof(double) + sizeof(int)) * cols, st>>>(rows, cols, A, w.Vm, U, W, sigma);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+
+// ------------------------------------------------------------------ QR with column pivoting
+// Householder QR with column pivoting, FP64, cooperative across CTAs (one warp per CTA, warp w
+// owns columns j = w mod gridDim.x). Step k: every CTA finds the same pivot p (largest remaining
+// squared column norm, first index on ties); the owner of column k swaps columns k and p and
+// builds the reflector H_k = I - tau v v^H (v_0 = 1) with H_k^H [alpha; x] = [beta; 0]
+// (barrier); every owner applies H_k^H to its columns j > k and recomputes their remaining
+// norms (barrier). On exit A holds R in its upper triangle and v below it, perm the column
+// order (A P = Q R, Q = H_0 H_1 ... H_{n-1}). Used to precondition one-sided Jacobi: on the
+// graded block Hankel matrices of the contour method, Jacobi on R^H needs several times fewer
+// sweeps than on A itself.
+__global__ void __launch_bounds__(32) qrcp_kernel(int rows, int cols, zd* __restrict__ A, zd* __restrict__ tau,
+                                                  int* __restrict__ perm, double* __restrict__ nrm2, GridBar bar) {
+    const int lane = threadIdx.x;
+    const int G = gridDim.x;
+    unsigned int epoch = 0;
+    for (int j = blockIdx.x; j < cols; j += G) {
+        const zd* a = A + (int64_t)j * rows;
+        double s = 0.0;
+        for (int i = lane; i < rows; i += 32) s += norm2(a[i]);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            nrm2[j] = s;
+            perm[j] = j;
+        }
+    }
+    grid_barrier(bar, epoch);
+    const int steps = min(rows, cols);
+    for (int k = 0; k < steps; ++k) {
+        const int owner = k % G;
+        if ((int)blockIdx.x == owner) {
+            // pivot: first index of the largest remaining norm among columns k..cols-1
+            double best = -1.0;
+            int bi = cols;
+            for (int j = k + lane; j < cols; j += 32) {
+                const double v = ldcg(nrm2 + j);
+                if (v > best) { best = v; bi = j; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            const int p = bi;
+            zd* ak = A + (int64_t)k * rows;
+            if (p != k) {
+                zd* ap = A + (int64_t)p * rows;
+                for (int i = lane; i < rows; i += 32) {
+                    const zd t = ldcg(ak + i);
+                    ak[i] = ldcg(ap + i);
+                    ap[i] = t;
+                }
+                if (lane == 0) {
+                    const double tn = ldcg(nrm2 + k);
+                    nrm2[k] = ldcg(nrm2 + p);
+                    nrm2[p] = tn;
+                    const int tp = __ldcg(perm + k);
+                    perm[k] = __ldcg(perm + p);
+                    perm[p] = tp;
+                }
+            }
+            __syncwarp();
+            // reflector of ak[k..rows-1]
+            double xs = 0.0;
+            for (int i = k + 1 + lane; i < rows; i += 32) xs += norm2(ldcg(ak + i));
+            for (int o = 16; o > 0; o >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, o);
+            const zd alpha = ldcg(ak + k);
+            zd t = mk(0.0, 0.0);
+            if (xs > 0.0 || alpha.im != 0.0) {
+                const double an = hypot(alpha.re, alpha.im);
+                const double bnorm = sqrt(an * an + xs);
+                const double beta = alpha.re >= 0 ? -bnorm : bnorm;  // beta real, sign opposite Re(alpha)
+                t = mk((beta - alpha.re) / beta, -alpha.im / beta);
+                const zd scale = cdiv(mk(1.0, 0.0), alpha - mk(beta, 0.0));
+                __syncwarp();
+                for (int i = k + 1 + lane; i < rows; i += 32) ak[i] = ldcg(ak + i) * scale;
+                __syncwarp();
+                if (lane == 0) ak[k] = mk(beta, 0.0);
+            }
+            if (lane == 0) tau[k] = t;
+            __threadfence();
+        }
+        grid_barrier(bar, epoch);
+        // apply H_k^H = I - conj(tau) v v^H to the owned columns j > k
+        const zd tk = ldcg(tau + k);
+        const zd* v = A + (int64_t)k * rows;
+        for (int j = blockIdx.x; j < cols; j += G) {
+            if (j <= k) continue;
+            zd* a = A + (int64_t)j * rows;
+            zd s = lane == 0 ? ldcg(a + k) : mk(0.0, 0.0);
+            for (int i = k + 1 + lane; i < rows; i += 32) s = fmac(s, ldcg(v + i), ldcg(a + i));
+            for (int o = 16; o > 0; o >>= 1) {
+                s.re += __shfl_xor_sync(0xffffffffu, s.re, o);
+                s.im += __shfl_xor_sync(0xffffffffu, s.im, o);
+            }
+            const zd f = conj(tk) * s;
+            double rest = 0.0;
+            if (lane == 0) a[k] = ldcg(a + k) - f;
+            for (int i = k + 1 + lane; i < rows; i += 32) {
+                a[i] = fms(ldcg(a + i), ldcg(v + i), f);
+                rest += norm2(a[i]);
+            }
+            for (int o = 16; o > 0; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
+            if (lane == 0) nrm2[j] = rest;
+        }
+        grid_barrier(bar, epoch);
+    }
+}
+
+// R^H of the upper triangle of A (n x n): Rh(i, j) = conj(A(j, i)) for i >= j, 0 above.
+__global__ void rh_from_qr_kernel(int n, const zd* __restrict__ A, zd* __restrict__ Rh) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * n) return;
+    const int i = (int)(t % n), j = (int)(t / n);
+    Rh[t] = i >= j ? conj(A[j + (int64_t)n * i]) : mk(0.0, 0.0);
+}
+
+// X <- Q X with Q = H_0 H_1 ... H_{n-1} from qrcp_kernel (reflectors below the diagonal of A):
+// one warp per column of X, reflectors applied from the last to the first.
+__global__ void apply_q_kernel(int rows, int nref, const zd* __restrict__ A, const zd* __restrict__ tau,
+                               int ncols, zd* __restrict__ X) {
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= ncols) return;
+    zd* x = X + (int64_t)c * rows;
+    for (int k = nref - 1; k >= 0; --k) {
+        const zd* v = A + (int64_t)k * rows;
+        zd s = lane == 0 ? x[k] : mk(0.0, 0.0);
+        for (int i = k + 1 + lane; i < rows; i += 32) s = fmac(s, v[i], x[i]);
+        for (int o = 16; o > 0; o >>= 1) {
+            s.re += __shfl_xor_sync(0xffffffffu, s.re, o);
+            s.im += __shfl_xor_sync(0xffffffffu, s.im, o);
+        }
+        const zd f = tau[k] * s;
+        __syncwarp();
+        if (lane == 0) x[k] = x[k] - f;
+        for (int i = k + 1 + lane; i < rows; i += 32) x[i] = fms(x[i], v[i], f);
+        __syncwarp();
+    }
+}
+
+// W(perm[i], c) = Uj(i, c)
+__global__ void permute_rows_kernel(int n, int ncols, const int* __restrict__ perm, const zd* __restrict__ Uj,
+                                    zd* __restrict__ W) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * ncols) return;
+    const int i = (int)(t % n), c = (int)(t / n);
+    W[perm[i] + (int64_t)n * c] = Uj[t];
+}
+
+// SVD of a square n x n matrix A (destroyed) preconditioned by QR with column pivoting:
+// A P = Q R, one-sided Jacobi on R^H = Uj Sigma Wj^H, then A = (Q Wj) Sigma (P Uj)^H.
+int qrcp_jacobi_svd(int n, zd* A, zd* U, zd* W, double* sigma, zd* work1, zd* work2, zd* tau, int* perm,
+                    double* nrm2, JacobiWork w, cudaStream_t st) {
+    if (n <= 0) return NEP_OK;
+    NEP_CUDA(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st));
+    int dev = 0, sms = 0;
+    NEP_CUDA(cudaGetDevice(&dev));
+    NEP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int per_sm = 0;
+    NEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qrcp_kernel, 32, 0));
+    int blocks = std::max(1, std::min(n, sms * std::max(per_sm, 1)));
+    GridBar gb{w.bar, w.bar + 1, w.err};
+    int rows = n, cols = n;
+    void* args[] = {&rows, &cols, &A, &tau, &perm, &nrm2, &gb};
+    NEP_CUDA(cudaLaunchCooperativeKernel((const void*)qrcp_kernel, dim3(blocks), dim3(32), args, 0, st));
+    count_launch();
+    rh_from_qr_kernel<<<ceil_div((int64_t)n * n, 256), 256, 0, st>>>(n, A, work1);
+    NEP_CHECK_LAUNCH();
+    // Jacobi on R^H: work1 -> Uj (work2), Wj (U)
+    NEP_TRY(jacobi_svd(n, n, work1, work2, U, sigma, w, st));
+    apply_q_kernel<<<ceil_div(n, 4), 128, 0, st>>>(n, n, A, tau, n, U);
+    NEP_CHECK_LAUNCH();
+    permute_rows_kernel<<<ceil_div((int64_t)n * n, 256), 256, 0, st>>>(n, n, perm, work2, W);
     NEP_CHECK_LAUNCH();
     return NEP_OK;
 }

@@ -669,7 +669,7 @@ static int run_extract(nep_plan* p, cudaStream_t st) {
     NEP_CUDA(cudaEventRecord(p->ev[4], st));
     // SVD of H and numerical rank
     NEP_CUDA(cudaMemcpyAsync(p->Hw, p->H, sizeof(zd) * LM * LM, cudaMemcpyDeviceToDevice, st));
-    NEP_TRY(jacobi_svd(LM, LM, p->Hw, p->U, p->W, p->sigma, p->jw, st));
+    NEP_TRY(qrcp_jacobi_svd(LM, p->Hw, p->U, p->W, p->sigma, p->T1, p->Bred, p->theta, p->its, p->lamg, p->jw, st));
     NEP_TRY(launch_rank(LM, p->sigma, p->o.rank_tol, p->scalars, st));
     int m = 0;
     NEP_TRY(read_scalar(p, p->scalars, &m, st));

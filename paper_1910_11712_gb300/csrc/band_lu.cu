@@ -69,12 +69,20 @@ __device__ __forceinline__ int warp_pivot(const cx<T>* pcol, int cnt, int lane) 
         T m = abs1(pcol[i]);
         if (m > best) { best = m; bi = i; }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        T ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    if constexpr (sizeof(T) == 4) {
+        // non-negative floats order like their bit patterns: max magnitude, then the smallest
+        // index among the lanes holding it (two warp reductions)
+        const unsigned mb = best < 0 ? 0u : __float_as_uint(best);
+        const unsigned mx = __reduce_max_sync(0xffffffffu, mb);
+        return (int)__reduce_min_sync(0xffffffffu, mb == mx ? (unsigned)bi : 0xffffffffu);
+    } else {
+        for (int o = 16; o > 0; o >>= 1) {
+            T ob = __shfl_xor_sync(0xffffffffu, best, o);
+            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        return bi;
     }
-    return bi;
 }
 
 // Pivot step by warp 0: chooses the pivot among pcol[0..cnt-1], swaps it to pcol[0],
@@ -95,9 +103,10 @@ __device__ __forceinline__ void pivot_step(cx<T>* pcol, cx<T>* lvec, int* piv_s,
     }
     __syncwarp();
     cx<T>* out = ab + (int64_t)c * ldab;
+    const cx<T> rpv = zero ? mk<T>(0, 0) : cdiv(mk<T>(1, 0), pv);
     for (int i = lane; i < kl; i += 32) {
         cx<T> l = mk<T>(0, 0);
-        if (!zero && c + 1 + i < n) l = cdiv(pcol[i + 1], pv);
+        if (!zero && c + 1 + i < n) l = pcol[i + 1] * rpv;
         lvec[i] = l;
         out[kv + 1 + i] = l;
     }
@@ -646,7 +655,7 @@ __device__ __forceinline__ void cp_async_int(int* smem, const int* gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
-template <typename T>
+template <typename T, int RH>
 __global__ void __launch_bounds__(512)
     band_solve_kernel(int n, int kl, int ku, int ldab, const cx<T>* __restrict__ ab_all,
                       const int* __restrict__ ipiv_all, int L, cx<T>* __restrict__ B_all,
@@ -656,26 +665,28 @@ __global__ void __launch_bounds__(512)
     const int kv = kl + ku;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    const int col = blockIdx.y * nwarps + warp;
-    const bool has_col = col < L;
+    const int col0 = (blockIdx.y * nwarps + warp) * RH;  // first right-hand side of this warp
+    const int nrh = max(0, min(RH, L - col0));
+    const bool has_col = nrh > 0;
     const cx<T>* ab = ab_all + (int64_t)j * n * ldab;
     const int* ipiv = ipiv_all + (int64_t)j * n;
-    cx<T>* b = B_all + ((int64_t)j * L + (has_col ? col : 0)) * n;
+    cx<T>* bbase = B_all + ((int64_t)j * L + (has_col ? col0 : 0)) * n;  // column r at bbase + r*n
 
     extern __shared__ unsigned char smem_raw[];
     const int RF = kl + 1, RB = kv + 1;
     const int WIN = RF > RB ? RF : RB;
     const int wide = kv > kl ? kv : (kl > 0 ? kl : 1);
-    // layout: win[nwarps][WIN] | nb[2][nwarps][CH] | stage[2][CH*wide] | diag[2][CH] | pst[2][CH]
-    cx<T>* win = reinterpret_cast<cx<T>*>(smem_raw) + (int64_t)warp * WIN;
-    cx<T>* nb0 = reinterpret_cast<cx<T>*>(smem_raw) + (int64_t)nwarps * WIN;
-    cx<T>* stage0 = nb0 + 2 * (int64_t)nwarps * CH;
+    // layout: win[nwarps][WIN*RH] | nb[2][nwarps][CH*RH] | stage[2][CH*wide] | diag[2][CH] | pst[2][CH]
+    cx<T>* win = reinterpret_cast<cx<T>*>(smem_raw) + (int64_t)warp * WIN * RH;
+    cx<T>* nb0 = reinterpret_cast<cx<T>*>(smem_raw) + (int64_t)nwarps * WIN * RH;
+    cx<T>* stage0 = nb0 + 2 * (int64_t)nwarps * CH * RH;
     cx<T>* diag0 = stage0 + 2 * (int64_t)CH * wide;
     int* pst0 = reinterpret_cast<int*>(diag0 + 2 * CH);
-    auto nbuf = [&](int bsel) { return nb0 + ((int64_t)bsel * nwarps + warp) * CH; };
+    auto nbuf = [&](int bsel) { return nb0 + ((int64_t)bsel * nwarps + warp) * CH * RH; };
     auto sbuf = [&](int bsel) { return stage0 + (int64_t)bsel * CH * wide; };
 
-    // ---- forward: row interchanges and unit lower L. Row r lives in slot r mod RF.
+    // ---- forward: row interchanges and unit lower L. Row r of right-hand side q lives at
+    //      win[(r mod RF)*RH + q].
     auto issue_fwd = [&](int c0, int bsel) {
         const int cn = min(CH, n - c0);
         cx<T>* st = sbuf(bsel);
@@ -686,15 +697,19 @@ __global__ void __launch_bounds__(512)
         for (int e = threadIdx.x; e < cn; e += blockDim.x) cp_async_int<T>(&pst0[bsel * CH + e], ipiv + c0 + e);
         if (has_col) {
             cx<T>* nb = nbuf(bsel);
-            for (int cc = lane; cc < cn; cc += 32) {
+            for (int e = lane; e < cn * RH; e += 32) {
+                const int cc = e / RH, q = e - cc * RH;
                 const int rn = c0 + cc + kl + 1;
-                if (rn < n) cp_async_cx(&nb[cc], b + rn);
-                else nb[cc] = mk<T>(0, 0);
+                if (rn < n && q < nrh) cp_async_cx(&nb[e], bbase + (int64_t)q * n + rn);
+                else nb[e] = mk<T>(0, 0);
             }
         }
         cp_async_commit();
     };
-    for (int i = lane; i < RF; i += 32) win[i] = (has_col && i < n) ? b[i] : mk<T>(0, 0);
+    for (int e = lane; e < RF * RH; e += 32) {
+        const int i = e / RH, q = e - i * RH;
+        win[e] = (q < nrh && i < n) ? bbase[(int64_t)q * n + i] : mk<T>(0, 0);
+    }
     int sc = 0;
     issue_fwd(0, 0);
     for (int c0 = 0, chunk = 0; c0 < n; c0 += CH, ++chunk) {
@@ -710,33 +725,35 @@ __global__ void __launch_bounds__(512)
             for (int cc = 0; cc < cn; ++cc) {
                 const int c = c0 + cc;
                 const int p = pst[cc] - c;
-                if (p != 0 && lane == 0) {
+                if (p != 0 && lane < RH) {
                     int s1 = sc + p;
                     if (s1 >= RF) s1 -= RF;
-                    const cx<T> t = win[sc];
-                    win[sc] = win[s1];
-                    win[s1] = t;
+                    const cx<T> t = win[sc * RH + lane];
+                    win[sc * RH + lane] = win[s1 * RH + lane];
+                    win[s1 * RH + lane] = t;
                 }
                 __syncwarp();
-                const cx<T> xc = win[sc];
                 const cx<T>* lc = st + cc * kl;
-                const int lim = min(kl, n - 1 - c);
-                for (int i = lane; i < lim; i += 32) {
+                const int lim = min(kl, n - 1 - c) * RH;
+                for (int e = lane; e < lim; e += 32) {
+                    const int i = e / RH, q = e - i * RH;
                     int s = sc + 1 + i;
                     if (s >= RF) s -= RF;
-                    win[s] = fms(win[s], lc[i], xc);
+                    win[s * RH + q] = fms(win[s * RH + q], lc[i], win[sc * RH + q]);
                 }
                 __syncwarp();
-                if (lane == 0) {
-                    b[c] = xc;
-                    win[sc] = nb[cc];
+                if (lane < nrh) {
+                    bbase[(int64_t)lane * n + c] = win[sc * RH + lane];
+                    win[sc * RH + lane] = nb[cc * RH + lane];
+                } else if (lane < RH) {
+                    win[sc * RH + lane] = nb[cc * RH + lane];
                 }
                 if (++sc == RF) sc = 0;
                 __syncwarp();
             }
         }
     }
-    // ---- backward: U with bandwidth kv; row r lives in slot r mod RB
+    // ---- backward: U with bandwidth kv; row r of right-hand side q at win[(r mod RB)*RH + q]
     cp_async_wait_group<0>();
     __syncthreads();
     auto issue_bwd = [&](int c1, int bsel) {
@@ -744,7 +761,6 @@ __global__ void __launch_bounds__(512)
         const int cbase = c1 - cn + 1;
         cx<T>* st = sbuf(bsel);
         cx<T>* dg = diag0 + bsel * CH;
-        // st[cc*kv + i] = U(c-1-i, c), c = cbase + cc, gathered from U rows (coalesced by row)
         const int rlo = cbase - kv, rhi = c1 - 1;
         const int nr = rhi - rlo + 1;
         for (int e = threadIdx.x; e < nr * cn; e += blockDim.x) {
@@ -755,23 +771,25 @@ __global__ void __launch_bounds__(512)
         for (int e = threadIdx.x; e < cn; e += blockDim.x) cp_async_cx(&dg[e], ab + (int64_t)(cbase + e) * ldab);
         if (has_col) {
             cx<T>* nb = nbuf(bsel);
-            for (int cc = lane; cc < cn; cc += 32) {
+            for (int e = lane; e < cn * RH; e += 32) {
+                const int cc = e / RH, q = e - cc * RH;
                 const int rn = cbase + cc - kv - 1;
-                if (rn >= 0) cp_async_cx(&nb[cc], b + rn);
-                else nb[cc] = mk<T>(0, 0);
+                if (rn >= 0 && q < nrh) cp_async_cx(&nb[e], bbase + (int64_t)q * n + rn);
+                else nb[e] = mk<T>(0, 0);
             }
         }
         cp_async_commit();
     };
-    for (int i = lane; i < RB; i += 32) {
+    for (int e = lane; e < RB * RH; e += 32) {
+        const int i = e / RH, q = e - i * RH;
         const int r = n - 1 - i;
-        if (r >= 0) win[r % RB] = has_col ? b[r] : mk<T>(0, 0);
+        if (r >= 0) win[(r % RB) * RH + q] = q < nrh ? bbase[(int64_t)q * n + r] : mk<T>(0, 0);
     }
     sc = (n - 1) % RB;
     issue_bwd(n - 1, 0);
     for (int c1 = n - 1, chunk = 0; c1 >= 0; c1 -= CH, ++chunk) {
         const int cn = min(CH, c1 + 1);
-        const int cbase = c1 - cn + 1;  // chunk columns cbase..c1
+        const int cbase = c1 - cn + 1;
         const int bsel = chunk & 1;
         cp_async_wait_group<0>();
         __syncthreads();
@@ -780,26 +798,28 @@ __global__ void __launch_bounds__(512)
             const cx<T>* st = sbuf(bsel);
             const cx<T>* dg = diag0 + bsel * CH;
             const cx<T>* nb = nbuf(bsel);
-            // lane cc holds 1/U(c, c) of chunk column cc (CH <= 32), fetched by shuffle per step
             const cx<T> rd = lane < cn ? cdiv(mk<T>(1, 0), dg[lane]) : mk<T>(0, 0);
             for (int cc = cn - 1; cc >= 0; --cc) {
                 const int c = cbase + cc;
                 cx<T> r;
                 r.re = __shfl_sync(0xffffffffu, rd.re, cc);
                 r.im = __shfl_sync(0xffffffffu, rd.im, cc);
-                const cx<T> xc = win[sc] * r;
+                if (lane < RH) win[sc * RH + lane] = win[sc * RH + lane] * r;
                 __syncwarp();
                 const cx<T>* uc = st + cc * kv;
-                const int lim = min(kv, c);
-                for (int i = lane; i < lim; i += 32) {
+                const int lim = min(kv, c) * RH;
+                for (int e = lane; e < lim; e += 32) {
+                    const int i = e / RH, q = e - i * RH;
                     int s = sc - 1 - i;
                     if (s < 0) s += RB;
-                    win[s] = fms(win[s], uc[i], xc);
+                    win[s * RH + q] = fms(win[s * RH + q], uc[i], win[sc * RH + q]);
                 }
                 __syncwarp();
-                if (lane == 0) {
-                    b[c] = xc;
-                    win[sc] = nb[cc];
+                if (lane < nrh) {
+                    bbase[(int64_t)lane * n + c] = win[sc * RH + lane];
+                    win[sc * RH + lane] = nb[cc * RH + lane];
+                } else if (lane < RH) {
+                    win[sc * RH + lane] = nb[cc * RH + lane];
                 }
                 if (--sc < 0) sc = RB - 1;
                 __syncwarp();
@@ -813,23 +833,25 @@ int launch_band_solve(const SplitDev& s, int npts, const cx<T>* ab, const int* i
                       const int* active, cudaStream_t st) {
     if (npts <= 0 || L <= 0) return NEP_OK;
     const int kv = s.kl + s.ku;
-    // few warps per CTA so that the (latency-bound) column chains of one point spread over SMs
-    const int wpb = L < 4 ? L : 4;
-    const int gy = (L + wpb - 1) / wpb;
+    // four right-hand sides per warp (the per-step overhead of a column is shared), two warps per CTA
+    constexpr int RH = 4;
+    const int warps_total = (L + RH - 1) / RH;
+    const int wpb = warps_total < 2 ? warps_total : 2;
+    const int gy = (warps_total + wpb - 1) / wpb;
     const int WIN = (s.kl + 1) > (kv + 1) ? (s.kl + 1) : (kv + 1);
     const int wide = kv > s.kl ? kv : (s.kl > 0 ? s.kl : 1);
     const size_t budget = 200 * 1024;
     int CH = 32;
     auto bytes = [&](int ch) {
-        return sizeof(cx<T>) * ((size_t)wpb * WIN + 2 * (size_t)wpb * ch + 2 * (size_t)ch * wide + 2 * ch) +
+        return sizeof(cx<T>) * ((size_t)wpb * WIN * RH + 2 * (size_t)wpb * ch * RH + 2 * (size_t)ch * wide + 2 * ch) +
                sizeof(int) * 2 * ch;
     };
     while (CH > 1 && bytes(CH) > budget) CH >>= 1;
     const size_t smem = bytes(CH);
     if (smem > 227 * 1024) return NEP_ERR_UNSUPPORTED;
-    NEP_CUDA(cudaFuncSetAttribute(band_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    NEP_CUDA(cudaFuncSetAttribute(band_solve_kernel<T, RH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(npts, gy);
-    band_solve_kernel<T><<<grid, wpb * 32, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, L, B, active, CH);
+    band_solve_kernel<T, RH><<<grid, wpb * 32, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, L, B, active, CH);
     NEP_CHECK_LAUNCH();
     return NEP_OK;
 }

@@ -109,7 +109,7 @@ int zgemm(int M, int N, int K, int opA, const zd* A, int lda, const zd* B, int l
 // ------------------------------------------------------------------ grid barrier
 // Barrier for a cooperative launch (all CTAs co-resident) on a monotonically increasing
 // arrival counter: barrier number e completes once the counter reaches e * gridDim.x, so it
-// needs one atomic per CTA and no reset. Every wait is bounded: after ~2^22 polls the CTA
+// needs one atomic per CTA and no reset. Every wait is bounded: after 2^24 polls (seconds) the CTA
 // records an error and continues.
 struct GridBar {
     unsigned int* count;
@@ -127,11 +127,10 @@ __device__ __forceinline__ void grid_barrier(GridBar b, unsigned int& epoch) {
         volatile unsigned int* vc = b.count;
         long long spins = 0;
         while (*vc < target) {
-            if (++spins > (1ll << 22)) {
+            if (++spins > (1ll << 24)) {
                 atomicExch(b.err, 1);
                 break;
             }
-            __nanosleep(32);
         }
         __threadfence();
     }
@@ -181,6 +180,54 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __r
                 if (p > q) { const int t = p; p = q; q = t; }
                 zd* ap = A + (int64_t)p * rows;
                 zd* aq = A + (int64_t)q * rows;
+                zd* vp = Vm + (int64_t)p * cols;
+                zd* vq = Vm + (int64_t)q * cols;
+                if (rows <= 256 && cols <= 256) {
+                    // both column pairs in registers: all loads issued up front
+                    zd xa[8], ya[8], xv[8], yv[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const int i = lane + 32 * t;
+                        xa[t] = i < rows ? ldcg(ap + i) : mk(0.0, 0.0);
+                        ya[t] = i < rows ? ldcg(aq + i) : mk(0.0, 0.0);
+                        xv[t] = i < cols ? ldcg(vp + i) : mk(0.0, 0.0);
+                        yv[t] = i < cols ? ldcg(vq + i) : mk(0.0, 0.0);
+                    }
+                    double al = 0.0, be = 0.0;
+                    zd ga = mk(0.0, 0.0);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        al += norm2(xa[t]);
+                        be += norm2(ya[t]);
+                        ga = fmac(ga, xa[t], ya[t]);
+                    }
+                    for (int o = 16; o > 0; o >>= 1) {
+                        al += __shfl_xor_sync(0xffffffffu, al, o);
+                        be += __shfl_xor_sync(0xffffffffu, be, o);
+                        ga.re += __shfl_xor_sync(0xffffffffu, ga.re, o);
+                        ga.im += __shfl_xor_sync(0xffffffffu, ga.im, o);
+                    }
+                    const double g = hypot(ga.re, ga.im);
+                    if (!(g > tol * sqrt(al * be)) || al == 0.0 || be == 0.0) continue;
+                    const double zeta = (be - al) / (2.0 * g);
+                    const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+                    const zd se = mk(sn * ga.re / g, sn * ga.im / g), sec = conj(se);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int i = lane + 32 * u;
+                        if (i < rows) {
+                            ap[i] = c * xa[u] - sec * ya[u];
+                            aq[i] = se * xa[u] + c * ya[u];
+                        }
+                        if (i < cols) {
+                            vp[i] = c * xv[u] - sec * yv[u];
+                            vq[i] = se * xv[u] + c * yv[u];
+                        }
+                    }
+                    if (lane == 0) atomicOr(&flags[sweep & 1], 1);
+                    continue;
+                }
                 double al = 0.0, be = 0.0;
                 zd ga = mk(0.0, 0.0);
                 for (int i = lane; i < rows; i += 32) {
@@ -207,8 +254,6 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __r
                     ap[i] = c * x - sec * y;
                     aq[i] = se * x + c * y;
                 }
-                zd* vp = Vm + (int64_t)p * cols;
-                zd* vq = Vm + (int64_t)q * cols;
                 for (int i = lane; i < cols; i += 32) {
                     const zd x = ldcg(vp + i), y = ldcg(vq + i);
                     vp[i] = c * x - sec * y;

@@ -828,15 +828,249 @@ __global__ void __launch_bounds__(512)
     }
 }
 
+// Register-window solve for narrow bands: one warp per right-hand side, the window rows live in
+// registers (slot r mod RS, lane = slot % 32, register = slot / 32), x_c is broadcast by shuffle
+// and each lane updates its own rows, so a column step is a few shuffles and one complex FMA
+// per owned row. dist[q] = (slot - current - 1) mod RS tracks which row a register holds.
+template <typename T, int RPL>
+__device__ __forceinline__ cx<T> sel_reg(const cx<T> (&a)[RPL], int q) {
+    cx<T> v = a[0];
+#pragma unroll
+    for (int t = 1; t < RPL; ++t)
+        if (t == q) v = a[t];
+    return v;
+}
+template <typename T, int RPL>
+__device__ __forceinline__ void set_reg(cx<T> (&a)[RPL], int q, cx<T> v) {
+#pragma unroll
+    for (int t = 0; t < RPL; ++t)
+        if (t == q) a[t] = v;
+}
+
+template <typename T, int RPLF, int RPLB>
+__global__ void __launch_bounds__(128)
+    band_solve_reg_kernel(int n, int kl, int ku, int ldab, const cx<T>* __restrict__ ab_all,
+                          const int* __restrict__ ipiv_all, int L, cx<T>* __restrict__ B_all,
+                          const int* __restrict__ active, int CH) {
+    const int j = blockIdx.x;
+    if (active && !active[j]) return;
+    constexpr int RSF = 32 * RPLF, RSB = 32 * RPLB;
+    const int kv = kl + ku;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const int col = blockIdx.y * nwarps + warp;
+    const bool has_col = col < L;
+    const cx<T>* ab = ab_all + (int64_t)j * n * ldab;
+    const int* ipiv = ipiv_all + (int64_t)j * n;
+    cx<T>* b = B_all + ((int64_t)j * L + (has_col ? col : 0)) * n;
+
+    extern __shared__ unsigned char smem_raw[];
+    const int wide = kv > kl ? kv : (kl > 0 ? kl : 1);
+    // layout: nb[2][nwarps][CH] | stage[2][CH*wide] | diag[2][CH] | pst[2][CH]
+    cx<T>* nb0 = reinterpret_cast<cx<T>*>(smem_raw);
+    cx<T>* stage0 = nb0 + 2 * (int64_t)nwarps * CH;
+    cx<T>* diag0 = stage0 + 2 * (int64_t)CH * wide;
+    int* pst0 = reinterpret_cast<int*>(diag0 + 2 * CH);
+    auto nbuf = [&](int bsel) { return nb0 + ((int64_t)bsel * nwarps + warp) * CH; };
+    auto sbuf = [&](int bsel) { return stage0 + (int64_t)bsel * CH * wide; };
+
+    // ---------------- forward
+    auto issue_fwd = [&](int c0, int bsel) {
+        const int cn = min(CH, n - c0);
+        cx<T>* st = sbuf(bsel);
+        for (int e = threadIdx.x; e < cn * kl; e += blockDim.x) {
+            const int cc = e / kl, i = e - cc * kl;
+            cp_async_cx(&st[e], ab + (int64_t)(c0 + cc) * ldab + kv + 1 + i);
+        }
+        for (int e = threadIdx.x; e < cn; e += blockDim.x) cp_async_int<T>(&pst0[bsel * CH + e], ipiv + c0 + e);
+        if (has_col) {
+            cx<T>* nb = nbuf(bsel);
+            for (int cc = lane; cc < cn; cc += 32) {
+                const int rn = c0 + cc + kl + 1;
+                if (rn < n) cp_async_cx(&nb[cc], b + rn);
+                else nb[cc] = mk<T>(0, 0);
+            }
+        }
+        cp_async_commit();
+    };
+    cx<T> a[RPLF];
+    int dist[RPLF];
+#pragma unroll
+    for (int q = 0; q < RPLF; ++q) {
+        const int s = lane + 32 * q;  // slot s holds row s at c = 0
+        a[q] = (has_col && s <= kl && s < n) ? b[s] : mk<T>(0, 0);
+        dist[q] = s == 0 ? RSF - 1 : s - 1;  // (s - 0 - 1) mod RSF
+    }
+    int sc = 0;
+    issue_fwd(0, 0);
+    for (int c0 = 0, chunk = 0; c0 < n; c0 += CH, ++chunk) {
+        const int cn = min(CH, n - c0);
+        const int bsel = chunk & 1;
+        cp_async_wait_group<0>();
+        __syncthreads();
+        if (c0 + CH < n) issue_fwd(c0 + CH, bsel ^ 1);
+        if (has_col) {
+            const cx<T>* st = sbuf(bsel);
+            const int* pst = pst0 + bsel * CH;
+            const cx<T>* nb = nbuf(bsel);
+            for (int cc = 0; cc < cn; ++cc) {
+                const int c = c0 + cc;
+                const int p = pst[cc] - c;
+                const int lc = sc & 31, qc = sc >> 5;
+                const cx<T> vc = shfl_cx(sel_reg(a, qc), lc);
+                cx<T> x = vc;
+                if (p != 0) {
+                    int sp = sc + p;
+                    if (sp >= RSF) sp -= RSF;
+                    const int lp = sp & 31, qp = sp >> 5;
+                    const cx<T> vp = shfl_cx(sel_reg(a, qp), lp);
+                    if (lane == lp) set_reg(a, qp, vc);
+                    x = vp;
+                }
+                const cx<T>* lcol = st + cc * kl;
+                const int lim = min(kl, n - 1 - c);
+#pragma unroll
+                for (int q = 0; q < RPLF; ++q)
+                    if (dist[q] < lim) a[q] = fms(a[q], lcol[dist[q]], x);
+                if (lane == lc) b[c] = x;
+                // row c+kl+1 enters
+                int sn = sc + kl + 1;
+                if (sn >= RSF) sn -= RSF;
+                if (lane == (sn & 31)) set_reg(a, sn >> 5, nb[cc]);
+#pragma unroll
+                for (int q = 0; q < RPLF; ++q) dist[q] = dist[q] == 0 ? RSF - 1 : dist[q] - 1;
+                if (++sc == RSF) sc = 0;
+            }
+        }
+    }
+    // ---------------- backward
+    cp_async_wait_group<0>();
+    __syncthreads();
+    auto issue_bwd = [&](int c1, int bsel) {
+        const int cn = min(CH, c1 + 1);
+        const int cbase = c1 - cn + 1;
+        cx<T>* st = sbuf(bsel);
+        cx<T>* dg = diag0 + bsel * CH;
+        const int rlo = cbase - kv, rhi = c1 - 1;
+        const int nr = rhi - rlo + 1;
+        for (int e = threadIdx.x; e < nr * cn; e += blockDim.x) {
+            const int ri = e / cn, cc = e - ri * cn;
+            const int r = rlo + ri, c = cbase + cc, t = c - r;
+            if (r >= 0 && t >= 1 && t <= kv) cp_async_cx(&st[cc * kv + (t - 1)], ab + (int64_t)r * ldab + t);
+        }
+        for (int e = threadIdx.x; e < cn; e += blockDim.x) cp_async_cx(&dg[e], ab + (int64_t)(cbase + e) * ldab);
+        if (has_col) {
+            cx<T>* nb = nbuf(bsel);
+            for (int cc = lane; cc < cn; cc += 32) {
+                const int rn = cbase + cc - kv - 1;
+                if (rn >= 0) cp_async_cx(&nb[cc], b + rn);
+                else nb[cc] = mk<T>(0, 0);
+            }
+        }
+        cp_async_commit();
+    };
+    // rows n-1-i (i <= kv) in slot (n-1-i) mod RSB; dist = (slot_current - 1 - slot) mod RSB
+    cx<T> w[RPLB];
+    int dw[RPLB];
+    const int s0 = (n - 1) % RSB;
+#pragma unroll
+    for (int q = 0; q < RPLB; ++q) {
+        const int s = lane + 32 * q;
+        int back = s0 - s;
+        if (back < 0) back += RSB;  // slot s holds row n-1-back
+        const int r = n - 1 - back;
+        w[q] = (has_col && back <= kv && r >= 0) ? b[r] : mk<T>(0, 0);
+        dw[q] = back == 0 ? RSB - 1 : back - 1;
+    }
+    sc = s0;
+    issue_bwd(n - 1, 0);
+    for (int c1 = n - 1, chunk = 0; c1 >= 0; c1 -= CH, ++chunk) {
+        const int cn = min(CH, c1 + 1);
+        const int cbase = c1 - cn + 1;
+        const int bsel = chunk & 1;
+        cp_async_wait_group<0>();
+        __syncthreads();
+        if (c1 - CH >= 0) issue_bwd(c1 - CH, bsel ^ 1);
+        if (has_col) {
+            const cx<T>* st = sbuf(bsel);
+            const cx<T>* dg = diag0 + bsel * CH;
+            const cx<T>* nb = nbuf(bsel);
+            const cx<T> rd = lane < cn ? cdiv(mk<T>(1, 0), dg[lane]) : mk<T>(0, 0);
+            for (int cc = cn - 1; cc >= 0; --cc) {
+                const int c = cbase + cc;
+                const cx<T> r = shfl_cx(rd, cc);
+                const int lc = sc & 31, qc = sc >> 5;
+                const cx<T> x = shfl_cx(sel_reg(w, qc), lc) * r;
+                const cx<T>* ucol = st + cc * kv;
+                const int lim = min(kv, c);
+#pragma unroll
+                for (int q = 0; q < RPLB; ++q)
+                    if (dw[q] < lim) w[q] = fms(w[q], ucol[dw[q]], x);
+                if (lane == lc) b[c] = x;
+                // row c-kv-1 enters its slot (c-kv-1) mod RSB
+                int sn = sc - kv - 1;
+                while (sn < 0) sn += RSB;
+                if (lane == (sn & 31)) set_reg(w, sn >> 5, nb[cc]);
+#pragma unroll
+                for (int q = 0; q < RPLB; ++q) dw[q] = dw[q] == 0 ? RSB - 1 : dw[q] - 1;
+                if (--sc < 0) sc = RSB - 1;
+            }
+        }
+    }
+}
+
+template <typename T, int RPLF, int RPLB>
+static int run_solve_reg(const SplitDev& s, int npts, const cx<T>* ab, const int* ipiv, int L, cx<T>* B,
+                         const int* active, cudaStream_t st) {
+    const int kv = s.kl + s.ku;
+    const int wpb = L < 4 ? L : 4;
+    const int gy = (L + wpb - 1) / wpb;
+    const int wide = kv > s.kl ? kv : (s.kl > 0 ? s.kl : 1);
+    int CH = 32;
+    auto bytes = [&](int ch) {
+        return sizeof(cx<T>) * (2 * (size_t)wpb * ch + 2 * (size_t)ch * wide + 2 * ch) + sizeof(int) * 2 * ch;
+    };
+    while (CH > 1 && bytes(CH) > 200 * 1024) CH >>= 1;
+    const size_t smem = bytes(CH);
+    NEP_CUDA(cudaFuncSetAttribute(band_solve_reg_kernel<T, RPLF, RPLB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    band_solve_reg_kernel<T, RPLF, RPLB><<<dim3(npts, gy), wpb * 32, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, L,
+                                                                              B, active, CH);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+
+template <typename T, int RPLF>
+static int solve_reg_b(const SplitDev& s, int npts, const cx<T>* ab, const int* ipiv, int L, cx<T>* B,
+                       const int* active, cudaStream_t st, int rplb) {
+    switch (rplb) {
+        case 1: return run_solve_reg<T, RPLF, 1>(s, npts, ab, ipiv, L, B, active, st);
+        case 2: return run_solve_reg<T, RPLF, 2>(s, npts, ab, ipiv, L, B, active, st);
+        case 3: return run_solve_reg<T, RPLF, 3>(s, npts, ab, ipiv, L, B, active, st);
+        case 4: return run_solve_reg<T, RPLF, 4>(s, npts, ab, ipiv, L, B, active, st);
+        case 5: return run_solve_reg<T, RPLF, 5>(s, npts, ab, ipiv, L, B, active, st);
+    }
+    return NEP_ERR_INTERNAL;
+}
+
 template <typename T>
 int launch_band_solve(const SplitDev& s, int npts, const cx<T>* ab, const int* ipiv, int L, cx<T>* B,
                       const int* active, cudaStream_t st) {
     if (npts <= 0 || L <= 0) return NEP_OK;
     const int kv = s.kl + s.ku;
-    // four right-hand sides per warp (the per-step overhead of a column is shared), two warps per CTA
-    constexpr int RH = 4;
-    const int warps_total = (L + RH - 1) / RH;
-    const int wpb = warps_total < 2 ? warps_total : 2;
+    // register windows for narrow bands: kl+1 <= 96 rows forward, kv+1 <= 160 rows backward
+    const int rplf = (s.kl + 1 + 31) / 32, rplb = (kv + 1 + 31) / 32;
+    if (s.kl >= 1 && rplf <= 3 && rplb <= 5) {
+        switch (rplf) {
+            case 1: return solve_reg_b<T, 1>(s, npts, ab, ipiv, L, B, active, st, rplb);
+            case 2: return solve_reg_b<T, 2>(s, npts, ab, ipiv, L, B, active, st, rplb);
+            case 3: return solve_reg_b<T, 3>(s, npts, ab, ipiv, L, B, active, st, rplb);
+        }
+    }
+    // general path: shared-memory windows, one right-hand side per warp, four warps per CTA
+    constexpr int RH = 1;
+    const int warps_total = L;
+    const int wpb = warps_total < 4 ? warps_total : 4;
     const int gy = (warps_total + wpb - 1) / wpb;
     const int WIN = (s.kl + 1) > (kv + 1) ? (s.kl + 1) : (kv + 1);
     const int wide = kv > s.kl ? kv : (s.kl > 0 ? s.kl : 1);

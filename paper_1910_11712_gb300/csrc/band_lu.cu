@@ -318,6 +318,13 @@ __global__ void __launch_bounds__(NW * 32, 1)
         cp_async_commit();
     }
 
+    // tcol[p] = (column slot - c - 1) mod CS: the column of register p is c+1+tcol[p];
+    // trow[q] = (row slot - c - 1) mod RS: the row of register q is c+1+trow[q]
+    int tcol[CPL], trow[RPW];
+#pragma unroll
+    for (int p = 0; p < CPL; ++p) tcol[p] = posmod(lane + 32 * p - 1, CS);
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) trow[q] = posmod(warp * RPW + q - 1, RS);
     for (int c = 0; c < n; ++c) {
         const int buf = c % (PF + 1);
         // (1) publish column c; its slot then starts column c+kv with zero fill
@@ -370,28 +377,24 @@ __global__ void __launch_bounds__(NW * 32, 1)
         if (prel != kl && warp == wp) {
 #pragma unroll
             for (int p = 0; p < CPL; ++p) {
-                const int cs = lane + 32 * p;
-                const int t = posmod(cs - c - 1, CS);  // column k = c+1+t
-                if (t < kv) {
+                if (tcol[p] < kv) {
                     cx<T> v = a[0][p];
 #pragma unroll
                     for (int q = 1; q < RPW; ++q)
                         if (q == qp) v = a[q][p];
-                    urow[t] = v;
+                    urow[tcol[p]] = v;
                 }
             }
         }
         if (prel != 0 && warp == wc) {
 #pragma unroll
             for (int p = 0; p < CPL; ++p) {
-                const int cs = lane + 32 * p;
-                const int t = posmod(cs - c - 1, CS);
-                if (t < kv) {
+                if (tcol[p] < kv) {
                     cx<T> v = a[0][p];
 #pragma unroll
                     for (int q = 1; q < RPW; ++q)
                         if (q == qc) v = a[q][p];
-                    oldc[t] = v;
+                    oldc[tcol[p]] = v;
                 }
             }
         }
@@ -401,39 +404,53 @@ __global__ void __launch_bounds__(NW * 32, 1)
         cx<T>* out = ab + (int64_t)c * ldab;
         for (int t = threadIdx.x; t < kv; t += blockDim.x)
             if (c + 1 + t < n) out[1 + t] = u[t];
-        // (4) row moves, new row c+kl, rank-1 update
+        // (4) row moves (only the owner warps), new row c+kl, rank-1 update
         const int rsn = (c + kl) % RS, wn = rsn / RPW, qn = rsn % RPW;
+        if (warp == wn || (warp == wp && prel != 0 && prel != kl)) {
+#pragma unroll
+            for (int p = 0; p < CPL; ++p) {
+                const int t = tcol[p];
+                if (t >= kv) continue;
+                if (prel != 0 && prel != kl && warp == wp) {
+#pragma unroll
+                    for (int q = 0; q < RPW; ++q)
+                        if (q == qp) a[q][p] = oldc[t];
+                }
+                if (warp == wn) {
+                    const cx<T> nv = (prel == kl) ? oldc[t] : nrow[buf][1 + t];
+#pragma unroll
+                    for (int q = 0; q < RPW; ++q)
+                        if (q == qn) a[q][p] = nv;
+                }
+            }
+        }
+        const bool interior = (c + kl < n) && (c + kv < n);  // no row or column beyond n-1
         cx<T> lq[RPW];
-        int rowok[RPW];
 #pragma unroll
-        for (int q = 0; q < RPW; ++q) {
-            const int i = posmod(warp * RPW + q - c - 1, RS);  // row c+1+i
-            rowok[q] = (i < kl) && (c + 1 + i < n);
-            lq[q] = rowok[q] ? lvec[i] : mk<T>(0, 0);
-        }
+        for (int q = 0; q < RPW; ++q) lq[q] = trow[q] < kl ? lvec[trow[q]] : mk<T>(0, 0);
+        if (interior) {
 #pragma unroll
-        for (int p = 0; p < CPL; ++p) {
-            const int cs = lane + 32 * p;
-            const int t = posmod(cs - c - 1, CS);
-            if (t >= kv) continue;
-            const cx<T> up = u[t];
-            if (prel != 0 && prel != kl && warp == wp) {
+            for (int p = 0; p < CPL; ++p) {
+                if (tcol[p] >= kv) continue;
+                const cx<T> up = u[tcol[p]];
 #pragma unroll
-                for (int q = 0; q < RPW; ++q)
-                    if (q == qp) a[q][p] = oldc[t];
+                for (int q = 0; q < RPW; ++q) a[q][p] = fms(a[q][p], lq[q], up);
             }
-            if (warp == wn) {
-                const cx<T> nv = (prel == kl) ? oldc[t] : nrow[buf][1 + t];
+        } else {
+#pragma unroll
+            for (int p = 0; p < CPL; ++p) {
+                if (tcol[p] >= kv || c + 1 + tcol[p] >= n) continue;
+                const cx<T> up = u[tcol[p]];
 #pragma unroll
                 for (int q = 0; q < RPW; ++q)
-                    if (q == qn) a[q][p] = nv;
-            }
-            if (c + 1 + t < n) {
-#pragma unroll
-                for (int q = 0; q < RPW; ++q)
-                    if (rowok[q]) a[q][p] = fms(a[q][p], lq[q], up);
+                    if (trow[q] < kl && c + 1 + trow[q] < n) a[q][p] = fms(a[q][p], lq[q], up);
             }
         }
+        // slot offsets for the next step
+#pragma unroll
+        for (int p = 0; p < CPL; ++p) tcol[p] = tcol[p] == 0 ? CS - 1 : tcol[p] - 1;
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) trow[q] = trow[q] == 0 ? RS - 1 : trow[q] - 1;
     }
     __syncthreads();
     if (threadIdx.x == 0) info_all[j] = info_s;

@@ -156,8 +156,13 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __r
                                                      int max_sweeps, double tol, int* __restrict__ flags,
                                                      int* __restrict__ sweeps_out, GridBar bar) {
     const int lane = threadIdx.x & 31;
-    const int gwarp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    // nsub warps per CTA: with several, the CTA works on one pair at a time (warps split rows, one
+    // warp per SM sub-partition so the pair gets the whole SM's FP64 rate); with one, each warp
+    // takes its own pair
+    const int nsub = blockDim.x >> 5;
+    const int gwarp = nsub > 1 ? (int)blockIdx.x : (int)(blockIdx.x * nsub + (threadIdx.x >> 5));
+    const int nwarps = nsub > 1 ? (int)gridDim.x : (int)(gridDim.x * nsub);
+    __shared__ double red4[8][4];
     const int P = cols + (cols & 1);
     // V = I
     unsigned int epoch = 0;
@@ -182,31 +187,44 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __r
                 zd* aq = A + (int64_t)q * rows;
                 zd* vp = Vm + (int64_t)p * cols;
                 zd* vq = Vm + (int64_t)q * cols;
-                if (rows <= 256 && cols <= 256) {
-                    // both column pairs in registers: all loads issued up front
-                    zd xa[8], ya[8], xv[8], yv[8];
+                if (rows <= 256 && cols <= 256 && nsub > 1) {
+                    // the CTA's warps split the rows: one register element per lane per column
+                    // (rows <= 32 * nsub * 2); partial dot products meet in shared memory
+                    const int tid = threadIdx.x, nthr = blockDim.x;
+                    zd xa[2], ya[2], xv[2], yv[2];
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) {
-                        const int i = lane + 32 * t;
+                    for (int t = 0; t < 2; ++t) {
+                        const int i = tid + nthr * t;
                         xa[t] = i < rows ? ldcg(ap + i) : mk(0.0, 0.0);
                         ya[t] = i < rows ? ldcg(aq + i) : mk(0.0, 0.0);
                         xv[t] = i < cols ? ldcg(vp + i) : mk(0.0, 0.0);
                         yv[t] = i < cols ? ldcg(vq + i) : mk(0.0, 0.0);
                     }
-                    double al = 0.0, be = 0.0;
-                    zd ga = mk(0.0, 0.0);
-#pragma unroll
-                    for (int t = 0; t < 8; ++t) {
-                        al += norm2(xa[t]);
-                        be += norm2(ya[t]);
-                        ga = fmac(ga, xa[t], ya[t]);
-                    }
+                    double al = norm2(xa[0]) + norm2(xa[1]), be = norm2(ya[0]) + norm2(ya[1]);
+                    zd ga = fmac(fmac(mk(0.0, 0.0), xa[0], ya[0]), xa[1], ya[1]);
                     for (int o = 16; o > 0; o >>= 1) {
                         al += __shfl_xor_sync(0xffffffffu, al, o);
                         be += __shfl_xor_sync(0xffffffffu, be, o);
                         ga.re += __shfl_xor_sync(0xffffffffu, ga.re, o);
                         ga.im += __shfl_xor_sync(0xffffffffu, ga.im, o);
                     }
+                    const int w = tid >> 5;
+                    if (lane == 0) {
+                        red4[w][0] = al;
+                        red4[w][1] = be;
+                        red4[w][2] = ga.re;
+                        red4[w][3] = ga.im;
+                    }
+                    __syncthreads();
+                    al = be = 0.0;
+                    ga = mk(0.0, 0.0);
+                    for (int q = 0; q < nsub; ++q) {
+                        al += red4[q][0];
+                        be += red4[q][1];
+                        ga.re += red4[q][2];
+                        ga.im += red4[q][3];
+                    }
+                    __syncthreads();
                     const double g = hypot(ga.re, ga.im);
                     if (!(g > tol * sqrt(al * be)) || al == 0.0 || be == 0.0) continue;
                     const double zeta = (be - al) / (2.0 * g);
@@ -214,8 +232,8 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __r
                     const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
                     const zd se = mk(sn * ga.re / g, sn * ga.im / g), sec = conj(se);
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int i = lane + 32 * u;
+                    for (int u = 0; u < 2; ++u) {
+                        const int i = tid + nthr * u;
                         if (i < rows) {
                             ap[i] = c * xa[u] - sec * ya[u];
                             aq[i] = se * xa[u] + c * ya[u];
@@ -225,7 +243,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __r
                             vq[i] = se * xv[u] + c * yv[u];
                         }
                     }
-                    if (lane == 0) atomicOr(&flags[sweep & 1], 1);
+                    if (tid == 0) atomicOr(&flags[sweep & 1], 1);
                     continue;
                 }
                 double al = 0.0, be = 0.0;
@@ -312,9 +330,11 @@ int jacobi_svd(int rows, int cols, zd* A, zd* U, zd* W, double* sigma, JacobiWor
     int dev = 0, sms = 0;
     NEP_CUDA(cudaGetDevice(&dev));
     NEP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    // one warp (one column pair) per CTA, so that each pair gets a whole SM's FP64 pipe
+    // one column pair per CTA of four warps (one per SM sub-partition) for matrices up to 256
+    // rows, so that each pair gets the whole SM's FP64 rate; one pair per warp beyond that
+    const int tpb = (rows <= 256 && cols <= 256) ? 128 : 32;
     int per_sm = 0;
-    NEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, 32, 0));
+    NEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, tpb, 0));
     int blocks = std::max(1, std::min(P / 2, sms * std::max(per_sm, 1)));
     GridBar gb{w.bar, w.bar + 1, w.err};
     int max_sweeps = 40;
@@ -322,7 +342,7 @@ int jacobi_svd(int rows, int cols, zd* A, zd* U, zd* W, double* sigma, JacobiWor
     // rotation angle is rounding noise
     double tol = std::max(rows, 1) * 2.220446049250313e-16;
     void* args[] = {&rows, &cols, &A, &w.Vm, &max_sweeps, &tol, &w.flags, &w.sweeps, &gb};
-    NEP_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(32), args, 0, st));
+    NEP_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(tpb), args, 0, st));
     count_launch();
     svd_finish_kernel<<<1, 256, (sizeof(double) + sizeof(int)) * cols, st>>>(rows, cols, A, w.Vm, U, W, sigma);
     NEP_CHECK_LAUNCH();

@@ -895,18 +895,17 @@ __global__ void __launch_bounds__(128)
     auto issue_fwd = [&](int c0, int bsel) {
         const int cn = min(CH, n - c0);
         cx<T>* st = sbuf(bsel);
-        for (int e = threadIdx.x; e < cn * kl; e += blockDim.x) {
-            const int cc = e / kl, i = e - cc * kl;
-            cp_async_cx(&st[e], ab + (int64_t)(c0 + cc) * ldab + kv + 1 + i);
+        // L columns of the chunk: warps over columns, lanes over rows (no integer division)
+        for (int cc = warp; cc < cn; cc += nwarps) {
+            const cx<T>* src = ab + (int64_t)(c0 + cc) * ldab + kv + 1;
+            for (int i = lane; i < kl; i += 32) cp_async_cx(&st[cc * kl + i], src + i);
         }
-        for (int e = threadIdx.x; e < cn; e += blockDim.x) cp_async_int<T>(&pst0[bsel * CH + e], ipiv + c0 + e);
-        if (has_col) {
+        if (warp == 0 && lane < cn) cp_async_int<T>(&pst0[bsel * CH + lane], ipiv + c0 + lane);
+        if (has_col && lane < cn) {
             cx<T>* nb = nbuf(bsel);
-            for (int cc = lane; cc < cn; cc += 32) {
-                const int rn = c0 + cc + kl + 1;
-                if (rn < n) cp_async_cx(&nb[cc], b + rn);
-                else nb[cc] = mk<T>(0, 0);
-            }
+            const int rn = c0 + lane + kl + 1;
+            if (rn < n) cp_async_cx(&nb[lane], b + rn);
+            else nb[lane] = mk<T>(0, 0);
         }
         cp_async_commit();
     };
@@ -968,21 +967,19 @@ __global__ void __launch_bounds__(128)
         const int cbase = c1 - cn + 1;
         cx<T>* st = sbuf(bsel);
         cx<T>* dg = diag0 + bsel * CH;
-        const int rlo = cbase - kv, rhi = c1 - 1;
-        const int nr = rhi - rlo + 1;
-        for (int e = threadIdx.x; e < nr * cn; e += blockDim.x) {
-            const int ri = e / cn, cc = e - ri * cn;
-            const int r = rlo + ri, c = cbase + cc, t = c - r;
-            if (r >= 0 && t >= 1 && t <= kv) cp_async_cx(&st[cc * kv + (t - 1)], ab + (int64_t)r * ldab + t);
+        // U rows rlo..c1-1, each contributing U(r, c) for the chunk columns c (lanes over c)
+        const int rlo = cbase - kv;
+        for (int r = rlo + warp; r < c1; r += nwarps) {
+            if (r < 0) continue;
+            const int c = cbase + lane, t = c - r;
+            if (lane < cn && t >= 1 && t <= kv) cp_async_cx(&st[lane * kv + (t - 1)], ab + (int64_t)r * ldab + t);
         }
-        for (int e = threadIdx.x; e < cn; e += blockDim.x) cp_async_cx(&dg[e], ab + (int64_t)(cbase + e) * ldab);
-        if (has_col) {
+        if (warp == 0 && lane < cn) cp_async_cx(&dg[lane], ab + (int64_t)(cbase + lane) * ldab);
+        if (has_col && lane < cn) {
             cx<T>* nb = nbuf(bsel);
-            for (int cc = lane; cc < cn; cc += 32) {
-                const int rn = cbase + cc - kv - 1;
-                if (rn >= 0) cp_async_cx(&nb[cc], b + rn);
-                else nb[cc] = mk<T>(0, 0);
-            }
+            const int rn = cbase + lane - kv - 1;
+            if (rn >= 0) cp_async_cx(&nb[lane], b + rn);
+            else nb[lane] = mk<T>(0, 0);
         }
         cp_async_commit();
     };

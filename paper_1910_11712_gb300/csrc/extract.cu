@@ -191,17 +191,24 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __r
                     // the CTA's warps split the rows: one register element per lane per column
                     // (rows <= 32 * nsub * 2); partial dot products meet in shared memory
                     const int tid = threadIdx.x, nthr = blockDim.x;
+                    const bool two = rows > nthr || cols > nthr;  // second element per thread needed
                     zd xa[2], ya[2], xv[2], yv[2];
 #pragma unroll
                     for (int t = 0; t < 2; ++t) {
                         const int i = tid + nthr * t;
-                        xa[t] = i < rows ? ldcg(ap + i) : mk(0.0, 0.0);
-                        ya[t] = i < rows ? ldcg(aq + i) : mk(0.0, 0.0);
-                        xv[t] = i < cols ? ldcg(vp + i) : mk(0.0, 0.0);
-                        yv[t] = i < cols ? ldcg(vq + i) : mk(0.0, 0.0);
+                        const bool ua = (t == 0 || two) && i < rows, uv = (t == 0 || two) && i < cols;
+                        xa[t] = ua ? ldcg(ap + i) : mk(0.0, 0.0);
+                        ya[t] = ua ? ldcg(aq + i) : mk(0.0, 0.0);
+                        xv[t] = uv ? ldcg(vp + i) : mk(0.0, 0.0);
+                        yv[t] = uv ? ldcg(vq + i) : mk(0.0, 0.0);
                     }
-                    double al = norm2(xa[0]) + norm2(xa[1]), be = norm2(ya[0]) + norm2(ya[1]);
-                    zd ga = fmac(fmac(mk(0.0, 0.0), xa[0], ya[0]), xa[1], ya[1]);
+                    double al = norm2(xa[0]), be = norm2(ya[0]);
+                    zd ga = fmac(mk(0.0, 0.0), xa[0], ya[0]);
+                    if (two) {
+                        al += norm2(xa[1]);
+                        be += norm2(ya[1]);
+                        ga = fmac(ga, xa[1], ya[1]);
+                    }
                     for (int o = 16; o > 0; o >>= 1) {
                         al += __shfl_xor_sync(0xffffffffu, al, o);
                         be += __shfl_xor_sync(0xffffffffu, be, o);
@@ -234,6 +241,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __r
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         const int i = tid + nthr * u;
+                        if (u == 1 && !two) break;
                         if (i < rows) {
                             ap[i] = c * xa[u] - sec * ya[u];
                             aq[i] = se * xa[u] + c * ya[u];
@@ -827,6 +835,221 @@ int small_eig(int m, const zd* A, zd* eval, zd* evec, int* status, void* gbuf, c
 template int small_eig<float>(int, const zd*, zd*, zd*, int*, void*, cudaStream_t);
 template int small_eig<double>(int, const zd*, zd*, zd*, int*, void*, cudaStream_t);
 
+// ------------------------------------------------------------------ eigenvalues, then inverse iteration
+// Faster variant for the reduced Hankel matrix: (1) one warp reduces to Hessenberg form and
+// runs the shifted QR iteration updating only the active block (eigenvalues only, no Schur
+// vectors); (2) one warp per eigenvalue solves (A - theta I) v = v twice by Gaussian
+// elimination with partial pivoting (inverse iteration) for the eigenvector.
+template <typename T>
+__global__ void hqr_eigvals_kernel(int m, const zd* __restrict__ Ain, zd* __restrict__ eval, int* __restrict__ status,
+                                   cx<T>* gbuf, int use_smem) {
+    extern __shared__ unsigned char sraw[];
+    const int ld = m + 1;
+    cx<T>* H = use_smem ? reinterpret_cast<cx<T>*>(sraw) : gbuf;
+    cx<T>* v = H + (int64_t)m * ld;
+    const int lane = threadIdx.x;
+    const T eps = sizeof(T) == 4 ? T(6e-8) : T(1.2e-16);
+    auto h = [&](int i, int j) -> cx<T>& { return H[i + (int64_t)ld * j]; };
+    for (int t = lane; t < m * m; t += 32) h(t % m, t / m) = cvt<T>(Ain[t]);
+    __syncwarp();
+    for (int k = 0; k + 2 < m; ++k) {
+        T nx = 0;
+        for (int i = k + 1 + lane; i < m; i += 32) nx += norm2(h(i, k));
+        for (int o = 16; o > 0; o >>= 1) nx += __shfl_xor_sync(0xffffffffu, nx, o);
+        nx = sqrt(nx);
+        if (nx == T(0)) continue;
+        const cx<T> x0 = h(k + 1, k);
+        const T a0 = hypot(x0.re, x0.im);
+        const cx<T> ph = a0 > 0 ? mk<T>(x0.re / a0, x0.im / a0) : mk<T>(1, 0);
+        for (int i = k + 1 + lane; i < m; i += 32) v[i] = h(i, k);
+        __syncwarp();
+        if (lane == 0) v[k + 1] = v[k + 1] + nx * ph;
+        __syncwarp();
+        T vv = 0;
+        for (int i = k + 1 + lane; i < m; i += 32) vv += norm2(v[i]);
+        for (int o = 16; o > 0; o >>= 1) vv += __shfl_xor_sync(0xffffffffu, vv, o);
+        const T sc = T(2) / vv;
+        for (int j = k + lane; j < m; j += 32) {
+            cx<T> sm = mk<T>(0, 0);
+            for (int i = k + 1; i < m; ++i) sm = fmac(sm, v[i], h(i, j));
+            sm = sc * sm;
+            for (int i = k + 1; i < m; ++i) h(i, j) = fms(h(i, j), v[i], sm);
+        }
+        __syncwarp();
+        for (int i = lane; i < m; i += 32) {
+            cx<T> sm = mk<T>(0, 0);
+            for (int j = k + 1; j < m; ++j) sm = fma_(sm, h(i, j), v[j]);
+            sm = sc * sm;
+            for (int j = k + 1; j < m; ++j) h(i, j) = fms(h(i, j), sm, conj(v[j]));
+        }
+        __syncwarp();
+        for (int i = k + 2 + lane; i < m; i += 32) h(i, k) = mk<T>(0, 0);
+        __syncwarp();
+    }
+    int ihi = m - 1, iter = 0, since = 0, fail = 0;
+    const int maxit = 60 * m + 100;
+    while (ihi > 0) {
+        if (iter++ > maxit) { fail = 1; break; }
+        int l = ihi;
+        while (l > 0) {
+            const T ref = abs1(h(l, l)) + abs1(h(l - 1, l - 1));
+            if (abs1(h(l, l - 1)) <= eps * (ref > 0 ? ref : T(1))) break;
+            --l;
+        }
+        __syncwarp();
+        if (l > 0 && lane == 0) h(l, l - 1) = mk<T>(0, 0);
+        __syncwarp();
+        if (l == ihi) { --ihi; since = 0; continue; }
+        ++since;
+        const cx<T> a = h(ihi - 1, ihi - 1), b = h(ihi - 1, ihi), c2 = h(ihi, ihi - 1), d = h(ihi, ihi);
+        cx<T> mu;
+        if (since % 11 == 10) {
+            mu = d + mk<T>(T(0.75) * abs1(c2), T(0));
+        } else {
+            const cx<T> tr = a + d, det = a * d - b * c2;
+            const cx<T> disc = csqrt_(tr * tr - T(4) * det);
+            const cx<T> r1 = T(0.5) * (tr + disc), r2 = T(0.5) * (tr - disc);
+            mu = norm2(r1 - d) < norm2(r2 - d) ? r1 : r2;
+        }
+        cx<T> x = h(l, l) - mu, y = h(l + 1, l);
+        for (int k = l; k < ihi; ++k) {
+            T cs;
+            cx<T> sn;
+            givens(x, y, &cs, &sn);
+            // active block only: rows k, k+1 over columns max(l, k-1)..ihi; columns k, k+1 over rows l..min(k+2, ihi)
+            for (int j = max(l, k - 1) + lane; j <= ihi; j += 32) {
+                const cx<T> p = h(k, j), q = h(k + 1, j);
+                h(k, j) = cs * p + sn * q;
+                h(k + 1, j) = cs * q - conj(sn) * p;
+            }
+            __syncwarp();
+            const int rlim = min(k + 2, ihi);
+            for (int i = l + lane; i <= rlim; i += 32) {
+                const cx<T> p = h(i, k), q = h(i, k + 1);
+                h(i, k) = cs * p + conj(sn) * q;
+                h(i, k + 1) = cs * q - sn * p;
+            }
+            __syncwarp();
+            if (k + 1 < ihi) {
+                x = h(k + 1, k);
+                y = h(k + 2, k);
+            }
+        }
+    }
+    __syncwarp();
+    for (int i = lane; i < m; i += 32) eval[i] = cvt<double>(h(i, i));
+    if (lane == 0 && status) *status = fail;
+}
+
+template <typename T>
+__global__ void inverse_iteration_kernel(int m, const zd* __restrict__ Ain, const zd* __restrict__ eval,
+                                         zd* __restrict__ evec, cx<T>* gbuf, int use_smem) {
+    extern __shared__ unsigned char sraw[];
+    const int e = blockIdx.x;
+    const int ld = m + 1;
+    cx<T>* A = use_smem ? reinterpret_cast<cx<T>*>(sraw) : gbuf + (int64_t)e * ((int64_t)m * ld + 2 * m);
+    cx<T>* x = A + (int64_t)m * ld;
+    int* piv = reinterpret_cast<int*>(x + m);
+    const int lane = threadIdx.x;
+    const T eps = sizeof(T) == 4 ? T(6e-8) : T(1.2e-16);
+    const cx<T> th = cvt<T>(eval[e]);
+    T anorm = 0;
+    for (int t = lane; t < m * m; t += 32) {
+        const int i = t % m, j = t / m;
+        cx<T> a = cvt<T>(Ain[t]);
+        if (i == j) a = a - th;
+        A[i + (int64_t)ld * j] = a;
+        anorm = fmax(anorm, abs1(a));
+    }
+    for (int o = 16; o > 0; o >>= 1) anorm = fmax(anorm, __shfl_xor_sync(0xffffffffu, anorm, o));
+    const T tiny = eps * (anorm > 0 ? anorm : T(1));
+    __syncwarp();
+    // LU with partial pivoting (row interchanges recorded in piv)
+    for (int k = 0; k < m; ++k) {
+        T best = T(-1);
+        int bi = k;
+        for (int i = k + lane; i < m; i += 32) {
+            const T a = abs1(A[i + (int64_t)ld * k]);
+            if (a > best) { best = a; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) piv[k] = bi;
+        if (bi != k)
+            for (int j = lane; j < m; j += 32) {
+                const cx<T> t = A[k + (int64_t)ld * j];
+                A[k + (int64_t)ld * j] = A[bi + (int64_t)ld * j];
+                A[bi + (int64_t)ld * j] = t;
+            }
+        __syncwarp();
+        cx<T> pv = A[k + (int64_t)ld * k];
+        if (abs1(pv) < tiny) pv = mk<T>(tiny, 0);  // singular to working precision: perturb the pivot
+        const cx<T> rp = cdiv(mk<T>(1, 0), pv);
+        __syncwarp();
+        if (lane == 0) A[k + (int64_t)ld * k] = pv;
+        for (int i = k + 1 + lane; i < m; i += 32) A[i + (int64_t)ld * k] = A[i + (int64_t)ld * k] * rp;
+        __syncwarp();
+        for (int i = k + 1 + lane; i < m; i += 32) {
+            const cx<T> l = A[i + (int64_t)ld * k];
+            for (int j = k + 1; j < m; ++j) A[i + (int64_t)ld * j] = fms(A[i + (int64_t)ld * j], l, A[k + (int64_t)ld * j]);
+        }
+        __syncwarp();
+    }
+    for (int i = lane; i < m; i += 32) x[i] = mk<T>(T(1), T(0));
+    __syncwarp();
+    for (int it = 0; it < 2; ++it) {
+        for (int k = 0; k < m; ++k) {
+            const int p = piv[k];
+            if (p != k && lane == 0) { const cx<T> t = x[k]; x[k] = x[p]; x[p] = t; }
+            __syncwarp();
+            const cx<T> xk = x[k];
+            for (int i = k + 1 + lane; i < m; i += 32) x[i] = fms(x[i], A[i + (int64_t)ld * k], xk);
+            __syncwarp();
+        }
+        for (int k = m - 1; k >= 0; --k) {
+            const cx<T> xk = cdiv(x[k], A[k + (int64_t)ld * k]);
+            __syncwarp();
+            if (lane == 0) x[k] = xk;
+            for (int i = lane; i < k; i += 32) x[i] = fms(x[i], A[i + (int64_t)ld * k], xk);
+            __syncwarp();
+        }
+        T nrm = 0;
+        for (int i = lane; i < m; i += 32) nrm += norm2(x[i]);
+        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        const T inv = nrm > 0 ? T(1) / sqrt(nrm) : T(0);
+        __syncwarp();
+        for (int i = lane; i < m; i += 32) x[i] = inv * x[i];
+        __syncwarp();
+    }
+    for (int i = lane; i < m; i += 32) evec[i + (int64_t)m * e] = cvt<double>(x[i]);
+}
+
+// Eigenvalues (and eigenvectors by inverse iteration) of a small complex matrix, precision T.
+// gbuf: m * ((m+1)*m + 2m) elements of cx<T>, used when shared memory is too small.
+template <typename T>
+int small_eig_fast(int m, const zd* A, zd* eval, zd* evec, int* status, void* gbuf, cudaStream_t st) {
+    if (m <= 0) return NEP_OK;
+    const size_t b1 = sizeof(cx<T>) * ((size_t)m * (m + 1) + m);
+    const int s1 = b1 <= 200 * 1024;
+    if (s1) NEP_CUDA(cudaFuncSetAttribute(hqr_eigvals_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1));
+    else if (!gbuf) return NEP_ERR_INTERNAL;
+    hqr_eigvals_kernel<T><<<1, 32, s1 ? b1 : 0, st>>>(m, A, eval, status, (cx<T>*)gbuf, s1);
+    NEP_CHECK_LAUNCH();
+    if (!evec) return NEP_OK;
+    const size_t b2 = sizeof(cx<T>) * ((size_t)m * (m + 1) + m) + sizeof(int) * m + 16;
+    const int s2 = b2 <= 200 * 1024;
+    if (s2)
+        NEP_CUDA(cudaFuncSetAttribute(inverse_iteration_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2));
+    else if (!gbuf) return NEP_ERR_INTERNAL;
+    inverse_iteration_kernel<T><<<m, 32, s2 ? b2 : 0, st>>>(m, A, eval, evec, (cx<T>*)gbuf, s2);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+template int small_eig_fast<float>(int, const zd*, zd*, zd*, int*, void*, cudaStream_t);
+
 // ------------------------------------------------------------------ helpers
 // Scale column c of X (rows x cols) by 1/|x_c|_2 (optionally fixing the phase so the first
 // entry of largest modulus is real positive); nrm_out[c] = |x_c|_2 before scaling.
@@ -949,24 +1172,26 @@ __global__ void __launch_bounds__(256) newton_kernel(SplitDev s, int k, const zd
             fv[s.nterms + tid] = fe.df;
         }
         __syncthreads();
-        // J(0:k, 0:k) = B(l) (rounded); rhs = -B(l) y and J(0:k, k) = B'(l) y in FP64, rounded
-        for (int e = tid; e < k * k; e += blockDim.x) {
-            const int r = e % k, q = e / k;
-            zd b = mk(0.0, 0.0);
-            for (int i = 0; i < s.nterms; ++i) b = fma_(b, fv[i], Bs[(int64_t)i * k * k + e]);
-            J[r + (int64_t)K1 * q] = cvt<float>(b);
+        // J(0:k, 0:k) = B(l) assembled in FP32 (it only steers the correction); the residual
+        // rhs = -B(l) y and J(0:k, k) = B'(l) y come from v_i = B_i y in FP64
+        {
+            zf f32[32];
+            for (int i = 0; i < s.nterms; ++i) f32[i] = cvt<float>(fv[i]);
+            for (int e = tid; e < k * k; e += blockDim.x) {
+                const int r = e % k, q = e / k;
+                zf b = mk(0.0f, 0.0f);
+                for (int i = 0; i < s.nterms; ++i) b = fma_(b, f32[i], cvt<float>(Bs[(int64_t)i * k * k + e]));
+                J[r + (int64_t)K1 * q] = b;
+            }
         }
         for (int r = tid; r < k; r += blockDim.x) {
             zd bd = mk(0.0, 0.0), gd = mk(0.0, 0.0);
-            for (int q = 0; q < k; ++q) {
-                zd b = mk(0.0, 0.0), d = mk(0.0, 0.0);
-                for (int i = 0; i < s.nterms; ++i) {
-                    const zd bi = Bs[(int64_t)i * k * k + r + (int64_t)k * q];
-                    b = fma_(b, fv[i], bi);
-                    d = fma_(d, fv[s.nterms + i], bi);
-                }
-                bd = fma_(bd, b, y[q]);
-                gd = fma_(gd, d, y[q]);
+            for (int i = 0; i < s.nterms; ++i) {
+                const zd* Bi = Bs + (int64_t)i * k * k + r;
+                zd v = mk(0.0, 0.0);
+                for (int q = 0; q < k; ++q) v = fma_(v, Bi[(int64_t)k * q], y[q]);
+                bd = fma_(bd, fv[i], v);
+                gd = fma_(gd, fv[s.nterms + i], v);
             }
             rhs[r] = cvt<float>(-bd);
             J[r + (int64_t)K1 * k] = cvt<float>(gd);

@@ -533,7 +533,7 @@ static int plan_alloc(nep_plan* p) {
     NEP_TRY(dalloc(&p->part, p->part_elems, st));
     if (sizeof(zd) * newton_scratch_elems(LM) > 200 * 1024)
         NEP_TRY(dalloc(&p->newton_scratch, (size_t)LM * newton_scratch_elems(LM), st));
-    NEP_CUDA(cudaMallocAsync(&p->eig_scratch, sizeof(zf) * ((size_t)2 * LM * (LM + 1) + LM) + 256, st));
+    NEP_CUDA(cudaMallocAsync(&p->eig_scratch, sizeof(zf) * (size_t)LM * ((size_t)LM * (LM + 1) + 2 * LM) + 256, st));
     NEP_TRY(dalloc(&p->jw.Vm, lm2, st));
     NEP_TRY(dalloc(&p->jw.flags, 2, st));
     NEP_TRY(dalloc(&p->jw.sweeps, 1, st));
@@ -684,7 +684,7 @@ static int run_extract(nep_plan* p, cudaStream_t st) {
     NEP_TRY(zgemm(LM, m, LM, 0, p->Hs, LM, p->W, LM, p->T1, LM, p->part, p->part_elems, st));
     NEP_TRY(zgemm(m, m, LM, 1, p->U, LM, p->T1, LM, p->Bred, m, p->part, p->part_elems, st));
     NEP_TRY(launch_scale_cols(m, m, p->Bred, m, p->sigma, 0, st));
-    NEP_TRY(small_eig<float>(m, p->Bred, p->theta, p->Tv, p->eigstat, p->eig_scratch, st));
+    NEP_TRY(small_eig_fast<float>(m, p->Bred, p->theta, p->Tv, p->eigstat, p->eig_scratch, st));
     NEP_TRY(launch_candidates(m, p->theta, mk(p->reg.center_re, p->reg.center_im), p->reg.a, p->cand, st));
     // Hankel eigenvector estimates X_H = [S_0 .. S_{M-1}] W_m Sigma_m^{-1} T
     NEP_TRY(launch_scale_rows(m, m, p->Tv, m, p->sigma, st));

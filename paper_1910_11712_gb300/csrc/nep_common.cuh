@@ -236,6 +236,8 @@ int qrcp_jacobi_svd(int n, zd* A, zd* U, zd* W, double* sigma, zd* work1, zd* wo
                     double* nrm2, JacobiWork w, cudaStream_t st);
 template <typename T>
 int small_eig(int m, const zd* A, zd* eval, zd* evec, int* status, void* gbuf, cudaStream_t st);
+template <typename T>
+int small_eig_fast(int m, const zd* A, zd* eval, zd* evec, int* status, void* gbuf, cudaStream_t st);
 // complex128-sized elements of one Newton candidate's work area (FP32 Jacobian + FP64 iterate)
 __host__ __device__ inline size_t newton_scratch_elems(int k) {
     const size_t K1 = (size_t)k + 1;

@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __r
     const int gwarp = nsub > 1 ? (int)blockIdx.x : (int)(blockIdx.x * nsub + (threadIdx.x >> 5));
     const int nwarps = nsub > 1 ? (int)gridDim.x : (int)(gridDim.x * nsub);
     __shared__ double red4[8][4];
+    __shared__ double rot4[4];
     const int P = cols + (cols & 1);
     // V = I
     unsigned int epoch = 0;
@@ -223,21 +224,39 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __r
                         red4[w][3] = ga.im;
                     }
                     __syncthreads();
-                    al = be = 0.0;
-                    ga = mk(0.0, 0.0);
-                    for (int q = 0; q < nsub; ++q) {
-                        al += red4[q][0];
-                        be += red4[q][1];
-                        ga.re += red4[q][2];
-                        ga.im += red4[q][3];
+                    // the rotation's scalars once per CTA: FP64 issue slots are scarce, so the
+                    // square roots and divisions are not repeated by every thread
+                    if (tid == 0) {
+                        al = be = 0.0;
+                        ga = mk(0.0, 0.0);
+                        for (int q = 0; q < nsub; ++q) {
+                            al += red4[q][0];
+                            be += red4[q][1];
+                            ga.re += red4[q][2];
+                            ga.im += red4[q][3];
+                        }
+                        const double g = hypot(ga.re, ga.im);
+                        double cc = 1.0, sr = 0.0, si = 0.0, doit = 0.0;
+                        if (g > tol * sqrt(al * be) && al != 0.0 && be != 0.0) {
+                            const double zeta = (be - al) / (2.0 * g);
+                            const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                            cc = 1.0 / sqrt(1.0 + t * t);
+                            const double sn = cc * t / g;
+                            sr = sn * ga.re;
+                            si = sn * ga.im;
+                            doit = 1.0;
+                        }
+                        rot4[0] = cc;
+                        rot4[1] = sr;
+                        rot4[2] = si;
+                        rot4[3] = doit;
                     }
                     __syncthreads();
-                    const double g = hypot(ga.re, ga.im);
-                    if (!(g > tol * sqrt(al * be)) || al == 0.0 || be == 0.0) continue;
-                    const double zeta = (be - al) / (2.0 * g);
-                    const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                    const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
-                    const zd se = mk(sn * ga.re / g, sn * ga.im / g), sec = conj(se);
+                    const double c = rot4[0];
+                    const zd se = mk(rot4[1], rot4[2]), sec = conj(se);
+                    const bool doit = rot4[3] != 0.0;
+                    __syncthreads();
+                    if (!doit) continue;
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         const int i = tid + nthr * u;

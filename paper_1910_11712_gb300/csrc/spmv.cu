@@ -54,18 +54,18 @@ __global__ void __launch_bounds__(256) split_residual_kernel(const int64_t* __re
         zd acc = v;
         for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) acc = fms(acc, tv[e], y[col[e]]);
         R[(int64_t)jl * n + r] = acc;
-        mr = hypot(acc.re, acc.im);
-        const zd yr = y[r];
-        my = hypot(yr.re, yr.im);
-        mv = hypot(v.re, v.im);
+        // squared moduli: the maxima are taken first and rooted once (FP64 issue is scarce)
+        mr = norm2(acc);
+        my = norm2(y[r]);
+        mv = norm2(v);
     }
     if (!nrm) return;
     mr = block_max(mr, red);
-    if (threadIdx.x == 0) atomic_max_nonneg_d(nrm + (int64_t)jl * 3 + 0, mr);
+    if (threadIdx.x == 0) atomic_max_nonneg_d(nrm + (int64_t)jl * 3 + 0, sqrt(mr));
     my = block_max(my, red);
-    if (threadIdx.x == 0) atomic_max_nonneg_d(nrm + (int64_t)jl * 3 + 1, my);
+    if (threadIdx.x == 0) atomic_max_nonneg_d(nrm + (int64_t)jl * 3 + 1, sqrt(my));
     mv = block_max(mv, red);
-    if (threadIdx.x == 0) atomic_max_nonneg_d(nrm + (int64_t)jl * 3 + 2, mv);
+    if (threadIdx.x == 0) atomic_max_nonneg_d(nrm + (int64_t)jl * 3 + 2, sqrt(mv));
 }
 
 int launch_split_residual(const SplitDev& s, int npts, const zd* tval, int L, const zd* V, const zd* Y, zd* R,
@@ -118,13 +118,13 @@ __global__ void __launch_bounds__(256) update_kernel(int64_t per_point, const cx
         const zd d = cvt<double>(D[g]);
         const zd y = Y[g] + d;
         Y[g] = y;
-        md = hypot(d.re, d.im);
-        my = hypot(y.re, y.im);
+        md = norm2(d);
+        my = norm2(y);
     }
     md = block_max(md, red);
-    if (threadIdx.x == 0) atomic_max_nonneg_d(dmax + j, md);
+    if (threadIdx.x == 0) atomic_max_nonneg_d(dmax + j, sqrt(md));
     my = block_max(my, red);
-    if (threadIdx.x == 0) atomic_max_nonneg_d(ymax + j, my);
+    if (threadIdx.x == 0) atomic_max_nonneg_d(ymax + j, sqrt(my));
 }
 
 // One thread per point: backward error of the residual just measured, stop rule, counters.

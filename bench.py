@@ -134,6 +134,59 @@ def cpu_baseline(p, steps_budget_s=20.0):
                       f"threads over quadrature points, {sum(times):.1f} s total"}
 
 
+def serving_bench(binding, prec, count, seed, workers, span_s, s_max, fp64_subset):
+    """Poisson request stream replayed in real time against the continuous-batching server.
+
+    A bounded sample (count requests, arrival times rescaled to span about span_s seconds) of
+    the delay/Drude request mix on s x s grids with n log-uniform in [16^2, s_max^2].
+    Latency = submit to result ready (queue + service); throughput = quadrature solves of all
+    requests / makespan. Baseline: plain FP64 solves one at a time on the first fp64_subset
+    requests.
+    """
+    import synth
+    reqs = synth.serving_requests(count=count, seed=seed, rate_hz=count / span_s, s_max=s_max)
+    probs = [synth.serving_problem(r) for r in reqs]
+    splits = [binding.Split.from_problem(p) for p in probs]
+    Vs = [synth.random_probe_block(p.n, p.L, r["seed"] % 1000) for p, r in zip(probs, reqs)]
+    srv = binding.Server(workers=workers)
+    srv.wait(srv.submit(splits[0], probs[0].region, probs[0].N, probs[0].L, probs[0].M, V=Vs[0], precision=prec))
+    t0 = time.perf_counter()
+    tickets = []
+    for p, r, sp, V in zip(probs, reqs, splits, Vs):
+        delay = r["arrival"] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit(sp, p.region, p.N, p.L, p.M, V=V, precision=prec))
+    results = [srv.wait(t) for t in tickets]
+    t1 = time.perf_counter()
+    srv.close()
+    lat = np.array([res["info"]["ms_latency"] for res in results])
+    solves = sum(p.N for p in probs)
+    out = {"requests": count, "workers": workers, "offered_rate_hz": count / span_s,
+           "n_range": [min(p.n for p in probs), max(p.n for p in probs)],
+           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "solves_per_s": solves / (t1 - t0), "makespan_s": t1 - t0,
+           "sample": f"first {count} requests of the seeded 2000-request stream (seed {seed}), "
+                     f"arrivals rescaled to {span_s:.0f} s"}
+    if fp64_subset:
+        tt, ns = 0.0, 0
+        for p, sp, V in list(zip(probs, splits, Vs))[:fp64_subset]:
+            torch_sync()
+            a = time.perf_counter()
+            binding.ciss_solve(sp, p.region, p.N, p.L, p.M, V=V, precision=binding.NEP_PREC_FP64)
+            torch_sync()
+            tt += time.perf_counter() - a
+            ns += p.N
+        out["fp64_one_at_a_time"] = {"requests": fp64_subset, "solves_per_s": ns / tt,
+                                     "mean_service_ms": 1e3 * tt / fp64_subset}
+    return out
+
+
+def torch_sync():
+    import torch
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -144,6 +197,9 @@ def main():
     ap.add_argument("--workload", default="delay2d_s64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=48)
+    ap.add_argument("--serving-smax", type=int, default=128)
     args = ap.parse_args()
     rank, world, local = dist_env()
     import synth
@@ -275,6 +331,8 @@ def main():
         }
         if e2e:
             line["e2e"] = e2e
+        if not args.no_serving:
+            line["serving"] = serving_bench(binding, prec, args.serving_requests, 0, 4, 10.0, args.serving_smax, 8)
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(p)
         print(json.dumps(line), flush=True)

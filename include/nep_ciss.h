@@ -150,6 +150,8 @@ typedef struct {
     int32_t flags;
     double max_backward;    /* max over points of the last measured backward error */
     double ms_assemble, ms_factor, ms_solve, ms_moments, ms_extract, ms_total;
+    double ms_queued;       /* server requests: submit to start of execution (0 otherwise) */
+    double ms_latency;      /* server requests: submit to result ready (0 otherwise) */
 } nep_result_info_t;
 int nep_result_info(nep_result_t r, nep_result_info_t *info);
 /* Singular values of the Hankel matrix (L*M of them, descending). */
@@ -173,6 +175,32 @@ int nep_plan_destroy(nep_plan_t p);
 /* Device buffers of a plan (for inspection/tests): name in {"F","coef","ab","ipiv","info",
  * "Y","S","mu","sigma","tnorm","beta","sweeps"}; returns the device pointer and its bytes. */
 int nep_plan_buffer(nep_plan_t p, const char *name, void **dev_ptr, size_t *bytes);
+
+/* ------------------------------------------------------------------ serving */
+/* Continuous-batching request server. Requests are admitted in arrival order as soon as a
+ * worker is free and their device footprint (nep_plan_bytes) fits the remaining budget;
+ * every worker drives its own CUDA stream, so the kernels of admitted requests overlap on
+ * the device. Each request runs exactly the computation of nep_ciss_solve on its inputs
+ * (same kernels, same launch shapes, no state shared between requests), so its result does
+ * not depend on what else is in flight. The split handle passed to nep_submit must stay
+ * alive until the request's result has been taken. */
+typedef struct nep_server *nep_server_t;
+#define NEP_PENDING 1 /* nep_poll: the request has not finished yet */
+/* workers >= 1 concurrent requests; hbm_budget_bytes == 0: 80% of the free device memory. */
+int nep_server_create(int32_t workers, uint64_t hbm_budget_bytes, nep_server_t *out);
+/* Copies the region, options and V (n x L complex, or NULL: drawn from opts->seed) and
+ * enqueues the request; *ticket identifies it. NEP_ERR_NOMEM if it can never fit the budget. */
+int nep_submit(nep_server_t s, nep_split_t h, const nep_region *r, int32_t N, int32_t L, int32_t M, const nep_opts *o,
+               const double *V_host, uint64_t *ticket);
+/* NEP_OK and *out (to be freed with nep_result_free) once done, NEP_PENDING before, or the
+ * request's error code. A ticket's result can be taken once. */
+int nep_poll(nep_server_t s, uint64_t ticket, nep_result_t *out);
+/* Blocks until the request is done; same returns as nep_poll without NEP_PENDING. */
+int nep_server_wait(nep_server_t s, uint64_t ticket, nep_result_t *out);
+/* Waits for all admitted and queued requests, then stops the workers. */
+int nep_server_destroy(nep_server_t s);
+/* Device bytes one solve of this shape allocates (what admission charges against the budget). */
+uint64_t nep_plan_bytes(nep_split_t h, int32_t N, int32_t L, int32_t M, int32_t precision);
 
 /* ------------------------------------------------------------------ step entry points */
 /* Trapezoid nodes on Gamma (host): theta_j = 2 pi (j + 1/2)/N, z_j, weights

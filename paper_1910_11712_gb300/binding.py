@@ -17,6 +17,7 @@ c_int32, c_int64, c_double, c_void_p, c_size_t = ctypes.c_int32, ctypes.c_int64,
 P_double = ctypes.POINTER(c_double)
 
 NEP_OK = 0
+NEP_PENDING = 1
 NEP_ERR_ARG, NEP_ERR_CUDA, NEP_ERR_REGION, NEP_ERR_NOMEM, NEP_ERR_UNSUPPORTED, NEP_ERR_INTERNAL = -1, -2, -3, -4, -5, -6
 NEP_WARN_SATURATED, NEP_WARN_REFINE, NEP_WARN_SINGULAR_NODE, NEP_WARN_NEWTON = 1, 2, 4, 8
 NEP_PREC_FP64, NEP_PREC_MIXED = 0, 1
@@ -54,7 +55,8 @@ class NepResultInfo(ctypes.Structure):
                 ("hankel_rank", c_int32), ("basis_rank", c_int32), ("ncandidates", c_int32),
                 ("max_sweeps", c_int32), ("svd_sweeps", c_int32), ("flags", c_int32), ("max_backward", c_double),
                 ("ms_assemble", c_double), ("ms_factor", c_double), ("ms_solve", c_double),
-                ("ms_moments", c_double), ("ms_extract", c_double), ("ms_total", c_double)]
+                ("ms_moments", c_double), ("ms_extract", c_double), ("ms_total", c_double),
+                ("ms_queued", c_double), ("ms_latency", c_double)]
 
 
 # name -> (restype, argtypes)
@@ -72,6 +74,13 @@ SIGNATURES = {
     "nep_result_free": (c_int32, [c_void_p]),
     "nep_last_error": (ctypes.c_char_p, []),
     "nep_kernel_launches": (ctypes.c_uint64, []),
+    "nep_server_create": (c_int32, [c_int32, ctypes.c_uint64, ctypes.POINTER(c_void_p)]),
+    "nep_submit": (c_int32, [c_void_p, c_void_p, ctypes.POINTER(NepRegion), c_int32, c_int32, c_int32,
+                             ctypes.POINTER(NepOpts), c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "nep_poll": (c_int32, [c_void_p, ctypes.c_uint64, ctypes.POINTER(c_void_p)]),
+    "nep_server_wait": (c_int32, [c_void_p, ctypes.c_uint64, ctypes.POINTER(c_void_p)]),
+    "nep_server_destroy": (c_int32, [c_void_p]),
+    "nep_plan_bytes": (ctypes.c_uint64, [c_void_p, c_int32, c_int32, c_int32, c_int32]),
     "nep_plan_create": (c_int32, [c_void_p, ctypes.POINTER(NepRegion), c_int32, c_int32, c_int32, ctypes.POINTER(NepOpts),
                                   ctypes.POINTER(c_void_p)]),
     "nep_plan_execute": (c_int32, [c_void_p, c_void_p, c_void_p]),
@@ -315,6 +324,56 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching request server (nep_server_*): submit, poll or wait."""
+
+    def __init__(self, workers: int = 4, hbm_budget_bytes: int = 0):
+        h = c_void_p()
+        check(load().nep_server_create(workers, hbm_budget_bytes, ctypes.byref(h)))
+        self.handle = h
+
+    def submit(self, split: Split, region, N, L, M, V=None, **opts) -> int:
+        r = region_struct(region)
+        o = opts_struct(**opts)
+        vptr = None
+        if V is not None:
+            self._keep = getattr(self, "_keep", [])
+            Vf = np.asfortranarray(V, dtype=np.complex128)
+            vptr = Vf.ctypes.data
+        t = ctypes.c_uint64()
+        check(load().nep_submit(self.handle, split.handle, ctypes.byref(r), N, L, M, ctypes.byref(o), vptr,
+                                ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int):
+        res = c_void_p()
+        rc = load().nep_poll(self.handle, ticket, ctypes.byref(res))
+        if rc == NEP_PENDING:
+            return None
+        check(rc)
+        return _result_dict(res)
+
+    def wait(self, ticket: int) -> dict:
+        res = c_void_p()
+        check(load().nep_server_wait(self.handle, ticket, ctypes.byref(res)))
+        return _result_dict(res)
+
+    def close(self):
+        if self.handle:
+            load().nep_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_bytes(split: Split, N, L, M, precision=NEP_PREC_MIXED) -> int:
+    return int(load().nep_plan_bytes(split.handle, N, L, M, precision))
 
 
 # ------------------------------------------------------------------ step entry points

@@ -33,11 +33,29 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
     return e == cudaErrorMemoryAllocation ? NEP_ERR_NOMEM : NEP_ERR_CUDA;
 }
 
+// When g_dry is set, allocations are only counted (plan footprint estimates for admission).
+static thread_local bool g_dry = false;
+static thread_local size_t g_dry_bytes = 0;
+
 template <typename T>
 static int dalloc(T** p, size_t count, cudaStream_t st) {
     *p = nullptr;
     if (count == 0) count = 1;
+    const size_t bytes = (sizeof(T) * count + 255) / 256 * 256;
+    if (g_dry) {
+        g_dry_bytes += bytes;
+        return NEP_OK;
+    }
     NEP_CUDA(cudaMallocAsync((void**)p, sizeof(T) * count, st));
+    return NEP_OK;
+}
+static int dalloc_raw(void** p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    if (g_dry) {
+        g_dry_bytes += (bytes + 255) / 256 * 256;
+        return NEP_OK;
+    }
+    NEP_CUDA(cudaMallocAsync(p, bytes, st));
     return NEP_OK;
 }
 
@@ -477,7 +495,7 @@ static int plan_alloc(nep_plan* p) {
     const size_t esz = p->mixed ? sizeof(zf) : sizeof(zd);
     NEP_TRY(dalloc(&p->F, (size_t)nt * N, st));
     NEP_TRY(dalloc(&p->coef, (size_t)N * K, st));
-    NEP_CUDA(cudaMallocAsync(&p->ab, esz * (size_t)N * n * h->ldab, st));
+    NEP_TRY(dalloc_raw(&p->ab, esz * (size_t)N * n * h->ldab, st));
     NEP_TRY(dalloc(&p->ipiv, (size_t)N * n, st));
     NEP_TRY(dalloc(&p->info, N, st));
     NEP_TRY(dalloc(&p->tnorm, N, st));
@@ -485,7 +503,7 @@ static int plan_alloc(nep_plan* p) {
     NEP_TRY(dalloc(&p->V, (size_t)n * L, st));
     NEP_TRY(dalloc(&p->Y, (size_t)N * n * L, st));
     NEP_TRY(dalloc(&p->R, (size_t)N * n * L, st));
-    NEP_CUDA(cudaMallocAsync(&p->D, esz * (size_t)N * n * L, st));
+    NEP_TRY(dalloc_raw(&p->D, esz * (size_t)N * n * L, st));
     NEP_TRY(dalloc(&p->nrm, (size_t)N * L * 3, st));
     NEP_TRY(dalloc(&p->dmax, N, st));
     NEP_TRY(dalloc(&p->ymax, N, st));
@@ -533,12 +551,13 @@ static int plan_alloc(nep_plan* p) {
     NEP_TRY(dalloc(&p->part, p->part_elems, st));
     if (sizeof(zd) * newton_scratch_elems(LM) > 200 * 1024)
         NEP_TRY(dalloc(&p->newton_scratch, (size_t)LM * newton_scratch_elems(LM), st));
-    NEP_CUDA(cudaMallocAsync(&p->eig_scratch, sizeof(zf) * (size_t)LM * ((size_t)LM * (LM + 1) + 2 * LM) + 256, st));
+    NEP_TRY(dalloc_raw(&p->eig_scratch, sizeof(zf) * (size_t)LM * ((size_t)LM * (LM + 1) + 2 * LM) + 256, st));
     NEP_TRY(dalloc(&p->jw.Vm, lm2, st));
     NEP_TRY(dalloc(&p->jw.flags, 2, st));
     NEP_TRY(dalloc(&p->jw.sweeps, 1, st));
     NEP_TRY(dalloc(&p->jw.bar, 2, st));
     NEP_TRY(dalloc(&p->jw.err, 1, st));
+    if (g_dry) return NEP_OK;
     NEP_CUDA(cudaMemsetAsync(p->jw.err, 0, sizeof(int), st));
     NEP_CUDA(cudaHostAlloc((void**)&p->h_pinned, 64 * sizeof(int), cudaHostAllocDefault));
     for (auto& e : p->ev) NEP_CUDA(cudaEventCreate(&e));
@@ -561,13 +580,40 @@ static void plan_free(nep_plan* p) {
         if (e) cudaEventDestroy(e);
 }
 
+namespace nep {
+// Device bytes a plan for (h, N, L, M, precision) allocates (the same list as plan_alloc).
+size_t plan_footprint(nep_split_t h, int N, int L, int M, int precision) {
+    nep_plan p;
+    p.h = h;
+    p.N = N;
+    p.L = L;
+    p.M = M;
+    p.K = 2 * M;
+    p.LM = L * M;
+    p.mixed = precision == NEP_PREC_MIXED;
+    g_dry = true;
+    g_dry_bytes = 0;
+    plan_alloc(&p);
+    g_dry = false;
+    return g_dry_bytes;
+}
+int plan_create_internal(nep_split_t h, const nep_region* r, int32_t N, int32_t L, int32_t M, const nep_opts* o,
+                         cudaStream_t alloc_stream, nep_plan_t* out);
+}  // namespace nep
+
 extern "C" int nep_plan_create(nep_split_t h, const nep_region* r, int32_t N, int32_t L, int32_t M, const nep_opts* o,
                                nep_plan_t* out) {
+    return plan_create_internal(h, r, N, L, M, o, 0, out);
+}
+
+int nep::plan_create_internal(nep_split_t h, const nep_region* r, int32_t N, int32_t L, int32_t M, const nep_opts* o,
+                              cudaStream_t alloc_stream, nep_plan_t* out) {
     if (!out) { set_error("out is NULL"); return NEP_ERR_ARG; }
     *out = nullptr;
     NEP_TRY(check_args(h, r, N, L, M));
     configure_pool_once();
     nep_plan* p = new nep_plan();
+    p->alloc_stream = alloc_stream;
     p->h = h;
     p->reg = *r;
     if (o) p->o = *o;
@@ -842,6 +888,14 @@ extern "C" int nep_plan_result(nep_plan_t p, nep_result_t* out) {
     *out = r;
     return NEP_OK;
 }
+
+namespace nep {
+void result_set_times(nep_result_t r, double queued_ms, double latency_ms) {
+    if (!r) return;
+    r->info.ms_queued = queued_ms;
+    r->info.ms_latency = latency_ms;
+}
+}  // namespace nep
 
 extern "C" int nep_ciss_solve(nep_split_t h, const nep_region* r, int32_t N, int32_t L, int32_t M, const nep_opts* o,
                               const double* V_host, nep_result_t* out) {

@@ -1,0 +1,84 @@
+"""Continuous-batching server: results are the same alone and in a concurrent mix; admission
+respects the device-memory budget; latencies are reported."""
+import numpy as np
+import pytest
+
+import synth
+from tests.gpu_util import torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bnd():
+    from paper_1910_11712_gb300 import binding
+    binding.load(build_if_missing=True)
+    return binding
+
+
+def _requests():
+    reqs = synth.serving_requests(count=10, seed=3, s_min=12, s_max=40)
+    out = []
+    for r in reqs:
+        p = synth.serving_problem(r)
+        V = synth.random_probe_block(p.n, p.L, r["seed"] % 1000)
+        out.append((p, V))
+    return out
+
+
+def test_results_identical_alone_and_in_mix(bnd):
+    torch_cuda()
+    reqs = _requests()
+    splits = [bnd.Split.from_problem(p) for p, _ in reqs]
+    alone = [bnd.ciss_solve(sp, p.region, p.N, p.L, p.M, V=V, precision=1) for sp, (p, V) in zip(splits, reqs)]
+    srv = bnd.Server(workers=4)
+    tickets = [srv.submit(sp, p.region, p.N, p.L, p.M, V=V, precision=1) for sp, (p, V) in zip(splits, reqs)]
+    mixed = [srv.wait(t) for t in tickets]
+    srv.close()
+    for a, b in zip(alone, mixed):
+        assert a["m"] == b["m"]
+        assert np.array_equal(a["lam"], b["lam"])  # bitwise: no state is shared between requests
+        assert np.array_equal(a["eta"], b["eta"])
+        assert np.array_equal(a["X"], b["X"])
+        assert b["info"]["ms_latency"] >= b["info"]["ms_queued"] >= 0.0
+        assert b["info"]["ms_latency"] > 0.0
+
+
+def test_admission_respects_budget(bnd):
+    torch_cuda()
+    p, V = _requests()[0]
+    sp = bnd.Split.from_problem(p)
+    need = bnd.plan_bytes(sp, p.N, p.L, p.M)
+    assert need > 0
+    small = bnd.Server(workers=2, hbm_budget_bytes=need // 2)
+    with pytest.raises(bnd.NepError) as e:
+        small.submit(sp, p.region, p.N, p.L, p.M, V=V)
+    assert e.value.code == bnd.NEP_ERR_NOMEM
+    small.close()
+    # room for exactly one request at a time: both still complete, one after the other
+    one = bnd.Server(workers=2, hbm_budget_bytes=int(need * 1.5))
+    t1 = one.submit(sp, p.region, p.N, p.L, p.M, V=V, precision=1)
+    t2 = one.submit(sp, p.region, p.N, p.L, p.M, V=V, precision=1)
+    r1, r2 = one.wait(t1), one.wait(t2)
+    one.close()
+    assert np.array_equal(r1["lam"], r2["lam"])
+    assert r2["info"]["ms_queued"] >= r1["info"]["ms_latency"] * 0.5
+
+
+def test_poll_pending_then_done(bnd):
+    torch_cuda()
+    p, V = _requests()[1]
+    sp = bnd.Split.from_problem(p)
+    srv = bnd.Server(workers=1)
+    t = srv.submit(sp, p.region, p.N, p.L, p.M, V=V)
+    res = None
+    import time
+    for _ in range(2000):
+        res = srv.poll(t)
+        if res is not None:
+            break
+        time.sleep(0.005)
+    assert res is not None and res["m"] >= 1
+    with pytest.raises(bnd.NepError):
+        srv.poll(t)  # a ticket's result can be taken once
+    srv.close()

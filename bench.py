@@ -105,6 +105,21 @@ def lu_flops(n, kl, ku, npts):
     return 8.0 * n * kl * (kl + ku) * npts
 
 
+def solve_flops(n, kl, ku, L, npts):
+    """Forward (kl) plus backward (kl+ku) complex FMAs per row and right-hand side, 8 flops each."""
+    return 8.0 * n * (2 * kl + ku) * L * npts
+
+
+def solve_bytes(n, ldab, L, npts, esz):
+    """Factor band and pivots read once, right-hand sides read and written once."""
+    return npts * (n * ldab * esz + 4 * n + 2 * n * L * esz)
+
+
+# DRAM bytes (read + write) of one solve launch from an ncu capture of the same launch,
+# keyed by (workload, precision); None where no capture of the current kernel exists.
+SOLVE_TRAFFIC = {}
+
+
 def fp32_alu_peak_tflops(sm_mhz):
     """152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -134,51 +149,83 @@ def cpu_baseline(p, steps_budget_s=20.0):
                       f"threads over quadrature points, {sum(times):.1f} s total"}
 
 
-def serving_bench(binding, prec, count, seed, workers, span_s, s_max, fp64_subset):
-    """Poisson request stream replayed in real time against the continuous-batching server.
+def serving_bench(binding, prec, count, seed, workers, s_max, loads=(0.5, 0.8, 1.2)):
+    """Continuous-batching serving on a bounded sample of the Poisson request stream.
 
-    A bounded sample (count requests, arrival times rescaled to span about span_s seconds) of
-    the delay/Drude request mix on s x s grids with n log-uniform in [16^2, s_max^2].
-    Latency = submit to result ready (queue + service); throughput = quadrature solves of all
-    requests / makespan. Baseline: plain FP64 solves one at a time on the first fp64_subset
-    requests.
+    Requests: the first `count` of the seeded delay/Drude stream (s x s grids, n log-uniform up to
+    s_max^2, N in {32,64,128}, L in {8,16,32}, M = 8). Capacity is the request rate of the whole
+    sample submitted at once; the stream is then replayed in real time at offered loads rho x
+    capacity (Poisson inter-arrival gaps rescaled). Latency = submission to result ready.
+    Baseline: plain FP64, one request at a time, every request's service time measured alone; its
+    latencies at each offered load come from a first-in-first-out replay of the same arrival
+    times with those service times.
     """
     import synth
-    reqs = synth.serving_requests(count=count, seed=seed, rate_hz=count / span_s, s_max=s_max)
+    reqs = synth.serving_requests(count=count, seed=seed, s_max=s_max)
     probs = [synth.serving_problem(r) for r in reqs]
     splits = [binding.Split.from_problem(p) for p in probs]
     Vs = [synth.random_probe_block(p.n, p.L, r["seed"] % 1000) for p, r in zip(probs, reqs)]
-    srv = binding.Server(workers=workers)
-    srv.wait(srv.submit(splits[0], probs[0].region, probs[0].N, probs[0].L, probs[0].M, V=Vs[0], precision=prec))
-    t0 = time.perf_counter()
-    tickets = []
-    for p, r, sp, V in zip(probs, reqs, splits, Vs):
-        delay = r["arrival"] - (time.perf_counter() - t0)
-        if delay > 0:
-            time.sleep(delay)
-        tickets.append(srv.submit(sp, p.region, p.N, p.L, p.M, V=V, precision=prec))
-    results = [srv.wait(t) for t in tickets]
-    t1 = time.perf_counter()
-    srv.close()
-    lat = np.array([res["info"]["ms_latency"] for res in results])
     solves = sum(p.N for p in probs)
-    out = {"requests": count, "workers": workers, "offered_rate_hz": count / span_s,
-           "n_range": [min(p.n for p in probs), max(p.n for p in probs)],
-           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-           "solves_per_s": solves / (t1 - t0), "makespan_s": t1 - t0,
-           "sample": f"first {count} requests of the seeded 2000-request stream (seed {seed}), "
-                     f"arrivals rescaled to {span_s:.0f} s"}
-    if fp64_subset:
-        tt, ns = 0.0, 0
-        for p, sp, V in list(zip(probs, splits, Vs))[:fp64_subset]:
-            torch_sync()
-            a = time.perf_counter()
-            binding.ciss_solve(sp, p.region, p.N, p.L, p.M, V=V, precision=binding.NEP_PREC_FP64)
-            torch_sync()
-            tt += time.perf_counter() - a
-            ns += p.N
-        out["fp64_one_at_a_time"] = {"requests": fp64_subset, "solves_per_s": ns / tt,
-                                     "mean_service_ms": 1e3 * tt / fp64_subset}
+    gaps = np.diff([0.0] + [r["arrival"] for r in reqs])
+    gaps = gaps / gaps.mean()
+
+    def submit(srv, i):
+        p = probs[i]
+        return srv.submit(splits[i], p.region, p.N, p.L, p.M, V=Vs[i], precision=prec)
+
+    srv = binding.Server(workers=workers)
+    for i in range(min(4, count)):  # warm the allocator pool and the library
+        srv.wait(submit(srv, i))
+    t0 = time.perf_counter()
+    tickets = [submit(srv, i) for i in range(count)]
+    for t in tickets:
+        srv.wait(t)
+    capacity = count / (time.perf_counter() - t0)
+
+    def replay(rate):
+        arrivals = np.cumsum(gaps) / rate
+        t0 = time.perf_counter()
+        tk = []
+        for i in range(count):
+            d = arrivals[i] - (time.perf_counter() - t0)
+            if d > 0:
+                time.sleep(d)
+            tk.append(submit(srv, i))
+        lat = np.array([srv.wait(t)["info"]["ms_latency"] for t in tk])
+        return arrivals, lat, time.perf_counter() - t0
+
+    out = {"requests": count, "workers": workers, "n_range": [min(p.n for p in probs), max(p.n for p in probs)],
+           "capacity_req_per_s": capacity, "capacity_solves_per_s": capacity * solves / count, "loads": []}
+    for rho in loads:
+        arrivals, lat, span = replay(rho * capacity)
+        out["loads"].append({"rho": rho, "offered_req_per_s": rho * capacity,
+                             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                             "solves_per_s": solves / span})
+    srv.close()
+    # plain FP64, one request at a time
+    service = []
+    for i, p in enumerate(probs):
+        torch_sync()
+        a = time.perf_counter()
+        binding.ciss_solve(splits[i], p.region, p.N, p.L, p.M, V=Vs[i], precision=binding.NEP_PREC_FP64)
+        torch_sync()
+        service.append(time.perf_counter() - a)
+    service = np.array(service)
+    base = {"solves_per_s": solves / service.sum(), "mean_service_ms": 1e3 * service.mean(), "loads": []}
+    for rho in loads:
+        arrivals = np.cumsum(gaps) / (rho * capacity)
+        free_at, lat = 0.0, []
+        for t_arr, sv in zip(arrivals, service):
+            start = max(t_arr, free_at)
+            free_at = start + sv
+            lat.append(1e3 * (free_at - t_arr))
+        base["loads"].append({"rho": rho, "p50_ms": float(np.percentile(lat, 50)),
+                              "p99_ms": float(np.percentile(lat, 99))})
+    out["fp64_one_at_a_time"] = base
+    out["sample"] = (f"first {count} requests of the seeded Poisson request stream (seed {seed}); "
+                     "loads relative to the measured mixed-precision capacity")
+    for sp in splits:
+        sp.close()
     return out
 
 
@@ -198,7 +245,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=48)
+    ap.add_argument("--serving-requests", type=int, default=40)
     ap.add_argument("--serving-smax", type=int, default=128)
     args = ap.parse_args()
     rank, world, local = dist_env()
@@ -274,6 +321,25 @@ def main():
         lu_ms.append(r["info"]["ms_factor"])
         for k in stage:
             stage[k] += r["info"][k] / 3
+    # dominant kernel of the step (largest share of the launch list): the banded triangular
+    # solve, all N points x L right-hand sides in one launch, through the library's step entry
+    # point on the plan's factors; CUDA events on the launching stream, one fresh right-hand
+    # side block per launch (each larger than L2 together with the factors it streams)
+    ab_ptr, _ = plan.buffer("ab")
+    ipiv_ptr, _ = plan.buffer("ipiv")
+    cdt = torch.complex64 if prec == binding.NEP_PREC_MIXED else torch.complex128
+    reps = 5
+    Bs = [torch.randn(p.N * p.L * p.n, dtype=cdt, device="cuda") for _ in range(reps + 1)]
+    binding.band_solve(split, p.N, prec, ab_ptr, ipiv_ptr, p.L, Bs[reps], stream)
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    k0.record()
+    for r_ in range(reps):
+        binding.band_solve(split, p.N, prec, ab_ptr, ipiv_ptr, p.L, Bs[r_], stream)
+    k1.record()
+    torch.cuda.synchronize()
+    solve_ms = k0.elapsed_time(k1) / reps
+    del Bs
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -305,24 +371,38 @@ def main():
         peaks = measured_peaks()
         cs = clk.summary()
         sm_mhz = cs["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-        flops = lu_flops(p.n, split.kl, split.ku, p.N)
-        lu = float(np.mean(lu_ms))
-        achieved = flops / (lu * 1e-3) / 1e12
-        peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0)) if prec == binding.NEP_PREC_MIXED else \
+        mixed = prec == binding.NEP_PREC_MIXED
+        esz = 8 if mixed else 16
+        alu_peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0)) if mixed else \
             fp64_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        alu_src = ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz" if mixed else
+                   "derived: 152 SMs x 1.75 FP64 FMA/clk (measured) x 2 flop x 2070 MHz")
+        s_flops = solve_flops(p.n, split.kl, split.ku, p.L, p.N)
+        s_bytes = solve_bytes(p.n, split.ldab, p.L, p.N, esz)
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        lu = float(np.mean(lu_ms))
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "c64+f64" if prec == binding.NEP_PREC_MIXED else "f64",
+            "vs_baseline": None, "dtype": "c64+f64" if mixed else "f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "n": p.n, "bandwidth": split.kl, "N": p.N, "L": p.L, "M": p.M,
                        "precision": args.precision, "l2": "inputs larger than L2 (band factors "
-                       f"{p.N * p.n * split.ldab * (8 if prec else 16) / 1e6:.0f} MB per step)"},
-            "roofline": {"kernel": "lu_reg_kernel (banded LU, all quadrature points in one launch)",
-                         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz" if prec else
-                         "derived: 152 SMs x 1.75 FP64 FMA/clk (measured) x 2 flop x 2070 MHz"},
+                       f"{p.N * p.n * split.ldab * esz / 1e6:.0f} MB per step)"},
+            "roofline": {"kernel": ("band_solve_reg_kernel" if split.kl + 1 <= 96 and split.kl + split.ku + 1 <= 160
+                                    else "band_solve_kernel") + " (forward + backward banded substitution, "
+                                   f"{p.N} points x {p.L} right-hand sides in one launch)",
+                         "bound": "alu", "achieved": s_flops / (solve_ms * 1e-3) / 1e12, "peak": alu_peak,
+                         "unit": "TFLOP/s", "frac": s_flops / (solve_ms * 1e-3) / 1e12 / alu_peak,
+                         "traffic": SOLVE_TRAFFIC.get((args.workload, args.precision)),
+                         "ms_per_launch": solve_ms, "peak_source": alu_src,
+                         "algorithmic": {"flops": s_flops, "bytes": s_bytes,
+                                         "hbm_gbs": s_bytes / (solve_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm,
+                                         "hbm_frac": s_bytes / (solve_ms * 1e-3) / 1e9 / hbm}},
+            "factor": {"kernel": "lu_regt_kernel" if split.kl <= 64 and split.kl + split.ku <= 128 else "lu_glb_kernel",
+                       "ms": lu, "achieved_tflops": lu_flops(p.n, split.kl, split.ku, p.N) / (lu * 1e-3) / 1e12,
+                       "peak_tflops": alu_peak,
+                       "frac": lu_flops(p.n, split.kl, split.ku, p.N) / (lu * 1e-3) / 1e12 / alu_peak},
             "stages_ms": stage, "clocks": cs, "gpu_launches": int(launches),
             "result": {"nconv": int(len(res["lam"])), "hankel_rank": res["m"], "max_eta": float(res["eta"].max())
                        if len(res["eta"]) else None, "max_backward": res["info"]["max_backward"],
@@ -332,7 +412,7 @@ def main():
         if e2e:
             line["e2e"] = e2e
         if not args.no_serving:
-            line["serving"] = serving_bench(binding, prec, args.serving_requests, 0, 4, 10.0, args.serving_smax, 8)
+            line["serving"] = serving_bench(binding, prec, args.serving_requests, 0, 4, args.serving_smax)
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(p)
         print(json.dumps(line), flush=True)

@@ -339,7 +339,6 @@ class Server:
         o = opts_struct(**opts)
         vptr = None
         if V is not None:
-            self._keep = getattr(self, "_keep", [])
             Vf = np.asfortranarray(V, dtype=np.complex128)
             vptr = Vf.ctypes.data
         t = ctypes.c_uint64()

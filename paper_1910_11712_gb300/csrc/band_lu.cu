@@ -1033,6 +1033,196 @@ __global__ void __launch_bounds__(128)
     }
 }
 
+// One substitution sweep (forward with L and the row interchanges, or backward with U) for
+// narrow bands, one warp per right-hand side. Step k handles row c = k (forward) or
+// c = n-1-k (backward); the row with step index k' lives in window slot s = k' mod RS,
+// RS = 32*RPL, held by lane s / RPL in register s % RPL. Consecutive steps therefore cycle
+// through the registers in a fixed order, so with the step loop unrolled by RPL every
+// register index is a compile-time constant. The row leaving the window at step k (row c
+// itself) is replaced in the same register by the row with step index k + RS, which needs
+// its first update only later (RS > window width).
+//
+// Per chunk of CH steps the CTA stages, for every step and every slot, the coefficient that
+// slot's row receives (zero outside the window) in slot order, so each lane reads its RPL
+// coefficients at fixed offsets and updates all its registers without predicates:
+//   forward  step c: rows c+d, d in [1, kl]:  a -= L(c+d, c) x_c,  L(c+d,c) = ab[c*ldab + kv + d]
+//   backward step c: rows c-d, d in [1, kv]:  w -= U(c-d, c) x_c,  U(c-d,c) = ab[(c-d)*ldab + d]
+// with x_c the row's value after the interchange with row ipiv[c] (forward) or the row's
+// value times 1/U(c,c) (backward).
+template <typename T, int RPL, bool BWD>
+__global__ void __launch_bounds__(128)
+    band_sweep_kernel(int n, int kl, int ku, int ldab, const cx<T>* __restrict__ ab_all,
+                      const int* __restrict__ ipiv_all, int L, cx<T>* __restrict__ B_all,
+                      const int* __restrict__ active, int CH) {
+    const int j = blockIdx.x;
+    if (active && !active[j]) return;
+    constexpr int RS = 32 * RPL;
+    const int kv = kl + ku;
+    const int W = BWD ? kv : kl;  // window width: rows updated per step
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const int col = blockIdx.y * nwarps + warp;
+    const bool has_col = col < L;
+    const cx<T>* ab = ab_all + (int64_t)j * n * ldab;
+    const int* ipiv = ipiv_all + (int64_t)j * n;
+    cx<T>* b = B_all + ((int64_t)j * L + (has_col ? col : 0)) * n;
+    auto row_of = [&](int k) { return BWD ? n - 1 - k : k; };
+
+    // layout: coef[2][CH*RS] | aux[2][CH] (1/U(c,c) backward) | nb[2][nwarps][CH] | ob[nwarps][CH] | piv[2][CH]
+    extern __shared__ unsigned char smem_raw[];
+    cx<T>* coef0 = reinterpret_cast<cx<T>*>(smem_raw);
+    cx<T>* aux0 = coef0 + 2 * (int64_t)CH * RS;
+    cx<T>* nb0 = aux0 + 2 * CH;
+    cx<T>* ob = nb0 + 2 * (int64_t)nwarps * CH + (int64_t)warp * CH;
+    int* piv0 = reinterpret_cast<int*>(ob - (int64_t)warp * CH + (int64_t)nwarps * CH);
+
+    auto issue = [&](int k0, int bsel) {
+        const int cn = min(CH, n - k0);
+        cx<T>* cf = coef0 + (int64_t)bsel * CH * RS;
+        // every slot of every step gets exactly one writer: the window rows d in [1, W] copy their
+        // coefficient (or zero past the matrix), the other RS - W slots (d = 0 and d > W) zero
+        auto slot_pos = [](int s) { return (s % RPL) * 32 + s / RPL; };
+        for (int cc = warp; cc < cn; cc += nwarps) {
+            const int k = k0 + cc;
+            for (int d = W + 1 + lane; d <= RS; d += 32) cf[cc * RS + slot_pos((k + d) % RS)] = mk<T>(0, 0);
+        }
+        if (!BWD) {
+            // column c = k of L: contiguous in memory, lanes over d
+            for (int cc = warp; cc < cn; cc += nwarps) {
+                const int k = k0 + cc;
+                const cx<T>* src = ab + (int64_t)k * ldab + kv;
+                for (int d = 1 + lane; d <= W; d += 32) {
+                    cx<T>* dst = &cf[cc * RS + slot_pos((k + d) % RS)];
+                    if (k + d < n) cp_async_cx(dst, src + d);
+                    else *dst = mk<T>(0, 0);
+                }
+            }
+            if (threadIdx.x < cn) piv0[bsel * CH + threadIdx.x] = ipiv[k0 + threadIdx.x] - (k0 + threadIdx.x);
+        } else {
+            // U(r, c) for the chunk's columns c = n-1-k: row r contiguous, lanes over c
+            const int chi = n - 1 - k0, clo = chi - cn + 1;
+            const int rlo = max(0, clo - kv);
+            for (int r = rlo + warp; r < chi; r += nwarps) {
+                const int pos = slot_pos((n - 1 - r) % RS);
+                for (int c = clo + lane; c <= chi; c += 32) {
+                    const int d = c - r;
+                    if (d >= 1 && d <= kv) cp_async_cx(&cf[(chi - c) * RS + pos], ab + (int64_t)r * ldab + d);
+                }
+            }
+            // rows past the matrix (c - d < 0) hold zero
+            for (int cc = warp; cc < cn; cc += nwarps) {
+                const int c = chi - cc;
+                for (int d = c + 1 + lane; d <= kv; d += 32) cf[cc * RS + slot_pos((k0 + cc + d) % RS)] = mk<T>(0, 0);
+            }
+            if (threadIdx.x < cn) {
+                const int c = chi - threadIdx.x;
+                aux0[bsel * CH + threadIdx.x] = cdiv(mk<T>(1, 0), ab[(int64_t)c * ldab]);
+            }
+        }
+        if (has_col) {
+            cx<T>* nb = nb0 + ((int64_t)bsel * nwarps + warp) * CH;
+            for (int cc = lane; cc < cn; cc += 32) {
+                const int k = k0 + cc + RS;
+                if (k < n) cp_async_cx(&nb[cc], b + row_of(k));
+                else nb[cc] = mk<T>(0, 0);
+            }
+        }
+        cp_async_commit();
+    };
+
+    cx<T> a[RPL];
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+        const int k = lane * RPL + q;
+        a[q] = (has_col && k < n) ? b[row_of(k)] : mk<T>(0, 0);
+    }
+    int lane_k = 0;  // lane holding the current step's row
+    issue(0, 0);
+    for (int k0 = 0, chunk = 0; k0 < n; k0 += CH, ++chunk) {
+        const int cn = min(CH, n - k0);
+        const int bsel = chunk & 1;
+        cp_async_wait_group<0>();
+        __syncthreads();
+        if (k0 + CH < n) issue(k0 + CH, bsel ^ 1);
+        if (has_col) {
+            const cx<T>* cf = coef0 + (int64_t)bsel * CH * RS + lane;
+            const cx<T>* aux = aux0 + bsel * CH;
+            const int* pv = piv0 + bsel * CH;
+            const cx<T>* nb = nb0 + ((int64_t)bsel * nwarps + warp) * CH;
+            for (int g = 0; g < cn; g += RPL) {
+#pragma unroll
+                for (int u = 0; u < RPL; ++u) {
+                    const int cc = g + u;
+                    if (cc < cn) {
+                        cx<T> x = shfl_cx(a[u], lane_k);
+                        if (!BWD) {
+                            const int p = pv[cc];
+                            if (p != 0) {
+                                // interchange rows c and c+p: slot of c+p is (lane_k*RPL + u + p) mod RS
+                                int sp = lane_k * RPL + u + p;
+                                if (sp >= RS) sp -= RS;
+                                const int lp = sp / RPL, qp = sp - lp * RPL;
+                                const cx<T> vp = shfl_cx(sel_reg(a, qp), lp);
+                                if (lane == lp) set_reg(a, qp, x);
+                                x = vp;
+                            }
+                        } else {
+                            x = x * aux[cc];
+                        }
+                        const cx<T>* c1 = cf + (int64_t)cc * RS;
+#pragma unroll
+                        for (int q = 0; q < RPL; ++q) a[q] = fms(a[q], c1[q * 32], x);
+                        if (lane == lane_k) a[u] = nb[cc];
+                        if (lane == 0) ob[cc] = x;
+                    }
+                    if (u == RPL - 1) lane_k = lane_k == 31 ? 0 : lane_k + 1;
+                }
+            }
+            __syncwarp();
+            for (int cc = lane; cc < cn; cc += 32) b[row_of(k0 + cc)] = ob[cc];
+            __syncwarp();
+        }
+    }
+}
+
+template <typename T, int RPL, bool BWD>
+static int run_sweep(const SplitDev& s, int npts, const cx<T>* ab, const int* ipiv, int L, cx<T>* B,
+                     const int* active, cudaStream_t st) {
+    constexpr int RS = 32 * RPL;
+    const int wpb = L < 4 ? L : 4;
+    const int gy = (L + wpb - 1) / wpb;
+    auto bytes = [&](int ch) {
+        return sizeof(cx<T>) * (2 * (size_t)ch * RS + 2 * (size_t)ch + 3 * (size_t)wpb * ch) + sizeof(int) * 2 * ch;
+    };
+    int CH = 32 - 32 % RPL;
+    while (CH > RPL && bytes(CH) > 200 * 1024) CH -= RPL;
+    const size_t smem = bytes(CH);
+    if (smem > 227 * 1024) return NEP_ERR_UNSUPPORTED;
+    NEP_CUDA(cudaFuncSetAttribute(band_sweep_kernel<T, RPL, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    band_sweep_kernel<T, RPL, BWD><<<dim3(npts, gy), wpb * 32, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, L, B,
+                                                                         active, CH);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+
+template <typename T, bool BWD>
+static int sweep_dispatch(int rpl, const SplitDev& s, int npts, const cx<T>* ab, const int* ipiv, int L, cx<T>* B,
+                          const int* active, cudaStream_t st) {
+    switch (rpl) {
+        case 1: return run_sweep<T, 1, BWD>(s, npts, ab, ipiv, L, B, active, st);
+        case 2: return run_sweep<T, 2, BWD>(s, npts, ab, ipiv, L, B, active, st);
+        case 3: return run_sweep<T, 3, BWD>(s, npts, ab, ipiv, L, B, active, st);
+        case 4: return run_sweep<T, 4, BWD>(s, npts, ab, ipiv, L, B, active, st);
+        case 5: return run_sweep<T, 5, BWD>(s, npts, ab, ipiv, L, B, active, st);
+        case 6: return run_sweep<T, 6, BWD>(s, npts, ab, ipiv, L, B, active, st);
+        case 7: return run_sweep<T, 7, BWD>(s, npts, ab, ipiv, L, B, active, st);
+        case 8: return run_sweep<T, 8, BWD>(s, npts, ab, ipiv, L, B, active, st);
+        case 9: return run_sweep<T, 9, BWD>(s, npts, ab, ipiv, L, B, active, st);
+    }
+    return NEP_ERR_UNSUPPORTED;
+}
+
 template <typename T, int RPLF, int RPLB>
 static int run_solve_reg(const SplitDev& s, int npts, const cx<T>* ab, const int* ipiv, int L, cx<T>* B,
                          const int* active, cudaStream_t st) {
@@ -1072,8 +1262,14 @@ int launch_band_solve(const SplitDev& s, int npts, const cx<T>* ab, const int* i
                       const int* active, cudaStream_t st) {
     if (npts <= 0 || L <= 0) return NEP_OK;
     const int kv = s.kl + s.ku;
-    // register windows for narrow bands: kl+1 <= 96 rows forward, kv+1 <= 160 rows backward
+    // register windows for narrow bands: two sweeps with slot-ordered coefficients while the
+    // windows fit (kl+1 <= 288 and kv+1 <= 288 rows)
     const int rplf = (s.kl + 1 + 31) / 32, rplb = (kv + 1 + 31) / 32;
+    if (s.kl >= 1 && rplf <= 9 && rplb <= 9) {
+        const int rc = sweep_dispatch<T, false>(rplf, s, npts, ab, ipiv, L, B, active, st);
+        if (rc != NEP_OK) return rc;
+        return sweep_dispatch<T, true>(rplb, s, npts, ab, ipiv, L, B, active, st);
+    }
     if (s.kl >= 1 && rplf <= 3 && rplb <= 5) {
         switch (rplf) {
             case 1: return solve_reg_b<T, 1>(s, npts, ab, ipiv, L, B, active, st, rplb);

@@ -8,5 +8,5 @@ Eq. (split)), contour regions, and the random probe block V.
 from .problems import (  # noqa: F401
     Problem, delay_1d, delay_2d, drude_2d, sqrt_3d, diagonal_delay, diagonal_drude,
     diagonal_sqrt, dense_drude_small, dense_linear_small, config_problem, CONFIGS,
-    random_probe_block, serving_requests,
+    random_probe_block, serving_requests, serving_problem,
 )

@@ -326,16 +326,17 @@ def main():
     # point on the plan's factors; CUDA events on the launching stream, one fresh right-hand
     # side block per launch (each larger than L2 together with the factors it streams)
     ab_ptr, _ = plan.buffer("ab")
+    ut_ptr, _ = plan.buffer("ut")
     ipiv_ptr, _ = plan.buffer("ipiv")
     cdt = torch.complex64 if prec == binding.NEP_PREC_MIXED else torch.complex128
     reps = 5
     Bs = [torch.randn(p.N * p.L * p.n, dtype=cdt, device="cuda") for _ in range(reps + 1)]
-    binding.band_solve(split, p.N, prec, ab_ptr, ipiv_ptr, p.L, Bs[reps], stream)
+    binding.band_solve_cols(split, p.N, prec, ab_ptr, ut_ptr, ipiv_ptr, p.L, Bs[reps], stream)
     k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     k0.record()
     for r_ in range(reps):
-        binding.band_solve(split, p.N, prec, ab_ptr, ipiv_ptr, p.L, Bs[r_], stream)
+        binding.band_solve_cols(split, p.N, prec, ab_ptr, ut_ptr, ipiv_ptr, p.L, Bs[r_], stream)
     k1.record()
     torch.cuda.synchronize()
     solve_ms = k0.elapsed_time(k1) / reps
@@ -389,7 +390,7 @@ def main():
             "config": {"workload": args.workload, "n": p.n, "bandwidth": split.kl, "N": p.N, "L": p.L, "M": p.M,
                        "precision": args.precision, "l2": "inputs larger than L2 (band factors "
                        f"{p.N * p.n * split.ldab * esz / 1e6:.0f} MB per step)"},
-            "roofline": {"kernel": ("band_solve_reg_kernel" if split.kl + 1 <= 96 and split.kl + split.ku + 1 <= 160
+            "roofline": {"kernel": ("band_sweep_kernel x2" if split.kl + 1 <= 288 and split.kl + split.ku + 1 <= 288
                                     else "band_solve_kernel") + " (forward + backward banded substitution, "
                                    f"{p.N} points x {p.L} right-hand sides in one launch)",
                          "bound": "alu", "achieved": s_flops / (solve_ms * 1e-3) / 1e12, "peak": alu_peak,

@@ -222,9 +222,20 @@ int nep_assemble_band(nep_split_t h, int32_t npts, const double *F_dev, int32_t 
 int nep_band_factor(nep_split_t h, int32_t npts, int32_t precision, void *ab_dev, int32_t *ipiv_dev,
                     int32_t *info_dev, void *stream);
 /* Kernel (b): solve T(z_j) X_j = B_j with the factors, in place on B (npts x n x L,
- * column-major per point, element type of the precision). */
+ * column-major per point, element type of the precision). For narrow bands (kl+1 <= 288 and
+ * kl+ku+1 <= 288) the call builds the column copy of U (nep_band_transpose_u) in a temporary
+ * of its own; a caller solving repeatedly with the same factors builds it once and calls
+ * nep_band_solve_cols instead. */
 int nep_band_solve(nep_split_t h, int32_t npts, int32_t precision, const void *ab_dev, const int32_t *ipiv_dev,
                    int32_t L, void *B_dev, void *stream);
+/* U of the factored band by columns: ut[j][c*(kl+ku+1) + d] = U(c-d, c) for d in [0, kl+ku]
+ * (zero where c-d < 0); ut_dev holds npts x n x (kl+ku+1) elements of the precision's type. */
+int nep_band_transpose_u(nep_split_t h, int32_t npts, int32_t precision, const void *ab_dev, void *ut_dev,
+                         void *stream);
+/* nep_band_solve with the column copy of U made by nep_band_transpose_u from the same factors
+ * (ut_dev may be NULL for bands too wide for the narrow-band sweeps). */
+int nep_band_solve_cols(nep_split_t h, int32_t npts, int32_t precision, const void *ab_dev, const void *ut_dev,
+                        const int32_t *ipiv_dev, int32_t L, void *B_dev, void *stream);
 /* Kernel (c): FP64 split-form residual R_j = V - T(z_j) Y_j (npts x n x L complex128). */
 int nep_split_residual(nep_split_t h, int32_t npts, const double *F_dev, int32_t L, const double *V_dev,
                        const double *Y_dev, double *R_dev, void *stream);

@@ -92,6 +92,9 @@ SIGNATURES = {
     "nep_assemble_band": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "nep_band_factor": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "nep_band_solve": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
+    "nep_band_transpose_u": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
+    "nep_band_solve_cols": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_void_p,
+                                      c_void_p]),
     "nep_split_residual": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "nep_moments": (c_int32, [c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "nep_jacobi_svd": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -401,6 +404,15 @@ def band_factor(split, npts, precision, ab_dev, ipiv_dev, info_dev, stream=0):
 
 def band_solve(split, npts, precision, ab_dev, ipiv_dev, L, B_dev, stream=0):
     check(load().nep_band_solve(split.handle, npts, precision, ptr(ab_dev), ptr(ipiv_dev), L, ptr(B_dev), stream))
+
+
+def band_transpose_u(split, npts, precision, ab_dev, ut_dev, stream=0):
+    check(load().nep_band_transpose_u(split.handle, npts, precision, ptr(ab_dev), ptr(ut_dev), stream))
+
+
+def band_solve_cols(split, npts, precision, ab_dev, ut_dev, ipiv_dev, L, B_dev, stream=0):
+    check(load().nep_band_solve_cols(split.handle, npts, precision, ptr(ab_dev), ptr(ut_dev), ptr(ipiv_dev), L,
+                                     ptr(B_dev), stream))
 
 
 def split_residual(split, npts, F_dev, L, V_dev, Y_dev, R_dev, stream=0):

@@ -25,39 +25,9 @@
 // per step: one after the pivot column is published, one after the multipliers are.
 // lu_glb_kernel runs the same elimination with the window in a global (L2-resident)
 // scratch array, for bands too wide for the register file.
-#include "nep_common.cuh"
+#include "band_util.cuh"
 
 namespace nep {
-
-template <typename T>
-__device__ __forceinline__ cx<T> shfl_cx(cx<T> v, int src) {
-    cx<T> r;
-    r.re = __shfl_sync(0xffffffffu, v.re, src);
-    r.im = __shfl_sync(0xffffffffu, v.im, src);
-    return r;
-}
-
-__device__ __forceinline__ int posmod(int a, int m) {
-    int r = a % m;
-    return r < 0 ? r + m : r;
-}
-
-
-// Asynchronous global->shared copy of one complex element (8 or 16 bytes); completion is
-// awaited with cp_async_wait_all() before the barrier that publishes the data.
-template <typename T>
-__device__ __forceinline__ void cp_async_cx(cx<T>* smem, const cx<T>* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    if constexpr (sizeof(cx<T>) == 16) {
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-    } else {
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-    }
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // First index of the maximum of |Re|+|Im| over pcol[0..cnt-1], computed by one warp.
 // Ties resolve to the smallest index (the same rule as LAPACK's izamax).
@@ -845,438 +815,14 @@ __global__ void __launch_bounds__(512)
     }
 }
 
-// Register-window solve for narrow bands: one warp per right-hand side, the window rows live in
-// registers (slot r mod RS, lane = slot % 32, register = slot / 32), x_c is broadcast by shuffle
-// and each lane updates its own rows, so a column step is a few shuffles and one complex FMA
-// per owned row. dist[q] = (slot - current - 1) mod RS tracks which row a register holds.
-template <typename T, int RPL>
-__device__ __forceinline__ cx<T> sel_reg(const cx<T> (&a)[RPL], int q) {
-    cx<T> v = a[0];
-#pragma unroll
-    for (int t = 1; t < RPL; ++t)
-        if (t == q) v = a[t];
-    return v;
-}
-template <typename T, int RPL>
-__device__ __forceinline__ void set_reg(cx<T> (&a)[RPL], int q, cx<T> v) {
-#pragma unroll
-    for (int t = 0; t < RPL; ++t)
-        if (t == q) a[t] = v;
-}
-
-template <typename T, int RPLF, int RPLB>
-__global__ void __launch_bounds__(128)
-    band_solve_reg_kernel(int n, int kl, int ku, int ldab, const cx<T>* __restrict__ ab_all,
-                          const int* __restrict__ ipiv_all, int L, cx<T>* __restrict__ B_all,
-                          const int* __restrict__ active, int CH) {
-    const int j = blockIdx.x;
-    if (active && !active[j]) return;
-    constexpr int RSF = 32 * RPLF, RSB = 32 * RPLB;
-    const int kv = kl + ku;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nwarps = blockDim.x >> 5;
-    const int col = blockIdx.y * nwarps + warp;
-    const bool has_col = col < L;
-    const cx<T>* ab = ab_all + (int64_t)j * n * ldab;
-    const int* ipiv = ipiv_all + (int64_t)j * n;
-    cx<T>* b = B_all + ((int64_t)j * L + (has_col ? col : 0)) * n;
-
-    extern __shared__ unsigned char smem_raw[];
-    const int wide = kv > kl ? kv : (kl > 0 ? kl : 1);
-    // layout: nb[2][nwarps][CH] | stage[2][CH*wide] | diag[2][CH] | pst[2][CH]
-    cx<T>* nb0 = reinterpret_cast<cx<T>*>(smem_raw);
-    cx<T>* stage0 = nb0 + 2 * (int64_t)nwarps * CH;
-    cx<T>* diag0 = stage0 + 2 * (int64_t)CH * wide;
-    int* pst0 = reinterpret_cast<int*>(diag0 + 2 * CH);
-    auto nbuf = [&](int bsel) { return nb0 + ((int64_t)bsel * nwarps + warp) * CH; };
-    auto sbuf = [&](int bsel) { return stage0 + (int64_t)bsel * CH * wide; };
-
-    // ---------------- forward
-    auto issue_fwd = [&](int c0, int bsel) {
-        const int cn = min(CH, n - c0);
-        cx<T>* st = sbuf(bsel);
-        // L columns of the chunk: warps over columns, lanes over rows (no integer division)
-        for (int cc = warp; cc < cn; cc += nwarps) {
-            const cx<T>* src = ab + (int64_t)(c0 + cc) * ldab + kv + 1;
-            for (int i = lane; i < kl; i += 32) cp_async_cx(&st[cc * kl + i], src + i);
-        }
-        if (warp == 0 && lane < cn) cp_async_int<T>(&pst0[bsel * CH + lane], ipiv + c0 + lane);
-        if (has_col && lane < cn) {
-            cx<T>* nb = nbuf(bsel);
-            const int rn = c0 + lane + kl + 1;
-            if (rn < n) cp_async_cx(&nb[lane], b + rn);
-            else nb[lane] = mk<T>(0, 0);
-        }
-        cp_async_commit();
-    };
-    cx<T> a[RPLF];
-    int dist[RPLF];
-#pragma unroll
-    for (int q = 0; q < RPLF; ++q) {
-        const int s = lane + 32 * q;  // slot s holds row s at c = 0
-        a[q] = (has_col && s <= kl && s < n) ? b[s] : mk<T>(0, 0);
-        dist[q] = s == 0 ? RSF - 1 : s - 1;  // (s - 0 - 1) mod RSF
-    }
-    int sc = 0;
-    issue_fwd(0, 0);
-    for (int c0 = 0, chunk = 0; c0 < n; c0 += CH, ++chunk) {
-        const int cn = min(CH, n - c0);
-        const int bsel = chunk & 1;
-        cp_async_wait_group<0>();
-        __syncthreads();
-        if (c0 + CH < n) issue_fwd(c0 + CH, bsel ^ 1);
-        if (has_col) {
-            const cx<T>* st = sbuf(bsel);
-            const int* pst = pst0 + bsel * CH;
-            const cx<T>* nb = nbuf(bsel);
-            for (int cc = 0; cc < cn; ++cc) {
-                const int c = c0 + cc;
-                const int p = pst[cc] - c;
-                const int lc = sc & 31, qc = sc >> 5;
-                const cx<T> vc = shfl_cx(sel_reg(a, qc), lc);
-                cx<T> x = vc;
-                if (p != 0) {
-                    int sp = sc + p;
-                    if (sp >= RSF) sp -= RSF;
-                    const int lp = sp & 31, qp = sp >> 5;
-                    const cx<T> vp = shfl_cx(sel_reg(a, qp), lp);
-                    if (lane == lp) set_reg(a, qp, vc);
-                    x = vp;
-                }
-                const cx<T>* lcol = st + cc * kl;
-                const int lim = min(kl, n - 1 - c);
-#pragma unroll
-                for (int q = 0; q < RPLF; ++q)
-                    if (dist[q] < lim) a[q] = fms(a[q], lcol[dist[q]], x);
-                if (lane == lc) b[c] = x;
-                // row c+kl+1 enters
-                int sn = sc + kl + 1;
-                if (sn >= RSF) sn -= RSF;
-                if (lane == (sn & 31)) set_reg(a, sn >> 5, nb[cc]);
-#pragma unroll
-                for (int q = 0; q < RPLF; ++q) dist[q] = dist[q] == 0 ? RSF - 1 : dist[q] - 1;
-                if (++sc == RSF) sc = 0;
-            }
-        }
-    }
-    // ---------------- backward
-    cp_async_wait_group<0>();
-    __syncthreads();
-    auto issue_bwd = [&](int c1, int bsel) {
-        const int cn = min(CH, c1 + 1);
-        const int cbase = c1 - cn + 1;
-        cx<T>* st = sbuf(bsel);
-        cx<T>* dg = diag0 + bsel * CH;
-        // U rows rlo..c1-1, each contributing U(r, c) for the chunk columns c (lanes over c)
-        const int rlo = cbase - kv;
-        for (int r = rlo + warp; r < c1; r += nwarps) {
-            if (r < 0) continue;
-            const int c = cbase + lane, t = c - r;
-            if (lane < cn && t >= 1 && t <= kv) cp_async_cx(&st[lane * kv + (t - 1)], ab + (int64_t)r * ldab + t);
-        }
-        if (warp == 0 && lane < cn) cp_async_cx(&dg[lane], ab + (int64_t)(cbase + lane) * ldab);
-        if (has_col && lane < cn) {
-            cx<T>* nb = nbuf(bsel);
-            const int rn = cbase + lane - kv - 1;
-            if (rn >= 0) cp_async_cx(&nb[lane], b + rn);
-            else nb[lane] = mk<T>(0, 0);
-        }
-        cp_async_commit();
-    };
-    // rows n-1-i (i <= kv) in slot (n-1-i) mod RSB; dist = (slot_current - 1 - slot) mod RSB
-    cx<T> w[RPLB];
-    int dw[RPLB];
-    const int s0 = (n - 1) % RSB;
-#pragma unroll
-    for (int q = 0; q < RPLB; ++q) {
-        const int s = lane + 32 * q;
-        int back = s0 - s;
-        if (back < 0) back += RSB;  // slot s holds row n-1-back
-        const int r = n - 1 - back;
-        w[q] = (has_col && back <= kv && r >= 0) ? b[r] : mk<T>(0, 0);
-        dw[q] = back == 0 ? RSB - 1 : back - 1;
-    }
-    sc = s0;
-    issue_bwd(n - 1, 0);
-    for (int c1 = n - 1, chunk = 0; c1 >= 0; c1 -= CH, ++chunk) {
-        const int cn = min(CH, c1 + 1);
-        const int cbase = c1 - cn + 1;
-        const int bsel = chunk & 1;
-        cp_async_wait_group<0>();
-        __syncthreads();
-        if (c1 - CH >= 0) issue_bwd(c1 - CH, bsel ^ 1);
-        if (has_col) {
-            const cx<T>* st = sbuf(bsel);
-            const cx<T>* dg = diag0 + bsel * CH;
-            const cx<T>* nb = nbuf(bsel);
-            const cx<T> rd = lane < cn ? cdiv(mk<T>(1, 0), dg[lane]) : mk<T>(0, 0);
-            for (int cc = cn - 1; cc >= 0; --cc) {
-                const int c = cbase + cc;
-                const cx<T> r = shfl_cx(rd, cc);
-                const int lc = sc & 31, qc = sc >> 5;
-                const cx<T> x = shfl_cx(sel_reg(w, qc), lc) * r;
-                const cx<T>* ucol = st + cc * kv;
-                const int lim = min(kv, c);
-#pragma unroll
-                for (int q = 0; q < RPLB; ++q)
-                    if (dw[q] < lim) w[q] = fms(w[q], ucol[dw[q]], x);
-                if (lane == lc) b[c] = x;
-                // row c-kv-1 enters its slot (c-kv-1) mod RSB
-                int sn = sc - kv - 1;
-                while (sn < 0) sn += RSB;
-                if (lane == (sn & 31)) set_reg(w, sn >> 5, nb[cc]);
-#pragma unroll
-                for (int q = 0; q < RPLB; ++q) dw[q] = dw[q] == 0 ? RSB - 1 : dw[q] - 1;
-                if (--sc < 0) sc = RSB - 1;
-            }
-        }
-    }
-}
-
-// One substitution sweep (forward with L and the row interchanges, or backward with U) for
-// narrow bands, one warp per right-hand side. Step k handles row c = k (forward) or
-// c = n-1-k (backward); the row with step index k' lives in window slot s = k' mod RS,
-// RS = 32*RPL, held by lane s / RPL in register s % RPL. Consecutive steps therefore cycle
-// through the registers in a fixed order, so with the step loop unrolled by RPL every
-// register index is a compile-time constant. The row leaving the window at step k (row c
-// itself) is replaced in the same register by the row with step index k + RS, which needs
-// its first update only later (RS > window width).
-//
-// Per chunk of CH steps the CTA stages, for every step and every slot, the coefficient that
-// slot's row receives (zero outside the window) in slot order, so each lane reads its RPL
-// coefficients at fixed offsets and updates all its registers without predicates:
-//   forward  step c: rows c+d, d in [1, kl]:  a -= L(c+d, c) x_c,  L(c+d,c) = ab[c*ldab + kv + d]
-//   backward step c: rows c-d, d in [1, kv]:  w -= U(c-d, c) x_c,  U(c-d,c) = ab[(c-d)*ldab + d]
-// with x_c the row's value after the interchange with row ipiv[c] (forward) or the row's
-// value times 1/U(c,c) (backward).
-template <typename T, int RPL, bool BWD>
-__global__ void __launch_bounds__(128)
-    band_sweep_kernel(int n, int kl, int ku, int ldab, const cx<T>* __restrict__ ab_all,
-                      const int* __restrict__ ipiv_all, int L, cx<T>* __restrict__ B_all,
-                      const int* __restrict__ active, int CH) {
-    const int j = blockIdx.x;
-    if (active && !active[j]) return;
-    constexpr int RS = 32 * RPL;
-    const int kv = kl + ku;
-    const int W = BWD ? kv : kl;  // window width: rows updated per step
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nwarps = blockDim.x >> 5;
-    const int col = blockIdx.y * nwarps + warp;
-    const bool has_col = col < L;
-    const cx<T>* ab = ab_all + (int64_t)j * n * ldab;
-    const int* ipiv = ipiv_all + (int64_t)j * n;
-    cx<T>* b = B_all + ((int64_t)j * L + (has_col ? col : 0)) * n;
-    auto row_of = [&](int k) { return BWD ? n - 1 - k : k; };
-
-    // layout: coef[2][CH*RS] | aux[2][CH] (1/U(c,c) backward) | nb[2][nwarps][CH] | ob[nwarps][CH] | piv[2][CH]
-    extern __shared__ unsigned char smem_raw[];
-    cx<T>* coef0 = reinterpret_cast<cx<T>*>(smem_raw);
-    cx<T>* aux0 = coef0 + 2 * (int64_t)CH * RS;
-    cx<T>* nb0 = aux0 + 2 * CH;
-    cx<T>* ob = nb0 + 2 * (int64_t)nwarps * CH + (int64_t)warp * CH;
-    int* piv0 = reinterpret_cast<int*>(ob - (int64_t)warp * CH + (int64_t)nwarps * CH);
-
-    auto issue = [&](int k0, int bsel) {
-        const int cn = min(CH, n - k0);
-        cx<T>* cf = coef0 + (int64_t)bsel * CH * RS;
-        // every slot of every step gets exactly one writer: the window rows d in [1, W] copy their
-        // coefficient (or zero past the matrix), the other RS - W slots (d = 0 and d > W) zero
-        auto slot_pos = [](int s) { return (s % RPL) * 32 + s / RPL; };
-        for (int cc = warp; cc < cn; cc += nwarps) {
-            const int k = k0 + cc;
-            for (int d = W + 1 + lane; d <= RS; d += 32) cf[cc * RS + slot_pos((k + d) % RS)] = mk<T>(0, 0);
-        }
-        if (!BWD) {
-            // column c = k of L: contiguous in memory, lanes over d
-            for (int cc = warp; cc < cn; cc += nwarps) {
-                const int k = k0 + cc;
-                const cx<T>* src = ab + (int64_t)k * ldab + kv;
-                for (int d = 1 + lane; d <= W; d += 32) {
-                    cx<T>* dst = &cf[cc * RS + slot_pos((k + d) % RS)];
-                    if (k + d < n) cp_async_cx(dst, src + d);
-                    else *dst = mk<T>(0, 0);
-                }
-            }
-            if (threadIdx.x < cn) piv0[bsel * CH + threadIdx.x] = ipiv[k0 + threadIdx.x] - (k0 + threadIdx.x);
-        } else {
-            // U(r, c) for the chunk's columns c = n-1-k: row r contiguous, lanes over c
-            const int chi = n - 1 - k0, clo = chi - cn + 1;
-            const int rlo = max(0, clo - kv);
-            for (int r = rlo + warp; r < chi; r += nwarps) {
-                const int pos = slot_pos((n - 1 - r) % RS);
-                for (int c = clo + lane; c <= chi; c += 32) {
-                    const int d = c - r;
-                    if (d >= 1 && d <= kv) cp_async_cx(&cf[(chi - c) * RS + pos], ab + (int64_t)r * ldab + d);
-                }
-            }
-            // rows past the matrix (c - d < 0) hold zero
-            for (int cc = warp; cc < cn; cc += nwarps) {
-                const int c = chi - cc;
-                for (int d = c + 1 + lane; d <= kv; d += 32) cf[cc * RS + slot_pos((k0 + cc + d) % RS)] = mk<T>(0, 0);
-            }
-            if (threadIdx.x < cn) {
-                const int c = chi - threadIdx.x;
-                aux0[bsel * CH + threadIdx.x] = cdiv(mk<T>(1, 0), ab[(int64_t)c * ldab]);
-            }
-        }
-        if (has_col) {
-            cx<T>* nb = nb0 + ((int64_t)bsel * nwarps + warp) * CH;
-            for (int cc = lane; cc < cn; cc += 32) {
-                const int k = k0 + cc + RS;
-                if (k < n) cp_async_cx(&nb[cc], b + row_of(k));
-                else nb[cc] = mk<T>(0, 0);
-            }
-        }
-        cp_async_commit();
-    };
-
-    cx<T> a[RPL];
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-        const int k = lane * RPL + q;
-        a[q] = (has_col && k < n) ? b[row_of(k)] : mk<T>(0, 0);
-    }
-    int lane_k = 0;  // lane holding the current step's row
-    issue(0, 0);
-    for (int k0 = 0, chunk = 0; k0 < n; k0 += CH, ++chunk) {
-        const int cn = min(CH, n - k0);
-        const int bsel = chunk & 1;
-        cp_async_wait_group<0>();
-        __syncthreads();
-        if (k0 + CH < n) issue(k0 + CH, bsel ^ 1);
-        if (has_col) {
-            const cx<T>* cf = coef0 + (int64_t)bsel * CH * RS + lane;
-            const cx<T>* aux = aux0 + bsel * CH;
-            const int* pv = piv0 + bsel * CH;
-            const cx<T>* nb = nb0 + ((int64_t)bsel * nwarps + warp) * CH;
-            for (int g = 0; g < cn; g += RPL) {
-#pragma unroll
-                for (int u = 0; u < RPL; ++u) {
-                    const int cc = g + u;
-                    if (cc < cn) {
-                        cx<T> x = shfl_cx(a[u], lane_k);
-                        if (!BWD) {
-                            const int p = pv[cc];
-                            if (p != 0) {
-                                // interchange rows c and c+p: slot of c+p is (lane_k*RPL + u + p) mod RS
-                                int sp = lane_k * RPL + u + p;
-                                if (sp >= RS) sp -= RS;
-                                const int lp = sp / RPL, qp = sp - lp * RPL;
-                                const cx<T> vp = shfl_cx(sel_reg(a, qp), lp);
-                                if (lane == lp) set_reg(a, qp, x);
-                                x = vp;
-                            }
-                        } else {
-                            x = x * aux[cc];
-                        }
-                        const cx<T>* c1 = cf + (int64_t)cc * RS;
-#pragma unroll
-                        for (int q = 0; q < RPL; ++q) a[q] = fms(a[q], c1[q * 32], x);
-                        if (lane == lane_k) a[u] = nb[cc];
-                        if (lane == 0) ob[cc] = x;
-                    }
-                    if (u == RPL - 1) lane_k = lane_k == 31 ? 0 : lane_k + 1;
-                }
-            }
-            __syncwarp();
-            for (int cc = lane; cc < cn; cc += 32) b[row_of(k0 + cc)] = ob[cc];
-            __syncwarp();
-        }
-    }
-}
-
-template <typename T, int RPL, bool BWD>
-static int run_sweep(const SplitDev& s, int npts, const cx<T>* ab, const int* ipiv, int L, cx<T>* B,
-                     const int* active, cudaStream_t st) {
-    constexpr int RS = 32 * RPL;
-    const int wpb = L < 4 ? L : 4;
-    const int gy = (L + wpb - 1) / wpb;
-    auto bytes = [&](int ch) {
-        return sizeof(cx<T>) * (2 * (size_t)ch * RS + 2 * (size_t)ch + 3 * (size_t)wpb * ch) + sizeof(int) * 2 * ch;
-    };
-    int CH = 32 - 32 % RPL;
-    while (CH > RPL && bytes(CH) > 200 * 1024) CH -= RPL;
-    const size_t smem = bytes(CH);
-    if (smem > 227 * 1024) return NEP_ERR_UNSUPPORTED;
-    NEP_CUDA(cudaFuncSetAttribute(band_sweep_kernel<T, RPL, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
-    band_sweep_kernel<T, RPL, BWD><<<dim3(npts, gy), wpb * 32, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, L, B,
-                                                                         active, CH);
-    NEP_CHECK_LAUNCH();
-    return NEP_OK;
-}
-
-template <typename T, bool BWD>
-static int sweep_dispatch(int rpl, const SplitDev& s, int npts, const cx<T>* ab, const int* ipiv, int L, cx<T>* B,
-                          const int* active, cudaStream_t st) {
-    switch (rpl) {
-        case 1: return run_sweep<T, 1, BWD>(s, npts, ab, ipiv, L, B, active, st);
-        case 2: return run_sweep<T, 2, BWD>(s, npts, ab, ipiv, L, B, active, st);
-        case 3: return run_sweep<T, 3, BWD>(s, npts, ab, ipiv, L, B, active, st);
-        case 4: return run_sweep<T, 4, BWD>(s, npts, ab, ipiv, L, B, active, st);
-        case 5: return run_sweep<T, 5, BWD>(s, npts, ab, ipiv, L, B, active, st);
-        case 6: return run_sweep<T, 6, BWD>(s, npts, ab, ipiv, L, B, active, st);
-        case 7: return run_sweep<T, 7, BWD>(s, npts, ab, ipiv, L, B, active, st);
-        case 8: return run_sweep<T, 8, BWD>(s, npts, ab, ipiv, L, B, active, st);
-        case 9: return run_sweep<T, 9, BWD>(s, npts, ab, ipiv, L, B, active, st);
-    }
-    return NEP_ERR_UNSUPPORTED;
-}
-
-template <typename T, int RPLF, int RPLB>
-static int run_solve_reg(const SplitDev& s, int npts, const cx<T>* ab, const int* ipiv, int L, cx<T>* B,
-                         const int* active, cudaStream_t st) {
-    const int kv = s.kl + s.ku;
-    const int wpb = L < 4 ? L : 4;
-    const int gy = (L + wpb - 1) / wpb;
-    const int wide = kv > s.kl ? kv : (s.kl > 0 ? s.kl : 1);
-    int CH = 32;
-    auto bytes = [&](int ch) {
-        return sizeof(cx<T>) * (2 * (size_t)wpb * ch + 2 * (size_t)ch * wide + 2 * ch) + sizeof(int) * 2 * ch;
-    };
-    while (CH > 1 && bytes(CH) > 200 * 1024) CH >>= 1;
-    const size_t smem = bytes(CH);
-    NEP_CUDA(cudaFuncSetAttribute(band_solve_reg_kernel<T, RPLF, RPLB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
-    band_solve_reg_kernel<T, RPLF, RPLB><<<dim3(npts, gy), wpb * 32, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, L,
-                                                                              B, active, CH);
-    NEP_CHECK_LAUNCH();
-    return NEP_OK;
-}
-
-template <typename T, int RPLF>
-static int solve_reg_b(const SplitDev& s, int npts, const cx<T>* ab, const int* ipiv, int L, cx<T>* B,
-                       const int* active, cudaStream_t st, int rplb) {
-    switch (rplb) {
-        case 1: return run_solve_reg<T, RPLF, 1>(s, npts, ab, ipiv, L, B, active, st);
-        case 2: return run_solve_reg<T, RPLF, 2>(s, npts, ab, ipiv, L, B, active, st);
-        case 3: return run_solve_reg<T, RPLF, 3>(s, npts, ab, ipiv, L, B, active, st);
-        case 4: return run_solve_reg<T, RPLF, 4>(s, npts, ab, ipiv, L, B, active, st);
-        case 5: return run_solve_reg<T, RPLF, 5>(s, npts, ab, ipiv, L, B, active, st);
-    }
-    return NEP_ERR_INTERNAL;
-}
-
 template <typename T>
-int launch_band_solve(const SplitDev& s, int npts, const cx<T>* ab, const int* ipiv, int L, cx<T>* B,
+int launch_band_solve(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* ut, const int* ipiv, int L, cx<T>* B,
                       const int* active, cudaStream_t st) {
     if (npts <= 0 || L <= 0) return NEP_OK;
     const int kv = s.kl + s.ku;
-    // register windows for narrow bands: two sweeps with slot-ordered coefficients while the
-    // windows fit (kl+1 <= 288 and kv+1 <= 288 rows)
-    const int rplf = (s.kl + 1 + 31) / 32, rplb = (kv + 1 + 31) / 32;
-    if (s.kl >= 1 && rplf <= 9 && rplb <= 9) {
-        const int rc = sweep_dispatch<T, false>(rplf, s, npts, ab, ipiv, L, B, active, st);
-        if (rc != NEP_OK) return rc;
-        return sweep_dispatch<T, true>(rplb, s, npts, ab, ipiv, L, B, active, st);
-    }
-    if (s.kl >= 1 && rplf <= 3 && rplb <= 5) {
-        switch (rplf) {
-            case 1: return solve_reg_b<T, 1>(s, npts, ab, ipiv, L, B, active, st, rplb);
-            case 2: return solve_reg_b<T, 2>(s, npts, ab, ipiv, L, B, active, st, rplb);
-            case 3: return solve_reg_b<T, 3>(s, npts, ab, ipiv, L, B, active, st, rplb);
-        }
-    }
+    // register windows for narrow bands (kl+1 <= 288 and kv+1 <= 288 rows): two sweeps with
+    // slot-ordered coefficients
+    if (band_sweeps_fit(s.kl, s.ku)) return band_sweeps<T>(s, npts, ab, ut, ipiv, L, B, active, st);
     // general path: shared-memory windows, one right-hand side per warp, four warps per CTA
     constexpr int RH = 1;
     const int warps_total = L;
@@ -1300,9 +846,9 @@ int launch_band_solve(const SplitDev& s, int npts, const cx<T>* ab, const int* i
     return NEP_OK;
 }
 
-template int launch_band_solve<float>(const SplitDev&, int, const cx<float>*, const int*, int, cx<float>*, const int*,
-                                      cudaStream_t);
-template int launch_band_solve<double>(const SplitDev&, int, const cx<double>*, const int*, int, cx<double>*,
-                                       const int*, cudaStream_t);
+template int launch_band_solve<float>(const SplitDev&, int, const cx<float>*, const cx<float>*, const int*, int,
+                                      cx<float>*, const int*, cudaStream_t);
+template int launch_band_solve<double>(const SplitDev&, int, const cx<double>*, const cx<double>*, const int*, int,
+                                       cx<double>*, const int*, cudaStream_t);
 
 }  // namespace nep

@@ -448,6 +448,7 @@ struct nep_plan {
     zd* F = nullptr;      // nterms x N
     zd* coef = nullptr;   // N x K (column k: w_j zeta_j^k)
     void* ab = nullptr;   // N x n x ldab of complex64/complex128
+    void* ut = nullptr;   // N x n x (kl+ku+1): U by columns for the narrow-band sweeps (else unused)
     int* ipiv = nullptr;  // N x n
     int* info = nullptr;  // N
     double* tnorm = nullptr;
@@ -496,6 +497,7 @@ static int plan_alloc(nep_plan* p) {
     NEP_TRY(dalloc(&p->F, (size_t)nt * N, st));
     NEP_TRY(dalloc(&p->coef, (size_t)N * K, st));
     NEP_TRY(dalloc_raw(&p->ab, esz * (size_t)N * n * h->ldab, st));
+    if (band_sweeps_fit(h->kl, h->ku)) NEP_TRY(dalloc_raw(&p->ut, esz * (size_t)N * n * (h->kl + h->ku + 1), st));
     NEP_TRY(dalloc(&p->ipiv, (size_t)N * n, st));
     NEP_TRY(dalloc(&p->info, N, st));
     NEP_TRY(dalloc(&p->tnorm, N, st));
@@ -566,7 +568,7 @@ static int plan_alloc(nep_plan* p) {
 
 static void plan_free(nep_plan* p) {
     cudaStream_t st = p->alloc_stream;
-    void* bufs[] = {p->F, p->coef, p->ab, p->ipiv, p->info, p->tnorm, p->tval, p->V, p->Y, p->R, p->D, p->nrm,
+    void* bufs[] = {p->F, p->coef, p->ab, p->ut, p->ipiv, p->info, p->tnorm, p->tval, p->V, p->Y, p->R, p->D, p->nrm,
                     p->dmax, p->ymax, p->prev, p->beta, p->active, p->sweeps, p->nactive, p->S, p->mu, p->vpart,
                     p->H, p->Hs, p->Hw, p->U, p->W, p->sigma, p->T1, p->Bred, p->theta, p->Tv, p->Z, p->cand,
                     p->XH, p->G, p->Gw, p->Wg, p->lamg, p->Q, p->Y0, p->AQ, p->Bs, p->lamn, p->Yn, p->Xc, p->Gx,
@@ -676,9 +678,11 @@ static int run_solves(nep_plan* p, cudaStream_t st) {
     NEP_TRY(launch_assemble<T>(s, N, p->F, ab, p->tnorm, p->tval, st));
     NEP_CUDA(cudaEventRecord(p->ev[1], st));
     NEP_TRY(launch_band_lu<T>(s, N, ab, p->ipiv, p->info, nullptr, st));
+    cx<T>* ut = reinterpret_cast<cx<T>*>(p->ut);
+    if (ut) NEP_TRY(band_transpose_u<T>(s, N, ab, ut, st));
     NEP_CUDA(cudaEventRecord(p->ev[2], st));
     NEP_TRY(launch_convert_rhs<T>(N, n, L, p->V, D, st));
-    NEP_TRY(launch_band_solve<T>(s, N, ab, p->ipiv, L, D, nullptr, st));
+    NEP_TRY(launch_band_solve<T>(s, N, ab, ut, p->ipiv, L, D, nullptr, st));
     NEP_TRY(launch_widen<T>(N, n, L, D, p->Y, st));
     NEP_TRY(launch_fill_int(N, p->active, 1, st));
     NEP_CUDA(cudaMemsetAsync(p->prev, 0, sizeof(double) * N, st));
@@ -686,7 +690,7 @@ static int run_solves(nep_plan* p, cudaStream_t st) {
     for (int sweep = 0; sweep < p->o.refine_max; ++sweep) {
         NEP_TRY(launch_split_residual(s, N, p->tval, L, p->V, p->Y, p->R, p->nrm, p->active, st));
         NEP_TRY(launch_refine_prepare<T>(N, n, L, p->R, D, p->active, st));
-        NEP_TRY(launch_band_solve<T>(s, N, ab, p->ipiv, L, D, p->active, st));
+        NEP_TRY(launch_band_solve<T>(s, N, ab, ut, p->ipiv, L, D, p->active, st));
         NEP_TRY(launch_refine_update<T>(N, n, L, D, p->Y, p->dmax, p->ymax, p->active, st));
         NEP_TRY(launch_refine_decide(N, L, sweep, p->o.refine_max, p->o.refine_tol, p->o.step_tol, p->nrm, p->tnorm,
                                      p->dmax, p->ymax, p->prev, p->beta, p->active, p->sweeps, p->nactive, st));
@@ -792,6 +796,7 @@ extern "C" int nep_plan_buffer(nep_plan_t p, const char* name, void** dev_ptr, s
     struct B { const char* nm; void* ptr; size_t bytes; } tab[] = {
         {"F", p->F, sizeof(zd) * h->nterms * N},   {"coef", p->coef, sizeof(zd) * N * K},
         {"ab", p->ab, esz * N * n * h->ldab},       {"ipiv", p->ipiv, sizeof(int) * N * n},
+        {"ut", p->ut, p->ut ? esz * N * n * (h->kl + h->ku + 1) : 0},
         {"info", p->info, sizeof(int) * N},         {"Y", p->Y, sizeof(zd) * N * n * L},
         {"S", p->S, sizeof(zd) * K * n * L},        {"mu", p->mu, sizeof(zd) * K * L * L},
         {"sigma", p->sigma, sizeof(double) * p->LM}, {"tnorm", p->tnorm, sizeof(double) * N},
@@ -987,14 +992,54 @@ extern "C" int nep_band_factor(nep_split_t h, int32_t npts, int32_t precision, v
     return NEP_ERR_ARG;
 }
 
+// The narrow-band sweeps read U by columns: the step entry point builds that copy in a
+// stream-ordered temporary for the call.
+template <typename T>
+static int band_solve_step(const SplitDev& s, int npts, const cx<T>* ab, const int* ipiv, int L, cx<T>* B,
+                           cudaStream_t st) {
+    if (!band_sweeps_fit(s.kl, s.ku) || npts <= 0 || L <= 0)
+        return launch_band_solve<T>(s, npts, ab, nullptr, ipiv, L, B, nullptr, st);
+    cx<T>* ut = nullptr;
+    NEP_CUDA(cudaMallocAsync((void**)&ut, sizeof(cx<T>) * (size_t)npts * s.n * (s.kl + s.ku + 1), st));
+    int rc = band_transpose_u<T>(s, npts, ab, ut, st);
+    if (!rc) rc = launch_band_solve<T>(s, npts, ab, ut, ipiv, L, B, nullptr, st);
+    cudaFreeAsync(ut, st);
+    return rc;
+}
+
 extern "C" int nep_band_solve(nep_split_t h, int32_t npts, int32_t precision, const void* ab_dev, const int32_t* ipiv_dev,
                               int32_t L, void* B_dev, void* stream) {
     if (!h || !ab_dev || !ipiv_dev || !B_dev || npts < 0 || L < 0) { set_error("nep_band_solve: bad arguments"); return NEP_ERR_ARG; }
     const SplitDev s = h->dev();
+    if (precision != NEP_PREC_MIXED && precision != NEP_PREC_FP64) { set_error("bad precision"); return NEP_ERR_ARG; }
+    return precision == NEP_PREC_MIXED
+               ? band_solve_step<float>(s, npts, (const zf*)ab_dev, ipiv_dev, L, (zf*)B_dev, (cudaStream_t)stream)
+               : band_solve_step<double>(s, npts, (const zd*)ab_dev, ipiv_dev, L, (zd*)B_dev, (cudaStream_t)stream);
+}
+
+extern "C" int nep_band_transpose_u(nep_split_t h, int32_t npts, int32_t precision, const void* ab_dev, void* ut_dev,
+                                    void* stream) {
+    if (!h || !ab_dev || !ut_dev || npts < 0) { set_error("nep_band_transpose_u: bad arguments"); return NEP_ERR_ARG; }
+    const SplitDev s = h->dev();
+    if (precision == NEP_PREC_MIXED) return band_transpose_u<float>(s, npts, (const zf*)ab_dev, (zf*)ut_dev, (cudaStream_t)stream);
+    if (precision == NEP_PREC_FP64) return band_transpose_u<double>(s, npts, (const zd*)ab_dev, (zd*)ut_dev, (cudaStream_t)stream);
+    set_error("bad precision");
+    return NEP_ERR_ARG;
+}
+
+extern "C" int nep_band_solve_cols(nep_split_t h, int32_t npts, int32_t precision, const void* ab_dev, const void* ut_dev,
+                                   const int32_t* ipiv_dev, int32_t L, void* B_dev, void* stream) {
+    if (!h || !ab_dev || !ipiv_dev || !B_dev || npts < 0 || L < 0) { set_error("nep_band_solve_cols: bad arguments"); return NEP_ERR_ARG; }
+    const SplitDev s = h->dev();
+    if (band_sweeps_fit(s.kl, s.ku) && !ut_dev) {
+        set_error("nep_band_solve_cols: this band needs the column copy of U (nep_band_transpose_u)");
+        return NEP_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
     if (precision == NEP_PREC_MIXED)
-        return launch_band_solve<float>(s, npts, (const zf*)ab_dev, ipiv_dev, L, (zf*)B_dev, nullptr, (cudaStream_t)stream);
+        return launch_band_solve<float>(s, npts, (const zf*)ab_dev, (const zf*)ut_dev, ipiv_dev, L, (zf*)B_dev, nullptr, st);
     if (precision == NEP_PREC_FP64)
-        return launch_band_solve<double>(s, npts, (const zd*)ab_dev, ipiv_dev, L, (zd*)B_dev, nullptr, (cudaStream_t)stream);
+        return launch_band_solve<double>(s, npts, (const zd*)ab_dev, (const zd*)ut_dev, ipiv_dev, L, (zd*)B_dev, nullptr, st);
     set_error("bad precision");
     return NEP_ERR_ARG;
 }

@@ -199,8 +199,16 @@ int launch_assemble(const SplitDev& s, int npts, const zd* F, cx<T>* ab, double*
 // band_lu.cu
 template <typename T>
 int launch_band_lu(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st);
+// Narrow-band substitution sweeps (register windows of kl+1 and kl+ku+1 rows, up to 288).
+inline bool band_sweeps_fit(int kl, int ku) { return kl >= 1 && kl + 1 <= 288 && kl + ku + 1 <= 288; }
+// ut (npts x n x (kl+ku+1)): the U factor by columns, written by band_transpose_u after the LU.
 template <typename T>
-int launch_band_solve(const SplitDev& s, int npts, const cx<T>* ab, const int* ipiv, int L, cx<T>* B,
+int band_sweeps(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* ut, const int* ipiv, int L, cx<T>* B,
+                const int* active, cudaStream_t st);
+template <typename T>
+int band_transpose_u(const SplitDev& s, int npts, const cx<T>* ab, cx<T>* ut, cudaStream_t st);
+template <typename T>
+int launch_band_solve(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* ut, const int* ipiv, int L, cx<T>* B,
                       const int* active, cudaStream_t st);
 // spmv.cu
 int launch_split_residual(const SplitDev& s, int npts, const zd* tval, int L, const zd* V, const zd* Y, zd* R,

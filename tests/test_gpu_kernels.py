@@ -46,6 +46,8 @@ PROBLEMS = {
     "band_70_64_64": lambda: _random_band_problem(70, 64, 64, 6),
     "band_300_70_9": lambda: _random_band_problem(300, 70, 9, 7),
     "band_33_1_1": lambda: _random_band_problem(33, 1, 1, 8),
+    "band_600_128_128": lambda: _random_band_problem(600, 128, 128, 9),   # widest register-window sweeps
+    "band_400_150_150": lambda: _random_band_problem(400, 150, 150, 10),  # beyond them: shared-memory solve
 }
 
 
@@ -167,6 +169,46 @@ def test_band_solve_matches_oracle(bnd, name, precision):
         cond = np.linalg.cond(T)
         tol = 1e-13 * cond if precision == 0 else 5e-6 * cond
         assert err <= max(tol, 1e-12), (err, cond)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["band_150_40_23", "band_600_128_128", "delay2d_s9", "band_400_150_150"])
+def test_transpose_u_and_solve_cols(bnd, name, precision):
+    """U by columns is a pure copy of the factored band; solving with it is bitwise the plain solve."""
+    torch = torch_cuda()
+    p = PROBLEMS[name]()
+    split = bnd.Split.from_problem(p)
+    npts, L = 2, 3
+    z = _points(p, npts)
+    F, _ = bnd.coefficients(split, z)
+    n, ldab, kl, ku = p.n, split.ldab, split.kl, split.ku
+    kv = kl + ku
+    fdt = torch.float64 if precision == 0 else torch.float32
+    ab = torch.zeros(npts * n * ldab * 2, dtype=fdt, device="cuda")
+    bnd.assemble_band(split, npts, to_dev(np.asfortranarray(F), torch), precision, ab)
+    ipiv = torch.zeros(npts * n, dtype=torch.int32, device="cuda")
+    info = torch.zeros(npts, dtype=torch.int32, device="cuda")
+    bnd.band_factor(split, npts, precision, ab, ipiv, info)
+    ut = torch.full((npts * n * (kv + 1) * 2,), float("nan"), dtype=fdt, device="cuda")
+    bnd.band_transpose_u(split, npts, precision, ab, ut)
+    rb = ab.cpu().numpy().view(np.complex128 if precision == 0 else np.complex64).reshape(npts, n, ldab)
+    uc = ut.cpu().numpy().view(np.complex128 if precision == 0 else np.complex64).reshape(npts, n, kv + 1)
+    for c in range(n):
+        d = np.arange(kv + 1)
+        ok = c - d >= 0
+        assert np.array_equal(uc[:, c, d[ok]], rb[:, c - d[ok], d[ok]])
+        assert np.all(uc[:, c, d[~ok]] == 0)
+    V = synth.random_probe_block(n, L, seed=12)
+    Vrep = np.concatenate([np.asfortranarray(V).ravel(order="F")] * npts)
+    B1 = to_dev(Vrep, torch) if precision == 0 else \
+        torch.from_numpy(Vrep.astype(np.complex64).view(np.float32).copy()).cuda()
+    B2 = B1.clone()
+    bnd.band_solve(split, npts, precision, ab, ipiv, L, B1)
+    wide = kl + 1 > 288 or kv + 1 > 288
+    bnd.band_solve_cols(split, npts, precision, ab, None if wide else ut, ipiv, L, B2)
+    torch.cuda.synchronize()
+    assert torch.equal(B1, B2)
+    assert torch.isfinite(B1).all()
 
 
 def test_split_residual_matches_oracle(bnd):

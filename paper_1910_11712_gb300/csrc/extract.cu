@@ -387,7 +387,8 @@ int jacobi_svd(int rows, int cols, zd* A, zd* U, zd* W, double* sigma, JacobiWor
 // graded block Hankel matrices of the contour method, Jacobi on R^H needs several times fewer
 // sweeps than on A itself.
 __global__ void __launch_bounds__(32) qrcp_kernel(int rows, int cols, zd* __restrict__ A, zd* __restrict__ tau,
-                                                  int* __restrict__ perm, double* __restrict__ nrm2, GridBar bar) {
+                                                  int* __restrict__ perm, double* __restrict__ nrm2, double stop2,
+                                                  int* __restrict__ steps_out, GridBar bar) {
     const int lane = threadIdx.x;
     const int G = gridDim.x;
     unsigned int epoch = 0;
@@ -403,21 +404,33 @@ __global__ void __launch_bounds__(32) qrcp_kernel(int rows, int cols, zd* __rest
     }
     grid_barrier(bar, epoch);
     const int steps = min(rows, cols);
+    double first = 0.0;  // |R_00|^2
+    int done = steps;
     for (int k = 0; k < steps; ++k) {
+        // pivot: first index of the largest remaining norm among columns k..cols-1 (every CTA
+        // finds the same one, so all agree on stopping)
+        double best = -1.0, rest = 0.0;
+        int bi = cols;
+        for (int j = k + lane; j < cols; j += 32) {
+            const double v = ldcg(nrm2 + j);
+            rest += v;
+            if (v > best) { best = v; bi = j; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            rest += __shfl_xor_sync(0xffffffffu, rest, o);
+        }
+        if (k == 0) first = best;
+        // ||R_22||_F^2 (the sum of the remaining squared column norms) <= stop2 |R_00|^2: dropping
+        // the trailing block moves no singular value by more than sqrt(stop2) |R_00|
+        if (rest <= stop2 * first) {
+            done = k;
+            break;
+        }
         const int owner = k % G;
         if ((int)blockIdx.x == owner) {
-            // pivot: first index of the largest remaining norm among columns k..cols-1
-            double best = -1.0;
-            int bi = cols;
-            for (int j = k + lane; j < cols; j += 32) {
-                const double v = ldcg(nrm2 + j);
-                if (v > best) { best = v; bi = j; }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-            }
             const int p = bi;
             zd* ak = A + (int64_t)k * rows;
             if (p != k) {
@@ -427,10 +440,9 @@ __global__ void __launch_bounds__(32) qrcp_kernel(int rows, int cols, zd* __rest
                     ak[i] = ldcg(ap + i);
                     ap[i] = t;
                 }
+                // nrm2 is not swapped: the other CTAs may still be searching it, and every
+                // column j > k gets its remaining norm recomputed after the barrier anyway
                 if (lane == 0) {
-                    const double tn = ldcg(nrm2 + k);
-                    nrm2[k] = ldcg(nrm2 + p);
-                    nrm2[p] = tn;
                     const int tp = __ldcg(perm + k);
                     perm[k] = __ldcg(perm + p);
                     perm[p] = tp;
@@ -482,14 +494,34 @@ __global__ void __launch_bounds__(32) qrcp_kernel(int rows, int cols, zd* __rest
         }
         grid_barrier(bar, epoch);
     }
+    if (blockIdx.x == 0) {
+        for (int k = done + lane; k < steps; k += 32) tau[k] = mk(0.0, 0.0);  // H_k = I beyond the stop
+        if (lane == 0) *steps_out = done;
+    }
 }
 
 // R^H of the upper triangle of A (n x n): Rh(i, j) = conj(A(j, i)) for i >= j, 0 above.
-__global__ void rh_from_qr_kernel(int n, const zd* __restrict__ A, zd* __restrict__ Rh) {
+__global__ void rh_from_qr_kernel(int n, int ncols, const zd* __restrict__ A, zd* __restrict__ Rh) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)n * n) return;
+    if (t >= (int64_t)n * ncols) return;
     const int i = (int)(t % n), j = (int)(t / n);
     Rh[t] = i >= j ? conj(A[j + (int64_t)n * i]) : mk(0.0, 0.0);
+}
+
+// U(:, c) = [Wj(:, c); 0] for c < mq (Wj: mq x mq), zero columns c >= mq of U and W, sigma[c] = 0
+// for c >= mq: the singular triplets of the dropped trailing block are reported as zero.
+__global__ void qr_pad_kernel(int n, int mq, const zd* __restrict__ Wj, zd* __restrict__ U, zd* __restrict__ W,
+                              double* __restrict__ sigma) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * n) return;
+    const int i = (int)(t % n), c = (int)(t / n);
+    if (c < mq) {
+        U[t] = i < mq ? Wj[i + (int64_t)mq * c] : mk(0.0, 0.0);
+    } else {
+        U[t] = mk(0.0, 0.0);
+        W[t] = mk(0.0, 0.0);
+        if (i == 0) sigma[c] = 0.0;
+    }
 }
 
 // X <- Q X with Q = H_0 H_1 ... H_{n-1} from qrcp_kernel (reflectors below the diagonal of A):
@@ -526,9 +558,13 @@ __global__ void permute_rows_kernel(int n, int ncols, const int* __restrict__ pe
 }
 
 // SVD of a square n x n matrix A (destroyed) preconditioned by QR with column pivoting:
-// A P = Q R, one-sided Jacobi on R^H = Uj Sigma Wj^H, then A = (Q Wj) Sigma (P Uj)^H.
-int qrcp_jacobi_svd(int n, zd* A, zd* U, zd* W, double* sigma, zd* work1, zd* work2, zd* tau, int* perm,
-                    double* nrm2, JacobiWork w, cudaStream_t st) {
+// A P = Q R, one-sided Jacobi on R^H = Uj Sigma Wj^H, then A = (Q Wj) Sigma (P Uj)^H. The QR stops
+// at the first step mq where the trailing block R_22 (rows and columns mq..n-1) has Frobenius
+// norm <= trunc |R_00|: its rows of R are dropped, which moves every singular value by at most
+// ||R_22||_2 <= trunc |R_00| <= trunc sigma_1 (Weyl), and Jacobi runs on the n x mq matrix
+// R(0:mq, :)^H only. Singular values and vectors beyond mq are returned as zero.
+int qrcp_jacobi_svd(int n, zd* A, zd* U, zd* W, double* sigma, zd* work1, zd* work2, zd* work3, zd* tau, int* perm,
+                    double* nrm2, int* steps_dev, int* steps_host, double trunc, JacobiWork w, cudaStream_t st) {
     if (n <= 0) return NEP_OK;
     NEP_CUDA(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st));
     int dev = 0, sms = 0;
@@ -539,17 +575,27 @@ int qrcp_jacobi_svd(int n, zd* A, zd* U, zd* W, double* sigma, zd* work1, zd* wo
     int blocks = std::max(1, std::min(n, sms * std::max(per_sm, 1)));
     GridBar gb{w.bar, w.bar + 1, w.err};
     int rows = n, cols = n;
-    void* args[] = {&rows, &cols, &A, &tau, &perm, &nrm2, &gb};
+    double stop2 = trunc * trunc;
+    void* args[] = {&rows, &cols, &A, &tau, &perm, &nrm2, &stop2, &steps_dev, &gb};
     NEP_CUDA(cudaLaunchCooperativeKernel((const void*)qrcp_kernel, dim3(blocks), dim3(32), args, 0, st));
     count_launch();
-    rh_from_qr_kernel<<<ceil_div((int64_t)n * n, 256), 256, 0, st>>>(n, A, work1);
+    NEP_CUDA(cudaMemcpyAsync(steps_host, steps_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NEP_CUDA(cudaStreamSynchronize(st));
+    const int mq = std::max(0, std::min(n, *steps_host));
+    if (mq > 0) {
+        rh_from_qr_kernel<<<ceil_div((int64_t)n * mq, 256), 256, 0, st>>>(n, mq, A, work1);
+        NEP_CHECK_LAUNCH();
+        // Jacobi on R(0:mq, :)^H: work1 -> Uj (work2, n x mq), Wj (work3, mq x mq)
+        NEP_TRY(jacobi_svd(n, mq, work1, work2, work3, sigma, w, st));
+    }
+    qr_pad_kernel<<<ceil_div((int64_t)n * n, 256), 256, 0, st>>>(n, mq, work3, U, W, sigma);
     NEP_CHECK_LAUNCH();
-    // Jacobi on R^H: work1 -> Uj (work2), Wj (U)
-    NEP_TRY(jacobi_svd(n, n, work1, work2, U, sigma, w, st));
-    apply_q_kernel<<<ceil_div(n, 4), 128, 0, st>>>(n, n, A, tau, n, U);
-    NEP_CHECK_LAUNCH();
-    permute_rows_kernel<<<ceil_div((int64_t)n * n, 256), 256, 0, st>>>(n, n, perm, work2, W);
-    NEP_CHECK_LAUNCH();
+    if (mq > 0) {
+        apply_q_kernel<<<ceil_div(mq, 4), 128, 0, st>>>(n, mq, A, tau, mq, U);
+        NEP_CHECK_LAUNCH();
+        permute_rows_kernel<<<ceil_div((int64_t)n * mq, 256), 256, 0, st>>>(n, mq, perm, work2, W);
+        NEP_CHECK_LAUNCH();
+    }
     return NEP_OK;
 }
 
@@ -1256,11 +1302,16 @@ __global__ void __launch_bounds__(256) newton_kernel(SplitDev s, int k, const zd
             const zf pv = J[col + (int64_t)K1 * col];
             for (int r = col + 1 + tid; r < K1; r += blockDim.x) g[r] = cdiv(J[r + (int64_t)K1 * col], pv);
             __syncthreads();
-            const int nr = K1 - col - 1;
-            for (int e = tid; e < nr * (nr + 1); e += blockDim.x) {
-                const int r = col + 1 + e % nr, q = col + 1 + e / nr;
-                if (q < K1) J[r + (int64_t)K1 * q] = fms(J[r + (int64_t)K1 * q], g[r], J[col + (int64_t)K1 * q]);
-                else rhs[r] = fms(rhs[r], g[r], rhs[col]);
+            // trailing update: warps over columns (the right-hand side as column K1), lanes over rows
+            for (int q = col + 1 + w; q <= K1; q += nw) {
+                if (q < K1) {
+                    const zf u = J[col + (int64_t)K1 * q];
+                    zf* jq = J + (int64_t)K1 * q;
+                    for (int r = col + 1 + lane; r < K1; r += 32) jq[r] = fms(jq[r], g[r], u);
+                } else {
+                    const zf u = rhs[col];
+                    for (int r = col + 1 + lane; r < K1; r += 32) rhs[r] = fms(rhs[r], g[r], u);
+                }
             }
             __syncthreads();
         }

@@ -719,7 +719,13 @@ static int run_extract(nep_plan* p, cudaStream_t st) {
     NEP_CUDA(cudaEventRecord(p->ev[4], st));
     // SVD of H and numerical rank
     NEP_CUDA(cudaMemcpyAsync(p->Hw, p->H, sizeof(zd) * LM * LM, cudaMemcpyDeviceToDevice, st));
-    NEP_TRY(qrcp_jacobi_svd(LM, p->Hw, p->U, p->W, p->sigma, p->T1, p->Bred, p->theta, p->its, p->lamg, p->jw, st));
+    // the QR preconditioner drops the trailing block of R once its Frobenius norm is below
+    // 1e-14 |R_00| (and 1e-2 of the rank tolerance): singular values move by at most 1e-14
+    // sigma_1, the size of the FP64 rounding error of a dense SVD of this order (n eps sigma_1),
+    // and Jacobi runs only on the numerically nonzero part
+    const double trunc = std::min(1e-14, 1e-2 * p->o.rank_tol);
+    NEP_TRY(qrcp_jacobi_svd(LM, p->Hw, p->U, p->W, p->sigma, p->T1, p->Bred, p->Tv, p->theta, p->its, p->lamg,
+                            p->scalars + 2, p->h_pinned + 8, trunc, p->jw, st));
     NEP_TRY(launch_rank(LM, p->sigma, p->o.rank_tol, p->scalars, st));
     int m = 0;
     NEP_TRY(read_scalar(p, p->scalars, &m, st));

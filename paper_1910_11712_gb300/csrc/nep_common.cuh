@@ -240,8 +240,8 @@ struct JacobiWork {
     int* err;
 };
 int jacobi_svd(int rows, int cols, zd* A, zd* U, zd* W, double* sigma, JacobiWork w, cudaStream_t st);
-int qrcp_jacobi_svd(int n, zd* A, zd* U, zd* W, double* sigma, zd* work1, zd* work2, zd* tau, int* perm,
-                    double* nrm2, JacobiWork w, cudaStream_t st);
+int qrcp_jacobi_svd(int n, zd* A, zd* U, zd* W, double* sigma, zd* work1, zd* work2, zd* work3, zd* tau, int* perm,
+                    double* nrm2, int* steps_dev, int* steps_host, double trunc, JacobiWork w, cudaStream_t st);
 template <typename T>
 int small_eig(int m, const zd* A, zd* eval, zd* evec, int* status, void* gbuf, cudaStream_t st);
 template <typename T>

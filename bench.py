@@ -117,7 +117,7 @@ def solve_bytes(n, ldab, L, npts, esz):
 
 # DRAM bytes (read + write) of one solve launch from an ncu capture of the same launch,
 # keyed by (workload, precision); None where no capture of the current kernel exists.
-SOLVE_TRAFFIC = {}
+SOLVE_TRAFFIC = {("delay2d_s64", "mixed"): (199.0 + 24.8 + 303.7 + 29.2) * 1e6}
 
 
 def fp32_alu_peak_tflops(sm_mhz):

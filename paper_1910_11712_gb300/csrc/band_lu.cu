@@ -44,14 +44,15 @@ __device__ __forceinline__ int warp_pivot(const cx<T>* pcol, int cnt, int lane) 
         // index among the lanes holding it (two warp reductions)
         const unsigned mb = best < 0 ? 0u : __float_as_uint(best);
         const unsigned mx = __reduce_max_sync(0xffffffffu, mb);
-        return (int)__reduce_min_sync(0xffffffffu, mb == mx ? (unsigned)bi : 0xffffffffu);
+        const int p = (int)__reduce_min_sync(0xffffffffu, mb == mx ? (unsigned)bi : 0xffffffffu);
+        return p < cnt ? p : 0;  // a column of NaNs matches no row: keep the diagonal
     } else {
         for (int o = 16; o > 0; o >>= 1) {
             T ob = __shfl_xor_sync(0xffffffffu, best, o);
             int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
-        return bi;
+        return bi < cnt ? bi : 0;
     }
 }
 

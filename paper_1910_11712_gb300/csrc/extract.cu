@@ -422,6 +422,7 @@ __global__ void __launch_bounds__(32) qrcp_kernel(int rows, int cols, zd* __rest
             if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
             rest += __shfl_xor_sync(0xffffffffu, rest, o);
         }
+        if (bi >= cols) bi = k;  // NaN norms match no column
         if (k == 0) first = best;
         // ||R_22||_F^2 (the sum of the remaining squared column norms) <= stop2 |R_00|^2: dropping
         // the trailing block moves no singular value by more than sqrt(stop2) |R_00|
@@ -1149,7 +1150,7 @@ __global__ void __launch_bounds__(256) normalize_columns_kernel(int rows, zd* __
             if (rmax[k] > tb || (rmax[k] == tb && redi[k] < ti)) { tb = rmax[k]; ti = redi[k]; }
         }
         red[0] = ts;
-        redi[0] = ti;
+        redi[0] = ti < rows ? ti : 0;  // NaN entries match no index
     }
     __syncthreads();
     const double nrm = sqrt(red[0]);

@@ -172,8 +172,10 @@ int nep_plan_create(nep_split_t h, const nep_region *r, int32_t N, int32_t L, in
 int nep_plan_execute(nep_plan_t p, const void *V_dev, void *stream);
 int nep_plan_result(nep_plan_t p, nep_result_t *out);
 int nep_plan_destroy(nep_plan_t p);
-/* Device buffers of a plan (for inspection/tests): name in {"F","coef","ab","ipiv","info",
- * "Y","S","mu","sigma","tnorm","beta","sweeps"}; returns the device pointer and its bytes. */
+/* Device buffers of a plan (for inspection/tests): name in {"F","coef","ab","ut","ipiv","info",
+ * "Y","S","mu","sigma","tnorm","beta","sweeps","H","newton_its","newton_ok","candidates",
+ * "newton_lambda"}; returns the device pointer and its bytes ("ut" is empty for bands too wide
+ * for the narrow-band sweeps). */
 int nep_plan_buffer(nep_plan_t p, const char *name, void **dev_ptr, size_t *bytes);
 
 /* ------------------------------------------------------------------ serving */

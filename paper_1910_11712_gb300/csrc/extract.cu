@@ -1183,32 +1183,83 @@ __global__ void term_spmm_kernel(SplitDev s, int k, const zd* __restrict__ Q, zd
 }
 
 // ------------------------------------------------------------------ Newton on the projected NEP
-// One CTA per candidate. Each step evaluates f_i, f_i' and the residual B(l) y in FP64, builds
-// the bordered Jacobian J = [[B(l), B'(l) y], [y^H, 0]] rounded to complex64 and solves
-// J [dy; dl] = -[B(l) y; 0] by Gaussian elimination with partial pivoting in FP32. Because the
-// residual is FP64, the iteration converges to the FP64 solution; the FP32 Jacobian only makes
-// the convergence linear with a rate ~ kappa(J) * 6e-8 instead of quadratic.
-__global__ void __launch_bounds__(256) newton_kernel(SplitDev s, int k, const zd* __restrict__ Bs,
-                                                     const zd* __restrict__ lam0, const zd* __restrict__ Y0, int ldy0,
-                                                     zd c, double rad, int maxit, double tol,
-                                                     zd* __restrict__ lam_out, zd* __restrict__ Yout,
+// One CTA per candidate. Each step evaluates f_i, f_i' at l, forms the residual B(l) y and
+// B'(l) y from the products v_i = B_i y, builds the bordered Jacobian
+// J = [[B(l), B'(l) y], [y^H, 0]] in complex64 and solves J [dy; dl] = -[B(l) y; 0] by Gaussian
+// elimination with partial pivoting in FP32 (rows are never moved: the pivot row of each
+// column is recorded and later columns skip it; one CTA barrier per column, the next pivot
+// found by the warp that updated that column). While the step is large, the residual is formed
+// in FP32 from the complex64 copies of the B_i: the iterate is then far from the FP64 fixed
+// point anyway. Once |dl| <= 1e-5 max(1, |l|), or the FP32 steps stop shrinking below 1e-3, the
+// residual is formed in FP64 from the FP64 B_i and y, so the iteration converges to the FP64
+// solution (the FP32 Jacobian only makes that final convergence linear, rate ~ kappa(J) 6e-8).
+// The stopping test |dl| <= tol max(1, |l|) is applied to FP64 steps only.
+__device__ __forceinline__ zf shfl_cx32(zf v, int src) {
+    return mk(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
+}
+struct NewtonLayout {
+    size_t J, rhs, rpv, y32, B32, y, fv, vb, prow, used, total;
+};
+__host__ __device__ inline NewtonLayout newton_layout(int k, int nterms) {
+    const size_t K1 = (size_t)k + 1;
+    NewtonLayout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += (bytes + 15) / 16 * 16;
+        return at;
+    };
+    L.J = take(sizeof(zf) * K1 * K1);
+    L.rhs = take(sizeof(zf) * K1);
+    L.rpv = take(sizeof(zf) * K1);
+    L.y32 = take(sizeof(zf) * K1);
+    L.B32 = take(sizeof(zf) * (size_t)nterms * k * k);
+    L.y = take(sizeof(zd) * K1);
+    L.fv = take(sizeof(zd) * 2 * (size_t)nterms);
+    L.vb = take(sizeof(zd) * (size_t)nterms * k);
+    L.prow = take(sizeof(int) * K1);
+    L.used = take(sizeof(int) * K1);
+    L.total = o;
+    return L;
+}
+size_t newton_scratch_bytes(int k, int nterms) { return newton_layout(k, nterms).total; }
+
+__global__ void convert_c64_kernel(int64_t count, const zd* __restrict__ in, zf* __restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count) out[t] = cvt<float>(in[t]);
+}
+
+template <int MB>  // rows per lane in the elimination: K1 <= 32 MB
+__global__ void __launch_bounds__(256, 1) newton_kernel(SplitDev s, int k, const zd* __restrict__ Bs,
+                                                     const zf* __restrict__ Bs32, const zd* __restrict__ lam0,
+                                                     const zd* __restrict__ Y0, int ldy0, zd c, double rad, int maxit,
+                                                     double tol, zd* __restrict__ lam_out, zd* __restrict__ Yout,
                                                      int* __restrict__ ok_out, int* __restrict__ its_out,
-                                                     zd* __restrict__ gscratch, int use_smem) {
+                                                     unsigned char* __restrict__ gscratch, int use_smem) {
     extern __shared__ unsigned char sraw[];
     const int cand = blockIdx.x;
-    const int K1 = k + 1;
-    unsigned char* base = use_smem ? sraw : reinterpret_cast<unsigned char*>(gscratch + (int64_t)cand * newton_scratch_elems(k));
-    zf* J = reinterpret_cast<zf*>(base);           // K1 x K1 complex64
-    zf* rhs = J + (int64_t)K1 * K1;                 // K1
-    zf* g = rhs + K1;                               // K1 (multipliers)
-    zd* y = reinterpret_cast<zd*>(g + K1 + (K1 & 1));  // k (FP64 iterate)
-    zd* fv = y + K1;                                 // 2 * nterms <= 64
+    const int K1 = k + 1, nt = s.nterms;
+    const NewtonLayout lay = newton_layout(k, nt);
+    unsigned char* base = use_smem ? sraw : gscratch + (int64_t)cand * lay.total;
+    zf* J = reinterpret_cast<zf*>(base + lay.J);      // K1 x K1, column-major
+    zf* rhs = reinterpret_cast<zf*>(base + lay.rhs);  // K1
+    zf* rpv = reinterpret_cast<zf*>(base + lay.rpv);  // 1 / pivot of each column
+    zf* y32 = reinterpret_cast<zf*>(base + lay.y32);  // complex64 copy of y
+    zf* B32 = reinterpret_cast<zf*>(base + lay.B32);  // nt x k x k
+    zd* y = reinterpret_cast<zd*>(base + lay.y);      // FP64 iterate
+    zd* fv = reinterpret_cast<zd*>(base + lay.fv);    // f_i, f_i'
+    zd* vb = reinterpret_cast<zd*>(base + lay.vb);    // v_i = B_i y, nt x k
+    int* prow = reinterpret_cast<int*>(base + lay.prow);
+    int* used = reinterpret_cast<int*>(base + lay.used);
     __shared__ double redd[32];
-    __shared__ int piv_s;
-    __shared__ int stop_s;
+    __shared__ zf f32s[32];
+    __shared__ int stop_s, fp64_s, sing_s;
     __shared__ zd lam_s;
+    __shared__ double dprev_s;
     const int tid = threadIdx.x;
     const int lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+
+    for (int64_t e = tid; e < (int64_t)nt * k * k; e += blockDim.x) B32[e] = Bs32[e];
     double ss = 0.0;
     for (int i = tid; i < k; i += blockDim.x) {
         y[i] = Y0[(int64_t)cand * ldy0 + i];
@@ -1223,41 +1274,72 @@ __global__ void __launch_bounds__(256) newton_kernel(SplitDev s, int k, const zd
         redd[0] = t;
         lam_s = lam0[cand];
         stop_s = 0;
+        fp64_s = 0;
+        dprev_s = 0.0;
     }
     __syncthreads();
     {
         const double inv = redd[0] > 0 ? 1.0 / sqrt(redd[0]) : 0.0;
-        for (int i = tid; i < k; i += blockDim.x) y[i] = inv * y[i];
+        for (int i = tid; i < k; i += blockDim.x) {
+            y[i] = inv * y[i];
+            y32[i] = cvt<float>(y[i]);
+        }
     }
     int ok = redd[0] > 0, it = 0;
     __syncthreads();
     for (it = 1; it <= maxit && ok; ++it) {
-        if (tid < s.nterms) {
+        const bool fp64 = fp64_s != 0;
+        if (tid < nt) {
             const FnEval fe = fn_eval(s.fn_nodes, s.fn_coef, s.fn_root[tid], lam_s);
             fv[tid] = fe.f;
-            fv[s.nterms + tid] = fe.df;
+            fv[nt + tid] = fe.df;
         }
+        for (int r = tid; r < K1; r += blockDim.x) used[r] = 0;
+        // v_i = B_i y, one (row, term) per thread: FP64 near the solution, FP32 before
+        for (int e = tid; e < nt * k; e += blockDim.x) {
+            const int i = e / k, r = e - i * k;
+            zd v;
+            if (fp64) {
+                const zd* Bi = Bs + (int64_t)i * k * k + r;
+                zd v0 = mk(0.0, 0.0), v1 = mk(0.0, 0.0);
+                int q = 0;
+#pragma unroll 4
+                for (; q + 1 < k; q += 2) {
+                    v0 = fma_(v0, Bi[(int64_t)k * q], y[q]);
+                    v1 = fma_(v1, Bi[(int64_t)k * (q + 1)], y[q + 1]);
+                }
+                if (q < k) v0 = fma_(v0, Bi[(int64_t)k * q], y[q]);
+                v = v0 + v1;
+            } else {
+                const zf* Bi = B32 + (int64_t)i * k * k + r;
+                zf v0 = mk(0.0f, 0.0f), v1 = mk(0.0f, 0.0f);
+                int q = 0;
+#pragma unroll 4
+                for (; q + 1 < k; q += 2) {
+                    v0 = fma_(v0, Bi[(int64_t)k * q], y32[q]);
+                    v1 = fma_(v1, Bi[(int64_t)k * (q + 1)], y32[q + 1]);
+                }
+                if (q < k) v0 = fma_(v0, Bi[(int64_t)k * q], y32[q]);
+                v = cvt<double>(v0 + v1);
+            }
+            vb[(int64_t)i * k + r] = v;
+        }
+        if (tid < nt) f32s[tid] = cvt<float>(fv[tid]);
         __syncthreads();
-        // J(0:k, 0:k) = B(l) assembled in FP32 (it only steers the correction); the residual
-        // rhs = -B(l) y and J(0:k, k) = B'(l) y come from v_i = B_i y in FP64
-        {
-            zf f32[32];
-            for (int i = 0; i < s.nterms; ++i) f32[i] = cvt<float>(fv[i]);
-            for (int e = tid; e < k * k; e += blockDim.x) {
-                const int r = e % k, q = e / k;
+        // J(0:k, 0:k) = B(l) in FP32 (warps over columns, lanes over rows); J(0:k, k) = B'(l) y,
+        // rhs = -B(l) y; the border row y^H
+        for (int q = w; q < k; q += nw)
+            for (int r = lane; r < k; r += 32) {
                 zf b = mk(0.0f, 0.0f);
-                for (int i = 0; i < s.nterms; ++i) b = fma_(b, f32[i], cvt<float>(Bs[(int64_t)i * k * k + e]));
+                for (int i = 0; i < nt; ++i) b = fma_(b, f32s[i], B32[(int64_t)i * k * k + r + (int64_t)k * q]);
                 J[r + (int64_t)K1 * q] = b;
             }
-        }
         for (int r = tid; r < k; r += blockDim.x) {
             zd bd = mk(0.0, 0.0), gd = mk(0.0, 0.0);
-            for (int i = 0; i < s.nterms; ++i) {
-                const zd* Bi = Bs + (int64_t)i * k * k + r;
-                zd v = mk(0.0, 0.0);
-                for (int q = 0; q < k; ++q) v = fma_(v, Bi[(int64_t)k * q], y[q]);
+            for (int i = 0; i < nt; ++i) {
+                const zd v = vb[(int64_t)i * k + r];
                 bd = fma_(bd, fv[i], v);
-                gd = fma_(gd, fv[s.nterms + i], v);
+                gd = fma_(gd, fv[nt + i], v);
             }
             rhs[r] = cvt<float>(-bd);
             J[r + (int64_t)K1 * k] = cvt<float>(gd);
@@ -1266,73 +1348,128 @@ __global__ void __launch_bounds__(256) newton_kernel(SplitDev s, int k, const zd
         if (tid == 0) {
             J[k + (int64_t)K1 * k] = mk(0.0f, 0.0f);
             rhs[k] = mk(0.0f, 0.0f);
+            sing_s = 0;
         }
         __syncthreads();
-        int singular = 0;
+        // Gaussian elimination with row indirection. A lane keeps its rows r = lane + 32 b
+        // (b < nb) in registers while it sweeps the columns of its warp; the multipliers of a
+        // column are formed once per lane. Warp 0 takes column col+1 first and finds its pivot
+        // (the first row maximising |Re|+|Im| among the rows that are not pivots yet) from the
+        // values it has just computed.
+        const int nb = (K1 + 31) >> 5;  // <= MB
+        // value of row r from the lane that holds it (all lanes call)
+        auto v_at = [&](const zf (&v)[MB], int r) {
+            const int br = r >> 5;
+            zf own = v[0];
+#pragma unroll
+            for (int b2 = 1; b2 < MB; ++b2)
+                if (b2 == br) own = v[b2];
+            return shfl_cx32(own, r & 31);
+        };
+        auto pick = [&](const zf (&v)[MB], const bool (&act)[MB], int col) {
+            float best = -1.0f;
+            int bi = K1;
+#pragma unroll
+            for (int b2 = 0; b2 < MB; ++b2)
+                if (b2 < nb && act[b2]) {
+                    const float a = abs1(v[b2]);
+                    if (a > best) { best = a; bi = lane + 32 * b2; }
+                }
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            const bool okp = best > 0.0f && bi < K1;  // the same in every lane after the butterfly
+            const zf pv = v_at(v, okp ? bi : 0);
+            if (lane == 0) {
+                prow[col] = okp ? bi : -1;
+                if (okp) rpv[col] = cdiv(mk(1.0f, 0.0f), pv);
+            }
+        };
+        if (w == 0) {
+            zf v[MB];
+            bool act[MB];
+#pragma unroll
+            for (int b2 = 0; b2 < MB; ++b2) {
+                const int r = lane + 32 * b2;
+                act[b2] = b2 < nb && r < K1;
+                v[b2] = act[b2] ? J[r] : mk(0.0f, 0.0f);
+            }
+            pick(v, act, 0);
+        }
+        __syncthreads();
         for (int col = 0; col < K1; ++col) {
-            if (w == 0) {
-                float best = -1.0f;
-                int bi = col;
-                for (int r = col + lane; r < K1; r += 32) {
-                    const float a = abs1(J[r + (int64_t)K1 * col]);
-                    if (a > best) { best = a; bi = r; }
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-                }
-                if (lane == 0) piv_s = best > 0 ? bi : -1;
+            const int p = prow[col];
+            if (p < 0) break;  // uniform: every thread reads the same value after the barrier
+            const zf rp = rpv[col];
+            // rows that are not pivots yet (row p is excluded explicitly: its used flag is set
+            // during this phase) and their multipliers
+            bool act[MB];
+            zf g[MB];
+#pragma unroll
+            for (int b2 = 0; b2 < MB; ++b2) {
+                const int r = lane + 32 * b2;
+                act[b2] = b2 < nb && r < K1 && r != p && !used[r];
+                g[b2] = act[b2] ? J[r + (int64_t)K1 * col] * rp : mk(0.0f, 0.0f);
             }
-            __syncthreads();
-            const int p = piv_s;
-            if (p < 0) { singular = 1; break; }
-            if (p != col) {
-                for (int q = col + tid; q < K1; q += blockDim.x) {
-                    const zf t = J[col + (int64_t)K1 * q];
-                    J[col + (int64_t)K1 * q] = J[p + (int64_t)K1 * q];
-                    J[p + (int64_t)K1 * q] = t;
-                }
-                if (tid == 0) {
-                    const zf t = rhs[col];
-                    rhs[col] = rhs[p];
-                    rhs[p] = t;
-                }
-            }
-            __syncthreads();
-            const zf pv = J[col + (int64_t)K1 * col];
-            for (int r = col + 1 + tid; r < K1; r += blockDim.x) g[r] = cdiv(J[r + (int64_t)K1 * col], pv);
-            __syncthreads();
-            // trailing update: warps over columns (the right-hand side as column K1), lanes over rows
             for (int q = col + 1 + w; q <= K1; q += nw) {
-                if (q < K1) {
-                    const zf u = J[col + (int64_t)K1 * q];
-                    zf* jq = J + (int64_t)K1 * q;
-                    for (int r = col + 1 + lane; r < K1; r += 32) jq[r] = fms(jq[r], g[r], u);
-                } else {
-                    const zf u = rhs[col];
-                    for (int r = col + 1 + lane; r < K1; r += 32) rhs[r] = fms(rhs[r], g[r], u);
-                }
+                zf* jq = q < K1 ? J + (int64_t)K1 * q : rhs;
+                const zf u = jq[p];
+                zf v[MB];
+#pragma unroll
+                for (int b2 = 0; b2 < MB; ++b2)
+                    if (act[b2]) v[b2] = jq[lane + 32 * b2];
+#pragma unroll
+                for (int b2 = 0; b2 < MB; ++b2)
+                    if (act[b2]) {
+                        v[b2] = fms(v[b2], g[b2], u);
+                        jq[lane + 32 * b2] = v[b2];
+                    }
+                if (w == 0 && q == col + 1 && q < K1) pick(v, act, q);
             }
+            if (tid == 0) used[p] = 1;
             __syncthreads();
         }
-        if (singular) { ok = 0; break; }
+        // singular bordered system (some column had no nonzero pivot)
+        if (tid == 0) {
+            int sg = 0;
+            for (int col = 0; col < K1; ++col) sg |= prow[col] < 0;
+            sing_s = sg;
+        }
+        __syncthreads();
+        if (sing_s) { ok = 0; break; }
+        // back substitution in pivot order (warp 0): lane holds the transformed right-hand sides of
+        // the pivots i = lane + 32 b; x_col = rhs(col) / U(col, col), then every earlier pivot row
+        // drops x_col times its entry in column col. The solution goes to y32 (rebuilt below).
         if (w == 0) {
-            for (int r = K1 - 1; r >= 0; --r) {
-                zf acc = mk(0.0f, 0.0f);
-                for (int q = r + 1 + lane; q < K1; q += 32) acc = fma_(acc, J[r + (int64_t)K1 * q], rhs[q]);
-                for (int o = 16; o > 0; o >>= 1) {
-                    acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
-                    acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+            zf rv[MB];
+            int pr[MB];
+#pragma unroll
+            for (int b2 = 0; b2 < MB; ++b2) {
+                const int i = lane + 32 * b2;
+                pr[b2] = (b2 < nb && i < K1) ? prow[i] : 0;
+                rv[b2] = (b2 < nb && i < K1) ? rhs[pr[b2]] : mk(0.0f, 0.0f);
+            }
+            for (int col = K1 - 1; col >= 0; --col) {
+                const int bc = col >> 5, lc = col & 31;
+                zf own = rv[0];
+#pragma unroll
+                for (int b2 = 1; b2 < MB; ++b2)
+                    if (b2 == bc) own = rv[b2];
+                const zf x = shfl_cx32(own, lc) * rpv[col];
+                if (lane == lc) y32[col] = x;
+#pragma unroll
+                for (int b2 = 0; b2 < MB; ++b2) {
+                    const int i = lane + 32 * b2;
+                    if (b2 < nb && i < col) rv[b2] = fms(rv[b2], J[pr[b2] + (int64_t)K1 * col], x);
                 }
-                if (lane == 0) rhs[r] = cdiv(rhs[r] - acc, J[r + (int64_t)K1 * r]);
-                __syncwarp();
             }
         }
         __syncthreads();
         double s2 = 0.0;
         for (int i = tid; i < k; i += blockDim.x) {
-            y[i] = y[i] + cvt<double>(rhs[i]);
+            y[i] = y[i] + cvt<double>(y32[i]);
             s2 += norm2(y[i]);
         }
         for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
@@ -1343,18 +1480,24 @@ __global__ void __launch_bounds__(256) newton_kernel(SplitDev s, int k, const zd
             double t = 0;
             for (int q = 0; q < nw; ++q) t += redd[q];
             redd[0] = t;
-            const zd dl = cvt<double>(rhs[k]);
+            const zd dl = cvt<double>(y32[k]);
             const zd nl = lam_s + dl;
             lam_s = nl;
-            const double al = hypot(nl.re, nl.im);
+            const double al = hypot(nl.re, nl.im), ad = hypot(dl.re, dl.im);
             int st = 0;
             if (!isfinite(nl.re) || !isfinite(nl.im) || hypot(nl.re - c.re, nl.im - c.im) > rad || !(t > 0)) st = 2;
-            else if (hypot(dl.re, dl.im) <= tol * fmax(1.0, al)) st = 1;
+            else if (fp64 && ad <= tol * fmax(1.0, al)) st = 1;
+            if (!fp64 && (ad <= 1e-5 * fmax(1.0, al) || (it > 2 && ad > 0.5 * dprev_s && ad <= 1e-3 * fmax(1.0, al))))
+                fp64_s = 1;
+            dprev_s = ad;
             stop_s = st;
         }
         __syncthreads();
         const double inv = redd[0] > 0 ? 1.0 / sqrt(redd[0]) : 0.0;
-        for (int i = tid; i < k; i += blockDim.x) y[i] = inv * y[i];
+        for (int i = tid; i < k; i += blockDim.x) {
+            y[i] = inv * y[i];
+            y32[i] = cvt<float>(y[i]);
+        }
         __syncthreads();
         if (stop_s == 2) { ok = 0; break; }
         if (stop_s == 1) break;
@@ -1367,20 +1510,30 @@ __global__ void __launch_bounds__(256) newton_kernel(SplitDev s, int k, const zd
     }
 }
 
-int launch_newton(const SplitDev& s, int k, int ncand, const zd* Bs, const zd* lam0, const zd* Y0, int ldy0, zd c,
-                  double rad, int maxit, double tol, zd* lam_out, zd* Yout, int* ok, int* its, zd* gscratch,
-                  cudaStream_t st) {
+int launch_newton(const SplitDev& s, int k, int ncand, const zd* Bs, zf* Bs32, const zd* lam0, const zd* Y0, int ldy0,
+                  zd c, double rad, int maxit, double tol, zd* lam_out, zd* Yout, int* ok, int* its,
+                  unsigned char* gscratch, cudaStream_t st) {
     if (ncand <= 0) return NEP_OK;
-    const size_t bytes = sizeof(zd) * newton_scratch_elems(k);
-    const int use_smem = bytes <= 200 * 1024;
-    if (use_smem)
-        NEP_CUDA(cudaFuncSetAttribute(newton_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    else if (!gscratch)
-        return NEP_ERR_INTERNAL;
-    newton_kernel<<<ncand, 256, use_smem ? bytes : 0, st>>>(s, k, Bs, lam0, Y0, ldy0, c, rad, maxit, tol, lam_out, Yout,
-                                                            ok, its, gscratch, use_smem);
+    const int64_t nb = (int64_t)s.nterms * k * k;
+    convert_c64_kernel<<<(int)((nb + 255) / 256), 256, 0, st>>>(nb, Bs, Bs32);
     NEP_CHECK_LAUNCH();
-    return NEP_OK;
+    const size_t bytes = newton_scratch_bytes(k, s.nterms);
+    const int use_smem = bytes <= 200 * 1024;
+    if (!use_smem && !gscratch) return NEP_ERR_INTERNAL;
+    auto run = [&](auto kern) -> int {
+        if (use_smem) NEP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        kern<<<ncand, 256, use_smem ? bytes : 0, st>>>(s, k, Bs, Bs32, lam0, Y0, ldy0, c, rad, maxit, tol, lam_out, Yout,
+                                                       ok, its, gscratch, use_smem);
+        NEP_CHECK_LAUNCH();
+        return NEP_OK;
+    };
+    const int K1 = k + 1;
+    if (K1 <= 64) return run(newton_kernel<2>);
+    if (K1 <= 96) return run(newton_kernel<3>);
+    if (K1 <= 160) return run(newton_kernel<5>);
+    if (K1 <= 288) return run(newton_kernel<9>);
+    set_error("projected Newton: basis of %d vectors exceeds 287", k);
+    return NEP_ERR_UNSUPPORTED;
 }
 
 // ------------------------------------------------------------------ residuals and selection

@@ -478,7 +478,8 @@ struct nep_plan {
     double* eta = nullptr;
     zd* part = nullptr;
     size_t part_elems = 0;
-    zd* newton_scratch = nullptr;
+    unsigned char* newton_scratch = nullptr;
+    zf* bs32 = nullptr;  // complex64 copy of the projected B_i for Newton
     void* eig_scratch = nullptr;
     JacobiWork jw{};
     int* h_pinned = nullptr;  // host-mapped scalars
@@ -551,8 +552,9 @@ static int plan_alloc(nep_plan* p) {
     NEP_TRY(dalloc(&p->eta, LM, st));
     p->part_elems = std::max<size_t>(16 * lm2, 1 << 16);
     NEP_TRY(dalloc(&p->part, p->part_elems, st));
-    if (sizeof(zd) * newton_scratch_elems(LM) > 200 * 1024)
-        NEP_TRY(dalloc(&p->newton_scratch, (size_t)LM * newton_scratch_elems(LM), st));
+    NEP_TRY(dalloc_raw((void**)&p->bs32, sizeof(zf) * (size_t)nt * LM * LM, st));
+    if (newton_scratch_bytes(LM, nt) > 200 * 1024)
+        NEP_TRY(dalloc_raw((void**)&p->newton_scratch, (size_t)LM * newton_scratch_bytes(LM, nt), st));
     NEP_TRY(dalloc_raw(&p->eig_scratch, sizeof(zf) * (size_t)LM * ((size_t)LM * (LM + 1) + 2 * LM) + 256, st));
     NEP_TRY(dalloc(&p->jw.Vm, lm2, st));
     NEP_TRY(dalloc(&p->jw.flags, 2, st));
@@ -572,7 +574,7 @@ static void plan_free(nep_plan* p) {
                     p->dmax, p->ymax, p->prev, p->beta, p->active, p->sweeps, p->nactive, p->S, p->mu, p->vpart,
                     p->H, p->Hs, p->Hw, p->U, p->W, p->sigma, p->T1, p->Bred, p->theta, p->Tv, p->Z, p->cand,
                     p->XH, p->G, p->Gw, p->Wg, p->lamg, p->Q, p->Y0, p->AQ, p->Bs, p->lamn, p->Yn, p->Xc, p->Gx,
-                    p->ok, p->its, p->order, p->scalars, p->eigstat, p->eta, p->part, p->newton_scratch,
+                    p->ok, p->its, p->order, p->scalars, p->eigstat, p->eta, p->part, p->newton_scratch, p->bs32,
                     p->eig_scratch, p->jw.Vm, p->jw.flags, p->jw.sweeps, p->jw.bar, p->jw.err};
     for (void* b : bufs)
         if (b) cudaFreeAsync(b, st);
@@ -766,7 +768,7 @@ static int run_extract(nep_plan* p, cudaStream_t st) {
                       p->part_elems, st));
     // Newton from every Hankel candidate
     const double rad = 4.0 * std::max(p->reg.a, p->reg.b);
-    NEP_TRY(launch_newton(s, kb, m, p->Bs, p->cand, p->Y0, kb, mk(p->reg.center_re, p->reg.center_im), rad,
+    NEP_TRY(launch_newton(s, kb, m, p->Bs, p->bs32, p->cand, p->Y0, kb, mk(p->reg.center_re, p->reg.center_im), rad,
                           p->o.newton_max, p->o.newton_tol, p->lamn, p->Yn, p->ok, p->its, p->newton_scratch, st));
     // eigenvectors, residuals, selection
     NEP_TRY(zgemm(n, m, kb, 0, p->Q, n, p->Yn, kb, p->Xc, n, p->part, p->part_elems, st));
@@ -808,6 +810,8 @@ extern "C" int nep_plan_buffer(nep_plan_t p, const char* name, void** dev_ptr, s
         {"sigma", p->sigma, sizeof(double) * p->LM}, {"tnorm", p->tnorm, sizeof(double) * N},
         {"beta", p->beta, sizeof(double) * N},      {"sweeps", p->sweeps, sizeof(int) * N},
         {"H", p->H, sizeof(zd) * p->LM * p->LM},
+        {"newton_its", p->its, sizeof(int) * p->LM},  {"newton_ok", p->ok, sizeof(int) * p->LM},
+        {"candidates", p->cand, sizeof(zd) * p->LM},  {"newton_lambda", p->lamn, sizeof(zd) * p->LM},
     };
     for (auto& b : tab)
         if (!strcmp(b.nm, name)) {

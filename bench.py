@@ -400,7 +400,7 @@ def main():
                          "algorithmic": {"flops": s_flops, "bytes": s_bytes,
                                          "hbm_gbs": s_bytes / (solve_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm,
                                          "hbm_frac": s_bytes / (solve_ms * 1e-3) / 1e9 / hbm}},
-            "factor": {"kernel": "lu_regt_kernel" if split.kl <= 64 and split.kl + split.ku <= 128 else "lu_glb_kernel",
+            "factor": {"kernel": "lu_regt_kernel" if split.kl <= 64 and split.kl + split.ku <= 128 else "lu_wide_kernel",
                        "ms": lu, "achieved_tflops": lu_flops(p.n, split.kl, split.ku, p.N) / (lu * 1e-3) / 1e12,
                        "peak_tflops": alu_peak,
                        "frac": lu_flops(p.n, split.kl, split.ku, p.N) / (lu * 1e-3) / 1e12 / alu_peak},

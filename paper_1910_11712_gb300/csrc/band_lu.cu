@@ -610,6 +610,9 @@ int launch_band_lu(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info,
             return pick_cpw<T, 16, 2>(s, npts, ab, ipiv, info, active, st, cpw);
         }
     }
+    // wide bands: blocked LU with the trailing window in global memory
+    if (s.kl >= 1 && band_lu_wide_fits(s.kl, (int)sizeof(cx<T>)))
+        return launch_band_lu_wide<T>(s, npts, ab, ipiv, info, active, st);
     // global-window path: per-point scratch of max(kl,1) x max(kv,1) elements
     const int RS = s.kl > 1 ? s.kl : 1, CS = kv > 1 ? kv : 1;
     const size_t win_bytes = sizeof(cx<T>) * (size_t)RS * CS * npts;

@@ -197,6 +197,11 @@ static inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b)
 template <typename T>
 int launch_assemble(const SplitDev& s, int npts, const zd* F, cx<T>* ab, double* tnorm, zd* tval, cudaStream_t st);
 // band_lu.cu
+// Blocked LU for wide bands (lu_wide.cu): panel in shared memory, trailing window in global memory.
+bool band_lu_wide_fits(int kl, int elem_bytes);
+template <typename T>
+int launch_band_lu_wide(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active,
+                        cudaStream_t st);
 template <typename T>
 int launch_band_lu(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st);
 // Narrow-band substitution sweeps (register windows of kl+1 and kl+ku+1 rows, up to 288).

@@ -229,17 +229,29 @@ static int run_sweep(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* 
     return NEP_OK;
 }
 
-// Right-hand sides per warp of the substitution sweeps: one for complex FP32 and two for complex
-// FP64 (measured fastest on the 64-point, 16-column, bandwidth-64 workload); NEP_SOLVE_RH=1 or 2
-// overrides it. A tuning knob only: the results are identical.
+// Right-hand sides per warp of the substitution sweeps. One warp per right-hand side keeps the
+// most chains in flight when there are few (N x L below ~2 per SM sub-partition); with more
+// chains than the GPU can interleave, two or four per warp share the coefficient loads and the
+// step bookkeeping (measured: bandwidth 64 with 1024 chains is fastest with one for complex FP32
+// and two for complex FP64; bandwidth 128 with 4096 chains gains 2x from four). NEP_SOLVE_RH
+// = 1, 2 or 4 overrides the choice: a tuning knob only, the results are identical.
 template <typename T>
-static int sweep_rh() {
-    static const int rh = [] {
+static int sweep_rh(int chains) {
+    static const int forced = [] {
         const char* e = std::getenv("NEP_SOLVE_RH");
         const int v = e ? std::atoi(e) : 0;
-        return (v == 1 || v == 2) ? v : (sizeof(T) == 4 ? 1 : 2);
+        return (v == 1 || v == 2 || v == 4) ? v : 0;
     }();
-    return rh;
+    if (forced) return forced;
+    static const int smsp = [] {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        return 4 * (sms > 0 ? sms : 152);
+    }();
+    // about one or two warps per sub-partition; complex FP64 (FP64-throughput-bound) takes at least two
+    const int rh = chains >= 6 * smsp ? 4 : chains >= 3 * smsp ? 2 : 1;
+    return sizeof(T) == 4 ? rh : (rh < 2 ? 2 : rh);
 }
 
 template <typename T, bool BWD, int RH>
@@ -262,8 +274,11 @@ static int sweep_rpl(int rpl, const SplitDev& s, int npts, const cx<T>* ab, cons
 template <typename T, bool BWD>
 static int sweep_dispatch(int rpl, const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* ut, const int* ipiv,
                           int L, cx<T>* B, const int* active, cudaStream_t st) {
-    if (sweep_rh<T>() == 1) return sweep_rpl<T, BWD, 1>(rpl, s, npts, ab, ut, ipiv, L, B, active, st);
-    return sweep_rpl<T, BWD, 2>(rpl, s, npts, ab, ut, ipiv, L, B, active, st);
+    switch (sweep_rh<T>(npts * L)) {
+        case 1: return sweep_rpl<T, BWD, 1>(rpl, s, npts, ab, ut, ipiv, L, B, active, st);
+        case 4: return sweep_rpl<T, BWD, 4>(rpl, s, npts, ab, ut, ipiv, L, B, active, st);
+        default: return sweep_rpl<T, BWD, 2>(rpl, s, npts, ab, ut, ipiv, L, B, active, st);
+    }
 }
 
 template <typename T>

@@ -108,6 +108,13 @@ typedef struct {
     int32_t newton_max;  /* Newton steps on the projected problem (30)                    */
     double newton_tol;   /* |dlambda| <= newton_tol * max(1, |lambda|) (1e-14)            */
     uint64_t seed;       /* probe block V when none is passed                             */
+    int32_t symmetric;   /* 1: solve only the nodes with Im z > 0 and take the others as   */
+                         /* their complex conjugates (real-symmetric contour halving).    */
+                         /* Needs a real operator (real A_i, f_i(conj z) = conj f_i(z) on */
+                         /* the nodes), a region symmetric about the real axis (real      */
+                         /* centre), an even N and a real V: plan creation returns        */
+                         /* NEP_ERR_ARG otherwise (V is checked at execute). Then S_k =   */
+                         /* 2 Re of the sum over those N/2 nodes. Default 0.              */
 } nep_opts;
 
 /* Defaults listed above. */
@@ -201,7 +208,8 @@ int nep_poll(nep_server_t s, uint64_t ticket, nep_result_t *out);
 int nep_server_wait(nep_server_t s, uint64_t ticket, nep_result_t *out);
 /* Waits for all admitted and queued requests, then stops the workers. */
 int nep_server_destroy(nep_server_t s);
-/* Device bytes one solve of this shape allocates (what admission charges against the budget). */
+/* Device bytes one solve of this shape allocates (what admission charges against the budget;
+ * a request with opts.symmetric set needs less). */
 uint64_t nep_plan_bytes(nep_split_t h, int32_t N, int32_t L, int32_t M, int32_t precision);
 
 /* ------------------------------------------------------------------ step entry points */

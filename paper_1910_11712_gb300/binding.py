@@ -47,7 +47,7 @@ class NepRegion(ctypes.Structure):
 class NepOpts(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("rank_tol", c_double), ("basis_tol", c_double), ("refine_tol", c_double),
                 ("step_tol", c_double), ("refine_max", c_int32), ("eig_tol", c_double), ("newton_max", c_int32),
-                ("newton_tol", c_double), ("seed", ctypes.c_uint64)]
+                ("newton_tol", c_double), ("seed", ctypes.c_uint64), ("symmetric", c_int32)]
 
 
 class NepResultInfo(ctypes.Structure):

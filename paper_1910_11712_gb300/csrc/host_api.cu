@@ -290,6 +290,7 @@ extern "C" void nep_opts_default(nep_opts* o) {
     o->newton_max = 30;
     o->newton_tol = 1e-14;
     o->seed = 0;
+    o->symmetric = 0;
 }
 
 extern "C" const char* nep_last_error(void) { return g_last_error.c_str(); }
@@ -442,6 +443,7 @@ struct nep_plan {
     nep_region reg;
     nep_opts o;
     int N = 0, L = 0, M = 0, K = 0, LM = 0;
+    int Np = 0;  // quadrature points solved: N, or N/2 under conjugate symmetry
     bool mixed = true;
     cudaStream_t alloc_stream = 0;
     // device buffers
@@ -492,7 +494,7 @@ struct nep_plan {
 
 static int plan_alloc(nep_plan* p) {
     const nep_split* h = p->h;
-    const int n = h->n, N = p->N, L = p->L, K = p->K, LM = p->LM, nt = h->nterms;
+    const int n = h->n, N = p->Np, L = p->L, K = p->K, LM = p->LM, nt = h->nterms;
     cudaStream_t st = p->alloc_stream;
     const size_t esz = p->mixed ? sizeof(zf) : sizeof(zd);
     NEP_TRY(dalloc(&p->F, (size_t)nt * N, st));
@@ -586,10 +588,11 @@ static void plan_free(nep_plan* p) {
 
 namespace nep {
 // Device bytes a plan for (h, N, L, M, precision) allocates (the same list as plan_alloc).
-size_t plan_footprint(nep_split_t h, int N, int L, int M, int precision) {
+size_t plan_footprint(nep_split_t h, int N, int L, int M, int precision, int symmetric) {
     nep_plan p;
     p.h = h;
     p.N = N;
+    p.Np = symmetric ? N / 2 : N;
     p.L = L;
     p.M = M;
     p.K = 2 * M;
@@ -633,21 +636,47 @@ int nep::plan_create_internal(nep_split_t h, const nep_region* r, int32_t N, int
     p->K = 2 * M;
     p->LM = L * M;
     p->mixed = p->o.precision == NEP_PREC_MIXED;
+    p->Np = N;
+    std::vector<zd> z, w, zeta;
+    make_nodes(r, N, z, w, zeta);
+    if (p->o.symmetric) {
+        // conjugate symmetry: z_{N-1-j} = conj z_j needs a real centre and an even N; T(conj z) =
+        // conj T(z) needs real A_i and f_i(conj z) = conj f_i(z) (checked on the nodes)
+        std::string why;
+        if (N % 2) why = "N is odd";
+        else if (r->center_im != 0.0) why = "the region's centre is not real";
+        else if (h->complex_vals) {
+            for (double v : h->val_im)
+                if (v != 0.0) { why = "some A_i has complex entries"; break; }
+        }
+        for (int j = 0; j < N / 2 && why.empty(); ++j)
+            for (int i = 0; i < h->nterms; ++i) {
+                const zd f = fn_eval(h->nodes.data(), h->coef.data(), h->roots[i], z[j]).f;
+                const zd g = fn_eval(h->nodes.data(), h->coef.data(), h->roots[i], conj(z[j])).f;
+                const double d = std::hypot(g.re - f.re, g.im + f.im), a = std::hypot(f.re, f.im);
+                if (!(d <= 1e-13 * std::max(a, 1e-300))) { why = "some f_i is not real (f(conj z) != conj f(z))"; break; }
+            }
+        if (!why.empty()) {
+            delete p;
+            set_error("symmetric quadrature not applicable: %s", why.c_str());
+            return NEP_ERR_ARG;
+        }
+        p->Np = N / 2;  // nodes j < N/2 have Im z > 0; node N-1-j is their conjugate
+    }
     int rc = plan_alloc(p);
     if (rc) {
         plan_free(p);
         delete p;
         return rc;
     }
-    // quadrature nodes, coefficient table and moment weights (host, FP64) -> device
-    std::vector<zd> z, w, zeta;
-    make_nodes(r, N, z, w, zeta);
-    std::vector<zd> F((size_t)h->nterms * N), coef((size_t)N * p->K);
-    for (int j = 0; j < N; ++j) {
+    // coefficient table and moment weights of the solved nodes (host, FP64) -> device
+    const int Np = p->Np;
+    std::vector<zd> F((size_t)h->nterms * Np), coef((size_t)Np * p->K);
+    for (int j = 0; j < Np; ++j) {
         for (int i = 0; i < h->nterms; ++i) F[i + (size_t)h->nterms * j] = fn_eval(h->nodes.data(), h->coef.data(), h->roots[i], z[j]).f;
         zd pw = mk(1.0, 0.0);
         for (int k = 0; k < p->K; ++k) {
-            coef[j + (size_t)N * k] = w[j] * pw;
+            coef[j + (size_t)Np * k] = w[j] * pw;
             pw = pw * zeta[j];
         }
     }
@@ -673,7 +702,7 @@ extern "C" int nep_plan_destroy(nep_plan_t p) {
 template <typename T>
 static int run_solves(nep_plan* p, cudaStream_t st) {
     const SplitDev s = p->h->dev();
-    const int N = p->N, n = s.n, L = p->L;
+    const int N = p->Np, n = s.n, L = p->L;
     cx<T>* ab = reinterpret_cast<cx<T>*>(p->ab);
     cx<T>* D = reinterpret_cast<cx<T>*>(p->D);
     NEP_CUDA(cudaEventRecord(p->ev[0], st));
@@ -713,9 +742,11 @@ static int read_scalar(nep_plan* p, const int* dptr, int* out, cudaStream_t st) 
 
 static int run_extract(nep_plan* p, cudaStream_t st) {
     const SplitDev s = p->h->dev();
-    const int n = s.n, N = p->N, L = p->L, M = p->M, K = p->K, LM = p->LM, nt = s.nterms;
-    // moments and Hankel matrices
-    NEP_TRY(launch_moments(n, L, N, K, p->coef, p->Y, p->S, st));
+    const int n = s.n, L = p->L, M = p->M, K = p->K, LM = p->LM, nt = s.nterms;
+    // moments and Hankel matrices; under conjugate symmetry the nodes not solved contribute the
+    // conjugates of the solved ones' terms: S_k = 2 Re sum_{Im z_j > 0} w_j zeta_j^k Y_j
+    NEP_TRY(launch_moments(n, L, p->Np, K, p->coef, p->Y, p->S, st));
+    if (p->Np != p->N) NEP_TRY(launch_double_real(int64_t(K) * n * L, p->S, st));
     NEP_TRY(launch_vh_times(n, L, K, p->V, p->S, p->mu, p->vpart, st));
     NEP_TRY(launch_hankel_build(L, M, p->mu, p->H, p->Hs, st));
     NEP_CUDA(cudaEventRecord(p->ev[4], st));
@@ -785,6 +816,13 @@ extern "C" int nep_plan_execute(nep_plan_t p, const void* V_dev, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     const int n = p->h->n, L = p->L;
     NEP_CUDA(cudaMemcpyAsync(p->V, V_dev, sizeof(zd) * (size_t)n * L, cudaMemcpyDeviceToDevice, st));
+    if (p->Np != p->N) {
+        // conjugate symmetry needs a real probe block
+        NEP_TRY(launch_count_imag(int64_t(n) * L, p->V, p->scalars + 3, st));
+        int nim = 0;
+        NEP_TRY(read_scalar(p, p->scalars + 3, &nim, st));
+        if (nim) { set_error("symmetric quadrature needs a real V (%d entries have an imaginary part)", nim); return NEP_ERR_ARG; }
+    }
     NEP_CUDA(cudaMemsetAsync(p->jw.err, 0, sizeof(int), st));
     int rc = p->mixed ? run_solves<float>(p, st) : run_solves<double>(p, st);
     if (rc) return rc;
@@ -799,7 +837,7 @@ extern "C" int nep_plan_execute(nep_plan_t p, const void* V_dev, void* stream) {
 extern "C" int nep_plan_buffer(nep_plan_t p, const char* name, void** dev_ptr, size_t* bytes) {
     if (!p || !name || !dev_ptr) { set_error("nep_plan_buffer: bad arguments"); return NEP_ERR_ARG; }
     const nep_split* h = p->h;
-    const size_t n = h->n, N = p->N, L = p->L, K = p->K;
+    const size_t n = h->n, N = p->Np, L = p->L, K = p->K;
     const size_t esz = p->mixed ? sizeof(zf) : sizeof(zd);
     struct B { const char* nm; void* ptr; size_t bytes; } tab[] = {
         {"F", p->F, sizeof(zd) * h->nterms * N},   {"coef", p->coef, sizeof(zd) * N * K},
@@ -832,7 +870,7 @@ struct nep_result {
 
 extern "C" int nep_plan_result(nep_plan_t p, nep_result_t* out) {
     if (!p || !out) { set_error("nep_plan_result: bad arguments"); return NEP_ERR_ARG; }
-    const int n = p->h->n, N = p->N, LM = p->LM;
+    const int n = p->h->n, N = p->Np, LM = p->LM;  // per-point arrays hold the solved points
     nep_result* r = new nep_result();
     r->n = n;
     r->m = p->m;
@@ -879,7 +917,7 @@ extern "C" int nep_plan_result(nep_plan_t p, nep_result_t* out) {
     r->flags = flags;
     nep_result_info_t& in = r->info;
     in.n = n;
-    in.N = N;
+    in.N = p->N;
     in.L = p->L;
     in.M = p->M;
     in.precision = p->o.precision;
@@ -912,6 +950,25 @@ void result_set_times(nep_result_t r, double queued_ms, double latency_ms) {
 }
 }  // namespace nep
 
+// Probe block drawn from a seed: a SplitMix64 stream and Box-Muller, Re and Im iid N(0,1)
+// (Im = 0 when real_only, as conjugate-symmetric quadrature needs).
+void nep::draw_probe_block(uint64_t seed, size_t count, bool real_only, double* out) {
+    uint64_t state = seed;
+    auto next = [&]() {
+        uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    auto unif = [&]() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); };
+    for (size_t i = 0; i < count; ++i) {
+        const double u1 = unif(), u2 = unif();
+        const double rr = std::sqrt(-2.0 * std::log(u1));
+        out[2 * i] = rr * std::cos(2 * M_PI * u2);
+        out[2 * i + 1] = real_only ? 0.0 : rr * std::sin(2 * M_PI * u2);
+    }
+}
+
 extern "C" int nep_ciss_solve(nep_split_t h, const nep_region* r, int32_t N, int32_t L, int32_t M, const nep_opts* o,
                               const double* V_host, nep_result_t* out) {
     if (!out) { set_error("out is NULL"); return NEP_ERR_ARG; }
@@ -923,20 +980,7 @@ extern "C" int nep_ciss_solve(nep_split_t h, const nep_region* r, int32_t N, int
     if (V_host) {
         memcpy(V.data(), V_host, sizeof(zd) * nl);
     } else {
-        // SplitMix64 stream + Box-Muller: Re, Im iid N(0,1)
-        uint64_t state = p->o.seed;
-        auto next = [&]() {
-            uint64_t z = (state += 0x9E3779B97F4A7C15ull);
-            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-            return z ^ (z >> 31);
-        };
-        auto unif = [&]() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); };
-        for (size_t i = 0; i < nl; ++i) {
-            const double u1 = unif(), u2 = unif();
-            const double rr = std::sqrt(-2.0 * std::log(u1));
-            V[i] = mk(rr * std::cos(2 * M_PI * u2), rr * std::sin(2 * M_PI * u2));
-        }
+        draw_probe_block(p->o.seed, nl, p->o.symmetric != 0, reinterpret_cast<double*>(V.data()));
     }
     int rc = NEP_OK;
     zd* dV = nullptr;

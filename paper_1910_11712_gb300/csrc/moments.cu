@@ -11,6 +11,8 @@
 // not by HBM.
 // vh_partial_kernel + vh_reduce_kernel: mu_k = V^H S_k over row chunks with a fixed-order
 // reduction (no atomics), so results do not depend on scheduling.
+#include <algorithm>
+
 #include "nep_common.cuh"
 
 namespace nep {
@@ -133,6 +135,37 @@ __global__ void hankel_build_kernel(int L, int M, const zd* __restrict__ mu, zd*
 int launch_hankel_build(int L, int M, const zd* mu, zd* H, zd* Hs, cudaStream_t st) {
     const int LM = L * M;
     hankel_build_kernel<<<ceil_div(LM * LM, 256), 256, 0, st>>>(L, M, mu, H, Hs);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+
+
+// ------------------------------------------------------------------ conjugate symmetry
+// x <- 2 Re x (the sum of a term and its complex conjugate), count entries.
+__global__ void double_real_kernel(int64_t count, zd* __restrict__ x) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count) x[t] = mk(2.0 * x[t].re, 0.0);
+}
+int launch_double_real(int64_t count, zd* x, cudaStream_t st) {
+    if (count <= 0) return NEP_OK;
+    double_real_kernel<<<(int)((count + 255) / 256), 256, 0, st>>>(count, x);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+
+// *out = number of entries of x with a nonzero imaginary part.
+__global__ void count_imag_kernel(int64_t count, const zd* __restrict__ x, int* __restrict__ out) {
+    int c = 0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+        c += x[t].im != 0.0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+int launch_count_imag(int64_t count, const zd* x, int* out, cudaStream_t st) {
+    NEP_CUDA(cudaMemsetAsync(out, 0, sizeof(int), st));
+    if (count <= 0) return NEP_OK;
+    const int blocks = (int)std::min<int64_t>((count + 255) / 256, 1024);
+    count_imag_kernel<<<blocks, 256, 0, st>>>(count, x, out);
     NEP_CHECK_LAUNCH();
     return NEP_OK;
 }

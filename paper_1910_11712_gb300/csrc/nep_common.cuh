@@ -212,6 +212,11 @@ int band_sweeps(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* ut, c
                 const int* active, cudaStream_t st);
 template <typename T>
 int band_transpose_u(const SplitDev& s, int npts, const cx<T>* ab, cx<T>* ut, cudaStream_t st);
+// moments.cu: conjugate-symmetric quadrature helpers
+int launch_double_real(int64_t count, zd* x, cudaStream_t st);
+int launch_count_imag(int64_t count, const zd* x, int* out, cudaStream_t st);
+// host_api.cu: seeded probe block (count complex entries; imaginary parts zero when real_only)
+void draw_probe_block(uint64_t seed, size_t count, bool real_only, double* out);
 template <typename T>
 int launch_band_solve(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* ut, const int* ipiv, int L, cx<T>* B,
                       const int* active, cudaStream_t st);

@@ -20,7 +20,7 @@
 #include "nep_common.cuh"
 
 namespace nep {
-size_t plan_footprint(nep_split_t h, int N, int L, int M, int precision);
+size_t plan_footprint(nep_split_t h, int N, int L, int M, int precision, int symmetric);
 int plan_create_internal(nep_split_t h, const nep_region* r, int32_t N, int32_t L, int32_t M, const nep_opts* o,
                          cudaStream_t alloc_stream, nep_plan_t* out);
 void result_set_times(nep_result_t r, double queued_ms, double latency_ms);
@@ -111,20 +111,7 @@ struct nep_server {
         if (rq->V.empty()) {
             // the probe block nep_ciss_solve draws for the same seed
             Vh.resize(2 * nl);
-            uint64_t state = rq->opts.seed;
-            auto next = [&]() {
-                uint64_t z = (state += 0x9E3779B97F4A7C15ull);
-                z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-                z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-                return z ^ (z >> 31);
-            };
-            auto unif = [&]() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); };
-            for (size_t i = 0; i < nl; ++i) {
-                const double u1 = unif(), u2 = unif();
-                const double rr = std::sqrt(-2.0 * std::log(u1));
-                Vh[2 * i] = rr * std::cos(2 * M_PI * u2);
-                Vh[2 * i + 1] = rr * std::sin(2 * M_PI * u2);
-            }
+            draw_probe_block(rq->opts.seed, nl, rq->opts.symmetric != 0, Vh.data());
             src = Vh.data();
         }
         void* dV = nullptr;
@@ -157,7 +144,7 @@ extern "C" uint64_t nep_plan_bytes(nep_split_t h, int32_t N, int32_t L, int32_t 
     if (!h || N < 1 || L < 1 || M < 1) return 0;
     int n = 0;
     nep_split_info(h, &n, nullptr, nullptr, nullptr, nullptr);
-    return plan_footprint(h, N, L, M, precision) + sizeof(double) * 2 * (size_t)n * L;
+    return plan_footprint(h, N, L, M, precision, 0) + sizeof(double) * 2 * (size_t)n * L;
 }
 
 extern "C" int nep_submit(nep_server_t s, nep_split_t h, const nep_region* r, int32_t N, int32_t L, int32_t M,
@@ -175,7 +162,7 @@ extern "C" int nep_submit(nep_server_t s, nep_split_t h, const nep_region* r, in
     if (o) rq->opts = *o;
     else nep_opts_default(&rq->opts);
     if (V_host) rq->V.assign(V_host, V_host + 2 * (size_t)n * L);
-    rq->bytes = plan_footprint(h, N, L, M, rq->opts.precision) + sizeof(double) * 2 * (size_t)n * L;
+    rq->bytes = plan_footprint(h, N, L, M, rq->opts.precision, rq->opts.symmetric) + sizeof(double) * 2 * (size_t)n * L;
     rq->submitted = Clock::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);

@@ -245,6 +245,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-symmetric", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=40)
     ap.add_argument("--serving-smax", type=int, default=128)
     args = ap.parse_args()
@@ -347,6 +348,32 @@ def main():
         ms = float(t.item())
     value = world * p.N / (ms * 1e-3)
 
+    # conjugate-symmetric quadrature on the same workload (real operators only): a real probe
+    # block, only the N/2 nodes above the real axis solved
+    symmetric = None
+    if not args.no_symmetric:
+        try:
+            Vr = np.asfortranarray(np.random.default_rng(rank).standard_normal((p.n, p.L)).astype(np.complex128))
+            Vrd = torch.from_numpy(Vr.ravel(order="F").view(np.float64).copy()).cuda()
+            plan_s = binding.Plan(split, p.region, p.N, p.L, p.M, precision=prec, symmetric=1)
+            for _ in range(3):
+                plan_s.execute(Vrd, stream)
+            torch.cuda.synchronize()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            for _ in range(args.steps):
+                plan_s.execute(Vrd, stream)
+            s1.record()
+            torch.cuda.synchronize()
+            ms_s = s0.elapsed_time(s1) / args.steps
+            rs = plan_s.result()
+            symmetric = {"ms_per_step": ms_s, "quadrature_nodes_per_s": p.N / (ms_s * 1e-3),
+                         "points_solved_per_step": p.N // 2, "nconv": int(len(rs["lam"])), "hankel_rank": rs["m"],
+                         "probe": "real N(0,1)"}
+            plan_s.close()
+        except binding.NepError as e:
+            symmetric = {"unavailable": str(e)}
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -412,6 +439,8 @@ def main():
         }
         if e2e:
             line["e2e"] = e2e
+        if symmetric:
+            line["symmetric"] = symmetric
         if not args.no_serving:
             line["serving"] = serving_bench(binding, prec, args.serving_requests, 0, 4, args.serving_smax)
         if not args.no_cpu:

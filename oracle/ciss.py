@@ -67,7 +67,8 @@ def solve_point(problem, kl: int, ku: int, coeffs, V: np.ndarray, *, refine_max:
 
     Refinement sweep: R = V - T Y (FP64 split-form product), D = T^{-1} R, Y += D;
     stop once the backward error of the iterate is <= REFINE_TOL and the relative
-    correction is <= REFINE_STEP_TOL or stopped halving. Returns a dict.
+    correction is <= REFINE_STEP_TOL (or the next one, extrapolated from the last contraction
+    ratio, would be) or stopped halving. Returns a dict.
     """
     T = band.assemble_sparse(problem.mats, coeffs)
     Tnorm = float(abs(T).sum(axis=1).max())
@@ -84,7 +85,9 @@ def solve_point(problem, kl: int, ku: int, coeffs, V: np.ndarray, *, refine_max:
         Y = Y + D
         sweeps += 1
         d = float(np.abs(D).max() / max(np.abs(Y).max(), 1e-300))
-        if beta <= REFINE_TOL and (d <= REFINE_STEP_TOL or d > 0.5 * prev):
+        # the next correction, extrapolated from the contraction seen so far, is what remains
+        small = d <= REFINE_STEP_TOL or (math.isfinite(prev) and d <= 0.5 * prev and d * (d / prev) <= REFINE_STEP_TOL)
+        if beta <= REFINE_TOL and (small or d > 0.5 * prev):
             break
         prev = d
     out = {"Y": np.asfortranarray(Y), "info": info, "beta": beta, "sweeps": sweeps, "Tnorm": Tnorm}

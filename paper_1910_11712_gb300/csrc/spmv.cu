@@ -145,8 +145,12 @@ __global__ void decide_kernel(int npts, int L, int sweep, int max_sweeps, double
     const double d = ymax[j] > 0 ? dmax[j] / ymax[j] : 0.0;
     beta_out[j] = beta;
     sweeps[j] = sweep + 1;
-    // prev starts at 0, read as "no previous correction"
-    const bool conv = beta <= tol && (d <= step_tol || (prev[j] > 0 && d > 0.5 * prev[j]));
+    // prev starts at 0, read as "no previous correction". Converged: backward error at the target
+    // and either the correction is at the FP64 level, or the contraction seen so far (d / prev)
+    // puts the next correction there (the error left after this one), or it stopped halving
+    const double pv = prev[j];
+    const bool small = d <= step_tol || (pv > 0 && d <= 0.5 * pv && d * (d / pv) <= step_tol);
+    const bool conv = beta <= tol && (small || (pv > 0 && d > 0.5 * pv));
     prev[j] = d;
     if (conv || sweep + 1 >= max_sweeps) {
         active[j] = 0;

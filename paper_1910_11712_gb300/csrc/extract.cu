@@ -148,22 +148,80 @@ __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 // ------------------------------------------------------------------ one-sided Jacobi SVD
 // A (rows x cols, column-major) is rotated in place until its columns are mutually
 // orthogonal: A V = U Sigma. Rotation of columns (p, q) with alpha = |a_p|^2,
-// beta = |a_q|^2, gamma = a_p^H a_q = |gamma| e^{i phi}: zeta = (beta - alpha)/(2|gamma|),
-// t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t,
+// beta = |a_q|^2, gamma = a_p^H a_q = |gamma| e^{i phi}: the angle with
+// tan(theta) = t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)), zeta = (beta - alpha)/(2|gamma|), zeroes
+// the new a_p^H a_q; with c = cos(theta), s = sin(theta)
 //   a_p <- c a_p - s e^{-i phi} a_q,   a_q <- s e^{i phi} a_p + c a_q   (same on V).
 // Pairs per round follow the circle method over P = cols rounded up to even.
+
+// c and s e^{i phi} = sr + i si of the rotation above, or false when the pair already counts as
+// orthogonal (|gamma| <= tol sqrt(alpha beta)) or a column is zero. Multiplying t through by
+// 2|gamma| gives, with D = beta - alpha and q = |D| + sqrt(D^2 + 4|gamma|^2),
+//   c = q / sqrt(q^2 + 4|gamma|^2),   s e^{i phi} = 2 sgn(D) gamma / sqrt(q^2 + 4|gamma|^2):
+// one square root and one reciprocal square root and no division (FP64 issue slots are the scarce
+// resource here). c^2 + |s|^2 = 1 holds to the rounding of the reciprocal square root whatever the
+// rounding of q, which only moves the angle. Outside the range where q^2 + 4|gamma|^2 is a normal
+// number far from overflow, the zeta form (scaled by |gamma|) is used instead.
+__device__ __forceinline__ bool jacobi_rotation(double al, double be, double gr, double gi, double tol, double& c,
+                                                double& sr, double& si) {
+    const double g2 = fma(gr, gr, gi * gi);
+    if (!(g2 > (tol * tol) * (al * be)) || al == 0.0 || be == 0.0) return false;
+    const double D = be - al, g4 = 4.0 * g2;
+    const double q = fabs(D) + sqrt(fma(D, D, g4));
+    const double h = fma(q, q, g4);
+    if (h >= 1e-280 && h <= 1e280) {
+        const double r = rsqrt(h);
+        const double f = (D >= 0.0 ? 2.0 : -2.0) * r;
+        c = q * r;
+        sr = f * gr;
+        si = f * gi;
+        return true;
+    }
+    const double g = hypot(gr, gi);
+    const double zeta = D / (2.0 * g);
+    const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    c = 1.0 / sqrt(1.0 + t * t);
+    const double sn = c * t / g;
+    sr = sn * gr;
+    si = sn * gi;
+    return true;
+}
+
+// x <- c x - conj(s e) y,  y <- (s e) x + c y  with s e = sr + i si: twelve FP64 operations.
+__device__ __forceinline__ void jacobi_apply(double c, double sr, double si, zd& x, zd& y) {
+    const zd xo = mk(fma(c, x.re, -fma(sr, y.re, si * y.im)), fma(c, x.im, fma(-sr, y.im, si * y.re)));
+    const zd yo = mk(fma(sr, x.re, fma(-si, x.im, c * y.re)), fma(sr, x.im, fma(si, x.re, c * y.im)));
+    x = xo;
+    y = yo;
+}
+
+// Sum of four per-lane values over the warp as a reduce-scatter: after the call lane l holds the
+// warp total of value (l >> 3) & 3. Six FP64 additions where four butterflies take twenty.
+__device__ __forceinline__ double warp_reduce_scatter4(double v0, double v1, double v2, double v3, int lane) {
+    const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0;
+    double k0 = h16 ? v2 : v0, k1 = h16 ? v3 : v1;
+    k0 += __shfl_xor_sync(0xffffffffu, h16 ? v0 : v2, 16);
+    k1 += __shfl_xor_sync(0xffffffffu, h16 ? v1 : v3, 16);
+    double k = h8 ? k1 : k0;
+    k += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+    for (int o = 4; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+    return k;
+}
+
 __global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __restrict__ A, zd* __restrict__ Vm,
                                                      int max_sweeps, double tol, int* __restrict__ flags,
                                                      int* __restrict__ sweeps_out, GridBar bar) {
     const int lane = threadIdx.x & 31;
-    // nsub warps per CTA: with several, the CTA works on one pair at a time (warps split rows, one
-    // warp per SM sub-partition so the pair gets the whole SM's FP64 rate); with one, each warp
-    // takes its own pair
+    // nsub warps per CTA (4 or 8): with several, the CTA works on one pair at a time (warps split
+    // rows, one warp per SM sub-partition so the pair gets the whole SM's FP64 rate); with one,
+    // each warp takes its own pair
     const int nsub = blockDim.x >> 5;
     const int gwarp = nsub > 1 ? (int)blockIdx.x : (int)(blockIdx.x * nsub + (threadIdx.x >> 5));
     const int nwarps = nsub > 1 ? (int)gridDim.x : (int)(gridDim.x * nsub);
-    __shared__ double red4[8][4];
-    __shared__ double rot4[4];
+    // per-warp partial sums, double-buffered: a warp writes buffer b of pair k + 2 only after the
+    // barrier of pair k + 1, which every warp reaches after reading buffer b of pair k
+    __shared__ double red4[2][8][4];
+    int buf = 0;
     const int P = cols + (cols & 1);
     // V = I
     unsigned int epoch = 0;
@@ -210,64 +268,34 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __r
                         be += norm2(ya[1]);
                         ga = fmac(ga, xa[1], ya[1]);
                     }
-                    for (int o = 16; o > 0; o >>= 1) {
-                        al += __shfl_xor_sync(0xffffffffu, al, o);
-                        be += __shfl_xor_sync(0xffffffffu, be, o);
-                        ga.re += __shfl_xor_sync(0xffffffffu, ga.re, o);
-                        ga.im += __shfl_xor_sync(0xffffffffu, ga.im, o);
-                    }
+                    const double ws = warp_reduce_scatter4(al, be, ga.re, ga.im, lane);
                     const int w = tid >> 5;
-                    if (lane == 0) {
-                        red4[w][0] = al;
-                        red4[w][1] = be;
-                        red4[w][2] = ga.re;
-                        red4[w][3] = ga.im;
-                    }
+                    if ((lane & 7) == 0) red4[buf][w][lane >> 3] = ws;
                     __syncthreads();
-                    // the rotation's scalars once per CTA: FP64 issue slots are scarce, so the
-                    // square roots and divisions are not repeated by every thread
-                    if (tid == 0) {
-                        al = be = 0.0;
-                        ga = mk(0.0, 0.0);
-                        for (int q = 0; q < nsub; ++q) {
-                            al += red4[q][0];
-                            be += red4[q][1];
-                            ga.re += red4[q][2];
-                            ga.im += red4[q][3];
-                        }
-                        const double g = hypot(ga.re, ga.im);
-                        double cc = 1.0, sr = 0.0, si = 0.0, doit = 0.0;
-                        if (g > tol * sqrt(al * be) && al != 0.0 && be != 0.0) {
-                            const double zeta = (be - al) / (2.0 * g);
-                            const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                            cc = 1.0 / sqrt(1.0 + t * t);
-                            const double sn = cc * t / g;
-                            sr = sn * ga.re;
-                            si = sn * ga.im;
-                            doit = 1.0;
-                        }
-                        rot4[0] = cc;
-                        rot4[1] = sr;
-                        rot4[2] = si;
-                        rot4[3] = doit;
-                    }
-                    __syncthreads();
-                    const double c = rot4[0];
-                    const zd se = mk(rot4[1], rot4[2]), sec = conj(se);
-                    const bool doit = rot4[3] != 0.0;
-                    __syncthreads();
-                    if (!doit) continue;
+                    // every warp adds the nsub partials itself, in the same order, so all warps
+                    // hold bit-identical rotation scalars without another barrier: lane l takes
+                    // value l & 3 of warp l >> 2
+                    double x = (lane >> 2) < nsub ? red4[buf][lane >> 2][lane & 3] : 0.0;
+                    buf ^= 1;
+                    for (int o = 4; o < 4 * nsub; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                    al = __shfl_sync(0xffffffffu, x, 0);
+                    be = __shfl_sync(0xffffffffu, x, 1);
+                    const double gr = __shfl_sync(0xffffffffu, x, 2), gi = __shfl_sync(0xffffffffu, x, 3);
+                    double c, sr, si;
+                    if (!jacobi_rotation(al, be, gr, gi, tol, c, sr, si)) continue;
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         const int i = tid + nthr * u;
                         if (u == 1 && !two) break;
                         if (i < rows) {
-                            ap[i] = c * xa[u] - sec * ya[u];
-                            aq[i] = se * xa[u] + c * ya[u];
+                            jacobi_apply(c, sr, si, xa[u], ya[u]);
+                            ap[i] = xa[u];
+                            aq[i] = ya[u];
                         }
                         if (i < cols) {
-                            vp[i] = c * xv[u] - sec * yv[u];
-                            vq[i] = se * xv[u] + c * yv[u];
+                            jacobi_apply(c, sr, si, xv[u], yv[u]);
+                            vp[i] = xv[u];
+                            vq[i] = yv[u];
                         }
                     }
                     if (tid == 0) atomicOr(&flags[sweep & 1], 1);
@@ -281,28 +309,23 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int rows, int cols, zd* __r
                     be += norm2(y);
                     ga = fmac(ga, x, y);
                 }
-                for (int o = 16; o > 0; o >>= 1) {
-                    al += __shfl_xor_sync(0xffffffffu, al, o);
-                    be += __shfl_xor_sync(0xffffffffu, be, o);
-                    ga.re += __shfl_xor_sync(0xffffffffu, ga.re, o);
-                    ga.im += __shfl_xor_sync(0xffffffffu, ga.im, o);
-                }
-                const double g = hypot(ga.re, ga.im);
-                if (!(g > tol * sqrt(al * be)) || al == 0.0 || be == 0.0) continue;
-                const double zeta = (be - al) / (2.0 * g);
-                const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-                const zd e = mk(ga.re / g, ga.im / g);  // e^{i phi}
-                const zd se = mk(s * e.re, s * e.im), sec = conj(se);
+                const double ws = warp_reduce_scatter4(al, be, ga.re, ga.im, lane);
+                al = __shfl_sync(0xffffffffu, ws, 0);
+                be = __shfl_sync(0xffffffffu, ws, 8);
+                const double gr = __shfl_sync(0xffffffffu, ws, 16), gi = __shfl_sync(0xffffffffu, ws, 24);
+                double c, sr, si;
+                if (!jacobi_rotation(al, be, gr, gi, tol, c, sr, si)) continue;
                 for (int i = lane; i < rows; i += 32) {
-                    const zd x = ldcg(ap + i), y = ldcg(aq + i);
-                    ap[i] = c * x - sec * y;
-                    aq[i] = se * x + c * y;
+                    zd x = ldcg(ap + i), y = ldcg(aq + i);
+                    jacobi_apply(c, sr, si, x, y);
+                    ap[i] = x;
+                    aq[i] = y;
                 }
                 for (int i = lane; i < cols; i += 32) {
-                    const zd x = ldcg(vp + i), y = ldcg(vq + i);
-                    vp[i] = c * x - sec * y;
-                    vq[i] = se * x + c * y;
+                    zd x = ldcg(vp + i), y = ldcg(vq + i);
+                    jacobi_apply(c, sr, si, x, y);
+                    vp[i] = x;
+                    vq[i] = y;
                 }
                 if (lane == 0) atomicOr(&flags[sweep & 1], 1);
             }

@@ -56,9 +56,27 @@ __device__ __forceinline__ int warp_pivot(const cx<T>* pcol, int cnt, int lane) 
     }
 }
 
-// Pivot step by warp 0: chooses the pivot among pcol[0..cnt-1], swaps it to pcol[0],
-// writes U(c,c), the multipliers (shared lvec and global L column) and ipiv.
+// 1/v for a nonzero pivot: conj(v) / |v|^2 with one correctly rounded reciprocal, where |v|^2 is
+// safely inside the normal range (the common case); Smith's scaled division otherwise.
 template <typename T>
+__device__ __forceinline__ cx<T> pivot_recip(cx<T> v) {
+    const T m = fmax(fabs(v.re), fabs(v.im));
+    const T lo = sizeof(T) == 4 ? T(1e-15) : T(1e-150), hi = sizeof(T) == 4 ? T(1e15) : T(1e150);
+    if (m >= lo && m <= hi) {
+        const T d = v.re * v.re + v.im * v.im;
+        T r;
+        if constexpr (sizeof(T) == 4) r = __frcp_rn(d);
+        else r = __drcp_rn(d);
+        return mk<T>(v.re * r, -v.im * r);
+    }
+    return cdiv(mk<T>(1, 0), v);
+}
+
+// Pivot step by warp 0: chooses the pivot among pcol[0..cnt-1], swaps it to pcol[0] and
+// writes the multipliers to shared lvec and the pivot offset to *piv_s. With GLOBAL it also
+// writes U(c,c), the L column and ipiv[c]; without, the caller copies them from pcol[0], lvec
+// and *piv_s after the barrier that follows (off the critical path of the elimination).
+template <typename T, bool GLOBAL = true>
 __device__ __forceinline__ void pivot_step(cx<T>* pcol, cx<T>* lvec, int* piv_s, int* info_s, int c, int n, int kl,
                                            int kv, int ldab, cx<T>* ab, int* ipiv, int lane) {
     const int cnt = min(kl, n - 1 - c) + 1;
@@ -74,16 +92,18 @@ __device__ __forceinline__ void pivot_step(cx<T>* pcol, cx<T>* lvec, int* piv_s,
     }
     __syncwarp();
     cx<T>* out = ab + (int64_t)c * ldab;
-    const cx<T> rpv = zero ? mk<T>(0, 0) : cdiv(mk<T>(1, 0), pv);
+    const cx<T> rpv = zero ? mk<T>(0, 0) : pivot_recip(pv);
     for (int i = lane; i < kl; i += 32) {
         cx<T> l = mk<T>(0, 0);
         if (!zero && c + 1 + i < n) l = pcol[i + 1] * rpv;
         lvec[i] = l;
-        out[kv + 1 + i] = l;
+        if (GLOBAL) out[kv + 1 + i] = l;
     }
     if (lane == 0) {
-        out[0] = zero ? mk<T>(0, 0) : pv;
-        ipiv[c] = c + p;
+        if (GLOBAL) {
+            out[0] = zero ? mk<T>(0, 0) : pv;
+            ipiv[c] = c + p;
+        }
         *piv_s = p;
         if (zero && *info_s == 0) *info_s = c + 1;
     }
@@ -325,23 +345,15 @@ __global__ void __launch_bounds__(NW * 32, 1)
         }
         cp_async_wait_group<PF - 1>();  // the group of row c+kl has landed
         __syncthreads();  // S1
-        // fetch row c+kl+PF (columns c+PF..c+PF+kv) into the slot freed by step c-1
-        {
-            const int r = c + kl + PF;
-            cx<T>* dst = nrow[(c + PF) % (PF + 1)];
-            for (int t = threadIdx.x; t <= kv; t += blockDim.x) {
-                if (r < n && c + PF + t < n) cp_async_cx(&dst[t], ab + (int64_t)r * ldab + t);
-                else dst[t] = mk<T>(0, 0);
-            }
-            cp_async_commit();
-        }
         if (warp == 0) {
             if (lane == 0) pcol[kl] = nrow[buf][0];
             __syncwarp();
-            pivot_step(pcol, lvec, &piv_s, &info_s, c, n, kl, kv, ldab, ab, ipiv, lane);
+            pivot_step<T, false>(pcol, lvec, &piv_s, &info_s, c, n, kl, kv, ldab, ab, ipiv, lane);
         }
         __syncthreads();  // S2
         const int prel = piv_s;
+        // U(c,c) for the global copy below: pcol is rewritten before S1 of the next step
+        const cx<T> ucc = threadIdx.x == blockDim.x - 1 ? pcol[0] : mk<T>(0, 0);
         const int rsc = c % RS, wc = rsc / RPW, qc = rsc % RPW;
         const int rsp = (c + prel) % RS, wp = rsp / RPW, qp = rsp % RPW;
         // (3) publish the pivot row (u) and, when row c moves, its old values
@@ -371,10 +383,29 @@ __global__ void __launch_bounds__(NW * 32, 1)
         }
         __syncthreads();  // S3
         const cx<T>* u = (prel == kl) ? &nrow[buf][1] : urow;
-        // U row c (columns c+1..c+kv) to global
+        // Memory traffic of the step, kept out of the pivot choice and the publication (it
+        // shares their queue): threads 0..kv-1 store U row c (columns c+1..c+kv), threads
+        // 128..128+kl-1 the L column from lvec (rewritten only after the next S1), the last
+        // thread U(c,c) and ipiv[c]; threads from 192 on fetch row c+kl+PF (columns
+        // c+PF..c+PF+kv) into the ring slot that step c-1 freed.
         cx<T>* out = ab + (int64_t)c * ldab;
-        for (int t = threadIdx.x; t < kv; t += blockDim.x)
-            if (c + 1 + t < n) out[1 + t] = u[t];
+        {
+            const int t = threadIdx.x;
+            if (t < kv && c + 1 + t < n) out[1 + t] = u[t];
+            if (t >= 128 && t < 128 + kl) out[kv + 1 + (t - 128)] = lvec[t - 128];
+            if (t == (int)blockDim.x - 1) {
+                out[0] = ucc;
+                ipiv[c] = c + prel;
+            }
+            const int r = c + kl + PF;
+            cx<T>* dst = nrow[(c + PF) % (PF + 1)];
+            for (int f = t - 192; f <= kv; f += blockDim.x - 192) {
+                if (f < 0) break;
+                if (r < n && c + PF + f < n) cp_async_cx(&dst[f], ab + (int64_t)r * ldab + f);
+                else dst[f] = mk<T>(0, 0);
+            }
+            cp_async_commit();
+        }
         // (4) row moves (only the owner warps), new row c+kl, rank-1 update
         const int rsn = (c + kl) % RS, wn = rsn / RPW, qn = rsn % RPW;
         if (warp == wn || (warp == wp && prel != 0 && prel != kl)) {

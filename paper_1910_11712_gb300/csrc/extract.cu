@@ -110,7 +110,7 @@ int zgemm(int M, int N, int K, int opA, const zd* A, int lda, const zd* B, int l
 // Barrier for a cooperative launch (all CTAs co-resident) on a monotonically increasing
 // arrival counter: barrier number e completes once the counter reaches e * gridDim.x, so it
 // needs one atomic per CTA and no reset. Every wait is bounded: after 2^24 polls (seconds) the CTA
-// records an error and continues.
+// records an error and continues, and once an error is recorded no barrier waits any more.
 struct GridBar {
     unsigned int* count;
     unsigned int* gen;  // unused by this barrier, kept for the work layout
@@ -125,8 +125,10 @@ __device__ __forceinline__ void grid_barrier(GridBar b, unsigned int& epoch) {
         __threadfence();
         atomicAdd(b.count, 1u);
         volatile unsigned int* vc = b.count;
+        volatile int* ve = b.err;
         long long spins = 0;
         while (*vc < target) {
+            if (*ve) break;  // another wait already timed out: do not add seconds per barrier
             if (++spins > (1ll << 24)) {
                 atomicExch(b.err, 1);
                 break;

@@ -251,8 +251,12 @@ def test_moments_kernel(bnd, K):
         assert np.abs(Sg[k] - ref).max() <= 1e-14 * np.abs(Y).max() * np.abs(coef).sum(axis=0).max()
 
 
+# shapes span both work splits (one pair per CTA of four warps up to 256 rows and columns, one
+# pair per warp beyond), two elements per thread (rows > 128), odd column counts (a padding
+# column in the round-robin) and a single column
 @pytest.mark.parametrize("shape,rank", [((40, 40), None), ((128, 128), None), ((96, 96), 30), ((200, 64), None),
-                                        ((17, 17), None)])
+                                        ((17, 17), None), ((129, 65), None), ((300, 120), None), ((257, 33), 20),
+                                        ((5, 1), None)])
 def test_jacobi_svd_matches_lapack(bnd, shape, rank):
     torch = torch_cuda()
     rows, cols = shape

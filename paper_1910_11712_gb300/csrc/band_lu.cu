@@ -18,13 +18,9 @@
 // a(r,k) -= l(r) u(k) with u the pivot row. Row c+kl enters the window at step c (its
 // first nonzero is column c) and column c+kv enters empty (fill-in only).
 //
-// lu_reg_kernel keeps the whole (kl x kv) window in registers: row r lives in slot
-// r mod RS (lane = slot % 32), column k in slot k mod CS (warp = slot / CPW). With
-// RS == kl and CS == kv the entering row/column reuse the slots of the leaving ones, so
-// every thread updates exactly RPL x CPW elements per step (balanced). Two CTA barriers
-// per step: one after the pivot column is published, one after the multipliers are.
-// lu_glb_kernel runs the same elimination with the window in a global (L2-resident)
-// scratch array, for bands too wide for the register file.
+// Three implementations share this elimination and its stored factors: lu_col.cu (register
+// window, kl <= 64 and kl + ku <= 128), lu_wide.cu (blocked, wider bands) and lu_glb_kernel
+// below, which keeps the window in a global (L2-resident) scratch array for bands beyond both.
 #include "band_util.cuh"
 
 namespace nep {
@@ -56,27 +52,9 @@ __device__ __forceinline__ int warp_pivot(const cx<T>* pcol, int cnt, int lane) 
     }
 }
 
-// 1/v for a nonzero pivot: conj(v) / |v|^2 with one correctly rounded reciprocal, where |v|^2 is
-// safely inside the normal range (the common case); Smith's scaled division otherwise.
+// Pivot step by warp 0: chooses the pivot among pcol[0..cnt-1], swaps it to pcol[0],
+// writes U(c,c), the multipliers (shared lvec and global L column) and ipiv.
 template <typename T>
-__device__ __forceinline__ cx<T> pivot_recip(cx<T> v) {
-    const T m = fmax(fabs(v.re), fabs(v.im));
-    const T lo = sizeof(T) == 4 ? T(1e-15) : T(1e-150), hi = sizeof(T) == 4 ? T(1e15) : T(1e150);
-    if (m >= lo && m <= hi) {
-        const T d = v.re * v.re + v.im * v.im;
-        T r;
-        if constexpr (sizeof(T) == 4) r = __frcp_rn(d);
-        else r = __drcp_rn(d);
-        return mk<T>(v.re * r, -v.im * r);
-    }
-    return cdiv(mk<T>(1, 0), v);
-}
-
-// Pivot step by warp 0: chooses the pivot among pcol[0..cnt-1], swaps it to pcol[0] and
-// writes the multipliers to shared lvec and the pivot offset to *piv_s. With GLOBAL it also
-// writes U(c,c), the L column and ipiv[c]; without, the caller copies them from pcol[0], lvec
-// and *piv_s after the barrier that follows (off the critical path of the elimination).
-template <typename T, bool GLOBAL = true>
 __device__ __forceinline__ void pivot_step(cx<T>* pcol, cx<T>* lvec, int* piv_s, int* info_s, int c, int n, int kl,
                                            int kv, int ldab, cx<T>* ab, int* ipiv, int lane) {
     const int cnt = min(kl, n - 1 - c) + 1;
@@ -97,365 +75,14 @@ __device__ __forceinline__ void pivot_step(cx<T>* pcol, cx<T>* lvec, int* piv_s,
         cx<T> l = mk<T>(0, 0);
         if (!zero && c + 1 + i < n) l = pcol[i + 1] * rpv;
         lvec[i] = l;
-        if (GLOBAL) out[kv + 1 + i] = l;
+        out[kv + 1 + i] = l;
     }
     if (lane == 0) {
-        if (GLOBAL) {
-            out[0] = zero ? mk<T>(0, 0) : pv;
-            ipiv[c] = c + p;
-        }
+        out[0] = zero ? mk<T>(0, 0) : pv;
+        ipiv[c] = c + p;
         *piv_s = p;
         if (zero && *info_s == 0) *info_s = c + 1;
     }
-}
-
-template <typename T, int NW, int RPL, int CPW>
-__global__ void __launch_bounds__(NW * 32, 1)
-    lu_reg_kernel(int n, int kl, int ku, int ldab, cx<T>* __restrict__ ab_all, int* __restrict__ ipiv_all,
-                  int* __restrict__ info_all, const int* __restrict__ active) {
-    const int j = blockIdx.x;
-    if (active && !active[j]) return;
-    constexpr int RS = 32 * RPL;
-    constexpr int CS = NW * CPW;
-    const int kv = kl + ku;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    cx<T>* ab = ab_all + (int64_t)j * n * ldab;
-    int* ipiv = ipiv_all + (int64_t)j * n;
-
-    __shared__ cx<T> nrow[2][CS + 1];
-    __shared__ cx<T> pcol[RS + 1];
-    __shared__ cx<T> lvec[RS];
-    __shared__ int piv_s, info_s;
-    if (threadIdx.x == 0) info_s = 0;
-
-    // window registers: a[q][p] = element (row slot lane + 32 q, column slot warp*CPW + p)
-    cx<T> a[RPL][CPW];
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-        const int r = lane + 32 * q;
-#pragma unroll
-        for (int p = 0; p < CPW; ++p) {
-            const int k = warp * CPW + p;
-            cx<T> v = mk<T>(0, 0);
-            const int t = k - r + kl;
-            if (r < kl && r < n && k < kv && k < n && t >= 0 && t <= kv) v = ab[(int64_t)r * ldab + t];
-            a[q][p] = v;
-        }
-    }
-    // row kl enters at step 0 with columns 0..kv
-    for (int t = threadIdx.x; t <= kv; t += blockDim.x) {
-        cx<T> v = mk<T>(0, 0);
-        if (kl < n && t < n) v = ab[(int64_t)kl * ldab + t];
-        nrow[0][t] = v;
-    }
-    __syncthreads();
-
-    for (int c = 0; c < n; ++c) {
-        const int buf = c & 1;
-        // (1) the owner warp publishes column c (rows c..c+kl-1), then empties the slot
-        //     that column c+kv takes over
-        {
-            const int csc = c % CS;
-            if (csc / CPW == warp) {
-                const int pc = csc % CPW;
-#pragma unroll
-                for (int p = 0; p < CPW; ++p) {
-                    if (p != pc) continue;
-#pragma unroll
-                    for (int q = 0; q < RPL; ++q) {
-                        const int rs = lane + 32 * q;
-                        const int i = posmod(rs - c, RS);
-                        if (i < kl) pcol[i] = a[q][p];
-                    }
-                }
-            }
-            const int csn = (c + kv) % CS;
-            if (csn / CPW == warp) {
-                const int pn = csn % CPW;
-#pragma unroll
-                for (int p = 0; p < CPW; ++p)
-                    if (p == pn)
-#pragma unroll
-                        for (int q = 0; q < RPL; ++q) a[q][p] = mk<T>(0, 0);
-            }
-        }
-        cp_async_wait_all();
-        __syncthreads();  // S1: pcol and nrow[buf] visible
-        // prefetch row c+1+kl (columns c+1..c+1+kv) for the next step, asynchronously
-        if (warp != 0 || NW == 1) {
-            const int r = c + 1 + kl;
-            const int t0 = (NW == 1) ? lane : threadIdx.x - 32;
-            const int ts = (NW == 1) ? 32 : blockDim.x - 32;
-            for (int t = t0; t <= kv; t += ts) {
-                if (r < n && c + 1 + t < n) cp_async_cx(&nrow[buf ^ 1][t], ab + (int64_t)r * ldab + t);
-                else nrow[buf ^ 1][t] = mk<T>(0, 0);
-            }
-        }
-        if (warp == 0) {
-            if (lane == 0) pcol[kl] = nrow[buf][0];
-            __syncwarp();
-            pivot_step(pcol, lvec, &piv_s, &info_s, c, n, kl, kv, ldab, ab, ipiv, lane);
-        }
-        __syncthreads();  // S2: pivot index and multipliers visible
-        const int prel = piv_s;
-        const cx<T>* nr = nrow[buf];
-        const int rsc = c % RS, lanec = rsc & 31, qc = rsc >> 5;
-        const int rsp = (c + prel) % RS, lanep = rsp & 31, qp = rsp >> 5;
-        const int rsn = (c + kl) % RS, lanen = rsn & 31, qn = rsn >> 5;
-        cx<T>* urow = ab + (int64_t)c * ldab;
-#pragma unroll
-        for (int p = 0; p < CPW; ++p) {
-            const int cs = warp * CPW + p;
-            const int k = c + 1 + posmod(cs - c - 1, CS);  // column held by this slot after step c
-            const bool colok = (k <= c + kv) && (k < n);
-            // value of row c in this column
-            cx<T> mine_c = a[0][p];
-#pragma unroll
-            for (int q = 1; q < RPL; ++q)
-                if (q == qc) mine_c = a[q][p];
-            const cx<T> vc = shfl_cx(mine_c, lanec);
-            const cx<T> vnew = (k - c <= kv) ? nr[k - c] : mk<T>(0, 0);
-            cx<T> u, newval;
-            if (prel == kl) {
-                u = vnew;
-                newval = vc;
-            } else {
-                newval = vnew;
-                if (prel != 0) {
-                    cx<T> mine_p = a[0][p];
-#pragma unroll
-                    for (int q = 1; q < RPL; ++q)
-                        if (q == qp) mine_p = a[q][p];
-                    u = shfl_cx(mine_p, lanep);
-                    if (lane == lanep) {
-#pragma unroll
-                        for (int q = 0; q < RPL; ++q)
-                            if (q == qp) a[q][p] = vc;
-                    }
-                } else {
-                    u = vc;
-                }
-            }
-            if (lane == lanec && colok) urow[k - c] = u;
-            if (lane == lanen) {
-#pragma unroll
-                for (int q = 0; q < RPL; ++q)
-                    if (q == qn) a[q][p] = newval;
-            }
-            if (colok) {
-#pragma unroll
-                for (int q = 0; q < RPL; ++q) {
-                    const int rs = lane + 32 * q;
-                    const int r = c + 1 + posmod(rs - c - 1, RS);
-                    if (r <= c + kl && r < n) a[q][p] = fms(a[q][p], lvec[r - c - 1], u);
-                }
-            }
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) info_all[j] = info_s;
-}
-
-// Register window, rows across warps and columns across lanes: row slot rs (r mod RS) is held
-// by warp rs / RPW (register index rs % RPW) and column slot cs (k mod CS) by lane cs % 32
-// (register index cs / 32). Per step: the lanes holding column c publish it (barrier 1); warp 0
-// picks the pivot and the multipliers (barrier 2); the warp holding the pivot row publishes it
-// (and the warp holding row c its old values when they move) (barrier 3); then every thread
-// swaps/inserts its own rows and applies a(r,k) -= l(r) u(k) to its RPW x CPL elements, with
-// l and u read from shared memory once per row and column.
-template <typename T, int NW, int RPW, int CPL>
-__global__ void __launch_bounds__(NW * 32, 1)
-    lu_regt_kernel(int n, int kl, int ku, int ldab, cx<T>* __restrict__ ab_all, int* __restrict__ ipiv_all,
-                   int* __restrict__ info_all, const int* __restrict__ active) {
-    const int j = blockIdx.x;
-    if (active && !active[j]) return;
-    constexpr int RS = NW * RPW;
-    constexpr int CS = 32 * CPL;
-    const int kv = kl + ku;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    cx<T>* ab = ab_all + (int64_t)j * n * ldab;
-    int* ipiv = ipiv_all + (int64_t)j * n;
-
-    // ring of PF+1 entering rows: row c+kl is fetched PF steps before step c
-    constexpr int PF = 8;
-    __shared__ cx<T> nrow[PF + 1][CS + 1];
-    __shared__ cx<T> pcol[RS + 1];
-    __shared__ cx<T> lvec[RS];
-    __shared__ cx<T> urow[CS];
-    __shared__ cx<T> oldc[CS];
-    __shared__ int piv_s, info_s;
-    if (threadIdx.x == 0) info_s = 0;
-
-    cx<T> a[RPW][CPL];
-#pragma unroll
-    for (int q = 0; q < RPW; ++q) {
-        const int r = warp * RPW + q;
-#pragma unroll
-        for (int p = 0; p < CPL; ++p) {
-            const int k = lane + 32 * p;
-            cx<T> v = mk<T>(0, 0);
-            const int t = k - r + kl;
-            if (r < kl && r < n && k < kv && k < n && t >= 0 && t <= kv) v = ab[(int64_t)r * ldab + t];
-            a[q][p] = v;
-        }
-    }
-    // rows kl .. kl+PF-1 (for steps 0 .. PF-1): one commit group per row
-    for (int d = 0; d < PF; ++d) {
-        const int r = kl + d;
-        for (int t = threadIdx.x; t <= kv; t += blockDim.x) {
-            if (r < n && d + t < n) cp_async_cx(&nrow[d][t], ab + (int64_t)r * ldab + t);
-            else nrow[d][t] = mk<T>(0, 0);
-        }
-        cp_async_commit();
-    }
-
-    // tcol[p] = (column slot - c - 1) mod CS: the column of register p is c+1+tcol[p];
-    // trow[q] = (row slot - c - 1) mod RS: the row of register q is c+1+trow[q]
-    int tcol[CPL], trow[RPW];
-#pragma unroll
-    for (int p = 0; p < CPL; ++p) tcol[p] = posmod(lane + 32 * p - 1, CS);
-#pragma unroll
-    for (int q = 0; q < RPW; ++q) trow[q] = posmod(warp * RPW + q - 1, RS);
-    for (int c = 0; c < n; ++c) {
-        const int buf = c % (PF + 1);
-        // (1) publish column c; its slot then starts column c+kv with zero fill
-        {
-            const int csc = c % CS;
-            if (lane == (csc & 31)) {
-                const int pc = csc >> 5;
-#pragma unroll
-                for (int p = 0; p < CPL; ++p) {
-                    if (p != pc) continue;
-#pragma unroll
-                    for (int q = 0; q < RPW; ++q) {
-                        const int i = posmod(warp * RPW + q - c, RS);
-                        if (i < kl) pcol[i] = a[q][p];
-                    }
-                }
-            }
-            const int csn = (c + kv) % CS;
-            if (lane == (csn & 31)) {
-                const int pn = csn >> 5;
-#pragma unroll
-                for (int p = 0; p < CPL; ++p)
-                    if (p == pn)
-#pragma unroll
-                        for (int q = 0; q < RPW; ++q) a[q][p] = mk<T>(0, 0);
-            }
-        }
-        cp_async_wait_group<PF - 1>();  // the group of row c+kl has landed
-        __syncthreads();  // S1
-        if (warp == 0) {
-            if (lane == 0) pcol[kl] = nrow[buf][0];
-            __syncwarp();
-            pivot_step<T, false>(pcol, lvec, &piv_s, &info_s, c, n, kl, kv, ldab, ab, ipiv, lane);
-        }
-        __syncthreads();  // S2
-        const int prel = piv_s;
-        // U(c,c) for the global copy below: pcol is rewritten before S1 of the next step
-        const cx<T> ucc = threadIdx.x == blockDim.x - 1 ? pcol[0] : mk<T>(0, 0);
-        const int rsc = c % RS, wc = rsc / RPW, qc = rsc % RPW;
-        const int rsp = (c + prel) % RS, wp = rsp / RPW, qp = rsp % RPW;
-        // (3) publish the pivot row (u) and, when row c moves, its old values
-        if (prel != kl && warp == wp) {
-#pragma unroll
-            for (int p = 0; p < CPL; ++p) {
-                if (tcol[p] < kv) {
-                    cx<T> v = a[0][p];
-#pragma unroll
-                    for (int q = 1; q < RPW; ++q)
-                        if (q == qp) v = a[q][p];
-                    urow[tcol[p]] = v;
-                }
-            }
-        }
-        if (prel != 0 && warp == wc) {
-#pragma unroll
-            for (int p = 0; p < CPL; ++p) {
-                if (tcol[p] < kv) {
-                    cx<T> v = a[0][p];
-#pragma unroll
-                    for (int q = 1; q < RPW; ++q)
-                        if (q == qc) v = a[q][p];
-                    oldc[tcol[p]] = v;
-                }
-            }
-        }
-        __syncthreads();  // S3
-        const cx<T>* u = (prel == kl) ? &nrow[buf][1] : urow;
-        // Memory traffic of the step, kept out of the pivot choice and the publication (it
-        // shares their queue): threads 0..kv-1 store U row c (columns c+1..c+kv), threads
-        // 128..128+kl-1 the L column from lvec (rewritten only after the next S1), the last
-        // thread U(c,c) and ipiv[c]; threads from 192 on fetch row c+kl+PF (columns
-        // c+PF..c+PF+kv) into the ring slot that step c-1 freed.
-        cx<T>* out = ab + (int64_t)c * ldab;
-        {
-            const int t = threadIdx.x;
-            if (t < kv && c + 1 + t < n) out[1 + t] = u[t];
-            if (t >= 128 && t < 128 + kl) out[kv + 1 + (t - 128)] = lvec[t - 128];
-            if (t == (int)blockDim.x - 1) {
-                out[0] = ucc;
-                ipiv[c] = c + prel;
-            }
-            const int r = c + kl + PF;
-            cx<T>* dst = nrow[(c + PF) % (PF + 1)];
-            for (int f = t - 192; f <= kv; f += blockDim.x - 192) {
-                if (f < 0) break;
-                if (r < n && c + PF + f < n) cp_async_cx(&dst[f], ab + (int64_t)r * ldab + f);
-                else dst[f] = mk<T>(0, 0);
-            }
-            cp_async_commit();
-        }
-        // (4) row moves (only the owner warps), new row c+kl, rank-1 update
-        const int rsn = (c + kl) % RS, wn = rsn / RPW, qn = rsn % RPW;
-        if (warp == wn || (warp == wp && prel != 0 && prel != kl)) {
-#pragma unroll
-            for (int p = 0; p < CPL; ++p) {
-                const int t = tcol[p];
-                if (t >= kv) continue;
-                if (prel != 0 && prel != kl && warp == wp) {
-#pragma unroll
-                    for (int q = 0; q < RPW; ++q)
-                        if (q == qp) a[q][p] = oldc[t];
-                }
-                if (warp == wn) {
-                    const cx<T> nv = (prel == kl) ? oldc[t] : nrow[buf][1 + t];
-#pragma unroll
-                    for (int q = 0; q < RPW; ++q)
-                        if (q == qn) a[q][p] = nv;
-                }
-            }
-        }
-        const bool interior = (c + kl < n) && (c + kv < n);  // no row or column beyond n-1
-        cx<T> lq[RPW];
-#pragma unroll
-        for (int q = 0; q < RPW; ++q) lq[q] = trow[q] < kl ? lvec[trow[q]] : mk<T>(0, 0);
-        if (interior) {
-#pragma unroll
-            for (int p = 0; p < CPL; ++p) {
-                if (tcol[p] >= kv) continue;
-                const cx<T> up = u[tcol[p]];
-#pragma unroll
-                for (int q = 0; q < RPW; ++q) a[q][p] = fms(a[q][p], lq[q], up);
-            }
-        } else {
-#pragma unroll
-            for (int p = 0; p < CPL; ++p) {
-                if (tcol[p] >= kv || c + 1 + tcol[p] >= n) continue;
-                const cx<T> up = u[tcol[p]];
-#pragma unroll
-                for (int q = 0; q < RPW; ++q)
-                    if (trow[q] < kl && c + 1 + trow[q] < n) a[q][p] = fms(a[q][p], lq[q], up);
-            }
-        }
-        // slot offsets for the next step
-#pragma unroll
-        for (int p = 0; p < CPL; ++p) tcol[p] = tcol[p] == 0 ? CS - 1 : tcol[p] - 1;
-#pragma unroll
-        for (int q = 0; q < RPW; ++q) trow[q] = trow[q] == 0 ? RS - 1 : trow[q] - 1;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) info_all[j] = info_s;
 }
 
 // Same elimination with the window W[cs*kl + rs] (row slot r mod kl, column slot k mod kv)
@@ -564,83 +191,12 @@ __global__ void __launch_bounds__(1024, 1)
 }
 
 // ------------------------------------------------------------------ dispatch
-template <typename T, int NW, int RPL, int CPW>
-static int run_reg(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st) {
-    lu_reg_kernel<T, NW, RPL, CPW><<<npts, NW * 32, 0, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, info, active);
-    NEP_CHECK_LAUNCH();
-    return NEP_OK;
-}
-
-template <typename T, int NW, int RPL>
-static int pick_cpw(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st,
-                    int cpw) {
-    switch (cpw) {
-        case 1: return run_reg<T, NW, RPL, 1>(s, npts, ab, ipiv, info, active, st);
-        case 2: return run_reg<T, NW, RPL, 2>(s, npts, ab, ipiv, info, active, st);
-        case 3: return run_reg<T, NW, RPL, 3>(s, npts, ab, ipiv, info, active, st);
-        case 4: return run_reg<T, NW, RPL, 4>(s, npts, ab, ipiv, info, active, st);
-        case 5: return run_reg<T, NW, RPL, 5>(s, npts, ab, ipiv, info, active, st);
-        case 6: return run_reg<T, NW, RPL, 6>(s, npts, ab, ipiv, info, active, st);
-        case 7: return run_reg<T, NW, RPL, 7>(s, npts, ab, ipiv, info, active, st);
-        case 8: return run_reg<T, NW, RPL, 8>(s, npts, ab, ipiv, info, active, st);
-    }
-    return NEP_ERR_INTERNAL;
-}
-
-// Register-window configuration for a band, or false if the band is too wide.
-template <typename T>
-static bool reg_config(int kl, int kv, int* nw, int* rpl, int* cpw) {
-    if (kl < 1 || kl > 64 || kv < 1) return false;
-    *rpl = (kl + 31) / 32;
-    *nw = sizeof(T) == 4 ? 32 : 16;
-    *cpw = (kv + *nw - 1) / *nw;
-    const int maxcpw = sizeof(T) == 4 ? 4 : 8;
-    return *cpw <= maxcpw;
-}
-
-template <typename T, int RPW, int CPL>
-static int run_regt(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st) {
-    lu_regt_kernel<T, 16, RPW, CPL><<<npts, 16 * 32, 0, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, info, active);
-    NEP_CHECK_LAUNCH();
-    return NEP_OK;
-}
-
-template <typename T, int RPW>
-static int regt_cpl(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st,
-                    int cpl) {
-    switch (cpl) {
-        case 1: return run_regt<T, RPW, 1>(s, npts, ab, ipiv, info, active, st);
-        case 2: return run_regt<T, RPW, 2>(s, npts, ab, ipiv, info, active, st);
-        case 3: return run_regt<T, RPW, 3>(s, npts, ab, ipiv, info, active, st);
-        case 4: return run_regt<T, RPW, 4>(s, npts, ab, ipiv, info, active, st);
-    }
-    return NEP_ERR_INTERNAL;
-}
-
 template <typename T>
 int launch_band_lu(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st) {
     if (npts <= 0) return NEP_OK;
     const int kv = s.kl + s.ku;
-    // transposed register window: 16 warps x RPW rows (kl <= 64), 32 lanes x CPL columns (kv <= 128)
-    if (s.kl >= 1 && s.kl <= 64 && kv >= 1 && kv <= 128) {
-        const int rpw = (s.kl + 15) / 16, cpl = (kv + 31) / 32;
-        switch (rpw) {
-            case 1: return regt_cpl<T, 1>(s, npts, ab, ipiv, info, active, st, cpl);
-            case 2: return regt_cpl<T, 2>(s, npts, ab, ipiv, info, active, st, cpl);
-            case 3: return regt_cpl<T, 3>(s, npts, ab, ipiv, info, active, st, cpl);
-            case 4: return regt_cpl<T, 4>(s, npts, ab, ipiv, info, active, st, cpl);
-        }
-    }
-    int nw, rpl, cpw;
-    if (reg_config<T>(s.kl, kv, &nw, &rpl, &cpw)) {
-        if (nw == 32) {
-            if (rpl == 1) return pick_cpw<T, 32, 1>(s, npts, ab, ipiv, info, active, st, cpw);
-            return pick_cpw<T, 32, 2>(s, npts, ab, ipiv, info, active, st, cpw);
-        } else {
-            if (rpl == 1) return pick_cpw<T, 16, 1>(s, npts, ab, ipiv, info, active, st, cpw);
-            return pick_cpw<T, 16, 2>(s, npts, ab, ipiv, info, active, st, cpw);
-        }
-    }
+    // register window, one barrier per step (lu_col.cu): kl <= 64, kv <= 128
+    if (band_lu_col_fits(s.kl, s.ku)) return launch_band_lu_col<T>(s, npts, ab, ipiv, info, active, st);
     // wide bands: blocked LU with the trailing window in global memory
     if (s.kl >= 1 && band_lu_wide_fits(s.kl, (int)sizeof(cx<T>)))
         return launch_band_lu_wide<T>(s, npts, ab, ipiv, info, active, st);

@@ -38,6 +38,22 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// 1/v for a nonzero pivot: conj(v) / |v|^2 with one correctly rounded reciprocal, where |v|^2 is
+// safely inside the normal range (the common case); Smith's scaled division otherwise.
+template <typename T>
+__device__ __forceinline__ cx<T> pivot_recip(cx<T> v) {
+    const T m = fmax(fabs(v.re), fabs(v.im));
+    const T lo = sizeof(T) == 4 ? T(1e-15) : T(1e-150), hi = sizeof(T) == 4 ? T(1e15) : T(1e150);
+    if (m >= lo && m <= hi) {
+        const T d = v.re * v.re + v.im * v.im;
+        T r;
+        if constexpr (sizeof(T) == 4) r = __frcp_rn(d);
+        else r = __drcp_rn(d);
+        return mk<T>(v.re * r, -v.im * r);
+    }
+    return cdiv(mk<T>(1, 0), v);
+}
+
 template <typename T, int RPL>
 __device__ __forceinline__ cx<T> sel_reg(const cx<T> (&a)[RPL], int q) {
     cx<T> v = a[0];

@@ -197,6 +197,11 @@ static inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b)
 template <typename T>
 int launch_assemble(const SplitDev& s, int npts, const zd* F, cx<T>* ab, double* tnorm, zd* tval, cudaStream_t st);
 // band_lu.cu
+// Register-window LU with one CTA barrier per column step (lu_col.cu): kl <= 64, kl + ku <= 128.
+bool band_lu_col_fits(int kl, int ku);
+template <typename T>
+int launch_band_lu_col(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active,
+                       cudaStream_t st);
 // Blocked LU for wide bands (lu_wide.cu): panel in shared memory, trailing window in global memory.
 bool band_lu_wide_fits(int kl, int elem_bytes);
 template <typename T>

@@ -9,17 +9,20 @@
 //
 // Register window with rows across lanes and columns across warps. Row slot s (lane s % 32,
 // register s / 32, s < kl) holds one window row and carries its row index as a label;
-// column slot s (warp s / CPW, register s % CPW, s < CS = 16 CPW >= kl+ku) holds column k with
-// k mod CS = s, also labelled. An interchange moves no data: the pivot row leaves the window
+// column slot s (warp s % 16, register s / 16, s < CS = 16 CPW >= kl+ku, a power of two) holds
+// column k with k mod CS = s. An interchange moves no data: the pivot row leaves the window
 // as row c of U, the entering row c+kl takes over its slot, and the slot of row c takes the
 // pivot row's label. The slot column c+1 leaves after step c+1's pivot takes column c+1+CS,
 // zero in every window row (beyond the band, or the band's next column when CS = kl+ku).
 // A column is held by one warp, so
 //   * the pivot row of a warp's columns passes through a per-warp shared buffer (no CTA
 //     barrier), and
-//   * the warp holding column c+1 computes that column's update first and chooses pivot c+1
-//     from it (warp reductions) while the other warps run step c (look-ahead); multipliers and
-//     pivot go to a double-buffered shared slot that the barrier ending the step publishes.
+//   * the warp holding column c+1 computes that column's update and chooses pivot c+1 from it
+//     (warp reductions) while the other warps run step c (look-ahead); multipliers and pivot go
+//     to a double-buffered shared slot that the barrier ending the step publishes. That warp
+//     runs its own part of step c at the start of step c+1, when the look-ahead has moved to the
+//     next warp (consecutive columns sit in consecutive warps), so the chain between two
+//     barriers is one column update and one pivot choice.
 // Rows entering the window are fetched PF steps ahead with cp.async by the other warps.
 #include "band_util.cuh"
 
@@ -47,34 +50,47 @@ __device__ __forceinline__ int warp_argmax_first(T best, int bi) {
     }
 }
 
-// acc - l u, the operations of fms(): for complex float as two packed f32x2 fused multiply-adds
-// over (re, im), (acc.re, acc.im) + (-l.re, -l.re)(u.re, u.im) then + (l.im, -l.im)(u.im, u.re),
-// lane for lane the same roundings as the scalar form.
-struct LPack {
-    unsigned long long nre, imm;  // (-l.re, -l.re), (l.im, -l.im)
-};
+// Packed pairs of floats for fma.rn.f32x2 (sm_100 and later): every lane is an ordinary fused
+// multiply-add with one rounding.
 __device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
     unsigned long long r;
     asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
     return r;
 }
-__device__ __forceinline__ LPack lpack(cx<float> l) { return LPack{pack2(-l.re, -l.re), pack2(l.im, -l.im)}; }
-__device__ __forceinline__ cx<float> fms_packed(cx<float> acc, const LPack& l, unsigned long long u,
-                                                unsigned long long us) {
-    unsigned long long a = pack2(acc.re, acc.im);
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a) : "l"(l.nre), "l"(u));
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a) : "l"(l.imm), "l"(us));
-    cx<float> r;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.re), "=f"(r.im) : "l"(a));
-    return r;
+__device__ __forceinline__ void unpack2(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// v, or +0 when z (by bit mask)
+template <typename T>
+__device__ __forceinline__ cx<T> mask_cx(cx<T> v, bool z) {
+    if constexpr (sizeof(T) == 8) {
+        const long long keep = z ? 0ll : -1ll;
+        return mk<T>(__longlong_as_double(__double_as_longlong(v.re) & keep),
+                     __longlong_as_double(__double_as_longlong(v.im) & keep));
+    } else {
+        const int keep = z ? 0 : -1;
+        return mk<T>(__int_as_float(__float_as_int(v.re) & keep), __int_as_float(__float_as_int(v.im) & keep));
+    }
 }
 
 template <typename T, int RPL, int CPW>
 __global__ void __launch_bounds__(512, 1)
     lu_col_kernel(int n, int kl, int ku, int ldab, cx<T>* __restrict__ ab_all, int* __restrict__ ipiv_all,
                   int* __restrict__ info_all, const int* __restrict__ active) {
-    constexpr int NW = 16, PF = 8, CS = NW * CPW;
-    constexpr bool PACKED = sizeof(T) == 4;
+    constexpr int NW = 16, PF = 8, RING = PF + 2, CS = NW * CPW;  // CS a power of two
+    // complex float with two row registers: the pair (row slot lane, row slot lane+32) of a
+    // column shares one 64-bit register for the real parts and one for the imaginary parts, so
+    // the update of a column is four f32x2 fused multiply-adds: with l = (l0, l1) and u the
+    // pivot row's value, re -= l.re u.re then re += l.im u.im, im -= l.re u.im then
+    // im -= l.im u.re, the operations of fms() lane for lane
+    constexpr bool PAIRED = sizeof(T) == 4 && RPL == 2;
+    static_assert((CS & (CS - 1)) == 0, "column slots must be a power of two");
     const int j = blockIdx.x;
     if (active && !active[j]) return;
     const int kv = kl + ku;
@@ -82,35 +98,82 @@ __global__ void __launch_bounds__(512, 1)
     cx<T>* ab = ab_all + (int64_t)j * n * ldab;
     int* ipiv = ipiv_all + (int64_t)j * n;
 
-    // row c+kl at [c % (PF+1)]: columns c .. c+CS (zero beyond c+kv)
-    __shared__ cx<T> nrow[PF + 1][CS + 1];
+    // row c+kl at [c % RING]: columns c .. c+CS (zero beyond c+kv); RING = PF + 2 keeps row
+    // c-1+kl readable during step c
+    __shared__ cx<T> nrow[RING][CS + 1];
     __shared__ cx<T> lvec[2][32 * RPL];  // multipliers of pivot step c by row slot, at [c & 1]
-    __shared__ cx<T> xrow[NW][CPW];      // per warp: the pivot row on its columns
+    // per warp: the pivot row on its columns, as (re, re, im, im) when PAIRED
+    __shared__ float4 xrow4[PAIRED ? NW : 1][PAIRED ? CPW : 1];
+    __shared__ cx<T> xrow[PAIRED ? 1 : NW][PAIRED ? 1 : CPW];
     __shared__ int piv_s[2], info_s;
     if (threadIdx.x == 0) info_s = 0;
 
+    cx<T> a[PAIRED ? 1 : RPL][CPW] = {};
+    unsigned long long are[PAIRED ? CPW : 1] = {}, aim[PAIRED ? CPW : 1] = {};
+    auto get = [&](int q, int p) __attribute__((always_inline)) -> cx<T> {
+        if constexpr (PAIRED) {
+            float r0, r1, i0, i1;
+            unpack2(are[p], r0, r1);
+            unpack2(aim[p], i0, i1);
+            return q == 0 ? mk<T>(r0, i0) : mk<T>(r1, i1);
+        } else {
+            return a[q][p];
+        }
+    };
+    auto set = [&](int q, int p, cx<T> v) __attribute__((always_inline)) {
+        if constexpr (PAIRED) {
+            float r0, r1, i0, i1;
+            unpack2(are[p], r0, r1);
+            unpack2(aim[p], i0, i1);
+            if (q == 0) {
+                r0 = v.re;
+                i0 = v.im;
+            } else {
+                r1 = v.re;
+                i1 = v.im;
+            }
+            are[p] = pack2(r0, r1);
+            aim[p] = pack2(i0, i1);
+        } else {
+            a[q][p] = v;
+        }
+    };
+    auto put_u = [&](int p, cx<T> v) __attribute__((always_inline)) {
+        if constexpr (PAIRED) xrow4[warp][p] = make_float4(v.re, v.re, v.im, v.im);
+        else xrow[warp][p] = v;
+    };
+    auto get_u = [&](int p) __attribute__((always_inline)) -> cx<T> {
+        if constexpr (PAIRED) {
+            const float4 u = xrow4[warp][p];
+            return mk<T>(u.x, u.z);
+        } else {
+            return xrow[warp][p];
+        }
+    };
+    // column slots interleave over the warps: slot s = p*NW + warp. Before step c the slot holds
+    // column k = c+1+((s-c-1) mod CS); toff is k - c
+    auto toff = [&](int p, int c) __attribute__((always_inline)) { return 1 + ((p * NW + warp - c - 1) & (CS - 1)); };
+
     bool vr[RPL];
-    int lab[RPL], colk[CPW];
-    cx<T> a[RPL][CPW];
+    int lab[RPL];
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
         vr[q] = lane + 32 * q < kl;
         lab[q] = vr[q] ? lane + 32 * q : 0x40000000;
     }
+    // rows 0..kl-1, columns 0..CS-1 (slot s holds column s until pivot 0 has used column 0)
 #pragma unroll
-    for (int p = 0; p < CPW; ++p) colk[p] = warp * CPW + p;
-    // rows 0..kl-1, columns 0..CS-1
+    for (int p = 0; p < CPW; ++p) {
 #pragma unroll
-    for (int q = 0; q < RPL; ++q)
-#pragma unroll
-        for (int p = 0; p < CPW; ++p) {
-            const int r = lane + 32 * q, k = colk[p], t = k - r + kl;
+        for (int q = 0; q < RPL; ++q) {
+            const int r = lane + 32 * q, k = p * NW + warp, t = k - r + kl;
             cx<T> v = mk<T>(0, 0);
             if (vr[q] && r < n && k < n && t >= 0 && t <= kv) v = ab[(int64_t)r * ldab + t];
-            a[q][p] = v;
+            set(q, p, v);
         }
+    }
     if (CS > kv)
-        for (int e = threadIdx.x; e < (PF + 1) * (CS - kv); e += blockDim.x)
+        for (int e = threadIdx.x; e < RING * (CS - kv); e += blockDim.x)
             nrow[e / (CS - kv)][kv + 1 + e % (CS - kv)] = mk<T>(0, 0);
     // rows kl .. kl+PF-1 (steps 0 .. PF-1): one commit group per row
     for (int d = 0; d < PF; ++d) {
@@ -125,9 +188,9 @@ __global__ void __launch_bounds__(512, 1)
     // Pivot of column c1 by the warp holding it: col[q] is the column's value in row slot q
     // (row lab[q], in c1 .. c1+kl-1); row c1+kl enters from nrow. Writes the multipliers by row
     // slot as they stand after the interchange (and to L), U(c1,c1), ipiv and the pivot row.
-    auto pivot = [&](int c1, const cx<T>(&col)[RPL]) {
+    auto pivot = [&](int c1, const cx<T>(&col)[RPL]) __attribute__((always_inline)) {
         const int nb = c1 & 1, re = c1 + kl;
-        const cx<T> ve = nrow[c1 % (PF + 1)][0];
+        const cx<T> ve = nrow[c1 % RING][0];
         T best = T(-1);
         int bi = 0x7fffffff;
 #pragma unroll
@@ -188,112 +251,156 @@ __global__ void __launch_bounds__(512, 1)
         }
     };
 
+    // Step cc on this warp's columns: publish the pivot row (row Pc; the entering row when
+    // Pc = cc+kl), the pivot's slot takes the entering row, a(r, k) -= l(r) u(k), U(cc, k) to
+    // the band, and the slot of column cc+1 (if this warp holds it) empties for column cc+1+CS.
+    auto run_step = [&](int cc, int Pc, const bool(&ispc)[RPL], const cx<T>(&lqc)[RPL]) __attribute__((always_inline)) {
+        const cx<T>* nrc = nrow[cc % RING];
+#pragma unroll
+        for (int q = 0; q < RPL; ++q)
+            if (ispc[q])
+#pragma unroll
+                for (int p = 0; p < CPW; ++p) {
+                    put_u(p, get(q, p));
+                    set(q, p, nrc[toff(p, cc)]);
+                }
+        if (Pc == cc + kl && lane == 0)
+#pragma unroll
+            for (int p = 0; p < CPW; ++p) put_u(p, nrc[toff(p, cc)]);
+        __syncwarp();
+        if constexpr (PAIRED) {
+            const unsigned long long nlre = pack2(-lqc[0].re, -lqc[1].re), lim = pack2(lqc[0].im, lqc[1].im),
+                                     nlim = pack2(-lqc[0].im, -lqc[1].im);
+#pragma unroll
+            for (int p = 0; p < CPW; ++p) {
+                const float4 u = xrow4[warp][p];
+                const unsigned long long ur = pack2(u.x, u.y), ui = pack2(u.z, u.w);
+                are[p] = fma2(nlre, ur, are[p]);
+                are[p] = fma2(lim, ui, are[p]);
+                aim[p] = fma2(nlre, ui, aim[p]);
+                aim[p] = fma2(nlim, ur, aim[p]);
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < CPW; ++p) {
+                const cx<T> u = xrow[warp][p];
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) a[q][p] = fms(a[q][p], lqc[q], u);
+            }
+        }
+        if (lane < CPW) {
+            const int t = toff(lane, cc);
+            if (t <= kv && cc + t < n) ab[(int64_t)cc * ldab + t] = get_u(lane);
+        }
+        // (a bit mask on every slot rather than a store to one: a store to a slot chosen at run
+        // time would move the window out of registers)
+        const int s1 = (cc + 1) & (CS - 1);
+#pragma unroll
+        for (int p = 0; p < CPW; ++p) {
+            const bool z = (s1 & (NW - 1)) == warp && p == s1 / NW;
+            if constexpr (PAIRED) {
+                const unsigned long long keep = z ? 0ull : ~0ull;
+                are[p] &= keep;
+                aim[p] &= keep;
+            } else {
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) a[q][p] = mask_cx(a[q][p], z);
+            }
+        }
+        __syncwarp();  // the buffer is read before the next step publishes into it
+    };
+
     cp_async_wait_group<PF - 1>();  // row kl
     __syncthreads();
     if (warp == 0) {
         cx<T> col[RPL];
 #pragma unroll
-        for (int q = 0; q < RPL; ++q) col[q] = a[q][0];
+        for (int q = 0; q < RPL; ++q) col[q] = get(q, 0);
         pivot(0, col);
-    }
-    // column 0 leaves: its slot holds column CS, zero in rows < kl
-    if (warp == 0) {
+        // column 0 leaves: its slot holds column CS, zero in rows < kl
 #pragma unroll
-        for (int q = 0; q < RPL; ++q) a[q][0] = mk<T>(0, 0);
-        colk[0] += CS;
+        for (int q = 0; q < RPL; ++q) set(q, 0, mk<T>(0, 0));
     }
     cp_async_wait_group<PF - 2>();  // row kl+1, for the look-ahead of step 0
     __syncthreads();
 
-    int s1 = 1 % CS;  // column slot of column c+1
+    // the warp that chose pivot c+1 during step c runs its own step c at the start of step c+1
+    bool deferred = false;
+    int Pd = 0;
+    bool ispd[RPL];
+    cx<T> lqd[RPL];
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+        ispd[q] = false;
+        lqd[q] = mk<T>(0, 0);
+    }
     for (int c = 0; c < n; ++c) {
+        if (deferred) {
+            run_step(c - 1, Pd, ispd, lqd);
+            deferred = false;
+        }
         const int cb = c & 1, re = c + kl;
         const int P = piv_s[cb];
-        const bool in_win = P != re;
-        const cx<T>* nr = nrow[c % (PF + 1)];
-        // the pivot row's slot takes the entering row; publish the pivot row on this warp's columns
         bool isp[RPL];
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-            isp[q] = in_win && lab[q] == P;
-            if (isp[q])
-#pragma unroll
-                for (int p = 0; p < CPW; ++p) xrow[warp][p] = a[q][p];
-        }
-        if (!in_win && lane == 0)
-#pragma unroll
-            for (int p = 0; p < CPW; ++p) xrow[warp][p] = nr[colk[p] - c];
-        // labels after the interchange
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) lab[q] = isp[q] ? re : (lab[q] == c ? P : lab[q]);
         cx<T> lq[RPL];
 #pragma unroll
-        for (int q = 0; q < RPL; ++q) lq[q] = vr[q] ? lvec[cb][lane + 32 * q] : mk<T>(0, 0);
-        __syncwarp();
-        cx<T>* urow = ab + (int64_t)c * ldab;
-        const int w1 = s1 / CPW, p1 = s1 % CPW;
-        const bool look = warp == w1 && c + 1 < n;
-        if (look) {
-            // column c+1 after step c, for the pivot of step c+1
-            const cx<T> u1 = xrow[warp][p1], vn1 = nr[1];
-            cx<T> col[RPL];
+        for (int q = 0; q < RPL; ++q) {
+            isp[q] = P != re && lab[q] == P;
+            lab[q] = isp[q] ? re : (lab[q] == c ? P : lab[q]);  // labels after the interchange
+            lq[q] = vr[q] ? lvec[cb][lane + 32 * q] : mk<T>(0, 0);
+        }
+        const int s1 = (c + 1) & (CS - 1), w1 = s1 & (NW - 1), p1 = s1 / NW;
+        if (warp == w1 && c + 1 < n) {
+            // column c+1 after step c, for the pivot of step c+1 (look-ahead); the rest of step
+            // c on this warp's columns waits for the next step
+            const cx<T>* nr = nrow[c % RING];
+            cx<T> mine[RPL];
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) mine[q] = mk<T>(0, 0);
 #pragma unroll
             for (int p = 0; p < CPW; ++p)
                 if (p == p1)
 #pragma unroll
-                    for (int q = 0; q < RPL; ++q) col[q] = fms(isp[q] ? vn1 : a[q][p], lq[q], u1);
-            pivot(c + 1, col);
-        }
-        // step c on every column of this warp (interchange, entering row, U(c, k), rank-1)
-        if constexpr (PACKED) {
-            LPack lp[RPL];
+                    for (int q = 0; q < RPL; ++q) mine[q] = get(q, p);
+            cx<T> up = mine[0];
+            bool has = isp[0];
 #pragma unroll
-            for (int q = 0; q < RPL; ++q) lp[q] = lpack(reinterpret_cast<const cx<float>&>(lq[q]));
-#pragma unroll
-            for (int p = 0; p < CPW; ++p) {
-                const int t = colk[p] - c;
-                const cx<T> u = xrow[warp][p], vn = nr[t];
-                if (lane == p && t <= kv && colk[p] < n) urow[t] = u;
-                const unsigned long long u2 = pack2(u.re, u.im), us2 = pack2(u.im, u.re);
-#pragma unroll
-                for (int q = 0; q < RPL; ++q) {
-                    const cx<T> x = isp[q] ? vn : a[q][p];
-                    a[q][p] = fms_packed(x, lp[q], u2, us2);
+            for (int q = 1; q < RPL; ++q)
+                if (isp[q]) {
+                    up = mine[q];
+                    has = true;
                 }
+            const int lp = __ffs(__ballot_sync(0xffffffffu, has)) - 1;
+            const cx<T> vn1 = nr[1];
+            const cx<T> u1 = P == re ? vn1 : shfl_cx(up, lp < 0 ? 0 : lp);
+            cx<T> col[RPL];
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) col[q] = fms(isp[q] ? vn1 : mine[q], lq[q], u1);
+            pivot(c + 1, col);
+            deferred = true;
+            Pd = P;
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+                ispd[q] = isp[q];
+                lqd[q] = lq[q];
             }
         } else {
-#pragma unroll
-            for (int p = 0; p < CPW; ++p) {
-                const int t = colk[p] - c;
-                const cx<T> u = xrow[warp][p], vn = nr[t];
-                if (lane == p && t <= kv && colk[p] < n) urow[t] = u;
-#pragma unroll
-                for (int q = 0; q < RPL; ++q) a[q][p] = fms(isp[q] ? vn : a[q][p], lq[q], u);
-            }
+            run_step(c, P, isp, lq);
         }
-        // column c+1 leaves at step c+1: its slot holds column c+1+CS, zero in the window rows
-#pragma unroll
-        for (int p = 0; p < CPW; ++p)
-            if (colk[p] == c + 1) {
-#pragma unroll
-                for (int q = 0; q < RPL; ++q) a[q][p] = mk<T>(0, 0);
-                colk[p] += CS;
-            }
-        // row c+kl+PF (columns c+PF .. c+PF+kv) into the ring slot step c-1 freed, by the warps
-        // after the look-ahead warp
+        // row c+kl+PF (columns c+PF .. c+PF+kv) into ring slot (c+PF) % RING, by the warps after
+        // the look-ahead warp (the one behind it runs two steps' updates in this step)
         {
-            const int idx = ((warp - w1 - 1 + NW) % NW) * 32 + lane;
+            const int idx = ((warp - w1 - 1) & (NW - 1)) * 32 + lane;
             const int r = c + kl + PF;
-            cx<T>* dst = nrow[(c + PF) % (PF + 1)];
-            if (idx < (NW - 1) * 32 && idx <= kv) {
+            cx<T>* dst = nrow[(c + PF) % RING];
+            if (idx < (NW - 2) * 32 && idx <= kv) {
                 if (r < n && c + PF + idx < n) cp_async_cx(&dst[idx], ab + (int64_t)r * ldab + idx);
                 else dst[idx] = mk<T>(0, 0);
             }
             cp_async_commit();
         }
-        s1 = s1 + 1 == CS ? 0 : s1 + 1;
         cp_async_wait_group<PF - 2>();  // row c+2+kl, for the look-ahead of step c+1
-        __syncthreads();                // pivot c+1 published; xrow and lvec[cb] free
+        __syncthreads();                // pivot c+1 published
     }
     if (threadIdx.x == 0) info_all[j] = info_s;
 }
@@ -309,15 +416,12 @@ static int run_col(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info,
 
 template <typename T, int RPL>
 static int col_cpw(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st) {
-    // 16 warps x CPW column slots >= kl + ku, CPW even
-    const int cpw = ((s.kl + s.ku + 15) / 16 + 1) & ~1;
-    switch (cpw) {
-        case 2: return run_col<T, RPL, 2>(s, npts, ab, ipiv, info, active, st);
-        case 4: return run_col<T, RPL, 4>(s, npts, ab, ipiv, info, active, st);
-        case 6: return run_col<T, RPL, 6>(s, npts, ab, ipiv, info, active, st);
-        case 8: return run_col<T, RPL, 8>(s, npts, ab, ipiv, info, active, st);
-    }
-    return NEP_ERR_INTERNAL;
+    // 16 warps x CPW column slots >= kl + ku, CPW a power of two
+    const int kv = s.kl + s.ku;
+    if (kv <= 16) return run_col<T, RPL, 1>(s, npts, ab, ipiv, info, active, st);
+    if (kv <= 32) return run_col<T, RPL, 2>(s, npts, ab, ipiv, info, active, st);
+    if (kv <= 64) return run_col<T, RPL, 4>(s, npts, ab, ipiv, info, active, st);
+    return run_col<T, RPL, 8>(s, npts, ab, ipiv, info, active, st);
 }
 
 template <typename T>

@@ -84,12 +84,13 @@ __global__ void __launch_bounds__(512, 1)
     lu_col_kernel(int n, int kl, int ku, int ldab, cx<T>* __restrict__ ab_all, int* __restrict__ ipiv_all,
                   int* __restrict__ info_all, const int* __restrict__ active) {
     constexpr int NW = 16, PF = 8, RING = PF + 2, CS = NW * CPW;  // CS a power of two
-    // complex float with two row registers: the pair (row slot lane, row slot lane+32) of a
-    // column shares one 64-bit register for the real parts and one for the imaginary parts, so
-    // the update of a column is four f32x2 fused multiply-adds: with l = (l0, l1) and u the
-    // pivot row's value, re -= l.re u.re then re += l.im u.im, im -= l.re u.im then
-    // im -= l.im u.re, the operations of fms() lane for lane
-    constexpr bool PAIRED = sizeof(T) == 4 && RPL == 2;
+    // complex float: the column registers pair up, (2h, 2h+1), one 64-bit register for the two
+    // real parts of a row and one for the imaginary parts. With u = (u0, u1) the pivot row on the
+    // pair and l the row's multiplier, a pair's update is four f32x2 fused multiply-adds,
+    // re -= l.re u.re, re += l.im u.im, im -= l.re u.im, im -= l.im u.re: the operations of fms()
+    // lane for lane. The pivot row's registers are the broadcast format as they stand.
+    constexpr bool PAIRED = sizeof(T) == 4 && CPW % 2 == 0;
+    constexpr int CPH = PAIRED ? CPW / 2 : 1;
     static_assert((CS & (CS - 1)) == 0, "column slots must be a power of two");
     const int j = blockIdx.x;
     if (active && !active[j]) return;
@@ -102,20 +103,20 @@ __global__ void __launch_bounds__(512, 1)
     // c-1+kl readable during step c
     __shared__ cx<T> nrow[RING][CS + 1];
     __shared__ cx<T> lvec[2][32 * RPL];  // multipliers of pivot step c by row slot, at [c & 1]
-    // per warp: the pivot row on its columns, as (re, re, im, im) when PAIRED
-    __shared__ float4 xrow4[PAIRED ? NW : 1][PAIRED ? CPW : 1];
+    // per warp: the pivot row on its columns; when PAIRED, (re 2h, re 2h+1, im 2h, im 2h+1)
+    __shared__ ulonglong2 xrow2[PAIRED ? NW : 1][CPH];
     __shared__ cx<T> xrow[PAIRED ? 1 : NW][PAIRED ? 1 : CPW];
     __shared__ int piv_s[2], info_s;
     if (threadIdx.x == 0) info_s = 0;
 
     cx<T> a[PAIRED ? 1 : RPL][CPW] = {};
-    unsigned long long are[PAIRED ? CPW : 1] = {}, aim[PAIRED ? CPW : 1] = {};
+    unsigned long long are[PAIRED ? RPL : 1][CPH] = {}, aim[PAIRED ? RPL : 1][CPH] = {};
     auto get = [&](int q, int p) __attribute__((always_inline)) -> cx<T> {
         if constexpr (PAIRED) {
             float r0, r1, i0, i1;
-            unpack2(are[p], r0, r1);
-            unpack2(aim[p], i0, i1);
-            return q == 0 ? mk<T>(r0, i0) : mk<T>(r1, i1);
+            unpack2(are[q][p >> 1], r0, r1);
+            unpack2(aim[q][p >> 1], i0, i1);
+            return (p & 1) ? mk<T>(r1, i1) : mk<T>(r0, i0);
         } else {
             return a[q][p];
         }
@@ -123,29 +124,26 @@ __global__ void __launch_bounds__(512, 1)
     auto set = [&](int q, int p, cx<T> v) __attribute__((always_inline)) {
         if constexpr (PAIRED) {
             float r0, r1, i0, i1;
-            unpack2(are[p], r0, r1);
-            unpack2(aim[p], i0, i1);
-            if (q == 0) {
-                r0 = v.re;
-                i0 = v.im;
-            } else {
+            unpack2(are[q][p >> 1], r0, r1);
+            unpack2(aim[q][p >> 1], i0, i1);
+            if (p & 1) {
                 r1 = v.re;
                 i1 = v.im;
+            } else {
+                r0 = v.re;
+                i0 = v.im;
             }
-            are[p] = pack2(r0, r1);
-            aim[p] = pack2(i0, i1);
+            are[q][p >> 1] = pack2(r0, r1);
+            aim[q][p >> 1] = pack2(i0, i1);
         } else {
             a[q][p] = v;
         }
     };
-    auto put_u = [&](int p, cx<T> v) __attribute__((always_inline)) {
-        if constexpr (PAIRED) xrow4[warp][p] = make_float4(v.re, v.re, v.im, v.im);
-        else xrow[warp][p] = v;
-    };
+    // the broadcast pivot row: element p of this warp's columns
     auto get_u = [&](int p) __attribute__((always_inline)) -> cx<T> {
         if constexpr (PAIRED) {
-            const float4 u = xrow4[warp][p];
-            return mk<T>(u.x, u.z);
+            const float* f = reinterpret_cast<const float*>(&xrow2[warp][p >> 1]);
+            return mk<T>(f[p & 1], f[2 + (p & 1)]);
         } else {
             return xrow[warp][p];
         }
@@ -256,29 +254,57 @@ __global__ void __launch_bounds__(512, 1)
     // the band, and the slot of column cc+1 (if this warp holds it) empties for column cc+1+CS.
     auto run_step = [&](int cc, int Pc, const bool(&ispc)[RPL], const cx<T>(&lqc)[RPL]) __attribute__((always_inline)) {
         const cx<T>* nrc = nrow[cc % RING];
+        // the pivot row's lane publishes its registers, then takes the entering row into them
 #pragma unroll
         for (int q = 0; q < RPL; ++q)
-            if (ispc[q])
+            if (ispc[q]) {
+                if constexpr (PAIRED) {
 #pragma unroll
-                for (int p = 0; p < CPW; ++p) {
-                    put_u(p, get(q, p));
-                    set(q, p, nrc[toff(p, cc)]);
+                    for (int h = 0; h < CPH; ++h) {
+                        xrow2[warp][h] = make_ulonglong2(are[q][h], aim[q][h]);
+                        const cx<T> v0 = nrc[toff(2 * h, cc)], v1 = nrc[toff(2 * h + 1, cc)];
+                        are[q][h] = pack2(v0.re, v1.re);
+                        aim[q][h] = pack2(v0.im, v1.im);
+                    }
+                } else {
+#pragma unroll
+                    for (int p = 0; p < CPW; ++p) {
+                        xrow[warp][p] = a[q][p];
+                        a[q][p] = nrc[toff(p, cc)];
+                    }
                 }
-        if (Pc == cc + kl && lane == 0)
+            }
+        if (Pc == cc + kl && lane == 0) {  // the pivot is the entering row itself
+            if constexpr (PAIRED) {
 #pragma unroll
-            for (int p = 0; p < CPW; ++p) put_u(p, nrc[toff(p, cc)]);
+                for (int h = 0; h < CPH; ++h) {
+                    const cx<T> v0 = nrc[toff(2 * h, cc)], v1 = nrc[toff(2 * h + 1, cc)];
+                    xrow2[warp][h] = make_ulonglong2(pack2(v0.re, v1.re), pack2(v0.im, v1.im));
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < CPW; ++p) xrow[warp][p] = nrc[toff(p, cc)];
+            }
+        }
         __syncwarp();
         if constexpr (PAIRED) {
-            const unsigned long long nlre = pack2(-lqc[0].re, -lqc[1].re), lim = pack2(lqc[0].im, lqc[1].im),
-                                     nlim = pack2(-lqc[0].im, -lqc[1].im);
+            unsigned long long nlre[RPL], lim[RPL], nlim[RPL];
 #pragma unroll
-            for (int p = 0; p < CPW; ++p) {
-                const float4 u = xrow4[warp][p];
-                const unsigned long long ur = pack2(u.x, u.y), ui = pack2(u.z, u.w);
-                are[p] = fma2(nlre, ur, are[p]);
-                are[p] = fma2(lim, ui, are[p]);
-                aim[p] = fma2(nlre, ui, aim[p]);
-                aim[p] = fma2(nlim, ur, aim[p]);
+            for (int q = 0; q < RPL; ++q) {
+                nlre[q] = pack2(-lqc[q].re, -lqc[q].re);
+                lim[q] = pack2(lqc[q].im, lqc[q].im);
+                nlim[q] = pack2(-lqc[q].im, -lqc[q].im);
+            }
+#pragma unroll
+            for (int h = 0; h < CPH; ++h) {
+                const ulonglong2 u = xrow2[warp][h];  // (re pair, im pair)
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) {
+                    are[q][h] = fma2(nlre[q], u.x, are[q][h]);
+                    are[q][h] = fma2(lim[q], u.y, are[q][h]);
+                    aim[q][h] = fma2(nlre[q], u.y, aim[q][h]);
+                    aim[q][h] = fma2(nlim[q], u.x, aim[q][h]);
+                }
             }
         } else {
 #pragma unroll
@@ -292,19 +318,28 @@ __global__ void __launch_bounds__(512, 1)
             const int t = toff(lane, cc);
             if (t <= kv && cc + t < n) ab[(int64_t)cc * ldab + t] = get_u(lane);
         }
-        // (a bit mask on every slot rather than a store to one: a store to a slot chosen at run
-        // time would move the window out of registers)
+        // the slot of column cc+1 empties for column cc+1+CS (in the warp holding it; a bit
+        // mask on every register rather than a store to one chosen at run time, which would
+        // move the window out of registers)
         const int s1 = (cc + 1) & (CS - 1);
-#pragma unroll
-        for (int p = 0; p < CPW; ++p) {
-            const bool z = (s1 & (NW - 1)) == warp && p == s1 / NW;
+        if ((s1 & (NW - 1)) == warp) {
+            const int pz = s1 / NW;
             if constexpr (PAIRED) {
-                const unsigned long long keep = z ? 0ull : ~0ull;
-                are[p] &= keep;
-                aim[p] &= keep;
+                const unsigned long long keep = (pz & 1) ? 0x00000000ffffffffull : 0xffffffff00000000ull;
+#pragma unroll
+                for (int h = 0; h < CPH; ++h) {
+                    const unsigned long long m = h == (pz >> 1) ? keep : ~0ull;
+#pragma unroll
+                    for (int q = 0; q < RPL; ++q) {
+                        are[q][h] &= m;
+                        aim[q][h] &= m;
+                    }
+                }
             } else {
 #pragma unroll
-                for (int q = 0; q < RPL; ++q) a[q][p] = mask_cx(a[q][p], z);
+                for (int p = 0; p < CPW; ++p)
+#pragma unroll
+                    for (int q = 0; q < RPL; ++q) a[q][p] = mask_cx(a[q][p], p == pz);
             }
         }
         __syncwarp();  // the buffer is read before the next step publishes into it

@@ -21,52 +21,63 @@
 namespace nep {
 
 // ------------------------------------------------------------------ dense products
-constexpr int GB = 32, GK = 8;
-
-__global__ void __launch_bounds__(256) zgemm_kernel(int M, int N, int K, int opA, const zd* __restrict__ A, int lda,
-                                                    const zd* __restrict__ B, int ldb, zd* __restrict__ C, int ldc,
-                                                    int kchunk, int64_t part_stride) {
-    __shared__ zd As[GK][GB + 1];
-    __shared__ zd Bs[GK][GB + 1];
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    const int m0 = blockIdx.x * GB, n0 = blockIdx.y * GB;
+// C = op(A) B (column-major, op in {A, A^H}). A CTA computes a BM x BN tile with (BM/TM) x (BN/TN)
+// threads of TM x TN outputs, K in steps of GK through shared memory; long K splits over CTAs
+// into a workspace reduced in a fixed order, so results never depend on scheduling. FP64
+// arithmetic is the bound on this part (about two FP64 FMAs per clock per SM), so the launcher
+// picks the tile shape and the split that waste the least of it: padding beyond M and N (the
+// reduced dimensions here are rarely multiples of 32) and SMs left idle or doubly loaded.
+constexpr int GK = 8;
+template <int BM, int BN, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    zgemm_kernel(int M, int N, int K, int opA, const zd* __restrict__ A, int lda, const zd* __restrict__ B, int ldb,
+                 zd* __restrict__ C, int ldc, int kchunk, int64_t part_stride) {
+    constexpr int TX = BM / TM, TY = BN / TN, NT = TX * TY;
+    __shared__ zd As[GK][BM + 1];
+    __shared__ zd Bs[GK][BN + 1];
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
     const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-    zd acc[2][2];
+    zd acc[TM][TN];
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < TM; ++a)
 #pragma unroll
-        for (int b = 0; b < 2; ++b) acc[a][b] = mk(0.0, 0.0);
+        for (int b = 0; b < TN; ++b) acc[a][b] = mk(0.0, 0.0);
     for (int k0 = kb; k0 < ke; k0 += GK) {
-        for (int t = threadIdx.x; t < GK * GB; t += 256) {
-            const int kk = t % GK, mm = t / GK;
+        // loads run along the contiguous index of each operand
+        for (int t = threadIdx.x; t < GK * BM; t += NT) {
+            const int kk = opA == 0 ? t / BM : t % GK, mm = opA == 0 ? t % BM : t / GK;
             const int gm = m0 + mm, gk = k0 + kk;
             zd v = mk(0.0, 0.0);
             if (gm < M && gk < ke) v = opA == 0 ? A[gm + (int64_t)lda * gk] : conj(A[gk + (int64_t)lda * gm]);
             As[kk][mm] = v;
-            const int nn = t / GK;
-            const int gn = n0 + nn;
-            zd w = mk(0.0, 0.0);
-            if (gn < N && gk < ke) w = B[gk + (int64_t)ldb * gn];
-            Bs[kk][nn] = w;
+        }
+        for (int t = threadIdx.x; t < GK * BN; t += NT) {
+            const int kk = t % GK, nn = t / GK;
+            const int gn = n0 + nn, gk = k0 + kk;
+            Bs[kk][nn] = (gn < N && gk < ke) ? B[gk + (int64_t)ldb * gn] : mk(0.0, 0.0);
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < GK; ++kk) {
-            const zd a0 = As[kk][tx], a1 = As[kk][tx + 16];
-            const zd b0 = Bs[kk][ty], b1 = Bs[kk][ty + 16];
-            acc[0][0] = fma_(acc[0][0], a0, b0);
-            acc[1][0] = fma_(acc[1][0], a1, b0);
-            acc[0][1] = fma_(acc[0][1], a0, b1);
-            acc[1][1] = fma_(acc[1][1], a1, b1);
+            zd av[TM], bv[TN];
+#pragma unroll
+            for (int a = 0; a < TM; ++a) av[a] = As[kk][tx + TX * a];
+#pragma unroll
+            for (int b = 0; b < TN; ++b) bv[b] = Bs[kk][ty + TY * b];
+#pragma unroll
+            for (int a = 0; a < TM; ++a)
+#pragma unroll
+                for (int b = 0; b < TN; ++b) acc[a][b] = fma_(acc[a][b], av[a], bv[b]);
         }
         __syncthreads();
     }
     zd* Cz = C + (int64_t)blockIdx.z * part_stride;
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < TM; ++a)
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const int gm = m0 + tx + 16 * a, gn = n0 + ty + 16 * b;
+        for (int b = 0; b < TN; ++b) {
+            const int gm = m0 + tx + TX * a, gn = n0 + ty + TY * b;
             if (gm < M && gn < N) Cz[gm + (int64_t)ldc * gn] = acc[a][b];
         }
 }
@@ -80,29 +91,71 @@ __global__ void zgemm_reduce_kernel(int M, int N, int splits, const zd* __restri
     C[m + (int64_t)ldc * n] = acc;
 }
 
+namespace {
+struct GemmShape {
+    int bm, bn;
+};
+constexpr GemmShape kGemmShapes[] = {{64, 32}, {64, 24}, {32, 32}, {32, 24}, {24, 24}, {32, 16}, {24, 16}};
+
+template <int BM, int BN, int TM, int TN>
+void zgemm_launch(dim3 grid, int M, int N, int K, int opA, const zd* A, int lda, const zd* B, int ldb, zd* C, int ldc,
+                  int kchunk, int64_t part_stride, cudaStream_t st) {
+    zgemm_kernel<BM, BN, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(M, N, K, opA, A, lda, B, ldb, C, ldc, kchunk,
+                                                                       part_stride);
+}
+}  // namespace
+
 // C = op(A) B. part: workspace of splits*M*N elements when K is long (nullptr => no split).
 int zgemm(int M, int N, int K, int opA, const zd* A, int lda, const zd* B, int ldb, zd* C, int ldc, zd* part,
           size_t part_elems, cudaStream_t st) {
     if (M <= 0 || N <= 0) return NEP_OK;
-    const int tiles = ceil_div(M, GB) * ceil_div(N, GB);
-    int splits = 1;
-    if (part && K > 256 && tiles < 152) {
-        splits = std::min(ceil_div(K, 256), std::max(1, 304 / tiles));
-        while (splits > 1 && (size_t)splits * M * N > part_elems) --splits;
+    static const int sms = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 152;
+    }();
+    // score = useful fraction of the padded tiles x SM load balance (mean over max CTAs per SM),
+    // a split costing a little for its partial sums and their reduction
+    int best = 0, best_splits = 1;
+    double best_score = -1.0;
+    for (int c = 0; c < (int)(sizeof(kGemmShapes) / sizeof(kGemmShapes[0])); ++c) {
+        const int bm = kGemmShapes[c].bm, bn = kGemmShapes[c].bn;
+        const int64_t tiles = (int64_t)ceil_div(M, bm) * ceil_div(N, bn);
+        const double pad = (double)M * N / ((double)ceil_div(M, bm) * bm * ceil_div(N, bn) * bn);
+        const int max_splits = part ? std::max(1, std::min<int>(K / 32, (int)std::min<size_t>(64, part_elems / ((size_t)M * N)))) : 1;
+        for (int sp = 1; sp <= max_splits; ++sp) {
+            const double ctas = (double)tiles * sp;
+            const double waves = std::ceil(ctas / sms);
+            const double score = pad * (ctas / sms) / waves * (sp > 1 ? 0.97 : 1.0);
+            if (score > best_score + 1e-9) {
+                best_score = score;
+                best = c;
+                best_splits = sp;
+            }
+        }
     }
-    const int kchunk = ceil_div(ceil_div(K, splits), GK) * GK;
-    splits = ceil_div(K, kchunk);
-    if (splits < 1) splits = 1;
-    dim3 grid(ceil_div(M, GB), ceil_div(N, GB), splits);
-    if (splits == 1) {
-        zgemm_kernel<<<grid, 256, 0, st>>>(M, N, K, opA, A, lda, B, ldb, C, ldc, kchunk, 0);
+    const int bm = kGemmShapes[best].bm, bn = kGemmShapes[best].bn;
+    const int kchunk = ceil_div(ceil_div(K, best_splits), GK) * GK;
+    const int splits = std::max(1, ceil_div(K, kchunk));
+    dim3 grid(ceil_div(M, bm), ceil_div(N, bn), splits);
+    zd* out = splits == 1 ? C : part;
+    const int ldo = splits == 1 ? ldc : M;
+    const int64_t ps = splits == 1 ? 0 : (int64_t)M * N;
+    switch (best) {
+        case 0: zgemm_launch<64, 32, 4, 2>(grid, M, N, K, opA, A, lda, B, ldb, out, ldo, kchunk, ps, st); break;
+        case 1: zgemm_launch<64, 24, 4, 2>(grid, M, N, K, opA, A, lda, B, ldb, out, ldo, kchunk, ps, st); break;
+        case 2: zgemm_launch<32, 32, 2, 2>(grid, M, N, K, opA, A, lda, B, ldb, out, ldo, kchunk, ps, st); break;
+        case 3: zgemm_launch<32, 24, 2, 2>(grid, M, N, K, opA, A, lda, B, ldb, out, ldo, kchunk, ps, st); break;
+        case 4: zgemm_launch<24, 24, 2, 2>(grid, M, N, K, opA, A, lda, B, ldb, out, ldo, kchunk, ps, st); break;
+        case 5: zgemm_launch<32, 16, 2, 1>(grid, M, N, K, opA, A, lda, B, ldb, out, ldo, kchunk, ps, st); break;
+        default: zgemm_launch<24, 16, 2, 1>(grid, M, N, K, opA, A, lda, B, ldb, out, ldo, kchunk, ps, st); break;
+    }
+    NEP_CHECK_LAUNCH();
+    if (splits > 1) {
+        zgemm_reduce_kernel<<<ceil_div((int64_t)M * N, 256), 256, 0, st>>>(M, N, splits, part, C, ldc);
         NEP_CHECK_LAUNCH();
-        return NEP_OK;
     }
-    zgemm_kernel<<<grid, 256, 0, st>>>(M, N, K, opA, A, lda, B, ldb, part, M, kchunk, (int64_t)M * N);
-    NEP_CHECK_LAUNCH();
-    zgemm_reduce_kernel<<<ceil_div((int64_t)M * N, 256), 256, 0, st>>>(M, N, splits, part, C, ldc);
-    NEP_CHECK_LAUNCH();
     return NEP_OK;
 }
 

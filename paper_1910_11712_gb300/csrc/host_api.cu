@@ -791,12 +791,13 @@ static int run_extract(nep_plan* p, cudaStream_t st) {
         return NEP_OK;
     }
     NEP_TRY(zgemm(n, kb, m, 0, p->XH, n, p->Wg, m, p->Q, n, p->part, p->part_elems, st));
-    NEP_TRY(zgemm(kb, m, n, 1, p->Q, n, p->XH, n, p->Y0, kb, p->part, p->part_elems, st));
-    // projected split form B_i = Q^H A_i Q
+    // Newton's starting vectors Q^H X_H = Z^H X_H^H X_H = Z^H G (Q = X_H Z): an m-sized product
+    // in place of an n-sized one (they only seed the iteration)
+    NEP_TRY(zgemm(kb, m, m, 1, p->Wg, m, p->G, m, p->Y0, kb, p->part, p->part_elems, st));
+    // projected split form B_i = Q^H A_i Q, all terms in one product: the A_i Q blocks are
+    // adjacent (n x nterms*kb) and so are the B_i (kb x nterms*kb)
     NEP_TRY(launch_term_spmm(s, kb, p->Q, p->AQ, st));
-    for (int i = 0; i < nt; ++i)
-        NEP_TRY(zgemm(kb, kb, n, 1, p->Q, n, p->AQ + (size_t)i * n * kb, n, p->Bs + (size_t)i * kb * kb, kb, p->part,
-                      p->part_elems, st));
+    NEP_TRY(zgemm(kb, nt * kb, n, 1, p->Q, n, p->AQ, n, p->Bs, kb, p->part, p->part_elems, st));
     // Newton from every Hankel candidate
     const double rad = 4.0 * std::max(p->reg.a, p->reg.b);
     NEP_TRY(launch_newton(s, kb, m, p->Bs, p->bs32, p->cand, p->Y0, kb, mk(p->reg.center_re, p->reg.center_im), rad,

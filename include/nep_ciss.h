@@ -185,6 +185,32 @@ int nep_plan_destroy(nep_plan_t p);
  * for the narrow-band sweeps). */
 int nep_plan_buffer(nep_plan_t p, const char *name, void **dev_ptr, size_t *bytes);
 
+/* ------------------------------------------------------------------ residual inverse iteration */
+/* Polish of eigenpair estimates by residual inverse iteration (Sec. 4.1, Algorithm (rii),
+ * Neumaier's method), for P pairs at once. For pair p, sigma_p is its starting eigenvalue:
+ * T(sigma_p) is assembled and factored once by the band LU (complex64 factors for
+ * NEP_PREC_MIXED, complex128 for NEP_PREC_FP64). Each iteration solves T(sigma_p) with the FP64
+ * residual T(lambda_k) x and the A_i x as right-hand sides, takes lambda from Newton's method on
+ * x^* T(sigma_p)^{-1} T(z) x = 0 (written as x^* T(sigma_p)^{-1} (T(lambda_k) x + sum_i
+ * (f_i(z) - f_i(lambda_k)) A_i x); stopped at |mu| < sqrt(eps) |lambda|), computes the FP64 scaled
+ * residual eta (Sec. 2 Eq. (sressplit)) and stops the pair once eta < tol; otherwise
+ * x <- x - T(sigma_p)^{-1} T(lambda) x, normalised.
+ *   lam_dev: P complex128 (in: starting eigenvalues; out: results)
+ *   X_dev:   n x P complex128, column-major (in: starting vectors; out: unit 2-norm, first entry
+ *            of largest modulus real positive)
+ *   eta_dev: P doubles (out); its_dev: P int32 vector updates per pair (out), or NULL
+ * At most max_it + 1 iterations; *iterations (or NULL) receives the number run. All pointers are
+ * the caller's device memory; the call allocates its work arrays (among them the factors of P
+ * points) on the stream and returns when they are done.
+ * Errors: NEP_ERR_ARG (P < 0, max_it < 0, NULL arrays with P > 0, unknown precision), CUDA errors. */
+int nep_rii(nep_split_t h, int32_t precision, int32_t P, double *lam_dev, double *X_dev, double *eta_dev,
+            int32_t *its_dev, double tol, int32_t max_it, int32_t *iterations, void *stream);
+/* The same polish, in place, for the eigenpairs of the plan's last nep_plan_execute whose eta is
+ * not below tol: nep_plan_result then returns the polished values (same pairs, same order).
+ * *polished (or NULL) receives the number of pairs polished. Errors: NEP_ERR_ARG (NULL plan,
+ * max_it < 0), CUDA errors. */
+int nep_plan_polish(nep_plan_t p, double tol, int32_t max_it, int32_t *polished, int32_t *iterations, void *stream);
+
 /* ------------------------------------------------------------------ serving */
 /* Continuous-batching request server. Requests are admitted in arrival order as soon as a
  * worker is free and their device footprint (nep_plan_bytes) fits the remaining budget;

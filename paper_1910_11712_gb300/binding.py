@@ -100,6 +100,10 @@ SIGNATURES = {
     "nep_jacobi_svd": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "nep_jacobi_svd_noalloc": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "nep_small_eig": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "nep_rii": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_double, c_int32,
+                          ctypes.POINTER(c_int32), c_void_p]),
+    "nep_plan_polish": (c_int32, [c_void_p, ctypes.c_double, c_int32, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
+                                  c_void_p]),
 }
 
 _lib = None
@@ -312,6 +316,13 @@ class Plan:
         check(load().nep_plan_result(self.handle, ctypes.byref(res)))
         return _result_dict(res)
 
+    def polish(self, tol=1e-10, max_it=10, stream=0):
+        """nep_plan_polish: residual inverse iteration on the returned pairs with eta >= tol.
+        Returns (pairs polished, iterations run)."""
+        done, its = c_int32(), c_int32()
+        check(load().nep_plan_polish(self.handle, tol, max_it, ctypes.byref(done), ctypes.byref(its), stream))
+        return done.value, its.value
+
     def buffer(self, name: str):
         p, b = c_void_p(), c_size_t()
         check(load().nep_plan_buffer(self.handle, name.encode(), ctypes.byref(p), ctypes.byref(b)))
@@ -430,6 +441,15 @@ def jacobi_svd(rows, cols, A_dev, W_dev, sigma_dev, stream=0):
 def jacobi_svd_noalloc(rows, cols, A_dev, W_dev, sigma_dev, stream=0):
     """nep_jacobi_svd without device allocations (fixed scratch compiled into the library)."""
     check(load().nep_jacobi_svd_noalloc(rows, cols, ptr(A_dev), ptr(W_dev), ptr(sigma_dev), stream))
+
+
+def rii(split, precision, P, lam_dev, X_dev, eta_dev, its_dev=None, tol=1e-10, max_it=10, stream=0):
+    """nep_rii: residual inverse iteration from P (lambda, x) estimates on the device, in place.
+    Returns the number of iterations run."""
+    its = c_int32()
+    check(load().nep_rii(split.handle, precision, P, ptr(lam_dev), ptr(X_dev), ptr(eta_dev), ptr(its_dev), tol,
+                         max_it, ctypes.byref(its), stream))
+    return its.value
 
 
 def kernel_launches() -> int:

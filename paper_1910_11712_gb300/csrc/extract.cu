@@ -979,6 +979,43 @@ int small_eig(int m, const zd* A, zd* eval, zd* evec, int* status, void* gbuf, c
 template int small_eig<float>(int, const zd*, zd*, zd*, int*, void*, cudaStream_t);
 template int small_eig<double>(int, const zd*, zd*, zd*, int*, void*, cudaStream_t);
 
+// The rotation of givens() from one reciprocal square root: c and s do not change when x and y are
+// scaled by a common positive factor, so after scaling by 1 / max(|Re|, |Im|) (no overflow or
+// underflow in the squares), with n^2 = |x|^2 + |y|^2,
+//   c = |x| / n = |x|^2 r,   s = (x / |x|) conj(y) / n = x conj(y) r,   r = 1 / sqrt(|x|^2 n^2).
+template <typename T>
+__device__ __forceinline__ void givens_rsqrt(cx<T> x, cx<T> y, T* c, cx<T>* s) {
+    const T mx = fmax(abs1(x), abs1(y));
+    if (!(mx > T(0))) {
+        *c = T(1);
+        *s = mk<T>(0, 0);
+        return;
+    }
+    T k;
+    if constexpr (sizeof(T) == 4) k = __frcp_rn(mx);
+    else k = __drcp_rn(mx);
+    x = k * x;
+    y = k * y;
+    const T ax2 = norm2(x), ay2 = norm2(y);
+    auto rs = [](T v) -> T {
+        if constexpr (sizeof(T) == 4) return rsqrtf(v);
+        else return rsqrt(v);
+    };
+    if (ay2 == T(0)) {
+        *c = T(1);
+        *s = mk<T>(0, 0);
+        return;
+    }
+    if (ax2 == T(0)) {
+        *c = T(0);
+        *s = rs(ay2) * conj(y);
+        return;
+    }
+    const T r = rs(ax2 * (ax2 + ay2));
+    *c = ax2 * r;
+    *s = r * (x * conj(y));
+}
+
 // ------------------------------------------------------------------ eigenvalues, then inverse iteration
 // Faster variant for the reduced Hankel matrix: (1) one warp reduces to Hessenberg form and
 // runs the shifted QR iteration updating only the active block (eigenvalues only, no Schur
@@ -1034,11 +1071,20 @@ __global__ void hqr_eigvals_kernel(int m, const zd* __restrict__ Ain, zd* __rest
     const int maxit = 60 * m + 100;
     while (ihi > 0) {
         if (iter++ > maxit) { fail = 1; break; }
-        int l = ihi;
-        while (l > 0) {
-            const T ref = abs1(h(l, l)) + abs1(h(l - 1, l - 1));
-            if (abs1(h(l, l - 1)) <= eps * (ref > 0 ? ref : T(1))) break;
-            --l;
+        // the largest l <= ihi with a negligible h(l, l-1) (0 if none), 32 subdiagonals per ballot
+        int l = 0;
+        for (int base = ihi; base > 0; base -= 32) {
+            const int li = base - lane;
+            bool small = false;
+            if (li > 0) {
+                const T ref = abs1(h(li, li)) + abs1(h(li - 1, li - 1));
+                small = abs1(h(li, li - 1)) <= eps * (ref > 0 ? ref : T(1));
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, small);
+            if (bal) {
+                l = base - (__ffs(bal) - 1);
+                break;
+            }
         }
         __syncwarp();
         if (l > 0 && lane == 0) h(l, l - 1) = mk<T>(0, 0);
@@ -1059,7 +1105,7 @@ __global__ void hqr_eigvals_kernel(int m, const zd* __restrict__ Ain, zd* __rest
         for (int k = l; k < ihi; ++k) {
             T cs;
             cx<T> sn;
-            givens(x, y, &cs, &sn);
+            givens_rsqrt(x, y, &cs, &sn);
             // active block only: rows k, k+1 over columns max(l, k-1)..ihi; columns k, k+1 over rows l..min(k+2, ihi)
             for (int j = max(l, k - 1) + lane; j <= ihi; j += 32) {
                 const cx<T> p = h(k, j), q = h(k + 1, j);

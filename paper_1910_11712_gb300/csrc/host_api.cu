@@ -869,6 +869,73 @@ struct nep_result {
     nep_result_info_t info{};
 };
 
+// ------------------------------------------------------------------ residual inverse iteration
+extern "C" int nep_rii(nep_split_t h, int32_t precision, int32_t P, double* lam_dev, double* X_dev, double* eta_dev,
+                       int32_t* its_dev, double tol, int32_t max_it, int32_t* iterations, void* stream) {
+    if (!h || P < 0 || max_it < 0 || (P > 0 && (!lam_dev || !X_dev || !eta_dev))) {
+        set_error("nep_rii: bad arguments");
+        return NEP_ERR_ARG;
+    }
+    if (precision != NEP_PREC_MIXED && precision != NEP_PREC_FP64) { set_error("nep_rii: bad precision"); return NEP_ERR_ARG; }
+    if (iterations) *iterations = 0;
+    if (P == 0) return NEP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const SplitDev s = h->dev();
+    int* its = its_dev;
+    if (!its) NEP_CUDA(cudaMallocAsync((void**)&its, sizeof(int) * (size_t)P, st));
+    int k = 0;
+    int rc = precision == NEP_PREC_MIXED
+                 ? rii_polish<float>(s, P, (zd*)lam_dev, (zd*)X_dev, eta_dev, its, tol, max_it, &k, st)
+                 : rii_polish<double>(s, P, (zd*)lam_dev, (zd*)X_dev, eta_dev, its, tol, max_it, &k, st);
+    if (!its_dev) cudaFreeAsync(its, st);
+    if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = NEP_ERR_CUDA;
+    if (!rc && iterations) *iterations = k;
+    return rc;
+}
+
+extern "C" int nep_plan_polish(nep_plan_t p, double tol, int32_t max_it, int32_t* polished, int32_t* iterations,
+                               void* stream) {
+    if (!p || max_it < 0) { set_error("nep_plan_polish: bad arguments"); return NEP_ERR_ARG; }
+    if (polished) *polished = 0;
+    if (iterations) *iterations = 0;
+    if (p->m <= 0 || p->kb <= 0) return NEP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = p->h->n, m = p->m;
+    // the returned eigenpairs whose eta is not below tol
+    std::vector<int> order(m + 1, 0);
+    std::vector<double> eta(m);
+    NEP_CUDA(cudaMemcpyAsync(order.data(), p->order, sizeof(int) * (m + 1), cudaMemcpyDeviceToHost, st));
+    NEP_CUDA(cudaMemcpyAsync(eta.data(), p->eta, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+    NEP_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> idx;
+    for (int q = 0; q < order[0]; ++q)
+        if (!(eta[order[1 + q]] < tol)) idx.push_back(order[1 + q]);
+    const int P = (int)idx.size();
+    if (P == 0) return NEP_OK;
+    int* didx = nullptr;
+    zd *lam = nullptr, *X = nullptr;
+    double* e = nullptr;
+    int* its = nullptr;
+    NEP_CUDA(cudaMallocAsync((void**)&didx, sizeof(int) * P, st));
+    NEP_CUDA(cudaMallocAsync((void**)&lam, sizeof(zd) * P, st));
+    NEP_CUDA(cudaMallocAsync((void**)&X, sizeof(zd) * (size_t)n * P, st));
+    NEP_CUDA(cudaMallocAsync((void**)&e, sizeof(double) * P, st));
+    NEP_CUDA(cudaMallocAsync((void**)&its, sizeof(int) * P, st));
+    int rc = NEP_OK, k = 0;
+    if (cudaMemcpyAsync(didx, idx.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = NEP_ERR_CUDA;
+    if (!rc) rc = launch_rii_move(n, P, didx, p->lamn, p->Xc, p->eta, lam, X, e, 0, st);
+    if (!rc) rc = p->mixed ? rii_polish<float>(p->h->dev(), P, lam, X, e, its, tol, max_it, &k, st)
+                           : rii_polish<double>(p->h->dev(), P, lam, X, e, its, tol, max_it, &k, st);
+    if (!rc) rc = launch_rii_move(n, P, didx, p->lamn, p->Xc, p->eta, lam, X, e, 1, st);
+    for (void* b : {(void*)didx, (void*)lam, (void*)X, (void*)e, (void*)its}) cudaFreeAsync(b, st);
+    if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = NEP_ERR_CUDA;
+    if (!rc) {
+        if (polished) *polished = P;
+        if (iterations) *iterations = k;
+    }
+    return rc;
+}
+
 extern "C" int nep_plan_result(nep_plan_t p, nep_result_t* out) {
     if (!p || !out) { set_error("nep_plan_result: bad arguments"); return NEP_ERR_ARG; }
     const int n = p->h->n, N = p->Np, LM = p->LM;  // per-point arrays hold the solved points

@@ -99,14 +99,22 @@ __global__ void __launch_bounds__(512, 1)
     cx<T>* ab = ab_all + (int64_t)j * n * ldab;
     int* ipiv = ipiv_all + (int64_t)j * n;
 
-    // row c+kl at [c % RING]: columns c .. c+CS (zero beyond c+kv); RING = PF + 2 keeps row
-    // c-1+kl readable during step c
-    __shared__ cx<T> nrow[RING][CS + 1];
-    __shared__ cx<T> lvec[2][32 * RPL];  // multipliers of pivot step c by row slot, at [c & 1]
+    // Row c+kl enters at step c from ring entry c % RING (RING = PF + 2 keeps row c-1+kl readable
+    // during step c): its value in column c in n0, and columns c+1 .. c+CS (zero beyond c+kv) in
+    // column-slot order, so that a warp's part is where its registers want it: per warp and
+    // register pair (re 2h, re 2h+1, im 2h, im 2h+1) when PAIRED, per warp and register otherwise.
+    __shared__ ulonglong2 nsp[PAIRED ? RING : 1][PAIRED ? NW : 1][CPH];
+    __shared__ cx<T> nsg[PAIRED ? 1 : RING][PAIRED ? 1 : NW][CPW];
+    __shared__ cx<T> n0[RING];
+    // multipliers of pivot step c by row slot at [c % 3] (three buffers: the warp that runs step c
+    // late reads them during step c+1, while pivot c+2 is written); when PAIRED also as the packed
+    // operands (-l.re, -l.re), (l.im, l.im), (-l.im, -l.im)
+    __shared__ cx<T> lvec[3][32 * RPL];
+    __shared__ unsigned long long lvp[PAIRED ? 3 : 1][3][32 * RPL];
     // per warp: the pivot row on its columns; when PAIRED, (re 2h, re 2h+1, im 2h, im 2h+1)
     __shared__ ulonglong2 xrow2[PAIRED ? NW : 1][CPH];
     __shared__ cx<T> xrow[PAIRED ? 1 : NW][PAIRED ? 1 : CPW];
-    __shared__ int piv_s[2], info_s;
+    __shared__ int piv_s[3], info_s;
     if (threadIdx.x == 0) info_s = 0;
 
     cx<T> a[PAIRED ? 1 : RPL][CPW] = {};
@@ -170,25 +178,43 @@ __global__ void __launch_bounds__(512, 1)
             set(q, p, v);
         }
     }
-    if (CS > kv)
-        for (int e = threadIdx.x; e < RING * (CS - kv); e += blockDim.x)
-            nrow[e / (CS - kv)][kv + 1 + e % (CS - kv)] = mk<T>(0, 0);
+    // element t (0 .. CS) of row r = c0 + kl, the row entering at step c0, into ring entry e
+    auto fetch = [&](int e, int c0, int t) __attribute__((always_inline)) {
+        const int r = c0 + kl, k = c0 + t;
+        const bool in = r < n && k < n && t <= kv;
+        const cx<T>* src = ab + (int64_t)r * ldab + t;
+        if (t == 0) {
+            if (in) cp_async_cx(&n0[e], src);
+            else n0[e] = mk<T>(0, 0);
+            return;
+        }
+        const int sl = k & (CS - 1), w = sl & (NW - 1), p = sl / NW;
+        if constexpr (PAIRED) {
+            float* f = reinterpret_cast<float*>(&nsp[e][w][p >> 1]);
+            if (in) {
+                cp_async_f32(f + (p & 1), reinterpret_cast<const float*>(src));
+                cp_async_f32(f + 2 + (p & 1), reinterpret_cast<const float*>(src) + 1);
+            } else {
+                f[p & 1] = 0.f;
+                f[2 + (p & 1)] = 0.f;
+            }
+        } else {
+            if (in) cp_async_cx(&nsg[e][w][p], src);
+            else nsg[e][w][p] = mk<T>(0, 0);
+        }
+    };
     // rows kl .. kl+PF-1 (steps 0 .. PF-1): one commit group per row
     for (int d = 0; d < PF; ++d) {
-        const int r = kl + d;
-        for (int t = threadIdx.x; t <= kv; t += blockDim.x) {
-            if (r < n && d + t < n) cp_async_cx(&nrow[d][t], ab + (int64_t)r * ldab + t);
-            else nrow[d][t] = mk<T>(0, 0);
-        }
+        for (int t = threadIdx.x; t <= CS; t += blockDim.x) fetch(d, d, t);
         cp_async_commit();
     }
 
     // Pivot of column c1 by the warp holding it: col[q] is the column's value in row slot q
-    // (row lab[q], in c1 .. c1+kl-1); row c1+kl enters from nrow. Writes the multipliers by row
+    // (row lab[q], in c1 .. c1+kl-1); row c1+kl enters from the ring. Writes the multipliers by row
     // slot as they stand after the interchange (and to L), U(c1,c1), ipiv and the pivot row.
     auto pivot = [&](int c1, const cx<T>(&col)[RPL]) __attribute__((always_inline)) {
-        const int nb = c1 & 1, re = c1 + kl;
-        const cx<T> ve = nrow[c1 % RING][0];
+        const int nb = c1 % 3, re = c1 + kl;
+        const cx<T> ve = n0[c1 % RING];
         T best = T(-1);
         int bi = 0x7fffffff;
 #pragma unroll
@@ -239,6 +265,11 @@ __global__ void __launch_bounds__(512, 1)
             }
             const cx<T> l = (!zero && nl < n) ? val * rpv : mk<T>(0, 0);
             lvec[nb][lane + 32 * q] = l;
+            if constexpr (PAIRED) {
+                lvp[nb][0][lane + 32 * q] = pack2(-l.re, -l.re);
+                lvp[nb][1][lane + 32 * q] = pack2(l.im, l.im);
+                lvp[nb][2][lane + 32 * q] = pack2(-l.im, -l.im);
+            }
             out[kv + nl - c1] = l;  // L(nl, c1) at kv + 1 + (nl - c1 - 1)
         }
         if (lane == 0) {
@@ -252,8 +283,8 @@ __global__ void __launch_bounds__(512, 1)
     // Step cc on this warp's columns: publish the pivot row (row Pc; the entering row when
     // Pc = cc+kl), the pivot's slot takes the entering row, a(r, k) -= l(r) u(k), U(cc, k) to
     // the band, and the slot of column cc+1 (if this warp holds it) empties for column cc+1+CS.
-    auto run_step = [&](int cc, int Pc, const bool(&ispc)[RPL], const cx<T>(&lqc)[RPL]) __attribute__((always_inline)) {
-        const cx<T>* nrc = nrow[cc % RING];
+    auto run_step = [&](int cc, int Pc, const bool(&ispc)[RPL]) __attribute__((always_inline)) {
+        const int e = cc % RING, lb = cc % 3;
         // the pivot row's lane publishes its registers, then takes the entering row into them
 #pragma unroll
         for (int q = 0; q < RPL; ++q)
@@ -262,28 +293,25 @@ __global__ void __launch_bounds__(512, 1)
 #pragma unroll
                     for (int h = 0; h < CPH; ++h) {
                         xrow2[warp][h] = make_ulonglong2(are[q][h], aim[q][h]);
-                        const cx<T> v0 = nrc[toff(2 * h, cc)], v1 = nrc[toff(2 * h + 1, cc)];
-                        are[q][h] = pack2(v0.re, v1.re);
-                        aim[q][h] = pack2(v0.im, v1.im);
+                        const ulonglong2 v = nsp[e][warp][h];
+                        are[q][h] = v.x;
+                        aim[q][h] = v.y;
                     }
                 } else {
 #pragma unroll
                     for (int p = 0; p < CPW; ++p) {
                         xrow[warp][p] = a[q][p];
-                        a[q][p] = nrc[toff(p, cc)];
+                        a[q][p] = nsg[e][warp][p];
                     }
                 }
             }
         if (Pc == cc + kl && lane == 0) {  // the pivot is the entering row itself
             if constexpr (PAIRED) {
 #pragma unroll
-                for (int h = 0; h < CPH; ++h) {
-                    const cx<T> v0 = nrc[toff(2 * h, cc)], v1 = nrc[toff(2 * h + 1, cc)];
-                    xrow2[warp][h] = make_ulonglong2(pack2(v0.re, v1.re), pack2(v0.im, v1.im));
-                }
+                for (int h = 0; h < CPH; ++h) xrow2[warp][h] = nsp[e][warp][h];
             } else {
 #pragma unroll
-                for (int p = 0; p < CPW; ++p) xrow[warp][p] = nrc[toff(p, cc)];
+                for (int p = 0; p < CPW; ++p) xrow[warp][p] = nsg[e][warp][p];
             }
         }
         __syncwarp();
@@ -291,9 +319,9 @@ __global__ void __launch_bounds__(512, 1)
             unsigned long long nlre[RPL], lim[RPL], nlim[RPL];
 #pragma unroll
             for (int q = 0; q < RPL; ++q) {
-                nlre[q] = pack2(-lqc[q].re, -lqc[q].re);
-                lim[q] = pack2(lqc[q].im, lqc[q].im);
-                nlim[q] = pack2(-lqc[q].im, -lqc[q].im);
+                nlre[q] = vr[q] ? lvp[lb][0][lane + 32 * q] : 0ull;
+                lim[q] = vr[q] ? lvp[lb][1][lane + 32 * q] : 0ull;
+                nlim[q] = vr[q] ? lvp[lb][2][lane + 32 * q] : 0ull;
             }
 #pragma unroll
             for (int h = 0; h < CPH; ++h) {
@@ -307,6 +335,9 @@ __global__ void __launch_bounds__(512, 1)
                 }
             }
         } else {
+            cx<T> lqc[RPL];
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) lqc[q] = vr[q] ? lvec[lb][lane + 32 * q] : mk<T>(0, 0);
 #pragma unroll
             for (int p = 0; p < CPW; ++p) {
                 const cx<T> u = xrow[warp][p];
@@ -363,33 +394,28 @@ __global__ void __launch_bounds__(512, 1)
     bool deferred = false;
     int Pd = 0;
     bool ispd[RPL];
-    cx<T> lqd[RPL];
 #pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-        ispd[q] = false;
-        lqd[q] = mk<T>(0, 0);
-    }
+    for (int q = 0; q < RPL; ++q) ispd[q] = false;
     for (int c = 0; c < n; ++c) {
         if (deferred) {
-            run_step(c - 1, Pd, ispd, lqd);
+            run_step(c - 1, Pd, ispd);
             deferred = false;
         }
-        const int cb = c & 1, re = c + kl;
+        const int cb = c % 3, re = c + kl;
         const int P = piv_s[cb];
         bool isp[RPL];
-        cx<T> lq[RPL];
 #pragma unroll
         for (int q = 0; q < RPL; ++q) {
             isp[q] = P != re && lab[q] == P;
             lab[q] = isp[q] ? re : (lab[q] == c ? P : lab[q]);  // labels after the interchange
-            lq[q] = vr[q] ? lvec[cb][lane + 32 * q] : mk<T>(0, 0);
         }
         const int s1 = (c + 1) & (CS - 1), w1 = s1 & (NW - 1), p1 = s1 / NW;
         if (warp == w1 && c + 1 < n) {
             // column c+1 after step c, for the pivot of step c+1 (look-ahead); the rest of step
             // c on this warp's columns waits for the next step
-            const cx<T>* nr = nrow[c % RING];
-            cx<T> mine[RPL];
+            cx<T> lq[RPL], mine[RPL];
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) lq[q] = vr[q] ? lvec[cb][lane + 32 * q] : mk<T>(0, 0);
 #pragma unroll
             for (int q = 0; q < RPL; ++q) mine[q] = mk<T>(0, 0);
 #pragma unroll
@@ -406,7 +432,13 @@ __global__ void __launch_bounds__(512, 1)
                     has = true;
                 }
             const int lp = __ffs(__ballot_sync(0xffffffffu, has)) - 1;
-            const cx<T> vn1 = nr[1];
+            cx<T> vn1;  // the entering row in column c+1
+            if constexpr (PAIRED) {
+                const float* f = reinterpret_cast<const float*>(&nsp[c % RING][warp][p1 >> 1]);
+                vn1 = mk<T>(f[p1 & 1], f[2 + (p1 & 1)]);
+            } else {
+                vn1 = nsg[c % RING][warp][p1];
+            }
             const cx<T> u1 = P == re ? vn1 : shfl_cx(up, lp < 0 ? 0 : lp);
             cx<T> col[RPL];
 #pragma unroll
@@ -415,23 +447,15 @@ __global__ void __launch_bounds__(512, 1)
             deferred = true;
             Pd = P;
 #pragma unroll
-            for (int q = 0; q < RPL; ++q) {
-                ispd[q] = isp[q];
-                lqd[q] = lq[q];
-            }
+            for (int q = 0; q < RPL; ++q) ispd[q] = isp[q];
         } else {
-            run_step(c, P, isp, lq);
+            run_step(c, P, isp);
         }
-        // row c+kl+PF (columns c+PF .. c+PF+kv) into ring slot (c+PF) % RING, by the warps after
-        // the look-ahead warp (the one behind it runs two steps' updates in this step)
+        // row c+kl+PF into ring entry (c+PF) % RING, by the warps after the look-ahead warp (the
+        // one behind it runs two steps' updates in this step)
         {
             const int idx = ((warp - w1 - 1) & (NW - 1)) * 32 + lane;
-            const int r = c + kl + PF;
-            cx<T>* dst = nrow[(c + PF) % RING];
-            if (idx < (NW - 2) * 32 && idx <= kv) {
-                if (r < n && c + PF + idx < n) cp_async_cx(&dst[idx], ab + (int64_t)r * ldab + idx);
-                else dst[idx] = mk<T>(0, 0);
-            }
+            if (idx < (NW - 2) * 32 && idx <= CS) fetch((c + PF) % RING, c + PF, idx);
             cp_async_commit();
         }
         cp_async_wait_group<PF - 2>();  // row c+2+kl, for the look-ahead of step c+1

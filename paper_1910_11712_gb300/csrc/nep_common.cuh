@@ -277,5 +277,14 @@ int launch_term_spmm(const SplitDev& s, int k, const zd* Q, zd* out, cudaStream_
 int launch_eta(const SplitDev& s, int ncand, const zd* lam, const zd* X, double* eta, cudaStream_t st);
 int launch_select(int ncand, const zd* lam, const double* eta, const int* ok, const zd* G, zd c, double ea, double eb,
                   double eig_tol, int* order, cudaStream_t st);
+// polish.cu: residual inverse iteration from P (lambda, x) estimates (x: n x P), T(sigma_p) factored at
+// the starting eigenvalues in the precision T of the band LU; eta (P) and its (P) written;
+// *max_its_host = outer iterations run.
+template <typename T>
+int rii_polish(const SplitDev& s, int P, zd* lam, zd* X, double* eta, int* its, double tol, int max_it,
+               int* max_its_host, cudaStream_t st);
+// dir 0: lam[q], X(:, q), eta[q] <- lam_c[idx[q]], X_c(:, idx[q]), eta_c[idx[q]]; dir 1: the reverse
+int launch_rii_move(int n, int P, const int* idx, zd* lam_c, zd* X_c, double* eta_c, zd* lam, zd* X, double* eta,
+                    int dir, cudaStream_t st);
 
 }  // namespace nep

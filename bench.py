@@ -144,9 +144,18 @@ def cpu_baseline(p, steps_budget_s=20.0):
         if time.perf_counter() > t_end or len(times) >= 3:
             break
     cores = max(1, min(32, os.cpu_count() or 1))
-    return {"value": p.N * len(times) / sum(times), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{len(times)} full CPU passes of {p.name} (N={p.N} quadrature solves each), "
-                      f"threads over quadrature points, {sum(times):.1f} s total"}
+    out = {"value": p.N * len(times) / sum(times), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{len(times)} full CPU passes of {p.name} (N={p.N} quadrature solves each), "
+                     f"threads over quadrature points, {sum(times):.1f} s total"}
+    # the oracle's residual inverse iteration on the same operator: one pair from a seeded start at
+    # the region's centre, three iterations without a stopping tolerance (one band LU at sigma, then
+    # per iteration the inner Newton loop's solves and the update's)
+    from oracle import rii
+    x0 = synth.random_probe_block(p.n, 1, 1)[:, 0]
+    t0 = time.perf_counter()
+    rii.rii(p, complex(p.region["center"]), x0, tol=0.0, max_it=2)
+    out["rii_s_per_pair_3_iterations"] = time.perf_counter() - t0
+    return out
 
 
 def serving_bench(binding, prec, count, seed, workers, s_max, loads=(0.5, 0.8, 1.2)):
@@ -246,6 +255,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-symmetric", action="store_true")
+    ap.add_argument("--no-polish", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=40)
     ap.add_argument("--serving-smax", type=int, default=128)
     args = ap.parse_args()
@@ -374,6 +384,28 @@ def main():
         except binding.NepError as e:
             symmetric = {"unavailable": str(e)}
 
+    # residual inverse iteration (Sec. 4.1, Algorithm rii) on the pairs just returned, to a tighter
+    # eta than the contour method's: one assembly + band LU at the P starting eigenvalues, then
+    # per iteration one band solve with nterms+1 right-hand sides per pair
+    polish = None
+    if not args.no_polish:
+        try:
+            plan.execute(Vd, stream)
+            torch.cuda.synchronize()
+            before = plan.result()
+            tol = 1e-13
+            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            q0.record()
+            npol, its = plan.polish(tol=tol, max_it=10, stream=stream)
+            q1.record()
+            torch.cuda.synchronize()
+            after = plan.result()
+            polish = {"tol": tol, "pairs": int(npol), "iterations": int(its), "ms": q0.elapsed_time(q1),
+                      "max_eta_before": float(before["eta"].max()) if len(before["eta"]) else None,
+                      "max_eta_after": float(after["eta"].max()) if len(after["eta"]) else None}
+        except binding.NepError as e:
+            polish = {"unavailable": str(e)}
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -427,7 +459,7 @@ def main():
                          "algorithmic": {"flops": s_flops, "bytes": s_bytes,
                                          "hbm_gbs": s_bytes / (solve_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm,
                                          "hbm_frac": s_bytes / (solve_ms * 1e-3) / 1e9 / hbm}},
-            "factor": {"kernel": "lu_regt_kernel" if split.kl <= 64 and split.kl + split.ku <= 128 else "lu_wide_kernel",
+            "factor": {"kernel": "lu_col_kernel" if split.kl <= 64 and split.kl + split.ku <= 128 else "lu_wide_kernel",
                        "ms": lu, "achieved_tflops": lu_flops(p.n, split.kl, split.ku, p.N) / (lu * 1e-3) / 1e12,
                        "peak_tflops": alu_peak,
                        "frac": lu_flops(p.n, split.kl, split.ku, p.N) / (lu * 1e-3) / 1e12 / alu_peak},
@@ -441,6 +473,8 @@ def main():
             line["e2e"] = e2e
         if symmetric:
             line["symmetric"] = symmetric
+        if polish:
+            line["polish"] = polish
         if not args.no_serving:
             line["serving"] = serving_bench(binding, prec, args.serving_requests, 0, 4, args.serving_smax)
         if not args.no_cpu:

@@ -29,8 +29,12 @@ namespace nep {
 // value after the interchange with row ipiv[c] (forward) or the row's value times 1/U(c,c)
 // (backward). Interchanges are rare in practice, so a chunk without any runs a loop without
 // the interchange test. Steps are RSP = RS + 1 elements apart in shared memory.
+// The second half of the CTA's warps are producers: they stage chunk c+1 into the other buffer
+// while the compute warps (one or more right-hand sides each) run chunk c, so the staging's index
+// work and copy issue stay off the compute warps' dependency chains. One CTA barrier per chunk:
+// each producer arrives once its copies have landed, the compute warps once the chunk is done.
 template <typename T, int RPL, bool BWD, int RH>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
     band_sweep_kernel(int n, int kl, int ku, int ldab, const cx<T>* __restrict__ ab_all,
                       const cx<T>* __restrict__ ut_all, const int* __restrict__ ipiv_all, int L,
                       cx<T>* __restrict__ B_all, const int* __restrict__ active, int CH) {
@@ -40,7 +44,9 @@ __global__ void __launch_bounds__(128)
     const int kv = kl + ku;
     const int W = BWD ? kv : kl;  // window width: rows updated per step
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nwarps = blockDim.x >> 5;
+    const int nwarps = (blockDim.x >> 5) / 2;  // compute warps; warps nwarps .. 2 nwarps-1 produce
+    const bool producer = warp >= nwarps;
+    const int pw = warp - nwarps;  // producer index
     const int col0 = (blockIdx.y * nwarps + warp) * RH;
     const int64_t cstride = BWD ? kv + 1 : ldab;
     const cx<T>* colbase = BWD ? ut_all + (int64_t)j * n * (kv + 1) : ab_all + (int64_t)j * n * ldab + kv;
@@ -49,7 +55,7 @@ __global__ void __launch_bounds__(128)
     cx<T>* bh[RH];
 #pragma unroll
     for (int h = 0; h < RH; ++h) {
-        has[h] = col0 + h < L;
+        has[h] = !producer && col0 + h < L;
         bh[h] = B_all + ((int64_t)j * L + (has[h] ? col0 + h : 0)) * n;
     }
     const bool any = has[0];
@@ -64,12 +70,13 @@ __global__ void __launch_bounds__(128)
     cx<T>* ob = ob0 + (int64_t)warp * RH * CH;
     int* piv0 = reinterpret_cast<int*>(ob0 + (int64_t)nwarps * RH * CH);
 
+    // run by the producer warps, which split the steps and the entering rows
     auto issue = [&](int k0, int bsel) {
         const int cn = min(CH, n - k0);
         cx<T>* cf = coef0 + (int64_t)bsel * CH * RSP;
         // every slot of every step has exactly one writer: the window rows d in [1, W] copy their
         // coefficient (zero past the matrix), the other RS - W slots (d = 0 and d > W) zero
-        for (int cc = warp; cc < cn; cc += nwarps) {
+        for (int cc = pw; cc < cn; cc += nwarps) {
             const int k = k0 + cc, km = k % RS;
             cx<T>* dst = cf + cc * RSP;
             const cx<T>* src = colbase + (BWD ? n - 1 - k : k) * cstride;
@@ -80,19 +87,25 @@ __global__ void __launch_bounds__(128)
                 else dst[sl] = mk<T>(0, 0);
             }
         }
-        if (threadIdx.x < cn) {
-            const int k = k0 + threadIdx.x;
-            if (!BWD) cp_async_i32(&piv0[bsel * CH + threadIdx.x], ipiv + k);
-            else cp_async_cx(&dg0[bsel * CH + threadIdx.x], colbase + (n - 1 - k) * cstride);
+        if (pw == 0 && lane < cn) {
+            const int k = k0 + lane;
+            if (!BWD) cp_async_i32(&piv0[bsel * CH + lane], ipiv + k);
+            else cp_async_cx(&dg0[bsel * CH + lane], colbase + (n - 1 - k) * cstride);
         }
-        cx<T>* nb = nb0 + ((int64_t)bsel * nwarps + warp) * RH * CH;
+        // the rows entering the window of compute warp pw during the chunk
+        for (int w = pw; w < nwarps; w += nwarps) {
+            cx<T>* nb = nb0 + ((int64_t)bsel * nwarps + w) * RH * CH;
 #pragma unroll
-        for (int h = 0; h < RH; ++h)
-            for (int cc = lane; cc < cn; cc += 32) {
-                const int k = k0 + cc + RS;
-                if (has[h] && k < n) cp_async_cx(&nb[h * CH + cc], bh[h] + row_of(k));
-                else nb[h * CH + cc] = mk<T>(0, 0);
+            for (int h = 0; h < RH; ++h) {
+                const int col = (blockIdx.y * nwarps + w) * RH + h;
+                const cx<T>* bw = B_all + ((int64_t)j * L + (col < L ? col : 0)) * n;
+                for (int cc = lane; cc < cn; cc += 32) {
+                    const int k = k0 + cc + RS;
+                    if (col < L && k < n) cp_async_cx(&nb[h * CH + cc], bw + row_of(k));
+                    else nb[h * CH + cc] = mk<T>(0, 0);
+                }
             }
+        }
         cp_async_commit();
     };
 
@@ -159,13 +172,16 @@ __global__ void __launch_bounds__(128)
         }
     };
 
-    issue(0, 0);
+    if (producer) issue(0, 0);
     for (int k0 = 0, chunk = 0; k0 < n; k0 += CH, ++chunk) {
         const int cn = min(CH, n - k0);
         const int bsel = chunk & 1;
-        cp_async_wait_group<0>();
-        __syncthreads();
-        if (k0 + CH < n) issue(k0 + CH, bsel ^ 1);
+        cp_async_wait_group<0>();  // the producer's copies of this chunk (a no-op elsewhere)
+        __syncthreads();           // chunk staged; the other buffer's chunk finished
+        if (producer) {
+            if (k0 + CH < n) issue(k0 + CH, bsel ^ 1);
+            continue;
+        }
         if (any) {
             const cx<T>* cf = coef0 + (int64_t)bsel * CH * RSP + lane * RPL;
             const int* pv = piv0 + bsel * CH;
@@ -211,7 +227,7 @@ static int run_sweep(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* 
                      cx<T>* B, const int* active, cudaStream_t st) {
     constexpr int RSP = 32 * RPL + 1;
     const int warps = (L + RH - 1) / RH;
-    const int wpb = warps < 4 ? warps : 4;
+    const int wpb = warps < 4 ? warps : 4;  // compute warps per CTA, and as many producer warps
     const int gy = (warps + wpb - 1) / wpb;
     auto bytes = [&](int ch) {
         return sizeof(cx<T>) * (2 * (size_t)ch * RSP + 2 * (size_t)ch + 3 * (size_t)wpb * RH * ch) +
@@ -223,7 +239,7 @@ static int run_sweep(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* 
     if (smem > 227 * 1024) return NEP_ERR_UNSUPPORTED;
     NEP_CUDA(cudaFuncSetAttribute(band_sweep_kernel<T, RPL, BWD, RH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
-    band_sweep_kernel<T, RPL, BWD, RH><<<dim3(npts, gy), wpb * 32, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ut,
+    band_sweep_kernel<T, RPL, BWD, RH><<<dim3(npts, gy), 2 * wpb * 32, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ut,
                                                                              ipiv, L, B, active, CH);
     NEP_CHECK_LAUNCH();
     return NEP_OK;

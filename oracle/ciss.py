@@ -40,6 +40,8 @@ REFINE_STEP_TOL = 1e-14   # relative correction at which the solve is converged 
 REFINE_MAX = 10
 NEWTON_MAX = 30
 NEWTON_TOL = 1e-14
+NEWTON_EARLY = 8          # after this many steps an unconverged iterate still outside Gamma ...
+NEWTON_EARLY_Q = 1.21     # ... by 10% (((Re(l-c))/a)^2 + ((Im(l-c))/b)^2 > 1.1^2) is abandoned
 EIG_TOL = 1e-8            # eta acceptance of a returned eigenpair
 DEDUP_LAMBDA = 1e-10
 DEDUP_VECTOR = 1e-8
@@ -191,13 +193,15 @@ def newton_projected(Bs, fns, lam0: complex, y0: np.ndarray, region: dict):
         [ B(lam)  B'(lam) y ] [dy  ]     [ B(lam) y ]
         [ u^H     0         ] [dlam] = - [    0     ]
     Stops when |dlam| <= NEWTON_TOL * max(1, |lam|) or after NEWTON_MAX steps; a
-    step leaving the disc |lam - c| <= 4 max(a, b) marks the candidate invalid.
+    step leaving the disc |lam - c| <= 4 max(a, b) marks the candidate invalid, and so does
+    an iterate still unconverged and outside Gamma by 10% after NEWTON_EARLY steps.
     """
     k = Bs[0].shape[0]
     y = y0 / np.linalg.norm(y0)
     lam = complex(lam0)
     c = complex(region["center"])
     rad = 4.0 * max(region["a"], region["b"])
+    ea, eb = float(region["a"]), float(region["b"])
     ok = True
     it = 0
     for it in range(1, NEWTON_MAX + 1):
@@ -221,6 +225,9 @@ def newton_projected(Bs, fns, lam0: complex, y0: np.ndarray, region: dict):
             ok = False
             break
         if abs(d[k]) <= NEWTON_TOL * max(1.0, abs(lam)):
+            break
+        if it >= NEWTON_EARLY and ((lam - c).real / ea) ** 2 + ((lam - c).imag / eb) ** 2 > NEWTON_EARLY_Q:
+            ok = False
             break
     return lam, y, ok, it
 

@@ -1356,7 +1356,8 @@ __global__ void convert_c64_kernel(int64_t count, const zd* __restrict__ in, zf*
 template <int MB>  // rows per lane in the elimination: K1 <= 32 MB
 __global__ void __launch_bounds__(256, 1) newton_kernel(SplitDev s, int k, const zd* __restrict__ Bs,
                                                      const zf* __restrict__ Bs32, const zd* __restrict__ lam0,
-                                                     const zd* __restrict__ Y0, int ldy0, zd c, double rad, int maxit,
+                                                     const zd* __restrict__ Y0, int ldy0, zd c, double rad, double ea,
+                                                     double eb, int maxit,
                                                      double tol, zd* __restrict__ lam_out, zd* __restrict__ Yout,
                                                      int* __restrict__ ok_out, int* __restrict__ its_out,
                                                      unsigned char* __restrict__ gscratch, int use_smem) {
@@ -1611,6 +1612,12 @@ __global__ void __launch_bounds__(256, 1) newton_kernel(SplitDev s, int k, const
             int st = 0;
             if (!isfinite(nl.re) || !isfinite(nl.im) || hypot(nl.re - c.re, nl.im - c.im) > rad || !(t > 0)) st = 2;
             else if (fp64 && ad <= tol * fmax(1.0, al)) st = 1;
+            // unconverged after 8 steps and still outside Gamma by 10%: abandoned (these
+            // candidates only end outside, and they are the ones that take the most steps)
+            if (st == 0 && it >= 8) {
+                const double qx = (nl.re - c.re) / ea, qy = (nl.im - c.im) / eb;
+                if (qx * qx + qy * qy > 1.21) st = 2;
+            }
             if (!fp64 && (ad <= 1e-5 * fmax(1.0, al) || (it > 2 && ad > 0.5 * dprev_s && ad <= 1e-3 * fmax(1.0, al))))
                 fp64_s = 1;
             dprev_s = ad;
@@ -1635,8 +1642,8 @@ __global__ void __launch_bounds__(256, 1) newton_kernel(SplitDev s, int k, const
 }
 
 int launch_newton(const SplitDev& s, int k, int ncand, const zd* Bs, zf* Bs32, const zd* lam0, const zd* Y0, int ldy0,
-                  zd c, double rad, int maxit, double tol, zd* lam_out, zd* Yout, int* ok, int* its,
-                  unsigned char* gscratch, cudaStream_t st) {
+                  zd c, double rad, double ea, double eb, int maxit, double tol, zd* lam_out, zd* Yout, int* ok,
+                  int* its, unsigned char* gscratch, cudaStream_t st) {
     if (ncand <= 0) return NEP_OK;
     const int64_t nb = (int64_t)s.nterms * k * k;
     convert_c64_kernel<<<(int)((nb + 255) / 256), 256, 0, st>>>(nb, Bs, Bs32);
@@ -1646,8 +1653,8 @@ int launch_newton(const SplitDev& s, int k, int ncand, const zd* Bs, zf* Bs32, c
     if (!use_smem && !gscratch) return NEP_ERR_INTERNAL;
     auto run = [&](auto kern) -> int {
         if (use_smem) NEP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-        kern<<<ncand, 256, use_smem ? bytes : 0, st>>>(s, k, Bs, Bs32, lam0, Y0, ldy0, c, rad, maxit, tol, lam_out, Yout,
-                                                       ok, its, gscratch, use_smem);
+        kern<<<ncand, 256, use_smem ? bytes : 0, st>>>(s, k, Bs, Bs32, lam0, Y0, ldy0, c, rad, ea, eb, maxit, tol,
+                                                       lam_out, Yout, ok, its, gscratch, use_smem);
         NEP_CHECK_LAUNCH();
         return NEP_OK;
     };

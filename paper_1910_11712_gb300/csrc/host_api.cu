@@ -801,7 +801,8 @@ static int run_extract(nep_plan* p, cudaStream_t st) {
     // Newton from every Hankel candidate
     const double rad = 4.0 * std::max(p->reg.a, p->reg.b);
     NEP_TRY(launch_newton(s, kb, m, p->Bs, p->bs32, p->cand, p->Y0, kb, mk(p->reg.center_re, p->reg.center_im), rad,
-                          p->o.newton_max, p->o.newton_tol, p->lamn, p->Yn, p->ok, p->its, p->newton_scratch, st));
+                          p->reg.a, p->reg.b, p->o.newton_max, p->o.newton_tol, p->lamn, p->Yn, p->ok, p->its,
+                          p->newton_scratch, st));
     // eigenvectors, residuals, selection
     NEP_TRY(zgemm(n, m, kb, 0, p->Q, n, p->Yn, kb, p->Xc, n, p->part, p->part_elems, st));
     NEP_TRY(launch_normalize_columns(n, m, p->Xc, 1, nullptr, st));

@@ -265,8 +265,8 @@ int small_eig_fast(int m, const zd* A, zd* eval, zd* evec, int* status, void* gb
 size_t newton_scratch_bytes(int k, int nterms);
 int launch_pchol(int m, const zd* G, double tol2, int* rank_out, zd* Z, zd* gwork, cudaStream_t st);
 int launch_newton(const SplitDev& s, int k, int ncand, const zd* Bs, zf* Bs32, const zd* lam0, const zd* Y0, int ldy0,
-                  zd c, double rad, int maxit, double tol, zd* lam_out, zd* Yout, int* ok, int* its,
-                  unsigned char* gscratch, cudaStream_t st);
+                  zd c, double rad, double ea, double eb, int maxit, double tol, zd* lam_out, zd* Yout, int* ok,
+                  int* its, unsigned char* gscratch, cudaStream_t st);
 int launch_scale_cols(int rows, int cols, zd* X, int ld, const double* s, int mode, cudaStream_t st);
 int launch_scale_rows(int rows, int cols, zd* X, int ld, const double* s, cudaStream_t st);
 int launch_candidates(int m, const zd* theta, zd c, double a, zd* lam, cudaStream_t st);

@@ -211,6 +211,46 @@ int nep_rii(nep_split_t h, int32_t precision, int32_t P, double *lam_dev, double
  * max_it < 0), CUDA errors. */
 int nep_plan_polish(nep_plan_t p, double tol, int32_t max_it, int32_t *polished, int32_t *iterations, void *stream);
 
+/* ------------------------------------------------------------------ left eigenvectors, resolvent */
+/* Left eigenvectors y^* T(lambda) = 0 (Sec. 2 Eq. (nep-left): right eigenvectors of T(lambda)^*)
+ * of P eigenpairs (lambda_p, x_p), requested through Sec. 3.2.5's interface. T(lambda_p) is
+ * assembled and factored once by the band LU (complex64 factors for NEP_PREC_MIXED, complex128
+ * for NEP_PREC_FP64); from y = x_p the first step is inverse iteration y <- T(lambda_p)^{-*} y,
+ * later steps y <- y - T(lambda_p)^{-*} (T(lambda_p)^* y) with the residual in FP64, each
+ * normalised to unit 2-norm. A pair stops when its left scaled residual
+ *   eta_L = ||T(lambda)^* y||_2 / (sum_i |f_i(lambda)| ||A_i||_1 ||y||_2)
+ * falls below tol, when a step gains less than a factor 2 (the floor set by the eigenvalue's own
+ * error), or after max_it steps. Finally y is scaled to y^* T'(lambda) x = 1 (the normalisation of
+ * Sec. 2 Eq. (resolvent)); a pair with y^* T'(lambda) x = 0 keeps its unit y and gets eta = +inf.
+ *   lam_dev: P complex128 eigenvalues; X_dev: n x P complex128 right eigenvectors (read only)
+ *   Y_dev:   n x P complex128, column-major (out)
+ *   eta_dev: P doubles (out: eta_L of the unit vector before the scaling); its_dev: P int32 steps
+ *            per pair (out), or NULL
+ * *iterations (or NULL) receives the largest step count. The caller owns every array; work arrays
+ * are allocated on the stream and the call returns when the stream is done.
+ * Errors: NEP_ERR_ARG (P < 0, max_it < 1, NULL arrays with P > 0, unknown precision), CUDA errors. */
+int nep_left_eigvecs(nep_split_t h, int32_t precision, int32_t P, const double *lam_dev, const double *X_dev,
+                     double *Y_dev, double *eta_dev, int32_t *its_dev, double tol, int32_t max_it,
+                     int32_t *iterations, void *stream);
+/* nep_left_eigvecs for the eigenpairs that the plan's last nep_plan_execute returned (as after
+ * nep_plan_polish, if called), in the order of nep_plan_result: Y_dev (n x capacity complex128)
+ * and eta_dev (capacity doubles) receive the first *nconv columns / entries. *nconv (or NULL)
+ * receives the number of returned pairs. Errors: NEP_ERR_ARG (NULL plan, max_it < 1, capacity < 0,
+ * NULL arrays with capacity > 0, more returned pairs than capacity), CUDA errors. */
+int nep_plan_left(nep_plan_t p, double tol, int32_t max_it, int32_t capacity, double *Y_dev, double *eta_dev,
+                  int32_t *nconv, int32_t *iterations, void *stream);
+/* Pole part of the resolvent, Keldysh's expansion (Sec. 2 Eq. (resolvent)) without its
+ * holomorphic remainder R(z):  out_{j,k} = sum_i (z_j - lambda_i)^{-1} x_i (y_i^* v_k)
+ * for nz points z_j and nv vectors v_k, with Keldysh-normalised left vectors y_i (as from
+ * nep_left_eigvecs). Inside a region holding all P eigenvalues and away from them, this is
+ * T(z)^{-1} v up to R(z) v. All arrays are the caller's device memory, complex128 column-major:
+ * lam_dev[P], X_dev and Y_dev n x P, z_dev[nz], V_dev n x nv, out_dev n x (nz*nv) with column
+ * j*nv + k for (z_j, v_k). Asynchronous on the stream (its work arrays are freed in stream order).
+ * Errors: NEP_ERR_ARG (n < 1, negative counts, NULL arrays that the counts need), CUDA errors. */
+int nep_apply_resolvent(int32_t n, int32_t P, const double *lam_dev, const double *X_dev, const double *Y_dev,
+                        int32_t nz, const double *z_dev, int32_t nv, const double *V_dev, double *out_dev,
+                        void *stream);
+
 /* ------------------------------------------------------------------ serving */
 /* Continuous-batching request server. Requests are admitted in arrival order as soon as a
  * worker is free and their device footprint (nep_plan_bytes) fits the remaining budget;
@@ -264,6 +304,14 @@ int nep_band_factor(nep_split_t h, int32_t npts, int32_t precision, void *ab_dev
  * nep_band_solve_cols instead. */
 int nep_band_solve(nep_split_t h, int32_t npts, int32_t precision, const void *ab_dev, const int32_t *ipiv_dev,
                    int32_t L, void *B_dev, void *stream);
+/* Conjugate-transpose solve T(z_j)^* X_j = B_j with the factors of nep_band_factor, in place on
+ * B (npts x n x L, column-major per point, element type of the precision): U^* forward, then
+ * the L factors' conjugate transposes and the interchanges in reverse order (the factorisation
+ * reused, as Sec. 4.5.4 does for the conjugate-transpose operator). An exactly zero pivot
+ * (info != 0) stands for a tiny one (1e-20 for complex64 factors, 1e-100 for complex128), which
+ * inverse iteration on a singular matrix wants. Asynchronous on the stream. */
+int nep_band_solve_adjoint(nep_split_t h, int32_t npts, int32_t precision, const void *ab_dev,
+                           const int32_t *ipiv_dev, int32_t L, void *B_dev, void *stream);
 /* U of the factored band by columns: ut[j][c*(kl+ku+1) + d] = U(c-d, c) for d in [0, kl+ku]
  * (zero where c-d < 0); ut_dev holds npts x n x (kl+ku+1) elements of the precision's type. */
 int nep_band_transpose_u(nep_split_t h, int32_t npts, int32_t precision, const void *ab_dev, void *ut_dev,

@@ -104,6 +104,14 @@ SIGNATURES = {
                           ctypes.POINTER(c_int32), c_void_p]),
     "nep_plan_polish": (c_int32, [c_void_p, ctypes.c_double, c_int32, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
                                   c_void_p]),
+    "nep_band_solve_adjoint": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_int32, c_void_p,
+                                         c_void_p]),
+    "nep_left_eigvecs": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                   ctypes.c_double, c_int32, ctypes.POINTER(c_int32), c_void_p]),
+    "nep_plan_left": (c_int32, [c_void_p, ctypes.c_double, c_int32, c_int32, c_void_p, c_void_p,
+                                ctypes.POINTER(c_int32), ctypes.POINTER(c_int32), c_void_p]),
+    "nep_apply_resolvent": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_int32,
+                                      c_void_p, c_void_p, c_void_p]),
 }
 
 _lib = None
@@ -323,6 +331,14 @@ class Plan:
         check(load().nep_plan_polish(self.handle, tol, max_it, ctypes.byref(done), ctypes.byref(its), stream))
         return done.value, its.value
 
+    def left(self, Y_dev, eta_dev, capacity, tol=1e-13, max_it=6, stream=0):
+        """nep_plan_left: Keldysh-normalised left eigenvectors of the returned pairs into Y_dev
+        (n x capacity complex128). Returns (pairs, steps run)."""
+        nc, its = c_int32(), c_int32()
+        check(load().nep_plan_left(self.handle, tol, max_it, capacity, ptr(Y_dev), ptr(eta_dev), ctypes.byref(nc),
+                                   ctypes.byref(its), stream))
+        return nc.value, its.value
+
     def buffer(self, name: str):
         p, b = c_void_p(), c_size_t()
         check(load().nep_plan_buffer(self.handle, name.encode(), ctypes.byref(p), ctypes.byref(b)))
@@ -450,6 +466,25 @@ def rii(split, precision, P, lam_dev, X_dev, eta_dev, its_dev=None, tol=1e-10, m
     check(load().nep_rii(split.handle, precision, P, ptr(lam_dev), ptr(X_dev), ptr(eta_dev), ptr(its_dev), tol,
                          max_it, ctypes.byref(its), stream))
     return its.value
+
+
+def band_solve_adjoint(split, npts, precision, ab_dev, ipiv_dev, L, B_dev, stream=0):
+    check(load().nep_band_solve_adjoint(split.handle, npts, precision, ptr(ab_dev), ptr(ipiv_dev), L, ptr(B_dev),
+                                        stream))
+
+
+def left_eigvecs(split, precision, P, lam_dev, X_dev, Y_dev, eta_dev, its_dev=None, tol=1e-13, max_it=6, stream=0):
+    """nep_left_eigvecs: Keldysh-normalised left eigenvectors of P pairs. Returns the steps run."""
+    its = c_int32()
+    check(load().nep_left_eigvecs(split.handle, precision, P, ptr(lam_dev), ptr(X_dev), ptr(Y_dev), ptr(eta_dev),
+                                  ptr(its_dev), tol, max_it, ctypes.byref(its), stream))
+    return its.value
+
+
+def apply_resolvent(n, P, lam_dev, X_dev, Y_dev, nz, z_dev, nv, V_dev, out_dev, stream=0):
+    """nep_apply_resolvent: out[:, j*nv + k] = sum_i x_i (y_i^* v_k) / (z_j - lambda_i)."""
+    check(load().nep_apply_resolvent(n, P, ptr(lam_dev), ptr(X_dev), ptr(Y_dev), nz, ptr(z_dev), nv, ptr(V_dev),
+                                     ptr(out_dev), stream))
 
 
 def kernel_launches() -> int:

@@ -83,7 +83,11 @@ struct nep_split {
     std::vector<int64_t> rowptr;
     std::vector<int32_t> col;
     std::vector<double> val, val_im;
-    std::vector<double> norms;
+    std::vector<double> norms, norms1;
+    // the union pattern by columns: entries colptr[c] .. colptr[c+1]-1 of column c, in
+    // increasing row order, are union-pattern entry cidx[k] in row crow[k]
+    std::vector<int64_t> colptr, cidx;
+    std::vector<int32_t> crow;
     std::vector<FnNode> nodes;
     std::vector<zd> coef;
     std::vector<int> roots;
@@ -93,6 +97,10 @@ struct nep_split {
     double* d_val = nullptr;
     double* d_val_im = nullptr;
     double* d_norms = nullptr;
+    double* d_norms1 = nullptr;
+    int64_t* d_colptr = nullptr;
+    int64_t* d_cidx = nullptr;
+    int32_t* d_crow = nullptr;
     FnNode* d_nodes = nullptr;
     zd* d_coef = nullptr;
     int* d_roots = nullptr;
@@ -110,6 +118,10 @@ struct nep_split {
         s.val = d_val;
         s.val_im = complex_vals ? d_val_im : nullptr;
         s.norms = d_norms;
+        s.norms1 = d_norms1;
+        s.colptr = d_colptr;
+        s.cidx = d_cidx;
+        s.crow = d_crow;
         s.fn_nodes = d_nodes;
         s.fn_coef = d_coef;
         s.fn_root = d_roots;
@@ -163,6 +175,10 @@ static void free_split_device(nep_split* h) {
     cudaFree(h->d_val);
     cudaFree(h->d_val_im);
     cudaFree(h->d_norms);
+    cudaFree(h->d_norms1);
+    cudaFree(h->d_colptr);
+    cudaFree(h->d_cidx);
+    cudaFree(h->d_crow);
     cudaFree(h->d_nodes);
     cudaFree(h->d_coef);
     cudaFree(h->d_roots);
@@ -237,6 +253,31 @@ extern "C" int nep_create_split(int32_t n, int32_t nterms, const nep_csr* A, con
         }
         h->norms[i] = nrm;
     }
+    // column view of the union pattern (counting sort by column, rows ascending) and ||A_i||_1
+    h->colptr.assign(n + 1, 0);
+    for (int64_t e = 0; e < h->nnz; ++e) ++h->colptr[h->col[e] + 1];
+    for (int c = 0; c < n; ++c) h->colptr[c + 1] += h->colptr[c];
+    h->cidx.assign(h->nnz, 0);
+    h->crow.assign(h->nnz, 0);
+    {
+        std::vector<int64_t> fill(h->colptr.begin(), h->colptr.end() - 1);
+        for (int r = 0; r < n; ++r)
+            for (int64_t e = h->rowptr[r]; e < h->rowptr[r + 1]; ++e) {
+                const int64_t k = fill[h->col[e]]++;
+                h->cidx[k] = e;
+                h->crow[k] = r;
+            }
+    }
+    h->norms1.assign(nterms, 0.0);
+    for (int i = 0; i < nterms; ++i)
+        for (int c = 0; c < n; ++c) {
+            double cs = 0.0;
+            for (int64_t k = h->colptr[c]; k < h->colptr[c + 1]; ++k) {
+                const size_t e = (size_t)i * h->nnz + h->cidx[k];
+                cs += std::hypot(h->val[e], h->val_im[e]);
+            }
+            h->norms1[i] = std::max(h->norms1[i], cs);
+        }
     for (int r = 0; r < n; ++r)
         for (int64_t e = h->rowptr[r]; e < h->rowptr[r + 1]; ++e) {
             h->kl = std::max(h->kl, r - h->col[e]);
@@ -252,6 +293,8 @@ extern "C" int nep_create_split(int32_t n, int32_t nterms, const nep_csr* A, con
     int rc = NEP_OK;
     if ((rc = upload(&h->d_rowptr, h->rowptr)) || (rc = upload(&h->d_col, h->col)) || (rc = upload(&h->d_val, h->val)) ||
         (rc = upload(&h->d_val_im, h->val_im)) || (rc = upload(&h->d_norms, h->norms)) ||
+        (rc = upload(&h->d_norms1, h->norms1)) || (rc = upload(&h->d_colptr, h->colptr)) ||
+        (rc = upload(&h->d_cidx, h->cidx)) || (rc = upload(&h->d_crow, h->crow)) ||
         (rc = upload(&h->d_nodes, h->nodes)) || (rc = upload(&h->d_coef, h->coef)) || (rc = upload(&h->d_roots, h->roots))) {
         free_split_device(h);
         delete h;
@@ -937,6 +980,90 @@ extern "C" int nep_plan_polish(nep_plan_t p, double tol, int32_t max_it, int32_t
     return rc;
 }
 
+extern "C" int nep_left_eigvecs(nep_split_t h, int32_t precision, int32_t P, const double* lam_dev,
+                                const double* X_dev, double* Y_dev, double* eta_dev, int32_t* its_dev, double tol,
+                                int32_t max_it, int32_t* iterations, void* stream) {
+    if (!h || P < 0 || max_it < 1 || (P > 0 && (!lam_dev || !X_dev || !Y_dev || !eta_dev))) {
+        set_error("nep_left_eigvecs: bad arguments");
+        return NEP_ERR_ARG;
+    }
+    if (precision != NEP_PREC_MIXED && precision != NEP_PREC_FP64) {
+        set_error("nep_left_eigvecs: bad precision");
+        return NEP_ERR_ARG;
+    }
+    if (iterations) *iterations = 0;
+    if (P == 0) return NEP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const SplitDev s = h->dev();
+    int* its = its_dev;
+    if (!its) NEP_CUDA(cudaMallocAsync((void**)&its, sizeof(int) * (size_t)P, st));
+    int k = 0;
+    int rc = precision == NEP_PREC_MIXED
+                 ? left_eigvecs<float>(s, P, (const zd*)lam_dev, (const zd*)X_dev, (zd*)Y_dev, eta_dev, its, tol,
+                                       max_it, &k, st)
+                 : left_eigvecs<double>(s, P, (const zd*)lam_dev, (const zd*)X_dev, (zd*)Y_dev, eta_dev, its, tol,
+                                        max_it, &k, st);
+    if (!its_dev) cudaFreeAsync(its, st);
+    if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = NEP_ERR_CUDA;
+    if (!rc && iterations) *iterations = k;
+    return rc;
+}
+
+extern "C" int nep_plan_left(nep_plan_t p, double tol, int32_t max_it, int32_t capacity, double* Y_dev,
+                             double* eta_dev, int32_t* nconv, int32_t* iterations, void* stream) {
+    if (!p || max_it < 1 || capacity < 0 || (capacity > 0 && (!Y_dev || !eta_dev))) {
+        set_error("nep_plan_left: bad arguments");
+        return NEP_ERR_ARG;
+    }
+    if (nconv) *nconv = 0;
+    if (iterations) *iterations = 0;
+    if (p->m <= 0 || p->kb <= 0) return NEP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = p->h->n, m = p->m;
+    std::vector<int> order(m + 1, 0);
+    NEP_CUDA(cudaMemcpyAsync(order.data(), p->order, sizeof(int) * (m + 1), cudaMemcpyDeviceToHost, st));
+    NEP_CUDA(cudaStreamSynchronize(st));
+    const int P = order[0];
+    if (nconv) *nconv = P;
+    if (P == 0) return NEP_OK;
+    if (P > capacity) {
+        set_error("nep_plan_left: %d returned pairs, room for %d", P, capacity);
+        return NEP_ERR_ARG;
+    }
+    int* didx = nullptr;
+    zd *lam = nullptr, *X = nullptr;
+    double* e = nullptr;
+    int* its = nullptr;
+    NEP_CUDA(cudaMallocAsync((void**)&didx, sizeof(int) * P, st));
+    NEP_CUDA(cudaMallocAsync((void**)&lam, sizeof(zd) * P, st));
+    NEP_CUDA(cudaMallocAsync((void**)&X, sizeof(zd) * (size_t)n * P, st));
+    NEP_CUDA(cudaMallocAsync((void**)&e, sizeof(double) * P, st));
+    NEP_CUDA(cudaMallocAsync((void**)&its, sizeof(int) * P, st));
+    int rc = NEP_OK, k = 0;
+    // the returned pairs in the order of nep_plan_result
+    if (cudaMemcpyAsync(didx, order.data() + 1, sizeof(int) * P, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = NEP_ERR_CUDA;
+    if (!rc) rc = launch_rii_move(n, P, didx, p->lamn, p->Xc, p->eta, lam, X, e, 0, st);
+    if (!rc) rc = p->mixed ? left_eigvecs<float>(p->h->dev(), P, lam, X, (zd*)Y_dev, eta_dev, its, tol, max_it, &k, st)
+                           : left_eigvecs<double>(p->h->dev(), P, lam, X, (zd*)Y_dev, eta_dev, its, tol, max_it, &k, st);
+    for (void* b : {(void*)didx, (void*)lam, (void*)X, (void*)e, (void*)its}) cudaFreeAsync(b, st);
+    if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = NEP_ERR_CUDA;
+    if (!rc && iterations) *iterations = k;
+    return rc;
+}
+
+extern "C" int nep_apply_resolvent(int32_t n, int32_t P, const double* lam_dev, const double* X_dev,
+                                   const double* Y_dev, int32_t nz, const double* z_dev, int32_t nv,
+                                   const double* V_dev, double* out_dev, void* stream) {
+    if (n < 1 || P < 0 || nz < 0 || nv < 0 || (P > 0 && (!lam_dev || !X_dev || !Y_dev)) ||
+        (nz > 0 && nv > 0 && (!z_dev || !V_dev || !out_dev))) {
+        set_error("nep_apply_resolvent: bad arguments");
+        return NEP_ERR_ARG;
+    }
+    return apply_resolvent(n, P, (const zd*)lam_dev, (const zd*)X_dev, (const zd*)Y_dev, nz, (const zd*)z_dev, nv,
+                           (const zd*)V_dev, (zd*)out_dev, (cudaStream_t)stream);
+}
+
 extern "C" int nep_plan_result(nep_plan_t p, nep_result_t* out) {
     if (!p || !out) { set_error("nep_plan_result: bad arguments"); return NEP_ERR_ARG; }
     const int n = p->h->n, N = p->Np, LM = p->LM;  // per-point arrays hold the solved points
@@ -1138,6 +1265,22 @@ extern "C" int nep_band_solve(nep_split_t h, int32_t npts, int32_t precision, co
     return precision == NEP_PREC_MIXED
                ? band_solve_step<float>(s, npts, (const zf*)ab_dev, ipiv_dev, L, (zf*)B_dev, (cudaStream_t)stream)
                : band_solve_step<double>(s, npts, (const zd*)ab_dev, ipiv_dev, L, (zd*)B_dev, (cudaStream_t)stream);
+}
+
+extern "C" int nep_band_solve_adjoint(nep_split_t h, int32_t npts, int32_t precision, const void* ab_dev,
+                                      const int32_t* ipiv_dev, int32_t L, void* B_dev, void* stream) {
+    if (!h || !ab_dev || !ipiv_dev || !B_dev || npts < 0 || L < 0) {
+        set_error("nep_band_solve_adjoint: bad arguments");
+        return NEP_ERR_ARG;
+    }
+    const SplitDev s = h->dev();
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == NEP_PREC_MIXED)
+        return launch_band_solve_adjoint<float>(s, npts, (const zf*)ab_dev, ipiv_dev, L, (zf*)B_dev, nullptr, st);
+    if (precision == NEP_PREC_FP64)
+        return launch_band_solve_adjoint<double>(s, npts, (const zd*)ab_dev, ipiv_dev, L, (zd*)B_dev, nullptr, st);
+    set_error("bad precision");
+    return NEP_ERR_ARG;
 }
 
 extern "C" int nep_band_transpose_u(nep_split_t h, int32_t npts, int32_t precision, const void* ab_dev, void* ut_dev,

@@ -164,6 +164,10 @@ struct SplitDev {
     const double* val;      // nterms x nnz real parts
     const double* val_im;   // nterms x nnz imaginary parts, or nullptr if all terms are real
     const double* norms;    // nterms, ||A_i||_inf
+    const double* norms1;   // nterms, ||A_i||_1
+    const int64_t* colptr;  // n+1: the pattern by columns, rows ascending within a column
+    const int64_t* cidx;    // nnz: union-pattern entry of each column-ordered entry
+    const int32_t* crow;    // nnz: its row
     const FnNode* fn_nodes;
     const zd* fn_coef;
     const int* fn_root;     // nterms root node indices
@@ -286,5 +290,18 @@ int rii_polish(const SplitDev& s, int P, zd* lam, zd* X, double* eta, int* its, 
 // dir 0: lam[q], X(:, q), eta[q] <- lam_c[idx[q]], X_c(:, idx[q]), eta_c[idx[q]]; dir 1: the reverse
 int launch_rii_move(int n, int P, const int* idx, zd* lam_c, zd* X_c, double* eta_c, zd* lam, zd* X, double* eta,
                     int dir, cudaStream_t st);
+
+// left.cu: conjugate-transpose solve T(z_j)^* W_j = B_j with the factors of T(z_j) (in place on B)
+template <typename T>
+int launch_band_solve_adjoint(const SplitDev& s, int npts, const cx<T>* ab, const int* ipiv, int L, cx<T>* B,
+                              const int* active, cudaStream_t st);
+// left eigenvectors Y (n x P) of P pairs (lam, X), Keldysh-normalised (y^* T'(lambda) x = 1); eta:
+// left scaled residual before the normalisation, its: steps per pair, *steps_host: steps run
+template <typename T>
+int left_eigvecs(const SplitDev& s, int P, const zd* lam, const zd* X, zd* Y, double* eta, int* its, double tol,
+                 int max_it, int* steps_host, cudaStream_t st);
+// out (n x nz*nv, column j*nv + k) = sum_i x_i (y_i^* v_k) / (z_j - lam_i)
+int apply_resolvent(int n, int P, const zd* lam, const zd* X, const zd* Y, int nz, const zd* z, int nv, const zd* V,
+                    zd* out, cudaStream_t st);
 
 }  // namespace nep

@@ -117,7 +117,7 @@ def solve_bytes(n, ldab, L, npts, esz):
 
 # DRAM bytes (read + write) of one solve launch from an ncu capture of the same launch,
 # keyed by (workload, precision); None where no capture of the current kernel exists.
-SOLVE_TRAFFIC = {("delay2d_s64", "mixed"): (199.0 + 24.8 + 303.7 + 29.2) * 1e6}
+SOLVE_TRAFFIC = {("delay2d_s64", "mixed"): (199.5 + 25.6 + 324.9 + 30.1) * 1e6}
 
 
 def fp32_alu_peak_tflops(sm_mhz):
@@ -406,6 +406,42 @@ def main():
         except binding.NepError as e:
             polish = {"unavailable": str(e)}
 
+    # left eigenvectors of the returned pairs (Sec. 2 Eq. (nep-left)) and the resolvent's pole part
+    # (Sec. 2 Eq. (resolvent)) applied to the probe block at points inside the region: one assembly
+    # + band LU at the P eigenvalues, then conjugate-transpose band solves (one per step and pair)
+    left_line = None
+    if not args.no_polish:
+        try:
+            res_l = plan.result()
+            P = int(len(res_l["lam"]))
+            if P > 0:
+                Yd = torch.zeros(2 * p.n * P, dtype=torch.float64, device="cuda")
+                etad = torch.zeros(P, dtype=torch.float64, device="cuda")
+                l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                l0.record()
+                nc, lsteps = plan.left(Yd, etad, P, tol=1e-13, max_it=6, stream=stream)
+                l1.record()
+                torch.cuda.synchronize()
+                c = complex(p.region["center"])
+                zs = c + 0.5 * float(p.region["a"]) * np.exp(2j * np.pi * (np.arange(8) + 0.5) / 8)
+                lamd = torch.from_numpy(np.ascontiguousarray(res_l["lam"]).view(np.float64).copy()).cuda()
+                Xd = torch.from_numpy(np.asfortranarray(res_l["X"]).ravel(order="F").view(np.float64).copy()).cuda()
+                zd = torch.from_numpy(zs.view(np.float64).copy()).cuda()
+                out = torch.zeros(2 * p.n * len(zs) * p.L, dtype=torch.float64, device="cuda")
+                for _ in range(3):
+                    binding.apply_resolvent(p.n, P, lamd, Xd, Yd, len(zs), zd, p.L, Vd, out, stream)
+                r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                r0.record()
+                binding.apply_resolvent(p.n, P, lamd, Xd, Yd, len(zs), zd, p.L, Vd, out, stream)
+                r1.record()
+                torch.cuda.synchronize()
+                eta_l = etad.cpu().numpy()
+                left_line = {"pairs": int(nc), "steps": int(lsteps), "ms": l0.elapsed_time(l1),
+                             "max_eta_left": float(eta_l.max()),
+                             "resolvent": {"points": len(zs), "vectors": p.L, "ms": r0.elapsed_time(r1)}}
+        except binding.NepError as e:
+            left_line = {"unavailable": str(e)}
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -475,6 +511,8 @@ def main():
             line["symmetric"] = symmetric
         if polish:
             line["polish"] = polish
+        if left_line:
+            line["left"] = left_line
         if not args.no_serving:
             line["serving"] = serving_bench(binding, prec, args.serving_requests, 0, 4, args.serving_smax)
         if not args.no_cpu:

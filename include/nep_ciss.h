@@ -46,6 +46,7 @@ extern "C" {
 #define NEP_WARN_REFINE 2        /* some quadrature solve missed the backward-error target */
 #define NEP_WARN_SINGULAR_NODE 4 /* an exactly zero pivot at some quadrature node         */
 #define NEP_WARN_NEWTON 8        /* a Newton iteration on the projected problem failed      */
+#define NEP_WARN_INTERP 16       /* NLEIGS: the interpolation degree test failed at max_degree */
 
 /* arithmetic of the quadrature solves */
 #define NEP_PREC_FP64 0  /* complex128 factors and solves ("plain FP64")                  */
@@ -250,6 +251,53 @@ int nep_plan_left(nep_plan_t p, double tol, int32_t max_it, int32_t capacity, do
 int nep_apply_resolvent(int32_t n, int32_t P, const double *lam_dev, const double *X_dev, const double *Y_dev,
                         int32_t nz, const double *z_dev, int32_t nv, const double *V_dev, double *out_dev,
                         void *stream);
+
+/* ------------------------------------------------------------------ NLEIGS (static variant) */
+/* Options of the rational-interpolation solver (Sec. 4.5). Zero fields take the defaults. */
+typedef struct {
+    double tol;          /* degree test max_i |d_i^d| < tol max_i |d_i^0|; default 1e-13        */
+    int32_t max_degree;  /* largest degree d; default 60, at most 63                             */
+    int32_t nboundary;   /* points discretising the boundary of the region; default 1024         */
+    int32_t krylov;      /* Arnoldi steps (no restart); default 100                               */
+    int32_t has_shift;   /* nonzero: use shift_re/im as the shift sigma, else the region centre  */
+    double shift_re, shift_im;
+    uint64_t seed;       /* seeded start vector (SplitMix64 + Box-Muller)                         */
+    double eig_tol;      /* acceptance: eta <= eig_tol and inside the region; default 1e-8        */
+} nep_nleigs_opts;
+/* The rational interpolant R_d(z) = sum_j b_j(z) D_j, D_j = sum_i d_i^j A_i, of Sec. 4.5.1 on the
+ * region (host computation):
+ *   - boundary of the region at nboundary points z_k = c + a cos(2 pi k/nb) + i b sin(2 pi k/nb);
+ *   - singularity set Xi: the roots of the denominators of rational nodes (and of the rational
+ *     denominator of a quotient), each square-root branch cut sampled at distances 0 and
+ *     10^(-4 + 8k/47), k < 48, from its branch point; exp contributes nothing; the outer function of
+ *     a composition is not searched;
+ *   - Leja-Bagby nodes sigma_j on the boundary and poles xi_j in Xi (Eq. (nleigsleja)), sigma_0 =
+ *     z_0, each Xi point used at most once, infinity once none is left; scalings beta_j with
+ *     max |b_j| = 1 on the boundary (Eq. (nleigsbj), beta_0 = 1);
+ *   - divided differences by the interpolation recurrence (Eq. (nleigsdd)); the degree d is the
+ *     first d >= 1 whose last pole, taken as infinity (Eq. (nleigsmatlin)), gives
+ *     max_i |d_i^d| < tol max_i |d_i^0|.
+ * Host arrays with room for cap = d+1 entries (d <= max_degree): sigma, xi complex[cap] (xi[0] and
+ * the last pole are infinity, written as (inf, 0)); beta double[cap]; dd complex[nterms*cap] with
+ * dd[i + nterms*j] = d_i^j. *degree, *converged (1 if the test held), *nsing (points of Xi); any
+ * output pointer may be NULL. Errors: NEP_ERR_ARG (bad region, cap < d+1, max_degree outside
+ * 1..63). */
+int nep_nleigs_interpolation(nep_split_t h, const nep_region *r, const nep_nleigs_opts *o, int32_t cap,
+                             double *sigma, double *xi, double *beta, double *dd, int32_t *degree,
+                             int32_t *converged, int32_t *nsing);
+/* NLEIGS, static variant with a full basis (Sec. 4.5.2, 4.5.3 "full basis"): shift-and-invert
+ * Arnoldi with o->krylov steps on S = (A - sigma B)^{-1} B for the linearisation (A, B) of
+ * Eq. (nleigsmatlin), applied through the block recurrences of Eqs. (nleigstoarreca) and
+ * (nleigstoarrecb) with one band LU of R_d(sigma) (FP64) and one band solve per step; classical
+ * Gram-Schmidt twice. Ritz values theta give lambda = sigma + 1/theta and x the first block of the
+ * Ritz vector; pairs inside the region with FP64 eta (Sec. 2 Eq. (sressplit), of the full T) at most
+ * eig_tol are returned, deduplicated and sorted as nep_ciss_solve does. *out receives a result
+ * object (nep_result_get; hankel_rank there is 0); *degree (or NULL) the interpolation degree.
+ * Needs nterms <= 8. The call allocates its work arrays on the stream ((d n) x (krylov+1)
+ * complex128 for the basis) and returns when they are done. Errors: NEP_ERR_ARG, NEP_ERR_REGION
+ * (a singularity of some f_i inside or on the region), CUDA errors. */
+int nep_nleigs_solve(nep_split_t h, const nep_region *r, const nep_nleigs_opts *o, nep_result_t *out,
+                     int32_t *degree, void *stream);
 
 /* ------------------------------------------------------------------ serving */
 /* Continuous-batching request server. Requests are admitted in arrival order as soon as a

@@ -50,6 +50,12 @@ class NepOpts(ctypes.Structure):
                 ("newton_tol", c_double), ("seed", ctypes.c_uint64), ("symmetric", c_int32)]
 
 
+class NepNleigsOpts(ctypes.Structure):
+    _fields_ = [("tol", c_double), ("max_degree", c_int32), ("nboundary", c_int32), ("krylov", c_int32),
+                ("has_shift", c_int32), ("shift_re", c_double), ("shift_im", c_double), ("seed", ctypes.c_uint64),
+                ("eig_tol", c_double)]
+
+
 class NepResultInfo(ctypes.Structure):
     _fields_ = [("n", c_int32), ("N", c_int32), ("L", c_int32), ("M", c_int32), ("precision", c_int32),
                 ("hankel_rank", c_int32), ("basis_rank", c_int32), ("ncandidates", c_int32),
@@ -110,6 +116,11 @@ SIGNATURES = {
                                    ctypes.c_double, c_int32, ctypes.POINTER(c_int32), c_void_p]),
     "nep_plan_left": (c_int32, [c_void_p, ctypes.c_double, c_int32, c_int32, c_void_p, c_void_p,
                                 ctypes.POINTER(c_int32), ctypes.POINTER(c_int32), c_void_p]),
+    "nep_nleigs_interpolation": (c_int32, [c_void_p, ctypes.POINTER(NepRegion), ctypes.POINTER(NepNleigsOpts), c_int32,
+                                           c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_int32),
+                                           ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
+    "nep_nleigs_solve": (c_int32, [c_void_p, ctypes.POINTER(NepRegion), ctypes.POINTER(NepNleigsOpts),
+                                   ctypes.POINTER(c_void_p), ctypes.POINTER(c_int32), c_void_p]),
     "nep_apply_resolvent": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_int32,
                                       c_void_p, c_void_p, c_void_p]),
 }
@@ -485,6 +496,45 @@ def apply_resolvent(n, P, lam_dev, X_dev, Y_dev, nz, z_dev, nv, V_dev, out_dev, 
     """nep_apply_resolvent: out[:, j*nv + k] = sum_i x_i (y_i^* v_k) / (z_j - lambda_i)."""
     check(load().nep_apply_resolvent(n, P, ptr(lam_dev), ptr(X_dev), ptr(Y_dev), nz, ptr(z_dev), nv, ptr(V_dev),
                                      ptr(out_dev), stream))
+
+
+def nleigs_opts(tol=0.0, max_degree=0, nboundary=0, krylov=0, shift=None, seed=0, eig_tol=0.0) -> NepNleigsOpts:
+    o = NepNleigsOpts()
+    o.tol, o.max_degree, o.nboundary, o.krylov, o.seed, o.eig_tol = tol, max_degree, nboundary, krylov, seed, eig_tol
+    if shift is not None:
+        o.has_shift, o.shift_re, o.shift_im = 1, complex(shift).real, complex(shift).imag
+    return o
+
+
+def nleigs_interpolation(split, region, **opts) -> dict:
+    """nep_nleigs_interpolation: nodes, poles (inf for none), scalings, divided differences dd[i, j]."""
+    lib = load()
+    r, o = region_struct(region), nleigs_opts(**opts)
+    d, conv, ns = c_int32(), c_int32(), c_int32()
+    check(lib.nep_nleigs_interpolation(split.handle, ctypes.byref(r), ctypes.byref(o), 0, None, None, None, None,
+                                       ctypes.byref(d), ctypes.byref(conv), ctypes.byref(ns)))
+    cap = d.value + 1
+    sig = np.zeros(cap, np.complex128)
+    xi = np.zeros(cap, np.complex128)
+    beta = np.zeros(cap)
+    dd = np.zeros(split.nterms * cap, np.complex128)
+    check(lib.nep_nleigs_interpolation(split.handle, ctypes.byref(r), ctypes.byref(o), cap, sig.ctypes.data,
+                                       xi.ctypes.data, beta.ctypes.data, dd.ctypes.data, ctypes.byref(d),
+                                       ctypes.byref(conv), ctypes.byref(ns)))
+    return {"d": d.value, "converged": bool(conv.value), "nsing": ns.value, "sigma": sig, "xi": xi, "beta": beta,
+            "dd": dd.reshape(cap, split.nterms).T.copy()}
+
+
+def nleigs_solve(split, region, stream=0, **opts) -> dict:
+    """nep_nleigs_solve: the result dict of ciss_solve plus the interpolation degree."""
+    lib = load()
+    r, o = region_struct(region), nleigs_opts(**opts)
+    res, d = c_void_p(), c_int32()
+    check(lib.nep_nleigs_solve(split.handle, ctypes.byref(r), ctypes.byref(o), ctypes.byref(res), ctypes.byref(d),
+                               stream))
+    out = _result_dict(res)
+    out["degree"] = d.value
+    return out
 
 
 def kernel_launches() -> int:

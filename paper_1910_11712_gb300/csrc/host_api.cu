@@ -1064,6 +1064,105 @@ extern "C" int nep_apply_resolvent(int32_t n, int32_t P, const double* lam_dev, 
                            (const zd*)V_dev, (zd*)out_dev, (cudaStream_t)stream);
 }
 
+// ============================================================================ NLEIGS
+struct NleigsParams {
+    double tol;
+    int dmax, nb, kmax, eig_ok;
+    zd shift;
+    uint64_t seed;
+    double eig_tol;
+};
+
+static int nleigs_params(nep_split_t h, const nep_region* r, const nep_nleigs_opts* o, NleigsParams* q) {
+    if (!h || !r) { set_error("null handle or region"); return NEP_ERR_ARG; }
+    if (!(r->a > 0) || !(r->b > 0)) { set_error("region semi-axes must be positive"); return NEP_ERR_ARG; }
+    nep_nleigs_opts z{};
+    if (!o) o = &z;
+    q->tol = o->tol > 0 ? o->tol : 1e-13;
+    q->dmax = o->max_degree > 0 ? o->max_degree : 60;
+    q->nb = o->nboundary > 0 ? o->nboundary : 1024;
+    q->kmax = o->krylov > 0 ? o->krylov : 100;
+    q->shift = o->has_shift ? mk(o->shift_re, o->shift_im) : mk(r->center_re, r->center_im);
+    q->seed = o->seed;
+    q->eig_tol = o->eig_tol > 0 ? o->eig_tol : 1e-8;
+    if (q->dmax > 63 || q->nb < 8 || q->nb > (1 << 20) || q->kmax > 2048) {
+        set_error("nleigs: max_degree <= 63, 8 <= nboundary <= 2^20, krylov <= 2048");
+        return NEP_ERR_ARG;
+    }
+    for (int i = 0; i < h->nterms; ++i) {
+        const int rc = check_region_node(h, h->roots[i], r, true);
+        if (rc) return rc;
+    }
+    return NEP_OK;
+}
+
+extern "C" int nep_nleigs_interpolation(nep_split_t h, const nep_region* r, const nep_nleigs_opts* o, int32_t cap,
+                                        double* sigma, double* xi, double* beta, double* dd, int32_t* degree,
+                                        int32_t* converged, int32_t* nsing) {
+    NleigsParams q;
+    NEP_TRY(nleigs_params(h, r, o, &q));
+    NleigsInterp it;
+    NEP_TRY(nleigs_interpolation(h->nodes, h->coef, h->roots, mk(r->center_re, r->center_im), r->a, r->b, q.tol,
+                                 q.dmax, q.nb, &it));
+    if (degree) *degree = it.d;
+    if (converged) *converged = it.converged;
+    if (nsing) *nsing = it.nsing;
+    const int d1 = it.d + 1, nt = h->nterms;
+    if ((sigma || xi || beta || dd) && cap < d1) {
+        set_error("nep_nleigs_interpolation: degree %d needs cap >= %d", it.d, d1);
+        return NEP_ERR_ARG;
+    }
+    for (int j = 0; j < d1; ++j) {
+        if (sigma) { sigma[2 * j] = it.sigma[j].re; sigma[2 * j + 1] = it.sigma[j].im; }
+        if (xi) { xi[2 * j] = it.xi[j].re; xi[2 * j + 1] = it.xi[j].im; }
+        if (beta) beta[j] = it.beta[j];
+        if (dd)
+            for (int i = 0; i < nt; ++i) {
+                dd[2 * (i + (size_t)nt * j)] = it.dd[i + (size_t)nt * j].re;
+                dd[2 * (i + (size_t)nt * j) + 1] = it.dd[i + (size_t)nt * j].im;
+            }
+    }
+    return NEP_OK;
+}
+
+extern "C" int nep_nleigs_solve(nep_split_t h, const nep_region* r, const nep_nleigs_opts* o, nep_result_t* out,
+                                int32_t* degree, void* stream) {
+    if (!out) { set_error("out is NULL"); return NEP_ERR_ARG; }
+    *out = nullptr;
+    NleigsParams q;
+    NEP_TRY(nleigs_params(h, r, o, &q));
+    if (h->nterms > 8) { set_error("nleigs: at most 8 terms"); return NEP_ERR_UNSUPPORTED; }
+    NleigsInterp it;
+    NEP_TRY(nleigs_interpolation(h->nodes, h->coef, h->roots, mk(r->center_re, r->center_im), r->a, r->b, q.tol,
+                                 q.dmax, q.nb, &it));
+    if (degree) *degree = it.d;
+    const size_t N = (size_t)it.d * h->n;
+    const int kmax = (int)std::min<size_t>((size_t)q.kmax, N);
+    std::vector<zd> start(N);
+    draw_probe_block(q.seed, N, false, reinterpret_cast<double*>(start.data()));
+    NleigsOut res;
+    cudaStream_t st = (cudaStream_t)stream;
+    NEP_TRY(nleigs_run(h->dev(), it, q.shift, kmax, reinterpret_cast<const double*>(start.data()),
+                       mk(r->center_re, r->center_im), r->a, r->b, q.eig_tol, &res, st));
+    nep_result* rr = new nep_result();
+    rr->n = h->n;
+    rr->nconv = (int)res.lam.size();
+    rr->m = 0;
+    rr->flags = (it.converged ? 0 : NEP_WARN_INTERP) | (res.lu_info ? NEP_WARN_SINGULAR_NODE : 0);
+    rr->info.n = h->n;
+    for (size_t q2 = 0; q2 < res.lam.size(); ++q2) {
+        rr->lam.push_back(res.lam[q2].re);
+        rr->lam.push_back(res.lam[q2].im);
+        rr->resid.push_back(res.eta[q2]);
+    }
+    for (const zd& v : res.X) {
+        rr->X.push_back(v.re);
+        rr->X.push_back(v.im);
+    }
+    *out = rr;
+    return NEP_OK;
+}
+
 extern "C" int nep_plan_result(nep_plan_t p, nep_result_t* out) {
     if (!p || !out) { set_error("nep_plan_result: bad arguments"); return NEP_ERR_ARG; }
     const int n = p->h->n, N = p->Np, LM = p->LM;  // per-point arrays hold the solved points

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <string>
+#include <vector>
 
 #include "../../include/nep_ciss.h"
 
@@ -300,6 +301,23 @@ int launch_band_solve_adjoint(const SplitDev& s, int npts, const cx<T>* ab, cons
 template <typename T>
 int left_eigvecs(const SplitDev& s, int P, const zd* lam, const zd* X, zd* Y, double* eta, int* its, double tol,
                  int max_it, int* steps_host, cudaStream_t st);
+// nleigs.cu: rational interpolation on the region (host) and shift-and-invert Arnoldi on its
+// linearisation (device)
+struct NleigsInterp {
+    int d = 0, converged = 0, nsing = 0;
+    std::vector<zd> sigma, xi;  // d+1 nodes; poles (xi[0] unused, infinity as (inf, 0))
+    std::vector<double> beta;   // d+1 scalings
+    std::vector<zd> dd;         // nterms x (d+1): dd[i + nterms j] = d_i^j
+};
+struct NleigsOut {
+    std::vector<zd> lam, X, ritz;
+    std::vector<double> eta;
+    int steps = 0, lu_info = 0;
+};
+int nleigs_interpolation(const std::vector<FnNode>& nodes, const std::vector<zd>& pool, const std::vector<int>& roots,
+                         zd c, double a, double b, double tol, int dmax, int nb, NleigsInterp* out);
+int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, const double* start_host, zd c,
+               double ea, double eb, double eig_tol, NleigsOut* res, cudaStream_t st);
 // out (n x nz*nv, column j*nv + k) = sum_i x_i (y_i^* v_k) / (z_j - lam_i)
 int apply_resolvent(int n, int P, const zd* lam, const zd* X, const zd* Y, int nz, const zd* z, int nv, const zd* V,
                     zd* out, cudaStream_t st);

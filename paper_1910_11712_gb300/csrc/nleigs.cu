@@ -1,0 +1,507 @@
+// NLEIGS, static variant (Sec. 4.5): a rational interpolant R_d(z) = sum_j b_j(z) D_j of the
+// split operator on a target set Sigma (the region's ellipse), linearised as the pencil (A, B)
+// of Sec. 4.5.1 Eq. (nleigsmatlin) with d blocks of n, and shift-and-invert Arnoldi on
+// S = (A - sigma B)^{-1} B with a full (d n)-vector basis.
+//
+// Host (small, FP64):
+//   * the boundary of Sigma at nb points, the singularity set Xi from the function trees
+//     (denominator roots of rational nodes and of a quotient's rational denominator, square-root
+//     cuts sampled at fixed distances; exp has none);
+//   * Leja-Bagby nodes sigma_j and poles xi_j (Sec. 4.5.1 Eq. (nleigsleja)), scalings beta_j
+//     with max |b_j| = 1 on the boundary (Eq. (nleigsbj));
+//   * scalar divided differences d_i^j by the interpolation recurrence of Eq. (nleigsdd),
+//     d_i^j = (f_i(sigma_j) - sum_{k<j} b_k(sigma_j) d_i^k) / b_j(sigma_j), and the degree: the
+//     first d >= 1 whose last pole, taken as infinity, gives max_i |d_i^d| < tol max_i |d_i^0|.
+// Device (FP64), one Arnoldi step w = S v (Sec. 4.5.2, Eqs. (nleigstoarreca), (nleigstoarrecb)):
+//   * with z = B v (z^j = v^{j-1} + beta_j/xi_j v^j), a particular solution p of the block rows
+//     1..d-1 with p^{d-1} = 0, p^{j-1} = (z^j - beta_j (1 - sigma/xi_j) p^j) / (sigma_{j-1} - sigma),
+//     and the per-term combinations c_i = sum_{j<=d-2} d_i^j p^j + d_i^d / beta_d v^{d-1}, one
+//     thread per row (nleigs_expand_kernel);
+//   * u = R_d(sigma)^{-1} (-sum_i A_i c_i): the split SpMV and the band LU of R_d(sigma)
+//     (= sum_i (sum_j b_j(sigma) d_i^j) A_i, factored once) with the substitution sweeps;
+//   * w^j = p^j + b_j(sigma) u (the null space of the lower block rows is b(sigma) (x) C^n);
+//   * classical Gram-Schmidt, twice, against the basis on the path's FP64 GEMM.
+// The Ritz pairs of the Hessenberg matrix give lambda = sigma + 1/theta with x the first block of
+// the Ritz vector; the pairs inside Sigma are accepted by the FP64 scaled residual of the full
+// T (not of R_d) like the contour method's.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "nep_common.cuh"
+
+namespace nep {
+
+namespace {
+
+typedef std::complex<double> cd;
+
+inline cd to_cd(zd z) { return cd(z.re, z.im); }
+inline zd to_zd(cd z) { return mk(z.real(), z.imag()); }
+
+// roots of c[0] x^m + ... + c[m] (c[0] the leading coefficient) by Durand-Kerner iteration
+std::vector<cd> poly_roots(std::vector<cd> c) {
+    while (!c.empty() && c.front() == cd(0.0)) c.erase(c.begin());
+    const int m = (int)c.size() - 1;
+    std::vector<cd> r;
+    if (m < 1) return r;
+    for (int k = 1; k <= m; ++k) c[k] /= c[0];
+    c[0] = 1.0;
+    if (m == 1) return {-c[1]};
+    double rad = 0.0;
+    for (int k = 1; k <= m; ++k) rad = std::max(rad, std::pow(std::abs(c[k]), 1.0 / k));
+    rad = 1.0 + rad;
+    for (int k = 0; k < m; ++k) r.push_back(rad * std::pow(cd(0.4, 0.9), k));
+    auto p = [&](cd x) {
+        cd v = 1.0;
+        for (int k = 1; k <= m; ++k) v = v * x + c[k];
+        return v;
+    };
+    for (int it = 0; it < 2000; ++it) {
+        double move = 0.0;
+        for (int k = 0; k < m; ++k) {
+            cd den = 1.0;
+            for (int j = 0; j < m; ++j)
+                if (j != k) den *= r[k] - r[j];
+            if (den == cd(0.0)) den = cd(1e-300);
+            const cd step = p(r[k]) / den;
+            r[k] -= step;
+            move = std::max(move, std::abs(step) / std::max(1.0, std::abs(r[k])));
+        }
+        if (move < 1e-16) break;
+    }
+    return r;
+}
+
+std::vector<cd> coef_slice(const std::vector<zd>& pool, int off, int len) {
+    std::vector<cd> c;
+    for (int t = 0; t < len; ++t) c.push_back(to_cd(pool[off + t]));
+    return c;
+}
+
+// singular points in z of node k whose input is scale * z
+void node_singularities(const std::vector<FnNode>& nodes, const std::vector<zd>& pool, int k, cd scale,
+                        const std::vector<double>& cut_t, std::vector<cd>* out, int depth) {
+    if (k < 0 || k >= (int)nodes.size() || depth > 16) return;
+    const FnNode& nd = nodes[k];
+    const cd s = to_cd(nd.alpha) * scale;  // the node's inner argument is s z
+    if (nd.kind == NEP_FN_RATIONAL) {
+        if (nd.den_len > 1)
+            for (cd r : poly_roots(coef_slice(pool, nd.den_off, nd.den_len))) out->push_back(r / s);
+    } else if (nd.kind == NEP_FN_SQRT) {
+        for (double t : cut_t) out->push_back((to_cd(nd.shift) - t) / s);
+    } else if (nd.kind == NEP_FN_COMBINE) {
+        if (nd.op == NEP_OP_COMPOSE) {
+            node_singularities(nodes, pool, nd.b, s, cut_t, out, depth + 1);
+        } else {
+            node_singularities(nodes, pool, nd.a, s, cut_t, out, depth + 1);
+            node_singularities(nodes, pool, nd.b, s, cut_t, out, depth + 1);
+            if (nd.op == NEP_OP_DIV && nd.b >= 0 && nodes[nd.b].kind == NEP_FN_RATIONAL && nodes[nd.b].num_len > 1) {
+                const cd sb = to_cd(nodes[nd.b].alpha) * s;
+                for (cd r : poly_roots(coef_slice(pool, nodes[nd.b].num_off, nodes[nd.b].num_len)))
+                    out->push_back(r / sb);
+            }
+        }
+    }
+}
+
+const double kInf = INFINITY;
+inline bool finite_pole(cd x) { return std::isfinite(x.real()) && std::isfinite(x.imag()); }
+
+// b_0 .. b_d at z (b_0 = 1/beta_0)
+void basis_at(cd z, const std::vector<cd>& sig, const std::vector<cd>& xi, const std::vector<double>& beta, int d,
+              std::vector<cd>* b) {
+    b->assign(d + 1, 0.0);
+    (*b)[0] = 1.0 / beta[0];
+    for (int j = 1; j <= d; ++j) {
+        cd g = (*b)[j - 1] * (z - sig[j - 1]) / beta[j];
+        if (finite_pole(xi[j])) g /= (1.0 - z / xi[j]);
+        (*b)[j] = g;
+    }
+}
+
+}  // namespace
+
+int nleigs_interpolation(const std::vector<FnNode>& nodes, const std::vector<zd>& pool, const std::vector<int>& roots,
+                         zd c, double a, double b, double tol, int dmax, int nb, NleigsInterp* out) {
+    const int nt = (int)roots.size();
+    std::vector<cd> bnd(nb);
+    for (int k = 0; k < nb; ++k) {
+        const double th = 6.283185307179586476925 * k / nb;
+        bnd[k] = to_cd(c) + cd(a * std::cos(th), b * std::sin(th));
+    }
+    std::vector<double> cut_t{0.0};
+    for (int k = 0; k < 48; ++k) cut_t.push_back(std::pow(10.0, -4.0 + 8.0 * k / 47.0));
+    std::vector<cd> Xi;
+    for (int i = 0; i < nt; ++i) node_singularities(nodes, pool, roots[i], 1.0, cut_t, &Xi, 0);
+    // Leja-Bagby: s_j on the boundary and on Xi, rescaled to max 1 on the boundary every step
+    std::vector<cd> sig(dmax + 1), xin(dmax + 1, cd(kInf, 0.0));
+    std::vector<char> used(Xi.size(), 0);
+    sig[0] = bnd[0];
+    std::vector<cd> sb(nb), sx(Xi.size());
+    for (int k = 0; k < nb; ++k) sb[k] = bnd[k] - sig[0];
+    for (size_t k = 0; k < Xi.size(); ++k) sx[k] = Xi[k] - sig[0];
+    for (int j = 0; j < dmax; ++j) {
+        int kb = 0;
+        for (int k = 1; k < nb; ++k)
+            if (std::abs(sb[k]) > std::abs(sb[kb])) kb = k;
+        sig[j + 1] = bnd[kb];
+        int kx = -1;
+        for (size_t k = 0; k < Xi.size(); ++k) {
+            const double v = std::abs(sx[k]);
+            if (used[k] || !std::isfinite(v)) continue;
+            if (kx < 0 || v < std::abs(sx[kx])) kx = (int)k;
+        }
+        if (kx >= 0) {
+            xin[j + 1] = Xi[kx];
+            used[kx] = 1;
+        }
+        const bool fin = finite_pole(xin[j + 1]);
+        double m = 0.0;
+        for (int k = 0; k < nb; ++k) {
+            sb[k] *= (bnd[k] - sig[j + 1]);
+            if (fin) sb[k] /= (1.0 - bnd[k] / xin[j + 1]);
+            m = std::max(m, std::abs(sb[k]));
+        }
+        for (size_t k = 0; k < Xi.size(); ++k) {
+            if (used[k] && (int)k == kx) {
+                sx[k] = cd(kInf, 0.0);
+                continue;
+            }
+            sx[k] *= (Xi[k] - sig[j + 1]);
+            if (fin) sx[k] /= (1.0 - Xi[k] / xin[j + 1]);
+        }
+        if (m > 0.0 && std::isfinite(m)) {
+            for (auto& v : sb) v /= m;
+            for (auto& v : sx) v /= m;
+        }
+    }
+    // f_i at the nodes
+    std::vector<cd> F((size_t)nt * (dmax + 1));
+    for (int j = 0; j <= dmax; ++j)
+        for (int i = 0; i < nt; ++i) F[i + (size_t)nt * j] = to_cd(fn_eval(nodes.data(), pool.data(), roots[i], to_zd(sig[j])).f);
+    int d = 1;
+    std::vector<cd> xi;
+    std::vector<double> beta;
+    std::vector<cd> dd;
+    bool converged = false;
+    for (d = 1; d <= dmax; ++d) {
+        xi.assign(xin.begin(), xin.begin() + d + 1);
+        xi[d] = cd(kInf, 0.0);  // the last pole of the interpolant is infinity
+        beta.assign(d + 1, 1.0);
+        std::vector<cd> bv(nb, 1.0);
+        for (int j = 1; j <= d; ++j) {
+            double m = 0.0;
+            for (int k = 0; k < nb; ++k) {
+                cd g = bv[k] * (bnd[k] - sig[j - 1]);
+                if (finite_pole(xi[j])) g /= (1.0 - bnd[k] / xi[j]);
+                bv[k] = g;
+                m = std::max(m, std::abs(g));
+            }
+            beta[j] = m;
+            for (auto& v : bv) v /= m;
+        }
+        // recurrence d_i^j = (f_i(sigma_j) - sum_{k<j} b_k(sigma_j) d_i^k) / b_j(sigma_j)
+        dd.assign((size_t)nt * (d + 1), 0.0);
+        std::vector<cd> bj;
+        for (int j = 0; j <= d; ++j) {
+            basis_at(sig[j], sig, xi, beta, d, &bj);
+            for (int i = 0; i < nt; ++i) {
+                cd acc = F[i + (size_t)nt * j];
+                for (int k = 0; k < j; ++k) acc -= bj[k] * dd[i + (size_t)nt * k];
+                dd[i + (size_t)nt * j] = acc / bj[j];
+            }
+        }
+        double d0 = 0.0, dl = 0.0;
+        for (int i = 0; i < nt; ++i) {
+            d0 = std::max(d0, std::abs(dd[i]));
+            dl = std::max(dl, std::abs(dd[i + (size_t)nt * d]));
+        }
+        if (dl < tol * d0) {
+            converged = true;
+            break;
+        }
+        if (d == dmax) break;
+    }
+    out->d = d;
+    out->converged = converged;
+    out->sigma.clear();
+    out->xi.clear();
+    out->dd.clear();
+    for (int j = 0; j <= d; ++j) {
+        out->sigma.push_back(to_zd(sig[j]));
+        out->xi.push_back(to_zd(xi[j]));
+    }
+    out->xi[0] = mk(kInf, 0.0);
+    out->beta = beta;
+    for (auto v : dd) out->dd.push_back(to_zd(v));
+    out->nsing = (int)Xi.size();
+    return NEP_OK;
+}
+
+// ------------------------------------------------------------------ device kernels
+constexpr int kNleigsMaxTerms = 8;
+
+struct ExpandCoef {
+    zd inv_ds[64];  // 1 / (sigma_{j-1} - shift), j = 1 .. d-1
+    zd g[64];       // beta_j / xi_j
+    zd e[64];       // beta_j (1 - shift / xi_j)
+    zd bsig[64];    // b_j(shift), j = 0 .. d-1
+};
+
+// p^{d-1} = 0, p^{j-1} = (v^{j-1} + g_j v^j - e_j p^j) inv_ds_j (j = d-1 .. 1), written to W;
+// C[i n + r] = sum_{j<=d-2} dd_i^j p^j + dd_i^d / beta_d v^{d-1}. One thread per row.
+__global__ void nleigs_expand_kernel(int n, int d, int nt, const zd* __restrict__ v, zd* __restrict__ W,
+                                     zd* __restrict__ C, const ExpandCoef* __restrict__ ec,
+                                     const zd* __restrict__ ddc /* nt x (d+1), column d already / beta_d */) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    zd acc[kNleigsMaxTerms];
+#pragma unroll
+    for (int i = 0; i < kNleigsMaxTerms; ++i) acc[i] = mk(0.0, 0.0);
+    zd vj = v[(int64_t)(d - 1) * n + r];  // v^{d-1}
+#pragma unroll
+    for (int i = 0; i < kNleigsMaxTerms; ++i)
+        if (i < nt) acc[i] = ddc[i + (int64_t)nt * d] * vj;
+    W[(int64_t)(d - 1) * n + r] = mk(0.0, 0.0);
+    zd pj = mk(0.0, 0.0);
+    for (int j = d - 1; j >= 1; --j) {
+        const zd vjm = v[(int64_t)(j - 1) * n + r];
+        const zd z = fma_(vjm, ec->g[j], vj);
+        const zd p = (z - ec->e[j] * pj) * ec->inv_ds[j];
+        W[(int64_t)(j - 1) * n + r] = p;
+#pragma unroll
+        for (int i = 0; i < kNleigsMaxTerms; ++i)
+            if (i < nt) acc[i] = fma_(acc[i], ddc[i + (int64_t)nt * (j - 1)], p);
+        pj = p;
+        vj = vjm;
+    }
+#pragma unroll
+    for (int i = 0; i < kNleigsMaxTerms; ++i)
+        if (i < nt) C[(int64_t)i * n + r] = acc[i];
+}
+
+// out[r] = -sum_e sum_i a_i(r, col e) C[i n + col e]; one warp per row
+__global__ void nleigs_spmv_kernel(SplitDev s, const zd* __restrict__ C, zd* __restrict__ out) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= s.n) return;
+    const int r = (int)gw;
+    zd acc = mk(0.0, 0.0);
+    for (int64_t e = s.rowptr[r] + lane; e < s.rowptr[r + 1]; e += 32) {
+        const int c = s.col[e];
+        for (int i = 0; i < s.nterms; ++i) {
+            const zd a = mk(s.val[(int64_t)i * s.nnz + e], s.val_im ? s.val_im[(int64_t)i * s.nnz + e] : 0.0);
+            acc = fma_(acc, a, C[(int64_t)i * s.n + c]);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+        acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+    }
+    if (lane == 0) out[r] = mk(-acc.re, -acc.im);
+}
+
+// W^j += b_j(shift) u, j = 0 .. d-1
+__global__ void nleigs_combine_kernel(int n, int d, const zd* __restrict__ u, zd* __restrict__ W,
+                                      const ExpandCoef* __restrict__ ec) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * d) return;
+    const int j = (int)(t / n), r = (int)(t % n);
+    W[t] = fma_(W[t], ec->bsig[j], u[r]);
+}
+
+// w -= u; Hcol[0..k] += hv
+__global__ void nleigs_gs_update_kernel(int64_t N, int k1, zd* __restrict__ w, const zd* __restrict__ u,
+                                        const zd* __restrict__ hv, zd* __restrict__ Hcol) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < N) w[t] = w[t] - u[t];
+    if (t < k1) Hcol[t] = Hcol[t] + hv[t];
+}
+
+// h = sqrt(Re nr); H sub-diagonal entry (or hlast) = h; w /= h (w = 0 after a breakdown)
+__global__ void nleigs_scale_kernel(int64_t N, zd* __restrict__ w, const zd* __restrict__ nr, zd* __restrict__ hsub) {
+    const double h = sqrt(fmax(nr->re, 0.0));
+    const double sc = h > 1e-300 ? 1.0 / h : 0.0;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < N) w[t] = sc * w[t];
+    if (t == 0) *hsub = mk(h, 0.0);
+}
+
+// lam = shift + 1/theta; ok = theta != 0 and finite
+__global__ void nleigs_ritz_kernel(int m, const zd* __restrict__ theta, zd shift, zd* __restrict__ lam,
+                                   int* __restrict__ ok) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const zd t = theta[i];
+    const bool nz = (t.re != 0.0 || t.im != 0.0) && isfinite(t.re) && isfinite(t.im);
+    lam[i] = nz ? shift + cdiv(mk(1.0, 0.0), t) : mk(0.0, 0.0);
+    ok[i] = nz && isfinite(lam[i].re) && isfinite(lam[i].im);
+}
+
+__global__ void nleigs_normalize_start_kernel(int64_t N, zd* __restrict__ w, const zd* __restrict__ nr) {
+    const double h = sqrt(fmax(nr->re, 0.0));
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < N) w[t] = (h > 0.0 ? 1.0 / h : 0.0) * w[t];
+}
+
+namespace {
+struct NlScratch {
+    std::vector<void*> bufs;
+    cudaStream_t st;
+    ~NlScratch() {
+        for (void* b : bufs) cudaFreeAsync(b, st);
+    }
+    template <typename U>
+    int get(U** out, size_t count) {
+        *out = nullptr;
+        void* p = nullptr;
+        const cudaError_t e = cudaMallocAsync(&p, sizeof(U) * std::max<size_t>(count, 1), st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync", __FILE__, __LINE__);
+        bufs.push_back(p);
+        *out = static_cast<U*>(p);
+        return NEP_OK;
+    }
+};
+}  // namespace
+
+int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, const double* start_host, zd c,
+               double ea, double eb, double eig_tol, NleigsOut* res, cudaStream_t st) {
+    const int n = s.n, nt = s.nterms, d = it.d;
+    if (nt > kNleigsMaxTerms || d < 1 || d > 63 || kmax < 1) return NEP_ERR_ARG;
+    const int64_t N = (int64_t)d * n;
+    NlScratch w{{}, st};
+    // host constants
+    ExpandCoef ec{};
+    std::vector<cd> sig, xi;
+    for (auto z : it.sigma) sig.push_back(to_cd(z));
+    for (auto z : it.xi) xi.push_back(to_cd(z));
+    const cd sh = to_cd(shift);
+    for (int j = 1; j <= d - 1; ++j) {
+        ec.inv_ds[j] = to_zd(1.0 / (sig[j - 1] - sh));
+        const bool fin = finite_pole(xi[j]);
+        ec.g[j] = to_zd(fin ? it.beta[j] / xi[j] : cd(0.0));
+        ec.e[j] = to_zd(it.beta[j] * (fin ? 1.0 - sh / xi[j] : cd(1.0)));
+    }
+    std::vector<cd> bs;
+    basis_at(sh, sig, xi, it.beta, d, &bs);
+    for (int j = 0; j < d; ++j) ec.bsig[j] = to_zd(bs[j]);
+    std::vector<zd> ddc(it.dd);  // nt x (d+1), column d divided by beta_d
+    for (int i = 0; i < nt; ++i) ddc[i + (size_t)nt * d] = to_zd(to_cd(ddc[i + (size_t)nt * d]) / it.beta[d]);
+    std::vector<zd> Fs(nt);      // R_d(shift) = sum_i Fs_i A_i
+    for (int i = 0; i < nt; ++i) {
+        cd acc = 0.0;
+        for (int j = 0; j <= d; ++j) acc += bs[j] * to_cd(it.dd[i + (size_t)nt * j]);
+        Fs[i] = to_zd(acc);
+    }
+    // device arrays
+    ExpandCoef* d_ec = nullptr;
+    zd *d_ddc = nullptr, *d_F = nullptr, *ab = nullptr, *ut = nullptr, *V = nullptr, *C = nullptr, *u = nullptr;
+    zd *Hm = nullptr, *hv = nullptr, *tmp = nullptr, *nr = nullptr, *part = nullptr, *hlast = nullptr;
+    int *ipiv = nullptr, *info = nullptr;
+    const int kv = s.kl + s.ku;
+    const size_t part_elems = (size_t)(kmax + 1) * 64;
+    NEP_TRY(w.get(&d_ec, 1));
+    NEP_TRY(w.get(&d_ddc, (size_t)nt * (d + 1)));
+    NEP_TRY(w.get(&d_F, (size_t)nt));
+    NEP_TRY(w.get(&ab, (size_t)n * s.ldab));
+    NEP_TRY(w.get(&ipiv, (size_t)n));
+    NEP_TRY(w.get(&info, 1));
+    if (band_sweeps_fit(s.kl, s.ku)) NEP_TRY(w.get(&ut, (size_t)n * (kv + 1)));
+    NEP_TRY(w.get(&V, (size_t)N * (kmax + 1)));
+    NEP_TRY(w.get(&C, (size_t)nt * n));
+    NEP_TRY(w.get(&u, (size_t)n));
+    NEP_TRY(w.get(&Hm, (size_t)kmax * kmax));
+    NEP_TRY(w.get(&hv, (size_t)kmax + 1));
+    NEP_TRY(w.get(&tmp, (size_t)N));
+    NEP_TRY(w.get(&nr, 1));
+    NEP_TRY(w.get(&hlast, 1));
+    NEP_TRY(w.get(&part, part_elems));
+    NEP_CUDA(cudaMemcpyAsync(d_ec, &ec, sizeof(ec), cudaMemcpyHostToDevice, st));
+    NEP_CUDA(cudaMemcpyAsync(d_ddc, ddc.data(), sizeof(zd) * ddc.size(), cudaMemcpyHostToDevice, st));
+    NEP_CUDA(cudaMemcpyAsync(d_F, Fs.data(), sizeof(zd) * nt, cudaMemcpyHostToDevice, st));
+    NEP_CUDA(cudaMemsetAsync(Hm, 0, sizeof(zd) * (size_t)kmax * kmax, st));
+    // R_d(shift): assembled and factored once, FP64
+    NEP_TRY(launch_assemble<double>(s, 1, d_F, ab, nullptr, nullptr, st));
+    NEP_TRY(launch_band_lu<double>(s, 1, ab, ipiv, info, nullptr, st));
+    if (ut) NEP_TRY(band_transpose_u<double>(s, 1, ab, ut, st));
+    // start vector, unit 2-norm
+    NEP_CUDA(cudaMemcpyAsync(V, start_host, sizeof(zd) * (size_t)N, cudaMemcpyHostToDevice, st));
+    NEP_TRY(zgemm(1, 1, (int)N, 1, V, (int)N, V, (int)N, nr, 1, part, part_elems, st));
+    nleigs_normalize_start_kernel<<<ceil_div(N, 256), 256, 0, st>>>(N, V, nr);
+    NEP_CHECK_LAUNCH();
+    for (int k = 0; k < kmax; ++k) {
+        const zd* vk = V + (int64_t)k * N;
+        zd* wk = V + (int64_t)(k + 1) * N;
+        nleigs_expand_kernel<<<ceil_div(n, 128), 128, 0, st>>>(n, d, nt, vk, wk, C, d_ec, d_ddc);
+        NEP_CHECK_LAUNCH();
+        nleigs_spmv_kernel<<<ceil_div((int64_t)n * 32, 256), 256, 0, st>>>(s, C, u);
+        NEP_CHECK_LAUNCH();
+        NEP_TRY(launch_band_solve<double>(s, 1, ab, ut, ipiv, 1, u, nullptr, st));
+        nleigs_combine_kernel<<<ceil_div(N, 256), 256, 0, st>>>(n, d, u, wk, d_ec);
+        NEP_CHECK_LAUNCH();
+        zd* Hcol = Hm + (int64_t)kmax * k;
+        for (int pass = 0; pass < 2; ++pass) {
+            NEP_TRY(zgemm(k + 1, 1, (int)N, 1, V, (int)N, wk, (int)N, hv, k + 1, part, part_elems, st));
+            NEP_TRY(zgemm((int)N, 1, k + 1, 0, V, (int)N, hv, k + 1, tmp, (int)N, nullptr, 0, st));
+            nleigs_gs_update_kernel<<<ceil_div(N, 256), 256, 0, st>>>(N, k + 1, wk, tmp, hv, Hcol);
+            NEP_CHECK_LAUNCH();
+        }
+        NEP_TRY(zgemm(1, 1, (int)N, 1, wk, (int)N, wk, (int)N, nr, 1, part, part_elems, st));
+        nleigs_scale_kernel<<<ceil_div(N, 256), 256, 0, st>>>(N, wk, nr, k + 1 < kmax ? Hcol + k + 1 : hlast);
+        NEP_CHECK_LAUNCH();
+    }
+    // Ritz pairs of the kmax x kmax Hessenberg matrix
+    const int m = kmax;
+    zd *theta = nullptr, *S = nullptr, *lam = nullptr, *X = nullptr, *G = nullptr;
+    double* eta = nullptr;
+    int *status = nullptr, *ok = nullptr, *order = nullptr;
+    zd* gbuf = nullptr;
+    NEP_TRY(w.get(&theta, m));
+    NEP_TRY(w.get(&S, (size_t)m * m));
+    NEP_TRY(w.get(&lam, m));
+    NEP_TRY(w.get(&X, (size_t)n * m));
+    NEP_TRY(w.get(&G, (size_t)m * m));
+    NEP_TRY(w.get(&eta, m));
+    NEP_TRY(w.get(&status, 1));
+    NEP_TRY(w.get(&ok, m));
+    NEP_TRY(w.get(&order, m + 1));
+    NEP_TRY(w.get(&gbuf, (size_t)2 * m * (m + 1) + m));
+    NEP_TRY(small_eig<double>(m, Hm, theta, S, status, gbuf, st));
+    nleigs_ritz_kernel<<<ceil_div(m, 128), 128, 0, st>>>(m, theta, shift, lam, ok);
+    NEP_CHECK_LAUNCH();
+    NEP_TRY(zgemm(n, m, m, 0, V, (int)N, S, m, X, n, nullptr, 0, st));
+    NEP_TRY(launch_normalize_columns(n, m, X, 1, nullptr, st));
+    NEP_TRY(launch_eta(s, m, lam, X, eta, st));
+    NEP_TRY(zgemm(m, m, n, 1, X, n, X, n, G, m, nullptr, 0, st));
+    NEP_TRY(launch_select(m, lam, eta, ok, G, c, ea, eb, eig_tol, order, st));
+    std::vector<int> ord(m + 1);
+    std::vector<zd> lh(m);
+    std::vector<double> eh(m);
+    NEP_CUDA(cudaMemcpyAsync(ord.data(), order, sizeof(int) * (m + 1), cudaMemcpyDeviceToHost, st));
+    NEP_CUDA(cudaMemcpyAsync(lh.data(), lam, sizeof(zd) * m, cudaMemcpyDeviceToHost, st));
+    NEP_CUDA(cudaMemcpyAsync(eh.data(), eta, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+    NEP_CUDA(cudaStreamSynchronize(st));
+    const int nc = std::max(0, std::min(ord[0], m));
+    res->lam.clear();
+    res->eta.clear();
+    res->X.assign((size_t)n * nc, mk(0.0, 0.0));
+    for (int q = 0; q < nc; ++q) {
+        const int i = ord[1 + q];
+        res->lam.push_back(lh[i]);
+        res->eta.push_back(eh[i]);
+        NEP_CUDA(cudaMemcpyAsync(res->X.data() + (size_t)n * q, X + (size_t)n * i, sizeof(zd) * n,
+                                 cudaMemcpyDeviceToHost, st));
+    }
+    // all Ritz values (diagnostics)
+    res->ritz.assign(lh.begin(), lh.end());
+    NEP_CUDA(cudaStreamSynchronize(st));
+    int info_h = 0;
+    NEP_CUDA(cudaMemcpy(&info_h, info, sizeof(int), cudaMemcpyDeviceToHost));
+    res->lu_info = info_h;
+    res->steps = kmax;
+    return NEP_OK;
+}
+
+}  // namespace nep

@@ -1,0 +1,128 @@
+"""NLEIGS, static variant, through the C ABI (nep_nleigs_interpolation, nep_nleigs_solve;
+Sec. 4.5) against the oracle and closed forms.
+
+  * the interpolation: the library's divided differences (interpolation recurrence) equal the
+    oracle's matrix-function divided differences for the library's own nodes, poles and
+    scalings; those satisfy the Leja-Bagby conditions and max |b_j| = 1 on the boundary; the
+    degree is the oracle's;
+  * the eigenvalues: Lambert W (decoupled delay), companion roots (decoupled Drude), quadratic
+    roots (decoupled square root), a linear pencil's generalized eigenvalues, and the oracle's
+    linearisation eigenvalues of a coupled delay problem;
+  * refusals: too many terms, a branch cut inside the region, bad options.
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+
+import synth
+from oracle import ciss, contour, fn, nleigs
+from tests.gpu_util import match_eigenvalues, torch_cuda
+from tests.test_oracle_pins import drude_reference, lambert_reference, sqrt_reference
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bnd():
+    from paper_1910_11712_gb300 import binding
+    binding.load(build_if_missing=True)
+    return binding
+
+
+PROBLEMS = {
+    "delay": lambda: synth.diagonal_delay(n=8, seed=0),
+    "drude": lambda: synth.diagonal_drude(n=6, seed=0),
+    "sqrt": lambda: synth.diagonal_sqrt(n=6, seed=0),
+    "linear": lambda: synth.dense_linear_small(n=8, seed=3),
+}
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_interpolation_matches_the_oracle(bnd, name):
+    torch_cuda()
+    p = PROBLEMS[name]()
+    split = bnd.Split.from_problem(p)
+    it = bnd.nleigs_interpolation(split, p.region)
+    ora = nleigs.interpolation(p.fns, p.region)
+    assert it["converged"]
+    assert it["d"] == ora["d"], (it["d"], ora["d"])
+    assert it["nsing"] == len(ora["Xi"])
+    d = it["d"]
+    sig, xi, beta = it["sigma"], it["xi"].copy(), it["beta"]
+    xi[~np.isfinite(xi)] = np.inf
+    # nodes on the boundary, scalings max |b_j| = 1 there
+    bndry = nleigs.boundary(p.region)
+    assert all(np.abs(bndry - s).min() <= 1e-12 for s in sig)
+    b = nleigs.basis(bndry, sig, xi, beta, d)
+    assert np.allclose(np.abs(b).max(axis=1), 1.0, rtol=1e-13)
+    # divided differences: recurrence (library) vs matrix functions (oracle) for the same nodes
+    ref = nleigs.divided_differences(p.fns, sig, xi, beta, d)
+    assert np.abs(it["dd"] - ref).max() <= 1e-11 * np.abs(ref[:, 0]).max()
+    # the interpolant reproduces the f_i on the boundary
+    r = it["dd"] @ b
+    f = np.array([fn.values(g, bndry) for g in p.fns])
+    assert np.abs(r - f).max() <= 1e-11 * np.abs(f).max()
+
+
+def _solve(bnd, p, **kw):
+    split = bnd.Split.from_problem(p)
+    it = bnd.nleigs_interpolation(split, p.region)
+    kw.setdefault("krylov", min(120, it["d"] * p.n))
+    return bnd.nleigs_solve(split, p.region, **kw)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_delay_eigenvalues_are_lambert_w(bnd, seed):
+    torch_cuda()
+    p = synth.diagonal_delay(n=8, seed=seed)
+    r = _solve(bnd, p)
+    ref = lambert_reference(p)
+    err, _ = match_eigenvalues(r["lam"], ref)
+    assert err <= 1e-11, err
+    assert r["eta"].max() <= 1e-12
+
+
+def test_drude_sqrt_and_linear_closed_forms(bnd):
+    torch_cuda()
+    p = synth.diagonal_drude(n=6, seed=0)
+    err, _ = match_eigenvalues(_solve(bnd, p)["lam"], drude_reference(p))
+    assert err <= 1e-10, err
+    p = synth.diagonal_sqrt(n=6, seed=0)
+    err, _ = match_eigenvalues(_solve(bnd, p)["lam"], sqrt_reference(p))
+    assert err <= 1e-10, err
+    p = synth.dense_linear_small(n=8, seed=3)
+    A, B = p.mats[0].toarray(), p.mats[1].toarray()
+    ref = [e for e in scipy.linalg.eig(A, B, right=False) if contour.inside(p.region, e)]
+    err, _ = match_eigenvalues(_solve(bnd, p)["lam"], ref)
+    assert err <= 1e-10, err
+
+
+def test_coupled_delay_problem_matches_the_oracle_linearisation(bnd):
+    torch_cuda()
+    p = synth.delay_2d(s=5, seed=1)
+    ora = nleigs.solve(p)
+    assert len(ora["lam"]) >= 3
+    r = _solve(bnd, p, krylov=150)
+    err, pairs = match_eigenvalues(r["lam"], ora["lam"])
+    assert err <= 1e-10, err
+    for i, j in pairs:
+        assert abs(abs(np.vdot(r["X"][:, i], ora["X"][:, j])) - 1.0) <= 1e-9
+    # the returned pairs are eigenpairs of T itself (oracle residual)
+    norms = ciss.term_norms_inf(p.mats)
+    for q in range(len(r["lam"])):
+        assert ciss.scaled_residual(p.mats, p.fns, norms, r["lam"][q], r["X"][:, q]) <= 1e-11
+
+
+def test_refusals(bnd):
+    torch_cuda()
+    p = synth.diagonal_sqrt(n=6, seed=0)
+    split = bnd.Split.from_problem(p)
+    with pytest.raises(bnd.NepError) as e:  # the cut (-inf, 1] crosses this region
+        bnd.nleigs_solve(split, {"center": 1.0, "a": 1.0, "b": 1.0})
+    assert e.value.code == bnd.NEP_ERR_REGION
+    with pytest.raises(bnd.NepError) as e:
+        bnd.nleigs_solve(split, p.region, max_degree=64)
+    assert e.value.code == bnd.NEP_ERR_ARG
+    with pytest.raises(bnd.NepError) as e:
+        bnd.nleigs_solve(split, {"center": 4.0, "a": 0.0, "b": 1.0})
+    assert e.value.code == bnd.NEP_ERR_ARG

@@ -256,6 +256,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-symmetric", action="store_true")
     ap.add_argument("--no-polish", action="store_true")
+    ap.add_argument("--no-nleigs", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=40)
     ap.add_argument("--serving-smax", type=int, default=128)
     args = ap.parse_args()
@@ -442,6 +443,30 @@ def main():
         except binding.NepError as e:
             left_line = {"unavailable": str(e)}
 
+    # NLEIGS, static variant (Sec. 4.5) on the same problem and region: interpolation degree, one
+    # FP64 band LU of R_d(sigma), then one band solve and two Gram-Schmidt passes per Arnoldi step
+    nleigs_line = None
+    if not args.no_nleigs:
+        try:
+            res_c = plan.result()
+            kry = 150
+            binding.nleigs_solve(split, p.region, krylov=kry, stream=stream)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rn = binding.nleigs_solve(split, p.region, krylov=kry, stream=stream)
+            torch.cuda.synchronize()
+            ms_n = 1e3 * (time.perf_counter() - t0)
+            matched = 0
+            for lam in rn["lam"]:
+                if len(res_c["lam"]) and np.abs(res_c["lam"] - lam).min() <= 1e-8 * max(1.0, abs(lam)):
+                    matched += 1
+            nleigs_line = {"degree": rn["degree"], "krylov": kry, "ms": ms_n, "pairs": int(len(rn["lam"])),
+                           "max_eta": float(rn["eta"].max()) if len(rn["eta"]) else None,
+                           "pairs_matching_contour": matched, "contour_pairs": int(len(res_c["lam"])),
+                           "timing": "host clock around the synchronous call (FP64 throughout)"}
+        except binding.NepError as e:
+            nleigs_line = {"unavailable": str(e)}
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -513,6 +538,8 @@ def main():
             line["polish"] = polish
         if left_line:
             line["left"] = left_line
+        if nleigs_line:
+            line["nleigs"] = nleigs_line
         if not args.no_serving:
             line["serving"] = serving_bench(binding, prec, args.serving_requests, 0, 4, args.serving_smax)
         if not args.no_cpu:

@@ -258,7 +258,7 @@ typedef struct {
     double tol;          /* degree test max_i |d_i^d| < tol max_i |d_i^0|; default 1e-13        */
     int32_t max_degree;  /* largest degree d; default 60, at most 63                             */
     int32_t nboundary;   /* points discretising the boundary of the region; default 1024         */
-    int32_t krylov;      /* Arnoldi steps (no restart); default 100                               */
+    int32_t krylov;      /* Arnoldi steps (no restart); default 100, at most 512                 */
     int32_t has_shift;   /* nonzero: use shift_re/im as the shift sigma, else the region centre  */
     double shift_re, shift_im;
     uint64_t seed;       /* seeded start vector (SplitMix64 + Box-Muller)                         */
@@ -288,9 +288,10 @@ int nep_nleigs_interpolation(nep_split_t h, const nep_region *r, const nep_nleig
 /* NLEIGS, static variant with a full basis (Sec. 4.5.2, 4.5.3 "full basis"): shift-and-invert
  * Arnoldi with o->krylov steps on S = (A - sigma B)^{-1} B for the linearisation (A, B) of
  * Eq. (nleigsmatlin), applied through the block recurrences of Eqs. (nleigstoarreca) and
- * (nleigstoarrecb) with one band LU of R_d(sigma) (FP64) and one band solve per step; classical
- * Gram-Schmidt twice. Ritz values theta give lambda = sigma + 1/theta and x the first block of the
- * Ritz vector; pairs inside the region with FP64 eta (Sec. 2 Eq. (sressplit), of the full T) at most
+ * (nleigstoarrecb) with one band LU of R_d(sigma) (complex64 factors) and per step one band solve
+ * with two corrections against the FP64 residual of R_d(sigma); classical Gram-Schmidt twice. Ritz values theta (complex64 Hessenberg QR, then FP64 inverse iteration on
+ * the Hessenberg matrix and a Rayleigh quotient) give lambda = sigma + 1/theta and x the first block
+ * of the Ritz vector; pairs inside the region with FP64 eta (Sec. 2 Eq. (sressplit), of the full T) at most
  * eig_tol are returned, deduplicated and sorted as nep_ciss_solve does. *out receives a result
  * object (nep_result_get; hankel_rank there is 0); *degree (or NULL) the interpolation degree.
  * Needs nterms <= 8. The call allocates its work arrays on the stream ((d n) x (krylov+1)

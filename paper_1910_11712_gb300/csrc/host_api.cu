@@ -1085,8 +1085,8 @@ static int nleigs_params(nep_split_t h, const nep_region* r, const nep_nleigs_op
     q->shift = o->has_shift ? mk(o->shift_re, o->shift_im) : mk(r->center_re, r->center_im);
     q->seed = o->seed;
     q->eig_tol = o->eig_tol > 0 ? o->eig_tol : 1e-8;
-    if (q->dmax > 63 || q->nb < 8 || q->nb > (1 << 20) || q->kmax > 2048) {
-        set_error("nleigs: max_degree <= 63, 8 <= nboundary <= 2^20, krylov <= 2048");
+    if (q->dmax > 63 || q->nb < 8 || q->nb > (1 << 20) || q->kmax > 512) {
+        set_error("nleigs: max_degree <= 63, 8 <= nboundary <= 2^20, krylov <= 512");
         return NEP_ERR_ARG;
     }
     for (int i = 0; i < h->nterms; ++i) {

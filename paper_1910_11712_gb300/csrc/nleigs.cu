@@ -17,10 +17,11 @@
 //     1..d-1 with p^{d-1} = 0, p^{j-1} = (z^j - beta_j (1 - sigma/xi_j) p^j) / (sigma_{j-1} - sigma),
 //     and the per-term combinations c_i = sum_{j<=d-2} d_i^j p^j + d_i^d / beta_d v^{d-1}, one
 //     thread per row (nleigs_expand_kernel);
-//   * u = R_d(sigma)^{-1} (-sum_i A_i c_i): the split SpMV and the band LU of R_d(sigma)
-//     (= sum_i (sum_j b_j(sigma) d_i^j) A_i, factored once) with the substitution sweeps;
+//   * u = R_d(sigma)^{-1} (-sum_i A_i c_i): the split SpMV, then the band LU of R_d(sigma)
+//     (= sum_i (sum_j b_j(sigma) d_i^j) A_i, factored once in complex64) with the substitution
+//     sweeps and two corrections against the FP64 residual of R_d(sigma);
 //   * w^j = p^j + b_j(sigma) u (the null space of the lower block rows is b(sigma) (x) C^n);
-//   * classical Gram-Schmidt, twice, against the basis on the path's FP64 GEMM.
+//   * classical Gram-Schmidt, twice, against the basis (FP64 dot and update kernels).
 // The Ritz pairs of the Hessenberg matrix give lambda = sigma + 1/theta with x the first block of
 // the Ritz vector; the pairs inside Sigma are accepted by the FP64 scaled residual of the full
 // T (not of R_d) like the contour method's.
@@ -242,6 +243,7 @@ int nleigs_interpolation(const std::vector<FnNode>& nodes, const std::vector<zd>
 
 // ------------------------------------------------------------------ device kernels
 constexpr int kNleigsMaxTerms = 8;
+constexpr int kNleigsRefine = 2;  // FP64-residual corrections per solve of R_d(sigma)
 
 struct ExpandCoef {
     zd inv_ds[64];  // 1 / (sigma_{j-1} - shift), j = 1 .. d-1
@@ -312,14 +314,6 @@ __global__ void nleigs_combine_kernel(int n, int d, const zd* __restrict__ u, zd
     W[t] = fma_(W[t], ec->bsig[j], u[r]);
 }
 
-// w -= u; Hcol[0..k] += hv
-__global__ void nleigs_gs_update_kernel(int64_t N, int k1, zd* __restrict__ w, const zd* __restrict__ u,
-                                        const zd* __restrict__ hv, zd* __restrict__ Hcol) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < N) w[t] = w[t] - u[t];
-    if (t < k1) Hcol[t] = Hcol[t] + hv[t];
-}
-
 // h = sqrt(Re nr); H sub-diagonal entry (or hlast) = h; w /= h (w = 0 after a breakdown)
 __global__ void nleigs_scale_kernel(int64_t N, zd* __restrict__ w, const zd* __restrict__ nr, zd* __restrict__ hsub) {
     const double h = sqrt(fmax(nr->re, 0.0));
@@ -327,6 +321,101 @@ __global__ void nleigs_scale_kernel(int64_t N, zd* __restrict__ w, const zd* __r
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < N) w[t] = sc * w[t];
     if (t == 0) *hsub = mk(h, 0.0);
+}
+
+// Ritz vector of theta_e (one warp per Ritz value, FP64): the upper Hessenberg H - theta I is
+// factored with adjacent-row pivoting (an exactly zero pivot stands for eps |H|), three steps of
+// inverse iteration from a constant vector follow, and theta becomes the Rayleigh quotient
+// s^H H s of the unit vector s. theta comes from the complex64 Hessenberg QR: inverse iteration
+// with that shift converges to the FP64 eigenvector at the rate |theta - theta_e| / gap.
+__global__ void __launch_bounds__(32) nleigs_ritz_vectors_kernel(int m, const zd* __restrict__ H,
+                                                                 zd* __restrict__ theta, zd* __restrict__ S,
+                                                                 zd* __restrict__ work, int* __restrict__ pivw) {
+    extern __shared__ zd y[];  // m
+    const int e = blockIdx.x, lane = threadIdx.x;
+    zd* A = work + (int64_t)e * m * m;
+    int* pv = pivw + (int64_t)e * m;
+    const zd th = theta[e];
+    double anorm = 0.0;
+    for (int64_t t = lane; t < (int64_t)m * m; t += 32) {
+        const int i = (int)(t % m), j = (int)(t / m);
+        zd a = i <= j + 1 ? H[t] : mk(0.0, 0.0);
+        if (i == j) a = a - th;
+        A[t] = a;
+        anorm = fmax(anorm, abs1(a));
+    }
+    for (int o = 16; o > 0; o >>= 1) anorm = fmax(anorm, __shfl_xor_sync(0xffffffffu, anorm, o));
+    const double tiny = 1.2e-16 * (anorm > 0.0 ? anorm : 1.0);
+    __syncwarp();
+    // Hessenberg LU: at column k only rows k and k+1 hold entries on or below the diagonal
+    for (int k = 0; k + 1 < m; ++k) {
+        const zd a0 = A[k + (int64_t)m * k], a1 = A[k + 1 + (int64_t)m * k];
+        const bool sw = abs1(a1) > abs1(a0);
+        __syncwarp();
+        if (sw)
+            for (int j = k + lane; j < m; j += 32) {
+                const zd t = A[k + (int64_t)m * j];
+                A[k + (int64_t)m * j] = A[k + 1 + (int64_t)m * j];
+                A[k + 1 + (int64_t)m * j] = t;
+            }
+        __syncwarp();
+        zd piv = A[k + (int64_t)m * k];
+        if (piv.re == 0.0 && piv.im == 0.0) piv = mk(tiny, 0.0);
+        const zd lm = cdiv(sw ? a0 : a1, piv);
+        for (int j = k + 1 + lane; j < m; j += 32) A[k + 1 + (int64_t)m * j] = fms(A[k + 1 + (int64_t)m * j], lm, A[k + (int64_t)m * j]);
+        __syncwarp();
+        if (lane == 0) {
+            A[k + (int64_t)m * k] = piv;
+            A[k + 1 + (int64_t)m * k] = lm;
+            pv[k] = sw;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        const zd d = A[(m - 1) + (int64_t)m * (m - 1)];
+        if (d.re == 0.0 && d.im == 0.0) A[(m - 1) + (int64_t)m * (m - 1)] = mk(tiny, 0.0);
+    }
+    const double inv_sqrt_m = 1.0 / sqrt((double)m);
+    for (int i = lane; i < m; i += 32) y[i] = mk(inv_sqrt_m, 0.0);
+    __syncwarp();
+    for (int it = 0; it < 3; ++it) {
+        if (lane == 0)  // forward: the interchanges and multipliers, in order
+            for (int k = 0; k + 1 < m; ++k) {
+                if (pv[k]) {
+                    const zd t = y[k];
+                    y[k] = y[k + 1];
+                    y[k + 1] = t;
+                }
+                y[k + 1] = fms(y[k + 1], A[k + 1 + (int64_t)m * k], y[k]);
+            }
+        __syncwarp();
+        for (int k = m - 1; k >= 0; --k) {  // backward with U, by columns
+            const zd yk = cdiv(y[k], A[k + (int64_t)m * k]);
+            __syncwarp();
+            if (lane == 0) y[k] = yk;
+            for (int i = lane; i < k; i += 32) y[i] = fms(y[i], A[i + (int64_t)m * k], yk);
+            __syncwarp();
+        }
+        double nn = 0.0;
+        for (int i = lane; i < m; i += 32) nn += norm2(y[i]);
+        for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+        const double sc = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+        for (int i = lane; i < m; i += 32) y[i] = sc * y[i];
+        __syncwarp();
+    }
+    // Rayleigh quotient s^H H s (H upper Hessenberg)
+    zd rq = mk(0.0, 0.0);
+    for (int i = lane; i < m; i += 32) {
+        zd hs = mk(0.0, 0.0);
+        for (int j = max(0, i - 1); j < m; ++j) hs = fma_(hs, H[i + (int64_t)m * j], y[j]);
+        rq = fmac(rq, y[i], hs);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        rq.re += __shfl_xor_sync(0xffffffffu, rq.re, o);
+        rq.im += __shfl_xor_sync(0xffffffffu, rq.im, o);
+    }
+    for (int i = lane; i < m; i += 32) S[i + (int64_t)m * e] = y[i];
+    if (lane == 0 && isfinite(rq.re) && isfinite(rq.im)) theta[e] = rq;
 }
 
 // lam = shift + 1/theta; ok = theta != 0 and finite
@@ -344,6 +433,53 @@ __global__ void nleigs_normalize_start_kernel(int64_t N, zd* __restrict__ w, con
     const double h = sqrt(fmax(nr->re, 0.0));
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < N) w[t] = (h > 0.0 ? 1.0 / h : 0.0) * w[t];
+}
+
+// part[c + nchunks j] = sum over rows of chunk c of conj(V[r + N j]) w[r]; grid (nchunks, K)
+__global__ void __launch_bounds__(256) nleigs_dots_kernel(int64_t N, int64_t chunk, const zd* __restrict__ V,
+                                                          const zd* __restrict__ w, zd* __restrict__ part) {
+    const int c = blockIdx.x, j = blockIdx.y;
+    const int64_t r0 = (int64_t)c * chunk, r1 = min(N, r0 + chunk);
+    const zd* v = V + (int64_t)j * N;
+    zd acc = mk(0.0, 0.0);
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) acc = fmac(acc, v[r], w[r]);
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+        acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+    }
+    __shared__ zd red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        zd t = mk(0.0, 0.0);
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t = t + red[q];
+        part[c + (int64_t)gridDim.x * j] = t;
+    }
+}
+
+// h[j] = sum_c part[c + nchunks j] (fixed order)
+__global__ void nleigs_dots_reduce_kernel(int nchunks, int K, const zd* __restrict__ part, zd* __restrict__ h) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= K) return;
+    zd t = mk(0.0, 0.0);
+    for (int c = 0; c < nchunks; ++c) t = t + part[c + (int64_t)nchunks * j];
+    h[j] = t;
+}
+
+// w[r] -= sum_{j<K} V[r + N j] h[j]; Hcol[j] += h[j] (block 0)
+__global__ void __launch_bounds__(256) nleigs_sub_kernel(int64_t N, int K, const zd* __restrict__ V,
+                                                         const zd* __restrict__ h, zd* __restrict__ w,
+                                                         zd* __restrict__ Hcol) {
+    extern __shared__ zd hs[];
+    for (int j = threadIdx.x; j < K; j += blockDim.x) hs[j] = h[j];
+    __syncthreads();
+    if (blockIdx.x == 0 && Hcol)
+        for (int j = threadIdx.x; j < K; j += blockDim.x) Hcol[j] = Hcol[j] + hs[j];
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    zd acc = w[r];
+    for (int j = 0; j < K; ++j) acc = fms(acc, V[r + (int64_t)j * N], hs[j]);
+    w[r] = acc;
 }
 
 namespace {
@@ -397,38 +533,68 @@ int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, co
     }
     // device arrays
     ExpandCoef* d_ec = nullptr;
-    zd *d_ddc = nullptr, *d_F = nullptr, *ab = nullptr, *ut = nullptr, *V = nullptr, *C = nullptr, *u = nullptr;
-    zd *Hm = nullptr, *hv = nullptr, *tmp = nullptr, *nr = nullptr, *part = nullptr, *hlast = nullptr;
+    zd *d_ddc = nullptr, *d_F = nullptr, *tval = nullptr, *V = nullptr, *C = nullptr, *rhs = nullptr, *u = nullptr;
+    zd *res_r = nullptr, *Hm = nullptr, *hv = nullptr, *nr = nullptr, *part = nullptr, *hlast = nullptr;
+    zf *ab = nullptr, *ut = nullptr, *B32 = nullptr;
+    double *tnorm = nullptr, *dmax = nullptr, *ymax = nullptr;
     int *ipiv = nullptr, *info = nullptr;
     const int kv = s.kl + s.ku;
-    const size_t part_elems = (size_t)(kmax + 1) * 64;
+    const int64_t chunk = 4096;
+    const int nchunks = (int)((N + chunk - 1) / chunk);
     NEP_TRY(w.get(&d_ec, 1));
     NEP_TRY(w.get(&d_ddc, (size_t)nt * (d + 1)));
     NEP_TRY(w.get(&d_F, (size_t)nt));
     NEP_TRY(w.get(&ab, (size_t)n * s.ldab));
+    NEP_TRY(w.get(&tval, (size_t)s.nnz));
+    NEP_TRY(w.get(&tnorm, 1));
     NEP_TRY(w.get(&ipiv, (size_t)n));
     NEP_TRY(w.get(&info, 1));
     if (band_sweeps_fit(s.kl, s.ku)) NEP_TRY(w.get(&ut, (size_t)n * (kv + 1)));
     NEP_TRY(w.get(&V, (size_t)N * (kmax + 1)));
     NEP_TRY(w.get(&C, (size_t)nt * n));
+    NEP_TRY(w.get(&rhs, (size_t)n));
     NEP_TRY(w.get(&u, (size_t)n));
+    NEP_TRY(w.get(&res_r, (size_t)n));
+    NEP_TRY(w.get(&B32, (size_t)n));
+    NEP_TRY(w.get(&dmax, 1));
+    NEP_TRY(w.get(&ymax, 1));
     NEP_TRY(w.get(&Hm, (size_t)kmax * kmax));
     NEP_TRY(w.get(&hv, (size_t)kmax + 1));
-    NEP_TRY(w.get(&tmp, (size_t)N));
     NEP_TRY(w.get(&nr, 1));
     NEP_TRY(w.get(&hlast, 1));
-    NEP_TRY(w.get(&part, part_elems));
+    NEP_TRY(w.get(&part, (size_t)nchunks * (kmax + 1)));
     NEP_CUDA(cudaMemcpyAsync(d_ec, &ec, sizeof(ec), cudaMemcpyHostToDevice, st));
     NEP_CUDA(cudaMemcpyAsync(d_ddc, ddc.data(), sizeof(zd) * ddc.size(), cudaMemcpyHostToDevice, st));
     NEP_CUDA(cudaMemcpyAsync(d_F, Fs.data(), sizeof(zd) * nt, cudaMemcpyHostToDevice, st));
     NEP_CUDA(cudaMemsetAsync(Hm, 0, sizeof(zd) * (size_t)kmax * kmax, st));
-    // R_d(shift): assembled and factored once, FP64
-    NEP_TRY(launch_assemble<double>(s, 1, d_F, ab, nullptr, nullptr, st));
-    NEP_TRY(launch_band_lu<double>(s, 1, ab, ipiv, info, nullptr, st));
-    if (ut) NEP_TRY(band_transpose_u<double>(s, 1, ab, ut, st));
+    // R_d(shift) factored once in complex64, its FP64 values kept for the refinement residual
+    NEP_TRY(launch_assemble<float>(s, 1, d_F, ab, tnorm, tval, st));
+    NEP_TRY(launch_band_lu<float>(s, 1, ab, ipiv, info, nullptr, st));
+    if (ut) NEP_TRY(band_transpose_u<float>(s, 1, ab, ut, st));
+    // ||x||^2 or x^H y over N entries into out (K = 1)
+    auto dots = [&](const zd* Vb, int K, const zd* x, zd* out) -> int {
+        nleigs_dots_kernel<<<dim3(nchunks, K), 256, 0, st>>>(N, chunk, Vb, x, part);
+        NEP_CHECK_LAUNCH();
+        nleigs_dots_reduce_kernel<<<ceil_div(K, 128), 128, 0, st>>>(nchunks, K, part, out);
+        NEP_CHECK_LAUNCH();
+        return NEP_OK;
+    };
+    // u = R_d(shift)^{-1} rhs: complex64 solve, then kNleigsRefine FP64-residual corrections
+    auto solve = [&]() -> int {
+        NEP_TRY(launch_convert_rhs<float>(1, n, 1, rhs, B32, st));
+        NEP_TRY(launch_band_solve<float>(s, 1, ab, ut, ipiv, 1, B32, nullptr, st));
+        NEP_TRY(launch_widen<float>(1, n, 1, B32, u, st));
+        for (int it2 = 0; it2 < kNleigsRefine; ++it2) {
+            NEP_TRY(launch_split_residual(s, 1, tval, 1, rhs, u, res_r, nullptr, nullptr, st));
+            NEP_TRY(launch_refine_prepare<float>(1, n, 1, res_r, B32, nullptr, st));
+            NEP_TRY(launch_band_solve<float>(s, 1, ab, ut, ipiv, 1, B32, nullptr, st));
+            NEP_TRY(launch_refine_update<float>(1, n, 1, B32, u, dmax, ymax, nullptr, st));
+        }
+        return NEP_OK;
+    };
     // start vector, unit 2-norm
     NEP_CUDA(cudaMemcpyAsync(V, start_host, sizeof(zd) * (size_t)N, cudaMemcpyHostToDevice, st));
-    NEP_TRY(zgemm(1, 1, (int)N, 1, V, (int)N, V, (int)N, nr, 1, part, part_elems, st));
+    NEP_TRY(dots(V, 1, V, nr));
     nleigs_normalize_start_kernel<<<ceil_div(N, 256), 256, 0, st>>>(N, V, nr);
     NEP_CHECK_LAUNCH();
     for (int k = 0; k < kmax; ++k) {
@@ -436,19 +602,18 @@ int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, co
         zd* wk = V + (int64_t)(k + 1) * N;
         nleigs_expand_kernel<<<ceil_div(n, 128), 128, 0, st>>>(n, d, nt, vk, wk, C, d_ec, d_ddc);
         NEP_CHECK_LAUNCH();
-        nleigs_spmv_kernel<<<ceil_div((int64_t)n * 32, 256), 256, 0, st>>>(s, C, u);
+        nleigs_spmv_kernel<<<ceil_div((int64_t)n * 32, 256), 256, 0, st>>>(s, C, rhs);
         NEP_CHECK_LAUNCH();
-        NEP_TRY(launch_band_solve<double>(s, 1, ab, ut, ipiv, 1, u, nullptr, st));
+        NEP_TRY(solve());
         nleigs_combine_kernel<<<ceil_div(N, 256), 256, 0, st>>>(n, d, u, wk, d_ec);
         NEP_CHECK_LAUNCH();
         zd* Hcol = Hm + (int64_t)kmax * k;
         for (int pass = 0; pass < 2; ++pass) {
-            NEP_TRY(zgemm(k + 1, 1, (int)N, 1, V, (int)N, wk, (int)N, hv, k + 1, part, part_elems, st));
-            NEP_TRY(zgemm((int)N, 1, k + 1, 0, V, (int)N, hv, k + 1, tmp, (int)N, nullptr, 0, st));
-            nleigs_gs_update_kernel<<<ceil_div(N, 256), 256, 0, st>>>(N, k + 1, wk, tmp, hv, Hcol);
+            NEP_TRY(dots(V, k + 1, wk, hv));
+            nleigs_sub_kernel<<<ceil_div(N, 256), 256, sizeof(zd) * (k + 1), st>>>(N, k + 1, V, hv, wk, Hcol);
             NEP_CHECK_LAUNCH();
         }
-        NEP_TRY(zgemm(1, 1, (int)N, 1, wk, (int)N, wk, (int)N, nr, 1, part, part_elems, st));
+        NEP_TRY(dots(wk, 1, wk, nr));
         nleigs_scale_kernel<<<ceil_div(N, 256), 256, 0, st>>>(N, wk, nr, k + 1 < kmax ? Hcol + k + 1 : hlast);
         NEP_CHECK_LAUNCH();
     }
@@ -457,7 +622,8 @@ int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, co
     zd *theta = nullptr, *S = nullptr, *lam = nullptr, *X = nullptr, *G = nullptr;
     double* eta = nullptr;
     int *status = nullptr, *ok = nullptr, *order = nullptr;
-    zd* gbuf = nullptr;
+    zd *gbuf = nullptr, *rwork = nullptr;
+    int* rpiv = nullptr;
     NEP_TRY(w.get(&theta, m));
     NEP_TRY(w.get(&S, (size_t)m * m));
     NEP_TRY(w.get(&lam, m));
@@ -467,8 +633,13 @@ int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, co
     NEP_TRY(w.get(&status, 1));
     NEP_TRY(w.get(&ok, m));
     NEP_TRY(w.get(&order, m + 1));
-    NEP_TRY(w.get(&gbuf, (size_t)2 * m * (m + 1) + m));
-    NEP_TRY(small_eig<double>(m, Hm, theta, S, status, gbuf, st));
+    NEP_TRY(w.get(&gbuf, (size_t)m * (m + 1) + m));  // complex64 elements fit twice over
+    NEP_TRY(w.get(&rwork, (size_t)m * m * m));
+    NEP_TRY(w.get(&rpiv, (size_t)m * m));
+    // Ritz values: complex64 Hessenberg QR, then FP64 inverse iteration and Rayleigh quotients
+    NEP_TRY(small_eig_fast<float>(m, Hm, theta, nullptr, status, gbuf, st));
+    nleigs_ritz_vectors_kernel<<<m, 32, sizeof(zd) * m, st>>>(m, Hm, theta, S, rwork, rpiv);
+    NEP_CHECK_LAUNCH();
     nleigs_ritz_kernel<<<ceil_div(m, 128), 128, 0, st>>>(m, theta, shift, lam, ok);
     NEP_CHECK_LAUNCH();
     NEP_TRY(zgemm(n, m, m, 0, V, (int)N, S, m, X, n, nullptr, 0, st));

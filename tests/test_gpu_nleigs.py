@@ -126,3 +126,23 @@ def test_refusals(bnd):
     with pytest.raises(bnd.NepError) as e:
         bnd.nleigs_solve(split, {"center": 4.0, "a": 0.0, "b": 1.0})
     assert e.value.code == bnd.NEP_ERR_ARG
+
+
+def test_full_size_delay_problem_agrees_with_the_contour_solver(bnd):
+    """n = 4096, bandwidth 64: no dense oracle at this size; every returned pair is checked by the
+    oracle's scaled residual on the host, and the eigenvalues against the contour solver's."""
+    torch = torch_cuda()
+    from tests.gpu_util import to_dev
+    p = synth.config_problem("delay2d_s64")
+    split = bnd.Split.from_problem(p)
+    plan = bnd.Plan(split, p.region, p.N, p.L, p.M, precision=0)
+    plan.execute(to_dev(np.asfortranarray(synth.random_probe_block(p.n, p.L, 0)), torch))
+    torch.cuda.synchronize()
+    rc = plan.result()
+    r = bnd.nleigs_solve(split, p.region, krylov=150)
+    assert len(rc["lam"]) >= 5 and len(r["lam"]) == len(rc["lam"]), (len(r["lam"]), len(rc["lam"]))
+    err, _ = match_eigenvalues(r["lam"], rc["lam"])
+    assert err <= 1e-9, err
+    norms = ciss.term_norms_inf(p.mats)
+    for q in range(len(r["lam"])):
+        assert ciss.scaled_residual(p.mats, p.fns, norms, r["lam"][q], r["X"][:, q]) <= 1e-11

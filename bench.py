@@ -246,7 +246,7 @@ def torch_sync():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=16)
+    ap.add_argument("--steps", type=int, default=24)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -257,7 +257,7 @@ def main():
     ap.add_argument("--no-symmetric", action="store_true")
     ap.add_argument("--no-polish", action="store_true")
     ap.add_argument("--no-nleigs", action="store_true")
-    ap.add_argument("--streams", type=int, default=4,
+    ap.add_argument("--streams", type=int, default=8,
                     help="concurrent pipelines in the timed region: one plan, stream and host thread each")
     ap.add_argument("--serving-requests", type=int, default=40)
     ap.add_argument("--serving-smax", type=int, default=128)

@@ -214,9 +214,11 @@ int nep_plan_polish(nep_plan_t p, double tol, int32_t max_it, int32_t *polished,
 
 /* ------------------------------------------------------------------ left eigenvectors, resolvent */
 /* Left eigenvectors y^* T(lambda) = 0 (Sec. 2 Eq. (nep-left): right eigenvectors of T(lambda)^*)
- * of P eigenpairs (lambda_p, x_p), requested through Sec. 3.2.5's interface. T(lambda_p) is
- * assembled and factored once by the band LU (complex64 factors for NEP_PREC_MIXED, complex128
- * for NEP_PREC_FP64); from y = x_p the first step is inverse iteration y <- T(lambda_p)^{-*} y,
+ * of P eigenpairs (lambda_p, x_p), requested through Sec. 3.2.5's interface. T(lambda_p)^* is
+ * assembled (as a band with the bandwidths swapped) and factored once by the band LU (complex64
+ * factors for NEP_PREC_MIXED, complex128 for NEP_PREC_FP64; an exactly zero pivot stands for a tiny
+ * one; should a result not be finite, all pairs are recomputed with the factors of T(lambda_p) and
+ * the conjugate-transpose solve); from y = x_p the first step is inverse iteration y <- T(lambda_p)^{-*} y,
  * later steps y <- y - T(lambda_p)^{-*} (T(lambda_p)^* y) with the residual in FP64, each
  * normalised to unit 2-norm. A pair stops when its left scaled residual
  *   eta_L = ||T(lambda)^* y||_2 / (sum_i |f_i(lambda)| ||A_i||_1 ||y||_2)

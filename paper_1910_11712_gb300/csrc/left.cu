@@ -2,6 +2,10 @@
 // both, and Sec. 4.5.4 applies the conjugate transpose of a factored operator with the same
 // factorisation), on the band LU of the path.
 //
+// Left eigenvectors factor T(lambda)^* itself (assembled from the split's column view with the
+// bandwidths swapped) and run the path's LU and substitution sweeps on it. The conjugate-transpose
+// solve below serves callers that must reuse the factors of T.
+//
 // Conjugate-transpose solve T^* w = b from the factors of T. The LU applies, at step c, the
 // interchange P_c of rows c and ipiv[c], then the elementary L_c = I + l_c e_c^T (l_c: the
 // stored multipliers of column c), so T = P_0 L_0 P_1 L_1 ... P_{n-1} L_{n-1} U and
@@ -231,6 +235,60 @@ template int launch_band_solve_adjoint<double>(const SplitDev&, int, const cx<do
                                                cx<double>*, const int*, cudaStream_t);
 
 // ------------------------------------------------------------------ left eigenvectors
+// Band storage of T(z_p)^* for P points (left eigenvectors are right eigenvectors of T^*,
+// Sec. 2): row r of T^* is the conjugate of column r of T, read through the split's column view;
+// T^* has lower bandwidth ku and upper bandwidth kl, so entry (r, c) goes to slot c - r + ku of a
+// row of ldab2 = 2 ku + kl + 1 slots. One warp per (point, row).
+template <typename T>
+__global__ void __launch_bounds__(256) assemble_adjoint_kernel(SplitDev s, int npts, const zd* __restrict__ F,
+                                                               cx<T>* __restrict__ ab, int ldab2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw >= (int64_t)npts * s.n) return;
+    const int j = (int)(gw / s.n), r = (int)(gw % s.n);
+    cx<T>* row = ab + ((int64_t)j * s.n + r) * ldab2;
+    for (int t = lane; t < ldab2; t += 32) row[t] = mk<T>(0, 0);
+    __syncwarp();
+    for (int64_t k = s.colptr[r] + lane; k < s.colptr[r + 1]; k += 32) {
+        const int64_t e = s.cidx[k];
+        zd v = mk(0.0, 0.0);
+        for (int i = 0; i < s.nterms; ++i)
+            v = fma_(v, F[i + (int64_t)s.nterms * j],
+                     mk(s.val[(int64_t)i * s.nnz + e], s.val_im ? s.val_im[(int64_t)i * s.nnz + e] : 0.0));
+        row[s.crow[k] - r + s.ku] = cvt<T>(conj(v));
+    }
+}
+
+// an exactly zero pivot of the factors stands for eps |U|_max of its point (the inverse-iteration
+// convention, eps of the factor precision): with a zero pivot the LU left that column's
+// multipliers at zero, so the factors become those of the matrix plus a tiny e_c e_c^T. One CTA
+// per point.
+template <typename T>
+__global__ void __launch_bounds__(256) fix_zero_pivots_kernel(int n, int ldab, int kv, cx<T>* __restrict__ ab_all) {
+    cx<T>* ab = ab_all + (int64_t)blockIdx.x * n * ldab;
+    __shared__ T part[8];
+    __shared__ T tiny;
+    T mx = T(0);
+    for (int64_t e = threadIdx.x; e < (int64_t)n * (kv + 1); e += blockDim.x) {
+        const int c = (int)(e / (kv + 1)), t = (int)(e % (kv + 1));
+        if (c + t < n) mx = fmax(mx, abs1(ab[(int64_t)c * ldab + t]));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T m = T(0);
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m = fmax(m, part[q]);
+        const T eps = sizeof(T) == 4 ? T(5.96e-8) : T(1.11e-16);
+        tiny = eps * (m > T(0) && isfinite(m) ? m : T(1));
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        cx<T>* d = ab + (int64_t)c * ldab;
+        if (d->re == T(0) && d->im == T(0)) *d = mk<T>(tiny, T(0));
+    }
+}
+
 // F[i + nterms p] = f_i(lam_p), Fd likewise with f_i'
 __global__ void left_coeffs_kernel(SplitDev s, int P, const zd* __restrict__ lam, zd* __restrict__ F,
                                    zd* __restrict__ Fd) {
@@ -259,7 +317,8 @@ __global__ void left_rhs_kernel(int64_t total, int n, const zd* __restrict__ src
     B[t] = cvt<T>(src[t]);
 }
 
-// y_p <- w (first step) or y_p - w, then unit 2-norm; one CTA per pair
+// y_p <- w (first step) or y_p - w, then unit 2-norm (scaled by the largest entry first: inverse
+// iteration at an eigenvalue makes w huge); one CTA per pair
 template <typename T>
 __global__ void __launch_bounds__(256) left_update_kernel(int n, int first, zd* __restrict__ Y,
                                                           const cx<T>* __restrict__ B,
@@ -270,19 +329,32 @@ __global__ void __launch_bounds__(256) left_update_kernel(int n, int first, zd* 
     const cx<T>* w = B + (int64_t)p * n;
     __shared__ double part[8];
     __shared__ double scale;
-    double ss = 0.0;
+    double mx = 0.0;
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
         const zd v = first ? cvt<double>(w[r]) : y[r] - cvt<double>(w[r]);
         y[r] = v;
-        ss += norm2(v);
+        mx = fmax(mx, abs1(v));
     }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t = fmax(t, part[q]);
+        scale = t > 0.0 && t <= 1.7e308 ? 1.0 / t : 0.0;
+    }
+    __syncthreads();
+    const double inv = scale;
+    double ss = 0.0;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) ss += norm2(inv * y[r]);
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    __syncthreads();
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = ss;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += part[q];
-        scale = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+        scale = t > 0.0 ? inv / sqrt(t) : 0.0;
     }
     __syncthreads();
     for (int r = threadIdx.x; r < n; r += blockDim.x) y[r] = scale * y[r];
@@ -311,14 +383,18 @@ __global__ void left_apply_kernel(SplitDev s, int P, const zd* __restrict__ F, c
 
 // eta_L of pair p (Sec. 2 Eq. (sressplit) for T^*, whose terms have ||A_i^*||_inf = ||A_i||_1).
 // The pair stops once eta_L < tol, or when a correction step gained less than a factor 2 (the
-// floor that the eigenvalue's own error sets). One CTA per pair.
+// floor that the eigenvalue's own error sets). A correction step that did not lower eta_L is
+// undone (y <- Yprev): with factors exact to rounding, y - T^{-*} T^* y can cancel to nothing.
+// One CTA per pair.
 __global__ void __launch_bounds__(256) left_eta_kernel(SplitDev s, const zd* __restrict__ F,
-                                                       const zd* __restrict__ Y, const zd* __restrict__ R,
-                                                       double tol, int step, int last, double* __restrict__ eta,
-                                                       int* __restrict__ active, int* __restrict__ its) {
+                                                       zd* __restrict__ Y, const zd* __restrict__ Yprev,
+                                                       const zd* __restrict__ R, double tol, int step, int last,
+                                                       double* __restrict__ eta, int* __restrict__ active,
+                                                       int* __restrict__ its) {
     const int p = blockIdx.x;
     if (!active[p]) return;
     __shared__ double part[2][8];
+    __shared__ int restore;
     double rr = 0.0, yy = 0.0;
     for (int r = threadIdx.x; r < s.n; r += blockDim.x) {
         rr += norm2(R[(int64_t)p * s.n + r]);
@@ -342,10 +418,18 @@ __global__ void __launch_bounds__(256) left_eta_kernel(SplitDev s, const zd* __r
         for (int i = 0; i < s.nterms; ++i) den += cabs_(F[(int64_t)p * s.nterms + i]) * s.norms1[i];
         const double e = (den > 0.0 && b > 0.0) ? sqrt(a) / (den * sqrt(b)) : INFINITY;
         const double prev = eta[p];
-        eta[p] = e;
-        its[p] = step + 1;
-        if (!(e >= tol) || last || (step >= 1 && e > 0.5 * prev)) active[p] = 0;
+        restore = step >= 1 && !(e < prev);
+        if (restore) {
+            active[p] = 0;
+        } else {
+            eta[p] = e;
+            its[p] = step + 1;
+            if (!(e >= tol) || last || (step >= 1 && e > 0.5 * prev)) active[p] = 0;
+        }
     }
+    __syncthreads();
+    if (restore)
+        for (int r = threadIdx.x; r < s.n; r += blockDim.x) Y[(int64_t)p * s.n + r] = Yprev[(int64_t)p * s.n + r];
 }
 
 __global__ void left_count_kernel(int P, const int* __restrict__ active, int* __restrict__ out) {
@@ -412,31 +496,63 @@ struct LeftScratch {
 };
 }  // namespace
 
+// counts the pairs whose y or eta is not finite
+__global__ void left_nonfinite_kernel(int64_t total, int n, const zd* __restrict__ Y, const double* __restrict__ eta,
+                                      int* __restrict__ cnt) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const zd v = Y[t];
+    const bool bad = !isfinite(v.re) || !isfinite(v.im) || (t % n == 0 && isnan(eta[t / n]));
+    if (bad) atomicAdd(cnt, 1);
+}
+
+// One route of the left iteration. adjoint = false: T(lambda)^* assembled and factored itself,
+// solved by the path's substitution sweeps. adjoint = true: T(lambda) factored, solved with the
+// conjugate-transpose kernel (the order of the two triangular solves reversed): the fallback for
+// a pair whose null vector spans more orders of magnitude than the first route's back
+// substitution can hold in complex64 (its entries grow from the last row up).
 template <typename T>
-int left_eigvecs(const SplitDev& s, int P, const zd* lam, const zd* X, zd* Y, double* eta, int* its, double tol,
-                 int max_it, int* steps_host, cudaStream_t st) {
-    if (steps_host) *steps_host = 0;
-    if (P <= 0) return NEP_OK;
+static int left_route(const SplitDev& s, bool adjoint, int P, const zd* lam, const zd* X, zd* Y, double* eta, int* its,
+                      double tol, int max_it, int* steps_host, int* nonfinite, cudaStream_t st) {
     const int n = s.n, nt = s.nterms;
     LeftScratch w{{}, st};
-    zd *F = nullptr, *Fd = nullptr, *AX = nullptr, *R = nullptr;
-    cx<T>*ab = nullptr, *B = nullptr;
+    zd *F = nullptr, *Fd = nullptr, *AX = nullptr, *R = nullptr, *Yprev = nullptr;
+    cx<T>*ab = nullptr, *ut = nullptr, *B = nullptr;
+    // the factored band: T(lambda)^* (bandwidths swapped) or T(lambda)
+    SplitDev sh = s;
+    if (!adjoint) {
+        sh.kl = s.ku;
+        sh.ku = s.kl;
+        sh.ldab = 2 * sh.kl + sh.ku + 1;
+    }
     int *ipiv = nullptr, *info = nullptr, *active = nullptr, *cnt = nullptr;
     NEP_TRY(w.get(&F, (size_t)nt * P));
     NEP_TRY(w.get(&Fd, (size_t)nt * P));
-    NEP_TRY(w.get(&ab, (size_t)P * n * s.ldab));
+    NEP_TRY(w.get(&ab, (size_t)P * n * sh.ldab));
+    if (!adjoint && band_sweeps_fit(sh.kl, sh.ku)) NEP_TRY(w.get(&ut, (size_t)P * n * (sh.kl + sh.ku + 1)));
     NEP_TRY(w.get(&ipiv, (size_t)P * n));
     NEP_TRY(w.get(&info, (size_t)P));
     NEP_TRY(w.get(&B, (size_t)P * n));
     NEP_TRY(w.get(&R, (size_t)P * n));
+    NEP_TRY(w.get(&Yprev, (size_t)P * n));
     NEP_TRY(w.get(&AX, (size_t)nt * n * P));
     NEP_TRY(w.get(&active, (size_t)P));
     NEP_TRY(w.get(&cnt, 1));
     left_coeffs_kernel<<<ceil_div(P * nt, 128), 128, 0, st>>>(s, P, lam, F, Fd);
     NEP_CHECK_LAUNCH();
-    // T(lambda_p) factored once (an exactly zero pivot is taken care of by the solve)
-    NEP_TRY(launch_assemble<T>(s, P, F, ab, nullptr, nullptr, st));
-    NEP_TRY(launch_band_lu<T>(s, P, ab, ipiv, info, nullptr, st));
+    if (adjoint) {
+        // T(lambda_p) factored once; the conjugate-transpose kernel takes care of a zero pivot
+        NEP_TRY(launch_assemble<T>(s, P, F, ab, nullptr, nullptr, st));
+        NEP_TRY(launch_band_lu<T>(s, P, ab, ipiv, info, nullptr, st));
+    } else {
+        // T(lambda_p)^* factored once with the path's LU; the substitution sweeps then solve with it
+        assemble_adjoint_kernel<T><<<ceil_div((int64_t)P * n * 32, 256), 256, 0, st>>>(s, P, F, ab, sh.ldab);
+        NEP_CHECK_LAUNCH();
+        NEP_TRY(launch_band_lu<T>(sh, P, ab, ipiv, info, nullptr, st));
+        fix_zero_pivots_kernel<T><<<P, 256, 0, st>>>(n, sh.ldab, sh.kl + sh.ku, ab);
+        NEP_CHECK_LAUNCH();
+        if (ut) NEP_TRY(band_transpose_u<T>(sh, P, ab, ut, st));
+    }
     left_init_kernel<<<ceil_div(P, 128), 128, 0, st>>>(P, active, its, eta);
     NEP_CHECK_LAUNCH();
     NEP_CUDA(cudaMemcpyAsync(Y, X, sizeof(zd) * (size_t)n * P, cudaMemcpyDeviceToDevice, st));
@@ -449,12 +565,18 @@ int left_eigvecs(const SplitDev& s, int P, const zd* lam, const zd* X, zd* Y, do
         // residual in FP64, which removes the factors' rounding from y
         left_rhs_kernel<T><<<ceil_div(total, 256), 256, 0, st>>>(total, n, k == 0 ? Y : R, B, active);
         count_launch();
-        if ((rc = launch_band_solve_adjoint<T>(s, P, ab, ipiv, 1, B, active, st))) break;
+        if (k > 0 && cudaMemcpyAsync(Yprev, Y, sizeof(zd) * (size_t)total, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+            rc = NEP_ERR_CUDA;
+            break;
+        }
+        if ((rc = adjoint ? launch_band_solve_adjoint<T>(s, P, ab, ipiv, 1, B, active, st)
+                          : launch_band_solve<T>(sh, P, ab, ut, ipiv, 1, B, active, st)))
+            break;
         left_update_kernel<T><<<P, 256, 0, st>>>(n, k == 0, Y, B, active);
         count_launch();
         left_apply_kernel<<<ceil_div(total, 256), 256, 0, st>>>(s, P, F, Y, R, active);
         count_launch();
-        left_eta_kernel<<<P, 256, 0, st>>>(s, F, Y, R, tol, k, k == max_it - 1, eta, active, its);
+        left_eta_kernel<<<P, 256, 0, st>>>(s, F, Y, Yprev, R, tol, k, k == max_it - 1, eta, active, its);
         count_launch();
         left_count_kernel<<<1, 32, 0, st>>>(P, active, cnt);
         count_launch();
@@ -470,12 +592,37 @@ int left_eigvecs(const SplitDev& s, int P, const zd* lam, const zd* X, zd* Y, do
             break;
         }
     }
+    if (!rc) {
+        if (steps_host) *steps_host = std::min(k, max_it);
+        rc = launch_term_spmm(s, P, X, AX, st);
+    }
+    if (!rc) {
+        left_keldysh_kernel<<<P, 256, 0, st>>>(n, nt, P, Fd, AX, Y, eta);
+        count_launch();
+        if (cudaMemsetAsync(cnt, 0, sizeof(int), st) != cudaSuccess) rc = NEP_ERR_CUDA;
+    }
+    if (!rc) {
+        left_nonfinite_kernel<<<ceil_div(total, 256), 256, 0, st>>>(total, n, Y, eta, cnt);
+        count_launch();
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "left eigenvector kernels", __FILE__, __LINE__);
+    }
+    if (!rc && (cudaMemcpyAsync(host, cnt, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess))
+        rc = NEP_ERR_CUDA;
+    if (!rc) *nonfinite = *host;
     cudaFreeHost(host);
-    if (rc) return rc;
-    if (steps_host) *steps_host = std::min(k, max_it);
-    NEP_TRY(launch_term_spmm(s, P, X, AX, st));
-    left_keldysh_kernel<<<P, 256, 0, st>>>(n, nt, P, Fd, AX, Y, eta);
-    NEP_CHECK_LAUNCH();
+    return rc;
+}
+
+template <typename T>
+int left_eigvecs(const SplitDev& s, int P, const zd* lam, const zd* X, zd* Y, double* eta, int* its, double tol,
+                 int max_it, int* steps_host, cudaStream_t st) {
+    if (steps_host) *steps_host = 0;
+    if (P <= 0) return NEP_OK;
+    int bad = 0;
+    NEP_TRY(left_route<T>(s, false, P, lam, X, Y, eta, its, tol, max_it, steps_host, &bad, st));
+    if (bad) NEP_TRY(left_route<T>(s, true, P, lam, X, Y, eta, its, tol, max_it, steps_host, &bad, st));
     return NEP_OK;
 }
 template int left_eigvecs<float>(const SplitDev&, int, const zd*, const zd*, zd*, double*, int*, double, int, int*,

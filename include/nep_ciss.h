@@ -265,6 +265,10 @@ typedef struct {
     double shift_re, shift_im;
     uint64_t seed;       /* seeded start vector (SplitMix64 + Box-Muller)                         */
     double eig_tol;      /* acceptance: eta <= eig_tol and inside the region; default 1e-8        */
+    int32_t exact_solves; /* nonzero: each Arnoldi solve gets two FP64-residual corrections; zero  */
+                          /* (default): plain complex64 solves, then the Ritz pairs inside the     */
+                          /* region with eta <= 1e-4 are polished by nep_rii's iteration (FP64     */
+                          /* residuals, tol 1e-13, at most 10 iterations) before the acceptance    */
 } nep_nleigs_opts;
 /* The rational interpolant R_d(z) = sum_j b_j(z) D_j, D_j = sum_i d_i^j A_i, of Sec. 4.5.1 on the
  * region (host computation):
@@ -291,7 +295,8 @@ int nep_nleigs_interpolation(nep_split_t h, const nep_region *r, const nep_nleig
  * Arnoldi with o->krylov steps on S = (A - sigma B)^{-1} B for the linearisation (A, B) of
  * Eq. (nleigsmatlin), applied through the block recurrences of Eqs. (nleigstoarreca) and
  * (nleigstoarrecb) with one band LU of R_d(sigma) (complex64 factors) and per step one band solve
- * with two corrections against the FP64 residual of R_d(sigma); classical Gram-Schmidt twice. Ritz values theta (complex64 Hessenberg QR, then FP64 inverse iteration on
+ * (with two corrections against the FP64 residual of R_d(sigma) when o->exact_solves is set);
+ * classical Gram-Schmidt twice. Ritz values theta (complex64 Hessenberg QR, then FP64 inverse iteration on
  * the Hessenberg matrix and a Rayleigh quotient) give lambda = sigma + 1/theta and x the first block
  * of the Ritz vector; pairs inside the region with FP64 eta (Sec. 2 Eq. (sressplit), of the full T) at most
  * eig_tol are returned, deduplicated and sorted as nep_ciss_solve does. *out receives a result

@@ -312,12 +312,14 @@ struct NleigsInterp {
 struct NleigsOut {
     std::vector<zd> lam, X, ritz;
     std::vector<double> eta;
-    int steps = 0, lu_info = 0;
+    int steps = 0, lu_info = 0, polished = 0, polish_its = 0;
 };
 int nleigs_interpolation(const std::vector<FnNode>& nodes, const std::vector<zd>& pool, const std::vector<int>& roots,
                          zd c, double a, double b, double tol, int dmax, int nb, NleigsInterp* out);
+// exact: complex64 solves with two FP64-residual corrections; otherwise plain complex64 solves and
+// residual inverse iteration on the converged Ritz pairs inside the region
 int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, const double* start_host, zd c,
-               double ea, double eb, double eig_tol, NleigsOut* res, cudaStream_t st);
+               double ea, double eb, double eig_tol, bool exact, NleigsOut* res, cudaStream_t st);
 // out (n x nz*nv, column j*nv + k) = sum_i x_i (y_i^* v_k) / (z_j - lam_i)
 int apply_resolvent(int n, int P, const zd* lam, const zd* X, const zd* Y, int nz, const zd* z, int nv, const zd* V,
                     zd* out, cudaStream_t st);

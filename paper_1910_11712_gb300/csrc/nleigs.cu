@@ -243,7 +243,8 @@ int nleigs_interpolation(const std::vector<FnNode>& nodes, const std::vector<zd>
 
 // ------------------------------------------------------------------ device kernels
 constexpr int kNleigsMaxTerms = 8;
-constexpr int kNleigsRefine = 2;  // FP64-residual corrections per solve of R_d(sigma)
+constexpr double kNleigsCandidate = 1e-4;  // eta of a Ritz pair worth polishing (fast mode)
+constexpr int kNleigsRefine = 2;  // FP64-residual corrections per solve of R_d(sigma), exact mode
 
 struct ExpandCoef {
     zd inv_ds[64];  // 1 / (sigma_{j-1} - shift), j = 1 .. d-1
@@ -503,7 +504,8 @@ struct NlScratch {
 }  // namespace
 
 int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, const double* start_host, zd c,
-               double ea, double eb, double eig_tol, NleigsOut* res, cudaStream_t st) {
+               double ea, double eb, double eig_tol, bool exact, NleigsOut* res, cudaStream_t st) {
+    const int refine = exact ? kNleigsRefine : 0;
     const int n = s.n, nt = s.nterms, d = it.d;
     if (nt > kNleigsMaxTerms || d < 1 || d > 63 || kmax < 1) return NEP_ERR_ARG;
     const int64_t N = (int64_t)d * n;
@@ -584,7 +586,7 @@ int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, co
         NEP_TRY(launch_convert_rhs<float>(1, n, 1, rhs, B32, st));
         NEP_TRY(launch_band_solve<float>(s, 1, ab, ut, ipiv, 1, B32, nullptr, st));
         NEP_TRY(launch_widen<float>(1, n, 1, B32, u, st));
-        for (int it2 = 0; it2 < kNleigsRefine; ++it2) {
+        for (int it2 = 0; it2 < refine; ++it2) {
             NEP_TRY(launch_split_residual(s, 1, tval, 1, rhs, u, res_r, nullptr, nullptr, st));
             NEP_TRY(launch_refine_prepare<float>(1, n, 1, res_r, B32, nullptr, st));
             NEP_TRY(launch_band_solve<float>(s, 1, ab, ut, ipiv, 1, B32, nullptr, st));
@@ -645,6 +647,41 @@ int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, co
     NEP_TRY(zgemm(n, m, m, 0, V, (int)N, S, m, X, n, nullptr, 0, st));
     NEP_TRY(launch_normalize_columns(n, m, X, 1, nullptr, st));
     NEP_TRY(launch_eta(s, m, lam, X, eta, st));
+    if (!exact) {
+        // the Arnoldi ran on complex64 solves: Ritz pairs inside the region that converged to that
+        // level (eta <= kNleigsCandidate) are polished by residual inverse iteration (FP64
+        // residuals) to tol 1e-13 before the acceptance test
+        std::vector<zd> lc(m);
+        std::vector<double> ec(m);
+        std::vector<int> okc(m);
+        NEP_CUDA(cudaMemcpyAsync(lc.data(), lam, sizeof(zd) * m, cudaMemcpyDeviceToHost, st));
+        NEP_CUDA(cudaMemcpyAsync(ec.data(), eta, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+        NEP_CUDA(cudaMemcpyAsync(okc.data(), ok, sizeof(int) * m, cudaMemcpyDeviceToHost, st));
+        NEP_CUDA(cudaStreamSynchronize(st));
+        std::vector<int> idx;
+        for (int i = 0; i < m; ++i) {
+            const double dr = (lc[i].re - c.re) / ea, di = (lc[i].im - c.im) / eb;
+            if (okc[i] && dr * dr + di * di < 1.0 && ec[i] <= kNleigsCandidate) idx.push_back(i);
+        }
+        const int P = (int)idx.size();
+        if (P > 0) {
+            int *didx = nullptr, *pits = nullptr;
+            zd *plam = nullptr, *pX = nullptr;
+            double* peta = nullptr;
+            NEP_TRY(w.get(&didx, P));
+            NEP_TRY(w.get(&pits, P));
+            NEP_TRY(w.get(&plam, P));
+            NEP_TRY(w.get(&pX, (size_t)n * P));
+            NEP_TRY(w.get(&peta, P));
+            NEP_CUDA(cudaMemcpyAsync(didx, idx.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
+            NEP_TRY(launch_rii_move(n, P, didx, lam, X, eta, plam, pX, peta, 0, st));
+            int its_max = 0;
+            NEP_TRY(rii_polish<float>(s, P, plam, pX, peta, pits, 1e-13, 10, &its_max, st));
+            NEP_TRY(launch_rii_move(n, P, didx, lam, X, eta, plam, pX, peta, 1, st));
+            res->polished = P;
+            res->polish_its = its_max;
+        }
+    }
     NEP_TRY(zgemm(m, m, n, 1, X, n, X, n, G, m, nullptr, 0, st));
     NEP_TRY(launch_select(m, lam, eta, ok, G, c, ea, eb, eig_tol, order, st));
     std::vector<int> ord(m + 1);

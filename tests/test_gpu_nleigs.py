@@ -146,3 +146,14 @@ def test_full_size_delay_problem_agrees_with_the_contour_solver(bnd):
     norms = ciss.term_norms_inf(p.mats)
     for q in range(len(r["lam"])):
         assert ciss.scaled_residual(p.mats, p.fns, norms, r["lam"][q], r["X"][:, q]) <= 1e-11
+
+
+def test_exact_solve_mode_matches_the_oracle_linearisation(bnd):
+    """exact_solves = 1: each Arnoldi solve corrected against the FP64 residual, no polish."""
+    torch_cuda()
+    p = synth.delay_2d(s=5, seed=1)
+    ora = nleigs.solve(p)
+    r = _solve(bnd, p, krylov=150, exact_solves=1)
+    err, _ = match_eigenvalues(r["lam"], ora["lam"])
+    assert err <= 1e-10, err
+    assert r["eta"].max() <= 1e-11

@@ -474,27 +474,6 @@ __global__ void __launch_bounds__(256) left_keldysh_kernel(int n, int nt, int P,
     for (int r = threadIdx.x; r < n; r += blockDim.x) y[r] = scale * y[r];
 }
 
-namespace {
-// stream-ordered work arrays of one call, freed on every return path
-struct LeftScratch {
-    std::vector<void*> bufs;
-    cudaStream_t st;
-    ~LeftScratch() {
-        for (void* b : bufs) cudaFreeAsync(b, st);
-    }
-    template <typename U>
-    int get(U** out, size_t count) {
-        *out = nullptr;
-        if (count == 0) return NEP_OK;
-        void* p = nullptr;
-        const cudaError_t e = cudaMallocAsync(&p, sizeof(U) * count, st);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync", __FILE__, __LINE__);
-        bufs.push_back(p);
-        *out = static_cast<U*>(p);
-        return NEP_OK;
-    }
-};
-}  // namespace
 
 // counts the pairs whose y or eta is not finite
 __global__ void left_nonfinite_kernel(int64_t total, int n, const zd* __restrict__ Y, const double* __restrict__ eta,
@@ -515,7 +494,7 @@ template <typename T>
 static int left_route(const SplitDev& s, bool adjoint, int P, const zd* lam, const zd* X, zd* Y, double* eta, int* its,
                       double tol, int max_it, int* steps_host, int* nonfinite, cudaStream_t st) {
     const int n = s.n, nt = s.nterms;
-    LeftScratch w{{}, st};
+    StreamScratch w(st);
     zd *F = nullptr, *Fd = nullptr, *AX = nullptr, *R = nullptr, *Yprev = nullptr;
     cx<T>*ab = nullptr, *ut = nullptr, *B = nullptr;
     // the factored band: T(lambda)^* (bandwidths swapped) or T(lambda)
@@ -649,7 +628,7 @@ int apply_resolvent(int n, int P, const zd* lam, const zd* X, const zd* Y, int n
         NEP_CUDA(cudaMemsetAsync(out, 0, sizeof(zd) * (size_t)n * nz * nv, st));
         return NEP_OK;
     }
-    LeftScratch w{{}, st};
+    StreamScratch w(st);
     zd *D = nullptr, *Wt = nullptr, *part = nullptr;
     const size_t part_elems = (size_t)P * nv * std::min(64, std::max(1, n / 32));
     NEP_TRY(w.get(&D, (size_t)P * nv));

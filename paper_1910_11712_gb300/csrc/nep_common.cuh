@@ -301,6 +301,29 @@ int launch_band_solve_adjoint(const SplitDev& s, int npts, const cx<T>* ab, cons
 template <typename T>
 int left_eigvecs(const SplitDev& s, int P, const zd* lam, const zd* X, zd* Y, double* eta, int* its, double tol,
                  int max_it, int* steps_host, cudaStream_t st);
+// Stream-ordered work arrays of one call (cudaMallocAsync on st), freed in stream order on every
+// return path.
+struct StreamScratch {
+    std::vector<void*> bufs;
+    cudaStream_t st;
+    explicit StreamScratch(cudaStream_t s) : st(s) {}
+    StreamScratch(const StreamScratch&) = delete;
+    StreamScratch& operator=(const StreamScratch&) = delete;
+    ~StreamScratch() {
+        for (void* b : bufs) cudaFreeAsync(b, st);
+    }
+    template <typename U>
+    int get(U** out, size_t count) {
+        *out = nullptr;
+        void* p = nullptr;
+        const cudaError_t e = cudaMallocAsync(&p, sizeof(U) * (count ? count : 1), st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync", __FILE__, __LINE__);
+        bufs.push_back(p);
+        *out = static_cast<U*>(p);
+        return NEP_OK;
+    }
+};
+
 // nleigs.cu: rational interpolation on the region (host) and shift-and-invert Arnoldi on its
 // linearisation (device)
 struct NleigsInterp {

@@ -483,25 +483,6 @@ __global__ void __launch_bounds__(256) nleigs_sub_kernel(int64_t N, int K, const
     w[r] = acc;
 }
 
-namespace {
-struct NlScratch {
-    std::vector<void*> bufs;
-    cudaStream_t st;
-    ~NlScratch() {
-        for (void* b : bufs) cudaFreeAsync(b, st);
-    }
-    template <typename U>
-    int get(U** out, size_t count) {
-        *out = nullptr;
-        void* p = nullptr;
-        const cudaError_t e = cudaMallocAsync(&p, sizeof(U) * std::max<size_t>(count, 1), st);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync", __FILE__, __LINE__);
-        bufs.push_back(p);
-        *out = static_cast<U*>(p);
-        return NEP_OK;
-    }
-};
-}  // namespace
 
 int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, const double* start_host, zd c,
                double ea, double eb, double eig_tol, bool exact, NleigsOut* res, cudaStream_t st) {
@@ -509,7 +490,7 @@ int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, co
     const int n = s.n, nt = s.nterms, d = it.d;
     if (nt > kNleigsMaxTerms || d < 1 || d > 63 || kmax < 1) return NEP_ERR_ARG;
     const int64_t N = (int64_t)d * n;
-    NlScratch w{{}, st};
+    StreamScratch w(st);
     // host constants
     ExpandCoef ec{};
     std::vector<cd> sig, xi;

@@ -161,27 +161,6 @@ __global__ void rii_count_kernel(int P, const int* __restrict__ active, int* __r
     if (threadIdx.x == 0) *out = cnt;
 }
 
-namespace {
-// stream-ordered work arrays of one call, freed on every return path
-struct Scratch {
-    std::vector<void*> bufs;
-    cudaStream_t st;
-    ~Scratch() {
-        for (void* b : bufs) cudaFreeAsync(b, st);
-    }
-    template <typename U>
-    int get(U** out, size_t count) {
-        *out = nullptr;
-        if (count == 0) return NEP_OK;
-        void* p = nullptr;
-        const cudaError_t e = cudaMallocAsync(&p, sizeof(U) * count, st);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync", __FILE__, __LINE__);
-        bufs.push_back(p);
-        *out = static_cast<U*>(p);
-        return NEP_OK;
-    }
-};
-}  // namespace
 
 template <typename T>
 int rii_polish(const SplitDev& s, int P, zd* lam, zd* X, double* eta, int* its, double tol, int max_it,
@@ -189,7 +168,7 @@ int rii_polish(const SplitDev& s, int P, zd* lam, zd* X, double* eta, int* its, 
     if (max_its_host) *max_its_host = 0;
     if (P <= 0) return NEP_OK;
     const int n = s.n, nt = s.nterms, kv = s.kl + s.ku;
-    Scratch w{{}, st};
+    StreamScratch w(st);
     zd *F = nullptr, *Fk = nullptr, *AX = nullptr, *c = nullptr;
     const int nc = nt + 1;
     cx<T>*ab = nullptr, *ut = nullptr, *B = nullptr;

@@ -207,7 +207,7 @@ int launch_band_lu(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info,
     NEP_CUDA(cudaMallocAsync((void**)&win, win_bytes, st));
     const size_t smem = sizeof(cx<T>) * (size_t)(2 * (kv + 1) + (s.kl + 1) + (s.kl > 1 ? s.kl : 1) + CS);
     if (smem > 48 * 1024)
-        NEP_CUDA(cudaFuncSetAttribute(lu_glb_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        NEP_CUDA(allow_max_dynamic_smem(lu_glb_kernel<T>));
     lu_glb_kernel<T><<<npts, 1024, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, info, active, win);
     count_launch();
     cudaError_t e = cudaGetLastError();
@@ -430,7 +430,7 @@ int launch_band_solve(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>*
     while (CH > 1 && bytes(CH) > budget) CH >>= 1;
     const size_t smem = bytes(CH);
     if (smem > 227 * 1024) return NEP_ERR_UNSUPPORTED;
-    NEP_CUDA(cudaFuncSetAttribute(band_solve_kernel<T, RH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    NEP_CUDA(allow_max_dynamic_smem(band_solve_kernel<T, RH>));
     dim3 grid(npts, gy);
     band_solve_kernel<T, RH><<<grid, wpb * 32, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, L, B, active, CH);
     NEP_CHECK_LAUNCH();

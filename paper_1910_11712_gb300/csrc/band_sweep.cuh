@@ -240,8 +240,7 @@ static int run_sweep(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* 
     while (CH > RPL && bytes(CH) > 200 * 1024) CH -= RPL;
     const size_t smem = bytes(CH);
     if (smem > 227 * 1024) return NEP_ERR_UNSUPPORTED;
-    NEP_CUDA(cudaFuncSetAttribute(band_sweep_kernel<T, RPL, BWD, RH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+    NEP_CUDA(allow_max_dynamic_smem(band_sweep_kernel<T, RPL, BWD, RH>));
     band_sweep_kernel<T, RPL, BWD, RH><<<dim3(npts, gy), 2 * wpb * 32, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ut,
                                                                              ipiv, L, B, active, CH);
     NEP_CHECK_LAUNCH();

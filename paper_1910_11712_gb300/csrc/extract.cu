@@ -776,7 +776,7 @@ int launch_pchol(int m, const zd* G, double tol2, int* rank_out, zd* Z, zd* gwor
     const size_t bytes = sizeof(zd) * (size_t)m * m + sizeof(double) * m + sizeof(int) * m + 64;
     const int use_smem = bytes <= 200 * 1024;
     if (use_smem)
-        NEP_CUDA(cudaFuncSetAttribute(pchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        NEP_CUDA(allow_max_dynamic_smem(pchol_kernel));
     else if (!gwork)
         return NEP_ERR_INTERNAL;
     pchol_kernel<<<1, 256, use_smem ? bytes : 0, st>>>(m, G, tol2, rank_out, Z, gwork, use_smem);
@@ -969,7 +969,7 @@ int small_eig(int m, const zd* A, zd* eval, zd* evec, int* status, void* gbuf, c
     const size_t bytes = sizeof(cx<T>) * ((size_t)2 * m * (m + 1) + m);
     const int use_smem = bytes <= 200 * 1024;
     if (use_smem)
-        NEP_CUDA(cudaFuncSetAttribute(schur_eig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        NEP_CUDA(allow_max_dynamic_smem(schur_eig_kernel<T>));
     else if (!gbuf)
         return NEP_ERR_INTERNAL;
     schur_eig_kernel<T><<<1, 32, use_smem ? bytes : 0, st>>>(m, A, eval, evec, status, (cx<T>*)gbuf, use_smem);
@@ -1224,7 +1224,7 @@ int small_eig_fast(int m, const zd* A, zd* eval, zd* evec, int* status, void* gb
     if (m <= 0) return NEP_OK;
     const size_t b1 = sizeof(cx<T>) * ((size_t)m * (m + 1) + m);
     const int s1 = b1 <= 200 * 1024;
-    if (s1) NEP_CUDA(cudaFuncSetAttribute(hqr_eigvals_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1));
+    if (s1) NEP_CUDA(allow_max_dynamic_smem(hqr_eigvals_kernel<T>));
     else if (!gbuf) return NEP_ERR_INTERNAL;
     hqr_eigvals_kernel<T><<<1, 32, s1 ? b1 : 0, st>>>(m, A, eval, status, (cx<T>*)gbuf, s1);
     NEP_CHECK_LAUNCH();
@@ -1232,7 +1232,7 @@ int small_eig_fast(int m, const zd* A, zd* eval, zd* evec, int* status, void* gb
     const size_t b2 = sizeof(cx<T>) * ((size_t)m * (m + 1) + m) + sizeof(int) * m + 16;
     const int s2 = b2 <= 200 * 1024;
     if (s2)
-        NEP_CUDA(cudaFuncSetAttribute(inverse_iteration_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2));
+        NEP_CUDA(allow_max_dynamic_smem(inverse_iteration_kernel<T>));
     else if (!gbuf) return NEP_ERR_INTERNAL;
     inverse_iteration_kernel<T><<<m, 32, s2 ? b2 : 0, st>>>(m, A, eval, evec, (cx<T>*)gbuf, s2);
     NEP_CHECK_LAUNCH();
@@ -1652,7 +1652,7 @@ int launch_newton(const SplitDev& s, int k, int ncand, const zd* Bs, zf* Bs32, c
     const int use_smem = bytes <= 200 * 1024;
     if (!use_smem && !gscratch) return NEP_ERR_INTERNAL;
     auto run = [&](auto kern) -> int {
-        if (use_smem) NEP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        if (use_smem) NEP_CUDA(allow_max_dynamic_smem(kern));
         kern<<<ncand, 256, use_smem ? bytes : 0, st>>>(s, k, Bs, Bs32, lam0, Y0, ldy0, c, rad, ea, eb, maxit, tol,
                                                        lam_out, Yout, ok, its, gscratch, use_smem);
         NEP_CHECK_LAUNCH();

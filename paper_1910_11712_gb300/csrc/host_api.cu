@@ -8,6 +8,7 @@
 #include <complex>
 #include <atomic>
 #include <mutex>
+#include <set>
 #include <vector>
 
 #include "nep_common.cuh"
@@ -72,6 +73,36 @@ static void configure_pool_once() {
 }
 
 }  // namespace nep
+
+int nep::smem_optin_bytes() {
+    static const int v = [] {
+        int dev = 0, b = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&b, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || b <= 0)
+            b = 227 * 1024;
+        return b;
+    }();
+    return v;
+}
+
+namespace {
+std::mutex g_smem_mu;
+std::set<std::pair<int, const void*>> g_smem_raised;
+}  // namespace
+
+bool nep::smem_limit_raised(const void* fn) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_smem_mu);
+    return g_smem_raised.count({dev, fn}) != 0;
+}
+
+void nep::smem_limit_mark(const void* fn) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_smem_mu);
+    g_smem_raised.insert({dev, fn});
+}
 
 using namespace nep;
 

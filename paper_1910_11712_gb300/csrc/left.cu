@@ -218,8 +218,7 @@ int launch_band_solve_adjoint(const SplitDev& s, int npts, const cx<T>* ab, cons
     while (R < kv + kAdjCH + 1 || R < s.kl + 2 * kAdjCH) R <<= 1;
     const size_t smem = sizeof(cx<T>) * ((size_t)R + 2 * kAdjCH * (kv + 1)) + sizeof(int) * 2 * kAdjCH;
     if (smem <= 200 * 1024) {
-        NEP_CUDA(cudaFuncSetAttribute(band_solve_adjoint_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+        NEP_CUDA(allow_max_dynamic_smem(band_solve_adjoint_kernel<T>));
         band_solve_adjoint_kernel<T><<<dim3(npts, L), 64, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, L, B,
                                                                        active, R);
     } else {

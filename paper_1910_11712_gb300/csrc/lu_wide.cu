@@ -279,7 +279,7 @@ static int run_wide(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info
     const size_t smem = wide_smem(s.kl, NB, chw, sizeof(cx<T>));
     cx<T>* win = nullptr;
     NEP_CUDA(cudaMallocAsync((void**)&win, sizeof(cx<T>) * (size_t)rwp * cwp * npts, st));
-    cudaError_t e = cudaFuncSetAttribute(lu_wide_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(lu_wide_kernel<T, NB>);
     if (e == cudaSuccess) {
         lu_wide_kernel<T, NB><<<npts, 512, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, info, active, win, rwp, cwp,
                                                       chw);

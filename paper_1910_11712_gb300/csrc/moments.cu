@@ -63,10 +63,10 @@ int launch_moments(int n, int L, int N, int K, const zd* coef, const zd* Y, zd* 
     const int blocks = ceil_div(nl, 256);
     const size_t sm = sizeof(zd) * (size_t)N * K;
     if (K == 16 && sm <= 96 * 1024) {
-        NEP_CUDA(cudaFuncSetAttribute(moments_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        NEP_CUDA(allow_max_dynamic_smem(moments_kernel<16>));
         moments_kernel<16><<<blocks, 256, sm, st>>>(nl, N, coef, Y, S);
     } else if (K == 8 && sm <= 96 * 1024) {
-        NEP_CUDA(cudaFuncSetAttribute(moments_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        NEP_CUDA(allow_max_dynamic_smem(moments_kernel<8>));
         moments_kernel<8><<<blocks, 256, sm, st>>>(nl, N, coef, Y, S);
     } else {
         moments_kernel_generic<<<blocks, 256, 0, st>>>(nl, N, K, coef, Y, S);
@@ -113,7 +113,7 @@ int launch_vh_times(int n, int L, int K, const zd* V, const zd* S, zd* mu, zd* p
     const int nch = ceil_div(n, VH_ROWS);
     const size_t sm = sizeof(zd) * 2 * VH_ROWS * L;
     if (sm > 200 * 1024) return NEP_ERR_UNSUPPORTED;
-    NEP_CUDA(cudaFuncSetAttribute(vh_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    NEP_CUDA(allow_max_dynamic_smem(vh_partial_kernel));
     vh_partial_kernel<<<dim3(nch, K), 256, sm, st>>>(n, L, K, V, S, part);
     NEP_CHECK_LAUNCH();
     vh_reduce_kernel<<<ceil_div(K * L * L, 256), 256, 0, st>>>(nch, L * L, K, part, mu);

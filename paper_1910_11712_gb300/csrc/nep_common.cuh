@@ -197,6 +197,27 @@ void count_launch();
 
 static inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// The device's opt-in dynamic shared memory per block (queried once).
+int smem_optin_bytes();
+// Raises a kernel's dynamic shared-memory limit to that maximum (less its static shared memory).
+// Every caller sets the same value,
+// so calls from several host threads (the request server's workers, concurrent plans) cannot lower
+// the limit between another thread's set and its launch; each launch still passes its own size.
+// (done once per kernel and device; two threads racing to do it set the same value)
+bool smem_limit_raised(const void* fn);
+void smem_limit_mark(const void* fn);
+template <typename K>
+inline cudaError_t allow_max_dynamic_smem(K kernel) {
+    if (smem_limit_raised((const void*)kernel)) return cudaSuccess;
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_optin_bytes() - (int)a.sharedSizeBytes);
+    if (e == cudaSuccess) smem_limit_mark((const void*)kernel);
+    return e;
+}
+
 // ----------------------------------------------------------------- launchers (per file)
 // assemble.cu
 template <typename T>

@@ -280,8 +280,10 @@ typedef struct {
  *   - Leja-Bagby nodes sigma_j on the boundary and poles xi_j in Xi (Eq. (nleigsleja)), sigma_0 =
  *     z_0, each Xi point used at most once, infinity once none is left; scalings beta_j with
  *     max |b_j| = 1 on the boundary (Eq. (nleigsbj), beta_0 = 1);
- *   - divided differences by the interpolation recurrence (Eq. (nleigsdd)); the degree d is the
- *     first d >= 1 whose last pole, taken as infinity (Eq. (nleigsmatlin)), gives
+ *   - divided differences d_i^j = e_j^T f_i(H K^{-1}) e_1 (Eq. (nleigsfdd)) through functions of
+ *     the lower-triangular H K^{-1} (matrix polynomials and triangular solves, exp by scaling and
+ *     squaring of its Taylor series, sqrt by the Bjorck-Hammarling recurrence); the degree d is
+ *     the first d >= 1 whose last pole, taken as infinity (Eq. (nleigsmatlin)), gives
  *     max_i |d_i^d| < tol max_i |d_i^0|.
  * Host arrays with room for cap = d+1 entries (d <= max_degree): sigma, xi complex[cap] (xi[0] and
  * the last pole are infinity, written as (inf, 0)); beta double[cap]; dd complex[nterms*cap] with
@@ -291,6 +293,11 @@ typedef struct {
 int nep_nleigs_interpolation(nep_split_t h, const nep_region *r, const nep_nleigs_opts *o, int32_t cap,
                              double *sigma, double *xi, double *beta, double *dd, int32_t *degree,
                              int32_t *converged, int32_t *nsing);
+/* The same from the function descriptions alone (nterms of them, as for nep_create_split): a host
+ * computation that touches no device, for callers without a split or without a GPU. */
+int nep_nleigs_interpolation_fns(int32_t nterms, const nep_fn *f, const nep_region *r, const nep_nleigs_opts *o,
+                                 int32_t cap, double *sigma, double *xi, double *beta, double *dd, int32_t *degree,
+                                 int32_t *converged, int32_t *nsing);
 /* NLEIGS, static variant with a full basis (Sec. 4.5.2, 4.5.3 "full basis"): shift-and-invert
  * Arnoldi with o->krylov steps on S = (A - sigma B)^{-1} B for the linearisation (A, B) of
  * Eq. (nleigsmatlin), applied through the block recurrences of Eqs. (nleigstoarreca) and

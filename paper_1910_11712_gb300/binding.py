@@ -119,6 +119,10 @@ SIGNATURES = {
     "nep_nleigs_interpolation": (c_int32, [c_void_p, ctypes.POINTER(NepRegion), ctypes.POINTER(NepNleigsOpts), c_int32,
                                            c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_int32),
                                            ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
+    "nep_nleigs_interpolation_fns": (c_int32, [c_int32, c_void_p, ctypes.POINTER(NepRegion),
+                                               ctypes.POINTER(NepNleigsOpts), c_int32, c_void_p, c_void_p, c_void_p,
+                                               c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
+                                               ctypes.POINTER(c_int32)]),
     "nep_nleigs_solve": (c_int32, [c_void_p, ctypes.POINTER(NepRegion), ctypes.POINTER(NepNleigsOpts),
                                    ctypes.POINTER(c_void_p), ctypes.POINTER(c_int32), c_void_p]),
     "nep_apply_resolvent": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_int32,
@@ -508,23 +512,36 @@ def nleigs_opts(tol=0.0, max_degree=0, nboundary=0, krylov=0, shift=None, seed=0
     return o
 
 
-def nleigs_interpolation(split, region, **opts) -> dict:
-    """nep_nleigs_interpolation: nodes, poles (inf for none), scalings, divided differences dd[i, j]."""
-    lib = load()
+def _interp_call(call, nterms, region, opts) -> dict:
     r, o = region_struct(region), nleigs_opts(**opts)
     d, conv, ns = c_int32(), c_int32(), c_int32()
-    check(lib.nep_nleigs_interpolation(split.handle, ctypes.byref(r), ctypes.byref(o), 0, None, None, None, None,
-                                       ctypes.byref(d), ctypes.byref(conv), ctypes.byref(ns)))
+    check(call(ctypes.byref(r), ctypes.byref(o), 0, None, None, None, None, ctypes.byref(d), ctypes.byref(conv),
+               ctypes.byref(ns)))
     cap = d.value + 1
     sig = np.zeros(cap, np.complex128)
     xi = np.zeros(cap, np.complex128)
     beta = np.zeros(cap)
-    dd = np.zeros(split.nterms * cap, np.complex128)
-    check(lib.nep_nleigs_interpolation(split.handle, ctypes.byref(r), ctypes.byref(o), cap, sig.ctypes.data,
-                                       xi.ctypes.data, beta.ctypes.data, dd.ctypes.data, ctypes.byref(d),
-                                       ctypes.byref(conv), ctypes.byref(ns)))
+    dd = np.zeros(nterms * cap, np.complex128)
+    check(call(ctypes.byref(r), ctypes.byref(o), cap, sig.ctypes.data, xi.ctypes.data, beta.ctypes.data,
+               dd.ctypes.data, ctypes.byref(d), ctypes.byref(conv), ctypes.byref(ns)))
     return {"d": d.value, "converged": bool(conv.value), "nsing": ns.value, "sigma": sig, "xi": xi, "beta": beta,
-            "dd": dd.reshape(cap, split.nterms).T.copy()}
+            "dd": dd.reshape(cap, nterms).T.copy()}
+
+
+def nleigs_interpolation(split, region, **opts) -> dict:
+    """nep_nleigs_interpolation: nodes, poles (inf for none), scalings, divided differences dd[i, j]."""
+    lib = load()
+    return _interp_call(lambda *a: lib.nep_nleigs_interpolation(split.handle, *a), split.nterms, region, opts)
+
+
+def nleigs_interpolation_fns(fns, region, **opts) -> dict:
+    """nep_nleigs_interpolation_fns: the same from the function descriptions alone (host only)."""
+    lib = load()
+    keep = _Keep()
+    fs = (NepFn * len(fns))()
+    for i, spec in enumerate(fns):
+        fs[i] = _fn_struct(keep, spec)
+    return _interp_call(lambda *a: lib.nep_nleigs_interpolation_fns(len(fns), fs, *a), len(fns), region, opts)
 
 
 def nleigs_solve(split, region, stream=0, **opts) -> dict:

@@ -1129,9 +1129,38 @@ static int nleigs_params(nep_split_t h, const nep_region* r, const nep_nleigs_op
     return NEP_OK;
 }
 
+static int nleigs_interp_out(nep_split_t h, const nep_region* r, const nep_nleigs_opts* o, int32_t cap,
+                             double* sigma, double* xi, double* beta, double* dd, int32_t* degree,
+                             int32_t* converged, int32_t* nsing);
+
 extern "C" int nep_nleigs_interpolation(nep_split_t h, const nep_region* r, const nep_nleigs_opts* o, int32_t cap,
                                         double* sigma, double* xi, double* beta, double* dd, int32_t* degree,
                                         int32_t* converged, int32_t* nsing) {
+    return nleigs_interp_out(h, r, o, cap, sigma, xi, beta, dd, degree, converged, nsing);
+}
+
+extern "C" int nep_nleigs_interpolation_fns(int32_t nterms, const nep_fn* f, const nep_region* r,
+                                            const nep_nleigs_opts* o, int32_t cap, double* sigma, double* xi,
+                                            double* beta, double* dd, int32_t* degree, int32_t* converged,
+                                            int32_t* nsing) {
+    if (nterms < 1 || nterms > 32 || !f) {
+        set_error("nep_nleigs_interpolation_fns: need 1 <= nterms <= 32 and non-NULL f");
+        return NEP_ERR_ARG;
+    }
+    // the function trees only, on the host: no matrices, no device memory
+    nep_split h;
+    h.nterms = nterms;
+    for (int i = 0; i < nterms; ++i) {
+        const int root = flatten_fn(&h, &f[i], 0);
+        if (root < 0) return NEP_ERR_ARG;
+        h.roots.push_back(root);
+    }
+    return nleigs_interp_out(&h, r, o, cap, sigma, xi, beta, dd, degree, converged, nsing);
+}
+
+static int nleigs_interp_out(nep_split_t h, const nep_region* r, const nep_nleigs_opts* o, int32_t cap,
+                             double* sigma, double* xi, double* beta, double* dd, int32_t* degree,
+                             int32_t* converged, int32_t* nsing) {
     NleigsParams q;
     NEP_TRY(nleigs_params(h, r, o, &q));
     NleigsInterp it;

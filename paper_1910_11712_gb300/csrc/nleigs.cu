@@ -9,9 +9,12 @@
 //     cuts sampled at fixed distances; exp has none);
 //   * Leja-Bagby nodes sigma_j and poles xi_j (Sec. 4.5.1 Eq. (nleigsleja)), scalings beta_j
 //     with max |b_j| = 1 on the boundary (Eq. (nleigsbj));
-//   * scalar divided differences d_i^j by the interpolation recurrence of Eq. (nleigsdd),
-//     d_i^j = (f_i(sigma_j) - sum_{k<j} b_k(sigma_j) d_i^k) / b_j(sigma_j), and the degree: the
-//     first d >= 1 whose last pole, taken as infinity, gives max_i |d_i^d| < tol max_i |d_i^0|.
+//   * scalar divided differences d_i^j = e_j^T f_i(H K^{-1}) e_1 (Eq. (nleigsfdd)) through
+//     functions of the lower-triangular H K^{-1}: matrix polynomials and triangular solves,
+//     exp by scaling and squaring of its Taylor series, sqrt by the Bjorck-Hammarling
+//     recurrence (the interpolation recurrence of Eq. (nleigsdd) loses digits to cancellation
+//     at about eps max|f| on the boundary, which decided the degree test); the degree: the first
+//     d >= 1 whose last pole, taken as infinity, gives max_i |d_i^d| < tol max_i |d_i^0|.
 // Device (FP64), one Arnoldi step w = S v (Sec. 4.5.2, Eqs. (nleigstoarreca), (nleigstoarrecb)):
 //   * with z = B v (z^j = v^{j-1} + beta_j/xi_j v^j), a particular solution p of the block rows
 //     1..d-1 with p^{d-1} = 0, p^{j-1} = (z^j - beta_j (1 - sigma/xi_j) p^j) / (sigma_{j-1} - sigma),
@@ -122,6 +125,116 @@ void basis_at(cd z, const std::vector<cd>& sig, const std::vector<cd>& xi, const
     }
 }
 
+// ---- functions of small lower-triangular matrices (the divided differences of Sec. 4.5.1
+// Eq. (nleigsfdd)): every matrix here is a function of one lower-triangular M, so all of them are
+// lower triangular and commute
+struct LMat {
+    int m = 0;
+    std::vector<cd> a;  // column-major, entries above the diagonal stay zero
+    explicit LMat(int m_ = 0) : m(m_), a((size_t)m_ * m_, 0.0) {}
+    cd& operator()(int i, int j) { return a[i + (size_t)m * j]; }
+    cd operator()(int i, int j) const { return a[i + (size_t)m * j]; }
+};
+
+LMat lm_eye(int m, cd v = 1.0) {
+    LMat r(m);
+    for (int i = 0; i < m; ++i) r(i, i) = v;
+    return r;
+}
+LMat lm_mul(const LMat& A, const LMat& B) {
+    LMat C(A.m);
+    for (int j = 0; j < A.m; ++j)
+        for (int i = j; i < A.m; ++i) {
+            cd acc = 0.0;
+            for (int k = j; k <= i; ++k) acc += A(i, k) * B(k, j);
+            C(i, j) = acc;
+        }
+    return C;
+}
+LMat lm_axpby(cd x, const LMat& A, cd y, const LMat& B) {
+    LMat C(A.m);
+    for (size_t t = 0; t < C.a.size(); ++t) C.a[t] = x * A.a[t] + y * B.a[t];
+    return C;
+}
+// L^{-1} B for lower-triangular L (forward substitution, column by column)
+LMat lm_solve(const LMat& L, const LMat& B) {
+    LMat X(B.m);
+    for (int j = 0; j < B.m; ++j)
+        for (int i = j; i < B.m; ++i) {
+            cd acc = B(i, j);
+            for (int k = j; k < i; ++k) acc -= L(i, k) * X(k, j);
+            X(i, j) = acc / L(i, i);
+        }
+    return X;
+}
+LMat lm_poly(const std::vector<cd>& c, const LMat& X) {  // c[0] the leading coefficient (Horner)
+    LMat R(X.m);
+    for (cd a : c) R = lm_axpby(1.0, lm_mul(R, X), 1.0, lm_eye(X.m, a));
+    return R;
+}
+// exp by scaling and squaring of the Taylor series: ||X / 2^s||_1 <= 1/2, 20 terms (truncation
+// below (1/2)^21 / 21!, far under the rounding of the squarings)
+LMat lm_exp(const LMat& X) {
+    double nrm = 0.0;
+    for (int j = 0; j < X.m; ++j) {
+        double cs = 0.0;
+        for (int i = j; i < X.m; ++i) cs += std::abs(X(i, j));
+        nrm = std::max(nrm, cs);
+    }
+    int sq = 0;
+    while (nrm > 0.5 && sq < 60) {
+        nrm *= 0.5;
+        ++sq;
+    }
+    const LMat Y = lm_axpby(std::ldexp(1.0, -sq), X, 0.0, X);
+    LMat E = lm_eye(X.m), term = lm_eye(X.m);
+    for (int k = 1; k <= 20; ++k) {
+        term = lm_axpby(1.0 / k, lm_mul(term, Y), 0.0, term);
+        E = lm_axpby(1.0, E, 1.0, term);
+    }
+    for (int k = 0; k < sq; ++k) E = lm_mul(E, E);
+    return E;
+}
+// principal square root of a lower-triangular T by the Bjorck-Hammarling recurrence, diagonal by
+// diagonal: R_ii = sqrt(T_ii), R_ij = (T_ij - sum_{j<k<i} R_ik R_kj) / (R_ii + R_jj)
+LMat lm_sqrt(const LMat& T) {
+    LMat R(T.m);
+    for (int i = 0; i < T.m; ++i) R(i, i) = std::sqrt(T(i, i));
+    for (int dist = 1; dist < T.m; ++dist)
+        for (int j = 0; j + dist < T.m; ++j) {
+            const int i = j + dist;
+            cd acc = T(i, j);
+            for (int k = j + 1; k < i; ++k) acc -= R(i, k) * R(k, j);
+            R(i, j) = acc / (R(i, i) + R(j, j));
+        }
+    return R;
+}
+
+// f_k(M) for the function tree at node k: beta h(alpha M)
+LMat lm_fn(const std::vector<FnNode>& nodes, const std::vector<zd>& pool, int k, const LMat& M, int depth) {
+    const FnNode& nd = nodes[k];
+    const LMat X = lm_axpby(to_cd(nd.alpha), M, 0.0, M);
+    LMat H(M.m);
+    if (nd.kind == NEP_FN_RATIONAL) {
+        H = lm_poly(coef_slice(pool, nd.num_off, nd.num_len), X);
+        if (nd.den_len > 0) H = lm_solve(lm_poly(coef_slice(pool, nd.den_off, nd.den_len), X), H);
+    } else if (nd.kind == NEP_FN_EXP) {
+        H = lm_exp(X);
+    } else if (nd.kind == NEP_FN_SQRT) {
+        H = lm_sqrt(lm_axpby(1.0, X, -1.0, lm_eye(M.m, to_cd(nd.shift))));
+    } else if (depth <= 16) {
+        if (nd.op == NEP_OP_COMPOSE) {
+            H = lm_fn(nodes, pool, nd.a, lm_fn(nodes, pool, nd.b, X, depth + 1), depth + 1);
+        } else {
+            const LMat A = lm_fn(nodes, pool, nd.a, X, depth + 1), B = lm_fn(nodes, pool, nd.b, X, depth + 1);
+            if (nd.op == NEP_OP_ADD) H = lm_axpby(1.0, A, 1.0, B);
+            else if (nd.op == NEP_OP_MUL) H = lm_mul(A, B);
+            else H = lm_solve(B, A);  // A B^{-1} = B^{-1} A: they commute
+        }
+    }
+    return lm_axpby(to_cd(nd.beta), H, 0.0, H);
+}
+
 }  // namespace
 
 int nleigs_interpolation(const std::vector<FnNode>& nodes, const std::vector<zd>& pool, const std::vector<int>& roots,
@@ -178,10 +291,6 @@ int nleigs_interpolation(const std::vector<FnNode>& nodes, const std::vector<zd>
             for (auto& v : sx) v /= m;
         }
     }
-    // f_i at the nodes
-    std::vector<cd> F((size_t)nt * (dmax + 1));
-    for (int j = 0; j <= dmax; ++j)
-        for (int i = 0; i < nt; ++i) F[i + (size_t)nt * j] = to_cd(fn_eval(nodes.data(), pool.data(), roots[i], to_zd(sig[j])).f);
     int d = 1;
     std::vector<cd> xi;
     std::vector<double> beta;
@@ -203,16 +312,19 @@ int nleigs_interpolation(const std::vector<FnNode>& nodes, const std::vector<zd>
             beta[j] = m;
             for (auto& v : bv) v /= m;
         }
-        // recurrence d_i^j = (f_i(sigma_j) - sum_{k<j} b_k(sigma_j) d_i^k) / b_j(sigma_j)
+        // d_i^j = e_j^T f_i(H K^{-1}) e_1 (Eq. (nleigsfdd), beta_0 = 1): H lower bidiagonal with the
+        // nodes on its diagonal and beta_j below, K with ones and beta_j / xi_j
+        LMat Hm(d + 1), Km = lm_eye(d + 1);
+        for (int j = 0; j <= d; ++j) Hm(j, j) = sig[j];
+        for (int j = 1; j <= d; ++j) {
+            Hm(j, j - 1) = beta[j];
+            Km(j, j - 1) = finite_pole(xi[j]) ? beta[j] / xi[j] : cd(0.0);
+        }
+        const LMat Mm = lm_mul(Hm, lm_solve(Km, lm_eye(d + 1)));
         dd.assign((size_t)nt * (d + 1), 0.0);
-        std::vector<cd> bj;
-        for (int j = 0; j <= d; ++j) {
-            basis_at(sig[j], sig, xi, beta, d, &bj);
-            for (int i = 0; i < nt; ++i) {
-                cd acc = F[i + (size_t)nt * j];
-                for (int k = 0; k < j; ++k) acc -= bj[k] * dd[i + (size_t)nt * k];
-                dd[i + (size_t)nt * j] = acc / bj[j];
-            }
+        for (int i = 0; i < nt; ++i) {
+            const LMat Fm = lm_fn(nodes, pool, roots[i], Mm, 0);
+            for (int j = 0; j <= d; ++j) dd[i + (size_t)nt * j] = Fm(j, 0);
         }
         double d0 = 0.0, dl = 0.0;
         for (int i = 0; i < nt; ++i) {

@@ -1,8 +1,8 @@
 """NLEIGS, static variant, through the C ABI (nep_nleigs_interpolation, nep_nleigs_solve;
 Sec. 4.5) against the oracle and closed forms.
 
-  * the interpolation: the library's divided differences (interpolation recurrence) equal the
-    oracle's matrix-function divided differences for the library's own nodes, poles and
+  * the interpolation: the library's divided differences (its own matrix functions) equal the
+    oracle's (scipy's) matrix-function divided differences for the library's own nodes, poles and
     scalings; those satisfy the Leja-Bagby conditions and max |b_j| = 1 on the boundary; the
     degree is the oracle's;
   * the eigenvalues: Lambert W (decoupled delay), companion roots (decoupled Drude), quadratic
@@ -55,7 +55,7 @@ def test_interpolation_matches_the_oracle(bnd, name):
     assert all(np.abs(bndry - s).min() <= 1e-12 for s in sig)
     b = nleigs.basis(bndry, sig, xi, beta, d)
     assert np.allclose(np.abs(b).max(axis=1), 1.0, rtol=1e-13)
-    # divided differences: recurrence (library) vs matrix functions (oracle) for the same nodes
+    # divided differences: the library's matrix functions vs scipy's (oracle) for the same nodes
     ref = nleigs.divided_differences(p.fns, sig, xi, beta, d)
     assert np.abs(it["dd"] - ref).max() <= 1e-11 * np.abs(ref[:, 0]).max()
     # the interpolant reproduces the f_i on the boundary

@@ -37,6 +37,20 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def job_throughput(ms_rank: float, world: int, units_per_step_rank: int, device: str = "cuda"):
+    """Whole-job throughput of independent replicas: every rank ran the same number of steps on
+    its own problem; the job's step time is the slowest rank's (max over ranks), and the job's
+    units are all ranks' units. Returns (ms per step of the job, units per second)."""
+    ms = ms_rank
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_rank], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_step_rank / (ms * 1e-3)
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples during the timed region."""
 
@@ -390,11 +404,7 @@ def main():
     torch.cuda.synchronize()
     solve_ms = k0.elapsed_time(k1) / reps
     del Bs
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * p.N / (ms * 1e-3)
+    ms, value = job_throughput(ms, world, p.N)
 
     # conjugate-symmetric quadrature on the same workload (real operators only): a real probe
     # block, only the N/2 nodes above the real axis solved

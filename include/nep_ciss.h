@@ -307,10 +307,12 @@ int nep_nleigs_interpolation_fns(int32_t nterms, const nep_fn *f, const nep_regi
  * the Hessenberg matrix and a Rayleigh quotient) give lambda = sigma + 1/theta and x the first block
  * of the Ritz vector; pairs inside the region with FP64 eta (Sec. 2 Eq. (sressplit), of the full T) at most
  * eig_tol are returned, deduplicated and sorted as nep_ciss_solve does. *out receives a result
- * object (nep_result_get; hankel_rank there is 0); *degree (or NULL) the interpolation degree.
- * Needs nterms <= 8. The call allocates its work arrays on the stream ((d n) x (krylov+1)
+ * object (nep_result_get; hankel_rank there is 0; flags NEP_WARN_INTERP if the degree test failed
+ * at max_degree, NEP_WARN_SINGULAR_NODE if R_d(sigma) had an exactly zero pivot); *degree (or NULL)
+ * the interpolation degree. The call allocates its work arrays on the stream ((d n) x (krylov+1)
  * complex128 for the basis) and returns when they are done. Errors: NEP_ERR_ARG, NEP_ERR_REGION
- * (a singularity of some f_i inside or on the region), CUDA errors. */
+ * (a singularity of some f_i inside or on the region), NEP_ERR_UNSUPPORTED (more than 8 terms),
+ * CUDA errors. */
 int nep_nleigs_solve(nep_split_t h, const nep_region *r, const nep_nleigs_opts *o, nep_result_t *out,
                      int32_t *degree, void *stream);
 

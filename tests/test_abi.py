@@ -62,3 +62,23 @@ def test_host_entry_points_without_gpu(built):
     h = ctypes.c_void_p()
     assert lib.nep_create_split(0, 1, None, None, ctypes.byref(h)) == binding.NEP_ERR_ARG
     assert b"nep_create_split" in lib.nep_last_error()
+
+
+def test_new_entry_points_refuse_bad_arguments_without_gpu(built):
+    """Argument checks of the left-vector, resolvent and NLEIGS entry points run on the host."""
+    from paper_1910_11712_gb300 import binding
+    lib = binding.load()
+    E = binding.NEP_ERR_ARG
+    assert lib.nep_band_solve_adjoint(None, 1, 1, None, None, 1, None, None) == E
+    assert lib.nep_left_eigvecs(None, 1, 1, None, None, None, None, None, 1e-13, 4, None, None) == E
+    assert lib.nep_plan_left(None, 1e-13, 4, 0, None, None, None, None, None) == E
+    assert lib.nep_apply_resolvent(0, 1, None, None, None, 1, None, 1, None, None, None) == E
+    assert lib.nep_apply_resolvent(8, -1, None, None, None, 1, None, 1, None, None, None) == E
+    region = binding.region_struct({"center": 0.0, "a": 1.0, "b": 1.0})
+    assert lib.nep_nleigs_solve(None, ctypes.byref(region), None, None, None, None) == E
+    assert lib.nep_nleigs_interpolation_fns(0, None, ctypes.byref(region), None, 0, None, None, None, None,
+                                            None, None, None) == E
+    # nothing to do is not an error: no pairs, no points
+    assert lib.nep_apply_resolvent(8, 0, None, None, None, 0, None, 0, None, None, None) == binding.NEP_OK
+    # pairs without their arrays are refused even with nothing to apply them to
+    assert lib.nep_apply_resolvent(8, 3, None, None, None, 0, None, 0, None, None, None) == E

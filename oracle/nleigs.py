@@ -18,7 +18,9 @@
     Eq. (nleigsmatlin));
   * the linearisation pencil (A, B) of Eq. (nleigsmatlin) built densely, its eigenvalues by a
     library generalized eigensolver: the eigenvalues of R_d(lambda) x = 0, with x the first
-    block of the eigenvector.
+    block of the eigenvector;
+  * Arnoldi on S = (A - sigma B)^{-1} B in the compact (TOAR) representation of Sec. 4.5.3
+    (Eqs. (nleigs-toar1)-(nleigs-toar4)), next to a plain full-basis Arnoldi on the explicit S.
 """
 from __future__ import annotations
 
@@ -233,3 +235,101 @@ def solve(problem, region=None, *, tol: float = TOL, dmax: int = DMAX, eig_tol: 
     return {"lam": np.array([out_l[i] for i in order], np.complex128),
             "X": np.stack([out_x[i] for i in order], axis=1) if order else np.zeros((n, 0), np.complex128),
             "eta": np.array([out_e[i] for i in order]), "interp": interp}
+
+
+def shift_invert_dense(problem, interp: dict, sigma: complex):
+    """The explicit S = (A - sigma B)^{-1} B of the dense pencil (small problems only)."""
+    A, B = linearization(problem.mats, interp)
+    return np.linalg.solve(A - sigma * B, B)
+
+
+def arnoldi_full(S: np.ndarray, v0: np.ndarray, k: int):
+    """Plain Arnoldi (classical Gram-Schmidt twice) on an explicit matrix: V (N x k+1), H (k+1 x k)."""
+    N = S.shape[0]
+    V = np.zeros((N, k + 1), np.complex128)
+    H = np.zeros((k + 1, k), np.complex128)
+    V[:, 0] = v0 / np.linalg.norm(v0)
+    for j in range(k):
+        w = S @ V[:, j]
+        for _ in range(2):
+            h = V[:, :j + 1].conj().T @ w
+            w = w - V[:, :j + 1] @ h
+            H[:j + 1, j] += h
+        H[j + 1, j] = np.linalg.norm(w)
+        V[:, j + 1] = w / H[j + 1, j]
+    return V, H
+
+
+def arnoldi_toar(problem, interp: dict, sigma: complex, w0: np.ndarray, k: int):
+    """Arnoldi on S in the compact (TOAR) representation of Sec. 4.5.3: every Krylov vector's d
+    blocks are U g^i for one orthonormal U (n x (k+d)) and coefficient vectors g^i. The expansion
+    follows Eqs. (nleigs-toar1)-(nleigs-toar4): the coefficient recurrence for y^1 .. y^{d-1}, the
+    solve with R_d(sigma) for y^0 in split form, its orthogonalisation against U (which extends U
+    by one vector), then the coefficients of S v. The Arnoldi orthogonalisation runs on the
+    stacked coefficients (U has orthonormal columns). w0: n x d start blocks.
+    Returns U, G (list of k+1 stacked coefficient vectors), H (k+1 x k)."""
+    from . import band
+    d, sig, xi, beta, dd = interp["d"], interp["sigma"], interp["xi"], interp["beta"], interp["dd"]
+    mats = problem.mats
+    inv_xi = np.array([1.0 / x if np.isfinite(x) else 0.0 for x in xi], np.complex128)
+    bs = basis(sigma, sig, xi, beta, d)[:, 0]                     # b_j(sigma)
+    Rd = sum(complex(dd[t] @ bs) * mats[t] for t in range(len(mats)))  # R_d(sigma), split form
+    Rd = Rd.toarray() if hasattr(Rd, "toarray") else np.asarray(Rd)
+    Q, R = np.linalg.qr(w0)                                       # U_d and g_1 (Algorithm, first lines)
+    U = Q
+    g = R.T.reshape(-1)                                           # blocks g^i = R[:, i], stacked
+    g = g / np.linalg.norm(g)
+    G = [g]
+    H = np.zeros((k + 1, k), np.complex128)
+    for j in range(k):
+        m = U.shape[1]
+        gb = G[-1].reshape(d, m)                                  # g^0 .. g^{d-1}
+        # Eq. (nleigs-toar1): gt^{d-1} .. gt^1 (gt^i stands for y^i in the coefficients)
+        gt = np.zeros((d, m), np.complex128)
+        for i in range(d - 1, 0, -1):
+            z = gb[i - 1] + beta[i] * inv_xi[i] * gb[i]
+            nxt = gt[i + 1] if i + 1 < d else 0.0
+            gt[i] = (z - beta[i] * (1.0 - sigma * inv_xi[i]) * nxt) / (sig[i - 1] - sigma)
+        # Eq. (nleigs-toar2) in split form: y^0 = R_d(sigma)^{-1} (-sum_t A_t U c_t)
+        rhs = np.zeros(problem.n, np.complex128)
+        for t, A in enumerate(mats):
+            c = sum(dd[t, i] * gt[i + 1] for i in range(d - 1)) + dd[t, d] / beta[d] * gb[d - 1]
+            rhs -= A @ (U @ c)
+        y0 = np.linalg.solve(Rd, rhs)
+        # Eq. (nleigs-toar3): orthogonalise y^0 against U, extend U
+        h = U.conj().T @ y0
+        r = y0 - U @ h
+        h2 = U.conj().T @ r
+        r = r - U @ h2
+        h = h + h2
+        rho = np.linalg.norm(r)
+        U = np.column_stack([U, r / rho])
+        gt0 = np.concatenate([h, [rho]])
+        # Eq. (nleigs-toar4): coefficients of S v in the extended basis
+        gn = np.zeros((d, m + 1), np.complex128)
+        for i in range(d - 1):
+            gn[i, :m] = gt[i + 1]
+            gn[i] += bs[i] * gt0
+        gn[d - 1] = bs[d - 1] * gt0
+        gvec = gn.reshape(-1)
+        # Arnoldi on the stacked coefficients (old vectors padded with zeros for the new column of U)
+        Gm = np.column_stack([np.pad(x.reshape(d, -1), ((0, 0), (0, m + 1 - x.size // d))).reshape(-1)
+                              for x in G])
+        for _ in range(2):
+            hh = Gm.conj().T @ gvec
+            gvec = gvec - Gm @ hh
+            H[:j + 1, j] += hh
+        H[j + 1, j] = np.linalg.norm(gvec)
+        G.append(gvec / H[j + 1, j])
+    return U, G, H
+
+
+def toar_vectors(U: np.ndarray, G: list, d: int) -> np.ndarray:
+    """The full Krylov vectors (I_d (x) U) g of the compact representation, as columns."""
+    m = U.shape[1]
+    cols = []
+    for g in G:
+        gb = g.reshape(d, -1)
+        gb = np.pad(gb, ((0, 0), (0, m - gb.shape[1])))
+        cols.append(np.concatenate([U @ gb[i] for i in range(d)]))
+    return np.column_stack(cols)

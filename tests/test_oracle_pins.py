@@ -177,3 +177,31 @@ def test_invariant_pair_of_returned_eigenpairs():
         Tsum += (A @ X) * fv[None, :]
         scale += np.abs(fv).max() * np.abs(A).sum(axis=1).max()
     assert np.linalg.norm(Tsum) / (scale * np.linalg.norm(X)) < 1e-13
+
+
+def diagonal_linear_on_node(z_node, n=6, seed=0, N=16):
+    """T(z) = diag(d) - z I on the unit circle around 0 with d_0 placed exactly on a quadrature node
+    (T(z_node) exactly singular) and the other d_i drawn strictly inside or outside the circle."""
+    from synth.problems import Problem, _rational, _sorted_csr
+    rng = np.random.default_rng(seed)
+    rad = np.concatenate([[0.0], rng.uniform(0.1, 0.7, n - 3), rng.uniform(1.3, 1.6, 2)])
+    d = rad * np.exp(2j * np.pi * rng.uniform(size=n))
+    d[0] = z_node
+    mats = [_sorted_csr(sp.diags(d, 0, format="csr")), _sorted_csr(sp.identity(n, format="csr"))]
+    fns = [_rational([1.0]), _rational([-1.0, 0.0])]
+    region = {"center": 0j, "a": 1.0, "b": 1.0}
+    return Problem("diagonal_linear_on_node", n, mats, fns, region, N=N, L=n, M=2, meta={"d": d})
+
+
+def test_singular_node_drops_out():
+    """An eigenvalue exactly on a quadrature node makes T(z_0) singular: that node contributes
+    nothing, the result stays finite and the eigenvalues strictly inside are the d_i exactly."""
+    z, _, _ = contour.nodes({"center": 0j, "a": 1.0, "b": 1.0}, 16)
+    p = diagonal_linear_on_node(z[0])
+    V = synth.random_probe_block(p.n, p.L, 0)
+    r = ciss.solve(p, V=V)
+    assert r["info"][0] != 0 and not np.any(r["info"][1:])
+    assert np.all(np.isfinite(r["S"]))
+    inside = [complex(x) for x in p.meta["d"][1:] if abs(x) < 1]
+    found = [l for l in r["lam"] if abs(l - p.meta["d"][0]) > 1e-8]
+    _match(found, inside, 1e-12)

@@ -85,3 +85,33 @@ def test_wrong_refinement_sign_caught(monkeypatch):
         return r
     monkeypatch.setattr(ciss, "solve_point", bad)
     assert moment_closed_form_error() > 1e-3
+
+
+def _lambert_matched(p, L):
+    V = synth.random_probe_block(p.n, L, 0)
+    r = ciss.solve(p, V=V, L=L)
+    ref = lambert_reference(p)
+    return sum(1 for e in ref if len(r["lam"]) and np.min(np.abs(r["lam"] - e)) <= 1e-12 * max(1.0, abs(e)))
+
+
+def test_eager_newton_abandonment_caught(monkeypatch):
+    """Giving up on a Newton iterate that is unconverged and outside Gamma by 10% after 3 steps
+    loses a Lambert W eigenvalue: on this decoupled delay problem (probe block of 2 columns) the
+    only Newton path that reaches lambda = -0.3211 lies outside Gamma at step 3 and converges
+    inside at step 9."""
+    p = synth.diagonal_delay(n=8, seed=8)
+    plain = _lambert_matched(p, 2)
+    assert plain >= 1
+    orig = ciss.newton_projected
+    c = complex(p.region["center"])
+    a, b = p.region["a"], p.region["b"]
+
+    def eager(Bs, fns, lam0, y0, region):
+        monkeypatch.setattr(ciss, "NEWTON_MAX", 3)
+        lam, y, ok, it = orig(Bs, fns, lam0, y0, region)
+        monkeypatch.setattr(ciss, "NEWTON_MAX", 30)
+        if ok and it == 3 and ((lam - c).real / a) ** 2 + ((lam - c).imag / b) ** 2 > 1.21:
+            return lam, y, False, it
+        return orig(Bs, fns, lam0, y0, region)
+    monkeypatch.setattr(ciss, "newton_projected", eager)
+    assert _lambert_matched(p, 2) < plain

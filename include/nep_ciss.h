@@ -45,7 +45,10 @@ extern "C" {
 #define NEP_WARN_SATURATED 1     /* Hankel rank m == L*M: the probe subspace may be too small */
 #define NEP_WARN_REFINE 2        /* some quadrature solve missed the backward-error target */
 #define NEP_WARN_SINGULAR_NODE 4 /* an exactly zero pivot at some quadrature node         */
-#define NEP_WARN_NEWTON 8        /* a Newton iteration on the projected problem failed      */
+#define NEP_WARN_NEWTON 8        /* a Newton iteration on the projected problem failed (singular */
+                                 /* bordered system or a non-finite iterate); candidates whose   */
+                                 /* iterates left the region are counted in nep_result_info_t's  */
+                                 /* newton_left and raise no warning                              */
 #define NEP_WARN_INTERP 16       /* NLEIGS: the interpolation degree test failed at max_degree */
 
 /* arithmetic of the quadrature solves */
@@ -116,6 +119,13 @@ typedef struct {
                          /* centre), an even N and a real V: plan creation returns        */
                          /* NEP_ERR_ARG otherwise (V is checked at execute). Then S_k =   */
                          /* 2 Re of the sum over those N/2 nodes. Default 0.              */
+    int32_t newton_abandon;     /* shortcut: a Newton iterate still unconverged after this many  */
+                                /* steps and outside Gamma by 10% (((Re(l-c))/a)^2 +             */
+                                /* ((Im(l-c))/b)^2 > 1.21) is given up as having left the region */
+                                /* (default 8; 0: never, iterate to newton_max)                   */
+    int32_t refine_extrapolate; /* shortcut: a refinement sweep also stops when the contraction  */
+                                /* seen so far puts the next correction below step_tol          */
+                                /* (default 1; 0: stop only on step_tol or no halving)           */
 } nep_opts;
 
 /* Defaults listed above. */
@@ -160,6 +170,8 @@ typedef struct {
     double ms_assemble, ms_factor, ms_solve, ms_moments, ms_extract, ms_total;
     double ms_queued;       /* server requests: submit to start of execution (0 otherwise) */
     double ms_latency;      /* server requests: submit to result ready (0 otherwise) */
+    int32_t newton_failed;  /* Newton runs that failed (these raise NEP_WARN_NEWTON)       */
+    int32_t newton_left;    /* Newton runs whose iterate left the region (no warning)      */
 } nep_result_info_t;
 int nep_result_info(nep_result_t r, nep_result_info_t *info);
 /* Singular values of the Hankel matrix (L*M of them, descending). */
@@ -168,6 +180,13 @@ int nep_result_free(nep_result_t r);
 const char *nep_last_error(void);
 /* Number of CUDA kernels this library has launched in the process so far (diagnostics). */
 uint64_t nep_kernel_launches(void);
+/* Bound on every device-side wait of the library (the grid barriers of its cooperative kernels:
+ * QR with column pivoting and the Jacobi SVD), in polls of the barrier word; process-wide, read
+ * at each launch. Default 2^24 polls (seconds). A wait that reaches the bound records an error
+ * and stops waiting, the kernel runs to its end without further waits (its loop bounds do not
+ * depend on the data, so it stays in bounds) and the call returns NEP_ERR_INTERNAL with the
+ * context usable. *previous (or NULL) receives the old bound. Errors: NEP_ERR_ARG (polls < 0). */
+int nep_set_wait_limit(int64_t polls, int64_t *previous);
 
 /* ------------------------------------------------------------------ device-resident plan */
 /* A plan owns the device workspace of one (operator, region, N, L, M, opts) solve so

@@ -47,7 +47,8 @@ class NepRegion(ctypes.Structure):
 class NepOpts(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("rank_tol", c_double), ("basis_tol", c_double), ("refine_tol", c_double),
                 ("step_tol", c_double), ("refine_max", c_int32), ("eig_tol", c_double), ("newton_max", c_int32),
-                ("newton_tol", c_double), ("seed", ctypes.c_uint64), ("symmetric", c_int32)]
+                ("newton_tol", c_double), ("seed", ctypes.c_uint64), ("symmetric", c_int32),
+                ("newton_abandon", c_int32), ("refine_extrapolate", c_int32)]
 
 
 class NepNleigsOpts(ctypes.Structure):
@@ -62,7 +63,8 @@ class NepResultInfo(ctypes.Structure):
                 ("max_sweeps", c_int32), ("svd_sweeps", c_int32), ("flags", c_int32), ("max_backward", c_double),
                 ("ms_assemble", c_double), ("ms_factor", c_double), ("ms_solve", c_double),
                 ("ms_moments", c_double), ("ms_extract", c_double), ("ms_total", c_double),
-                ("ms_queued", c_double), ("ms_latency", c_double)]
+                ("ms_queued", c_double), ("ms_latency", c_double), ("newton_failed", c_int32),
+                ("newton_left", c_int32)]
 
 
 # name -> (restype, argtypes)
@@ -80,6 +82,7 @@ SIGNATURES = {
     "nep_result_free": (c_int32, [c_void_p]),
     "nep_last_error": (ctypes.c_char_p, []),
     "nep_kernel_launches": (ctypes.c_uint64, []),
+    "nep_set_wait_limit": (c_int32, [ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "nep_server_create": (c_int32, [c_int32, ctypes.c_uint64, ctypes.POINTER(c_void_p)]),
     "nep_submit": (c_int32, [c_void_p, c_void_p, ctypes.POINTER(NepRegion), c_int32, c_int32, c_int32,
                              ctypes.POINTER(NepOpts), c_void_p, ctypes.POINTER(ctypes.c_uint64)]),

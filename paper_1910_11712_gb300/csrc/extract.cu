@@ -162,12 +162,15 @@ int zgemm(int M, int N, int K, int opA, const zd* A, int lda, const zd* B, int l
 // ------------------------------------------------------------------ grid barrier
 // Barrier for a cooperative launch (all CTAs co-resident) on a monotonically increasing
 // arrival counter: barrier number e completes once the counter reaches e * gridDim.x, so it
-// needs one atomic per CTA and no reset. Every wait is bounded: after 2^24 polls (seconds) the CTA
-// records an error and continues, and once an error is recorded no barrier waits any more.
+// needs one atomic per CTA and no reset. Every wait is bounded: after `limit` polls (2^24 by
+// default: seconds) the CTA records an error and continues, and once an error is recorded no
+// barrier waits any more. The kernels using it have data-independent loop bounds, so a wait that
+// gave up leaves wrong values but no out-of-range access; the host returns NEP_ERR_INTERNAL.
 struct GridBar {
     unsigned int* count;
     unsigned int* gen;  // unused by this barrier, kept for the work layout
     int* err;
+    long long limit;
 };
 
 __device__ __forceinline__ void grid_barrier(GridBar b, unsigned int& epoch) {
@@ -182,7 +185,7 @@ __device__ __forceinline__ void grid_barrier(GridBar b, unsigned int& epoch) {
         long long spins = 0;
         while (*vc < target) {
             if (*ve) break;  // another wait already timed out: do not add seconds per barrier
-            if (++spins > (1ll << 24)) {
+            if (++spins > b.limit) {
                 atomicExch(b.err, 1);
                 break;
             }
@@ -441,7 +444,7 @@ int jacobi_svd(int rows, int cols, zd* A, zd* U, zd* W, double* sigma, JacobiWor
     int per_sm = 0;
     NEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, tpb, 0));
     int blocks = std::max(1, std::min(P / 2, sms * std::max(per_sm, 1)));
-    GridBar gb{w.bar, w.bar + 1, w.err};
+    GridBar gb{w.bar, w.bar + 1, w.err, wait_limit()};
     int max_sweeps = 40;
     // columns count as orthogonal once |a_p^H a_q| <= rows * eps * |a_p| |a_q|: below that the
     // rotation angle is rounding noise
@@ -652,7 +655,7 @@ int qrcp_jacobi_svd(int n, zd* A, zd* U, zd* W, double* sigma, zd* work1, zd* wo
     int per_sm = 0;
     NEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qrcp_kernel, 32, 0));
     int blocks = std::max(1, std::min(n, sms * std::max(per_sm, 1)));
-    GridBar gb{w.bar, w.bar + 1, w.err};
+    GridBar gb{w.bar, w.bar + 1, w.err, wait_limit()};
     int rows = n, cols = n;
     double stop2 = trunc * trunc;
     void* args[] = {&rows, &cols, &A, &tau, &perm, &nrm2, &stop2, &steps_dev, &gb};
@@ -1357,7 +1360,7 @@ template <int MB>  // rows per lane in the elimination: K1 <= 32 MB
 __global__ void __launch_bounds__(256, 1) newton_kernel(SplitDev s, int k, const zd* __restrict__ Bs,
                                                      const zf* __restrict__ Bs32, const zd* __restrict__ lam0,
                                                      const zd* __restrict__ Y0, int ldy0, zd c, double rad, double ea,
-                                                     double eb, int maxit,
+                                                     double eb, int maxit, int abandon,
                                                      double tol, zd* __restrict__ lam_out, zd* __restrict__ Yout,
                                                      int* __restrict__ ok_out, int* __restrict__ its_out,
                                                      unsigned char* __restrict__ gscratch, int use_smem) {
@@ -1609,14 +1612,17 @@ __global__ void __launch_bounds__(256, 1) newton_kernel(SplitDev s, int k, const
             const zd nl = lam_s + dl;
             lam_s = nl;
             const double al = hypot(nl.re, nl.im), ad = hypot(dl.re, dl.im);
+            // st: 1 converged, 2 failed (not finite, zero iterate), 3 left the region (beyond the
+            // disc |l - c| <= rad, or unconverged after `abandon` steps and outside Gamma by 10%:
+            // a shortcut for candidates whose iterates end outside, where acceptance drops them;
+            // abandon = 0 turns it off)
             int st = 0;
-            if (!isfinite(nl.re) || !isfinite(nl.im) || hypot(nl.re - c.re, nl.im - c.im) > rad || !(t > 0)) st = 2;
+            if (!isfinite(nl.re) || !isfinite(nl.im) || !(t > 0)) st = 2;
+            else if (hypot(nl.re - c.re, nl.im - c.im) > rad) st = 3;
             else if (fp64 && ad <= tol * fmax(1.0, al)) st = 1;
-            // unconverged after 8 steps and still outside Gamma by 10%: abandoned (these
-            // candidates only end outside, and they are the ones that take the most steps)
-            if (st == 0 && it >= 8) {
+            if (st == 0 && abandon > 0 && it >= abandon) {
                 const double qx = (nl.re - c.re) / ea, qy = (nl.im - c.im) / eb;
-                if (qx * qx + qy * qy > 1.21) st = 2;
+                if (qx * qx + qy * qy > 1.21) st = 3;
             }
             if (!fp64 && (ad <= 1e-5 * fmax(1.0, al) || (it > 2 && ad > 0.5 * dprev_s && ad <= 1e-3 * fmax(1.0, al))))
                 fp64_s = 1;
@@ -1631,6 +1637,7 @@ __global__ void __launch_bounds__(256, 1) newton_kernel(SplitDev s, int k, const
         }
         __syncthreads();
         if (stop_s == 2) { ok = 0; break; }
+        if (stop_s == 3) { ok = 2; break; }
         if (stop_s == 1) break;
     }
     for (int i = tid; i < k; i += blockDim.x) Yout[(int64_t)cand * k + i] = y[i];
@@ -1642,7 +1649,7 @@ __global__ void __launch_bounds__(256, 1) newton_kernel(SplitDev s, int k, const
 }
 
 int launch_newton(const SplitDev& s, int k, int ncand, const zd* Bs, zf* Bs32, const zd* lam0, const zd* Y0, int ldy0,
-                  zd c, double rad, double ea, double eb, int maxit, double tol, zd* lam_out, zd* Yout, int* ok,
+                  zd c, double rad, double ea, double eb, int maxit, int abandon, double tol, zd* lam_out, zd* Yout, int* ok,
                   int* its, unsigned char* gscratch, cudaStream_t st) {
     if (ncand <= 0) return NEP_OK;
     const int64_t nb = (int64_t)s.nterms * k * k;
@@ -1653,7 +1660,7 @@ int launch_newton(const SplitDev& s, int k, int ncand, const zd* Bs, zf* Bs32, c
     if (!use_smem && !gscratch) return NEP_ERR_INTERNAL;
     auto run = [&](auto kern) -> int {
         if (use_smem) NEP_CUDA(allow_max_dynamic_smem(kern));
-        kern<<<ncand, 256, use_smem ? bytes : 0, st>>>(s, k, Bs, Bs32, lam0, Y0, ldy0, c, rad, ea, eb, maxit, tol,
+        kern<<<ncand, 256, use_smem ? bytes : 0, st>>>(s, k, Bs, Bs32, lam0, Y0, ldy0, c, rad, ea, eb, maxit, abandon, tol,
                                                        lam_out, Yout, ok, its, gscratch, use_smem);
         NEP_CHECK_LAUNCH();
         return NEP_OK;
@@ -1707,7 +1714,8 @@ __global__ void __launch_bounds__(256) eta_kernel(SplitDev s, const zd* __restri
     }
 }
 
-// Keep candidates inside the ellipse with eta <= eig_tol and a converged Newton run; drop
+// Keep candidates inside the ellipse with eta <= eig_tol and a Newton run that neither failed nor
+// left the region (ok == 1); drop
 // duplicates (|dl| <= 1e-10 max(1,|l|) and |x_a^H x_b| >= 1 - 1e-8; keep the smaller eta);
 // order by (Re, Im). order_out[0] = count, then the selected candidate indices.
 __global__ void select_kernel(int ncand, const zd* __restrict__ lam, const double* __restrict__ eta,
@@ -1721,7 +1729,7 @@ __global__ void select_kernel(int ncand, const zd* __restrict__ lam, const doubl
     for (int a = 0; a < ncand; ++a) {
         const zd d = lam[a] - c;
         const double q = (d.re / ea) * (d.re / ea) + (d.im / eb) * (d.im / eb);
-        if (ok[a] && q < 1.0 && eta[a] <= eig_tol) byeta[nk++] = a;
+        if (ok[a] == 1 && q < 1.0 && eta[a] <= eig_tol) byeta[nk++] = a;
     }
     // insertion sort by eta (stable)
     for (int i = 1; i < nk; ++i) {

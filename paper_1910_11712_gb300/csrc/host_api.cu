@@ -19,6 +19,8 @@ static thread_local std::string g_last_error;
 static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static std::atomic<long long> g_wait_limit{1ll << 24};
+long long wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
     char buf[1024];
@@ -365,11 +367,20 @@ extern "C" void nep_opts_default(nep_opts* o) {
     o->newton_tol = 1e-14;
     o->seed = 0;
     o->symmetric = 0;
+    o->newton_abandon = 8;
+    o->refine_extrapolate = 1;
 }
 
 extern "C" const char* nep_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" uint64_t nep_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+extern "C" int nep_set_wait_limit(int64_t polls, int64_t* previous) {
+    if (polls < 0) { set_error("nep_set_wait_limit: polls must be >= 0"); return NEP_ERR_ARG; }
+    const long long old = g_wait_limit.exchange((long long)polls);
+    if (previous) *previous = old;
+    return NEP_OK;
+}
 
 // ============================================================================ region checks
 typedef std::complex<double> C;
@@ -792,12 +803,13 @@ static int run_solves(nep_plan* p, cudaStream_t st) {
     NEP_TRY(launch_fill_int(N, p->active, 1, st));
     NEP_CUDA(cudaMemsetAsync(p->prev, 0, sizeof(double) * N, st));
     NEP_CUDA(cudaMemsetAsync(p->sweeps, 0, sizeof(int) * N, st));
+    NEP_TRY(launch_drop_singular(N, n, L, p->info, p->Y, p->active, p->beta, st));
     for (int sweep = 0; sweep < p->o.refine_max; ++sweep) {
         NEP_TRY(launch_split_residual(s, N, p->tval, L, p->V, p->Y, p->R, p->nrm, p->active, st));
         NEP_TRY(launch_refine_prepare<T>(N, n, L, p->R, D, p->active, st));
         NEP_TRY(launch_band_solve<T>(s, N, ab, ut, p->ipiv, L, D, p->active, st));
         NEP_TRY(launch_refine_update<T>(N, n, L, D, p->Y, p->dmax, p->ymax, p->active, st));
-        NEP_TRY(launch_refine_decide(N, L, sweep, p->o.refine_max, p->o.refine_tol, p->o.step_tol, p->nrm, p->tnorm,
+        NEP_TRY(launch_refine_decide(N, L, sweep, p->o.refine_max, p->o.refine_tol, p->o.step_tol, p->o.refine_extrapolate, p->nrm, p->tnorm,
                                      p->dmax, p->ymax, p->prev, p->beta, p->active, p->sweeps, p->nactive, st));
         NEP_CUDA(cudaMemcpyAsync(p->h_pinned, p->nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
         NEP_CUDA(cudaStreamSynchronize(st));
@@ -875,7 +887,7 @@ static int run_extract(nep_plan* p, cudaStream_t st) {
     // Newton from every Hankel candidate
     const double rad = 4.0 * std::max(p->reg.a, p->reg.b);
     NEP_TRY(launch_newton(s, kb, m, p->Bs, p->bs32, p->cand, p->Y0, kb, mk(p->reg.center_re, p->reg.center_im), rad,
-                          p->reg.a, p->reg.b, p->o.newton_max, p->o.newton_tol, p->lamn, p->Yn, p->ok, p->its,
+                          p->reg.a, p->reg.b, p->o.newton_max, p->o.newton_abandon, p->o.newton_tol, p->lamn, p->Yn, p->ok, p->its,
                           p->newton_scratch, st));
     // eigenvectors, residuals, selection
     NEP_TRY(zgemm(n, m, kb, 0, p->Q, n, p->Yn, kb, p->Xc, n, p->part, p->part_elems, st));
@@ -1269,8 +1281,12 @@ extern "C" int nep_plan_result(nep_plan_t p, nep_result_t* out) {
         if (info[j]) flags |= NEP_WARN_SINGULAR_NODE;
     }
     if (p->m == LM) flags |= NEP_WARN_SATURATED;
-    for (int c = 0; c < p->m && p->kb > 0; ++c)
-        if (!ok[c]) flags |= NEP_WARN_NEWTON;
+    int nfail = 0, nleft = 0;
+    for (int c = 0; c < p->m && p->kb > 0; ++c) {
+        nfail += ok[c] == 0;
+        nleft += ok[c] == 2;
+    }
+    if (nfail) flags |= NEP_WARN_NEWTON;
     r->flags = flags;
     nep_result_info_t& in = r->info;
     in.n = n;
@@ -1285,6 +1301,8 @@ extern "C" int nep_plan_result(nep_plan_t p, nep_result_t* out) {
     in.svd_sweeps = p->svd_sweeps;
     in.flags = flags;
     in.max_backward = mb;
+    in.newton_failed = nfail;
+    in.newton_left = nleft;
     float t[5] = {0, 0, 0, 0, 0};
     for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&t[i], p->ev[i], p->ev[i + 1]);
     in.ms_assemble = t[0];

@@ -184,6 +184,8 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
         if (e_ != cudaSuccess) return ::nep::cuda_fail(e_, #call, __FILE__, __LINE__); \
     } while (0)
 void count_launch();
+// polls a device-side wait makes before it gives up and records an error (nep_set_wait_limit)
+long long wait_limit();
 #define NEP_CHECK_LAUNCH()         \
     do {                           \
         ::nep::count_launch();     \
@@ -263,7 +265,8 @@ int launch_refine_prepare(int npts, int n, int L, const zd* R, cx<T>* D, const i
 template <typename T>
 int launch_refine_update(int npts, int n, int L, const cx<T>* D, zd* Y, double* dmax, double* ymax,
                          const int* active, cudaStream_t st);
-int launch_refine_decide(int npts, int L, int sweep, int max_sweeps, double tol, double step_tol, const double* nrm,
+int launch_refine_decide(int npts, int L, int sweep, int max_sweeps, double tol, double step_tol, int extrapolate,
+                         const double* nrm,
                          const double* tnorm, const double* dmax, const double* ymax, double* prev, double* beta,
                          int* active, int* sweeps, int* nactive, cudaStream_t st);
 // moments.cu
@@ -291,12 +294,13 @@ int small_eig_fast(int m, const zd* A, zd* eval, zd* evec, int* status, void* gb
 size_t newton_scratch_bytes(int k, int nterms);
 int launch_pchol(int m, const zd* G, double tol2, int* rank_out, zd* Z, zd* gwork, cudaStream_t st);
 int launch_newton(const SplitDev& s, int k, int ncand, const zd* Bs, zf* Bs32, const zd* lam0, const zd* Y0, int ldy0,
-                  zd c, double rad, double ea, double eb, int maxit, double tol, zd* lam_out, zd* Yout, int* ok,
+                  zd c, double rad, double ea, double eb, int maxit, int abandon, double tol, zd* lam_out, zd* Yout, int* ok,
                   int* its, unsigned char* gscratch, cudaStream_t st);
 int launch_scale_cols(int rows, int cols, zd* X, int ld, const double* s, int mode, cudaStream_t st);
 int launch_scale_rows(int rows, int cols, zd* X, int ld, const double* s, cudaStream_t st);
 int launch_candidates(int m, const zd* theta, zd c, double a, zd* lam, cudaStream_t st);
 int launch_fill_int(int n, int* p, int v, cudaStream_t st);
+int launch_drop_singular(int npts, int n, int L, const int* info, zd* Y, int* active, double* beta, cudaStream_t st);
 int launch_rank(int n, const double* sigma, double tol, int* out, cudaStream_t st);
 int launch_normalize_columns(int rows, int cols, zd* X, int fix_phase, double* nrm, cudaStream_t st);
 int launch_term_spmm(const SplitDev& s, int k, const zd* Q, zd* out, cudaStream_t st);

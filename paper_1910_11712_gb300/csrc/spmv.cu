@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256) update_kernel(int64_t per_point, const cx
 }
 
 // One thread per point: backward error of the residual just measured, stop rule, counters.
-__global__ void decide_kernel(int npts, int L, int sweep, int max_sweeps, double tol, double step_tol,
+__global__ void decide_kernel(int npts, int L, int sweep, int max_sweeps, double tol, double step_tol, int extrapolate,
                               const double* __restrict__ nrm, const double* __restrict__ tnorm,
                               const double* __restrict__ dmax, const double* __restrict__ ymax,
                               double* __restrict__ prev, double* __restrict__ beta_out, int* __restrict__ active,
@@ -146,10 +146,11 @@ __global__ void decide_kernel(int npts, int L, int sweep, int max_sweeps, double
     beta_out[j] = beta;
     sweeps[j] = sweep + 1;
     // prev starts at 0, read as "no previous correction". Converged: backward error at the target
-    // and either the correction is at the FP64 level, or the contraction seen so far (d / prev)
-    // puts the next correction there (the error left after this one), or it stopped halving
+    // and either the correction is at the FP64 level or it stopped halving. With extrapolate set,
+    // a sweep is also saved when the contraction seen so far (d / prev) puts the next correction
+    // at the FP64 level (the error left after this one): a shortcut, not a different target
     const double pv = prev[j];
-    const bool small = d <= step_tol || (pv > 0 && d <= 0.5 * pv && d * (d / pv) <= step_tol);
+    const bool small = d <= step_tol || (extrapolate && pv > 0 && d <= 0.5 * pv && d * (d / pv) <= step_tol);
     const bool conv = beta <= tol && (small || (pv > 0 && d > 0.5 * pv));
     prev[j] = d;
     if (conv || sweep + 1 >= max_sweeps) {
@@ -157,6 +158,26 @@ __global__ void decide_kernel(int npts, int L, int sweep, int max_sweeps, double
     } else {
         atomicAdd(nactive, 1);
     }
+}
+
+// A node whose factorisation met an exactly zero pivot (info != 0: T(z_j) singular, an eigenvalue
+// on the contour at that node) has no resolvent to sample: its Y_j is set to zero, so it drops out
+// of the moment sums, and it takes no refinement sweeps. One CTA per point.
+__global__ void drop_singular_kernel(int npts, int64_t nl, const int* __restrict__ info, zd* __restrict__ Y,
+                                     int* __restrict__ active, double* __restrict__ beta) {
+    const int j = blockIdx.x;
+    if (!info[j]) return;
+    for (int64_t e = threadIdx.x; e < nl; e += blockDim.x) Y[(int64_t)j * nl + e] = mk(0.0, 0.0);
+    if (threadIdx.x == 0) {
+        active[j] = 0;
+        beta[j] = 0.0;
+    }
+}
+int launch_drop_singular(int npts, int n, int L, const int* info, zd* Y, int* active, double* beta, cudaStream_t st) {
+    if (npts <= 0) return NEP_OK;
+    drop_singular_kernel<<<npts, 256, 0, st>>>(npts, (int64_t)n * L, info, Y, active, beta);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
 }
 
 template <typename T>
@@ -191,11 +212,13 @@ int launch_refine_update(int npts, int n, int L, const cx<T>* D, zd* Y, double* 
     NEP_CHECK_LAUNCH();
     return NEP_OK;
 }
-int launch_refine_decide(int npts, int L, int sweep, int max_sweeps, double tol, double step_tol, const double* nrm,
+int launch_refine_decide(int npts, int L, int sweep, int max_sweeps, double tol, double step_tol, int extrapolate,
+                         const double* nrm,
                          const double* tnorm, const double* dmax, const double* ymax, double* prev, double* beta,
                          int* active, int* sweeps, int* nactive, cudaStream_t st) {
     NEP_CUDA(cudaMemsetAsync(nactive, 0, sizeof(int), st));
-    decide_kernel<<<ceil_div(npts, 128), 128, 0, st>>>(npts, L, sweep, max_sweeps, tol, step_tol, nrm, tnorm, dmax,
+    decide_kernel<<<ceil_div(npts, 128), 128, 0, st>>>(npts, L, sweep, max_sweeps, tol, step_tol, extrapolate, nrm,
+                                                      tnorm, dmax,
                                                       ymax, prev, beta, active, sweeps, nactive);
     NEP_CHECK_LAUNCH();
     return NEP_OK;

@@ -184,3 +184,43 @@ def test_invalid_arguments_rejected(bnd):
         with pytest.raises(bnd.NepError) as e:
             bnd.Plan(split, p.region, N, L, M)
         assert e.value.code == bnd.NEP_ERR_ARG
+
+
+def _run_opts(bnd, p, V, precision, L=None, **opts):
+    torch = torch_cuda()
+    L = L or p.L
+    split = bnd.Split.from_problem(p)
+    plan = bnd.Plan(split, p.region, p.N, L, p.M, precision=precision, **opts)
+    plan.execute(to_dev(np.asfortranarray(V), torch))
+    torch.cuda.synchronize()
+    res = plan.result()
+    res["plan"] = plan
+    return res
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("case", ["diag_delay_s8_L2", "delay1d_n64_wide", "drude_small"])
+def test_device_shortcuts_do_not_change_results(bnd, precision, case):
+    """The device's two shortcuts (Newton iterates given up outside Gamma after 8 steps; a refinement
+    sweep saved when the observed contraction puts the next correction below the step tolerance)
+    return the same eigenvalues as the device without them and as the plain oracle, which has
+    neither. The first case is the one whose only Newton path to lambda = -0.3211 lies outside
+    Gamma at step 3; a shortcut taken too early would lose it."""
+    if case == "diag_delay_s8_L2":
+        p, L = synth.diagonal_delay(n=8, seed=8), 2
+    elif case == "delay1d_n64_wide":
+        p, L = synth.config_problem("delay1d_n64_wide"), None
+    else:
+        p, L = synth.dense_drude_small(n=6, seed=0), None
+    L = L or p.L
+    V = synth.random_probe_block(p.n, L, 0)
+    ora = ciss.solve(p, V=V, L=L)
+    fast = _run_opts(bnd, p, V, precision, L=L)
+    plain = _run_opts(bnd, p, V, precision, L=L, newton_abandon=0, refine_extrapolate=0)
+    for res in (fast, plain):
+        err, _ = match_eigenvalues(res["lam"], ora["lam"])
+        assert err <= EIG_TOL, err
+        assert not (res["flags"] & bnd.NEP_WARN_NEWTON), res["info"]
+    err, _ = match_eigenvalues(fast["lam"], plain["lam"])
+    assert err <= EIG_TOL
+    assert fast["info"]["max_sweeps"] <= plain["info"]["max_sweeps"]

@@ -197,6 +197,9 @@ int launch_band_lu(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info,
     const int kv = s.kl + s.ku;
     // register window, one barrier per step (lu_col.cu): kl <= 64, kv <= 128
     if (band_lu_col_fits(s.kl, s.ku)) return launch_band_lu_col<T>(s, npts, ab, ipiv, info, active, st);
+    // wide bands in complex64: trailing updates on the tensor core
+    if constexpr (sizeof(T) == 4)
+        if (lu_tc_enabled() && band_lu_tc_fits(s.kl)) return launch_band_lu_tc(s, npts, ab, ipiv, info, active, st);
     // wide bands: blocked LU with the trailing window in global memory
     if (s.kl >= 1 && band_lu_wide_fits(s.kl, (int)sizeof(cx<T>)))
         return launch_band_lu_wide<T>(s, npts, ab, ipiv, info, active, st);

@@ -235,6 +235,13 @@ bool band_lu_wide_fits(int kl, int elem_bytes);
 template <typename T>
 int launch_band_lu_wide(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active,
                         cudaStream_t st);
+// The same blocked LU in complex64 with the trailing update on the tensor core (lu_tc.cu): TMA-staged
+// operand tiles, tcgen05 MMA (TF32 hi/lo split, 4M complex form) into tensor memory. kl > 64.
+bool band_lu_tc_fits(int kl);
+int launch_band_lu_tc(const SplitDev& s, int npts, zf* ab, int* ipiv, int* info, const int* active, cudaStream_t st);
+// Whether complex64 wide-band LUs use the tensor-core kernel (default yes; NEP_LU_TC=0 selects the
+// FP32 SIMT kernel, for comparisons).
+bool lu_tc_enabled();
 template <typename T>
 int launch_band_lu(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st);
 // Narrow-band substitution sweeps (register windows of kl+1 and kl+ku+1 rows, up to 288).

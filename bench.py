@@ -144,6 +144,120 @@ def fp64_alu_peak_tflops(sm_mhz):
     return 152 * 1.75 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def tf32_peak_tflops(peaks):
+    """TF32 dense tensor peak: the measured bf16 burst figure x the nominal TF32/bf16 ratio (1.125/2.25)."""
+    return peaks.get("bf16_tflops", 1900.0) * 0.5
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def arm_bench(binding, p, prec, V, streams, steps, warmup):
+    """Throughput of one workload at one precision: `streams` independent pipelines (a plan, a
+    non-blocking stream and a host thread each), `steps` full passes in all, CUDA events around them;
+    then one pass alone for the latency and the per-stage device times."""
+    import torch
+    split = binding.Split.from_problem(p)
+    S = max(1, min(streams, steps))
+    plans = [binding.Plan(split, p.region, p.N, p.L, p.M, precision=prec) for _ in range(S)]
+    strs = [torch.cuda.Stream() for _ in range(S)]
+    Vd = torch.from_numpy(np.asfortranarray(V).ravel(order="F").view(np.float64).copy()).cuda()
+    for i in range(S):
+        for _ in range(max(1, warmup)):
+            plans[i].execute(Vd, strs[i].cuda_stream)
+    torch.cuda.synchronize()
+
+    def run(i):
+        for _ in range(i, steps, S):
+            plans[i].execute(Vd, strs[i].cuda_stream)
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for st_ in strs:
+        st_.wait_event(e0)
+    th = [threading.Thread(target=run, args=(i,)) for i in range(S)]
+    for t_ in th:
+        t_.start()
+    for t_ in th:
+        t_.join()
+    for st_ in strs:
+        ev = torch.cuda.Event()
+        ev.record(st_)
+        torch.cuda.current_stream().wait_event(ev)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    plans[0].execute(Vd, strs[0].cuda_stream)
+    torch.cuda.synchronize()
+    r = plans[0].result()
+    info = r["info"]
+    out = {"ms_per_step": ms, "value": p.N / (ms * 1e-3), "streams": S, "steps": steps,
+           "single_pass_ms": info["ms_total"],
+           "stages_ms": {k: info[k] for k in ("ms_assemble", "ms_factor", "ms_solve", "ms_moments", "ms_extract")},
+           "result": {"nconv": int(len(r["lam"])), "hankel_rank": r["m"], "max_backward": info["max_backward"],
+                      "max_sweeps": info["max_sweeps"], "flags": r["flags"],
+                      "max_eta": float(r["eta"].max()) if len(r["eta"]) else None}}
+    for pl in plans:
+        pl.close()
+    split.close()
+    return out
+
+
+def wide_config_bench(binding, name, peaks, streams, steps, rank=0):
+    """A wide-band workload (Drude 128x128, bandwidth 128; square root 24^3, bandwidth 576): the
+    mixed path (complex64 factors with the tensor-core trailing update, FP64 refinement) over
+    `streams` pipelines, one plain FP64 pass beside it, and the roofline of its dominant kernel,
+    the banded LU: algorithmic flops 8 n kl (kl+ku) per point over the LU's device time against the
+    TF32 tensor peak; the tensor work executed is 3x that (the hi/lo split's three products)."""
+    import synth
+    p = synth.config_problem(name, seed=rank)
+    V = synth.random_probe_block(p.n, p.L, rank)
+    split = binding.Split.from_problem(p)
+    kl, ku = split.kl, split.ku
+    split.close()
+    mixed = arm_bench(binding, p, binding.NEP_PREC_MIXED, V, streams, steps, 1)
+    fp64 = arm_bench(binding, p, binding.NEP_PREC_FP64, V, 1, 1, 1)
+    lu_ms = mixed["stages_ms"]["ms_factor"]
+    fl = lu_flops(p.n, kl, ku, p.N)
+    peak = tf32_peak_tflops(peaks)
+    ach = fl / (lu_ms * 1e-3) / 1e12
+    return {"workload": name, "n": p.n, "bandwidth": kl, "N": p.N, "L": p.L, "M": p.M,
+            "ms_per_step": mixed["ms_per_step"], "value": mixed["value"], "unit": UNIT, "mixed": mixed,
+            "fp64": fp64, "mixed_over_fp64": mixed["value"] / fp64["value"],
+            "roofline": {"kernel": "lu_tc_kernel (banded LU, trailing update on tcgen05 kind::tf32)", "bound": "tensor",
+                         "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "executed_tensor_frac": 3 * ach / peak, "traffic": None,
+                         "ms_per_launch": lu_ms, "algorithmic_flops": fl,
+                         "peak_source": "measured bf16 burst (MEASURED_PEAKS.json) x nominal TF32/bf16 ratio 0.5"}}
+
+
+def cpu_sample_points(p, npts, threads):
+    """The oracle's quadrature solves (assembly, band LU, solves, FP64 refinement) at the first npts
+    nodes, with `threads` threads over points; returns solves per second."""
+    from oracle import ciss
+    import synth
+    import concurrent.futures as cf
+    from oracle import band, contour
+    V = synth.random_probe_block(p.n, p.L, 0)
+    z, _, _ = contour.nodes(p.region, p.N)
+    F = contour.coefficient_table(p.fns, z)
+    kl, ku = band.bandwidths(p.mats)
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(threads) as ex:
+        list(ex.map(lambda j: ciss.solve_point(p, kl, ku, F[:, j], V), range(npts)))
+    return npts / (time.perf_counter() - t0)
+
+
 def cpu_baseline(p, steps_budget_s=20.0):
     """The oracle as it stands on this host's cores: full passes of the same workload until ~budget."""
     from oracle import ciss
@@ -159,8 +273,12 @@ def cpu_baseline(p, steps_budget_s=20.0):
             break
     cores = max(1, min(32, os.cpu_count() or 1))
     out = {"value": p.N * len(times) / sum(times), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "cpu_model": cpu_model(), "nproc": os.cpu_count(),
            "sample": f"{len(times)} full CPU passes of {p.name} (N={p.N} quadrature solves each), "
                      f"threads over quadrature points, {sum(times):.1f} s total"}
+    # one thread: the quadrature solves alone at the first 4 nodes (they are ~all of a pass's time)
+    out["one_thread"] = {"value": cpu_sample_points(p, 4, 1), "unit": UNIT,
+                         "sample": f"quadrature solves at 4 of the {p.N} nodes of {p.name}, one thread"}
     # the oracle's residual inverse iteration on the same operator: one pair from a seeded start at
     # the region's centre, three iterations without a stopping tolerance (one band LU at sigma, then
     # per iteration the inner Newton loop's solves and the update's)
@@ -179,9 +297,8 @@ def serving_bench(binding, prec, count, seed, workers, s_max, loads=(0.5, 0.8, 1
     s_max^2, N in {32,64,128}, L in {8,16,32}, M = 8). Capacity is the request rate of the whole
     sample submitted at once; the stream is then replayed in real time at offered loads rho x
     capacity (Poisson inter-arrival gaps rescaled). Latency = submission to result ready.
-    Baseline: plain FP64, one request at a time, every request's service time measured alone; its
-    latencies at each offered load come from a first-in-first-out replay of the same arrival
-    times with those service times.
+    Baseline: plain FP64, one request at a time (a server with one worker), replayed under the same
+    arrival times and measured the same way.
     """
     import synth
     reqs = synth.serving_requests(count=count, seed=seed, s_max=s_max)
@@ -192,20 +309,11 @@ def serving_bench(binding, prec, count, seed, workers, s_max, loads=(0.5, 0.8, 1
     gaps = np.diff([0.0] + [r["arrival"] for r in reqs])
     gaps = gaps / gaps.mean()
 
-    def submit(srv, i):
+    def submit(srv, i, pr):
         p = probs[i]
-        return srv.submit(splits[i], p.region, p.N, p.L, p.M, V=Vs[i], precision=prec)
+        return srv.submit(splits[i], p.region, p.N, p.L, p.M, V=Vs[i], precision=pr)
 
-    srv = binding.Server(workers=workers)
-    for i in range(min(4, count)):  # warm the allocator pool and the library
-        srv.wait(submit(srv, i))
-    t0 = time.perf_counter()
-    tickets = [submit(srv, i) for i in range(count)]
-    for t in tickets:
-        srv.wait(t)
-    capacity = count / (time.perf_counter() - t0)
-
-    def replay(rate):
+    def replay(srv, rate, pr):
         arrivals = np.cumsum(gaps) / rate
         t0 = time.perf_counter()
         tk = []
@@ -213,40 +321,40 @@ def serving_bench(binding, prec, count, seed, workers, s_max, loads=(0.5, 0.8, 1
             d = arrivals[i] - (time.perf_counter() - t0)
             if d > 0:
                 time.sleep(d)
-            tk.append(submit(srv, i))
+            tk.append(submit(srv, i, pr))
         lat = np.array([srv.wait(t)["info"]["ms_latency"] for t in tk])
-        return arrivals, lat, time.perf_counter() - t0
+        span = time.perf_counter() - t0
+        return {"rho": None, "offered_req_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "solves_per_s": solves / span}
 
+    srv = binding.Server(workers=workers)
+    for i in range(min(4, count)):  # warm the allocator pool and the library
+        srv.wait(submit(srv, i, prec))
+    t0 = time.perf_counter()
+    tickets = [submit(srv, i, prec) for i in range(count)]
+    for t in tickets:
+        srv.wait(t)
+    capacity = count / (time.perf_counter() - t0)
     out = {"requests": count, "workers": workers, "n_range": [min(p.n for p in probs), max(p.n for p in probs)],
            "capacity_req_per_s": capacity, "capacity_solves_per_s": capacity * solves / count, "loads": []}
     for rho in loads:
-        arrivals, lat, span = replay(rho * capacity)
-        out["loads"].append({"rho": rho, "offered_req_per_s": rho * capacity,
-                             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                             "solves_per_s": solves / span})
+        r_ = replay(srv, rho * capacity, prec)
+        r_["rho"] = rho
+        out["loads"].append(r_)
     srv.close()
-    # plain FP64, one request at a time
-    service = []
-    for i, p in enumerate(probs):
-        torch_sync()
-        a = time.perf_counter()
-        binding.ciss_solve(splits[i], p.region, p.N, p.L, p.M, V=Vs[i], precision=binding.NEP_PREC_FP64)
-        torch_sync()
-        service.append(time.perf_counter() - a)
-    service = np.array(service)
-    base = {"solves_per_s": solves / service.sum(), "mean_service_ms": 1e3 * service.mean(), "loads": []}
+    # plain FP64, one request at a time, under the same arrival times
+    srv64 = binding.Server(workers=1)
+    srv64.wait(submit(srv64, 0, binding.NEP_PREC_FP64))
+    base = {"loads": [], "measured": "a one-worker server in plain FP64, replayed under the same arrivals"}
     for rho in loads:
-        arrivals = np.cumsum(gaps) / (rho * capacity)
-        free_at, lat = 0.0, []
-        for t_arr, sv in zip(arrivals, service):
-            start = max(t_arr, free_at)
-            free_at = start + sv
-            lat.append(1e3 * (free_at - t_arr))
-        base["loads"].append({"rho": rho, "p50_ms": float(np.percentile(lat, 50)),
-                              "p99_ms": float(np.percentile(lat, 99))})
+        r_ = replay(srv64, rho * capacity, binding.NEP_PREC_FP64)
+        r_["rho"] = rho
+        base["loads"].append(r_)
+    srv64.close()
     out["fp64_one_at_a_time"] = base
-    out["sample"] = (f"first {count} requests of the seeded Poisson request stream (seed {seed}); "
-                     "loads relative to the measured mixed-precision capacity")
+    out["sample"] = (f"first {count} requests of the seeded Poisson request stream (seed {seed}; the full "
+                     "stream is 2000 requests, --serving-requests 2000); loads relative to the measured "
+                     "mixed-precision capacity")
     for sp in splits:
         sp.close()
     return out
@@ -265,12 +373,16 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="delay2d_s64")
+    ap.add_argument("--points", type=int, default=0,
+                    help="override the workload's quadrature points (small cases for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-symmetric", action="store_true")
     ap.add_argument("--no-polish", action="store_true")
     ap.add_argument("--no-nleigs", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 arm on the same workload")
+    ap.add_argument("--no-wide", action="store_true", help="skip the bandwidth-128 and -576 workloads")
     ap.add_argument("--streams", type=int, default=8,
                     help="concurrent pipelines in the timed region: one plan, stream and host thread each")
     ap.add_argument("--serving-requests", type=int, default=40)
@@ -279,6 +391,8 @@ def main():
     rank, world, local = dist_env()
     import synth
     p = synth.config_problem(args.workload, seed=rank)
+    if args.points > 0:
+        p.N = args.points
 
     if args.impl == "reference":
         if rank != 0:
@@ -559,6 +673,17 @@ def main():
                       f"{Ke} requests",
                "single_call": {"value": p.N / (sum(tt) / len(tt)), "api": "nep_create_split + nep_ciss_solve"}}
 
+    # the plain FP64 GPU path on the same workload (the metric's comparison arm), same concurrency
+    fp64_arm = None
+    if not args.no_fp64 and prec == binding.NEP_PREC_MIXED:
+        fp64_arm = arm_bench(binding, p, binding.NEP_PREC_FP64, V, S, args.steps, args.warmup)
+        fp64_arm["dtype"] = "f64"
+    # the wide-band workloads (bandwidth 128 and 576), where the LU runs on the tensor core
+    wide = {}
+    if not args.no_wide and prec == binding.NEP_PREC_MIXED:
+        for key, name, steps_w in (("c3", "drude2d_s128", 8), ("c4", "sqrt3d_s24", 4)):
+            wide[key] = wide_config_bench(binding, name, measured_peaks(), 4, steps_w, rank)
+
     line = None
     if rank == 0:
         peaks = measured_peaks()
@@ -580,7 +705,8 @@ def main():
             "single_stream": {"ms_per_step": ms_single, "value": world * p.N / (ms_single * 1e-3)},
             "vs_baseline": None, "dtype": "c64+f64" if mixed else "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "n": p.n, "bandwidth": split.kl, "N": p.N, "L": p.L, "M": p.M,
+            "config": {"workload": args.workload + (f" with N={p.N}" if args.points > 0 else ""), "n": p.n,
+                       "bandwidth": split.kl, "N": p.N, "L": p.L, "M": p.M,
                        "precision": args.precision, "l2": "inputs larger than L2 (band factors "
                        f"{p.N * p.n * split.ldab * esz / 1e6:.0f} MB per step)",
                        "streams": S, "concurrency": f"{S} independent plans on {S} non-blocking streams, one host "
@@ -588,14 +714,17 @@ def main():
             "roofline": {"kernel": ("band_sweep_kernel x2" if split.kl + 1 <= 288 and split.kl + split.ku + 1 <= 288
                                     else "band_solve_kernel") + " (forward + backward banded substitution, "
                                    f"{p.N} points x {p.L} right-hand sides in one launch)",
-                         "bound": "alu", "achieved": s_flops / (solve_ms * 1e-3) / 1e12, "peak": alu_peak,
-                         "unit": "TFLOP/s", "frac": s_flops / (solve_ms * 1e-3) / 1e12 / alu_peak,
+                         "bound": "hbm", "achieved": s_bytes / (solve_ms * 1e-3) / 1e9, "peak": hbm,
+                         "unit": "GB/s", "frac": s_bytes / (solve_ms * 1e-3) / 1e9 / hbm,
                          "traffic": SOLVE_TRAFFIC.get((args.workload, args.precision)),
-                         "ms_per_launch": solve_ms, "peak_source": alu_src,
-                         "algorithmic": {"flops": s_flops, "bytes": s_bytes,
-                                         "hbm_gbs": s_bytes / (solve_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm,
-                                         "hbm_frac": s_bytes / (solve_ms * 1e-3) / 1e9 / hbm}},
-            "factor": {"kernel": "lu_col_kernel" if split.kl <= 64 and split.kl + split.ku <= 128 else "lu_wide_kernel",
+                         "ms_per_launch": solve_ms,
+                         "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                         "algorithmic_bytes": s_bytes,
+                         "alu": {"achieved_tflops": s_flops / (solve_ms * 1e-3) / 1e12, "peak_tflops": alu_peak,
+                                 "frac": s_flops / (solve_ms * 1e-3) / 1e12 / alu_peak, "peak_source": alu_src,
+                                 "flops": s_flops}},
+            "factor": {"kernel": "lu_col_kernel" if split.kl <= 64 and split.kl + split.ku <= 128 else
+                       ("lu_tc_kernel" if mixed else "lu_wide_kernel"),
                        "ms": lu, "achieved_tflops": lu_flops(p.n, split.kl, split.ku, p.N) / (lu * 1e-3) / 1e12,
                        "peak_tflops": alu_peak,
                        "frac": lu_flops(p.n, split.kl, split.ku, p.N) / (lu * 1e-3) / 1e12 / alu_peak},
@@ -615,10 +744,23 @@ def main():
             line["left"] = left_line
         if nleigs_line:
             line["nleigs"] = nleigs_line
+        if fp64_arm:
+            line["fp64"] = fp64_arm
+            line["mixed_over_fp64"] = value / (world * fp64_arm["value"])
+        for key, blk in wide.items():
+            line[key] = blk
         if not args.no_serving:
             line["serving"] = serving_bench(binding, prec, args.serving_requests, 0, 4, args.serving_smax)
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(p)
+            if "c3" in wide:
+                p3 = synth.config_problem("drude2d_s128", seed=0)
+                cores = max(1, min(32, os.cpu_count() or 1))
+                v3 = cpu_sample_points(p3, 2 * cores, cores)
+                line["c3"]["cpu_baseline"] = {"value": v3, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                              "sample": f"quadrature solves at {2 * cores} of the 128 nodes of "
+                                                        "drude2d_s128 (assembly, band LU, FP64 refinement), "
+                                                        f"{cores} threads over points"}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

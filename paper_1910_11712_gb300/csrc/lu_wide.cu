@@ -13,7 +13,7 @@
 //      each column is computed;
 //   2. for the trailing columns, in chunks: the panel's interchanges (composed once into one
 //      permutation of the rows involved), then U12 = L~11^{-1} A12 by forward substitution
-//      (k ascending), written to the output rows;
+//      (k ascending; a warp per column, lanes over its rows), written to the output rows;
 //   3. A22 -= L~21 U12 (k ascending) on the chunk.
 // Applying the panel's interchanges first and its eliminations after changes neither the
 // operations nor their order on any element of the trailing columns (a value ending in row r
@@ -47,8 +47,7 @@ __global__ void __launch_bounds__(512, 1)
     extern __shared__ unsigned char smem_raw[];
     cx<T>* Ps = reinterpret_cast<cx<T>*>(smem_raw);  // RW x NB panel, column-major (local rows)
     cx<T>* Us = Ps + (int64_t)RW * NB;               // NB x CHW: U12 chunk, column jc at Us[NB*jc]
-    cx<T>* Xs = Us + (int64_t)NB * CHW;              // NB x CHW: values moving into partner rows
-    int* src = reinterpret_cast<int*>(Xs + (int64_t)NB * CHW);  // RW: row permutation of the panel
+    int* src = reinterpret_cast<int*>(Us + (int64_t)NB * CHW);  // RW: row permutation of the panel
     int* plist = src + RW;                                      // partner rows (local, >= nbc)
     __shared__ int piv_sh[NB];
     __shared__ int info_s, npart_s;
@@ -171,22 +170,23 @@ __global__ void __launch_bounds__(512, 1)
         const int mr = rend - (p0 + nbc);
         for (int c0 = p0 + nbc; c0 < cend; c0 += CHW) {
             const int cw = min(CHW, cend - c0);
-            // interchanges and U12, one thread per column
-            for (int jc = tid; jc < cw; jc += nthr) {
+            // interchanges and U12, one warp per column with lane k on row p0 + k (NB <= 32):
+            // u_i -= l_ik u_k for k ascending, the substitution's order of operations
+            for (int jc = warp; jc < cw; jc += nwarp) {
                 const int q = c0 + jc;
-                cx<T>* u = Us + (int64_t)NB * jc;
-                cx<T>* x = Xs + (int64_t)NB * jc;
-                for (int k = 0; k < nbc; ++k) u[k] = W[wi(p0 + src[k], q)];
-                for (int t = 0; t < npart; ++t) x[t] = W[wi(p0 + src[plist[t]], q)];
-                for (int t = 0; t < npart; ++t) W[wi(p0 + plist[t], q)] = x[t];
-                for (int k = 0; k < nbc; ++k) {
-                    const cx<T> uk = u[k];
-                    const cx<T>* lk = Ps + (int64_t)RW * k;
-                    for (int i = k + 1; i < nbc; ++i) u[i] = fms(u[i], lk[i], uk);
+                const cx<T> u0 = lane < nbc ? W[wi(p0 + src[lane], q)] : mk<T>(0, 0);
+                const cx<T> x = lane < npart ? W[wi(p0 + src[plist[lane]], q)] : mk<T>(0, 0);
+                __syncwarp();
+                if (lane < npart) W[wi(p0 + plist[lane], q)] = x;
+                cx<T> u = u0;
+                for (int k = 0; k + 1 < nbc; ++k) {
+                    const cx<T> uk = shfl_cx(u, k);
+                    if (lane > k && lane < nbc) u = fms(u, Ps[lane + (int64_t)RW * k], uk);
                 }
-                for (int k = 0; k < nbc; ++k) {
-                    const int r = p0 + k;
-                    if (q - r <= kv) ab[(int64_t)r * ldab + (q - r)] = u[k];
+                if (lane < nbc) {
+                    Us[(int64_t)NB * jc + lane] = u;
+                    const int r = p0 + lane;
+                    if (q - r <= kv) ab[(int64_t)r * ldab + (q - r)] = u;
                 }
             }
             __syncthreads();
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(512, 1)
 // Shared memory of lu_wide_kernel for a band and panel width.
 static size_t wide_smem(int kl, int nb, int chw, size_t esz) {
     const size_t rw = (size_t)kl + nb;
-    return esz * (rw * nb + 2 * (size_t)nb * chw) + sizeof(int) * (rw + nb);
+    return esz * (rw * nb + (size_t)nb * chw) + sizeof(int) * (rw + nb);
 }
 
 template <typename T, int NB>

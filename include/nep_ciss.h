@@ -75,11 +75,34 @@ typedef struct {
  *                    first (nnum, nden coefficients); nden == 0 means q = 1.
  *   NEP_FN_EXP       h(x) = exp(x).
  *   NEP_FN_SQRT      h(x) = sqrt(x - shift), principal branch (cut on x - shift <= 0).
- *   NEP_FN_COMBINE   h = a + b, a * b, a / b or a(b(.)) (op), a and b nested nep_fn. */
+ *   NEP_FN_COMBINE   h = a + b, a * b, a / b or a(b(.)) (op), a and b nested nep_fn.
+ *   NEP_FN_CALLBACK  g is the user's host function eval (the callback form of Sec. 3.2.1): eval(z, count,
+ *                    f, df, ctx) writes g(z_k) to f and g'(z_k) to df (complex arrays of count entries,
+ *                    interleaved re, im; df may be NULL, then only f is wanted). alpha, beta are not
+ *                    applied. The library copies eval and ctx and calls eval on the host only: at plan
+ *                    creation for the quadrature nodes, and during the extraction step for the Newton
+ *                    iterates and the returned eigenvalues (one call per term per Newton step, all
+ *                    candidates at once); under the request server, from its worker threads (eval must
+ *                    then be thread-safe). Device code never evaluates such a term: the projected
+ *                    Newton steps run one per launch with the values passed in (slower than the
+ *                    all-device path).
+ *   NEP_FN_TABLE     g tabulated at the quadrature nodes of one solve: table holds table_count = N
+ *                    complex values (interleaved), g(z_j) for the nodes z_j of nep_nodes(region, N)
+ *                    in order; a solve with another N returns NEP_ERR_ARG. Values off the nodes (g and
+ *                    g' at Newton iterates and eigenvalues) come from eval, which must then be given:
+ *                    a table term without eval makes nep_plan_create / nep_ciss_solve return
+ *                    NEP_ERR_UNSUPPORTED (the band assembly and solve entry points take coefficient
+ *                    tables directly).
+ * CALLBACK and TABLE terms appear only at the top level of a term (not inside COMBINE). Entry points
+ * that evaluate the functions on the device elsewhere (nep_rii, nep_plan_polish, nep_left_eigvecs,
+ * nep_plan_left, nep_nleigs_*) return NEP_ERR_UNSUPPORTED for a split with such terms. */
 #define NEP_FN_RATIONAL 0
 #define NEP_FN_EXP 1
 #define NEP_FN_SQRT 2
 #define NEP_FN_COMBINE 3
+#define NEP_FN_CALLBACK 4
+#define NEP_FN_TABLE 5
+typedef void (*nep_fn_eval_t)(const double *z, int32_t count, double *f, double *df, void *ctx);
 #define NEP_OP_ADD 0
 #define NEP_OP_MUL 1
 #define NEP_OP_DIV 2
@@ -94,6 +117,10 @@ typedef struct nep_fn {
     int32_t op;
     const struct nep_fn *a;
     const struct nep_fn *b;
+    nep_fn_eval_t eval;      /* NEP_FN_CALLBACK, NEP_FN_TABLE (off the nodes); NULL otherwise */
+    void *ctx;               /* passed to eval                                                */
+    const double *table;     /* NEP_FN_TABLE: complex[table_count], copied at creation       */
+    int32_t table_count;
 } nep_fn;
 
 /* Ellipse Gamma: z(t) = center + a cos t + i b sin t (a: real semi-axis, b: imaginary). */
@@ -158,6 +185,13 @@ int nep_ciss_solve(nep_split_t h, const nep_region *r, int32_t N, int32_t L, int
  * Pointers stay valid until nep_result_free. */
 int nep_result_get(nep_result_t r, int32_t *nconv, const double **lambda, const double **X, const double **resid,
                    int32_t *hankel_rank, int32_t *flags);
+/* Per quadrature point (the npts nodes solved: N, or N/2 under the conjugate-symmetric option, in
+ * node order): refinement sweeps run, LU status (0, or 1 + the first column with an exactly zero
+ * pivot: that node was dropped from the moments) and the last measured normwise backward error
+ * (0 for a dropped node). Pointers (any may be NULL) stay valid until nep_result_free. Results of
+ * NLEIGS carry no points (*npts = 0). */
+int nep_result_points(nep_result_t r, int32_t *npts, const int32_t **sweeps, const int32_t **lu_info,
+                      const double **backward);
 typedef struct {
     int32_t n, N, L, M, precision;
     int32_t hankel_rank;    /* m */

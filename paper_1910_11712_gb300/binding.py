@@ -21,7 +21,7 @@ NEP_PENDING = 1
 NEP_ERR_ARG, NEP_ERR_CUDA, NEP_ERR_REGION, NEP_ERR_NOMEM, NEP_ERR_UNSUPPORTED, NEP_ERR_INTERNAL = -1, -2, -3, -4, -5, -6
 NEP_WARN_SATURATED, NEP_WARN_REFINE, NEP_WARN_SINGULAR_NODE, NEP_WARN_NEWTON = 1, 2, 4, 8
 NEP_PREC_FP64, NEP_PREC_MIXED = 0, 1
-FN_KIND = {"rational": 0, "exp": 1, "sqrt": 2, "combine": 3}
+FN_KIND = {"rational": 0, "exp": 1, "sqrt": 2, "combine": 3, "callback": 4, "table": 5}
 FN_OP = {"add": 0, "mul": 1, "div": 2, "compose": 3}
 
 
@@ -34,10 +34,14 @@ class NepFn(ctypes.Structure):
     pass
 
 
+# void eval(const double* z, int32_t count, double* f, double* df, void* ctx)
+NEP_FN_EVAL = ctypes.CFUNCTYPE(None, P_double, c_int32, P_double, P_double, c_void_p)
+
 NepFn._fields_ = [("kind", c_int32), ("alpha_re", c_double), ("alpha_im", c_double), ("beta_re", c_double),
                   ("beta_im", c_double), ("shift_re", c_double), ("shift_im", c_double), ("nnum", c_int32),
                   ("nden", c_int32), ("num", P_double), ("den", P_double), ("op", c_int32),
-                  ("a", ctypes.POINTER(NepFn)), ("b", ctypes.POINTER(NepFn))]
+                  ("a", ctypes.POINTER(NepFn)), ("b", ctypes.POINTER(NepFn)), ("eval", NEP_FN_EVAL),
+                  ("ctx", c_void_p), ("table", P_double), ("table_count", c_int32)]
 
 
 class NepRegion(ctypes.Structure):
@@ -98,6 +102,8 @@ SIGNATURES = {
     "nep_plan_buffer": (c_int32, [c_void_p, ctypes.c_char_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_size_t)]),
     "nep_nodes": (c_int32, [ctypes.POINTER(NepRegion), c_int32, c_void_p, c_void_p, c_void_p]),
     "nep_coefficients": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "nep_result_points": (c_int32, [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(ctypes.POINTER(c_int32)),
+                                    ctypes.POINTER(ctypes.POINTER(c_int32)), ctypes.POINTER(P_double)]),
     "nep_assemble_band": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "nep_band_factor": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "nep_band_solve": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
@@ -212,6 +218,23 @@ def _fn_struct(keep, spec) -> NepFn:
         den = spec.get("den")
         f.nden = 0 if den is None else len(den)
         f.den = _cplx_array(keep, den) if den is not None else P_double()
+    if spec.get("fn") is not None:
+        # host function: fn(z) -> (f, df) for a complex array z (the library calls it on the host only)
+        fn = spec["fn"]
+
+        def trampoline(zp, count, fp, dfp, ctx, fn=fn):
+            z = np.ctypeslib.as_array(zp, (2 * count,)).view(np.complex128)
+            fv, dfv = fn(z.copy())
+            np.ctypeslib.as_array(fp, (2 * count,))[:] = np.asarray(fv, np.complex128).view(np.float64)
+            if dfp:
+                np.ctypeslib.as_array(dfp, (2 * count,))[:] = np.asarray(dfv, np.complex128).view(np.float64)
+        cb = NEP_FN_EVAL(trampoline)
+        keep.refs.append(cb)
+        f.eval = cb
+    if spec["kind"] == "table":
+        vals = np.ascontiguousarray(spec["values"], dtype=np.complex128)
+        f.table = _cplx_array(keep, list(vals))
+        f.table_count = len(vals)
     if spec["kind"] == "combine":
         f.op = FN_OP[spec["op"]]
         fa, fb = _fn_struct(keep, spec["a"]), _fn_struct(keep, spec["b"])
@@ -263,6 +286,7 @@ class Split:
         h = c_void_p()
         check(lib.nep_create_split(n, len(mats), csrs, fs, ctypes.byref(h)))
         self.handle = h
+        self._keep = keep  # host callbacks must outlive the split
         self.n = n
         self.nterms = len(mats)
         info = [c_int32() for _ in range(5)]
@@ -302,8 +326,14 @@ def _result_dict(res) -> dict:
     sp_, cnt = P_double(), c_int32()
     check(lib.nep_result_hankel_sigma(res, ctypes.byref(sp_), ctypes.byref(cnt)))
     sigma = np.ctypeslib.as_array(sp_, (cnt.value,)).copy() if cnt.value else np.zeros(0)
+    npts, sw_p, li_p, be_p = c_int32(), ctypes.POINTER(c_int32)(), ctypes.POINTER(c_int32)(), P_double()
+    check(lib.nep_result_points(res, ctypes.byref(npts), ctypes.byref(sw_p), ctypes.byref(li_p), ctypes.byref(be_p)))
+    q = npts.value
+    points = {"sweeps": np.ctypeslib.as_array(sw_p, (q,)).copy() if q else np.zeros(0, np.int32),
+              "lu_info": np.ctypeslib.as_array(li_p, (q,)).copy() if q else np.zeros(0, np.int32),
+              "backward": np.ctypeslib.as_array(be_p, (q,)).copy() if q else np.zeros(0)}
     out = {"lam": lam, "X": np.asfortranarray(X), "eta": eta, "m": m.value, "flags": flags.value, "sigma": sigma,
-           "info": {f: getattr(info, f) for f, _ in NepResultInfo._fields_}}
+           "info": {f: getattr(info, f) for f, _ in NepResultInfo._fields_}, "points": points}
     lib.nep_result_free(res)
     return out
 

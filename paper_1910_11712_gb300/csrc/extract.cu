@@ -1363,7 +1363,9 @@ __global__ void __launch_bounds__(256, 1) newton_kernel(SplitDev s, int k, const
                                                      double eb, int maxit, int abandon,
                                                      double tol, zd* __restrict__ lam_out, zd* __restrict__ Yout,
                                                      int* __restrict__ ok_out, int* __restrict__ its_out,
-                                                     unsigned char* __restrict__ gscratch, int use_smem) {
+                                                     unsigned char* __restrict__ gscratch, int use_smem,
+                                                     const zd* __restrict__ fv_ext, double* __restrict__ nstate,
+                                                     int steps) {
     extern __shared__ unsigned char sraw[];
     const int cand = blockIdx.x;
     const int K1 = k + 1, nt = s.nterms;
@@ -1386,41 +1388,69 @@ __global__ void __launch_bounds__(256, 1) newton_kernel(SplitDev s, int k, const
     __shared__ double dprev_s;
     const int tid = threadIdx.x;
     const int lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+    // step mode (host-supplied functions): nstate[4 cand ..] = steps done, finished, FP64 phase,
+    // last |dlambda|; the iterate stays in this candidate's global work area between launches, and
+    // each launch runs `steps` steps with f_i, f_i' at the current iterate from fv_ext
+    double* stc = nstate ? nstate + 4 * (int64_t)cand : nullptr;
+    const int it0 = stc ? (int)stc[0] : 0;
+    if (stc && stc[1] != 0.0) return;
 
     for (int64_t e = tid; e < (int64_t)nt * k * k; e += blockDim.x) B32[e] = Bs32[e];
-    double ss = 0.0;
-    for (int i = tid; i < k; i += blockDim.x) {
-        y[i] = Y0[(int64_t)cand * ldy0 + i];
-        ss += norm2(y[i]);
-    }
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (lane == 0) redd[w] = ss;
-    __syncthreads();
-    if (tid == 0) {
-        double t = 0;
-        for (int q = 0; q < nw; ++q) t += redd[q];
-        redd[0] = t;
-        lam_s = lam0[cand];
-        stop_s = 0;
-        fp64_s = 0;
-        dprev_s = 0.0;
-    }
-    __syncthreads();
-    {
-        const double inv = redd[0] > 0 ? 1.0 / sqrt(redd[0]) : 0.0;
-        for (int i = tid; i < k; i += blockDim.x) {
-            y[i] = inv * y[i];
-            y32[i] = cvt<float>(y[i]);
+    if (it0 > 0) {
+        // resume: the iterate y (and its complex64 copy) is still in the work area
+        if (tid == 0) {
+            lam_s = lam_out[cand];
+            stop_s = 0;
+            fp64_s = stc[2] != 0.0;
+            dprev_s = stc[3];
         }
+        __syncthreads();
     }
-    int ok = redd[0] > 0, it = 0;
+    double ss = 0.0;
+    int ok = 1, it = 0;
+    if (it0 == 0) {
+        for (int i = tid; i < k; i += blockDim.x) {
+            y[i] = Y0[(int64_t)cand * ldy0 + i];
+            ss += norm2(y[i]);
+        }
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0) redd[w] = ss;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0;
+            for (int q = 0; q < nw; ++q) t += redd[q];
+            redd[0] = t;
+            lam_s = lam0[cand];
+            stop_s = 0;
+            fp64_s = 0;
+            dprev_s = 0.0;
+        }
+        __syncthreads();
+        {
+            const double inv = redd[0] > 0 ? 1.0 / sqrt(redd[0]) : 0.0;
+            for (int i = tid; i < k; i += blockDim.x) {
+                y[i] = inv * y[i];
+                y32[i] = cvt<float>(y[i]);
+            }
+        }
+        ok = redd[0] > 0;
+    } else {
+        ok = ok_out[cand];
+    }
+    const int itend = stc ? min(maxit, it0 + steps) : maxit;
+    bool finished = false;  // stopped (converged, failed, left) rather than out of steps
     __syncthreads();
-    for (it = 1; it <= maxit && ok; ++it) {
+    for (it = it0 + 1; it <= itend && ok; ++it) {
         const bool fp64 = fp64_s != 0;
         if (tid < nt) {
-            const FnEval fe = fn_eval(s.fn_nodes, s.fn_coef, s.fn_root[tid], lam_s);
-            fv[tid] = fe.f;
-            fv[nt + tid] = fe.df;
+            if (fv_ext) {
+                fv[tid] = fv_ext[(int64_t)cand * 2 * nt + tid];
+                fv[nt + tid] = fv_ext[(int64_t)cand * 2 * nt + nt + tid];
+            } else {
+                const FnEval fe = fn_eval(s.fn_nodes, s.fn_coef, s.fn_root[tid], lam_s);
+                fv[tid] = fe.f;
+                fv[nt + tid] = fe.df;
+            }
         }
         for (int r = tid; r < K1; r += blockDim.x) used[r] = 0;
         // v_i = B_i y, one (row, term) per thread: FP64 near the solution, FP32 before
@@ -1566,7 +1596,7 @@ __global__ void __launch_bounds__(256, 1) newton_kernel(SplitDev s, int k, const
             sing_s = sg;
         }
         __syncthreads();
-        if (sing_s) { ok = 0; break; }
+        if (sing_s) { ok = 0; finished = true; break; }
         // back substitution in pivot order (warp 0): lane holds the transformed right-hand sides of
         // the pivots i = lane + 32 b; x_col = rhs(col) / U(col, col), then every earlier pivot row
         // drops x_col times its entry in column col. The solution goes to y32 (rebuilt below).
@@ -1636,32 +1666,41 @@ __global__ void __launch_bounds__(256, 1) newton_kernel(SplitDev s, int k, const
             y32[i] = cvt<float>(y[i]);
         }
         __syncthreads();
-        if (stop_s == 2) { ok = 0; break; }
-        if (stop_s == 3) { ok = 2; break; }
-        if (stop_s == 1) break;
+        if (stop_s == 2) { ok = 0; finished = true; break; }
+        if (stop_s == 3) { ok = 2; finished = true; break; }
+        if (stop_s == 1) { finished = true; break; }
     }
+    if (!ok) finished = true;
+    const int done_its = finished ? it : it - 1;  // steps taken so far
     for (int i = tid; i < k; i += blockDim.x) Yout[(int64_t)cand * k + i] = y[i];
     if (tid == 0) {
         lam_out[cand] = lam_s;
         ok_out[cand] = ok;
-        its_out[cand] = min(it, maxit);
+        its_out[cand] = min(done_its, maxit);
+        if (stc) {
+            stc[0] = done_its;
+            stc[1] = (finished || done_its >= maxit) ? 1.0 : 0.0;
+            stc[2] = fp64_s ? 1.0 : 0.0;
+            stc[3] = dprev_s;
+        }
     }
 }
 
 int launch_newton(const SplitDev& s, int k, int ncand, const zd* Bs, zf* Bs32, const zd* lam0, const zd* Y0, int ldy0,
                   zd c, double rad, double ea, double eb, int maxit, int abandon, double tol, zd* lam_out, zd* Yout, int* ok,
-                  int* its, unsigned char* gscratch, cudaStream_t st) {
+                  int* its, unsigned char* gscratch, cudaStream_t st, const zd* fv_ext, double* nstate, int steps) {
     if (ncand <= 0) return NEP_OK;
     const int64_t nb = (int64_t)s.nterms * k * k;
     convert_c64_kernel<<<(int)((nb + 255) / 256), 256, 0, st>>>(nb, Bs, Bs32);
     NEP_CHECK_LAUNCH();
     const size_t bytes = newton_scratch_bytes(k, s.nterms);
-    const int use_smem = bytes <= 200 * 1024;
+    const int use_smem = bytes <= 200 * 1024 && !nstate;  // step mode keeps the iterate in global memory
     if (!use_smem && !gscratch) return NEP_ERR_INTERNAL;
     auto run = [&](auto kern) -> int {
         if (use_smem) NEP_CUDA(allow_max_dynamic_smem(kern));
         kern<<<ncand, 256, use_smem ? bytes : 0, st>>>(s, k, Bs, Bs32, lam0, Y0, ldy0, c, rad, ea, eb, maxit, abandon, tol,
-                                                       lam_out, Yout, ok, its, gscratch, use_smem);
+                                                       lam_out, Yout, ok, its, gscratch, use_smem, fv_ext,
+                                                       nstate, steps);
         NEP_CHECK_LAUNCH();
         return NEP_OK;
     };
@@ -1676,12 +1715,15 @@ int launch_newton(const SplitDev& s, int k, int ncand, const zd* Bs, zf* Bs32, c
 
 // ------------------------------------------------------------------ residuals and selection
 // eta_c = |sum_i f_i(l_c) A_i x_c|_2 / (sum_i |f_i(l_c)| |A_i|_inf |x_c|_2), one CTA per pair.
+// fv_ext (or nullptr): f_i(l_c) from the host, at fv_ext[c * 2 nterms + i], for host-supplied functions.
 __global__ void __launch_bounds__(256) eta_kernel(SplitDev s, const zd* __restrict__ lam, const zd* __restrict__ X,
-                                                  double* __restrict__ eta) {
+                                                  double* __restrict__ eta, const zd* __restrict__ fv_ext) {
     __shared__ zd fv[32];
     __shared__ double red[2][32];
     const int cnd = blockIdx.x;
-    if (threadIdx.x < s.nterms) fv[threadIdx.x] = fn_eval(s.fn_nodes, s.fn_coef, s.fn_root[threadIdx.x], lam[cnd]).f;
+    if (threadIdx.x < s.nterms)
+        fv[threadIdx.x] = fv_ext ? fv_ext[(int64_t)cnd * 2 * s.nterms + threadIdx.x]
+                                 : fn_eval(s.fn_nodes, s.fn_coef, s.fn_root[threadIdx.x], lam[cnd]).f;
     __syncthreads();
     const zd* x = X + (int64_t)cnd * s.n;
     double rr = 0.0, xx = 0.0;
@@ -1849,9 +1891,10 @@ int launch_term_spmm(const SplitDev& s, int k, const zd* Q, zd* out, cudaStream_
     NEP_CHECK_LAUNCH();
     return NEP_OK;
 }
-int launch_eta(const SplitDev& s, int ncand, const zd* lam, const zd* X, double* eta, cudaStream_t st) {
+int launch_eta(const SplitDev& s, int ncand, const zd* lam, const zd* X, double* eta, cudaStream_t st,
+               const zd* fv_ext) {
     if (ncand <= 0) return NEP_OK;
-    eta_kernel<<<ncand, 256, 0, st>>>(s, lam, X, eta);
+    eta_kernel<<<ncand, 256, 0, st>>>(s, lam, X, eta, fv_ext);
     NEP_CHECK_LAUNCH();
     return NEP_OK;
 }

@@ -109,10 +109,20 @@ void nep::smem_limit_mark(const void* fn) {
 using namespace nep;
 
 // ============================================================================ split operator
+// A term whose function the host supplies (NEP_FN_CALLBACK, NEP_FN_TABLE): never evaluated on the device.
+struct ExtTerm {
+    int kind = -1;  // -1: built-in (a device function tree)
+    nep_fn_eval_t eval = nullptr;
+    void* ctx = nullptr;
+    std::vector<zd> table;
+};
+
 struct nep_split {
     int n = 0, nterms = 0, kl = 0, ku = 0, ldab = 0;
     int64_t nnz = 0;
     bool complex_vals = false;
+    std::vector<ExtTerm> ext;  // per term
+    bool has_ext = false;
     std::vector<int64_t> rowptr;
     std::vector<int32_t> col;
     std::vector<double> val, val_im;
@@ -183,6 +193,8 @@ static int flatten_fn(nep_split* h, const nep_fn* f, int depth) {
         nd.den_len = f->nden;
         for (int i = 0; i < f->nden; ++i) h->coef.push_back(mk(f->den[2 * i], f->den[2 * i + 1]));
     } else if (f->kind == NEP_FN_EXP || f->kind == NEP_FN_SQRT) {
+    } else if (f->kind == NEP_FN_CALLBACK || f->kind == NEP_FN_TABLE) {
+        if (depth > 0) { set_error("callback and table functions are allowed only at the top level of a term"); return -1; }
     } else if (f->kind == NEP_FN_COMBINE) {
         if (f->op < NEP_OP_ADD || f->op > NEP_OP_COMPOSE) { set_error("bad combine op %d", f->op); return -1; }
         const int self = (int)h->nodes.size();
@@ -317,10 +329,23 @@ extern "C" int nep_create_split(int32_t n, int32_t nterms, const nep_csr* A, con
             h->ku = std::max(h->ku, h->col[e] - r);
         }
     h->ldab = 2 * h->kl + h->ku + 1;
+    h->ext.resize(nterms);
     for (int i = 0; i < nterms; ++i) {
         const int root = flatten_fn(h, &f[i], 0);
         if (root < 0) { delete h; return NEP_ERR_ARG; }
         h->roots.push_back(root);
+        if (f[i].kind == NEP_FN_CALLBACK || f[i].kind == NEP_FN_TABLE) {
+            ExtTerm& e = h->ext[i];
+            e.kind = f[i].kind;
+            e.eval = f[i].eval;
+            e.ctx = f[i].ctx;
+            if (e.kind == NEP_FN_CALLBACK && !e.eval) { set_error("term %d: NEP_FN_CALLBACK needs eval", i); delete h; return NEP_ERR_ARG; }
+            if (e.kind == NEP_FN_TABLE) {
+                if (!f[i].table || f[i].table_count < 1) { set_error("term %d: NEP_FN_TABLE needs table and table_count >= 1", i); delete h; return NEP_ERR_ARG; }
+                for (int k = 0; k < f[i].table_count; ++k) e.table.push_back(mk(f[i].table[2 * k], f[i].table[2 * k + 1]));
+            }
+            h->has_ext = true;
+        }
     }
     cudaGetDevice(&h->device);
     int rc = NEP_OK;
@@ -507,18 +532,45 @@ extern "C" int nep_nodes(const nep_region* r, int32_t N, double* z, double* w, d
     return NEP_OK;
 }
 
+// f_i (and f_i' if dF) of every term at count points on the host, F[i + nterms k]: built-in terms by
+// their function trees, host-supplied terms through the user's eval (one call per term for all
+// points). A table term without eval has no values off its nodes: NEP_ERR_UNSUPPORTED.
+int nep::host_terms(const nep_split* h, const zd* z, int count, zd* F, zd* dF) {
+    std::vector<zd> f(count), df(count);
+    for (int i = 0; i < h->nterms; ++i) {
+        const ExtTerm& e = h->ext[i];
+        if (e.kind < 0) {
+            for (int k = 0; k < count; ++k) {
+                const FnEval v = fn_eval(h->nodes.data(), h->coef.data(), h->roots[i], z[k]);
+                F[i + (size_t)h->nterms * k] = v.f;
+                if (dF) dF[i + (size_t)h->nterms * k] = v.df;
+            }
+            continue;
+        }
+        if (!e.eval) {
+            set_error("term %d is tabulated at the quadrature nodes only: it needs eval for other points", i);
+            return NEP_ERR_UNSUPPORTED;
+        }
+        if (count == 0) continue;
+        e.eval(reinterpret_cast<const double*>(z), count, reinterpret_cast<double*>(f.data()),
+               dF ? reinterpret_cast<double*>(df.data()) : nullptr, e.ctx);
+        for (int k = 0; k < count; ++k) {
+            F[i + (size_t)h->nterms * k] = f[k];
+            if (dF) dF[i + (size_t)h->nterms * k] = df[k];
+        }
+    }
+    return NEP_OK;
+}
+
+bool nep::split_has_host_terms(const nep_split* h) { return h && h->has_ext; }
+
 extern "C" int nep_coefficients(nep_split_t h, int32_t N, const double* z, double* F, double* dF) {
     if (!h || !z || !F || N < 1) { set_error("nep_coefficients: bad arguments"); return NEP_ERR_ARG; }
-    for (int j = 0; j < N; ++j)
-        for (int i = 0; i < h->nterms; ++i) {
-            const FnEval e = fn_eval(h->nodes.data(), h->coef.data(), h->roots[i], mk(z[2 * j], z[2 * j + 1]));
-            F[2 * (i + (int64_t)h->nterms * j)] = e.f.re;
-            F[2 * (i + (int64_t)h->nterms * j) + 1] = e.f.im;
-            if (dF) {
-                dF[2 * (i + (int64_t)h->nterms * j)] = e.df.re;
-                dF[2 * (i + (int64_t)h->nterms * j) + 1] = e.df.im;
-            }
-        }
+    std::vector<zd> zz(N), FF((size_t)h->nterms * N), dd(dF ? (size_t)h->nterms * N : 0);
+    for (int j = 0; j < N; ++j) zz[j] = mk(z[2 * j], z[2 * j + 1]);
+    NEP_TRY(host_terms(h, zz.data(), N, FF.data(), dF ? dd.data() : nullptr));
+    memcpy(F, FF.data(), sizeof(zd) * FF.size());
+    if (dF) memcpy(dF, dd.data(), sizeof(zd) * dd.size());
     return NEP_OK;
 }
 
@@ -567,6 +619,9 @@ struct nep_plan {
     size_t part_elems = 0;
     unsigned char* newton_scratch = nullptr;
     zf* bs32 = nullptr;  // complex64 copy of the projected B_i for Newton
+    // host-supplied functions: Newton one step per launch with f_i, f_i' from the host
+    double* nstate = nullptr;  // 4 per candidate: steps done, finished, FP64 phase, last |dlambda|
+    zd* fvx = nullptr;         // per candidate: f_i then f_i' (2 nterms)
     void* eig_scratch = nullptr;
     JacobiWork jw{};
     int* h_pinned = nullptr;  // host-mapped scalars
@@ -640,8 +695,12 @@ static int plan_alloc(nep_plan* p) {
     p->part_elems = std::max<size_t>(16 * lm2, 1 << 16);
     NEP_TRY(dalloc(&p->part, p->part_elems, st));
     NEP_TRY(dalloc_raw((void**)&p->bs32, sizeof(zf) * (size_t)nt * LM * LM, st));
-    if (newton_scratch_bytes(LM, nt) > 200 * 1024)
+    if (newton_scratch_bytes(LM, nt) > 200 * 1024 || h->has_ext)
         NEP_TRY(dalloc_raw((void**)&p->newton_scratch, (size_t)LM * newton_scratch_bytes(LM, nt), st));
+    if (h->has_ext) {
+        NEP_TRY(dalloc(&p->nstate, (size_t)4 * LM, st));
+        NEP_TRY(dalloc(&p->fvx, (size_t)2 * nt * LM, st));
+    }
     NEP_TRY(dalloc_raw(&p->eig_scratch, sizeof(zf) * (size_t)LM * ((size_t)LM * (LM + 1) + 2 * LM) + 256, st));
     NEP_TRY(dalloc(&p->jw.Vm, lm2, st));
     NEP_TRY(dalloc(&p->jw.flags, 2, st));
@@ -722,6 +781,20 @@ int nep::plan_create_internal(nep_split_t h, const nep_region* r, int32_t N, int
     p->LM = L * M;
     p->mixed = p->o.precision == NEP_PREC_MIXED;
     p->Np = N;
+    for (int i = 0; i < h->nterms; ++i) {
+        const ExtTerm& e = h->ext[i];
+        if (e.kind == NEP_FN_TABLE && (int)e.table.size() != N) {
+            delete p;
+            set_error("term %d is tabulated at %d nodes, the solve has N = %d", i, (int)e.table.size(), N);
+            return NEP_ERR_ARG;
+        }
+        if (e.kind == NEP_FN_TABLE && !e.eval) {
+            delete p;
+            set_error("term %d is tabulated at the nodes only: the extraction step needs its values elsewhere "
+                      "(give eval, or use the assembly and solve entry points with the table)", i);
+            return NEP_ERR_UNSUPPORTED;
+        }
+    }
     std::vector<zd> z, w, zeta;
     make_nodes(r, N, z, w, zeta);
     if (p->o.symmetric) {
@@ -736,8 +809,21 @@ int nep::plan_create_internal(nep_split_t h, const nep_region* r, int32_t N, int
         }
         for (int j = 0; j < N / 2 && why.empty(); ++j)
             for (int i = 0; i < h->nterms; ++i) {
-                const zd f = fn_eval(h->nodes.data(), h->coef.data(), h->roots[i], z[j]).f;
-                const zd g = fn_eval(h->nodes.data(), h->coef.data(), h->roots[i], conj(z[j])).f;
+                zd f, g;
+                const ExtTerm& e = h->ext[i];
+                if (e.kind == NEP_FN_TABLE) {  // conj z_j is the node N-1-j
+                    f = e.table[j];
+                    g = e.table[N - 1 - j];
+                } else if (e.kind == NEP_FN_CALLBACK) {
+                    const zd zz[2] = {z[j], conj(z[j])};
+                    zd ff[2];
+                    e.eval(reinterpret_cast<const double*>(zz), 2, reinterpret_cast<double*>(ff), nullptr, e.ctx);
+                    f = ff[0];
+                    g = ff[1];
+                } else {
+                    f = fn_eval(h->nodes.data(), h->coef.data(), h->roots[i], z[j]).f;
+                    g = fn_eval(h->nodes.data(), h->coef.data(), h->roots[i], conj(z[j])).f;
+                }
                 const double d = std::hypot(g.re - f.re, g.im + f.im), a = std::hypot(f.re, f.im);
                 if (!(d <= 1e-13 * std::max(a, 1e-300))) { why = "some f_i is not real (f(conj z) != conj f(z))"; break; }
             }
@@ -757,8 +843,25 @@ int nep::plan_create_internal(nep_split_t h, const nep_region* r, int32_t N, int
     // coefficient table and moment weights of the solved nodes (host, FP64) -> device
     const int Np = p->Np;
     std::vector<zd> F((size_t)h->nterms * Np), coef((size_t)Np * p->K);
+    if (h->has_ext) {
+        // tabulated terms from their tables, callbacks through eval (one call per term), built-in
+        // terms by their function trees
+        for (int i = 0; i < h->nterms; ++i) {
+            const ExtTerm& e = h->ext[i];
+            if (e.kind == NEP_FN_TABLE) {
+                for (int j = 0; j < Np; ++j) F[i + (size_t)h->nterms * j] = e.table[j];
+            } else if (e.kind == NEP_FN_CALLBACK) {
+                std::vector<zd> ff(Np);
+                e.eval(reinterpret_cast<const double*>(z.data()), Np, reinterpret_cast<double*>(ff.data()), nullptr, e.ctx);
+                for (int j = 0; j < Np; ++j) F[i + (size_t)h->nterms * j] = ff[j];
+            } else {
+                for (int j = 0; j < Np; ++j) F[i + (size_t)h->nterms * j] = fn_eval(h->nodes.data(), h->coef.data(), h->roots[i], z[j]).f;
+            }
+        }
+    }
     for (int j = 0; j < Np; ++j) {
-        for (int i = 0; i < h->nterms; ++i) F[i + (size_t)h->nterms * j] = fn_eval(h->nodes.data(), h->coef.data(), h->roots[i], z[j]).f;
+        if (!h->has_ext)
+            for (int i = 0; i < h->nterms; ++i) F[i + (size_t)h->nterms * j] = fn_eval(h->nodes.data(), h->coef.data(), h->roots[i], z[j]).f;
         zd pw = mk(1.0, 0.0);
         for (int k = 0; k < p->K; ++k) {
             coef[j + (size_t)Np * k] = w[j] * pw;
@@ -816,6 +919,61 @@ static int run_solves(nep_plan* p, cudaStream_t st) {
         if (p->h_pinned[0] == 0) break;
     }
     NEP_CUDA(cudaEventRecord(p->ev[3], st));
+    return NEP_OK;
+}
+
+// f_i (and f_i' when with_d) at the m device values lam_dev, evaluated on the host (host-supplied
+// functions) into p->fvx: per candidate f_i then f_i'. Only finite values are handed to the
+// functions; a candidate with a non-finite value gets zeros (its eta is then infinite).
+static int host_values_at(nep_plan* p, const zd* lam_dev, int m, bool with_d, cudaStream_t st,
+                          const std::vector<char>* skip = nullptr) {
+    const int nt = p->h->nterms;
+    std::vector<zd> lam(m), fv((size_t)2 * nt * m, mk(0.0, 0.0));
+    NEP_CUDA(cudaMemcpyAsync(lam.data(), lam_dev, sizeof(zd) * m, cudaMemcpyDeviceToHost, st));
+    NEP_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> idx;
+    std::vector<zd> zs;
+    for (int c = 0; c < m; ++c)
+        if (std::isfinite(lam[c].re) && std::isfinite(lam[c].im) && !(skip && (*skip)[c])) {
+            idx.push_back(c);
+            zs.push_back(lam[c]);
+        }
+    const int cnt = (int)idx.size();
+    std::vector<zd> F((size_t)nt * cnt), dF(with_d ? (size_t)nt * cnt : 0);
+    NEP_TRY(host_terms(p->h, zs.data(), cnt, F.data(), with_d ? dF.data() : nullptr));
+    for (int q = 0; q < cnt; ++q)
+        for (int i = 0; i < nt; ++i) {
+            fv[(size_t)idx[q] * 2 * nt + i] = F[i + (size_t)nt * q];
+            if (with_d) fv[(size_t)idx[q] * 2 * nt + nt + i] = dF[i + (size_t)nt * q];
+        }
+    NEP_CUDA(cudaMemcpyAsync(p->fvx, fv.data(), sizeof(zd) * fv.size(), cudaMemcpyHostToDevice, st));
+    NEP_CUDA(cudaStreamSynchronize(st));
+    return NEP_OK;
+}
+
+// Projected Newton for splits with host-supplied functions: one step per launch over all candidates,
+// f_i and f_i' at each unfinished candidate's current iterate evaluated on the host in between (the
+// same kernel, iterate kept in global memory; the same stopping rules).
+static int newton_host_functions(nep_plan* p, const SplitDev& s, int kb, int m, double rad, cudaStream_t st) {
+    NEP_CUDA(cudaMemsetAsync(p->nstate, 0, sizeof(double) * 4 * m, st));
+    std::vector<double> stv((size_t)4 * m);
+    std::vector<char> done(m, 0);
+    for (int step = 1; step <= p->o.newton_max; ++step) {
+        if (step > 1) {
+            NEP_CUDA(cudaMemcpyAsync(stv.data(), p->nstate, sizeof(double) * 4 * m, cudaMemcpyDeviceToHost, st));
+            NEP_CUDA(cudaStreamSynchronize(st));
+            bool any = false;
+            for (int c = 0; c < m; ++c) {
+                done[c] = stv[4 * (size_t)c + 1] != 0.0;
+                any |= !done[c];
+            }
+            if (!any) break;
+        }
+        NEP_TRY(host_values_at(p, step == 1 ? p->cand : p->lamn, m, true, st, &done));
+        NEP_TRY(launch_newton(s, kb, m, p->Bs, p->bs32, p->cand, p->Y0, kb, mk(p->reg.center_re, p->reg.center_im), rad,
+                              p->reg.a, p->reg.b, p->o.newton_max, p->o.newton_abandon, p->o.newton_tol, p->lamn, p->Yn,
+                              p->ok, p->its, p->newton_scratch, st, p->fvx, p->nstate, 1));
+    }
     return NEP_OK;
 }
 
@@ -886,13 +1044,22 @@ static int run_extract(nep_plan* p, cudaStream_t st) {
     NEP_TRY(zgemm(kb, nt * kb, n, 1, p->Q, n, p->AQ, n, p->Bs, kb, p->part, p->part_elems, st));
     // Newton from every Hankel candidate
     const double rad = 4.0 * std::max(p->reg.a, p->reg.b);
-    NEP_TRY(launch_newton(s, kb, m, p->Bs, p->bs32, p->cand, p->Y0, kb, mk(p->reg.center_re, p->reg.center_im), rad,
-                          p->reg.a, p->reg.b, p->o.newton_max, p->o.newton_abandon, p->o.newton_tol, p->lamn, p->Yn, p->ok, p->its,
-                          p->newton_scratch, st));
+    if (p->h->has_ext) {
+        NEP_TRY(newton_host_functions(p, s, kb, m, rad, st));
+    } else {
+        NEP_TRY(launch_newton(s, kb, m, p->Bs, p->bs32, p->cand, p->Y0, kb, mk(p->reg.center_re, p->reg.center_im), rad,
+                              p->reg.a, p->reg.b, p->o.newton_max, p->o.newton_abandon, p->o.newton_tol, p->lamn, p->Yn,
+                              p->ok, p->its, p->newton_scratch, st));
+    }
     // eigenvectors, residuals, selection
     NEP_TRY(zgemm(n, m, kb, 0, p->Q, n, p->Yn, kb, p->Xc, n, p->part, p->part_elems, st));
     NEP_TRY(launch_normalize_columns(n, m, p->Xc, 1, nullptr, st));
-    NEP_TRY(launch_eta(s, m, p->lamn, p->Xc, p->eta, st));
+    if (p->h->has_ext) {
+        NEP_TRY(host_values_at(p, p->lamn, m, false, st));
+        NEP_TRY(launch_eta(s, m, p->lamn, p->Xc, p->eta, st, p->fvx));
+    } else {
+        NEP_TRY(launch_eta(s, m, p->lamn, p->Xc, p->eta, st));
+    }
     NEP_TRY(zgemm(m, m, n, 1, p->Xc, n, p->Xc, n, p->Gx, m, p->part, p->part_elems, st));
     NEP_TRY(launch_select(m, p->lamn, p->eta, p->ok, p->Gx, mk(p->reg.center_re, p->reg.center_im), p->reg.a, p->reg.b,
                           p->o.eig_tol, p->order, st));
@@ -953,12 +1120,18 @@ extern "C" int nep_plan_buffer(nep_plan_t p, const char* name, void** dev_ptr, s
 struct nep_result {
     int n = 0, nconv = 0, m = 0, flags = 0;
     std::vector<double> lam, X, resid, sigma;
+    std::vector<int32_t> pt_sweeps, pt_info;  // per solved quadrature point
+    std::vector<double> pt_beta;
     nep_result_info_t info{};
 };
 
 // ------------------------------------------------------------------ residual inverse iteration
 extern "C" int nep_rii(nep_split_t h, int32_t precision, int32_t P, double* lam_dev, double* X_dev, double* eta_dev,
                        int32_t* its_dev, double tol, int32_t max_it, int32_t* iterations, void* stream) {
+    if (h && h->has_ext) {
+        set_error("this entry point evaluates the functions on the device: not available with callback or table terms");
+        return NEP_ERR_UNSUPPORTED;
+    }
     if (!h || P < 0 || max_it < 0 || (P > 0 && (!lam_dev || !X_dev || !eta_dev))) {
         set_error("nep_rii: bad arguments");
         return NEP_ERR_ARG;
@@ -982,6 +1155,10 @@ extern "C" int nep_rii(nep_split_t h, int32_t precision, int32_t P, double* lam_
 
 extern "C" int nep_plan_polish(nep_plan_t p, double tol, int32_t max_it, int32_t* polished, int32_t* iterations,
                                void* stream) {
+    if (p && p->h && p->h->has_ext) {
+        set_error("this entry point evaluates the functions on the device: not available with callback or table terms");
+        return NEP_ERR_UNSUPPORTED;
+    }
     if (!p || max_it < 0) { set_error("nep_plan_polish: bad arguments"); return NEP_ERR_ARG; }
     if (polished) *polished = 0;
     if (iterations) *iterations = 0;
@@ -1026,6 +1203,10 @@ extern "C" int nep_plan_polish(nep_plan_t p, double tol, int32_t max_it, int32_t
 extern "C" int nep_left_eigvecs(nep_split_t h, int32_t precision, int32_t P, const double* lam_dev,
                                 const double* X_dev, double* Y_dev, double* eta_dev, int32_t* its_dev, double tol,
                                 int32_t max_it, int32_t* iterations, void* stream) {
+    if (h && h->has_ext) {
+        set_error("this entry point evaluates the functions on the device: not available with callback or table terms");
+        return NEP_ERR_UNSUPPORTED;
+    }
     if (!h || P < 0 || max_it < 1 || (P > 0 && (!lam_dev || !X_dev || !Y_dev || !eta_dev))) {
         set_error("nep_left_eigvecs: bad arguments");
         return NEP_ERR_ARG;
@@ -1054,6 +1235,10 @@ extern "C" int nep_left_eigvecs(nep_split_t h, int32_t precision, int32_t P, con
 
 extern "C" int nep_plan_left(nep_plan_t p, double tol, int32_t max_it, int32_t capacity, double* Y_dev,
                              double* eta_dev, int32_t* nconv, int32_t* iterations, void* stream) {
+    if (p && p->h && p->h->has_ext) {
+        set_error("this entry point evaluates the functions on the device: not available with callback or table terms");
+        return NEP_ERR_UNSUPPORTED;
+    }
     if (!p || max_it < 1 || capacity < 0 || (capacity > 0 && (!Y_dev || !eta_dev))) {
         set_error("nep_plan_left: bad arguments");
         return NEP_ERR_ARG;
@@ -1148,6 +1333,10 @@ static int nleigs_interp_out(nep_split_t h, const nep_region* r, const nep_nleig
 extern "C" int nep_nleigs_interpolation(nep_split_t h, const nep_region* r, const nep_nleigs_opts* o, int32_t cap,
                                         double* sigma, double* xi, double* beta, double* dd, int32_t* degree,
                                         int32_t* converged, int32_t* nsing) {
+    if (h && h->has_ext) {
+        set_error("this entry point evaluates the functions on the device: not available with callback or table terms");
+        return NEP_ERR_UNSUPPORTED;
+    }
     return nleigs_interp_out(h, r, o, cap, sigma, xi, beta, dd, degree, converged, nsing);
 }
 
@@ -1201,6 +1390,10 @@ static int nleigs_interp_out(nep_split_t h, const nep_region* r, const nep_nleig
 
 extern "C" int nep_nleigs_solve(nep_split_t h, const nep_region* r, const nep_nleigs_opts* o, nep_result_t* out,
                                 int32_t* degree, void* stream) {
+    if (h && h->has_ext) {
+        set_error("this entry point evaluates the functions on the device: not available with callback or table terms");
+        return NEP_ERR_UNSUPPORTED;
+    }
     if (!out) { set_error("out is NULL"); return NEP_ERR_ARG; }
     *out = nullptr;
     NleigsParams q;
@@ -1281,6 +1474,9 @@ extern "C" int nep_plan_result(nep_plan_t p, nep_result_t* out) {
         if (info[j]) flags |= NEP_WARN_SINGULAR_NODE;
     }
     if (p->m == LM) flags |= NEP_WARN_SATURATED;
+    r->pt_sweeps.assign(sweeps.begin(), sweeps.end());
+    r->pt_info.assign(info.begin(), info.end());
+    r->pt_beta = beta;
     int nfail = 0, nleft = 0;
     for (int c = 0; c < p->m && p->kb > 0; ++c) {
         nfail += ok[c] == 0;
@@ -1377,6 +1573,16 @@ extern "C" int nep_result_get(nep_result_t r, int32_t* nconv, const double** lam
     if (resid) *resid = r->resid.data();
     if (hankel_rank) *hankel_rank = r->m;
     if (flags) *flags = r->flags;
+    return NEP_OK;
+}
+
+extern "C" int nep_result_points(nep_result_t r, int32_t* npts, const int32_t** sweeps, const int32_t** lu_info,
+                                 const double** backward) {
+    if (!r) { set_error("null result"); return NEP_ERR_ARG; }
+    if (npts) *npts = (int32_t)r->pt_sweeps.size();
+    if (sweeps) *sweeps = r->pt_sweeps.data();
+    if (lu_info) *lu_info = r->pt_info.data();
+    if (backward) *backward = r->pt_beta.data();
     return NEP_OK;
 }
 

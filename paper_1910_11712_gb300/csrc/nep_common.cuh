@@ -129,6 +129,10 @@ __host__ __device__ inline FnEval fn_eval(const FnNode* nodes, const zd* coef, i
     } else if (nd.kind == NEP_FN_SQRT) {
         h = csqrt_(x - nd.shift);
         dh = cdiv(mk(0.5, 0.0), h);
+    } else if (nd.kind == NEP_FN_CALLBACK || nd.kind == NEP_FN_TABLE) {
+        // host-supplied functions have no device form; callers pass their values in instead
+        h = mk((double)NAN, (double)NAN);
+        dh = h;
     } else {  // combine
         if (depth > 16) return FnEval{mk(0.0, 0.0), mk(0.0, 0.0)};
         if (nd.op == NEP_OP_COMPOSE) {
@@ -184,6 +188,11 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
         if (e_ != cudaSuccess) return ::nep::cuda_fail(e_, #call, __FILE__, __LINE__); \
     } while (0)
 void count_launch();
+// f_i (and f_i') of every term at count points on the host, F[i + nterms k]; host-supplied terms through
+// the user's function (host_api.cu). NEP_ERR_UNSUPPORTED for a tabulated term without eval.
+int host_terms(const ::nep_split* h, const zd* z, int count, zd* F, zd* dF);
+// whether any term is host-supplied (callback or table): such splits have no device function tree
+bool split_has_host_terms(const ::nep_split* h);
 // polls a device-side wait makes before it gives up and records an error (nep_set_wait_limit)
 long long wait_limit();
 #define NEP_CHECK_LAUNCH()         \
@@ -302,7 +311,8 @@ size_t newton_scratch_bytes(int k, int nterms);
 int launch_pchol(int m, const zd* G, double tol2, int* rank_out, zd* Z, zd* gwork, cudaStream_t st);
 int launch_newton(const SplitDev& s, int k, int ncand, const zd* Bs, zf* Bs32, const zd* lam0, const zd* Y0, int ldy0,
                   zd c, double rad, double ea, double eb, int maxit, int abandon, double tol, zd* lam_out, zd* Yout, int* ok,
-                  int* its, unsigned char* gscratch, cudaStream_t st);
+                  int* its, unsigned char* gscratch, cudaStream_t st, const zd* fv_ext = nullptr,
+                  double* nstate = nullptr, int steps = 0);
 int launch_scale_cols(int rows, int cols, zd* X, int ld, const double* s, int mode, cudaStream_t st);
 int launch_scale_rows(int rows, int cols, zd* X, int ld, const double* s, cudaStream_t st);
 int launch_candidates(int m, const zd* theta, zd c, double a, zd* lam, cudaStream_t st);
@@ -311,7 +321,8 @@ int launch_drop_singular(int npts, int n, int L, const int* info, zd* Y, int* ac
 int launch_rank(int n, const double* sigma, double tol, int* out, cudaStream_t st);
 int launch_normalize_columns(int rows, int cols, zd* X, int fix_phase, double* nrm, cudaStream_t st);
 int launch_term_spmm(const SplitDev& s, int k, const zd* Q, zd* out, cudaStream_t st);
-int launch_eta(const SplitDev& s, int ncand, const zd* lam, const zd* X, double* eta, cudaStream_t st);
+int launch_eta(const SplitDev& s, int ncand, const zd* lam, const zd* X, double* eta, cudaStream_t st,
+               const zd* fv_ext = nullptr);
 int launch_select(int ncand, const zd* lam, const double* eta, const int* ok, const zd* G, zd c, double ea, double eb,
                   double eig_tol, int* order, cudaStream_t st);
 // polish.cu: residual inverse iteration from P (lambda, x) estimates (x: n x P), T(sigma_p) factored at

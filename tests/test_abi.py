@@ -82,3 +82,27 @@ def test_new_entry_points_refuse_bad_arguments_without_gpu(built):
     assert lib.nep_apply_resolvent(8, 0, None, None, None, 0, None, 0, None, None, None) == binding.NEP_OK
     # pairs without their arrays are refused even with nothing to apply them to
     assert lib.nep_apply_resolvent(8, 3, None, None, None, 0, None, 0, None, None, None) == E
+
+
+def test_host_function_terms_are_validated_without_gpu(built):
+    """A callback term needs eval, a table term needs values, and neither may sit inside a combination:
+    nep_create_split refuses these before touching a device."""
+    import numpy as np
+    from paper_1910_11712_gb300 import binding
+    lib = binding.load()
+    keep = binding._Keep()
+    n = 4
+    rp = keep.arr(np.arange(n + 1), np.int64)
+    ci = keep.arr(np.arange(n), np.int32)
+    va = keep.arr(np.ones(n), np.float64)
+    csr = binding.NepCsr(n, n, rp.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                         ci.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), va.ctypes.data_as(binding.P_double), None)
+    h = ctypes.c_void_p()
+    f = binding._fn_struct(keep, {"kind": "callback"})  # no eval
+    assert lib.nep_create_split(n, 1, ctypes.byref(csr), ctypes.byref(f), ctypes.byref(h)) == binding.NEP_ERR_ARG
+    f = binding._fn_struct(keep, {"kind": "table", "values": []})
+    assert lib.nep_create_split(n, 1, ctypes.byref(csr), ctypes.byref(f), ctypes.byref(h)) == binding.NEP_ERR_ARG
+    inner = {"kind": "callback", "fn": lambda z: (np.exp(-z), -np.exp(-z))}
+    f = binding._fn_struct(keep, {"kind": "combine", "op": "add", "a": inner, "b": {"kind": "exp"}})
+    assert lib.nep_create_split(n, 1, ctypes.byref(csr), ctypes.byref(f), ctypes.byref(h)) == binding.NEP_ERR_ARG
+    assert b"top level" in lib.nep_last_error()

@@ -14,7 +14,9 @@ What it computes, step by step, in complex128 (each module cites its passage):
   ciss.py       solves T(z_j) Y_j = V with FP64 refinement, moments, block Hankel
                 SVD, reduced eigenproblem, Rayleigh-Ritz projection (Eq. (narnoldi-split))
                 with Newton (Eq. (newton)) and the scaled residual (Eq. (sressplit));
-  count.py      eigenvalue count inside the contour by the argument principle.
+  count.py      eigenvalue count inside the contour by the argument principle;
+  interpol.py   the polynomial interpolation solver of Sec. 4.4 (Chebyshev coefficients, Eq.
+                (polinterpcoef), and the dense Chebyshev-basis linearisation of P_d).
 
 Parity status of each function is listed in its docstring; all intermediate
 Hankel/Rayleigh-Ritz matrices depend on the random probe block V and are

@@ -104,3 +104,73 @@ def test_rii_without_residual_update_caught(monkeypatch):
         return orig(problem, lam0, x0, **kw)
     monkeypatch.setattr(rii, "rii", bad)
     assert _rii_error() > 1e-6
+
+
+def _interpol_errors():
+    """(delay error vs Lambert W, quadratic error vs its companion eigenvalues), inf on failure."""
+    from oracle import interpol
+    from tests.test_oracle_interpol import lambert_real, quadratic_problem, real_delay_problem
+    out = []
+    p = real_delay_problem(seed=0)
+    try:
+        r = interpol.solve(p, p.region, 40)
+        ref = lambert_real(p)
+        out.append(np.abs(np.sort(r["lam"].real) - ref).max() if len(r["lam"]) == len(ref) else np.inf)
+    except Exception:
+        out.append(np.inf)
+    p, A = quadratic_problem()
+    n = p.n
+    Z, I = np.zeros((n, n)), np.eye(n)
+    ref = scipy.linalg.eigvals(np.block([[Z, I], [-A[0], -A[1]]]), np.block([[I, Z], [Z, A[2]]]))
+    ref = ref[np.abs(ref / 1.5) < 1]
+    try:
+        r = interpol.solve(p, p.region, 4)
+        out.append(max(np.min(np.abs(r["lam"] - l)) for l in ref) if len(r["lam"]) == len(ref) else np.inf)
+    except Exception:
+        out.append(np.inf)
+    return out
+
+
+def test_interpol_unplanted():
+    assert max(_interpol_errors()) < 1e-10
+
+
+def test_interpol_node_off_by_half_caught(monkeypatch):
+    """Chebyshev points of the second kind's spacing (omega_j = j pi / (d+1)) instead of Eq. (interpolnu)."""
+    from oracle import interpol
+
+    def bad(d):
+        om = np.arange(d + 1) * np.pi / (d + 1)
+        return om, np.cos(om)
+    monkeypatch.setattr(interpol, "chebyshev_nodes", bad)
+    assert max(_interpol_errors()) > 1e-6
+
+
+def test_interpol_unhalved_c0_caught(monkeypatch):
+    """P_d with C_0 instead of C_0 / 2 (Eq. (polinterp))."""
+    from oracle import interpol
+    orig = interpol.coefficients
+
+    def bad(fns, region, d):
+        c = orig(fns, region, d)
+        c[:, 0] *= 2.0
+        return c
+    monkeypatch.setattr(interpol, "coefficients", bad)
+    assert max(_interpol_errors()) > 1e-6
+
+
+def test_interpol_wrong_recurrence_row_caught(monkeypatch):
+    """theta tau_k = tau_{k+1} + tau_{k-1} (the factor 1/2 of the Chebyshev recurrence dropped) in the
+    linearisation's middle rows."""
+    from oracle import interpol
+    orig = interpol.pencil
+
+    def bad(mats, c):
+        A, B = orig(mats, c)
+        n = mats[0].shape[0]
+        d = c.shape[1] - 1
+        for k in range(1, d - 1):
+            B[k * n:(k + 1) * n, k * n:(k + 1) * n] *= 0.5
+        return A, B
+    monkeypatch.setattr(interpol, "pencil", bad)
+    assert max(_interpol_errors()) > 1e-6

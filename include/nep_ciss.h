@@ -369,6 +369,43 @@ int nep_nleigs_interpolation_fns(int32_t nterms, const nep_fn *f, const nep_regi
 int nep_nleigs_solve(nep_split_t h, const nep_region *r, const nep_nleigs_opts *o, nep_result_t *out,
                      int32_t *degree, void *stream);
 
+/* ------------------------------------------------------------------ Interpol (Chebyshev interpolation) */
+/* Options of the polynomial interpolation solver (Sec. 4.4). Zero fields take the defaults. */
+typedef struct {
+    int32_t degree;       /* interpolation degree d, 2 .. 63 (the paper leaves it to the user); default 40 */
+    int32_t krylov;       /* Arnoldi steps (no restart); default 60, at most 512                           */
+    int32_t has_shift;    /* nonzero: shift_re/im (a value of lambda) as the shift; else the interval's    */
+    double shift_re, shift_im; /* centre                                                                */
+    uint64_t seed;        /* seeded start vector (SplitMix64 + Box-Muller)                                 */
+    double eig_tol;       /* acceptance: eta of T (Eq. (sressplit)) <= eig_tol inside the region; 1e-8     */
+    int32_t fast_solves;  /* nonzero: plain complex64 solves, then residual inverse iteration on T for the  */
+                          /* Ritz pairs inside the region with eta <= 1e-4 (their eigenvalues then are T's, */
+                          /* not P_d's); zero (default): each solve gets two FP64-residual corrections      */
+} nep_interpol_opts;
+/* Chebyshev coefficients of the f_i on the interval I = [c - a, c + a], the real axis of the region's
+ * ellipse (real centre c; a = real semi-axis), lambda = a theta + c (host computation, no device):
+ * nodes nu_j = cos(omega_j), omega_j = (j + 1/2) pi / (d + 1), j = 0 .. d (Eq. (interpolnu)) and
+ * c_ik = 2/(d+1) sum_j f_i(lambda(nu_j)) cos(k omega_j) (Eq. (polinterpcoef)), so that
+ * P_d(theta) = sum_i (c_i0/2 + sum_{k>=1} c_ik tau_k(theta)) A_i. coef: complex[nterms * (d+1)] with
+ * coef[i + nterms k] = c_ik. Errors: NEP_ERR_ARG (bad region, complex centre, degree outside 2 .. 63). */
+int nep_interpol_coefficients(int32_t nterms, const nep_fn *f, const nep_region *r, int32_t degree, double *coef);
+/* The polynomial interpolation solver (Sec. 4.4, "Interpol") for eigenvalues on or near a real interval:
+ * the coefficients above, then the eigenproblem P_d(theta) x = 0 by shift-and-invert Arnoldi on its
+ * Chebyshev-basis linearisation (block rows -theta u_0 + u_1 = 0, u_{k-1} - 2 theta u_k + u_{k+1} = 0 and
+ * sum_{k<d} C'_k u_k + C_d (2 theta u_{d-1} - u_{d-2}) = 0 for u_k = tau_k(theta) x), applied through
+ * the block recurrences with one band LU of P_d(sigma) (complex64 factors) and one band solve per step;
+ * classical Gram-Schmidt twice, Ritz values as nep_nleigs_solve. The region filter of Sec. 4.4: pairs
+ * with lambda strictly inside the region's ellipse (its imaginary semi-axis sets the vicinity of the
+ * interval) and the scaled residual of T itself <= eig_tol, sorted and deduplicated as nep_ciss_solve
+ * does; x is the first block of the Ritz vector. *out receives a result object (hankel_rank 0, no
+ * points; NEP_WARN_SINGULAR_NODE if P_d(sigma) had an exactly zero pivot). The call allocates its work
+ * arrays on the stream ((d n) x (krylov+1) complex128) and returns when they are done.
+ * Errors: NEP_ERR_ARG (bad region, complex centre, options out of range), NEP_ERR_REGION (a
+ * singularity of some f_i inside or on the region), NEP_ERR_UNSUPPORTED (more than 8 terms, or
+ * callback/table terms), CUDA errors. */
+int nep_interpol_solve(nep_split_t h, const nep_region *r, const nep_interpol_opts *o, nep_result_t *out,
+                       void *stream);
+
 /* ------------------------------------------------------------------ serving */
 /* Continuous-batching request server. Requests are admitted in arrival order as soon as a
  * worker is free and their device footprint (nep_plan_bytes) fits the remaining budget;

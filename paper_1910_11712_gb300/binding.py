@@ -61,6 +61,11 @@ class NepNleigsOpts(ctypes.Structure):
                 ("eig_tol", c_double), ("exact_solves", c_int32)]
 
 
+class NepInterpolOpts(ctypes.Structure):
+    _fields_ = [("degree", c_int32), ("krylov", c_int32), ("has_shift", c_int32), ("shift_re", c_double),
+                ("shift_im", c_double), ("seed", ctypes.c_uint64), ("eig_tol", c_double), ("fast_solves", c_int32)]
+
+
 class NepResultInfo(ctypes.Structure):
     _fields_ = [("n", c_int32), ("N", c_int32), ("L", c_int32), ("M", c_int32), ("precision", c_int32),
                 ("hankel_rank", c_int32), ("basis_rank", c_int32), ("ncandidates", c_int32),
@@ -134,6 +139,10 @@ SIGNATURES = {
                                                ctypes.POINTER(c_int32)]),
     "nep_nleigs_solve": (c_int32, [c_void_p, ctypes.POINTER(NepRegion), ctypes.POINTER(NepNleigsOpts),
                                    ctypes.POINTER(c_void_p), ctypes.POINTER(c_int32), c_void_p]),
+    "nep_interpol_coefficients": (c_int32, [c_int32, ctypes.POINTER(NepFn), ctypes.POINTER(NepRegion), c_int32,
+                                            c_void_p]),
+    "nep_interpol_solve": (c_int32, [c_void_p, ctypes.POINTER(NepRegion), ctypes.POINTER(NepInterpolOpts),
+                                     ctypes.POINTER(c_void_p), c_void_p]),
     "nep_apply_resolvent": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_int32,
                                       c_void_p, c_void_p, c_void_p]),
 }
@@ -587,6 +596,31 @@ def nleigs_solve(split, region, stream=0, **opts) -> dict:
     out = _result_dict(res)
     out["degree"] = d.value
     return out
+
+
+def interpol_coefficients(fns, region, degree) -> np.ndarray:
+    """nep_interpol_coefficients (host only): c[i, k] = c_ik, the Chebyshev coefficients of each f_i."""
+    lib = load()
+    keep = _Keep()
+    fs = (NepFn * len(fns))()
+    for i, spec in enumerate(fns):
+        fs[i] = _fn_struct(keep, spec)
+    r = region_struct(region)
+    out = np.zeros(len(fns) * (degree + 1), np.complex128)
+    check(lib.nep_interpol_coefficients(len(fns), fs, ctypes.byref(r), degree, out.ctypes.data))
+    return out.reshape(degree + 1, len(fns)).T.copy()
+
+
+def interpol_solve(split, region, stream=0, **opts) -> dict:
+    """nep_interpol_solve (Sec. 4.4): the result dict of ciss_solve."""
+    lib = load()
+    r = region_struct(region)
+    o = NepInterpolOpts()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    res = c_void_p()
+    check(lib.nep_interpol_solve(split.handle, ctypes.byref(r), ctypes.byref(o), ctypes.byref(res), stream))
+    return _result_dict(res)
 
 
 def kernel_launches() -> int:

@@ -1430,6 +1430,105 @@ extern "C" int nep_nleigs_solve(nep_split_t h, const nep_region* r, const nep_nl
     return NEP_OK;
 }
 
+// ----------------------------------------------------------------- Interpol (Sec. 4.4)
+// c[i + nt k] = 2/(d+1) sum_j f_i(lambda(nu_j)) cos(k omega_j), omega_j = (j + 1/2) pi / (d+1),
+// nu_j = cos omega_j, lambda = a theta + center (Eqs. (interpolnu), (polinterpcoef))
+static int interpol_coefs(const nep_split* h, const nep_region* r, int d, std::vector<zd>* c) {
+    if (!r || !(r->a > 0) || !(r->b > 0)) { set_error("interpol: region semi-axes must be positive"); return NEP_ERR_ARG; }
+    if (r->center_im != 0.0) { set_error("interpol: the interval is the real axis of a region with a real centre"); return NEP_ERR_ARG; }
+    if (d < 2 || d > 63) { set_error("interpol: degree must be in 2 .. 63"); return NEP_ERR_ARG; }
+    const int nt = h->nterms;
+    std::vector<zd> lam(d + 1), F((size_t)nt * (d + 1));
+    std::vector<double> om(d + 1);
+    for (int j = 0; j <= d; ++j) {
+        om[j] = (j + 0.5) * M_PI / (d + 1);
+        lam[j] = mk(r->a * std::cos(om[j]) + r->center_re, 0.0);
+    }
+    NEP_TRY(host_terms(h, lam.data(), d + 1, F.data(), nullptr));
+    c->assign((size_t)nt * (d + 1), mk(0.0, 0.0));
+    for (int i = 0; i < nt; ++i)
+        for (int k = 0; k <= d; ++k) {
+            zd s = mk(0.0, 0.0);
+            for (int j = 0; j <= d; ++j) s = s + std::cos(k * om[j]) * F[i + (size_t)nt * j];
+            (*c)[i + (size_t)nt * k] = (2.0 / (d + 1)) * s;
+        }
+    return NEP_OK;
+}
+
+extern "C" int nep_interpol_coefficients(int32_t nterms, const nep_fn* f, const nep_region* r, int32_t degree,
+                                         double* coef) {
+    if (nterms < 1 || nterms > 32 || !f || !coef) { set_error("nep_interpol_coefficients: bad arguments"); return NEP_ERR_ARG; }
+    nep_split h;  // the function trees only, on the host
+    h.nterms = nterms;
+    h.ext.resize(nterms);
+    for (int i = 0; i < nterms; ++i) {
+        if (f[i].kind == NEP_FN_CALLBACK || f[i].kind == NEP_FN_TABLE) {
+            set_error("nep_interpol_coefficients: built-in function kinds only");
+            return NEP_ERR_UNSUPPORTED;
+        }
+        const int root = flatten_fn(&h, &f[i], 0);
+        if (root < 0) return NEP_ERR_ARG;
+        h.roots.push_back(root);
+    }
+    std::vector<zd> c;
+    NEP_TRY(interpol_coefs(&h, r, degree, &c));
+    memcpy(coef, c.data(), sizeof(zd) * c.size());
+    return NEP_OK;
+}
+
+extern "C" int nep_interpol_solve(nep_split_t h, const nep_region* r, const nep_interpol_opts* o, nep_result_t* out,
+                                  void* stream) {
+    if (!out) { set_error("out is NULL"); return NEP_ERR_ARG; }
+    *out = nullptr;
+    if (!h || !r) { set_error("null handle or region"); return NEP_ERR_ARG; }
+    if (h->has_ext) {
+        set_error("this entry point evaluates the functions on the device: not available with callback or table terms");
+        return NEP_ERR_UNSUPPORTED;
+    }
+    if (h->nterms > 8) { set_error("interpol: at most 8 terms"); return NEP_ERR_UNSUPPORTED; }
+    nep_interpol_opts z{};
+    if (!o) o = &z;
+    const int d = o->degree > 0 ? o->degree : 40;
+    const int kry = o->krylov > 0 ? o->krylov : 60;
+    const double eig_tol = o->eig_tol > 0 ? o->eig_tol : 1e-8;
+    if (kry > 512) { set_error("interpol: krylov <= 512"); return NEP_ERR_ARG; }
+    std::vector<zd> c;
+    NEP_TRY(interpol_coefs(h, r, d, &c));
+    for (int i = 0; i < h->nterms; ++i) {
+        const int rc = check_region_node(h, h->roots[i], r, true);
+        if (rc) return rc;
+    }
+    // the shift in theta: (lambda_shift - centre) / a
+    const zd ls = o->has_shift ? mk(o->shift_re, o->shift_im) : mk(r->center_re, 0.0);
+    const zd sigma = mk((ls.re - r->center_re) / r->a, ls.im / r->a);
+    const size_t N = (size_t)d * h->n;
+    const int kmax = (int)std::min<size_t>((size_t)kry, N);
+    std::vector<zd> start(N);
+    draw_probe_block(o->seed, N, false, reinterpret_cast<double*>(start.data()));
+    NleigsOut res;
+    cudaStream_t st = (cudaStream_t)stream;
+    NEP_TRY(interpol_run(h->dev(), c, d, sigma, r->a, r->center_re, kmax, reinterpret_cast<const double*>(start.data()),
+                         mk(r->center_re, r->center_im), r->a, r->b, eig_tol, o->fast_solves == 0, &res, st));
+    nep_result* rr = new nep_result();
+    rr->n = h->n;
+    rr->nconv = (int)res.lam.size();
+    rr->m = 0;
+    rr->flags = res.lu_info ? NEP_WARN_SINGULAR_NODE : 0;
+    rr->info.n = h->n;
+    rr->info.flags = rr->flags;
+    for (size_t q2 = 0; q2 < res.lam.size(); ++q2) {
+        rr->lam.push_back(res.lam[q2].re);
+        rr->lam.push_back(res.lam[q2].im);
+        rr->resid.push_back(res.eta[q2]);
+    }
+    for (const zd& v : res.X) {
+        rr->X.push_back(v.re);
+        rr->X.push_back(v.im);
+    }
+    *out = rr;
+    return NEP_OK;
+}
+
 extern "C" int nep_plan_result(nep_plan_t p, nep_result_t* out) {
     if (!p || !out) { set_error("nep_plan_result: bad arguments"); return NEP_ERR_ARG; }
     const int n = p->h->n, N = p->Np, LM = p->LM;  // per-point arrays hold the solved points

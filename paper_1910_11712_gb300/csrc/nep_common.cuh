@@ -386,6 +386,11 @@ int nleigs_interpolation(const std::vector<FnNode>& nodes, const std::vector<zd>
 // residual inverse iteration on the converged Ritz pairs inside the region
 int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, const double* start_host, zd c,
                double ea, double eb, double eig_tol, bool exact, NleigsOut* res, cudaStream_t st);
+// Interpol (Sec. 4.4): Krylov on the Chebyshev-basis linearisation of P_d; c: nt x (d+1) coefficients
+// of Eq. (polinterpcoef), lambda = alpha theta + beta, sigma the shift in theta
+int interpol_run(const SplitDev& s, const std::vector<zd>& c, int d, zd sigma, double alpha, double beta, int kmax,
+                 const double* start_host, zd center, double ea, double eb, double eig_tol, bool exact, NleigsOut* res,
+                 cudaStream_t st);
 // out (n x nz*nv, column j*nv + k) = sum_i x_i (y_i^* v_k) / (z_j - lam_i)
 int apply_resolvent(int n, int P, const zd* lam, const zd* X, const zd* Y, int nz, const zd* z, int nv, const zd* V,
                     zd* out, cudaStream_t st);

@@ -397,6 +397,48 @@ __global__ void nleigs_expand_kernel(int n, int d, int nt, const zd* __restrict_
         if (i < nt) C[(int64_t)i * n + r] = acc[i];
 }
 
+// The Chebyshev-basis linearisation of P_d(theta) = sum_k C'_k tau_k(theta) (Sec. 4.4): block rows
+// -theta u_0 + u_1 = 0, u_{k-1} - 2 theta u_k + u_{k+1} = 0 (1 <= k <= d-2) and the last row
+// sum_{k<d} C'_k u_k + C_d (2 theta u_{d-1} - u_{d-2}) = 0, i.e. B v = (v_0, 2 v_1, .., 2 v_{d-2},
+// -2 C_d v_{d-1}). The solve (A - sigma B) w = B v: the particular solution p with p_0 = 0,
+// p_1 = v_0, p_{k+1} = 2 v_k + 2 sigma p_k - p_{k-1} (k = 1 .. d-2) is written to W, then
+// P_d(sigma) w_0 = -sum_i A_i C_i with the per-term combinations
+//   C_i = sum_{k<d} c'_ik p_k + c_id (2 sigma p_{d-1} - p_{d-2} + 2 v_{d-1}),
+// and w_k = p_k + tau_k(sigma) w_0 (nleigs_combine_kernel). cc: nt x (d+1), c'_i0 = c_i0 / 2.
+// One thread per row.
+__global__ void cheb_expand_kernel(int n, int d, int nt, const zd* __restrict__ v, zd* __restrict__ W,
+                                   zd* __restrict__ C, zd sigma, const zd* __restrict__ cc) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    zd acc[kNleigsMaxTerms];
+#pragma unroll
+    for (int i = 0; i < kNleigsMaxTerms; ++i) acc[i] = mk(0.0, 0.0);
+    zd pm = mk(0.0, 0.0);          // p_{k-1}
+    zd pk = v[r];                  // p_1 = v_0
+    W[r] = mk(0.0, 0.0);           // p_0
+    W[(int64_t)n + r] = pk;
+#pragma unroll
+    for (int i = 0; i < kNleigsMaxTerms; ++i)
+        if (i < nt) acc[i] = cc[i + (int64_t)nt * 1] * pk;
+    const zd two_sigma = mk(2.0 * sigma.re, 2.0 * sigma.im);
+    for (int k = 1; k <= d - 2; ++k) {
+        const zd vk = v[(int64_t)k * n + r];
+        const zd pn = fma_(mk(2.0 * vk.re, 2.0 * vk.im) - pm, two_sigma, pk);  // 2 v_k + 2 sigma p_k - p_{k-1}
+        W[(int64_t)(k + 1) * n + r] = pn;
+#pragma unroll
+        for (int i = 0; i < kNleigsMaxTerms; ++i)
+            if (i < nt) acc[i] = fma_(acc[i], cc[i + (int64_t)nt * (k + 1)], pn);
+        pm = pk;
+        pk = pn;
+    }
+    // pk = p_{d-1}, pm = p_{d-2}
+    const zd vl = v[(int64_t)(d - 1) * n + r];
+    const zd tail = fma_(mk(2.0 * vl.re, 2.0 * vl.im) - pm, two_sigma, pk);  // 2 sigma p_{d-1} - p_{d-2} + 2 v_{d-1}
+#pragma unroll
+    for (int i = 0; i < kNleigsMaxTerms; ++i)
+        if (i < nt) C[(int64_t)i * n + r] = fma_(acc[i], cc[i + (int64_t)nt * d], tail);
+}
+
 // out[r] = -sum_e sum_i a_i(r, col e) C[i n + col e]; one warp per row
 __global__ void nleigs_spmv_kernel(SplitDev s, const zd* __restrict__ C, zd* __restrict__ out) {
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -532,13 +574,14 @@ __global__ void __launch_bounds__(32) nleigs_ritz_vectors_kernel(int m, const zd
 }
 
 // lam = shift + 1/theta; ok = theta != 0 and finite
-__global__ void nleigs_ritz_kernel(int m, const zd* __restrict__ theta, zd shift, zd* __restrict__ lam,
+// lambda = shift + scale / theta for a Ritz value theta of S = (A - sigma B)^{-1} B
+__global__ void nleigs_ritz_kernel(int m, const zd* __restrict__ theta, zd shift, zd scale, zd* __restrict__ lam,
                                    int* __restrict__ ok) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     const zd t = theta[i];
     const bool nz = (t.re != 0.0 || t.im != 0.0) && isfinite(t.re) && isfinite(t.im);
-    lam[i] = nz ? shift + cdiv(mk(1.0, 0.0), t) : mk(0.0, 0.0);
+    lam[i] = nz ? shift + cdiv(scale, t) : mk(0.0, 0.0);
     ok[i] = nz && isfinite(lam[i].re) && isfinite(lam[i].im);
 }
 
@@ -596,15 +639,32 @@ __global__ void __launch_bounds__(256) nleigs_sub_kernel(int64_t N, int K, const
 }
 
 
+// A block linearisation (A, B) of d blocks of n with its shift-and-invert recurrences: which expand
+// kernel applies S = (A - sigma B)^{-1} B up to the solve, the per-term coefficients it combines, the
+// combine weights (ec.bsig), the shifted matrix in split form (Fs) and the map from a Ritz value
+// theta of S to lambda = lam_shift + lam_scale / theta.
+struct KrylovLin {
+    int kind = 0;  // 0: rational Newton basis (NLEIGS, Sec. 4.5); 1: Chebyshev basis (Interpol, Sec. 4.4)
+    int d = 0;
+    ExpandCoef ec{};
+    std::vector<zd> coef;  // nt x (d+1)
+    std::vector<zd> Fs;    // nt
+    zd sigma{}, lam_shift{}, lam_scale{};
+};
+static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, const double* start_host, zd c, double ea,
+                          double eb, double eig_tol, bool exact, NleigsOut* res, cudaStream_t st);
+
 int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, const double* start_host, zd c,
                double ea, double eb, double eig_tol, bool exact, NleigsOut* res, cudaStream_t st) {
-    const int refine = exact ? kNleigsRefine : 0;
-    const int n = s.n, nt = s.nterms, d = it.d;
+    const int nt = s.nterms, d = it.d;
     if (nt > kNleigsMaxTerms || d < 1 || d > 63 || kmax < 1) return NEP_ERR_ARG;
-    const int64_t N = (int64_t)d * n;
-    StreamScratch w(st);
-    // host constants
-    ExpandCoef ec{};
+    KrylovLin lin;
+    lin.kind = 0;
+    lin.d = d;
+    lin.sigma = shift;
+    lin.lam_shift = shift;
+    lin.lam_scale = mk(1.0, 0.0);
+    ExpandCoef& ec = lin.ec;
     std::vector<cd> sig, xi;
     for (auto z : it.sigma) sig.push_back(to_cd(z));
     for (auto z : it.xi) xi.push_back(to_cd(z));
@@ -618,14 +678,60 @@ int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, co
     std::vector<cd> bs;
     basis_at(sh, sig, xi, it.beta, d, &bs);
     for (int j = 0; j < d; ++j) ec.bsig[j] = to_zd(bs[j]);
-    std::vector<zd> ddc(it.dd);  // nt x (d+1), column d divided by beta_d
+    std::vector<zd>& ddc = lin.coef;  // nt x (d+1), column d divided by beta_d
+    ddc = it.dd;
     for (int i = 0; i < nt; ++i) ddc[i + (size_t)nt * d] = to_zd(to_cd(ddc[i + (size_t)nt * d]) / it.beta[d]);
-    std::vector<zd> Fs(nt);      // R_d(shift) = sum_i Fs_i A_i
+    lin.Fs.assign(nt, mk(0.0, 0.0));  // R_d(shift) = sum_i Fs_i A_i
     for (int i = 0; i < nt; ++i) {
         cd acc = 0.0;
         for (int j = 0; j <= d; ++j) acc += bs[j] * to_cd(it.dd[i + (size_t)nt * j]);
-        Fs[i] = to_zd(acc);
+        lin.Fs[i] = to_zd(acc);
     }
+    return krylov_lin_run(s, lin, kmax, start_host, c, ea, eb, eig_tol, exact, res, st);
+}
+
+// Interpol (Sec. 4.4): the Chebyshev coefficients c (nt x (d+1), Eq. (polinterpcoef)) of the f_i on the
+// real axis [center - a, center + a] of the region, lambda = a theta + center, and shift-and-invert
+// Arnoldi on the Chebyshev-basis linearisation of P_d with the shift sigma (in theta).
+int interpol_run(const SplitDev& s, const std::vector<zd>& c, int d, zd sigma, double alpha, double beta, int kmax,
+                 const double* start_host, zd center, double ea, double eb, double eig_tol, bool exact, NleigsOut* res,
+                 cudaStream_t st) {
+    const int nt = s.nterms;
+    if (nt > kNleigsMaxTerms || d < 2 || d > 63 || kmax < 1) return NEP_ERR_ARG;
+    KrylovLin lin;
+    lin.kind = 1;
+    lin.d = d;
+    lin.sigma = sigma;
+    lin.lam_shift = mk(alpha * sigma.re + beta, alpha * sigma.im);
+    lin.lam_scale = mk(alpha, 0.0);
+    lin.coef = c;
+    for (int i = 0; i < nt; ++i) lin.coef[i] = mk(0.5 * c[i].re, 0.5 * c[i].im);  // C'_0 = C_0 / 2
+    // tau_k(sigma), k = 0 .. d, and P_d(sigma) = sum_k c'_ik tau_k(sigma) A_i
+    std::vector<cd> tau(d + 1);
+    const cd sg = to_cd(sigma);
+    tau[0] = 1.0;
+    tau[1] = sg;
+    for (int k = 1; k < d; ++k) tau[k + 1] = 2.0 * sg * tau[k] - tau[k - 1];
+    for (int k = 0; k < d; ++k) lin.ec.bsig[k] = to_zd(tau[k]);
+    lin.Fs.assign(nt, mk(0.0, 0.0));
+    for (int i = 0; i < nt; ++i) {
+        cd acc = 0.0;
+        for (int k = 0; k <= d; ++k) acc += tau[k] * to_cd(lin.coef[i + (size_t)nt * k]);
+        lin.Fs[i] = to_zd(acc);
+    }
+    return krylov_lin_run(s, lin, kmax, start_host, center, ea, eb, eig_tol, exact, res, st);
+}
+
+static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, const double* start_host, zd c, double ea,
+                          double eb, double eig_tol, bool exact, NleigsOut* res, cudaStream_t st) {
+    const int refine = exact ? kNleigsRefine : 0;
+    const int n = s.n, nt = s.nterms, d = lin.d;
+    const int64_t N = (int64_t)d * n;
+    const ExpandCoef& ec = lin.ec;
+    const std::vector<zd>& ddc = lin.coef;
+    const std::vector<zd>& Fs = lin.Fs;
+    const zd shift = lin.lam_shift;
+    StreamScratch w(st);
     // device arrays
     ExpandCoef* d_ec = nullptr;
     zd *d_ddc = nullptr, *d_F = nullptr, *tval = nullptr, *V = nullptr, *C = nullptr, *rhs = nullptr, *u = nullptr;
@@ -695,7 +801,10 @@ int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, co
     for (int k = 0; k < kmax; ++k) {
         const zd* vk = V + (int64_t)k * N;
         zd* wk = V + (int64_t)(k + 1) * N;
-        nleigs_expand_kernel<<<ceil_div(n, 128), 128, 0, st>>>(n, d, nt, vk, wk, C, d_ec, d_ddc);
+        if (lin.kind == 0)
+            nleigs_expand_kernel<<<ceil_div(n, 128), 128, 0, st>>>(n, d, nt, vk, wk, C, d_ec, d_ddc);
+        else
+            cheb_expand_kernel<<<ceil_div(n, 128), 128, 0, st>>>(n, d, nt, vk, wk, C, lin.sigma, d_ddc);
         NEP_CHECK_LAUNCH();
         nleigs_spmv_kernel<<<ceil_div((int64_t)n * 32, 256), 256, 0, st>>>(s, C, rhs);
         NEP_CHECK_LAUNCH();
@@ -735,7 +844,7 @@ int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, co
     NEP_TRY(small_eig_fast<float>(m, Hm, theta, nullptr, status, gbuf, st));
     nleigs_ritz_vectors_kernel<<<m, 32, sizeof(zd) * m, st>>>(m, Hm, theta, S, rwork, rpiv);
     NEP_CHECK_LAUNCH();
-    nleigs_ritz_kernel<<<ceil_div(m, 128), 128, 0, st>>>(m, theta, shift, lam, ok);
+    nleigs_ritz_kernel<<<ceil_div(m, 128), 128, 0, st>>>(m, theta, shift, lin.lam_scale, lam, ok);
     NEP_CHECK_LAUNCH();
     NEP_TRY(zgemm(n, m, m, 0, V, (int)N, S, m, X, n, nullptr, 0, st));
     NEP_TRY(launch_normalize_columns(n, m, X, 1, nullptr, st));

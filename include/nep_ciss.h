@@ -231,6 +231,16 @@ int nep_set_wait_limit(int64_t polls, int64_t *previous);
 int nep_plan_create(nep_split_t h, const nep_region *r, int32_t N, int32_t L, int32_t M, const nep_opts *o,
                     nep_plan_t *out);
 int nep_plan_execute(nep_plan_t p, const void *V_dev, void *stream);
+/* nep_plan_execute for several plans at once, with shared launches: the banded LU and the substitution
+ * sweeps of all their quadrature points run in launches shared across the plans (one per kernel
+ * instance: points of problems of uneven n, bandwidth, N and L share a launch when their band shapes
+ * fall in the same class), the assembly, refinement residuals, moments and extraction per plan, in
+ * plan order, all on one stream, with one host read of every plan's active count per refinement
+ * sweep. Every point runs the kernel instance and arguments of its plan alone, so each plan's results
+ * are bitwise those of nep_plan_execute. V_devs[i]: plan i's probe block (device memory). Plans of one
+ * precision, each at most once, without callback or table terms.
+ * Errors: NEP_ERR_ARG, NEP_ERR_UNSUPPORTED, and those of nep_plan_execute. */
+int nep_plan_execute_batch(int32_t count, nep_plan_t *plans, const void *const *V_devs, void *stream);
 int nep_plan_result(nep_plan_t p, nep_result_t *out);
 int nep_plan_destroy(nep_plan_t p);
 /* Device buffers of a plan (for inspection/tests): name in {"F","coef","ab","ut","ipiv","info",

@@ -102,6 +102,7 @@ SIGNATURES = {
     "nep_plan_create": (c_int32, [c_void_p, ctypes.POINTER(NepRegion), c_int32, c_int32, c_int32, ctypes.POINTER(NepOpts),
                                   ctypes.POINTER(c_void_p)]),
     "nep_plan_execute": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "nep_plan_execute_batch": (c_int32, [c_int32, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), c_void_p]),
     "nep_plan_result": (c_int32, [c_void_p, ctypes.POINTER(c_void_p)]),
     "nep_plan_destroy": (c_int32, [c_void_p]),
     "nep_plan_buffer": (c_int32, [c_void_p, ctypes.c_char_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_size_t)]),
@@ -596,6 +597,14 @@ def nleigs_solve(split, region, stream=0, **opts) -> dict:
     out = _result_dict(res)
     out["degree"] = d.value
     return out
+
+
+def execute_batch(plans, V_devs, stream=0):
+    """nep_plan_execute_batch: several plans' passes with the LU and the sweeps in shared launches."""
+    k = len(plans)
+    ph = (c_void_p * k)(*[pl.handle.value if isinstance(pl.handle, c_void_p) else pl.handle for pl in plans])
+    vh = (c_void_p * k)(*[ptr(v) for v in V_devs])
+    check(load().nep_plan_execute_batch(k, ph, vh, stream))
 
 
 def interpol_coefficients(fns, region, degree) -> np.ndarray:

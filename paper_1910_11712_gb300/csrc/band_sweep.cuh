@@ -37,8 +37,17 @@ template <typename T, int RPL, bool BWD, int RH>
 __global__ void __launch_bounds__(256)
     band_sweep_kernel(int n, int kl, int ku, int ldab, const cx<T>* __restrict__ ab_all,
                       const cx<T>* __restrict__ ut_all, const int* __restrict__ ipiv_all, int L,
-                      cx<T>* __restrict__ B_all, const int* __restrict__ active, int CH) {
-    const int j = blockIdx.x;
+                      cx<T>* __restrict__ B_all, const int* __restrict__ active, int CH,
+                      const PointDesc* __restrict__ pd) {
+    int j = blockIdx.x;
+    if (pd) {  // a point of one of several problems sharing the launch (the grid covers the largest L)
+        const PointDesc d = pd[blockIdx.x];
+        n = d.n, kl = d.kl, ku = d.ku, ldab = d.ldab, L = d.L;
+        ab_all = static_cast<const cx<T>*>(d.ab), ut_all = static_cast<const cx<T>*>(d.ut), ipiv_all = d.ipiv;
+        B_all = static_cast<cx<T>*>(d.B), active = d.active;
+        j = 0;
+        if ((int)blockIdx.y * ((blockDim.x >> 5) / 2) * RH >= L) return;  // no right-hand side of this point here
+    }
     if (active && !active[j]) return;
     constexpr int RS = 32 * RPL, RSP = RS + 1;
     const int kv = kl + ku;
@@ -242,9 +251,58 @@ static int run_sweep(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* 
     if (smem > 227 * 1024) return NEP_ERR_UNSUPPORTED;
     NEP_CUDA(allow_max_dynamic_smem(band_sweep_kernel<T, RPL, BWD, RH>));
     band_sweep_kernel<T, RPL, BWD, RH><<<dim3(npts, gy), 2 * wpb * 32, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ut,
-                                                                             ipiv, L, B, active, CH);
+                                                                             ipiv, L, B, active, CH, nullptr);
     NEP_CHECK_LAUNCH();
     return NEP_OK;
+}
+
+// The same sweep over points of several problems (descriptors pd_dev[count]; maxL the most
+// right-hand sides of any of them): the launch shape of run_sweep, per-point arithmetic unchanged.
+template <typename T, int RPL, bool BWD, int RH>
+static int run_sweep_batch(int count, int maxL, const PointDesc* pd_dev, cudaStream_t st) {
+    constexpr int RSP = 32 * RPL + 1;
+    const int warps = (maxL + RH - 1) / RH;
+    const int wpb = 4;
+    const int gy = (warps + wpb - 1) / wpb;
+    auto bytes = [&](int ch) {
+        return sizeof(cx<T>) * (2 * (size_t)ch * RSP + 2 * (size_t)ch + 3 * (size_t)wpb * RH * ch) +
+               sizeof(int) * 2 * ch;
+    };
+    int CH = 32 - 32 % RPL;
+    while (CH > RPL && bytes(CH) > 200 * 1024) CH -= RPL;
+    const size_t smem = bytes(CH);
+    if (smem > 227 * 1024) return NEP_ERR_UNSUPPORTED;
+    NEP_CUDA(allow_max_dynamic_smem(band_sweep_kernel<T, RPL, BWD, RH>));
+    band_sweep_kernel<T, RPL, BWD, RH><<<dim3(count, gy), 2 * wpb * 32, smem, st>>>(0, 0, 0, 0, nullptr, nullptr,
+                                                                              nullptr, maxL, nullptr, nullptr, CH,
+                                                                              pd_dev);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+
+template <typename T, bool BWD, int RH>
+static int sweep_batch_rpl(int rpl, int count, int maxL, const PointDesc* pd, cudaStream_t st) {
+    switch (rpl) {
+        case 1: return run_sweep_batch<T, 1, BWD, RH>(count, maxL, pd, st);
+        case 2: return run_sweep_batch<T, 2, BWD, RH>(count, maxL, pd, st);
+        case 3: return run_sweep_batch<T, 3, BWD, RH>(count, maxL, pd, st);
+        case 4: return run_sweep_batch<T, 4, BWD, RH>(count, maxL, pd, st);
+        case 5: return run_sweep_batch<T, 5, BWD, RH>(count, maxL, pd, st);
+        case 6: return run_sweep_batch<T, 6, BWD, RH>(count, maxL, pd, st);
+        case 7: return run_sweep_batch<T, 7, BWD, RH>(count, maxL, pd, st);
+        case 8: return run_sweep_batch<T, 8, BWD, RH>(count, maxL, pd, st);
+        case 9: return run_sweep_batch<T, 9, BWD, RH>(count, maxL, pd, st);
+    }
+    return NEP_ERR_UNSUPPORTED;
+}
+
+template <typename T, bool BWD>
+static int sweep_batch_dispatch(int rpl, int rh, int count, int maxL, const PointDesc* pd, cudaStream_t st) {
+    switch (rh) {
+        case 1: return sweep_batch_rpl<T, BWD, 1>(rpl, count, maxL, pd, st);
+        case 4: return sweep_batch_rpl<T, BWD, 4>(rpl, count, maxL, pd, st);
+        default: return sweep_batch_rpl<T, BWD, 2>(rpl, count, maxL, pd, st);
+    }
 }
 
 // Right-hand sides per warp of the substitution sweeps. One warp per right-hand side keeps the
@@ -297,6 +355,24 @@ static int sweep_dispatch(int rpl, const SplitDev& s, int npts, const cx<T>* ab,
         case 4: return sweep_rpl<T, BWD, 4>(rpl, s, npts, ab, ut, ipiv, L, B, active, st);
         default: return sweep_rpl<T, BWD, 2>(rpl, s, npts, ab, ut, ipiv, L, B, active, st);
     }
+}
+
+// Sweep launch shape of a problem: rows per lane of the forward and backward windows and right-hand
+// sides per warp (from the problem's own chain count N L). Points of problems with equal keys share
+// batched launches.
+template <typename T>
+void sweep_key(int kl, int ku, int npts, int L, int* rplf, int* rplb, int* rh) {
+    *rplf = (kl + 1 + 31) / 32;
+    *rplb = (kl + ku + 1 + 31) / 32;
+    *rh = sweep_rh<T>(npts * L);
+}
+
+template <typename T>
+int band_sweeps_batch(int rplf, int rplb, int rh, int count, int maxL, const PointDesc* pd, cudaStream_t st) {
+    if (count <= 0 || maxL <= 0) return NEP_OK;
+    const int rc = sweep_batch_dispatch<T, false>(rplf, rh, count, maxL, pd, st);
+    if (rc != NEP_OK) return rc;
+    return sweep_batch_dispatch<T, true>(rplb, rh, count, maxL, pd, st);
 }
 
 template <typename T>

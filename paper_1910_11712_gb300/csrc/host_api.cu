@@ -9,6 +9,8 @@
 #include <atomic>
 #include <mutex>
 #include <set>
+#include <map>
+#include <tuple>
 #include <vector>
 
 #include "nep_common.cuh"
@@ -977,6 +979,130 @@ static int newton_host_functions(nep_plan* p, const SplitDev& s, int kb, int m, 
     return NEP_OK;
 }
 
+// ----------------------------------------------------------------- several plans, shared launches
+// The quadrature solves of several plans (problems of uneven n, bandwidth, N and L) with the banded
+// LU and the substitution sweeps of all their points in shared launches: one per kernel instance
+// (points of equal band shape class), the rest per plan. Each point runs the same kernel instance
+// with the same arguments as in its plan alone, so every result is bitwise the plan's own.
+template <typename T>
+static int run_solves_batch(const std::vector<nep_plan*>& ps, cudaStream_t st) {
+    StreamScratch scratch(st);
+    std::vector<std::vector<PointDesc>> keep;  // host copies live until the launches that read them
+    auto upload = [&](const std::vector<PointDesc>& v, PointDesc** out) -> int {
+        keep.push_back(v);
+        NEP_TRY(scratch.get(out, v.size()));
+        NEP_CUDA(cudaMemcpyAsync(*out, keep.back().data(), sizeof(PointDesc) * v.size(), cudaMemcpyHostToDevice, st));
+        return NEP_OK;
+    };
+    auto point = [&](nep_plan* p, int j, void* B, const int* active) {
+        const nep_split* h = p->h;
+        PointDesc d{};
+        d.n = h->n, d.kl = h->kl, d.ku = h->ku, d.ldab = h->ldab, d.L = p->L;
+        d.ab = reinterpret_cast<cx<T>*>(p->ab) + (int64_t)j * h->n * h->ldab;
+        d.ut = p->ut ? reinterpret_cast<const cx<T>*>(p->ut) + (int64_t)j * h->n * (h->kl + h->ku + 1) : nullptr;
+        d.ipiv = p->ipiv + (int64_t)j * h->n;
+        d.info = p->info + j;
+        d.B = B ? reinterpret_cast<cx<T>*>(B) + (int64_t)j * h->n * p->L : nullptr;
+        d.active = active ? active + j : nullptr;
+        return d;
+    };
+    // assembly, per plan
+    for (nep_plan* p : ps) {
+        const SplitDev s = p->h->dev();
+        NEP_CUDA(cudaEventRecord(p->ev[0], st));
+        NEP_TRY(launch_assemble<T>(s, p->Np, p->F, reinterpret_cast<cx<T>*>(p->ab), p->tnorm, p->tval, st));
+        NEP_CUDA(cudaEventRecord(p->ev[1], st));
+    }
+    // LU: register-window instances and the tensor-core kernel over all points; other shapes per plan
+    std::map<int, std::vector<PointDesc>> col;
+    std::vector<PointDesc> tc;
+    for (nep_plan* p : ps) {
+        const SplitDev s = p->h->dev();
+        if (band_lu_col_fits(s.kl, s.ku)) {
+            for (int j = 0; j < p->Np; ++j) col[lu_col_instance(s.kl, s.ku)].push_back(point(p, j, nullptr, nullptr));
+        } else if (sizeof(T) == 4 && lu_tc_enabled() && band_lu_tc_fits(s.kl)) {
+            for (int j = 0; j < p->Np; ++j) tc.push_back(point(p, j, nullptr, nullptr));
+        } else {
+            NEP_TRY(launch_band_lu<T>(s, p->Np, reinterpret_cast<cx<T>*>(p->ab), p->ipiv, p->info, nullptr, st));
+        }
+    }
+    for (auto& g : col) {
+        PointDesc* pd = nullptr;
+        NEP_TRY(upload(g.second, &pd));
+        NEP_TRY(launch_band_lu_col_batch<T>(g.first, (int)g.second.size(), pd, st));
+    }
+    if (!tc.empty()) NEP_TRY(launch_band_lu_tc_batch(tc, st));
+    for (nep_plan* p : ps) {
+        const SplitDev s = p->h->dev();
+        if (p->ut) NEP_TRY(band_transpose_u<T>(s, p->Np, reinterpret_cast<cx<T>*>(p->ab), reinterpret_cast<cx<T>*>(p->ut), st));
+        NEP_CUDA(cudaEventRecord(p->ev[2], st));
+    }
+    // one solve of every live plan's points: register-window sweeps in shared launches per shape key
+    auto solve_all = [&](const std::vector<nep_plan*>& live, bool masked) -> int {
+        std::map<std::tuple<int, int, int>, std::vector<PointDesc>> groups;
+        std::map<std::tuple<int, int, int>, int> maxL;
+        for (nep_plan* p : live) {
+            const SplitDev s = p->h->dev();
+            if (p->ut) {
+                int a, b, r;
+                sweep_key<T>(s.kl, s.ku, p->Np, p->L, &a, &b, &r);
+                const auto key = std::make_tuple(a, b, r);
+                for (int j = 0; j < p->Np; ++j) groups[key].push_back(point(p, j, p->D, masked ? p->active : nullptr));
+                maxL[key] = std::max(maxL[key], p->L);
+            } else {
+                NEP_TRY(launch_band_solve<T>(s, p->Np, reinterpret_cast<cx<T>*>(p->ab), nullptr, p->ipiv, p->L,
+                                             reinterpret_cast<cx<T>*>(p->D), masked ? p->active : nullptr, st));
+            }
+        }
+        for (auto& g : groups) {
+            PointDesc* pd = nullptr;
+            NEP_TRY(upload(g.second, &pd));
+            NEP_TRY(band_sweeps_batch<T>(std::get<0>(g.first), std::get<1>(g.first), std::get<2>(g.first),
+                                         (int)g.second.size(), maxL[g.first], pd, st));
+        }
+        return NEP_OK;
+    };
+    for (nep_plan* p : ps) NEP_TRY(launch_convert_rhs<T>(p->Np, p->h->n, p->L, p->V, reinterpret_cast<cx<T>*>(p->D), st));
+    NEP_TRY(solve_all(ps, false));
+    for (nep_plan* p : ps) {
+        const int N = p->Np, n = p->h->n, L = p->L;
+        NEP_TRY(launch_widen<T>(N, n, L, reinterpret_cast<cx<T>*>(p->D), p->Y, st));
+        NEP_TRY(launch_fill_int(N, p->active, 1, st));
+        NEP_CUDA(cudaMemsetAsync(p->prev, 0, sizeof(double) * N, st));
+        NEP_CUDA(cudaMemsetAsync(p->sweeps, 0, sizeof(int) * N, st));
+        NEP_TRY(launch_drop_singular(N, n, L, p->info, p->Y, p->active, p->beta, st));
+    }
+    // refinement: each plan's sweeps as alone, the solves of all live plans shared; one host read of
+    // every plan's active count per sweep
+    std::vector<nep_plan*> live;
+    for (nep_plan* p : ps)
+        if (p->o.refine_max > 0) live.push_back(p);
+    for (int sweep = 0; !live.empty(); ++sweep) {
+        for (nep_plan* p : live) {
+            const SplitDev s = p->h->dev();
+            NEP_TRY(launch_split_residual(s, p->Np, p->tval, p->L, p->V, p->Y, p->R, p->nrm, p->active, st));
+            NEP_TRY(launch_refine_prepare<T>(p->Np, s.n, p->L, p->R, reinterpret_cast<cx<T>*>(p->D), p->active, st));
+        }
+        NEP_TRY(solve_all(live, true));
+        for (nep_plan* p : live) {
+            const SplitDev s = p->h->dev();
+            NEP_TRY(launch_refine_update<T>(p->Np, s.n, p->L, reinterpret_cast<cx<T>*>(p->D), p->Y, p->dmax, p->ymax,
+                                            p->active, st));
+            NEP_TRY(launch_refine_decide(p->Np, p->L, sweep, p->o.refine_max, p->o.refine_tol, p->o.step_tol,
+                                         p->o.refine_extrapolate, p->nrm, p->tnorm, p->dmax, p->ymax, p->prev, p->beta,
+                                         p->active, p->sweeps, p->nactive, st));
+            NEP_CUDA(cudaMemcpyAsync(p->h_pinned, p->nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+        }
+        NEP_CUDA(cudaStreamSynchronize(st));
+        std::vector<nep_plan*> next;
+        for (nep_plan* p : live)
+            if (p->h_pinned[0] != 0 && sweep + 1 < p->o.refine_max) next.push_back(p);
+        live.swap(next);
+    }
+    for (nep_plan* p : ps) NEP_CUDA(cudaEventRecord(p->ev[3], st));
+    return NEP_OK;
+}
+
 static int read_scalar(nep_plan* p, const int* dptr, int* out, cudaStream_t st) {
     NEP_CUDA(cudaMemcpyAsync(p->h_pinned, dptr, sizeof(int), cudaMemcpyDeviceToHost, st));
     NEP_CUDA(cudaStreamSynchronize(st));
@@ -1086,6 +1212,42 @@ extern "C" int nep_plan_execute(nep_plan_t p, const void* V_dev, void* stream) {
     int err = 0;
     NEP_TRY(read_scalar(p, p->jw.err, &err, st));
     if (err) { set_error("a bounded grid barrier of the Jacobi SVD timed out"); return NEP_ERR_INTERNAL; }
+    return NEP_OK;
+}
+
+extern "C" int nep_plan_execute_batch(int32_t count, nep_plan_t* plans, const void* const* V_devs, void* stream) {
+    if (count < 1 || !plans || !V_devs) { set_error("nep_plan_execute_batch: bad arguments"); return NEP_ERR_ARG; }
+    std::vector<nep_plan*> ps;
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i] || !V_devs[i]) { set_error("nep_plan_execute_batch: null plan or V at %d", i); return NEP_ERR_ARG; }
+        for (nep_plan* q : ps)
+            if (q == plans[i]) { set_error("nep_plan_execute_batch: plan %d appears twice", i); return NEP_ERR_ARG; }
+        if (plans[i]->mixed != plans[0]->mixed) { set_error("nep_plan_execute_batch: plans of one precision only"); return NEP_ERR_ARG; }
+        if (plans[i]->h->has_ext) { set_error("nep_plan_execute_batch: callback or table terms are not batched"); return NEP_ERR_UNSUPPORTED; }
+        ps.push_back(plans[i]);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < count; ++i) {
+        nep_plan* p = ps[i];
+        const int n = p->h->n, L = p->L;
+        NEP_CUDA(cudaMemcpyAsync(p->V, V_devs[i], sizeof(zd) * (size_t)n * L, cudaMemcpyDeviceToDevice, st));
+        if (p->Np != p->N) {
+            NEP_TRY(launch_count_imag(int64_t(n) * L, p->V, p->scalars + 3, st));
+            int nim = 0;
+            NEP_TRY(read_scalar(p, p->scalars + 3, &nim, st));
+            if (nim) { set_error("plan %d: symmetric quadrature needs a real V", i); return NEP_ERR_ARG; }
+        }
+        NEP_CUDA(cudaMemsetAsync(p->jw.err, 0, sizeof(int), st));
+    }
+    int rc = ps[0]->mixed ? run_solves_batch<float>(ps, st) : run_solves_batch<double>(ps, st);
+    if (rc) return rc;
+    for (nep_plan* p : ps) {
+        NEP_TRY(run_extract(p, st));
+        NEP_CUDA(cudaEventRecord(p->ev[5], st));
+        int err = 0;
+        NEP_TRY(read_scalar(p, p->jw.err, &err, st));
+        if (err) { set_error("a bounded grid barrier of the Jacobi SVD timed out"); return NEP_ERR_INTERNAL; }
+    }
     return NEP_OK;
 }
 

@@ -82,7 +82,7 @@ __device__ __forceinline__ cx<T> mask_cx(cx<T> v, bool z) {
 template <typename T, int RPL, int CPW>
 __global__ void __launch_bounds__(512, 1)
     lu_col_kernel(int n, int kl, int ku, int ldab, cx<T>* __restrict__ ab_all, int* __restrict__ ipiv_all,
-                  int* __restrict__ info_all, const int* __restrict__ active) {
+                  int* __restrict__ info_all, const int* __restrict__ active, const PointDesc* __restrict__ pd) {
     constexpr int NW = 16, PF = 8, RING = PF + 2, CS = NW * CPW;  // CS a power of two
     // complex float: the column registers pair up, (2h, 2h+1), one 64-bit register for the two
     // real parts of a row and one for the imaginary parts. With u = (u0, u1) the pivot row on the
@@ -92,7 +92,13 @@ __global__ void __launch_bounds__(512, 1)
     constexpr bool PAIRED = sizeof(T) == 4 && CPW % 2 == 0;
     constexpr int CPH = PAIRED ? CPW / 2 : 1;
     static_assert((CS & (CS - 1)) == 0, "column slots must be a power of two");
-    const int j = blockIdx.x;
+    int j = blockIdx.x;
+    if (pd) {  // a point of one of several problems sharing the launch
+        const PointDesc d = pd[blockIdx.x];
+        n = d.n, kl = d.kl, ku = d.ku, ldab = d.ldab;
+        ab_all = static_cast<cx<T>*>(d.ab), ipiv_all = d.ipiv, info_all = d.info, active = d.active;
+        j = 0;
+    }
     if (active && !active[j]) return;
     const int kv = kl + ku;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -467,20 +473,21 @@ __global__ void __launch_bounds__(512, 1)
 bool band_lu_col_fits(int kl, int ku) { return kl >= 1 && kl <= 64 && ku >= 0 && kl + ku <= 128; }
 
 template <typename T, int RPL, int CPW>
-static int run_col(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st) {
-    lu_col_kernel<T, RPL, CPW><<<npts, 512, 0, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, info, active);
+static int run_col(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st,
+                   const PointDesc* pd = nullptr) {
+    lu_col_kernel<T, RPL, CPW><<<npts, 512, 0, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, info, active, pd);
     NEP_CHECK_LAUNCH();
     return NEP_OK;
 }
 
 template <typename T, int RPL>
-static int col_cpw(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st) {
+static int col_cpw(int kv, const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active,
+                   cudaStream_t st, const PointDesc* pd) {
     // 16 warps x CPW column slots >= kl + ku, CPW a power of two
-    const int kv = s.kl + s.ku;
-    if (kv <= 16) return run_col<T, RPL, 1>(s, npts, ab, ipiv, info, active, st);
-    if (kv <= 32) return run_col<T, RPL, 2>(s, npts, ab, ipiv, info, active, st);
-    if (kv <= 64) return run_col<T, RPL, 4>(s, npts, ab, ipiv, info, active, st);
-    return run_col<T, RPL, 8>(s, npts, ab, ipiv, info, active, st);
+    if (kv <= 16) return run_col<T, RPL, 1>(s, npts, ab, ipiv, info, active, st, pd);
+    if (kv <= 32) return run_col<T, RPL, 2>(s, npts, ab, ipiv, info, active, st, pd);
+    if (kv <= 64) return run_col<T, RPL, 4>(s, npts, ab, ipiv, info, active, st, pd);
+    return run_col<T, RPL, 8>(s, npts, ab, ipiv, info, active, st, pd);
 }
 
 template <typename T>
@@ -488,9 +495,25 @@ int launch_band_lu_col(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* i
                        cudaStream_t st) {
     if (npts <= 0) return NEP_OK;
     if (!band_lu_col_fits(s.kl, s.ku)) return NEP_ERR_INTERNAL;
-    return s.kl <= 32 ? col_cpw<T, 1>(s, npts, ab, ipiv, info, active, st)
-                      : col_cpw<T, 2>(s, npts, ab, ipiv, info, active, st);
+    return s.kl <= 32 ? col_cpw<T, 1>(s.kl + s.ku, s, npts, ab, ipiv, info, active, st, nullptr)
+                      : col_cpw<T, 2>(s.kl + s.ku, s, npts, ab, ipiv, info, active, st, nullptr);
 }
+
+int lu_col_instance(int kl, int ku) {
+    const int kv = kl + ku;
+    return (kl <= 32 ? 0 : 4) + (kv <= 16 ? 0 : kv <= 32 ? 1 : kv <= 64 ? 2 : 3);
+}
+
+template <typename T>
+int launch_band_lu_col_batch(int instance, int count, const PointDesc* pd_dev, cudaStream_t st) {
+    if (count <= 0) return NEP_OK;
+    SplitDev s{};  // sizes and buffers come from the descriptors
+    const int kv = (instance & 3) == 0 ? 16 : (instance & 3) == 1 ? 32 : (instance & 3) == 2 ? 64 : 128;
+    return instance < 4 ? col_cpw<T, 1>(kv, s, count, nullptr, nullptr, nullptr, nullptr, st, pd_dev)
+                        : col_cpw<T, 2>(kv, s, count, nullptr, nullptr, nullptr, nullptr, st, pd_dev);
+}
+template int launch_band_lu_col_batch<float>(int, int, const PointDesc*, cudaStream_t);
+template int launch_band_lu_col_batch<double>(int, int, const PointDesc*, cudaStream_t);
 
 template int launch_band_lu_col<float>(const SplitDev&, int, cx<float>*, int*, int*, const int*, cudaStream_t);
 template int launch_band_lu_col<double>(const SplitDev&, int, cx<double>*, int*, int*, const int*, cudaStream_t);

@@ -68,15 +68,24 @@ __global__ void __launch_bounds__(512, 1)
     lu_tc_kernel(int n, int kl, int ku, int ldab, zf* __restrict__ ab_all, int* __restrict__ ipiv_all,
                  int* __restrict__ info_all, const int* __restrict__ active, zf* __restrict__ win_all, int RWp,
                  int CWp, float* __restrict__ aimg_all, int nmt_max, const __grid_constant__ CUtensorMap tmap,
-                 int* __restrict__ err) {
-    const int j = blockIdx.x;
-    if (active && !active[j]) return;
+                 int* __restrict__ err, const PointDesc* __restrict__ pd) {
+    const int j = blockIdx.x;  // also the point's operand image and its TMA coordinate
+    zf* ab = ab_all + (int64_t)j * n * ldab;
+    int* ipiv = ipiv_all + (int64_t)j * n;
+    int* info_out = info_all + j;
+    zf* W = win_all + (int64_t)j * RWp * CWp;
+    if (pd) {  // a point of one of several problems sharing the launch
+        const PointDesc d = pd[j];
+        n = d.n, kl = d.kl, ku = d.ku, ldab = d.ldab, RWp = d.RWp, CWp = d.CWp;
+        ab = static_cast<zf*>(d.ab), ipiv = d.ipiv, info_out = d.info, W = static_cast<zf*>(d.win);
+        active = d.active;
+        if (active && !active[0]) return;
+    } else if (active && !active[j]) {
+        return;
+    }
     const int kv = kl + ku;
     const int RW = kl + NB;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nthr = blockDim.x, nwarp = nthr >> 5;
-    zf* ab = ab_all + (int64_t)j * n * ldab;
-    int* ipiv = ipiv_all + (int64_t)j * n;
-    zf* W = win_all + (int64_t)j * RWp * CWp;
     float* aimg = aimg_all + (int64_t)j * nmt_max * (TILE_BYTES / 4);
     auto wi = [&](int r, int c) -> int64_t { return (int64_t)(r % RWp) + (int64_t)RWp * (c % CWp); };
 
@@ -513,7 +522,7 @@ __global__ void __launch_bounds__(512, 1)
         tc::tc_fence_after();
         tc::tmem_dealloc(tmem, TMEM_COLS);
     }
-    if (tid == 0) info_all[j] = *abort_v ? n + 1 : info_s;
+    if (tid == 0) *info_out = *abort_v ? n + 1 : info_s;
 }
 
 // ------------------------------------------------------------------ host side
@@ -584,7 +593,7 @@ int launch_band_lu_tc(const SplitDev& s, int npts, zf* ab, int* ipiv, int* info,
     if (e == cudaSuccess) e = allow_max_dynamic_smem(lu_tc_kernel);
     if (e == cudaSuccess) {
         lu_tc_kernel<<<npts, 512, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, info, active, win, rwp, cwp, aimg,
-                                              nmt_max, tmap, err);
+                                              nmt_max, tmap, err, nullptr);
         count_launch();
         e = cudaGetLastError();
     }
@@ -595,6 +604,76 @@ int launch_band_lu_tc(const SplitDev& s, int npts, zf* ab, int* ipiv, int* info,
     if (aimg) cudaFreeAsync(aimg, st);
     if (err) cudaFreeAsync(err, st);
     if (e != cudaSuccess) return cuda_fail(e, "lu_tc_kernel", __FILE__, __LINE__);
+    if (herr) {
+        set_error("lu_tc_kernel: a bounded wait on the tensor-core pipeline expired");
+        return NEP_ERR_INTERNAL;
+    }
+    return NEP_OK;
+}
+
+// The tensor-core LU over points of several complex64 problems (each with kl > 64 and within the
+// shared-memory budget): windows per point, one operand-image array and tensor map for the batch.
+int launch_band_lu_tc_batch(const std::vector<PointDesc>& items_in, cudaStream_t st) {
+    const int count = (int)items_in.size();
+    if (count <= 0) return NEP_OK;
+    auto encode = encode_fn();
+    if (!encode) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return NEP_ERR_CUDA;
+    }
+    std::vector<PointDesc> items(items_in);
+    size_t smem = 0, win_elems = 0;
+    int nmt_max = 1;
+    for (auto& d : items) {
+        if (!band_lu_tc_fits(d.kl)) return NEP_ERR_UNSUPPORTED;
+        const int kv = d.kl + d.ku;
+        d.RWp = (d.kl + NB + NB - 1) / NB * NB;
+        d.CWp = (kv + NB + NB - 1) / NB * NB;
+        win_elems += (size_t)d.RWp * d.CWp;
+        smem = std::max(smem, lu_tc_smem(d.kl));
+        nmt_max = std::max(nmt_max, (d.kl + MT - 1) / MT);
+    }
+    zf* win = nullptr;
+    float* aimg = nullptr;
+    int* err = nullptr;
+    PointDesc* pd = nullptr;
+    NEP_CUDA(cudaMallocAsync((void**)&win, sizeof(zf) * win_elems, st));
+    cudaError_t e = cudaMallocAsync((void**)&aimg, (size_t)TILE_BYTES * nmt_max * count, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&err, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&pd, sizeof(PointDesc) * count, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    size_t off = 0;
+    for (auto& d : items) {
+        d.win = win + off;
+        off += (size_t)d.RWp * d.CWp;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pd, items.data(), sizeof(PointDesc) * count, cudaMemcpyHostToDevice, st);
+    CUtensorMap tmap;
+    if (e == cudaSuccess) {
+        const cuuint64_t dims[3] = {64, (cuuint64_t)nmt_max * 256, (cuuint64_t)count};
+        const cuuint64_t strides[2] = {256, (cuuint64_t)nmt_max * TILE_BYTES};
+        const cuuint32_t box[3] = {64, 256, 1};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        if (encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, aimg, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            e = cudaErrorInvalidValue;
+    }
+    if (e == cudaSuccess) e = allow_max_dynamic_smem(lu_tc_kernel);
+    if (e == cudaSuccess) {
+        lu_tc_kernel<<<count, 512, smem, st>>>(0, 0, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, aimg,
+                                               nmt_max, tmap, err, pd);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (win) cudaFreeAsync(win, st);
+    if (aimg) cudaFreeAsync(aimg, st);
+    if (err) cudaFreeAsync(err, st);
+    if (pd) cudaFreeAsync(pd, st);
+    if (e != cudaSuccess) return cuda_fail(e, "lu_tc_kernel (batch)", __FILE__, __LINE__);
     if (herr) {
         set_error("lu_tc_kernel: a bounded wait on the tensor-core pipeline expired");
         return NEP_ERR_INTERNAL;

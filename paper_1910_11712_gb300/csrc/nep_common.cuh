@@ -90,6 +90,20 @@ template <typename T, typename U> __host__ __device__ __forceinline__ cx<T> cvt(
 // ----------------------------------------------------------------- scalar functions
 // Flattened function tree: node k has kind/op, scaling alpha/beta, shift, coefficient
 // ranges into a shared coefficient pool, and child node indices (combine).
+// One quadrature point of some problem in a launch shared by several problems: a kernel given an
+// array of these takes block b's sizes and buffers from entry b instead of its uniform arguments
+// (point index 0 within them), with the same arithmetic per point.
+struct PointDesc {
+    int n, kl, ku, ldab, L, RWp, CWp, pad;
+    void* ab;           // this point's band (factors)
+    const void* ut;     // its column copy of U (sweeps)
+    int* ipiv;
+    int* info;
+    void* B;            // its right-hand sides, n x L column-major
+    const int* active;  // its refinement flag, or nullptr
+    void* win;          // its LU window (wide bands)
+};
+
 struct FnNode {
     int kind, op, a, b;
     int num_off, num_len, den_off, den_len;
@@ -241,6 +255,18 @@ int launch_band_lu_col(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* i
                        cudaStream_t st);
 // Blocked LU for wide bands (lu_wide.cu): panel in shared memory, trailing window in global memory.
 bool band_lu_wide_fits(int kl, int elem_bytes);
+// Points of several problems in shared launches (PointDesc arrays on the device):
+// the register-window LU's template instance of a band shape (points with equal instances share a launch)
+int lu_col_instance(int kl, int ku);
+template <typename T>
+int launch_band_lu_col_batch(int instance, int count, const PointDesc* pd_dev, cudaStream_t st);
+// the narrow-band sweeps' launch shape of a problem, and the sweeps over points of equal shape
+template <typename T>
+void sweep_key(int kl, int ku, int npts, int L, int* rplf, int* rplb, int* rh);
+template <typename T>
+int band_sweeps_batch(int rplf, int rplb, int rh, int count, int maxL, const PointDesc* pd, cudaStream_t st);
+// the tensor-core LU over points of several complex64 problems (each kl > 64)
+int launch_band_lu_tc_batch(const std::vector<PointDesc>& items, cudaStream_t st);
 template <typename T>
 int launch_band_lu_wide(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active,
                         cudaStream_t st);

@@ -153,6 +153,11 @@ typedef struct {
     int32_t refine_extrapolate; /* shortcut: a refinement sweep also stops when the contraction  */
                                 /* seen so far puts the next correction below step_tol          */
                                 /* (default 1; 0: stop only on step_tol or no halving)           */
+    int32_t lu_kernel;  /* LU of complex64 bands with kl > 64: 0 the tuned or default choice, 1 tensor    */
+                        /* core with TF32 hi/lo operands (3 products, ~FP32), 2 tensor core with TF32     */
+                        /* operands (1 product), 3 FP32 SIMT kernel. Results of 1-3 differ by rounding.   */
+    int32_t solve_rh;   /* right-hand sides per warp of the narrow-band sweeps: 0 tuned or default, 1, 2, */
+                        /* 4 (a launch shape only: results identical)                                     */
 } nep_opts;
 
 /* Defaults listed above. */
@@ -248,6 +253,30 @@ int nep_plan_destroy(nep_plan_t p);
  * "newton_lambda"}; returns the device pointer and its bytes ("ut" is empty for bands too wide
  * for the narrow-band sweeps). */
 int nep_plan_buffer(nep_plan_t p, const char *name, void **dev_ptr, size_t *bytes);
+
+/* ------------------------------------------------------------------ autotuning */
+/* The implementation's own choices for a problem shape (the paper has no counterpart): nep_autotune
+ * times full passes (nep_plan_execute; one warm-up, the mean of two, CUDA events on the stream) of
+ * every candidate of opts->lu_kernel (complex64 bands with kl > 64: tensor core with TF32 hi/lo
+ * operands, tensor core with TF32 operands, FP32 SIMT) times opts->solve_rh (1, 2, 4 for the narrow-band
+ * sweeps), each on its own plan of this shape, and keeps the fastest candidate whose quadrature solves
+ * all reach the backward-error target (no NEP_WARN_REFINE, max backward error <= refine_tol: accuracy
+ * is part of the objective; a TF32-operand LU that refinement cannot repair is never chosen). The
+ * choice goes into a process-wide table keyed by (n, kl, ku, L, precision), which later plans of that
+ * shape use when their opts leave lu_kernel / solve_rh at 0, and, if cache_path is not NULL, is appended
+ * to that text file (one line per tuned shape) for nep_tune_load. V_dev: the probe block (device).
+ * Errors: NEP_ERR_ARG, NEP_ERR_UNSUPPORTED (callback or table terms), NEP_ERR_INTERNAL (no candidate
+ * met the accuracy target), and those of nep_plan_create / nep_plan_execute. */
+typedef struct {
+    int32_t lu_kernel, solve_rh;  /* the choice (as nep_opts; 0: not applicable to this shape) */
+    double ms;                    /* its device time per pass                              */
+    int32_t candidates, accurate; /* candidates timed, and those meeting the accuracy target */
+} nep_tune_result;
+int nep_autotune(nep_split_t h, const nep_region *r, int32_t N, int32_t L, int32_t M, const nep_opts *o,
+                 const void *V_dev, const char *cache_path, nep_tune_result *out, void *stream);
+/* Loads a cache file written by nep_autotune into the process-wide table (later lines win);
+ * *entries (or NULL) receives the number of lines read. Errors: NEP_ERR_ARG (no such file). */
+int nep_tune_load(const char *path, int32_t *entries);
 
 /* ------------------------------------------------------------------ residual inverse iteration */
 /* Polish of eigenpair estimates by residual inverse iteration (Sec. 4.1, Algorithm (rii),

@@ -52,7 +52,8 @@ class NepOpts(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("rank_tol", c_double), ("basis_tol", c_double), ("refine_tol", c_double),
                 ("step_tol", c_double), ("refine_max", c_int32), ("eig_tol", c_double), ("newton_max", c_int32),
                 ("newton_tol", c_double), ("seed", ctypes.c_uint64), ("symmetric", c_int32),
-                ("newton_abandon", c_int32), ("refine_extrapolate", c_int32)]
+                ("newton_abandon", c_int32), ("refine_extrapolate", c_int32), ("lu_kernel", c_int32),
+                ("solve_rh", c_int32)]
 
 
 class NepNleigsOpts(ctypes.Structure):
@@ -64,6 +65,11 @@ class NepNleigsOpts(ctypes.Structure):
 class NepInterpolOpts(ctypes.Structure):
     _fields_ = [("degree", c_int32), ("krylov", c_int32), ("has_shift", c_int32), ("shift_re", c_double),
                 ("shift_im", c_double), ("seed", ctypes.c_uint64), ("eig_tol", c_double), ("fast_solves", c_int32)]
+
+
+class NepTuneResult(ctypes.Structure):
+    _fields_ = [("lu_kernel", c_int32), ("solve_rh", c_int32), ("ms", c_double), ("candidates", c_int32),
+                ("accurate", c_int32)]
 
 
 class NepResultInfo(ctypes.Structure):
@@ -102,6 +108,9 @@ SIGNATURES = {
     "nep_plan_create": (c_int32, [c_void_p, ctypes.POINTER(NepRegion), c_int32, c_int32, c_int32, ctypes.POINTER(NepOpts),
                                   ctypes.POINTER(c_void_p)]),
     "nep_plan_execute": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "nep_autotune": (c_int32, [c_void_p, ctypes.POINTER(NepRegion), c_int32, c_int32, c_int32, ctypes.POINTER(NepOpts),
+                               c_void_p, ctypes.c_char_p, ctypes.POINTER(NepTuneResult), c_void_p]),
+    "nep_tune_load": (c_int32, [ctypes.c_char_p, ctypes.POINTER(c_int32)]),
     "nep_plan_execute_batch": (c_int32, [c_int32, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), c_void_p]),
     "nep_plan_result": (c_int32, [c_void_p, ctypes.POINTER(c_void_p)]),
     "nep_plan_destroy": (c_int32, [c_void_p]),
@@ -597,6 +606,21 @@ def nleigs_solve(split, region, stream=0, **opts) -> dict:
     out = _result_dict(res)
     out["degree"] = d.value
     return out
+
+
+def autotune(split, region, N, L, M, V_dev, cache_path=None, stream=0, **opts) -> dict:
+    """nep_autotune: the fastest accurate (lu_kernel, solve_rh) for this shape, kept for later plans."""
+    r, o, t = region_struct(region), opts_struct(**opts), NepTuneResult()
+    cp = cache_path.encode() if cache_path else None
+    check(load().nep_autotune(split.handle, ctypes.byref(r), N, L, M, ctypes.byref(o), ptr(V_dev), cp,
+                              ctypes.byref(t), stream))
+    return {f: getattr(t, f) for f, _ in NepTuneResult._fields_}
+
+
+def tune_load(path) -> int:
+    n = c_int32()
+    check(load().nep_tune_load(path.encode(), ctypes.byref(n)))
+    return n.value
 
 
 def execute_batch(plans, V_devs, stream=0):

@@ -192,14 +192,16 @@ __global__ void __launch_bounds__(1024, 1)
 
 // ------------------------------------------------------------------ dispatch
 template <typename T>
-int launch_band_lu(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st) {
+int launch_band_lu(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st,
+                   int lu_kernel) {
     if (npts <= 0) return NEP_OK;
     const int kv = s.kl + s.ku;
     // register window, one barrier per step (lu_col.cu): kl <= 64, kv <= 128
     if (band_lu_col_fits(s.kl, s.ku)) return launch_band_lu_col<T>(s, npts, ab, ipiv, info, active, st);
     // wide bands in complex64: trailing updates on the tensor core
     if constexpr (sizeof(T) == 4)
-        if (lu_tc_enabled() && band_lu_tc_fits(s.kl)) return launch_band_lu_tc(s, npts, ab, ipiv, info, active, st);
+        if (lu_kernel != LU_SIMT && (lu_kernel != LU_AUTO || lu_tc_enabled()) && band_lu_tc_fits(s.kl))
+            return launch_band_lu_tc(s, npts, ab, ipiv, info, active, st, lu_kernel == LU_TC1 ? 1 : 3);
     // wide bands: blocked LU with the trailing window in global memory
     if (s.kl >= 1 && band_lu_wide_fits(s.kl, (int)sizeof(cx<T>)))
         return launch_band_lu_wide<T>(s, npts, ab, ipiv, info, active, st);
@@ -219,8 +221,8 @@ int launch_band_lu(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info,
     return NEP_OK;
 }
 
-template int launch_band_lu<float>(const SplitDev&, int, cx<float>*, int*, int*, const int*, cudaStream_t);
-template int launch_band_lu<double>(const SplitDev&, int, cx<double>*, int*, int*, const int*, cudaStream_t);
+template int launch_band_lu<float>(const SplitDev&, int, cx<float>*, int*, int*, const int*, cudaStream_t, int);
+template int launch_band_lu<double>(const SplitDev&, int, cx<double>*, int*, int*, const int*, cudaStream_t, int);
 
 // ------------------------------------------------------------------ banded solves
 // One warp per right-hand side column, one CTA per (point, group of columns). Forward
@@ -411,12 +413,12 @@ __global__ void __launch_bounds__(512)
 
 template <typename T>
 int launch_band_solve(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* ut, const int* ipiv, int L, cx<T>* B,
-                      const int* active, cudaStream_t st) {
+                      const int* active, cudaStream_t st, int rh_force) {
     if (npts <= 0 || L <= 0) return NEP_OK;
     const int kv = s.kl + s.ku;
     // register windows for narrow bands (kl+1 <= 288 and kv+1 <= 288 rows): two sweeps with
     // slot-ordered coefficients
-    if (band_sweeps_fit(s.kl, s.ku)) return band_sweeps<T>(s, npts, ab, ut, ipiv, L, B, active, st);
+    if (band_sweeps_fit(s.kl, s.ku)) return band_sweeps<T>(s, npts, ab, ut, ipiv, L, B, active, st, rh_force);
     // general path: shared-memory windows, one right-hand side per warp, four warps per CTA
     constexpr int RH = 1;
     const int warps_total = L;
@@ -441,8 +443,8 @@ int launch_band_solve(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>*
 }
 
 template int launch_band_solve<float>(const SplitDev&, int, const cx<float>*, const cx<float>*, const int*, int,
-                                      cx<float>*, const int*, cudaStream_t);
+                                      cx<float>*, const int*, cudaStream_t, int);
 template int launch_band_solve<double>(const SplitDev&, int, const cx<double>*, const cx<double>*, const int*, int,
-                                       cx<double>*, const int*, cudaStream_t);
+                                       cx<double>*, const int*, cudaStream_t, int);
 
 }  // namespace nep

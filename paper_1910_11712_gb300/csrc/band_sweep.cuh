@@ -349,8 +349,8 @@ static int sweep_rpl(int rpl, const SplitDev& s, int npts, const cx<T>* ab, cons
 
 template <typename T, bool BWD>
 static int sweep_dispatch(int rpl, const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* ut, const int* ipiv,
-                          int L, cx<T>* B, const int* active, cudaStream_t st) {
-    switch (sweep_rh<T>(npts * L)) {
+                          int L, cx<T>* B, const int* active, cudaStream_t st, int rh_force) {
+    switch (rh_force == 1 || rh_force == 2 || rh_force == 4 ? rh_force : sweep_rh<T>(npts * L)) {
         case 1: return sweep_rpl<T, BWD, 1>(rpl, s, npts, ab, ut, ipiv, L, B, active, st);
         case 4: return sweep_rpl<T, BWD, 4>(rpl, s, npts, ab, ut, ipiv, L, B, active, st);
         default: return sweep_rpl<T, BWD, 2>(rpl, s, npts, ab, ut, ipiv, L, B, active, st);
@@ -361,10 +361,10 @@ static int sweep_dispatch(int rpl, const SplitDev& s, int npts, const cx<T>* ab,
 // sides per warp (from the problem's own chain count N L). Points of problems with equal keys share
 // batched launches.
 template <typename T>
-void sweep_key(int kl, int ku, int npts, int L, int* rplf, int* rplb, int* rh) {
+void sweep_key(int kl, int ku, int npts, int L, int* rplf, int* rplb, int* rh, int rh_force) {
     *rplf = (kl + 1 + 31) / 32;
     *rplb = (kl + ku + 1 + 31) / 32;
-    *rh = sweep_rh<T>(npts * L);
+    *rh = rh_force == 1 || rh_force == 2 || rh_force == 4 ? rh_force : sweep_rh<T>(npts * L);
 }
 
 template <typename T>
@@ -377,13 +377,13 @@ int band_sweeps_batch(int rplf, int rplb, int rh, int count, int maxL, const Poi
 
 template <typename T>
 int band_sweeps(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* ut, const int* ipiv, int L, cx<T>* B,
-                const int* active, cudaStream_t st) {
+                const int* active, cudaStream_t st, int rh_force) {
     if (npts <= 0 || L <= 0) return NEP_OK;
     if (!band_sweeps_fit(s.kl, s.ku) || !ut) return NEP_ERR_UNSUPPORTED;
     const int rplf = (s.kl + 1 + 31) / 32, rplb = (s.kl + s.ku + 1 + 31) / 32;
-    const int rc = sweep_dispatch<T, false>(rplf, s, npts, ab, ut, ipiv, L, B, active, st);
+    const int rc = sweep_dispatch<T, false>(rplf, s, npts, ab, ut, ipiv, L, B, active, st, rh_force);
     if (rc != NEP_OK) return rc;
-    return sweep_dispatch<T, true>(rplb, s, npts, ab, ut, ipiv, L, B, active, st);
+    return sweep_dispatch<T, true>(rplb, s, npts, ab, ut, ipiv, L, B, active, st, rh_force);
 }
 
 template <typename T>

@@ -396,6 +396,8 @@ extern "C" void nep_opts_default(nep_opts* o) {
     o->symmetric = 0;
     o->newton_abandon = 8;
     o->refine_extrapolate = 1;
+    o->lu_kernel = 0;
+    o->solve_rh = 0;
 }
 
 extern "C" const char* nep_last_error(void) { return g_last_error.c_str(); }
@@ -576,6 +578,30 @@ extern "C" int nep_coefficients(nep_split_t h, int32_t N, const double* z, doubl
     return NEP_OK;
 }
 
+// ============================================================================ tuning table
+// Process-wide choices of nep_autotune (or a loaded cache file), keyed by the problem's shape: the plan
+// of a matching shape takes them when its options leave lu_kernel / solve_rh at 0.
+struct TuneKey {
+    int n, kl, ku, L, precision;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(n, kl, ku, L, precision) < std::tie(o.n, o.kl, o.ku, o.L, o.precision);
+    }
+};
+struct TuneChoice {
+    int lu_kernel = 0, solve_rh = 0;
+    double ms = 0;
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneChoice> g_tune;
+
+static bool tune_lookup(const TuneKey& k, TuneChoice* c) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune.find(k);
+    if (it == g_tune.end()) return false;
+    *c = it->second;
+    return true;
+}
+
 // ============================================================================ plan
 struct nep_plan {
     nep_split_t h = nullptr;
@@ -627,6 +653,7 @@ struct nep_plan {
     void* eig_scratch = nullptr;
     JacobiWork jw{};
     int* h_pinned = nullptr;  // host-mapped scalars
+    int lu_kernel = 0, solve_rh = 0;  // resolved tuning choices
     // last run
     int m = 0, kb = 0, max_sweeps_seen = 0, flags = 0, svd_sweeps = 0;
     double max_beta = 0;
@@ -782,6 +809,18 @@ int nep::plan_create_internal(nep_split_t h, const nep_region* r, int32_t N, int
     p->K = 2 * M;
     p->LM = L * M;
     p->mixed = p->o.precision == NEP_PREC_MIXED;
+    {
+        TuneChoice tc;
+        const bool tuned = tune_lookup(TuneKey{h->n, h->kl, h->ku, L, p->o.precision}, &tc);
+        p->lu_kernel = p->o.lu_kernel ? p->o.lu_kernel : (tuned ? tc.lu_kernel : 0);
+        p->solve_rh = p->o.solve_rh ? p->o.solve_rh : (tuned ? tc.solve_rh : 0);
+        if (p->lu_kernel < 0 || p->lu_kernel > 3 || !(p->solve_rh == 0 || p->solve_rh == 1 || p->solve_rh == 2 ||
+                                                     p->solve_rh == 4)) {
+            delete p;
+            set_error("lu_kernel must be 0..3 and solve_rh 0, 1, 2 or 4");
+            return NEP_ERR_ARG;
+        }
+    }
     p->Np = N;
     for (int i = 0; i < h->nterms; ++i) {
         const ExtTerm& e = h->ext[i];
@@ -898,12 +937,12 @@ static int run_solves(nep_plan* p, cudaStream_t st) {
     NEP_CUDA(cudaEventRecord(p->ev[0], st));
     NEP_TRY(launch_assemble<T>(s, N, p->F, ab, p->tnorm, p->tval, st));
     NEP_CUDA(cudaEventRecord(p->ev[1], st));
-    NEP_TRY(launch_band_lu<T>(s, N, ab, p->ipiv, p->info, nullptr, st));
+    NEP_TRY(launch_band_lu<T>(s, N, ab, p->ipiv, p->info, nullptr, st, p->lu_kernel));
     cx<T>* ut = reinterpret_cast<cx<T>*>(p->ut);
     if (ut) NEP_TRY(band_transpose_u<T>(s, N, ab, ut, st));
     NEP_CUDA(cudaEventRecord(p->ev[2], st));
     NEP_TRY(launch_convert_rhs<T>(N, n, L, p->V, D, st));
-    NEP_TRY(launch_band_solve<T>(s, N, ab, ut, p->ipiv, L, D, nullptr, st));
+    NEP_TRY(launch_band_solve<T>(s, N, ab, ut, p->ipiv, L, D, nullptr, st, p->solve_rh));
     NEP_TRY(launch_widen<T>(N, n, L, D, p->Y, st));
     NEP_TRY(launch_fill_int(N, p->active, 1, st));
     NEP_CUDA(cudaMemsetAsync(p->prev, 0, sizeof(double) * N, st));
@@ -912,7 +951,7 @@ static int run_solves(nep_plan* p, cudaStream_t st) {
     for (int sweep = 0; sweep < p->o.refine_max; ++sweep) {
         NEP_TRY(launch_split_residual(s, N, p->tval, L, p->V, p->Y, p->R, p->nrm, p->active, st));
         NEP_TRY(launch_refine_prepare<T>(N, n, L, p->R, D, p->active, st));
-        NEP_TRY(launch_band_solve<T>(s, N, ab, ut, p->ipiv, L, D, p->active, st));
+        NEP_TRY(launch_band_solve<T>(s, N, ab, ut, p->ipiv, L, D, p->active, st, p->solve_rh));
         NEP_TRY(launch_refine_update<T>(N, n, L, D, p->Y, p->dmax, p->ymax, p->active, st));
         NEP_TRY(launch_refine_decide(N, L, sweep, p->o.refine_max, p->o.refine_tol, p->o.step_tol, p->o.refine_extrapolate, p->nrm, p->tnorm,
                                      p->dmax, p->ymax, p->prev, p->beta, p->active, p->sweeps, p->nactive, st));
@@ -1015,15 +1054,18 @@ static int run_solves_batch(const std::vector<nep_plan*>& ps, cudaStream_t st) {
     }
     // LU: register-window instances and the tensor-core kernel over all points; other shapes per plan
     std::map<int, std::vector<PointDesc>> col;
-    std::vector<PointDesc> tc;
+    std::vector<PointDesc> tc[2];  // tensor-core LU with 3 and with 1 products
     for (nep_plan* p : ps) {
         const SplitDev s = p->h->dev();
+        const bool tc_ok = sizeof(T) == 4 && p->lu_kernel != LU_SIMT && (p->lu_kernel != LU_AUTO || lu_tc_enabled()) &&
+                           band_lu_tc_fits(s.kl);
         if (band_lu_col_fits(s.kl, s.ku)) {
             for (int j = 0; j < p->Np; ++j) col[lu_col_instance(s.kl, s.ku)].push_back(point(p, j, nullptr, nullptr));
-        } else if (sizeof(T) == 4 && lu_tc_enabled() && band_lu_tc_fits(s.kl)) {
-            for (int j = 0; j < p->Np; ++j) tc.push_back(point(p, j, nullptr, nullptr));
+        } else if (tc_ok) {
+            for (int j = 0; j < p->Np; ++j) tc[p->lu_kernel == LU_TC1].push_back(point(p, j, nullptr, nullptr));
         } else {
-            NEP_TRY(launch_band_lu<T>(s, p->Np, reinterpret_cast<cx<T>*>(p->ab), p->ipiv, p->info, nullptr, st));
+            NEP_TRY(launch_band_lu<T>(s, p->Np, reinterpret_cast<cx<T>*>(p->ab), p->ipiv, p->info, nullptr, st,
+                                      p->lu_kernel));
         }
     }
     for (auto& g : col) {
@@ -1031,7 +1073,8 @@ static int run_solves_batch(const std::vector<nep_plan*>& ps, cudaStream_t st) {
         NEP_TRY(upload(g.second, &pd));
         NEP_TRY(launch_band_lu_col_batch<T>(g.first, (int)g.second.size(), pd, st));
     }
-    if (!tc.empty()) NEP_TRY(launch_band_lu_tc_batch(tc, st));
+    if (!tc[0].empty()) NEP_TRY(launch_band_lu_tc_batch(tc[0], st, 3));
+    if (!tc[1].empty()) NEP_TRY(launch_band_lu_tc_batch(tc[1], st, 1));
     for (nep_plan* p : ps) {
         const SplitDev s = p->h->dev();
         if (p->ut) NEP_TRY(band_transpose_u<T>(s, p->Np, reinterpret_cast<cx<T>*>(p->ab), reinterpret_cast<cx<T>*>(p->ut), st));
@@ -1045,13 +1088,14 @@ static int run_solves_batch(const std::vector<nep_plan*>& ps, cudaStream_t st) {
             const SplitDev s = p->h->dev();
             if (p->ut) {
                 int a, b, r;
-                sweep_key<T>(s.kl, s.ku, p->Np, p->L, &a, &b, &r);
+                sweep_key<T>(s.kl, s.ku, p->Np, p->L, &a, &b, &r, p->solve_rh);
                 const auto key = std::make_tuple(a, b, r);
                 for (int j = 0; j < p->Np; ++j) groups[key].push_back(point(p, j, p->D, masked ? p->active : nullptr));
                 maxL[key] = std::max(maxL[key], p->L);
             } else {
                 NEP_TRY(launch_band_solve<T>(s, p->Np, reinterpret_cast<cx<T>*>(p->ab), nullptr, p->ipiv, p->L,
-                                             reinterpret_cast<cx<T>*>(p->D), masked ? p->active : nullptr, st));
+                                             reinterpret_cast<cx<T>*>(p->D), masked ? p->active : nullptr, st,
+                                             p->solve_rh));
             }
         }
         for (auto& g : groups) {
@@ -1247,6 +1291,98 @@ extern "C" int nep_plan_execute_batch(int32_t count, nep_plan_t* plans, const vo
         int err = 0;
         NEP_TRY(read_scalar(p, p->jw.err, &err, st));
         if (err) { set_error("a bounded grid barrier of the Jacobi SVD timed out"); return NEP_ERR_INTERNAL; }
+    }
+    return NEP_OK;
+}
+
+// ----------------------------------------------------------------- autotuning
+extern "C" int nep_tune_load(const char* path, int32_t* entries) {
+    if (!path) { set_error("nep_tune_load: null path"); return NEP_ERR_ARG; }
+    FILE* f = fopen(path, "r");
+    if (!f) { set_error("nep_tune_load: cannot open %s", path); return NEP_ERR_ARG; }
+    char line[512];
+    int count = 0;
+    while (fgets(line, sizeof line, f)) {
+        TuneKey k{};
+        TuneChoice c;
+        if (sscanf(line, "nep-tune n=%d kl=%d ku=%d L=%d precision=%d lu_kernel=%d solve_rh=%d ms=%lf", &k.n, &k.kl,
+                   &k.ku, &k.L, &k.precision, &c.lu_kernel, &c.solve_rh, &c.ms) == 8) {
+            std::lock_guard<std::mutex> g(g_tune_mu);
+            g_tune[k] = c;  // later lines win
+            ++count;
+        }
+    }
+    fclose(f);
+    if (entries) *entries = count;
+    return NEP_OK;
+}
+
+extern "C" int nep_autotune(nep_split_t h, const nep_region* r, int32_t N, int32_t L, int32_t M, const nep_opts* o,
+                            const void* V_dev, const char* cache_path, nep_tune_result* out, void* stream) {
+    if (!h || !r || !V_dev || !out) { set_error("nep_autotune: bad arguments"); return NEP_ERR_ARG; }
+    if (h->has_ext) { set_error("nep_autotune: callback or table terms are not tuned"); return NEP_ERR_UNSUPPORTED; }
+    nep_opts base;
+    if (o) base = *o;
+    else nep_opts_default(&base);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool wide_c64 = base.precision == NEP_PREC_MIXED && h->kl > 64 && band_lu_tc_fits(h->kl);
+    const std::vector<int> lus = wide_c64 ? std::vector<int>{LU_TC3, LU_TC1, LU_SIMT} : std::vector<int>{LU_AUTO};
+    const std::vector<int> rhs = band_sweeps_fit(h->kl, h->ku) ? std::vector<int>{1, 2, 4} : std::vector<int>{0};
+    *out = nep_tune_result{};
+    double best = 1e300;
+    cudaEvent_t e0, e1;
+    NEP_CUDA(cudaEventCreate(&e0));
+    NEP_CUDA(cudaEventCreate(&e1));
+    int rc = NEP_OK;
+    for (int lu : lus)
+        for (int rh : rhs) {
+            nep_opts oo = base;
+            oo.lu_kernel = lu;
+            oo.solve_rh = rh;
+            nep_plan_t p = nullptr;
+            if ((rc = nep_plan_create(h, r, N, L, M, &oo, &p))) break;
+            // one pass to warm up, then the mean of two timed passes (device time, CUDA events)
+            float ms = 0;
+            rc = nep_plan_execute(p, V_dev, st);
+            if (!rc && cudaEventRecord(e0, st) != cudaSuccess) rc = NEP_ERR_CUDA;
+            for (int it = 0; it < 2 && !rc; ++it) rc = nep_plan_execute(p, V_dev, st);
+            if (!rc && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = NEP_ERR_CUDA;
+            nep_result_t res = nullptr;
+            if (!rc) rc = nep_plan_result(p, &res);
+            nep_plan_destroy(p);
+            if (rc) break;
+            // accuracy gate: every quadrature solve at the backward-error target, no worse flags
+            nep_result_info_t ri{};
+            nep_result_info(res, &ri);
+            const bool accurate = !(ri.flags & NEP_WARN_REFINE) && ri.max_backward <= base.refine_tol;
+            nep_result_free(res);
+            ++out->candidates;
+            if (!accurate) continue;
+            ++out->accurate;
+            if (ms / 2 < best) {
+                best = ms / 2;
+                out->lu_kernel = lu;
+                out->solve_rh = rh;
+                out->ms = ms / 2;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (out->accurate == 0) { set_error("nep_autotune: no candidate met the accuracy target"); return NEP_ERR_INTERNAL; }
+    const TuneKey k{h->n, h->kl, h->ku, L, base.precision};
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune[k] = TuneChoice{out->lu_kernel, out->solve_rh, out->ms};
+    }
+    if (cache_path) {
+        FILE* f = fopen(cache_path, "a");
+        if (!f) { set_error("nep_autotune: cannot append to %s", cache_path); return NEP_ERR_ARG; }
+        fprintf(f, "nep-tune n=%d kl=%d ku=%d L=%d precision=%d lu_kernel=%d solve_rh=%d ms=%.6f\n", k.n, k.kl, k.ku,
+                k.L, k.precision, out->lu_kernel, out->solve_rh, out->ms);
+        fclose(f);
     }
     return NEP_OK;
 }

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(512, 1)
     lu_tc_kernel(int n, int kl, int ku, int ldab, zf* __restrict__ ab_all, int* __restrict__ ipiv_all,
                  int* __restrict__ info_all, const int* __restrict__ active, zf* __restrict__ win_all, int RWp,
                  int CWp, float* __restrict__ aimg_all, int nmt_max, const __grid_constant__ CUtensorMap tmap,
-                 int* __restrict__ err, const PointDesc* __restrict__ pd) {
+                 int* __restrict__ err, const PointDesc* __restrict__ pd, int passes) {
     const int j = blockIdx.x;  // also the point's operand image and its TMA coordinate
     zf* ab = ab_all + (int64_t)j * n * ldab;
     int* ipiv = ipiv_all + (int64_t)j * n;
@@ -389,8 +389,8 @@ __global__ void __launch_bounds__(512, 1)
                 const uint32_t d = tmem + (uint32_t)(b * NT);
                 const uint32_t abase = tc::smem_u32(b ? Abuf1 : Abuf0), bbase = tc::smem_u32(Bimg);
                 const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};  // hi*hi, hi*lo, lo*hi
-#pragma unroll
-                for (int ps = 0; ps < 3; ++ps)
+                // passes = 3: hi*hi + hi*lo + lo*hi (~FP32); passes = 1: hi*hi alone (TF32 operands)
+                for (int ps = 0; ps < passes; ++ps)
 #pragma unroll
                     for (int s = 0; s < KR / 8; ++s) {
                         const uint64_t ad = tc::smem_desc(abase + (uint32_t)(pa[ps] * PART * 4) + s * 2 * LBO, LBO, SBO);
@@ -552,7 +552,8 @@ bool band_lu_tc_fits(int kl) {
     return lu_tc_smem(kl) <= 227 * 1024;
 }
 
-int launch_band_lu_tc(const SplitDev& s, int npts, zf* ab, int* ipiv, int* info, const int* active, cudaStream_t st) {
+int launch_band_lu_tc(const SplitDev& s, int npts, zf* ab, int* ipiv, int* info, const int* active, cudaStream_t st,
+                      int passes) {
     if (npts <= 0) return NEP_OK;
     if (!band_lu_tc_fits(s.kl)) return NEP_ERR_UNSUPPORTED;
     auto encode = encode_fn();
@@ -593,7 +594,7 @@ int launch_band_lu_tc(const SplitDev& s, int npts, zf* ab, int* ipiv, int* info,
     if (e == cudaSuccess) e = allow_max_dynamic_smem(lu_tc_kernel);
     if (e == cudaSuccess) {
         lu_tc_kernel<<<npts, 512, smem, st>>>(s.n, s.kl, s.ku, s.ldab, ab, ipiv, info, active, win, rwp, cwp, aimg,
-                                              nmt_max, tmap, err, nullptr);
+                                              nmt_max, tmap, err, nullptr, passes);
         count_launch();
         e = cudaGetLastError();
     }
@@ -613,7 +614,7 @@ int launch_band_lu_tc(const SplitDev& s, int npts, zf* ab, int* ipiv, int* info,
 
 // The tensor-core LU over points of several complex64 problems (each with kl > 64 and within the
 // shared-memory budget): windows per point, one operand-image array and tensor map for the batch.
-int launch_band_lu_tc_batch(const std::vector<PointDesc>& items_in, cudaStream_t st) {
+int launch_band_lu_tc_batch(const std::vector<PointDesc>& items_in, cudaStream_t st, int passes) {
     const int count = (int)items_in.size();
     if (count <= 0) return NEP_OK;
     auto encode = encode_fn();
@@ -662,7 +663,7 @@ int launch_band_lu_tc_batch(const std::vector<PointDesc>& items_in, cudaStream_t
     if (e == cudaSuccess) e = allow_max_dynamic_smem(lu_tc_kernel);
     if (e == cudaSuccess) {
         lu_tc_kernel<<<count, 512, smem, st>>>(0, 0, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, aimg,
-                                               nmt_max, tmap, err, pd);
+                                               nmt_max, tmap, err, pd, passes);
         count_launch();
         e = cudaGetLastError();
     }

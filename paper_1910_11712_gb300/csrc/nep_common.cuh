@@ -90,6 +90,10 @@ template <typename T, typename U> __host__ __device__ __forceinline__ cx<T> cvt(
 // ----------------------------------------------------------------- scalar functions
 // Flattened function tree: node k has kind/op, scaling alpha/beta, shift, coefficient
 // ranges into a shared coefficient pool, and child node indices (combine).
+// LU kernel choices for complex64 bands with kl > 64 (nep_opts.lu_kernel): the library's default
+// (tensor core, 3 x TF32), the tensor core with TF32 operands, the FP32 SIMT kernel
+enum { LU_AUTO = 0, LU_TC3 = 1, LU_TC1 = 2, LU_SIMT = 3 };
+
 // One quadrature point of some problem in a launch shared by several problems: a kernel given an
 // array of these takes block b's sizes and buffers from entry b instead of its uniform arguments
 // (point index 0 within them), with the same arithmetic per point.
@@ -262,29 +266,33 @@ template <typename T>
 int launch_band_lu_col_batch(int instance, int count, const PointDesc* pd_dev, cudaStream_t st);
 // the narrow-band sweeps' launch shape of a problem, and the sweeps over points of equal shape
 template <typename T>
-void sweep_key(int kl, int ku, int npts, int L, int* rplf, int* rplb, int* rh);
+void sweep_key(int kl, int ku, int npts, int L, int* rplf, int* rplb, int* rh, int rh_force = 0);
 template <typename T>
 int band_sweeps_batch(int rplf, int rplb, int rh, int count, int maxL, const PointDesc* pd, cudaStream_t st);
 // the tensor-core LU over points of several complex64 problems (each kl > 64)
-int launch_band_lu_tc_batch(const std::vector<PointDesc>& items, cudaStream_t st);
+int launch_band_lu_tc_batch(const std::vector<PointDesc>& items, cudaStream_t st, int passes = 3);
+
 template <typename T>
 int launch_band_lu_wide(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active,
                         cudaStream_t st);
 // The same blocked LU in complex64 with the trailing update on the tensor core (lu_tc.cu): TMA-staged
 // operand tiles, tcgen05 MMA (TF32 hi/lo split, 4M complex form) into tensor memory. kl > 64.
 bool band_lu_tc_fits(int kl);
-int launch_band_lu_tc(const SplitDev& s, int npts, zf* ab, int* ipiv, int* info, const int* active, cudaStream_t st);
+// passes: 3 (TF32 hi/lo split, ~FP32 products) or 1 (TF32 operands)
+int launch_band_lu_tc(const SplitDev& s, int npts, zf* ab, int* ipiv, int* info, const int* active, cudaStream_t st,
+                      int passes = 3);
 // Whether complex64 wide-band LUs use the tensor-core kernel (default yes; NEP_LU_TC=0 selects the
 // FP32 SIMT kernel, for comparisons).
 bool lu_tc_enabled();
 template <typename T>
-int launch_band_lu(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st);
+int launch_band_lu(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active, cudaStream_t st,
+                   int lu_kernel = LU_AUTO);
 // Narrow-band substitution sweeps (register windows of kl+1 and kl+ku+1 rows, up to 288).
 inline bool band_sweeps_fit(int kl, int ku) { return kl >= 1 && kl + 1 <= 288 && kl + ku + 1 <= 288; }
 // ut (npts x n x (kl+ku+1)): the U factor by columns, written by band_transpose_u after the LU.
 template <typename T>
 int band_sweeps(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* ut, const int* ipiv, int L, cx<T>* B,
-                const int* active, cudaStream_t st);
+                const int* active, cudaStream_t st, int rh_force = 0);
 template <typename T>
 int band_transpose_u(const SplitDev& s, int npts, const cx<T>* ab, cx<T>* ut, cudaStream_t st);
 // moments.cu: conjugate-symmetric quadrature helpers
@@ -294,7 +302,7 @@ int launch_count_imag(int64_t count, const zd* x, int* out, cudaStream_t st);
 void draw_probe_block(uint64_t seed, size_t count, bool real_only, double* out);
 template <typename T>
 int launch_band_solve(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* ut, const int* ipiv, int L, cx<T>* B,
-                      const int* active, cudaStream_t st);
+                      const int* active, cudaStream_t st, int rh_force = 0);
 // spmv.cu
 int launch_split_residual(const SplitDev& s, int npts, const zd* tval, int L, const zd* V, const zd* Y, zd* R,
                           double* nrm, const int* active, cudaStream_t st);

@@ -39,16 +39,16 @@ def test_struct_layouts_match_c(built, tmp_path):
     import subprocess
     from paper_1910_11712_gb300 import binding
     c = tmp_path / "sz.c"
-    c.write_text('#include <stdio.h>\n#include "nep_ciss.h"\nint main(){printf("%zu %zu %zu %zu %zu %zu %zu",'
+    c.write_text('#include <stdio.h>\n#include "nep_ciss.h"\nint main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu",'
                  'sizeof(nep_fn), sizeof(nep_opts), sizeof(nep_result_info_t), sizeof(nep_csr), sizeof(nep_region),'
-                 'sizeof(nep_nleigs_opts), sizeof(nep_interpol_opts));}')
+                 'sizeof(nep_nleigs_opts), sizeof(nep_interpol_opts), sizeof(nep_tune_result));}')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)])
     sizes = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     assert sizes == [ctypes.sizeof(binding.NepFn), ctypes.sizeof(binding.NepOpts),
                      ctypes.sizeof(binding.NepResultInfo), ctypes.sizeof(binding.NepCsr),
                      ctypes.sizeof(binding.NepRegion), ctypes.sizeof(binding.NepNleigsOpts),
-                     ctypes.sizeof(binding.NepInterpolOpts)]
+                     ctypes.sizeof(binding.NepInterpolOpts), ctypes.sizeof(binding.NepTuneResult)]
 
 
 def test_host_entry_points_without_gpu(built):

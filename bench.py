@@ -290,7 +290,7 @@ def cpu_baseline(p, steps_budget_s=20.0):
     return out
 
 
-def serving_bench(binding, prec, count, seed, workers, s_max, loads=(0.5, 0.8, 1.2)):
+def serving_bench(binding, prec, count, seed, workers, s_max, loads=(0.5, 0.8, 1.2), max_batch=1, fp64=True):
     """Continuous-batching serving on a bounded sample of the Poisson request stream.
 
     Requests: the first `count` of the seeded delay/Drude stream (s x s grids, n log-uniform up to
@@ -327,7 +327,7 @@ def serving_bench(binding, prec, count, seed, workers, s_max, loads=(0.5, 0.8, 1
         return {"rho": None, "offered_req_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "solves_per_s": solves / span}
 
-    srv = binding.Server(workers=workers)
+    srv = binding.Server(workers=workers, max_batch=max_batch)
     for i in range(min(4, count)):  # warm the allocator pool and the library
         srv.wait(submit(srv, i, prec))
     t0 = time.perf_counter()
@@ -335,13 +335,19 @@ def serving_bench(binding, prec, count, seed, workers, s_max, loads=(0.5, 0.8, 1
     for t in tickets:
         srv.wait(t)
     capacity = count / (time.perf_counter() - t0)
-    out = {"requests": count, "workers": workers, "n_range": [min(p.n for p in probs), max(p.n for p in probs)],
+    out = {"requests": count, "workers": workers, "max_batch": max_batch,
+           "n_range": [min(p.n for p in probs), max(p.n for p in probs)],
            "capacity_req_per_s": capacity, "capacity_solves_per_s": capacity * solves / count, "loads": []}
     for rho in loads:
         r_ = replay(srv, rho * capacity, prec)
         r_["rho"] = rho
         out["loads"].append(r_)
     srv.close()
+    if not fp64:
+        for sp in splits:
+            sp.close()
+        out["sample"] = f"first {count} requests of the seeded Poisson request stream (seed {seed})"
+        return out
     # plain FP64, one request at a time, under the same arrival times
     srv64 = binding.Server(workers=1)
     srv64.wait(submit(srv64, 0, binding.NEP_PREC_FP64))
@@ -751,6 +757,9 @@ def main():
             line[key] = blk
         if not args.no_serving:
             line["serving"] = serving_bench(binding, prec, args.serving_requests, 0, 4, args.serving_smax)
+            # the same stream with shared launches: two workers, batches of up to four requests
+            line["serving_batched"] = serving_bench(binding, prec, args.serving_requests, 0, 2, args.serving_smax,
+                                                    max_batch=4, fp64=False)
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(p)
             if "c3" in wide:

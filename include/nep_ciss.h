@@ -457,6 +457,12 @@ typedef struct nep_server *nep_server_t;
 #define NEP_PENDING 1 /* nep_poll: the request has not finished yet */
 /* workers >= 1 concurrent requests; hbm_budget_bytes == 0: 80% of the free device memory. */
 int nep_server_create(int32_t workers, uint64_t hbm_budget_bytes, nep_server_t *out);
+/* The same with shared launches: a free worker takes up to max_batch requests from the head of the
+ * queue (in arrival order, while they fit the budget and share a precision; requests with callback or
+ * table terms run alone) and runs them as one nep_plan_execute_batch, so the LU and the sweeps of all
+ * their quadrature points share launches; each result stays bitwise the one it gets alone.
+ * max_batch == 1 is nep_server_create. Errors: NEP_ERR_ARG (workers < 1, max_batch < 1), NEP_ERR_CUDA. */
+int nep_server_create_batched(int32_t workers, int32_t max_batch, uint64_t hbm_budget_bytes, nep_server_t *out);
 /* Copies the region, options and V (n x L complex, or NULL: drawn from opts->seed) and
  * enqueues the request; *ticket identifies it. NEP_ERR_NOMEM if it can never fit the budget. */
 int nep_submit(nep_server_t s, nep_split_t h, const nep_region *r, int32_t N, int32_t L, int32_t M, const nep_opts *o,

@@ -99,6 +99,7 @@ SIGNATURES = {
     "nep_kernel_launches": (ctypes.c_uint64, []),
     "nep_set_wait_limit": (c_int32, [ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "nep_server_create": (c_int32, [c_int32, ctypes.c_uint64, ctypes.POINTER(c_void_p)]),
+    "nep_server_create_batched": (c_int32, [c_int32, c_int32, ctypes.c_uint64, ctypes.POINTER(c_void_p)]),
     "nep_submit": (c_int32, [c_void_p, c_void_p, ctypes.POINTER(NepRegion), c_int32, c_int32, c_int32,
                              ctypes.POINTER(NepOpts), c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
     "nep_poll": (c_int32, [c_void_p, ctypes.c_uint64, ctypes.POINTER(c_void_p)]),
@@ -426,9 +427,12 @@ class Plan:
 class Server:
     """Continuous-batching request server (nep_server_*): submit, poll or wait."""
 
-    def __init__(self, workers: int = 4, hbm_budget_bytes: int = 0):
+    def __init__(self, workers: int = 4, hbm_budget_bytes: int = 0, max_batch: int = 1):
         h = c_void_p()
-        check(load().nep_server_create(workers, hbm_budget_bytes, ctypes.byref(h)))
+        if max_batch > 1:
+            check(load().nep_server_create_batched(workers, max_batch, hbm_budget_bytes, ctypes.byref(h)))
+        else:
+            check(load().nep_server_create(workers, hbm_budget_bytes, ctypes.byref(h)))
         self.handle = h
 
     def submit(self, split: Split, region, N, L, M, V=None, **opts) -> int:

@@ -8,6 +8,11 @@
 // different requests overlap on the device while each request's computation is exactly the
 // one nep_ciss_solve performs on the same inputs. Factors and moments stay in the request's
 // device-resident plan until its result is copied out.
+//
+// With max_batch > 1 (nep_server_create_batched) a free worker takes up to max_batch requests from the
+// head of the queue at once (in arrival order, while they fit the budget and share a precision) and
+// runs them as one batch (nep_plan_execute_batch): the LU and the sweeps of all their quadrature
+// points in shared launches, each request's results bitwise those it gets alone.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -53,6 +58,7 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 
 struct nep_server {
     int device = 0;
+    int max_batch = 1;
     size_t budget = 0, in_use = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -68,7 +74,7 @@ struct nep_server {
         cudaStream_t st = nullptr;
         cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
         for (;;) {
-            Request* rq = nullptr;
+            std::vector<Request*> batch;
             {
                 std::unique_lock<std::mutex> lk(mu);
                 cv_work.wait(lk, [&] {
@@ -76,28 +82,85 @@ struct nep_server {
                            (!queue.empty() && in_use + queue.front()->bytes <= budget);
                 });
                 if (queue.empty()) break;
-                rq = queue.front();
-                queue.pop_front();
-                in_use += rq->bytes;
-                ++running;
+                // the head, then its successors in order while they fit and can share launches
+                do {
+                    Request* rq = queue.front();
+                    if (!batch.empty() && (rq->opts.precision != batch[0]->opts.precision ||
+                                           split_has_host_terms(rq->h) || split_has_host_terms(batch[0]->h)))
+                        break;
+                    queue.pop_front();
+                    in_use += rq->bytes;
+                    batch.push_back(rq);
+                } while ((int)batch.size() < max_batch && !queue.empty() && in_use + queue.front()->bytes <= budget);
+                running += (int)batch.size();
             }
-            rq->started = Clock::now();
-            int rc = run(rq, st);
+            const Clock::time_point t0 = Clock::now();
+            for (Request* rq : batch) rq->started = t0;
+            const int rc = batch.size() == 1 ? run(batch[0], st) : run_batch(batch, st);
             {
                 std::lock_guard<std::mutex> lk(mu);
-                rq->finished = Clock::now();
-                rq->status = rc;
-                if (rc != NEP_OK) rq->error = nep_last_error();
-                else result_set_times(rq->result, ms_between(rq->submitted, rq->started),
-                                      ms_between(rq->submitted, rq->finished));
-                in_use -= rq->bytes;
-                --running;
+                const Clock::time_point t1 = Clock::now();
+                for (Request* rq : batch) {
+                    rq->finished = t1;
+                    rq->status = rc;
+                    if (rc != NEP_OK) {
+                        rq->error = nep_last_error();
+                        if (rq->result) {
+                            nep_result_free(rq->result);
+                            rq->result = nullptr;
+                        }
+                    } else {
+                        result_set_times(rq->result, ms_between(rq->submitted, rq->started),
+                                         ms_between(rq->submitted, rq->finished));
+                    }
+                    in_use -= rq->bytes;
+                }
+                running -= (int)batch.size();
             }
             cv_done.notify_all();
             cv_work.notify_all();
         }
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
+    }
+
+    // the request's probe block on the device (its own, or the one nep_ciss_solve draws for its seed)
+    static int upload_V(Request* rq, void** dV, cudaStream_t st) {
+        int n = 0;
+        nep_split_info(rq->h, &n, nullptr, nullptr, nullptr, nullptr);
+        const size_t nl = (size_t)n * rq->L;
+        std::vector<double> Vh;
+        const double* src = rq->V.data();
+        if (rq->V.empty()) {
+            Vh.resize(2 * nl);
+            draw_probe_block(rq->opts.seed, nl, rq->opts.symmetric != 0, Vh.data());
+            src = Vh.data();
+        }
+        *dV = nullptr;
+        if (cudaMallocAsync(dV, sizeof(double) * 2 * nl, st) != cudaSuccess) return NEP_ERR_NOMEM;
+        if (cudaMemcpyAsync(*dV, src, sizeof(double) * 2 * nl, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return NEP_ERR_CUDA;
+        return NEP_OK;
+    }
+
+    static int run_batch(std::vector<Request*>& rqs, cudaStream_t st) {
+        const int k = (int)rqs.size();
+        std::vector<nep_plan_t> plans(k, nullptr);
+        std::vector<void*> dV(k, nullptr);
+        int rc = NEP_OK;
+        for (int i = 0; i < k && !rc; ++i) {
+            rc = plan_create_internal(rqs[i]->h, &rqs[i]->region, rqs[i]->N, rqs[i]->L, rqs[i]->M, &rqs[i]->opts, st,
+                                      &plans[i]);
+            if (!rc) rc = upload_V(rqs[i], &dV[i], st);
+        }
+        if (!rc) rc = nep_plan_execute_batch(k, plans.data(), const_cast<const void* const*>(dV.data()), st);
+        for (int i = 0; i < k && !rc; ++i) rc = nep_plan_result(plans[i], &rqs[i]->result);
+        for (int i = 0; i < k; ++i) {
+            if (dV[i]) cudaFreeAsync(dV[i], st);
+            if (plans[i]) nep_plan_destroy(plans[i]);
+        }
+        return rc;
     }
 
     static int run(Request* rq, cudaStream_t st) {
@@ -128,9 +191,18 @@ struct nep_server {
 };
 
 extern "C" int nep_server_create(int32_t workers, uint64_t hbm_budget_bytes, nep_server_t* out) {
-    if (!out || workers < 1) { set_error("nep_server_create: need workers >= 1"); return NEP_ERR_ARG; }
+    return nep_server_create_batched(workers, 1, hbm_budget_bytes, out);
+}
+
+extern "C" int nep_server_create_batched(int32_t workers, int32_t max_batch, uint64_t hbm_budget_bytes,
+                                         nep_server_t* out) {
+    if (!out || workers < 1 || max_batch < 1) {
+        set_error("nep_server_create: need workers >= 1 and max_batch >= 1");
+        return NEP_ERR_ARG;
+    }
     *out = nullptr;
     nep_server* s = new nep_server();
+    s->max_batch = max_batch;
     cudaGetDevice(&s->device);
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { delete s; set_error("cudaMemGetInfo failed"); return NEP_ERR_CUDA; }

@@ -26,12 +26,15 @@ def _requests():
     return out
 
 
-def test_results_identical_alone_and_in_mix(bnd):
+@pytest.mark.parametrize("workers,max_batch", [(4, 1), (2, 4)])
+def test_results_identical_alone_and_in_mix(bnd, workers, max_batch):
+    """Each request's result is bitwise the same alone and in the mix: with one request per worker
+    (separate streams), and with batches of up to four requests sharing the LU and sweep launches."""
     torch_cuda()
     reqs = _requests()
     splits = [bnd.Split.from_problem(p) for p, _ in reqs]
     alone = [bnd.ciss_solve(sp, p.region, p.N, p.L, p.M, V=V, precision=1) for sp, (p, V) in zip(splits, reqs)]
-    srv = bnd.Server(workers=4)
+    srv = bnd.Server(workers=workers, max_batch=max_batch)
     tickets = [srv.submit(sp, p.region, p.N, p.L, p.M, V=V, precision=1) for sp, (p, V) in zip(splits, reqs)]
     mixed = [srv.wait(t) for t in tickets]
     srv.close()

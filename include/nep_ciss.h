@@ -474,8 +474,9 @@ int nep_poll(nep_server_t s, uint64_t ticket, nep_result_t *out);
 int nep_server_wait(nep_server_t s, uint64_t ticket, nep_result_t *out);
 /* Waits for all admitted and queued requests, then stops the workers. */
 int nep_server_destroy(nep_server_t s);
-/* Device bytes one solve of this shape allocates (what admission charges against the budget;
- * a request with opts.symmetric set needs less). */
+/* Device bytes one solve of this shape allocates with the full quadrature: an upper bound. Admission
+ * charges each request its own footprint, which is smaller for a request with opts.symmetric set (only
+ * the N/2 nodes above the real axis are held), so budgets sized with this figure are conservative. */
 uint64_t nep_plan_bytes(nep_split_t h, int32_t N, int32_t L, int32_t M, int32_t precision);
 
 /* ------------------------------------------------------------------ step entry points */

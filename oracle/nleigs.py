@@ -303,17 +303,22 @@ def arnoldi_toar(problem, interp: dict, sigma: complex, w0: np.ndarray, k: int):
         r = r - U @ h2
         h = h + h2
         rho = np.linalg.norm(r)
-        U = np.column_stack([U, r / rho])
-        gt0 = np.concatenate([h, [rho]])
-        # Eq. (nleigs-toar4): coefficients of S v in the extended basis
-        gn = np.zeros((d, m + 1), np.complex128)
+        if rho <= 64 * np.finfo(float).eps * max(np.linalg.norm(y0), np.finfo(float).tiny):
+            # y^0 already lies in span(U) (at the latest once U has n columns): U is not extended
+            mp, gt0 = m, h
+        else:
+            mp = m + 1
+            U = np.column_stack([U, r / rho])
+            gt0 = np.concatenate([h, [rho]])
+        # Eq. (nleigs-toar4): coefficients of S v in the (possibly extended) basis
+        gn = np.zeros((d, mp), np.complex128)
         for i in range(d - 1):
             gn[i, :m] = gt[i + 1]
             gn[i] += bs[i] * gt0
         gn[d - 1] = bs[d - 1] * gt0
         gvec = gn.reshape(-1)
-        # Arnoldi on the stacked coefficients (old vectors padded with zeros for the new column of U)
-        Gm = np.column_stack([np.pad(x.reshape(d, -1), ((0, 0), (0, m + 1 - x.size // d))).reshape(-1)
+        # Arnoldi on the stacked coefficients (old vectors padded with zeros for a new column of U)
+        Gm = np.column_stack([np.pad(x.reshape(d, -1), ((0, 0), (0, mp - x.size // d))).reshape(-1)
                               for x in G])
         for _ in range(2):
             hh = Gm.conj().T @ gvec

@@ -37,3 +37,22 @@ def test_toar_equals_the_full_basis_arnoldi(name):
         lam = sigma + 1.0 / theta[q]
         x = Vt[:n, :k] @ s[:, q]
         assert ciss.scaled_residual(p.mats, p.fns, norms, lam, x) <= 1e-9
+
+
+def test_toar_with_fewer_rows_than_basis_vectors():
+    """n < d + k: y^0 falls into span(U) once U has n columns; U then stops growing (no column of
+    NaNs), and the Krylov vectors and Hessenberg matrix still equal the full-basis Arnoldi's."""
+    p = synth.diagonal_delay(n=6, seed=1)
+    it = nleigs.interpolation(p.fns, p.region)
+    d, n, k = it["d"], p.n, 12
+    assert n < d + k
+    sigma = complex(p.region["center"]) + 0.1j
+    rng = np.random.default_rng(7)
+    w0 = rng.standard_normal((n, d)) + 1j * rng.standard_normal((n, d))
+    U, G, H = nleigs.arnoldi_toar(p, it, sigma, w0, k)
+    assert U.shape == (n, n) and np.all(np.isfinite(U))
+    assert np.abs(U.conj().T @ U - np.eye(n)).max() <= 1e-12
+    S = nleigs.shift_invert_dense(p, it, sigma)
+    V, Hf = nleigs.arnoldi_full(S, w0.T.reshape(-1), k)
+    assert np.abs(nleigs.toar_vectors(U, G, d) - V).max() <= 1e-10
+    assert np.abs(H - Hf).max() <= 1e-10 * np.abs(Hf).max()

@@ -58,3 +58,40 @@ def test_noalloc_svd_rejects_sizes_beyond_the_fixed_block(bnd):
         bnd.jacobi_svd_noalloc(rows, cols, Ad, Wd, sd)
     assert e.value.code == bnd.NEP_ERR_ARG
     assert "exceeds the fixed scratch" in str(e.value)
+
+
+def _device_memory_state():
+    """(free device bytes, used and reserved bytes of the device's default stream-ordered pool),
+    read through the CUDA runtime the library itself links."""
+    import ctypes
+    rt = ctypes.CDLL("libcudart.so.13")
+    dev = ctypes.c_int()
+    assert rt.cudaGetDevice(ctypes.byref(dev)) == 0
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), dev) == 0
+    used, reserved = ctypes.c_uint64(), ctypes.c_uint64()
+    assert rt.cudaMemPoolGetAttribute(pool, 7, ctypes.byref(used)) == 0      # cudaMemPoolAttrUsedMemCurrent
+    assert rt.cudaMemPoolGetAttribute(pool, 5, ctypes.byref(reserved)) == 0  # cudaMemPoolAttrReservedMemCurrent
+    free, total = ctypes.c_size_t(), ctypes.c_size_t()
+    assert rt.cudaMemGetInfo(ctypes.byref(free), ctypes.byref(total)) == 0
+    return free.value, used.value, reserved.value
+
+
+def test_noalloc_svd_allocates_no_device_memory(bnd):
+    """The promise itself: around a call (after a first one has loaded the kernels), neither the
+    device's free memory nor the default memory pool's use changes. The inputs and outputs are
+    allocated beforehand."""
+    torch = torch_cuda()
+    rows, cols = 120, 100
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((rows, cols)) + 1j * rng.standard_normal((rows, cols))
+    Ad = to_dev(np.asfortranarray(A), torch)
+    Wd = torch.zeros(cols * cols * 2, dtype=torch.float64, device="cuda")
+    sd = torch.zeros(cols, dtype=torch.float64, device="cuda")
+    bnd.jacobi_svd_noalloc(rows, cols, Ad, Wd, sd)
+    torch.cuda.synchronize()
+    before = _device_memory_state()
+    for _ in range(2):
+        bnd.jacobi_svd_noalloc(rows, cols, Ad, Wd, sd)
+    torch.cuda.synchronize()
+    assert _device_memory_state() == before

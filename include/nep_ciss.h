@@ -361,6 +361,8 @@ typedef struct {
                           /* (default): plain complex64 solves, then the Ritz pairs inside the     */
                           /* region with eta <= 1e-4 are polished by nep_rii's iteration (FP64     */
                           /* residuals, tol 1e-13, at most 10 iterations) before the acceptance    */
+    int32_t full_basis;   /* nonzero: Arnoldi on full (d n)-vectors; zero (default): the compact TOAR   */
+                          /* basis of Sec. 4.5.3, U (n x m, m <= d + krylov) and coefficient vectors    */
 } nep_nleigs_opts;
 /* The rational interpolant R_d(z) = sum_j b_j(z) D_j, D_j = sum_i d_i^j A_i, of Sec. 4.5.1 on the
  * region (host computation):
@@ -390,12 +392,15 @@ int nep_nleigs_interpolation(nep_split_t h, const nep_region *r, const nep_nleig
 int nep_nleigs_interpolation_fns(int32_t nterms, const nep_fn *f, const nep_region *r, const nep_nleigs_opts *o,
                                  int32_t cap, double *sigma, double *xi, double *beta, double *dd, int32_t *degree,
                                  int32_t *converged, int32_t *nsing);
-/* NLEIGS, static variant with a full basis (Sec. 4.5.2, 4.5.3 "full basis"): shift-and-invert
- * Arnoldi with o->krylov steps on S = (A - sigma B)^{-1} B for the linearisation (A, B) of
- * Eq. (nleigsmatlin), applied through the block recurrences of Eqs. (nleigstoarreca) and
- * (nleigstoarrecb) with one band LU of R_d(sigma) (complex64 factors) and per step one band solve
- * (with two corrections against the FP64 residual of R_d(sigma) when o->exact_solves is set);
- * classical Gram-Schmidt twice. Ritz values theta (complex64 Hessenberg QR, then FP64 inverse iteration on
+/* NLEIGS, static variant (Sec. 4.5.2, 4.5.3): shift-and-invert Arnoldi with o->krylov steps on
+ * S = (A - sigma B)^{-1} B for the linearisation (A, B) of Eq. (nleigsmatlin), applied through the
+ * block recurrences of Eqs. (nleigstoarreca) and (nleigstoarrecb) with one band LU of R_d(sigma)
+ * (complex64 factors) and per step one band solve (with two corrections against the FP64 residual of
+ * R_d(sigma) when o->exact_solves is set). By default the basis is the compact one of Sec. 4.5.3
+ * (Eqs. (nleigs-toar1)-(nleigs-toar4)): Krylov vectors (I_d (x) U) g with U orthonormal (n x m, one new
+ * column per step, none when the new direction already lies in span U) and coefficient vectors g,
+ * Gram-Schmidt on n-vectors for U and on d m coefficient vectors for the Arnoldi; o->full_basis
+ * keeps full (d n)-vectors. Classical Gram-Schmidt twice in both. Ritz values theta (complex64 Hessenberg QR, then FP64 inverse iteration on
  * the Hessenberg matrix and a Rayleigh quotient) give lambda = sigma + 1/theta and x the first block
  * of the Ritz vector; pairs inside the region with FP64 eta (Sec. 2 Eq. (sressplit), of the full T) at most
  * eig_tol are returned, deduplicated and sorted as nep_ciss_solve does. *out receives a result

@@ -1598,6 +1598,7 @@ struct NleigsParams {
     uint64_t seed;
     double eig_tol;
     bool exact;
+    bool toar;
 };
 
 static int nleigs_params(nep_split_t h, const nep_region* r, const nep_nleigs_opts* o, NleigsParams* q) {
@@ -1613,6 +1614,7 @@ static int nleigs_params(nep_split_t h, const nep_region* r, const nep_nleigs_op
     q->seed = o->seed;
     q->eig_tol = o->eig_tol > 0 ? o->eig_tol : 1e-8;
     q->exact = o->exact_solves != 0;
+    q->toar = o->full_basis == 0;
     if (q->dmax > 63 || q->nb < 8 || q->nb > (1 << 20) || q->kmax > 512) {
         set_error("nleigs: max_degree <= 63, 8 <= nboundary <= 2^20, krylov <= 512");
         return NEP_ERR_ARG;
@@ -1708,7 +1710,7 @@ extern "C" int nep_nleigs_solve(nep_split_t h, const nep_region* r, const nep_nl
     NleigsOut res;
     cudaStream_t st = (cudaStream_t)stream;
     NEP_TRY(nleigs_run(h->dev(), it, q.shift, kmax, reinterpret_cast<const double*>(start.data()),
-                       mk(r->center_re, r->center_im), r->a, r->b, q.eig_tol, q.exact, &res, st));
+                       mk(r->center_re, r->center_im), r->a, r->b, q.eig_tol, q.exact, &res, st, q.toar));
     nep_result* rr = new nep_result();
     rr->n = h->n;
     rr->nconv = (int)res.lam.size();

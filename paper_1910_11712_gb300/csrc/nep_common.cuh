@@ -419,7 +419,7 @@ int nleigs_interpolation(const std::vector<FnNode>& nodes, const std::vector<zd>
 // exact: complex64 solves with two FP64-residual corrections; otherwise plain complex64 solves and
 // residual inverse iteration on the converged Ritz pairs inside the region
 int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, const double* start_host, zd c,
-               double ea, double eb, double eig_tol, bool exact, NleigsOut* res, cudaStream_t st);
+               double ea, double eb, double eig_tol, bool exact, NleigsOut* res, cudaStream_t st, bool toar = true);
 // Interpol (Sec. 4.4): Krylov on the Chebyshev-basis linearisation of P_d; c: nt x (d+1) coefficients
 // of Eq. (polinterpcoef), lambda = alpha theta + beta, sigma the shift in theta
 int interpol_run(const SplitDev& s, const std::vector<zd>& c, int d, zd sigma, double alpha, double beta, int kmax,

@@ -639,12 +639,74 @@ __global__ void __launch_bounds__(256) nleigs_sub_kernel(int64_t N, int K, const
 }
 
 
+// ---- the compact (TOAR) basis of Sec. 4.5.3: Krylov vectors (I_d (x) U) g with U (n x m) orthonormal,
+// growing by one column per step, and coefficient blocks g^i in C^m. Coefficient vectors are stored
+// with a fixed stride: block i of vector k at G[k d Mx + i Mx .. + m), zeros beyond m.
+
+// Eq. (nleigs-toar1) on coefficients: pt^{d-1} = 0, pt^{j-1} = (g^{j-1} + g_j g^j - e_j pt^j) inv_ds_j
+// (j = d-1 .. 1: the recurrence of nleigs_expand_kernel, acting on U's coordinates), and the per-term
+// combinations Cc[t Mx + q] = sum_{j<=d-2} ddc[t, j] pt^j_q + ddc[t, d] g^{d-1}_q, whose images U Cc_t
+// enter the split SpMV of Eq. (nleigs-toar2). One thread per coordinate q < m.
+__global__ void toar_coef_kernel(int d, int m, int Mx, int nt, const zd* __restrict__ g, zd* __restrict__ pt,
+                                 zd* __restrict__ Cc, const ExpandCoef* __restrict__ ec,
+                                 const zd* __restrict__ ddc) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= m) return;
+    zd acc[kNleigsMaxTerms];
+    zd gj = g[(int64_t)(d - 1) * Mx + q];
+#pragma unroll
+    for (int i = 0; i < kNleigsMaxTerms; ++i) acc[i] = i < nt ? ddc[i + (int64_t)nt * d] * gj : mk(0.0, 0.0);
+    pt[(int64_t)(d - 1) * Mx + q] = mk(0.0, 0.0);
+    zd pj = mk(0.0, 0.0);
+    for (int j = d - 1; j >= 1; --j) {
+        const zd gjm = g[(int64_t)(j - 1) * Mx + q];
+        const zd z = fma_(gjm, ec->g[j], gj);
+        const zd pv = (z - ec->e[j] * pj) * ec->inv_ds[j];
+        pt[(int64_t)(j - 1) * Mx + q] = pv;
+#pragma unroll
+        for (int i = 0; i < kNleigsMaxTerms; ++i)
+            if (i < nt) acc[i] = fma_(acc[i], ddc[i + (int64_t)nt * (j - 1)], pv);
+        pj = pv;
+        gj = gjm;
+    }
+#pragma unroll
+    for (int i = 0; i < kNleigsMaxTerms; ++i)
+        if (i < nt) Cc[(int64_t)i * Mx + q] = acc[i];
+}
+
+// Eq. (nleigs-toar4): the coefficients of S v in the (possibly extended) basis,
+// gn^i = [pt^i ; 0] + b_i(sigma) [h ; rho] (rho only when U grew), zeros beyond mnew.
+__global__ void toar_next_kernel(int d, int m, int mnew, int Mx, const zd* __restrict__ pt, const zd* __restrict__ h,
+                                 const zd* __restrict__ rho, const ExpandCoef* __restrict__ ec, zd* __restrict__ gn) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)d * Mx) return;
+    const int i = (int)(t / Mx), q = (int)(t - (int64_t)i * Mx);
+    zd v = mk(0.0, 0.0);
+    if (q < m) v = fma_(pt[t], ec->bsig[i], h[q]);
+    else if (q == m && mnew > m) v = ec->bsig[i] * (*rho);
+    gn[t] = v;
+}
+
+// column i of U from block i of the start vector (start of the compact basis); w0 is d x n
+__global__ void toar_copy_kernel(int n, const zd* __restrict__ src, zd* __restrict__ dst) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) dst[r] = src[r];
+}
+// the start coefficients: g^i = (h_i ; rho_i) for the Gram-Schmidt of the start blocks
+__global__ void toar_start_coef_kernel(int i, int Mx, const zd* __restrict__ h, const zd* __restrict__ rho,
+                                       zd* __restrict__ g) {
+    const int q = threadIdx.x;
+    if (q < i) g[(int64_t)i * Mx + q] = h[q];
+    if (q == i) g[(int64_t)i * Mx + q] = *rho;
+}
+
 // A block linearisation (A, B) of d blocks of n with its shift-and-invert recurrences: which expand
 // kernel applies S = (A - sigma B)^{-1} B up to the solve, the per-term coefficients it combines, the
 // combine weights (ec.bsig), the shifted matrix in split form (Fs) and the map from a Ritz value
 // theta of S to lambda = lam_shift + lam_scale / theta.
 struct KrylovLin {
     int kind = 0;  // 0: rational Newton basis (NLEIGS, Sec. 4.5); 1: Chebyshev basis (Interpol, Sec. 4.4)
+    bool toar = false;  // compact basis (Sec. 4.5.3) instead of full (d n)-vectors (kind 0 only)
     int d = 0;
     ExpandCoef ec{};
     std::vector<zd> coef;  // nt x (d+1)
@@ -655,11 +717,12 @@ static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, con
                           double eb, double eig_tol, bool exact, NleigsOut* res, cudaStream_t st);
 
 int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, const double* start_host, zd c,
-               double ea, double eb, double eig_tol, bool exact, NleigsOut* res, cudaStream_t st) {
+               double ea, double eb, double eig_tol, bool exact, NleigsOut* res, cudaStream_t st, bool toar) {
     const int nt = s.nterms, d = it.d;
     if (nt > kNleigsMaxTerms || d < 1 || d > 63 || kmax < 1) return NEP_ERR_ARG;
     KrylovLin lin;
     lin.kind = 0;
+    lin.toar = toar && s.n >= d;
     lin.d = d;
     lin.sigma = shift;
     lin.lam_shift = shift;
@@ -751,7 +814,7 @@ static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, con
     NEP_TRY(w.get(&ipiv, (size_t)n));
     NEP_TRY(w.get(&info, 1));
     if (band_sweeps_fit(s.kl, s.ku)) NEP_TRY(w.get(&ut, (size_t)n * (kv + 1)));
-    NEP_TRY(w.get(&V, (size_t)N * (kmax + 1)));
+    NEP_TRY(w.get(&V, (size_t)N * (lin.toar ? 1 : kmax + 1)));
     NEP_TRY(w.get(&C, (size_t)nt * n));
     NEP_TRY(w.get(&rhs, (size_t)n));
     NEP_TRY(w.get(&u, (size_t)n));
@@ -763,7 +826,7 @@ static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, con
     NEP_TRY(w.get(&hv, (size_t)kmax + 1));
     NEP_TRY(w.get(&nr, 1));
     NEP_TRY(w.get(&hlast, 1));
-    NEP_TRY(w.get(&part, (size_t)nchunks * (kmax + 1)));
+    NEP_TRY(w.get(&part, (size_t)std::max<int64_t>(nchunks, ((int64_t)d * (d + kmax) + chunk - 1) / chunk) * (kmax + 1)));
     NEP_CUDA(cudaMemcpyAsync(d_ec, &ec, sizeof(ec), cudaMemcpyHostToDevice, st));
     NEP_CUDA(cudaMemcpyAsync(d_ddc, ddc.data(), sizeof(zd) * ddc.size(), cudaMemcpyHostToDevice, st));
     NEP_CUDA(cudaMemcpyAsync(d_F, Fs.data(), sizeof(zd) * nt, cudaMemcpyHostToDevice, st));
@@ -793,6 +856,105 @@ static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, con
         }
         return NEP_OK;
     };
+    // compact basis (Sec. 4.5.3): U, the coefficient vectors Gc (stride d Mx), their Hessenberg matrix
+    const int Mx = d + kmax;
+    zd *U = nullptr, *Gc = nullptr, *pt = nullptr, *Cc = nullptr, *hacc = nullptr, *hv2 = nullptr, *partn = nullptr;
+    zd *rho = nullptr, *nr0 = nullptr;
+    int m_cur = 0;
+    const int nchunks_n = (int)((n + chunk - 1) / chunk);
+    const int64_t NG = (int64_t)d * Mx;
+    const int nchunks_g = (int)((NG + chunk - 1) / chunk);
+    auto dots_n = [&](const zd* Vb, int K, const zd* x, zd* out) -> int {  // over n entries
+        nleigs_dots_kernel<<<dim3(nchunks_n, K), 256, 0, st>>>(n, chunk, Vb, x, partn);
+        NEP_CHECK_LAUNCH();
+        nleigs_dots_reduce_kernel<<<ceil_div(K, 128), 128, 0, st>>>(nchunks_n, K, partn, out);
+        NEP_CHECK_LAUNCH();
+        return NEP_OK;
+    };
+    auto dots_g = [&](const zd* Vb, int K, const zd* x, zd* out) -> int {  // over d Mx coefficient entries
+        nleigs_dots_kernel<<<dim3(nchunks_g, K), 256, 0, st>>>(NG, chunk, Vb, x, part);
+        NEP_CHECK_LAUNCH();
+        nleigs_dots_reduce_kernel<<<ceil_div(K, 128), 128, 0, st>>>(nchunks_g, K, part, out);
+        NEP_CHECK_LAUNCH();
+        return NEP_OK;
+    };
+    // u (n) orthogonalised against the m columns of U twice into the column slot m of U; the
+    // coefficients accumulate in hacc, rho = its remaining norm; returns whether U grew (not a breakdown)
+    double* host_pair = nullptr;  // ||u||^2, rho
+    std::vector<double> hp(4, 0.0);
+    auto extend = [&](const zd* u, int m, bool* grew) -> int {
+        zd* col = U + (int64_t)m * n;
+        toar_copy_kernel<<<ceil_div(n, 256), 256, 0, st>>>(n, u, col);
+        NEP_CHECK_LAUNCH();
+        NEP_TRY(dots_n(col, 1, col, nr0));
+        NEP_CUDA(cudaMemsetAsync(hacc, 0, sizeof(zd) * Mx, st));
+        for (int pass = 0; pass < 2 && m > 0; ++pass) {
+            NEP_TRY(dots_n(U, m, col, hv2));
+            nleigs_sub_kernel<<<ceil_div(n, 256), 256, sizeof(zd) * m, st>>>(n, m, U, hv2, col, hacc);
+            NEP_CHECK_LAUNCH();
+        }
+        NEP_TRY(dots_n(col, 1, col, nr));
+        nleigs_scale_kernel<<<ceil_div(n, 256), 256, 0, st>>>(n, col, nr, rho);
+        NEP_CHECK_LAUNCH();
+        NEP_CUDA(cudaMemcpyAsync(hp.data(), nr0, sizeof(double), cudaMemcpyDeviceToHost, st));
+        NEP_CUDA(cudaMemcpyAsync(hp.data() + 2, rho, sizeof(double), cudaMemcpyDeviceToHost, st));
+        NEP_CUDA(cudaStreamSynchronize(st));
+        *grew = hp[2] > 64 * 2.220446049250313e-16 * std::sqrt(std::max(hp[0], 0.0)) && hp[2] > 0.0;
+        return NEP_OK;
+    };
+    (void)host_pair;
+    if (lin.toar) {
+        NEP_TRY(w.get(&U, (size_t)n * (Mx + 1)));
+        NEP_TRY(w.get(&Gc, (size_t)NG * (kmax + 1)));
+        NEP_TRY(w.get(&pt, (size_t)NG));
+        NEP_TRY(w.get(&Cc, (size_t)nt * Mx));
+        NEP_TRY(w.get(&hacc, (size_t)Mx));
+        NEP_TRY(w.get(&hv2, (size_t)Mx));
+        NEP_TRY(w.get(&partn, (size_t)nchunks_n * (Mx + 1)));
+        NEP_TRY(w.get(&rho, 1));
+        NEP_TRY(w.get(&nr0, 1));
+        NEP_CUDA(cudaMemsetAsync(Gc, 0, sizeof(zd) * (size_t)NG * (kmax + 1), st));
+        // start: the d blocks of the start vector by Gram-Schmidt into U, their coordinates into G_0
+        zd* w0 = V;  // the start vector's staging (d blocks of n), the full basis is not used
+        NEP_CUDA(cudaMemcpyAsync(w0, start_host, sizeof(zd) * (size_t)N, cudaMemcpyHostToDevice, st));
+        for (int i = 0; i < d; ++i) {
+            bool grew = false;
+            NEP_TRY(extend(w0 + (int64_t)i * n, m_cur, &grew));
+            if (!grew) { set_error("nleigs: start blocks linearly dependent"); return NEP_ERR_INTERNAL; }
+            toar_start_coef_kernel<<<1, 64, 0, st>>>(i, Mx, hacc, rho, Gc);
+            NEP_CHECK_LAUNCH();
+            ++m_cur;
+        }
+        NEP_TRY(dots_g(Gc, 1, Gc, nr));
+        nleigs_normalize_start_kernel<<<ceil_div(NG, 256), 256, 0, st>>>(NG, Gc, nr);
+        NEP_CHECK_LAUNCH();
+        for (int k = 0; k < kmax; ++k) {
+            const zd* gk = Gc + (int64_t)k * NG;
+            zd* gn = Gc + (int64_t)(k + 1) * NG;
+            toar_coef_kernel<<<ceil_div(m_cur, 128), 128, 0, st>>>(d, m_cur, Mx, nt, gk, pt, Cc, d_ec, d_ddc);
+            NEP_CHECK_LAUNCH();
+            NEP_TRY(zgemm(n, nt, m_cur, 0, U, n, Cc, Mx, C, n, nullptr, 0, st));  // C_t = U Cc_t
+            nleigs_spmv_kernel<<<ceil_div((int64_t)n * 32, 256), 256, 0, st>>>(s, C, rhs);
+            NEP_CHECK_LAUNCH();
+            NEP_TRY(solve());  // y^0 = R_d(shift)^{-1} rhs in u (Eq. (nleigs-toar2))
+            bool grew = false;
+            NEP_TRY(extend(u, m_cur, &grew));  // Eq. (nleigs-toar3)
+            const int mnew = grew ? m_cur + 1 : m_cur;
+            toar_next_kernel<<<ceil_div(NG, 256), 256, 0, st>>>(d, m_cur, mnew, Mx, pt, hacc, rho, d_ec, gn);
+            NEP_CHECK_LAUNCH();
+            m_cur = mnew;
+            // Arnoldi on the coefficient vectors, classical Gram-Schmidt twice
+            zd* Hcol = Hm + (int64_t)kmax * k;
+            for (int pass = 0; pass < 2; ++pass) {
+                NEP_TRY(dots_g(Gc, k + 1, gn, hv));
+                nleigs_sub_kernel<<<ceil_div(NG, 256), 256, sizeof(zd) * (k + 1), st>>>(NG, k + 1, Gc, hv, gn, Hcol);
+                NEP_CHECK_LAUNCH();
+            }
+            NEP_TRY(dots_g(gn, 1, gn, nr));
+            nleigs_scale_kernel<<<ceil_div(NG, 256), 256, 0, st>>>(NG, gn, nr, k + 1 < kmax ? Hcol + k + 1 : hlast);
+            NEP_CHECK_LAUNCH();
+        }
+    } else {
     // start vector, unit 2-norm
     NEP_CUDA(cudaMemcpyAsync(V, start_host, sizeof(zd) * (size_t)N, cudaMemcpyHostToDevice, st));
     NEP_TRY(dots(V, 1, V, nr));
@@ -821,6 +983,7 @@ static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, con
         nleigs_scale_kernel<<<ceil_div(N, 256), 256, 0, st>>>(N, wk, nr, k + 1 < kmax ? Hcol + k + 1 : hlast);
         NEP_CHECK_LAUNCH();
     }
+    }
     // Ritz pairs of the kmax x kmax Hessenberg matrix
     const int m = kmax;
     zd *theta = nullptr, *S = nullptr, *lam = nullptr, *X = nullptr, *G = nullptr;
@@ -846,7 +1009,15 @@ static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, con
     NEP_CHECK_LAUNCH();
     nleigs_ritz_kernel<<<ceil_div(m, 128), 128, 0, st>>>(m, theta, shift, lin.lam_scale, lam, ok);
     NEP_CHECK_LAUNCH();
-    NEP_TRY(zgemm(n, m, m, 0, V, (int)N, S, m, X, n, nullptr, 0, st));
+    if (lin.toar) {
+        // x = first block of the Ritz vector = U (G^0 S), G^0 the coordinates of block 0
+        zd* Z = nullptr;
+        NEP_TRY(w.get(&Z, (size_t)m_cur * m));
+        NEP_TRY(zgemm(m_cur, m, m, 0, Gc, (int)NG, S, m, Z, m_cur, nullptr, 0, st));
+        NEP_TRY(zgemm(n, m, m_cur, 0, U, n, Z, m_cur, X, n, nullptr, 0, st));
+    } else {
+        NEP_TRY(zgemm(n, m, m, 0, V, (int)N, S, m, X, n, nullptr, 0, st));
+    }
     NEP_TRY(launch_normalize_columns(n, m, X, 1, nullptr, st));
     NEP_TRY(launch_eta(s, m, lam, X, eta, st));
     if (!exact) {

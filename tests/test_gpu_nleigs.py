@@ -157,3 +157,32 @@ def test_exact_solve_mode_matches_the_oracle_linearisation(bnd):
     err, _ = match_eigenvalues(r["lam"], ora["lam"])
     assert err <= 1e-10, err
     assert r["eta"].max() <= 1e-11
+
+
+@pytest.mark.parametrize("full_basis", [0, 1])
+def test_compact_and_full_basis_match_the_oracle_linearisation(bnd, full_basis):
+    """n = 36 >= d: the compact (TOAR) basis of Sec. 4.5.3 (default) and the full basis give the
+    oracle's linearisation eigenvalues and vectors."""
+    torch_cuda()
+    p = synth.delay_2d(s=6, seed=1)
+    split = bnd.Split.from_problem(p)
+    assert p.n >= bnd.nleigs_interpolation(split, p.region)["d"]
+    ora = nleigs.solve(p)
+    assert len(ora["lam"]) >= 3
+    r = _solve(bnd, p, krylov=150, full_basis=full_basis)
+    err, pairs = match_eigenvalues(r["lam"], ora["lam"])
+    assert err <= 1e-10, err
+    for i, j in pairs:
+        assert abs(abs(np.vdot(r["X"][:, i], ora["X"][:, j])) - 1.0) <= 1e-9
+
+
+def test_compact_basis_equals_full_basis_at_full_size(bnd):
+    """n = 4096: the same start vector and steps give the same eigenpairs with either basis."""
+    torch_cuda()
+    p = synth.config_problem("delay2d_s64")
+    split = bnd.Split.from_problem(p)
+    a = bnd.nleigs_solve(split, p.region, krylov=100)
+    b = bnd.nleigs_solve(split, p.region, krylov=100, full_basis=1)
+    assert len(a["lam"]) == len(b["lam"]) >= 5
+    err, _ = match_eigenvalues(a["lam"], b["lam"])
+    assert err <= 1e-10, err

@@ -338,3 +338,65 @@ def toar_vectors(U: np.ndarray, G: list, d: int) -> np.ndarray:
         gb = np.pad(gb, ((0, 0), (0, m - gb.shape[1])))
         cols.append(np.concatenate([U @ gb[i] for i in range(d)]))
     return np.column_stack(cols)
+
+
+
+def krylov_schur(S: np.ndarray, v0: np.ndarray, ncv: int, nkeep: int, wanted, tol: float = 1e-12,
+                 max_restarts: int = 20):
+    """Shift-and-invert Arnoldi on an explicit S with thick restarts in Krylov-Schur form and locking
+    (the restart the paper runs on top of Algorithm (nleigs), Sec. 4.5.3), plain FP64.
+
+    The decomposition S V[:, :k] = V[:, :k+1] Hf[:k+1, :k] is extended to k = ncv by Arnoldi steps
+    (classical Gram-Schmidt twice). With H = Hf[:ncv, :ncv] and b = Hf[ncv, :], a Ritz pair (theta, y)
+    of H (unit y) has the residual estimate |b^T y|; `wanted(theta)` marks the pairs sought, converged
+    when |b^T y| <= tol |theta|. The run stops once every wanted pair has converged (at least one is
+    wanted) or after max_restarts restarts. A restart keeps an orthonormal basis Q of the selected Ritz
+    vectors (converged wanted ones first, then the other wanted ones, then the rest, each by decreasing
+    |theta|, i.e. nearest the shift first; nkeep of them, at least one more than the converged ones):
+    V[:, :p] <- V[:, :ncv] Q, V[:, p] <- V[:, ncv], Hf[:p, :p] <- Q^H H Q and Hf[p, :p] <- b^T Q with the
+    entries of the converged (locked) vectors set to zero, so they stay an invariant subspace.
+    Returns V, Hf, the restarts run, the Ritz values and vectors of the last cycle, the residual
+    estimates, and the wanted and converged indices."""
+    N = S.shape[0]
+    V = np.zeros((N, ncv + 1), np.complex128)
+    Hf = np.zeros((ncv + 1, ncv), np.complex128)
+    V[:, 0] = v0 / np.linalg.norm(v0)
+    k0, restarts = 0, 0
+    while True:
+        for j in range(k0, ncv):
+            w = S @ V[:, j]
+            for _ in range(2):
+                hh = V[:, :j + 1].conj().T @ w
+                w = w - V[:, :j + 1] @ hh
+                Hf[:j + 1, j] += hh
+            Hf[j + 1, j] = np.linalg.norm(w)
+            V[:, j + 1] = w / Hf[j + 1, j]
+        H, b = Hf[:ncv, :ncv], Hf[ncv, :]
+        theta, Y = np.linalg.eig(H)
+        Y = Y / np.linalg.norm(Y, axis=0, keepdims=True)
+        res = np.abs(b @ Y)
+        want = [q for q in range(ncv) if wanted(theta[q])]
+        conv = [q for q in want if res[q] <= tol * abs(theta[q])]
+        if (want and len(conv) == len(want)) or restarts >= max_restarts:
+            return {"V": V, "Hf": Hf, "restarts": restarts, "theta": theta, "Y": Y, "res": res,
+                    "wanted": want, "converged": conv}
+        by_size = lambda qs: sorted(qs, key=lambda q: -abs(theta[q]))
+        conv_s = by_size(conv)
+        rest = by_size([q for q in want if q not in conv])
+        others = by_size([q for q in range(ncv) if q not in want])
+        p = min(ncv - 1, max(nkeep, len(conv) + 1))
+        sel = (conv_s + rest + others)[:p]
+        Q, _ = np.linalg.qr(Y[:, sel])
+        Hn = Q.conj().T @ H @ Q
+        bn = b @ Q
+        bn[:len(conv_s)] = 0.0
+        Vn = V[:, :ncv] @ Q
+        vlast = V[:, ncv].copy()
+        V[:] = 0.0
+        V[:, :p] = Vn
+        V[:, p] = vlast
+        Hf[:] = 0.0
+        Hf[:p, :p] = Hn
+        Hf[p, :p] = bn
+        k0 = p
+        restarts += 1

@@ -107,3 +107,15 @@ def test_host_function_terms_are_validated_without_gpu(built):
     f = binding._fn_struct(keep, {"kind": "combine", "op": "add", "a": inner, "b": {"kind": "exp"}})
     assert lib.nep_create_split(n, 1, ctypes.byref(csr), ctypes.byref(f), ctypes.byref(h)) == binding.NEP_ERR_ARG
     assert b"top level" in lib.nep_last_error()
+
+
+def test_tune_cache_loader_without_gpu(built, tmp_path):
+    """nep_tune_load reads the autotuner's cache lines (later lines win, others ignored) on the host."""
+    from paper_1910_11712_gb300 import binding
+    f = tmp_path / "tune.txt"
+    f.write_text("nep-tune n=4096 kl=64 ku=64 L=16 precision=1 lu_kernel=0 solve_rh=2 ms=22.5\n"
+                 "a comment line\n"
+                 "nep-tune n=16384 kl=128 ku=128 L=32 precision=1 lu_kernel=1 solve_rh=4 ms=151.0\n")
+    assert binding.tune_load(str(f)) == 2
+    with pytest.raises(binding.NepError):
+        binding.tune_load(str(tmp_path / "missing.txt"))

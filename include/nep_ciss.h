@@ -211,6 +211,8 @@ typedef struct {
     double ms_latency;      /* server requests: submit to result ready (0 otherwise) */
     int32_t newton_failed;  /* Newton runs that failed (these raise NEP_WARN_NEWTON)       */
     int32_t newton_left;    /* Newton runs whose iterate left the region (no warning)      */
+    int32_t krylov_steps;   /* NLEIGS, Interpol: Arnoldi steps run, over all restart cycles */
+    int32_t restarts;       /* NLEIGS, Interpol: Krylov-Schur restarts run                  */
 } nep_result_info_t;
 int nep_result_info(nep_result_t r, nep_result_info_t *info);
 /* Singular values of the Hankel matrix (L*M of them, descending). */
@@ -352,7 +354,7 @@ typedef struct {
     double tol;          /* degree test max_i |d_i^d| < tol max_i |d_i^0|; default 1e-13        */
     int32_t max_degree;  /* largest degree d; default 60, at most 63                             */
     int32_t nboundary;   /* points discretising the boundary of the region; default 1024         */
-    int32_t krylov;      /* Arnoldi steps (no restart); default 100, at most 512                 */
+    int32_t krylov;      /* Arnoldi steps of a cycle (the basis size); default 100, at most 512  */
     int32_t has_shift;   /* nonzero: use shift_re/im as the shift sigma, else the region centre  */
     double shift_re, shift_im;
     uint64_t seed;       /* seeded start vector (SplitMix64 + Box-Muller)                         */
@@ -363,6 +365,13 @@ typedef struct {
                           /* residuals, tol 1e-13, at most 10 iterations) before the acceptance    */
     int32_t full_basis;   /* nonzero: Arnoldi on full (d n)-vectors; zero (default): the compact TOAR   */
                           /* basis of Sec. 4.5.3, U (n x m, m <= d + krylov) and coefficient vectors    */
+    int32_t max_restarts; /* Krylov-Schur restarts with locking after the first cycle of krylov steps;  */
+                          /* 0 (default): one cycle, no restart                                          */
+    int32_t keep;         /* vectors kept at a restart, < krylov; default krylov / 2                     */
+    double restart_tol;   /* a Ritz pair has converged when |b^T s| <= restart_tol |theta|; default     */
+                          /* 1e-10 with exact_solves, 1e-6 without                                       */
+    int32_t nev;          /* restarts stop once nev wanted pairs have converged; 0 (default): once      */
+                          /* every wanted Ritz pair of the cycle has converged (at least one)            */
 } nep_nleigs_opts;
 /* The rational interpolant R_d(z) = sum_j b_j(z) D_j, D_j = sum_i d_i^j A_i, of Sec. 4.5.1 on the
  * region (host computation):
@@ -400,14 +409,26 @@ int nep_nleigs_interpolation_fns(int32_t nterms, const nep_fn *f, const nep_regi
  * (Eqs. (nleigs-toar1)-(nleigs-toar4)): Krylov vectors (I_d (x) U) g with U orthonormal (n x m, one new
  * column per step, none when the new direction already lies in span U) and coefficient vectors g,
  * Gram-Schmidt on n-vectors for U and on d m coefficient vectors for the Arnoldi; o->full_basis
- * keeps full (d n)-vectors. Classical Gram-Schmidt twice in both. Ritz values theta (complex64 Hessenberg QR, then FP64 inverse iteration on
- * the Hessenberg matrix and a Rayleigh quotient) give lambda = sigma + 1/theta and x the first block
- * of the Ritz vector; pairs inside the region with FP64 eta (Sec. 2 Eq. (sressplit), of the full T) at most
+ * keeps full (d n)-vectors. Classical Gram-Schmidt twice in both. Ritz values theta (complex64 QR, then
+ * FP64 inverse iteration on the projected matrix and a Rayleigh quotient) give lambda = sigma + 1/theta
+ * and x the first block of the Ritz vector. With o->max_restarts > 0, Krylov-Schur restarts with
+ * locking follow each cycle of krylov steps (Sec. 4.5.3): the Ritz pairs with lambda inside the region
+ * are wanted, converged when |b^T s| <= restart_tol |theta| (b the last row of the (k+1) x k Arnoldi
+ * matrix); the run stops once o->nev wanted pairs have converged (nev = 0: every wanted pair of the
+ * cycle, at least one) or after max_restarts restarts; else
+ * the basis is cut to the invariant subspace of p = max(keep, converged + 1) Ritz values (converged
+ * first, then wanted, then the others, each nearest the shift first), Q = the leading p Schur vectors
+ * of H after the FP64 Schur form is reordered to put those first, plus the last Arnoldi vector; H
+ * becomes the leading p x p block of the reordered Schur factor with the coupling row b^T Q, whose
+ * entries for the converged (locked) vectors are zeroed, and the compact basis is compressed to the
+ * leading left singular vectors of its coefficient blocks (U <- U W, one-sided Jacobi SVD, at most
+ * d + kept vectors); the Arnoldi continues from there; pairs inside the region with FP64 eta (Sec. 2 Eq. (sressplit), of the full T) at most
  * eig_tol are returned, deduplicated and sorted as nep_ciss_solve does. *out receives a result
  * object (nep_result_get; hankel_rank there is 0; flags NEP_WARN_INTERP if the degree test failed
  * at max_degree, NEP_WARN_SINGULAR_NODE if R_d(sigma) had an exactly zero pivot); *degree (or NULL)
- * the interpolation degree. The call allocates its work arrays on the stream ((d n) x (krylov+1)
- * complex128 for the basis) and returns when they are done. Errors: NEP_ERR_ARG, NEP_ERR_REGION
+ * the interpolation degree; nep_result_info gives the Arnoldi steps run and the restarts. The call
+ * allocates its work arrays on the stream ((d n) x (krylov+1) complex128 for the full basis, n x
+ * (d + krylov + 1) for the compact one) and returns when they are done. Errors: NEP_ERR_ARG, NEP_ERR_REGION
  * (a singularity of some f_i inside or on the region), NEP_ERR_UNSUPPORTED (more than 8 terms),
  * CUDA errors. */
 int nep_nleigs_solve(nep_split_t h, const nep_region *r, const nep_nleigs_opts *o, nep_result_t *out,
@@ -417,7 +438,7 @@ int nep_nleigs_solve(nep_split_t h, const nep_region *r, const nep_nleigs_opts *
 /* Options of the polynomial interpolation solver (Sec. 4.4). Zero fields take the defaults. */
 typedef struct {
     int32_t degree;       /* interpolation degree d, 2 .. 63 (the paper leaves it to the user); default 40 */
-    int32_t krylov;       /* Arnoldi steps (no restart); default 60, at most 512                           */
+    int32_t krylov;       /* Arnoldi steps of a cycle (the basis size); default 60, at most 512            */
     int32_t has_shift;    /* nonzero: shift_re/im (a value of lambda) as the shift; else the interval's    */
     double shift_re, shift_im; /* centre                                                                */
     uint64_t seed;        /* seeded start vector (SplitMix64 + Box-Muller)                                 */
@@ -425,6 +446,10 @@ typedef struct {
     int32_t fast_solves;  /* nonzero: plain complex64 solves, then residual inverse iteration on T for the  */
                           /* Ritz pairs inside the region with eta <= 1e-4 (their eigenvalues then are T's, */
                           /* not P_d's); zero (default): each solve gets two FP64-residual corrections      */
+    int32_t max_restarts; /* Krylov-Schur restarts as for nep_nleigs_opts (0: none)                        */
+    int32_t keep;         /* vectors kept at a restart, < krylov; default krylov / 2                        */
+    double restart_tol;   /* convergence of a Ritz pair, as for nep_nleigs_opts (default 1e-10, fast 1e-6)  */
+    int32_t nev;          /* wanted eigenvalues that end the restarts, as for nep_nleigs_opts              */
 } nep_interpol_opts;
 /* Chebyshev coefficients of the f_i on the interval I = [c - a, c + a], the real axis of the region's
  * ellipse (real centre c; a = real semi-axis), lambda = a theta + c (host computation, no device):
@@ -438,7 +463,8 @@ int nep_interpol_coefficients(int32_t nterms, const nep_fn *f, const nep_region 
  * Chebyshev-basis linearisation (block rows -theta u_0 + u_1 = 0, u_{k-1} - 2 theta u_k + u_{k+1} = 0 and
  * sum_{k<d} C'_k u_k + C_d (2 theta u_{d-1} - u_{d-2}) = 0 for u_k = tau_k(theta) x), applied through
  * the block recurrences with one band LU of P_d(sigma) (complex64 factors) and one band solve per step;
- * classical Gram-Schmidt twice, Ritz values as nep_nleigs_solve. The region filter of Sec. 4.4: pairs
+ * classical Gram-Schmidt twice, Ritz values and Krylov-Schur restarts (o->max_restarts) as
+ * nep_nleigs_solve with its full basis. The region filter of Sec. 4.4: pairs
  * with lambda strictly inside the region's ellipse (its imaginary semi-axis sets the vicinity of the
  * interval) and the scaled residual of T itself <= eig_tol, sorted and deduplicated as nep_ciss_solve
  * does; x is the first block of the Ritz vector. *out receives a result object (hankel_rank 0, no

@@ -342,15 +342,16 @@ def toar_vectors(U: np.ndarray, G: list, d: int) -> np.ndarray:
 
 
 def krylov_schur(S: np.ndarray, v0: np.ndarray, ncv: int, nkeep: int, wanted, tol: float = 1e-12,
-                 max_restarts: int = 20):
+                 max_restarts: int = 20, nev: int = 0):
     """Shift-and-invert Arnoldi on an explicit S with thick restarts in Krylov-Schur form and locking
     (the restart the paper runs on top of Algorithm (nleigs), Sec. 4.5.3), plain FP64.
 
     The decomposition S V[:, :k] = V[:, :k+1] Hf[:k+1, :k] is extended to k = ncv by Arnoldi steps
     (classical Gram-Schmidt twice). With H = Hf[:ncv, :ncv] and b = Hf[ncv, :], a Ritz pair (theta, y)
     of H (unit y) has the residual estimate |b^T y|; `wanted(theta)` marks the pairs sought, converged
-    when |b^T y| <= tol |theta|. The run stops once every wanted pair has converged (at least one is
-    wanted) or after max_restarts restarts. A restart keeps an orthonormal basis Q of the selected Ritz
+    when |b^T y| <= tol |theta|. The run stops once nev wanted pairs have converged (the number of
+    eigenvalues sought, which also sets the basis size in the experiments of Sec. 6; nev = 0: every
+    wanted pair of the cycle, at least one) or after max_restarts restarts. A restart keeps an orthonormal basis Q of the selected Ritz
     vectors (converged wanted ones first, then the other wanted ones, then the rest, each by decreasing
     |theta|, i.e. nearest the shift first; nkeep of them, at least one more than the converged ones):
     V[:, :p] <- V[:, :ncv] Q, V[:, p] <- V[:, ncv], Hf[:p, :p] <- Q^H H Q and Hf[p, :p] <- b^T Q with the
@@ -377,7 +378,8 @@ def krylov_schur(S: np.ndarray, v0: np.ndarray, ncv: int, nkeep: int, wanted, to
         res = np.abs(b @ Y)
         want = [q for q in range(ncv) if wanted(theta[q])]
         conv = [q for q in want if res[q] <= tol * abs(theta[q])]
-        if (want and len(conv) == len(want)) or restarts >= max_restarts:
+        done = len(conv) >= nev if nev > 0 else (want and len(conv) == len(want))
+        if done or restarts >= max_restarts:
             return {"V": V, "Hf": Hf, "restarts": restarts, "theta": theta, "Y": Y, "res": res,
                     "wanted": want, "converged": conv}
         by_size = lambda qs: sorted(qs, key=lambda q: -abs(theta[q]))

@@ -59,12 +59,14 @@ class NepOpts(ctypes.Structure):
 class NepNleigsOpts(ctypes.Structure):
     _fields_ = [("tol", c_double), ("max_degree", c_int32), ("nboundary", c_int32), ("krylov", c_int32),
                 ("has_shift", c_int32), ("shift_re", c_double), ("shift_im", c_double), ("seed", ctypes.c_uint64),
-                ("eig_tol", c_double), ("exact_solves", c_int32), ("full_basis", c_int32)]
+                ("eig_tol", c_double), ("exact_solves", c_int32), ("full_basis", c_int32),
+                ("max_restarts", c_int32), ("keep", c_int32), ("restart_tol", c_double), ("nev", c_int32)]
 
 
 class NepInterpolOpts(ctypes.Structure):
     _fields_ = [("degree", c_int32), ("krylov", c_int32), ("has_shift", c_int32), ("shift_re", c_double),
-                ("shift_im", c_double), ("seed", ctypes.c_uint64), ("eig_tol", c_double), ("fast_solves", c_int32)]
+                ("shift_im", c_double), ("seed", ctypes.c_uint64), ("eig_tol", c_double), ("fast_solves", c_int32),
+                ("max_restarts", c_int32), ("keep", c_int32), ("restart_tol", c_double), ("nev", c_int32)]
 
 
 class NepTuneResult(ctypes.Structure):
@@ -79,7 +81,7 @@ class NepResultInfo(ctypes.Structure):
                 ("ms_assemble", c_double), ("ms_factor", c_double), ("ms_solve", c_double),
                 ("ms_moments", c_double), ("ms_extract", c_double), ("ms_total", c_double),
                 ("ms_queued", c_double), ("ms_latency", c_double), ("newton_failed", c_int32),
-                ("newton_left", c_int32)]
+                ("newton_left", c_int32), ("krylov_steps", c_int32), ("restarts", c_int32)]
 
 
 # name -> (restype, argtypes)
@@ -559,10 +561,11 @@ def apply_resolvent(n, P, lam_dev, X_dev, Y_dev, nz, z_dev, nv, V_dev, out_dev, 
 
 
 def nleigs_opts(tol=0.0, max_degree=0, nboundary=0, krylov=0, shift=None, seed=0, eig_tol=0.0,
-                exact_solves=0, full_basis=0) -> NepNleigsOpts:
+                exact_solves=0, full_basis=0, max_restarts=0, keep=0, restart_tol=0.0, nev=0) -> NepNleigsOpts:
     o = NepNleigsOpts()
     o.tol, o.max_degree, o.nboundary, o.krylov, o.seed, o.eig_tol = tol, max_degree, nboundary, krylov, seed, eig_tol
     o.exact_solves, o.full_basis = exact_solves, full_basis
+    o.max_restarts, o.keep, o.restart_tol, o.nev = max_restarts, keep, restart_tol, nev
     if shift is not None:
         o.has_shift, o.shift_re, o.shift_im = 1, complex(shift).real, complex(shift).imag
     return o

@@ -804,24 +804,15 @@ __device__ void givens(cx<T> x, cx<T> y, T* c, cx<T>* s) {
     *s = (T(1) / nrm) * (ph * conj(y));
 }
 
+// The Schur form of the m x m matrix in H (one warp, leading dimension ld): H <- Z^H H Z upper
+// triangular, Z accumulating the transformations (Z must hold I, or a unitary to be updated, on
+// entry); v is m scratch elements. Returns 1 if the QR iteration hit its sweep limit.
 template <typename T>
-__global__ void schur_eig_kernel(int m, const zd* __restrict__ Ain, zd* __restrict__ eval, zd* __restrict__ evec,
-                                 int* __restrict__ status, cx<T>* gbuf, int use_smem) {
-    extern __shared__ unsigned char sraw[];
-    const int ld = m + 1;
-    cx<T>* H = use_smem ? reinterpret_cast<cx<T>*>(sraw) : gbuf;
-    cx<T>* Z = H + (int64_t)m * ld;
-    cx<T>* v = Z + (int64_t)m * ld;  // m
-    const int lane = threadIdx.x;
+__device__ int schur_form(int m, cx<T>* H, cx<T>* Z, cx<T>* v, int ld) {
+    const int lane = threadIdx.x & 31;
     const T eps = sizeof(T) == 4 ? T(6e-8) : T(1.2e-16);
     auto h = [&](int i, int j) -> cx<T>& { return H[i + (int64_t)ld * j]; };
     auto z = [&](int i, int j) -> cx<T>& { return Z[i + (int64_t)ld * j]; };
-    for (int t = lane; t < m * m; t += 32) {
-        const int i = t % m, j = t / m;
-        h(i, j) = cvt<T>(Ain[i + (int64_t)m * j]);
-        z(i, j) = mk<T>(i == j ? T(1) : T(0), T(0));
-    }
-    __syncwarp();
     // Hessenberg reduction
     for (int k = 0; k + 2 < m; ++k) {
         T nx = 0;
@@ -933,6 +924,29 @@ __global__ void schur_eig_kernel(int m, const zd* __restrict__ Ain, zd* __restri
         }
     }
     __syncwarp();
+    return fail;
+}
+
+template <typename T>
+__global__ void schur_eig_kernel(int m, const zd* __restrict__ Ain, zd* __restrict__ eval, zd* __restrict__ evec,
+                                 int* __restrict__ status, cx<T>* gbuf, int use_smem) {
+    extern __shared__ unsigned char sraw[];
+    const int ld = m + 1;
+    cx<T>* H = use_smem ? reinterpret_cast<cx<T>*>(sraw) : gbuf;
+    cx<T>* Z = H + (int64_t)m * ld;
+    cx<T>* v = Z + (int64_t)m * ld;  // m
+    const int lane = threadIdx.x;
+    const T eps = sizeof(T) == 4 ? T(6e-8) : T(1.2e-16);
+    auto h = [&](int i, int j) -> cx<T>& { return H[i + (int64_t)ld * j]; };
+    auto z = [&](int i, int j) -> cx<T>& { return Z[i + (int64_t)ld * j]; };
+    for (int t = lane; t < m * m; t += 32) {
+        const int i = t % m, j = t / m;
+        h(i, j) = cvt<T>(Ain[i + (int64_t)m * j]);
+        z(i, j) = mk<T>(i == j ? T(1) : T(0), T(0));
+    }
+    __syncwarp();
+    const int fail = schur_form<T>(m, H, Z, v, ld);
+    __syncwarp();
     for (int i = lane; i < m; i += 32) eval[i] = cvt<double>(h(i, i));
     if (lane == 0 && status) *status = fail;
     if (!evec) return;
@@ -981,6 +995,109 @@ int small_eig(int m, const zd* A, zd* eval, zd* evec, int* status, void* gbuf, c
 }
 template int small_eig<float>(int, const zd*, zd*, zd*, int*, void*, cudaStream_t);
 template int small_eig<double>(int, const zd*, zd*, zd*, int*, void*, cudaStream_t);
+
+// ------------------------------------------------------------------ Krylov-Schur restart
+// The FP64 Schur form H = Z T Z^H of an m x m matrix (one warp): eval = diag(T), T (upper
+// triangular) and Z written with leading dimension m. gbuf (2 m (m+1) + m complex128) is used when
+// shared memory is too small.
+__global__ void ks_schur_kernel(int m, const zd* __restrict__ A, zd* __restrict__ eval, zd* __restrict__ Tout,
+                                zd* __restrict__ Zout, int* __restrict__ status, zd* gbuf, int use_smem) {
+    extern __shared__ unsigned char sraw[];
+    const int ld = m + 1, lane = threadIdx.x;
+    zd* H = use_smem ? reinterpret_cast<zd*>(sraw) : gbuf;
+    zd* Z = H + (int64_t)m * ld;
+    zd* v = Z + (int64_t)m * ld;
+    for (int t = lane; t < m * m; t += 32) {
+        const int i = t % m, j = t / m;
+        H[i + (int64_t)ld * j] = A[t];
+        Z[i + (int64_t)ld * j] = mk(i == j ? 1.0 : 0.0, 0.0);
+    }
+    __syncwarp();
+    const int fail = schur_form<double>(m, H, Z, v, ld);
+    for (int t = lane; t < m * m; t += 32) {
+        const int i = t % m, j = t / m;
+        Tout[t] = i <= j ? H[i + (int64_t)ld * j] : mk(0.0, 0.0);
+        Zout[t] = Z[i + (int64_t)ld * j];
+    }
+    for (int i = lane; i < m; i += 32) eval[i] = H[i + (int64_t)ld * i];
+    if (lane == 0 && status) *status = fail;
+}
+
+// Reorders the Schur form (T, Z, leading dimension m) so that the diagonal entries that stood at
+// positions sel[0 .. p) come first, in that order: each is moved up by swaps of adjacent diagonal
+// entries, the swap at k by the rotation G with G [T(k,k+1); T(k+1,k+1) - T(k,k)] = [r; 0] (that
+// vector is the eigenvector of the 2 x 2 block for T(k+1,k+1)): rows k, k+1 of T <- G (rows),
+// columns k, k+1 of T and of Z <- (columns) G^H, then T(k+1,k) = 0 and the two diagonal entries
+// exchanged exactly. One warp.
+__global__ void ks_reorder_kernel(int m, int p, const int* __restrict__ sel, zd* __restrict__ T, zd* __restrict__ Z) {
+    extern __shared__ int posbuf[];  // pos[m]: current position of original index q; at[m]: inverse
+    int* pos = posbuf;
+    int* at = posbuf + m;
+    const int lane = threadIdx.x;
+    for (int q = lane; q < m; q += 32) {
+        pos[q] = q;
+        at[q] = q;
+    }
+    __syncwarp();
+    auto t = [&](int i, int j) -> zd& { return T[i + (int64_t)m * j]; };
+    for (int dst = 0; dst < p; ++dst) {
+        const int q = sel[dst];
+        for (int j = pos[q]; j > dst; --j) {
+            const int k = j - 1;
+            const zd a = t(k, k), b = t(k + 1, k + 1);
+            double cs;
+            zd sn;
+            givens(t(k, k + 1), b - a, &cs, &sn);
+            __syncwarp();
+            for (int c = k + lane; c < m; c += 32) {
+                const zd x = t(k, c), y = t(k + 1, c);
+                t(k, c) = cs * x + sn * y;
+                t(k + 1, c) = cs * y - conj(sn) * x;
+            }
+            __syncwarp();
+            for (int r = lane; r <= k + 1; r += 32) {
+                const zd x = t(r, k), y = t(r, k + 1);
+                t(r, k) = cs * x + conj(sn) * y;
+                t(r, k + 1) = cs * y - sn * x;
+            }
+            for (int r = lane; r < m; r += 32) {
+                const zd x = Z[r + (int64_t)m * k], y = Z[r + (int64_t)m * (k + 1)];
+                Z[r + (int64_t)m * k] = cs * x + conj(sn) * y;
+                Z[r + (int64_t)m * (k + 1)] = cs * y - sn * x;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                t(k + 1, k) = mk(0.0, 0.0);
+                t(k, k) = b;
+                t(k + 1, k + 1) = a;
+                const int qa = at[k], qb = at[k + 1];
+                at[k] = qb;
+                at[k + 1] = qa;
+                pos[qb] = k;
+                pos[qa] = k + 1;
+            }
+            __syncwarp();
+        }
+    }
+}
+
+int launch_ks_schur(int m, const zd* A, zd* eval, zd* T, zd* Z, int* status, zd* gbuf, cudaStream_t st) {
+    if (m <= 0) return NEP_OK;
+    const size_t bytes = sizeof(zd) * ((size_t)2 * m * (m + 1) + m);
+    const int use_smem = bytes <= 200 * 1024;
+    if (use_smem) NEP_CUDA(allow_max_dynamic_smem(ks_schur_kernel));
+    else if (!gbuf) return NEP_ERR_INTERNAL;
+    ks_schur_kernel<<<1, 32, use_smem ? bytes : 0, st>>>(m, A, eval, T, Z, status, gbuf, use_smem);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+
+int launch_ks_reorder(int m, int p, const int* sel, zd* T, zd* Z, cudaStream_t st) {
+    if (m <= 0 || p <= 0) return NEP_OK;
+    ks_reorder_kernel<<<1, 32, sizeof(int) * 2 * m, st>>>(m, p, sel, T, Z);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
 
 // The rotation of givens() from one reciprocal square root: c and s do not change when x and y are
 // scaled by a common positive factor, so after scaling by 1 / max(|Re|, |Im|) (no overflow or
@@ -1242,6 +1359,7 @@ int small_eig_fast(int m, const zd* A, zd* eval, zd* evec, int* status, void* gb
     return NEP_OK;
 }
 template int small_eig_fast<float>(int, const zd*, zd*, zd*, int*, void*, cudaStream_t);
+template int small_eig_fast<double>(int, const zd*, zd*, zd*, int*, void*, cudaStream_t);
 
 // ------------------------------------------------------------------ helpers
 // Scale column c of X (rows x cols) by 1/|x_c|_2 (optionally fixing the phase so the first

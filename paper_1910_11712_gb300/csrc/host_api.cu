@@ -1599,7 +1599,26 @@ struct NleigsParams {
     double eig_tol;
     bool exact;
     bool toar;
+    int max_restarts, keep, nev;
+    double restart_tol;
 };
+
+// Krylov-Schur restart options of NLEIGS and Interpol on a cycle of kmax Arnoldi steps
+static int ks_params(int max_restarts, int keep, double tol, int nev, int kmax, bool exact, KsOpts* ks) {
+    if (max_restarts < 0 || max_restarts > 10000 || keep < 0 || tol < 0 || nev < 0) {
+        set_error("restarts: need 0 <= max_restarts <= 10000, keep >= 0, restart_tol >= 0, nev >= 0");
+        return NEP_ERR_ARG;
+    }
+    if (max_restarts > 0 && (kmax < 2 || keep >= kmax)) {
+        set_error("restarts: need krylov >= 2 and keep < krylov (krylov %d, keep %d)", kmax, keep);
+        return NEP_ERR_ARG;
+    }
+    ks->max_restarts = max_restarts;
+    ks->keep = keep > 0 ? keep : std::max(1, kmax / 2);
+    ks->tol = tol > 0 ? tol : (exact ? 1e-10 : 1e-6);
+    ks->nev = nev;
+    return NEP_OK;
+}
 
 static int nleigs_params(nep_split_t h, const nep_region* r, const nep_nleigs_opts* o, NleigsParams* q) {
     if (!h || !r) { set_error("null handle or region"); return NEP_ERR_ARG; }
@@ -1615,6 +1634,10 @@ static int nleigs_params(nep_split_t h, const nep_region* r, const nep_nleigs_op
     q->eig_tol = o->eig_tol > 0 ? o->eig_tol : 1e-8;
     q->exact = o->exact_solves != 0;
     q->toar = o->full_basis == 0;
+    q->max_restarts = o->max_restarts;
+    q->keep = o->keep;
+    q->restart_tol = o->restart_tol;
+    q->nev = o->nev;
     if (q->dmax > 63 || q->nb < 8 || q->nb > (1 << 20) || q->kmax > 512) {
         set_error("nleigs: max_degree <= 63, 8 <= nboundary <= 2^20, krylov <= 512");
         return NEP_ERR_ARG;
@@ -1707,16 +1730,21 @@ extern "C" int nep_nleigs_solve(nep_split_t h, const nep_region* r, const nep_nl
     const int kmax = (int)std::min<size_t>((size_t)q.kmax, N);
     std::vector<zd> start(N);
     draw_probe_block(q.seed, N, false, reinterpret_cast<double*>(start.data()));
+    KsOpts ks;
+    NEP_TRY(ks_params(q.max_restarts, q.keep, q.restart_tol, q.nev, kmax, q.exact, &ks));
     NleigsOut res;
     cudaStream_t st = (cudaStream_t)stream;
     NEP_TRY(nleigs_run(h->dev(), it, q.shift, kmax, reinterpret_cast<const double*>(start.data()),
-                       mk(r->center_re, r->center_im), r->a, r->b, q.eig_tol, q.exact, &res, st, q.toar));
+                       mk(r->center_re, r->center_im), r->a, r->b, q.eig_tol, q.exact, &res, st, q.toar, ks));
     nep_result* rr = new nep_result();
     rr->n = h->n;
     rr->nconv = (int)res.lam.size();
     rr->m = 0;
     rr->flags = (it.converged ? 0 : NEP_WARN_INTERP) | (res.lu_info ? NEP_WARN_SINGULAR_NODE : 0);
     rr->info.n = h->n;
+    rr->info.flags = rr->flags;
+    rr->info.krylov_steps = res.steps;
+    rr->info.restarts = res.restarts;
     for (size_t q2 = 0; q2 < res.lam.size(); ++q2) {
         rr->lam.push_back(res.lam[q2].re);
         rr->lam.push_back(res.lam[q2].im);
@@ -1805,10 +1833,12 @@ extern "C" int nep_interpol_solve(nep_split_t h, const nep_region* r, const nep_
     const int kmax = (int)std::min<size_t>((size_t)kry, N);
     std::vector<zd> start(N);
     draw_probe_block(o->seed, N, false, reinterpret_cast<double*>(start.data()));
+    KsOpts ks;
+    NEP_TRY(ks_params(o->max_restarts, o->keep, o->restart_tol, o->nev, kmax, o->fast_solves == 0, &ks));
     NleigsOut res;
     cudaStream_t st = (cudaStream_t)stream;
     NEP_TRY(interpol_run(h->dev(), c, d, sigma, r->a, r->center_re, kmax, reinterpret_cast<const double*>(start.data()),
-                         mk(r->center_re, r->center_im), r->a, r->b, eig_tol, o->fast_solves == 0, &res, st));
+                         mk(r->center_re, r->center_im), r->a, r->b, eig_tol, o->fast_solves == 0, &res, st, ks));
     nep_result* rr = new nep_result();
     rr->n = h->n;
     rr->nconv = (int)res.lam.size();
@@ -1816,6 +1846,8 @@ extern "C" int nep_interpol_solve(nep_split_t h, const nep_region* r, const nep_
     rr->flags = res.lu_info ? NEP_WARN_SINGULAR_NODE : 0;
     rr->info.n = h->n;
     rr->info.flags = rr->flags;
+    rr->info.krylov_steps = res.steps;
+    rr->info.restarts = res.restarts;
     for (size_t q2 = 0; q2 < res.lam.size(); ++q2) {
         rr->lam.push_back(res.lam[q2].re);
         rr->lam.push_back(res.lam[q2].im);

@@ -340,6 +340,11 @@ template <typename T>
 int small_eig(int m, const zd* A, zd* eval, zd* evec, int* status, void* gbuf, cudaStream_t st);
 template <typename T>
 int small_eig_fast(int m, const zd* A, zd* eval, zd* evec, int* status, void* gbuf, cudaStream_t st);
+// Krylov-Schur restart: the FP64 Schur form A = Z T Z^H (eval = diag T; gbuf 2 m (m+1) + m elements,
+// needed when it does not fit in shared memory), and its reordering that brings the diagonal entries
+// at positions sel[0 .. p) to the front in that order
+int launch_ks_schur(int m, const zd* A, zd* eval, zd* T, zd* Z, int* status, zd* gbuf, cudaStream_t st);
+int launch_ks_reorder(int m, int p, const int* sel, zd* T, zd* Z, cudaStream_t st);
 // complex128-sized elements of one Newton candidate's work area (FP32 Jacobian + FP64 iterate)
 size_t newton_scratch_bytes(int k, int nterms);
 int launch_pchol(int m, const zd* G, double tol2, int* rank_out, zd* Z, zd* gwork, cudaStream_t st);
@@ -412,19 +417,30 @@ struct NleigsInterp {
 struct NleigsOut {
     std::vector<zd> lam, X, ritz;
     std::vector<double> eta;
-    int steps = 0, lu_info = 0, polished = 0, polish_its = 0;
+    int steps = 0, restarts = 0, lu_info = 0, polished = 0, polish_its = 0;
+};
+// Krylov-Schur restarts of the shift-and-invert Arnoldi (NLEIGS, Interpol): none when max_restarts
+// is 0 (one cycle); keep: vectors kept at a restart (at least one more than the converged ones);
+// a Ritz pair has converged when its residual estimate |b^T s| <= tol |theta|; the restarts stop
+// once nev wanted pairs have converged (nev = 0: all wanted pairs of the cycle, at least one)
+struct KsOpts {
+    int max_restarts = 0;
+    int keep = 0;
+    double tol = 1e-10;
+    int nev = 0;
 };
 int nleigs_interpolation(const std::vector<FnNode>& nodes, const std::vector<zd>& pool, const std::vector<int>& roots,
                          zd c, double a, double b, double tol, int dmax, int nb, NleigsInterp* out);
 // exact: complex64 solves with two FP64-residual corrections; otherwise plain complex64 solves and
 // residual inverse iteration on the converged Ritz pairs inside the region
 int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, const double* start_host, zd c,
-               double ea, double eb, double eig_tol, bool exact, NleigsOut* res, cudaStream_t st, bool toar = true);
+               double ea, double eb, double eig_tol, bool exact, NleigsOut* res, cudaStream_t st, bool toar = true,
+               const KsOpts& ks = KsOpts());
 // Interpol (Sec. 4.4): Krylov on the Chebyshev-basis linearisation of P_d; c: nt x (d+1) coefficients
 // of Eq. (polinterpcoef), lambda = alpha theta + beta, sigma the shift in theta
 int interpol_run(const SplitDev& s, const std::vector<zd>& c, int d, zd sigma, double alpha, double beta, int kmax,
                  const double* start_host, zd center, double ea, double eb, double eig_tol, bool exact, NleigsOut* res,
-                 cudaStream_t st);
+                 cudaStream_t st, const KsOpts& ks = KsOpts());
 // out (n x nz*nv, column j*nv + k) = sum_i x_i (y_i^* v_k) / (z_j - lam_i)
 int apply_resolvent(int n, int P, const zd* lam, const zd* X, const zd* Y, int nz, const zd* z, int nv, const zd* V,
                     zd* out, cudaStream_t st);

@@ -573,6 +573,155 @@ __global__ void __launch_bounds__(32) nleigs_ritz_vectors_kernel(int m, const zd
     if (lane == 0 && isfinite(rq.re) && isfinite(rq.im)) theta[e] = rq;
 }
 
+// ---- Krylov-Schur restart with locking, on top of the Arnoldi of Sec. 4.5.3. After a restart the
+// projected matrix H (m x m) is no longer Hessenberg: the kept p x p block Q^H H Q (upper triangular:
+// Q holds leading Schur vectors), the coupling row p below it, then Hessenberg columns p .. m-1 from
+// the continued Arnoldi.
+
+// Ritz vector of theta_e for a general H (one warp per Ritz value, FP64): H - theta I by Gaussian
+// elimination with partial pivoting (whole rows swapped; an exactly zero pivot stands for eps |H|),
+// three steps of inverse iteration from a constant vector, theta replaced by the Rayleigh quotient
+// s^H H s of the unit vector s.
+__global__ void __launch_bounds__(32) ks_ritz_vectors_kernel(int m, const zd* __restrict__ H, zd* __restrict__ theta,
+                                                             zd* __restrict__ S, zd* __restrict__ work,
+                                                             int* __restrict__ pivw) {
+    extern __shared__ zd y[];  // m
+    const int e = blockIdx.x, lane = threadIdx.x;
+    zd* A = work + (int64_t)e * m * m;
+    int* pv = pivw + (int64_t)e * m;
+    const zd th = theta[e];
+    double anorm = 0.0;
+    for (int64_t t = lane; t < (int64_t)m * m; t += 32) {
+        const int i = (int)(t % m), j = (int)(t / m);
+        zd a = H[t];
+        if (i == j) a = a - th;
+        A[t] = a;
+        anorm = fmax(anorm, abs1(a));
+    }
+    for (int o = 16; o > 0; o >>= 1) anorm = fmax(anorm, __shfl_xor_sync(0xffffffffu, anorm, o));
+    const double tiny = 1.2e-16 * (anorm > 0.0 ? anorm : 1.0);
+    __syncwarp();
+    for (int k = 0; k < m; ++k) {
+        double best = -1.0;
+        int bi = k;
+        for (int i = k + lane; i < m; i += 32) {
+            const double a = abs1(A[i + (int64_t)m * k]);
+            if (a > best) {
+                best = a;
+                bi = i;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        if (lane == 0) pv[k] = bi;
+        if (bi != k)
+            for (int j = lane; j < m; j += 32) {
+                const zd t = A[k + (int64_t)m * j];
+                A[k + (int64_t)m * j] = A[bi + (int64_t)m * j];
+                A[bi + (int64_t)m * j] = t;
+            }
+        __syncwarp();
+        zd piv = A[k + (int64_t)m * k];
+        if (piv.re == 0.0 && piv.im == 0.0) piv = mk(tiny, 0.0);
+        const zd rp = cdiv(mk(1.0, 0.0), piv);
+        __syncwarp();
+        if (lane == 0) A[k + (int64_t)m * k] = piv;
+        for (int i = k + 1 + lane; i < m; i += 32) A[i + (int64_t)m * k] = A[i + (int64_t)m * k] * rp;
+        __syncwarp();
+        for (int i = k + 1 + lane; i < m; i += 32) {
+            const zd l = A[i + (int64_t)m * k];
+            for (int j = k + 1; j < m; ++j) A[i + (int64_t)m * j] = fms(A[i + (int64_t)m * j], l, A[k + (int64_t)m * j]);
+        }
+        __syncwarp();
+    }
+    const double inv_sqrt_m = 1.0 / sqrt((double)m);
+    for (int i = lane; i < m; i += 32) y[i] = mk(inv_sqrt_m, 0.0);
+    __syncwarp();
+    for (int it = 0; it < 3; ++it) {
+        for (int k = 0; k < m; ++k) {  // forward: the interchanges and the unit lower factor
+            const int p = pv[k];
+            if (p != k && lane == 0) {
+                const zd t = y[k];
+                y[k] = y[p];
+                y[p] = t;
+            }
+            __syncwarp();
+            const zd yk = y[k];
+            for (int i = k + 1 + lane; i < m; i += 32) y[i] = fms(y[i], A[i + (int64_t)m * k], yk);
+            __syncwarp();
+        }
+        for (int k = m - 1; k >= 0; --k) {  // backward with U, by columns
+            const zd yk = cdiv(y[k], A[k + (int64_t)m * k]);
+            __syncwarp();
+            if (lane == 0) y[k] = yk;
+            for (int i = lane; i < k; i += 32) y[i] = fms(y[i], A[i + (int64_t)m * k], yk);
+            __syncwarp();
+        }
+        double nn = 0.0;
+        for (int i = lane; i < m; i += 32) nn += norm2(y[i]);
+        for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+        const double sc = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+        for (int i = lane; i < m; i += 32) y[i] = sc * y[i];
+        __syncwarp();
+    }
+    zd rq = mk(0.0, 0.0);
+    for (int i = lane; i < m; i += 32) {
+        zd hs = mk(0.0, 0.0);
+        for (int j = 0; j < m; ++j) hs = fma_(hs, H[i + (int64_t)m * j], y[j]);
+        rq = fmac(rq, y[i], hs);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        rq.re += __shfl_xor_sync(0xffffffffu, rq.re, o);
+        rq.im += __shfl_xor_sync(0xffffffffu, rq.im, o);
+    }
+    for (int i = lane; i < m; i += 32) S[i + (int64_t)m * e] = y[i];
+    if (lane == 0 && isfinite(rq.re) && isfinite(rq.im)) theta[e] = rq;
+}
+
+// res[q] = |b^T s_q|, the residual estimate of the Ritz pair q (unit s_q): b is the row m of the
+// (m+1) x m matrix Hf (leading dimension ldh) of the decomposition S V_m = V_{m+1} Hf
+__global__ void ks_residual_kernel(int m, int ldh, const zd* __restrict__ Hf, const zd* __restrict__ S,
+                                   double* __restrict__ res) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= m) return;
+    zd acc = mk(0.0, 0.0);
+    for (int j = 0; j < m; ++j) acc = fma_(acc, Hf[m + (int64_t)ldh * j], S[j + (int64_t)m * q]);
+    res[q] = sqrt(norm2(acc));
+}
+
+// bn[j] = sum_i b_i Q[i, j] for j < p, b the row m of Hf; zero for the nlock locked columns, whose
+// coupling to the rest is dropped so that they stay an invariant subspace
+__global__ void ks_coupling_kernel(int m, int ldh, int p, int nlock, const zd* __restrict__ Hf,
+                                   const zd* __restrict__ Q, zd* __restrict__ bn) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= p) return;
+    zd acc = mk(0.0, 0.0);
+    if (j >= nlock)
+        for (int i = 0; i < m; ++i) acc = fma_(acc, Hf[m + (int64_t)ldh * i], Q[i + (int64_t)m * j]);
+    bn[j] = acc;
+}
+
+// row p of Hf (leading dimension ldh) = bn[0 .. p)
+__global__ void ks_set_row_kernel(int p, int ldh, const zd* __restrict__ bn, zd* __restrict__ Hf) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < p) Hf[p + (int64_t)ldh * j] = bn[j];
+}
+
+// A = M^H (rows x m, rows >= ncols, zero rows from ncols on): M is the m x ncols matrix whose
+// columns are the coefficient blocks g_k^i (column k d + i, leading dimension Mx)
+__global__ void ks_blocks_h_kernel(int m, int Mx, int ncols, int rows, const zd* __restrict__ G, zd* __restrict__ A) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)rows * m) return;
+    const int r = (int)(t % rows), q = (int)(t / rows);
+    A[t] = r < ncols ? conj(G[q + (int64_t)Mx * r]) : mk(0.0, 0.0);
+}
+
 // lam = shift + 1/theta; ok = theta != 0 and finite
 // lambda = shift + scale / theta for a Ritz value theta of S = (A - sigma B)^{-1} B
 __global__ void nleigs_ritz_kernel(int m, const zd* __restrict__ theta, zd shift, zd scale, zd* __restrict__ lam,
@@ -714,10 +863,11 @@ struct KrylovLin {
     zd sigma{}, lam_shift{}, lam_scale{};
 };
 static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, const double* start_host, zd c, double ea,
-                          double eb, double eig_tol, bool exact, NleigsOut* res, cudaStream_t st);
+                          double eb, double eig_tol, bool exact, const KsOpts& ks, NleigsOut* res, cudaStream_t st);
 
 int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, const double* start_host, zd c,
-               double ea, double eb, double eig_tol, bool exact, NleigsOut* res, cudaStream_t st, bool toar) {
+               double ea, double eb, double eig_tol, bool exact, NleigsOut* res, cudaStream_t st, bool toar,
+               const KsOpts& ks) {
     const int nt = s.nterms, d = it.d;
     if (nt > kNleigsMaxTerms || d < 1 || d > 63 || kmax < 1) return NEP_ERR_ARG;
     KrylovLin lin;
@@ -750,7 +900,7 @@ int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, co
         for (int j = 0; j <= d; ++j) acc += bs[j] * to_cd(it.dd[i + (size_t)nt * j]);
         lin.Fs[i] = to_zd(acc);
     }
-    return krylov_lin_run(s, lin, kmax, start_host, c, ea, eb, eig_tol, exact, res, st);
+    return krylov_lin_run(s, lin, kmax, start_host, c, ea, eb, eig_tol, exact, ks, res, st);
 }
 
 // Interpol (Sec. 4.4): the Chebyshev coefficients c (nt x (d+1), Eq. (polinterpcoef)) of the f_i on the
@@ -758,7 +908,7 @@ int nleigs_run(const SplitDev& s, const NleigsInterp& it, zd shift, int kmax, co
 // Arnoldi on the Chebyshev-basis linearisation of P_d with the shift sigma (in theta).
 int interpol_run(const SplitDev& s, const std::vector<zd>& c, int d, zd sigma, double alpha, double beta, int kmax,
                  const double* start_host, zd center, double ea, double eb, double eig_tol, bool exact, NleigsOut* res,
-                 cudaStream_t st) {
+                 cudaStream_t st, const KsOpts& ks) {
     const int nt = s.nterms;
     if (nt > kNleigsMaxTerms || d < 2 || d > 63 || kmax < 1) return NEP_ERR_ARG;
     KrylovLin lin;
@@ -782,11 +932,11 @@ int interpol_run(const SplitDev& s, const std::vector<zd>& c, int d, zd sigma, d
         for (int k = 0; k <= d; ++k) acc += tau[k] * to_cd(lin.coef[i + (size_t)nt * k]);
         lin.Fs[i] = to_zd(acc);
     }
-    return krylov_lin_run(s, lin, kmax, start_host, center, ea, eb, eig_tol, exact, res, st);
+    return krylov_lin_run(s, lin, kmax, start_host, center, ea, eb, eig_tol, exact, ks, res, st);
 }
 
 static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, const double* start_host, zd c, double ea,
-                          double eb, double eig_tol, bool exact, NleigsOut* res, cudaStream_t st) {
+                          double eb, double eig_tol, bool exact, const KsOpts& ks, NleigsOut* res, cudaStream_t st) {
     const int refine = exact ? kNleigsRefine : 0;
     const int n = s.n, nt = s.nterms, d = lin.d;
     const int64_t N = (int64_t)d * n;
@@ -798,7 +948,7 @@ static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, con
     // device arrays
     ExpandCoef* d_ec = nullptr;
     zd *d_ddc = nullptr, *d_F = nullptr, *tval = nullptr, *V = nullptr, *C = nullptr, *rhs = nullptr, *u = nullptr;
-    zd *res_r = nullptr, *Hm = nullptr, *hv = nullptr, *nr = nullptr, *part = nullptr, *hlast = nullptr;
+    zd *res_r = nullptr, *Hf = nullptr, *hv = nullptr, *nr = nullptr, *part = nullptr;
     zf *ab = nullptr, *ut = nullptr, *B32 = nullptr;
     double *tnorm = nullptr, *dmax = nullptr, *ymax = nullptr;
     int *ipiv = nullptr, *info = nullptr;
@@ -822,15 +972,15 @@ static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, con
     NEP_TRY(w.get(&B32, (size_t)n));
     NEP_TRY(w.get(&dmax, 1));
     NEP_TRY(w.get(&ymax, 1));
-    NEP_TRY(w.get(&Hm, (size_t)kmax * kmax));
+    const int ldh = kmax + 1;  // Hf: (kmax+1) x kmax, S V_k = V_{k+1} Hf[:k+1, :k]
+    NEP_TRY(w.get(&Hf, (size_t)ldh * kmax));
     NEP_TRY(w.get(&hv, (size_t)kmax + 1));
     NEP_TRY(w.get(&nr, 1));
-    NEP_TRY(w.get(&hlast, 1));
     NEP_TRY(w.get(&part, (size_t)std::max<int64_t>(nchunks, ((int64_t)d * (d + kmax) + chunk - 1) / chunk) * (kmax + 1)));
     NEP_CUDA(cudaMemcpyAsync(d_ec, &ec, sizeof(ec), cudaMemcpyHostToDevice, st));
     NEP_CUDA(cudaMemcpyAsync(d_ddc, ddc.data(), sizeof(zd) * ddc.size(), cudaMemcpyHostToDevice, st));
     NEP_CUDA(cudaMemcpyAsync(d_F, Fs.data(), sizeof(zd) * nt, cudaMemcpyHostToDevice, st));
-    NEP_CUDA(cudaMemsetAsync(Hm, 0, sizeof(zd) * (size_t)kmax * kmax, st));
+    NEP_CUDA(cudaMemsetAsync(Hf, 0, sizeof(zd) * (size_t)ldh * kmax, st));
     // R_d(shift) factored once in complex64, its FP64 values kept for the refinement residual
     NEP_TRY(launch_assemble<float>(s, 1, d_F, ab, tnorm, tval, st));
     NEP_TRY(launch_band_lu<float>(s, 1, ab, ipiv, info, nullptr, st));
@@ -880,7 +1030,6 @@ static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, con
     };
     // u (n) orthogonalised against the m columns of U twice into the column slot m of U; the
     // coefficients accumulate in hacc, rho = its remaining norm; returns whether U grew (not a breakdown)
-    double* host_pair = nullptr;  // ||u||^2, rho
     std::vector<double> hp(4, 0.0);
     auto extend = [&](const zd* u, int m, bool* grew) -> int {
         zd* col = U + (int64_t)m * n;
@@ -902,7 +1051,6 @@ static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, con
         *grew = hp[2] > 64 * 2.220446049250313e-16 * std::sqrt(std::max(hp[0], 0.0)) && hp[2] > 0.0;
         return NEP_OK;
     };
-    (void)host_pair;
     if (lin.toar) {
         NEP_TRY(w.get(&U, (size_t)n * (Mx + 1)));
         NEP_TRY(w.get(&Gc, (size_t)NG * (kmax + 1)));
@@ -928,7 +1076,18 @@ static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, con
         NEP_TRY(dots_g(Gc, 1, Gc, nr));
         nleigs_normalize_start_kernel<<<ceil_div(NG, 256), 256, 0, st>>>(NG, Gc, nr);
         NEP_CHECK_LAUNCH();
-        for (int k = 0; k < kmax; ++k) {
+    } else {
+        // start vector, unit 2-norm
+        NEP_CUDA(cudaMemcpyAsync(V, start_host, sizeof(zd) * (size_t)N, cudaMemcpyHostToDevice, st));
+        NEP_TRY(dots(V, 1, V, nr));
+        nleigs_normalize_start_kernel<<<ceil_div(N, 256), 256, 0, st>>>(N, V, nr);
+        NEP_CHECK_LAUNCH();
+    }
+    // Arnoldi step k: the next Krylov vector from vector k, orthogonalised against vectors 0 .. k
+    // into column k of Hf (its subdiagonal entry included)
+    auto step = [&](int k) -> int {
+        zd* Hcol = Hf + (int64_t)ldh * k;
+        if (lin.toar) {
             const zd* gk = Gc + (int64_t)k * NG;
             zd* gn = Gc + (int64_t)(k + 1) * NG;
             toar_coef_kernel<<<ceil_div(m_cur, 128), 128, 0, st>>>(d, m_cur, Mx, nt, gk, pt, Cc, d_ec, d_ddc);
@@ -944,23 +1103,16 @@ static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, con
             NEP_CHECK_LAUNCH();
             m_cur = mnew;
             // Arnoldi on the coefficient vectors, classical Gram-Schmidt twice
-            zd* Hcol = Hm + (int64_t)kmax * k;
             for (int pass = 0; pass < 2; ++pass) {
                 NEP_TRY(dots_g(Gc, k + 1, gn, hv));
                 nleigs_sub_kernel<<<ceil_div(NG, 256), 256, sizeof(zd) * (k + 1), st>>>(NG, k + 1, Gc, hv, gn, Hcol);
                 NEP_CHECK_LAUNCH();
             }
             NEP_TRY(dots_g(gn, 1, gn, nr));
-            nleigs_scale_kernel<<<ceil_div(NG, 256), 256, 0, st>>>(NG, gn, nr, k + 1 < kmax ? Hcol + k + 1 : hlast);
+            nleigs_scale_kernel<<<ceil_div(NG, 256), 256, 0, st>>>(NG, gn, nr, Hcol + k + 1);
             NEP_CHECK_LAUNCH();
+            return NEP_OK;
         }
-    } else {
-    // start vector, unit 2-norm
-    NEP_CUDA(cudaMemcpyAsync(V, start_host, sizeof(zd) * (size_t)N, cudaMemcpyHostToDevice, st));
-    NEP_TRY(dots(V, 1, V, nr));
-    nleigs_normalize_start_kernel<<<ceil_div(N, 256), 256, 0, st>>>(N, V, nr);
-    NEP_CHECK_LAUNCH();
-    for (int k = 0; k < kmax; ++k) {
         const zd* vk = V + (int64_t)k * N;
         zd* wk = V + (int64_t)(k + 1) * N;
         if (lin.kind == 0)
@@ -973,26 +1125,26 @@ static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, con
         NEP_TRY(solve());
         nleigs_combine_kernel<<<ceil_div(N, 256), 256, 0, st>>>(n, d, u, wk, d_ec);
         NEP_CHECK_LAUNCH();
-        zd* Hcol = Hm + (int64_t)kmax * k;
         for (int pass = 0; pass < 2; ++pass) {
             NEP_TRY(dots(V, k + 1, wk, hv));
             nleigs_sub_kernel<<<ceil_div(N, 256), 256, sizeof(zd) * (k + 1), st>>>(N, k + 1, V, hv, wk, Hcol);
             NEP_CHECK_LAUNCH();
         }
         NEP_TRY(dots(wk, 1, wk, nr));
-        nleigs_scale_kernel<<<ceil_div(N, 256), 256, 0, st>>>(N, wk, nr, k + 1 < kmax ? Hcol + k + 1 : hlast);
+        nleigs_scale_kernel<<<ceil_div(N, 256), 256, 0, st>>>(N, wk, nr, Hcol + k + 1);
         NEP_CHECK_LAUNCH();
-    }
-    }
-    // Ritz pairs of the kmax x kmax Hessenberg matrix
+        return NEP_OK;
+    };
+    // Ritz pairs of H = Hf[:m, :m] and the restart work arrays
     const int m = kmax;
-    zd *theta = nullptr, *S = nullptr, *lam = nullptr, *X = nullptr, *G = nullptr;
+    zd *theta = nullptr, *S = nullptr, *lam = nullptr, *X = nullptr, *G = nullptr, *Hc = nullptr;
     double* eta = nullptr;
     int *status = nullptr, *ok = nullptr, *order = nullptr;
     zd *gbuf = nullptr, *rwork = nullptr;
     int* rpiv = nullptr;
     NEP_TRY(w.get(&theta, m));
     NEP_TRY(w.get(&S, (size_t)m * m));
+    NEP_TRY(w.get(&Hc, (size_t)m * m));
     NEP_TRY(w.get(&lam, m));
     NEP_TRY(w.get(&X, (size_t)n * m));
     NEP_TRY(w.get(&G, (size_t)m * m));
@@ -1003,16 +1155,167 @@ static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, con
     NEP_TRY(w.get(&gbuf, (size_t)m * (m + 1) + m));  // complex64 elements fit twice over
     NEP_TRY(w.get(&rwork, (size_t)m * m * m));
     NEP_TRY(w.get(&rpiv, (size_t)m * m));
-    // Ritz values: complex64 Hessenberg QR, then FP64 inverse iteration and Rayleigh quotients
-    NEP_TRY(small_eig_fast<float>(m, Hm, theta, nullptr, status, gbuf, st));
-    nleigs_ritz_vectors_kernel<<<m, 32, sizeof(zd) * m, st>>>(m, Hm, theta, S, rwork, rpiv);
-    NEP_CHECK_LAUNCH();
+    double* kres = nullptr;
+    int* ksel = nullptr;
+    zd *Tq = nullptr, *Zq = nullptr, *sgbuf = nullptr, *bn = nullptr, *tmp = nullptr;
+    size_t tmp_elems = 0;
+    if (ks.max_restarts > 0) {
+        NEP_TRY(w.get(&kres, m));
+        NEP_TRY(w.get(&ksel, m));
+        NEP_TRY(w.get(&Tq, (size_t)m * m));
+        NEP_TRY(w.get(&Zq, (size_t)m * m));
+        NEP_TRY(w.get(&sgbuf, (size_t)2 * m * (m + 1) + m));
+        NEP_TRY(w.get(&bn, m));
+        const int64_t rows_max = lin.toar ? std::max<int64_t>(n, NG) : N;
+        tmp_elems = (size_t)std::min<int64_t>(rows_max * (lin.toar ? Mx : m), (int64_t)1 << 22);
+        tmp_elems = std::max<size_t>(tmp_elems, (size_t)(lin.toar ? Mx : m));
+        NEP_TRY(w.get(&tmp, tmp_elems));
+    }
+    // X[:, :kout] = X[:, :kin] Qm (rows x kin, leading dimension ld; Qm kin x kout, kout <= kin),
+    // in row chunks through tmp
+    auto right_mul = [&](zd* Xb, int64_t ld, int64_t rows, int kin, const zd* Qm, int kout) -> int {
+        const int64_t R = std::max<int64_t>(1, (int64_t)tmp_elems / kout);
+        for (int64_t r0 = 0; r0 < rows; r0 += R) {
+            const int rr = (int)std::min<int64_t>(R, rows - r0);
+            NEP_TRY(zgemm(rr, kout, kin, 0, Xb + r0, (int)ld, Qm, kin, tmp, rr, nullptr, 0, st));
+            NEP_CUDA(cudaMemcpy2DAsync(Xb + r0, sizeof(zd) * ld, tmp, sizeof(zd) * rr, sizeof(zd) * rr, kout,
+                                       cudaMemcpyDeviceToDevice, st));
+        }
+        return NEP_OK;
+    };
+    // the compact basis after a restart to p + 1 vectors: U <- U W_r and the coefficients <- W_r^H
+    // (coefficients), W_r the leading left singular vectors of the m_cur x d (p+1) matrix of all
+    // coefficient blocks (one-sided Jacobi on its conjugate transpose); singular values below
+    // rows * eps * sigma_1 are dropped, and at most d + p kept (the blocks of p + 1 vectors of a Krylov
+    // subspace span at most d + p directions, Sec. 4.5.3)
+    zd *Ah = nullptr, *Wj = nullptr, *Vmj = nullptr;
+    double* sgj = nullptr;
+    int *jflags = nullptr, *jsweeps = nullptr, *jerr = nullptr;
+    unsigned* jbar = nullptr;
+    auto compress = [&](int p) -> int {
+        const int ncols = d * (p + 1), rows = std::max(ncols, m_cur);
+        if (!Ah) {
+            const size_t rmax = (size_t)std::max(d * (kmax + 1), Mx);
+            NEP_TRY(w.get(&Ah, rmax * Mx));
+            NEP_TRY(w.get(&Wj, (size_t)Mx * Mx));
+            NEP_TRY(w.get(&Vmj, (size_t)Mx * Mx));
+            NEP_TRY(w.get(&sgj, (size_t)Mx));
+            NEP_TRY(w.get(&jflags, 2));
+            NEP_TRY(w.get(&jsweeps, 1));
+            NEP_TRY(w.get(&jerr, 1));
+            NEP_TRY(w.get(&jbar, 2));
+        }
+        NEP_CUDA(cudaMemsetAsync(jerr, 0, sizeof(int), st));
+        ks_blocks_h_kernel<<<ceil_div((int64_t)rows * m_cur, 256), 256, 0, st>>>(m_cur, Mx, ncols, rows, Gc, Ah);
+        NEP_CHECK_LAUNCH();
+        JacobiWork jw{Vmj, jflags, jsweeps, jbar, jerr};
+        NEP_TRY(jacobi_svd(rows, m_cur, Ah, nullptr, Wj, sgj, jw, st));
+        std::vector<double> sg(m_cur);
+        int jerr_h = 0;
+        NEP_CUDA(cudaMemcpyAsync(sg.data(), sgj, sizeof(double) * m_cur, cudaMemcpyDeviceToHost, st));
+        NEP_CUDA(cudaMemcpyAsync(&jerr_h, jerr, sizeof(int), cudaMemcpyDeviceToHost, st));
+        NEP_CUDA(cudaStreamSynchronize(st));
+        if (jerr_h) { set_error("nleigs: a bounded grid barrier timed out in the restart's SVD"); return NEP_ERR_INTERNAL; }
+        int r = 0;
+        while (r < m_cur && sg[r] > rows * 2.220446049250313e-16 * sg[0]) ++r;
+        r = std::max(1, std::min(r, d + p));
+        NEP_TRY(right_mul(U, n, n, m_cur, Wj, r));
+        NEP_TRY(zgemm(r, ncols, m_cur, 1, Wj, m_cur, Gc, Mx, Ah, r, nullptr, 0, st));
+        NEP_CUDA(cudaMemsetAsync(Gc, 0, sizeof(zd) * (size_t)ncols * Mx, st));
+        NEP_CUDA(cudaMemcpy2DAsync(Gc, sizeof(zd) * Mx, Ah, sizeof(zd) * r, sizeof(zd) * r, ncols,
+                                   cudaMemcpyDeviceToDevice, st));
+        m_cur = r;
+        return NEP_OK;
+    };
+    int k0 = 0, restarts = 0, total_steps = 0;
+    std::vector<zd> th_h(m);
+    std::vector<double> res_h(m);
+    for (;;) {
+        for (int k = k0; k < kmax; ++k) {
+            NEP_TRY(step(k));
+            ++total_steps;
+        }
+        // Ritz values: QR after a Hessenberg reduction, then FP64 inverse iteration and Rayleigh
+        // quotients (adjacent-row pivoting while H is still Hessenberg). Without restarts the QR runs
+        // in complex64; with them it is the FP64 Schur form H = Z T Z^H that the restart reorders (in
+        // FP64 also because the locked block's entries below the diagonal, zero up to rounding, can
+        // lie below 1e-20 |H|, whose squares FP32 cannot hold)
+        NEP_CUDA(cudaMemcpy2DAsync(Hc, sizeof(zd) * m, Hf, sizeof(zd) * ldh, sizeof(zd) * m, m,
+                                   cudaMemcpyDeviceToDevice, st));
+        if (ks.max_restarts > 0) NEP_TRY(launch_ks_schur(m, Hc, theta, Tq, Zq, status, sgbuf, st));
+        else NEP_TRY(small_eig_fast<float>(m, Hc, theta, nullptr, status, gbuf, st));
+        if (restarts == 0)
+            nleigs_ritz_vectors_kernel<<<m, 32, sizeof(zd) * m, st>>>(m, Hc, theta, S, rwork, rpiv);
+        else
+            ks_ritz_vectors_kernel<<<m, 32, sizeof(zd) * m, st>>>(m, Hc, theta, S, rwork, rpiv);
+        NEP_CHECK_LAUNCH();
+        if (restarts >= ks.max_restarts) break;
+        ks_residual_kernel<<<ceil_div(m, 128), 128, 0, st>>>(m, ldh, Hf, S, kres);
+        NEP_CHECK_LAUNCH();
+        NEP_CUDA(cudaMemcpyAsync(th_h.data(), theta, sizeof(zd) * m, cudaMemcpyDeviceToHost, st));
+        NEP_CUDA(cudaMemcpyAsync(res_h.data(), kres, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+        NEP_CUDA(cudaStreamSynchronize(st));
+        // wanted: lambda = lam_shift + lam_scale / theta strictly inside the region; converged:
+        // residual estimate |b^T s| <= tol |theta|
+        std::vector<int> conv, rest, others;
+        for (int q = 0; q < m; ++q) {
+            const cd t = to_cd(th_h[q]);
+            bool want = false;
+            if (std::abs(t) > 0.0 && std::isfinite(t.real()) && std::isfinite(t.imag())) {
+                const cd l = to_cd(lin.lam_shift) + to_cd(lin.lam_scale) / t;
+                const double dr = (l.real() - c.re) / ea, di = (l.imag() - c.im) / eb;
+                want = dr * dr + di * di < 1.0;
+            }
+            if (want && res_h[q] <= ks.tol * std::abs(t)) conv.push_back(q);
+            else if (want) rest.push_back(q);
+            else others.push_back(q);
+        }
+        if (ks.nev > 0 ? (int)conv.size() >= ks.nev : (conv.size() + rest.size() > 0 && rest.empty())) break;
+        auto by_size = [&](std::vector<int>& v) {
+            std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return std::abs(to_cd(th_h[a])) > std::abs(to_cd(th_h[b])); });
+        };
+        by_size(conv);
+        by_size(rest);
+        by_size(others);
+        const int nconv = (int)conv.size();
+        const int p = std::min(m - 1, std::max(ks.keep, nconv + 1));
+        std::vector<int> sel(conv);
+        sel.insert(sel.end(), rest.begin(), rest.end());
+        sel.insert(sel.end(), others.begin(), others.end());
+        sel.resize(p);
+        NEP_CUDA(cudaMemcpyAsync(ksel, sel.data(), sizeof(int) * p, cudaMemcpyHostToDevice, st));
+        // the kept Ritz values to the front of the Schur form: Q = Z[:, :p] spans their invariant
+        // subspace, H <- T[:p, :p] = Q^H H Q, the coupling row b^T Q with the locked entries zeroed
+        NEP_TRY(launch_ks_reorder(m, p, ksel, Tq, Zq, st));
+        const int pk = p, nlock = nconv;
+        const zd* Qk = Zq;
+        ks_coupling_kernel<<<ceil_div(pk, 128), 128, 0, st>>>(m, ldh, pk, nlock, Hf, Qk, bn);
+        NEP_CHECK_LAUNCH();
+        // basis: vectors 0 .. pk-1 <- V_m Q, vector pk <- vector m
+        if (lin.toar) {
+            NEP_TRY(right_mul(Gc, NG, NG, m, Qk, pk));
+            NEP_CUDA(cudaMemcpyAsync(Gc + (int64_t)pk * NG, Gc + (int64_t)m * NG, sizeof(zd) * NG,
+                                     cudaMemcpyDeviceToDevice, st));
+            NEP_TRY(compress(pk));
+        } else {
+            NEP_TRY(right_mul(V, N, N, m, Qk, pk));
+            NEP_CUDA(cudaMemcpyAsync(V + (int64_t)pk * N, V + (int64_t)m * N, sizeof(zd) * N,
+                                     cudaMemcpyDeviceToDevice, st));
+        }
+        NEP_CUDA(cudaMemsetAsync(Hf, 0, sizeof(zd) * (size_t)ldh * kmax, st));
+        NEP_CUDA(cudaMemcpy2DAsync(Hf, sizeof(zd) * ldh, Tq, sizeof(zd) * m, sizeof(zd) * pk, pk,
+                                   cudaMemcpyDeviceToDevice, st));
+        ks_set_row_kernel<<<ceil_div(pk, 128), 128, 0, st>>>(pk, ldh, bn, Hf);
+        NEP_CHECK_LAUNCH();
+        k0 = pk;
+        ++restarts;
+    }
     nleigs_ritz_kernel<<<ceil_div(m, 128), 128, 0, st>>>(m, theta, shift, lin.lam_scale, lam, ok);
     NEP_CHECK_LAUNCH();
     if (lin.toar) {
         // x = first block of the Ritz vector = U (G^0 S), G^0 the coordinates of block 0
         zd* Z = nullptr;
-        NEP_TRY(w.get(&Z, (size_t)m_cur * m));
+        NEP_TRY(w.get(&Z, (size_t)Mx * m));
         NEP_TRY(zgemm(m_cur, m, m, 0, Gc, (int)NG, S, m, Z, m_cur, nullptr, 0, st));
         NEP_TRY(zgemm(n, m, m_cur, 0, U, n, Z, m_cur, X, n, nullptr, 0, st));
     } else {
@@ -1081,7 +1384,8 @@ static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, con
     int info_h = 0;
     NEP_CUDA(cudaMemcpy(&info_h, info, sizeof(int), cudaMemcpyDeviceToHost));
     res->lu_info = info_h;
-    res->steps = kmax;
+    res->steps = total_steps;
+    res->restarts = restarts;
     return NEP_OK;
 }
 

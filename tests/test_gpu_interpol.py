@@ -79,3 +79,20 @@ def test_refusals(bnd):
     with pytest.raises(bnd.NepError) as e:
         bnd.interpol_solve(split, p.region, degree=64)
     assert e.value.code == bnd.NEP_ERR_ARG
+
+
+def test_coupled_delay_with_restarts(bnd):
+    """Krylov-Schur restarts (cycles of 40 restarted to 24 vectors, until as many pairs as the oracle
+    pencil has inside the region have converged) reach the oracle pencil's eigenvalues that one
+    120-step cycle reaches."""
+    torch_cuda()
+    p = synth.delay_2d(s=5, seed=3, center=-1.5, radius=1.5)
+    region = {"center": -1.5 + 0j, "a": 1.5, "b": 0.3}
+    d = 30
+    ora = interpol.solve(p, region, d)
+    split = bnd.Split.from_problem(p)
+    res = bnd.interpol_solve(split, region, degree=d, krylov=40, keep=24, max_restarts=30, nev=len(ora["lam"]))
+    assert res["info"]["restarts"] >= 1
+    assert len(res["lam"]) == len(ora["lam"])
+    err, _ = match_eigenvalues(res["lam"], ora["lam"])
+    assert err <= 1e-9

@@ -186,3 +186,79 @@ def test_compact_basis_equals_full_basis_at_full_size(bnd):
     assert len(a["lam"]) == len(b["lam"]) >= 5
     err, _ = match_eigenvalues(a["lam"], b["lam"])
     assert err <= 1e-10, err
+
+
+def _oracle_restarted(p, ncv, nkeep):
+    """The oracle's Krylov-Schur restart on the explicit S of the linearisation (shift: the centre)."""
+    it = nleigs.interpolation(p.fns, p.region)
+    sigma = complex(p.region["center"])
+    S = nleigs.shift_invert_dense(p, it, sigma)
+    rng = np.random.default_rng(3)
+    v0 = rng.standard_normal(S.shape[0]) + 1j * rng.standard_normal(S.shape[0])
+    wanted = lambda th: contour.inside(p.region, np.array([sigma + 1.0 / th]))[0]
+    r = nleigs.krylov_schur(S, v0, ncv=ncv, nkeep=nkeep, wanted=wanted, tol=1e-10, max_restarts=40)
+    assert r["restarts"] >= 1 and len(r["converged"]) == len(r["wanted"])
+    return np.array([sigma + 1.0 / r["theta"][q] for q in r["converged"]])
+
+
+@pytest.mark.parametrize("full_basis", [0, 1])
+def test_restarted_arnoldi_finds_what_the_oracle_restart_finds(bnd, full_basis):
+    """Krylov-Schur restarts with locking (Sec. 4.5.3): cycles of 40 steps restarted to 30 vectors
+    find every eigenvalue of the linearisation inside the region (23 of them), the set the oracle's
+    restarted Arnoldi on the explicit operator converges to; one cycle of 40 steps alone does not.
+    Both bases (n = 36 >= d: the compact basis is compressed at each restart)."""
+    torch_cuda()
+    p = synth.delay_2d(s=6, seed=1)
+    split = bnd.Split.from_problem(p)
+    lam_o = _oracle_restarted(p, 40, 30)
+    ref = nleigs.solve(p)["lam"]
+    assert len(lam_o) == len(ref) == 23
+    kw = dict(krylov=40, keep=30, max_restarts=40, restart_tol=1e-10, full_basis=full_basis)
+    r = bnd.nleigs_solve(split, p.region, exact_solves=1, **kw)
+    assert 1 <= r["info"]["restarts"] <= 40
+    assert r["info"]["krylov_steps"] > 40
+    assert len(r["lam"]) == len(lam_o), (len(r["lam"]), len(lam_o))
+    err, pairs = match_eigenvalues(r["lam"], lam_o)
+    assert err <= 1e-10, err
+    assert r["eta"].max() <= 1e-10  # the pairs converged to |b^T s| <= 1e-10 |theta|
+    # complex64 solves (convergence at 1e-6, then the polish) give the same eigenvalues
+    kw["restart_tol"] = 0.0
+    f = bnd.nleigs_solve(split, p.region, **kw)
+    assert len(f["lam"]) == len(lam_o)
+    err, _ = match_eigenvalues(f["lam"], lam_o)
+    assert err <= 1e-10, err
+    one = bnd.nleigs_solve(split, p.region, krylov=40, exact_solves=1, full_basis=full_basis)
+    assert one["info"]["restarts"] == 0 and one["info"]["krylov_steps"] == 40
+    assert len(one["lam"]) < len(lam_o)
+
+
+def test_restarted_compact_basis_at_full_size(bnd):
+    """n = 4096: cycles of 40 steps restarted to 20 vectors give the contour solver's eigenvalues
+    (FP64 plan) and the same set as one 100-step cycle."""
+    torch = torch_cuda()
+    from tests.gpu_util import to_dev
+    p = synth.config_problem("delay2d_s64")
+    split = bnd.Split.from_problem(p)
+    plan = bnd.Plan(split, p.region, p.N, p.L, p.M, precision=0)
+    plan.execute(to_dev(np.asfortranarray(synth.random_probe_block(p.n, p.L, 0)), torch))
+    torch.cuda.synchronize()
+    rc = plan.result()
+    r = bnd.nleigs_solve(split, p.region, krylov=40, keep=20, max_restarts=30)
+    assert r["info"]["restarts"] >= 1
+    assert len(r["lam"]) == len(rc["lam"]) >= 5, (len(r["lam"]), len(rc["lam"]))
+    err, _ = match_eigenvalues(r["lam"], rc["lam"])
+    assert err <= 1e-9, err
+    norms = ciss.term_norms_inf(p.mats)
+    for q in range(len(r["lam"])):
+        assert ciss.scaled_residual(p.mats, p.fns, norms, r["lam"][q], r["X"][:, q]) <= 1e-11
+
+
+def test_restart_option_refusals(bnd):
+    torch_cuda()
+    p = synth.diagonal_delay(n=8, seed=0)
+    split = bnd.Split.from_problem(p)
+    for kw in (dict(krylov=20, keep=20, max_restarts=3), dict(krylov=20, max_restarts=-1),
+               dict(krylov=1, max_restarts=2)):
+        with pytest.raises(bnd.NepError) as e:
+            bnd.nleigs_solve(split, p.region, **kw)
+        assert e.value.code == bnd.NEP_ERR_ARG

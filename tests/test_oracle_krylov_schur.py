@@ -68,3 +68,15 @@ def test_planted_unorthonormalised_restart_caught(monkeypatch):
     bad_orth = np.abs(V.conj().T @ V - np.eye(k + 1)).max()
     bad_rel = np.abs(S @ V[:, :k] - V @ Hf).max() / np.abs(S).max()
     assert bad_orth > 1e-6 or bad_rel > 1e-6
+
+
+def test_nev_stops_once_that_many_wanted_pairs_converged():
+    """With nev set, the run ends once nev wanted pairs have converged: nev = 3 stops earlier than
+    the default (all wanted pairs), and its converged pairs are Lambert W eigenvalues."""
+    p, S, v0, sigma, wanted = _setup()
+    ref = lambert_reference(p)
+    few = nleigs.krylov_schur(S, v0, ncv=24, nkeep=14, wanted=wanted, tol=1e-12, max_restarts=40, nev=3)
+    full = nleigs.krylov_schur(S, v0, ncv=24, nkeep=14, wanted=wanted, tol=1e-12, max_restarts=40)
+    assert len(few["converged"]) >= 3 and few["restarts"] <= full["restarts"]
+    for e in _eigs(few, sigma):
+        assert np.min(np.abs(np.array(ref) - e)) <= 1e-10 * max(1.0, abs(e))

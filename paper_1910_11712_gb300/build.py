@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnepciss.so")
-SOURCES = ["assemble.cu", "band_lu.cu", "band_sweep_f.cu", "band_sweep_d.cu", "lu_wide.cu", "lu_tc.cu", "lu_col.cu", "polish.cu", "left.cu", "nleigs.cu", "spmv.cu", "moments.cu", "extract.cu", "host_api.cu", "server.cu", "noalloc.cu"]
+SOURCES = ["assemble.cu", "band_lu.cu", "band_sweep_f.cu", "band_sweep_d.cu", "lu_wide.cu", "lu_tc.cu", "lu_col.cu", "band_solve_blocked.cu", "polish.cu", "left.cu", "nleigs.cu", "spmv.cu", "moments.cu", "extract.cu", "host_api.cu", "server.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

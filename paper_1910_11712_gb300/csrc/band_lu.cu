@@ -21,6 +21,7 @@
 // Three implementations share this elimination and its stored factors: lu_col.cu (register
 // window, kl <= 64 and kl + ku <= 128), lu_wide.cu (blocked, wider bands) and lu_glb_kernel
 // below, which keeps the window in a global (L2-resident) scratch array for bands beyond both.
+#include <cstdlib>
 #include "band_util.cuh"
 
 namespace nep {
@@ -419,6 +420,17 @@ int launch_band_solve(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>*
     // register windows for narrow bands (kl+1 <= 288 and kv+1 <= 288 rows): two sweeps with
     // slot-ordered coefficients
     if (band_sweeps_fit(s.kl, s.ku)) return band_sweeps<T>(s, npts, ab, ut, ipiv, L, B, active, st, rh_force);
+    // complex64 factors: blocked substitution (NEP_SOLVE_UNBLOCKED=1 keeps the per-step sweeps below)
+    if constexpr (sizeof(T) == 4) {
+        static const bool unblocked = [] {
+            const char* e = std::getenv("NEP_SOLVE_UNBLOCKED");
+            return e && e[0] == '1';
+        }();
+        if (!unblocked) {
+            const int rc = launch_band_solve_blocked(s, npts, ab, ipiv, L, B, active, st);
+            if (rc != NEP_ERR_UNSUPPORTED) return rc;
+        }
+    }
     // general path: shared-memory windows, one right-hand side per warp, four warps per CTA
     constexpr int RH = 1;
     const int warps_total = L;

@@ -289,6 +289,11 @@ int launch_band_lu(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info,
                    int lu_kernel = LU_AUTO);
 // Narrow-band substitution sweeps (register windows of kl+1 and kl+ku+1 rows, up to 288).
 inline bool band_sweeps_fit(int kl, int ku) { return kl >= 1 && kl + 1 <= 288 && kl + ku + 1 <= 288; }
+// band_solve_blocked.cu: the blocked substitution for complex64 factors of wider bands (NB-step
+// blocks, products for the rows beyond each block); NEP_ERR_UNSUPPORTED when its windows do not fit
+int band_solve_blocked_rhs(int kl, int ku, int L);
+int launch_band_solve_blocked(const SplitDev& s, int npts, const zf* ab, const int* ipiv, int L, zf* B,
+                              const int* active, cudaStream_t st);
 // ut (npts x n x (kl+ku+1)): the U factor by columns, written by band_transpose_u after the LU.
 template <typename T>
 int band_sweeps(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* ut, const int* ipiv, int L, cx<T>* B,

@@ -298,3 +298,42 @@ def test_small_eig_matches_lapack(bnd, m):
     for i in range(m):
         v = Vv[:, i]
         assert np.linalg.norm(A @ v - lam[i] * v) <= 1e-10 * np.linalg.norm(v) * max(1.0, np.linalg.norm(A, 2))
+
+
+@pytest.mark.parametrize("n,kl,ku,L", [(403, 150, 150, 5), (320, 300, 10, 3), (517, 300, 40, 20), (400, 20, 300, 17),
+                                       (1000, 576, 576, 24), (45, 0, 0, 4), (50, 0, 6, 3)])
+def test_blocked_band_solve_matches_oracle(bnd, n, kl, ku, L):
+    """The blocked complex64 substitution for bands beyond the register-window sweeps (16-step blocks):
+    n not a multiple of the block, n below the backward window, several CTAs per point (L > 16), kl much
+    larger or smaller than ku, the bandwidth-576 shape, and bands narrower than a block (kl = 0); the
+    oracle's dense FP64 solve."""
+    torch = torch_cuda()
+    p = _random_band_problem(n, kl, ku, n + kl)
+    split = bnd.Split.from_problem(p)
+    assert (split.kl, split.ku) == (kl, ku)
+    assert kl == 0 or not (kl + 1 <= 288 and kl + ku + 1 <= 288)  # kl = 0: never the register sweeps
+    npts = 2
+    z = _points(p, npts)
+    F, _ = bnd.coefficients(split, z)
+    ab = torch.zeros(npts * n * split.ldab * 2, dtype=torch.float32, device="cuda")
+    bnd.assemble_band(split, npts, to_dev(np.asfortranarray(F), torch), 1, ab)
+    ipiv = torch.zeros(npts * n, dtype=torch.int32, device="cuda")
+    info = torch.zeros(npts, dtype=torch.int32, device="cuda")
+    bnd.band_factor(split, npts, 1, ab, ipiv, info)
+    assert not info.cpu().numpy().any()
+    piv = ipiv.cpu().numpy().reshape(npts, n)
+    if kl > 0:
+        assert (piv != np.arange(n)).sum() > n // 4  # row interchanges are exercised
+    V = synth.random_probe_block(n, L, seed=12)
+    Vrep = np.concatenate([np.asfortranarray(V).ravel(order="F")] * npts)
+    B = torch.from_numpy(Vrep.astype(np.complex64).view(np.float32).copy()).cuda()
+    bnd.band_solve(split, npts, 1, ab, ipiv, L, B)
+    torch.cuda.synchronize()
+    Xg = from_dev_c64(B).astype(np.complex128).reshape(npts, L, n)
+    Fo = contour.coefficient_table(p.fns, z)
+    for j in range(npts):
+        T = band.assemble_dense(p.mats, Fo[:, j])
+        Xo = np.linalg.solve(T, V)
+        err = np.abs(Xg[j].T - Xo).max() / np.abs(Xo).max()
+        cond = np.linalg.cond(T)
+        assert err <= max(5e-6 * cond, 1e-12), (err, cond)

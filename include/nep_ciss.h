@@ -420,9 +420,10 @@ int nep_nleigs_interpolation_fns(int32_t nterms, const nep_fn *f, const nep_regi
  * first, then wanted, then the others, each nearest the shift first), Q = the leading p Schur vectors
  * of H after the FP64 Schur form is reordered to put those first, plus the last Arnoldi vector; H
  * becomes the leading p x p block of the reordered Schur factor with the coupling row b^T Q, whose
- * entries for the converged (locked) vectors are zeroed, and the compact basis is compressed to the
- * leading left singular vectors of its coefficient blocks (U <- U W, one-sided Jacobi SVD, at most
- * d + kept vectors); the Arnoldi continues from there; pairs inside the region with FP64 eta (Sec. 2 Eq. (sressplit), of the full T) at most
+ * entries for the converged (locked) vectors are zeroed, and the compact basis is compressed to an
+ * orthonormal basis W of the range of its coefficient blocks (U <- U W; QR with column pivoting
+ * stopped at a relative Frobenius mass of 1e-13, at most d + kept vectors); the Arnoldi continues
+ * from there. Pairs inside the region with FP64 eta (Sec. 2 Eq. (sressplit), of the full T) at most
  * eig_tol are returned, deduplicated and sorted as nep_ciss_solve does. *out receives a result
  * object (nep_result_get; hankel_rank there is 0; flags NEP_WARN_INTERP if the degree test failed
  * at max_degree, NEP_WARN_SINGULAR_NODE if R_d(sigma) had an exactly zero pivot); *degree (or NULL)

@@ -630,6 +630,14 @@ __global__ void apply_q_kernel(int rows, int nref, const zd* __restrict__ A, con
     }
 }
 
+// Q (rows x r) = the first r columns of the identity
+__global__ void eye_cols_kernel(int rows, int r, zd* __restrict__ Q) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)rows * r) return;
+    const int i = (int)(t % rows), c = (int)(t / rows);
+    Q[t] = mk(i == c ? 1.0 : 0.0, 0.0);
+}
+
 // W(perm[i], c) = Uj(i, c)
 __global__ void permute_rows_kernel(int n, int ncols, const int* __restrict__ perm, const zd* __restrict__ Uj,
                                     zd* __restrict__ W) {
@@ -678,6 +686,44 @@ int qrcp_jacobi_svd(int n, zd* A, zd* U, zd* W, double* sigma, zd* work1, zd* wo
         permute_rows_kernel<<<ceil_div((int64_t)n * mq, 256), 256, 0, st>>>(n, mq, perm, work2, W);
         NEP_CHECK_LAUNCH();
     }
+    return NEP_OK;
+}
+
+// An orthonormal basis of the range of A (rows x cols, column-major, overwritten): Householder QR
+// with column pivoting (qrcp_kernel), stopped once the remaining columns' squared Frobenius mass is
+// at most trunc^2 |R_00|^2; r = min(its steps, rmax) (at least 1) and Q (rows x r) = H_0 ... H_{r-1}
+// applied to the first r columns of the identity. tau: min(rows, cols); perm, nrm2: cols.
+int qr_range_basis(int rows, int cols, zd* A, zd* Q, int rmax, double trunc, zd* tau, int* perm, double* nrm2,
+                   int* steps_dev, unsigned* bar, int* err, int* r_out, cudaStream_t st) {
+    *r_out = 0;
+    if (rows <= 0 || cols <= 0) return NEP_OK;
+    NEP_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
+    NEP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    int dev = 0, sms = 0;
+    NEP_CUDA(cudaGetDevice(&dev));
+    NEP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int per_sm = 0;
+    NEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qrcp_kernel, 32, 0));
+    int blocks = std::max(1, std::min(cols, sms * std::max(per_sm, 1)));
+    GridBar gb{bar, bar + 1, err, wait_limit()};
+    double stop2 = trunc * trunc;
+    void* args[] = {&rows, &cols, &A, &tau, &perm, &nrm2, &stop2, &steps_dev, &gb};
+    NEP_CUDA(cudaLaunchCooperativeKernel((const void*)qrcp_kernel, dim3(blocks), dim3(32), args, 0, st));
+    count_launch();
+    int steps = 0, e = 0;
+    NEP_CUDA(cudaMemcpyAsync(&steps, steps_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NEP_CUDA(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NEP_CUDA(cudaStreamSynchronize(st));
+    if (e) {
+        set_error("qr_range_basis: a bounded grid barrier timed out");
+        return NEP_ERR_INTERNAL;
+    }
+    const int r = std::max(1, std::min(std::min(steps, rmax), std::min(rows, cols)));
+    eye_cols_kernel<<<ceil_div((int64_t)rows * r, 256), 256, 0, st>>>(rows, r, Q);
+    NEP_CHECK_LAUNCH();
+    apply_q_kernel<<<ceil_div(r, 4), 128, 0, st>>>(rows, r, A, tau, r, Q);
+    NEP_CHECK_LAUNCH();
+    *r_out = r;
     return NEP_OK;
 }
 
@@ -804,59 +850,73 @@ __device__ void givens(cx<T> x, cx<T> y, T* c, cx<T>* s) {
     *s = (T(1) / nrm) * (ph * conj(y));
 }
 
-// The Schur form of the m x m matrix in H (one warp, leading dimension ld): H <- Z^H H Z upper
-// triangular, Z accumulating the transformations (Z must hold I, or a unitary to be updated, on
-// entry); v is m scratch elements. Returns 1 if the QR iteration hit its sweep limit.
+// The Schur form of the m x m matrix in H (one CTA of blockDim.x threads, a multiple of 32;
+// leading dimension ld): H <- Z^H H Z upper triangular, Z accumulating the transformations (Z must
+// hold I, or a unitary to be updated, on entry); v is m scratch elements, red blockDim.x / 32
+// (unused with one warp). Returns 1 if the QR iteration hit its sweep limit. With several warps
+// the rotations' row, column and Z updates spread over them (FP64 issues slowly on one warp).
 template <typename T>
-__device__ int schur_form(int m, cx<T>* H, cx<T>* Z, cx<T>* v, int ld) {
-    const int lane = threadIdx.x & 31;
+__device__ int schur_form(int m, cx<T>* H, cx<T>* Z, cx<T>* v, int ld, T* red) {
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, nw = nthr >> 5;
+    const int tz = (tid + nthr / 2) % nthr;  // Z rows go to the other half of the threads
     const T eps = sizeof(T) == 4 ? T(6e-8) : T(1.2e-16);
     auto h = [&](int i, int j) -> cx<T>& { return H[i + (int64_t)ld * j]; };
     auto z = [&](int i, int j) -> cx<T>& { return Z[i + (int64_t)ld * j]; };
+    auto sync = [&]() {
+        if (nw > 1) __syncthreads();
+        else __syncwarp();
+    };
+    auto bsum = [&](T x) -> T {
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (nw == 1) return x;
+        if (lane == 0) red[tid >> 5] = x;
+        __syncthreads();
+        T t = 0;
+        for (int w = 0; w < nw; ++w) t += red[w];
+        __syncthreads();
+        return t;
+    };
     // Hessenberg reduction
     for (int k = 0; k + 2 < m; ++k) {
         T nx = 0;
-        for (int i = k + 1 + lane; i < m; i += 32) nx += norm2(h(i, k));
-        for (int o = 16; o > 0; o >>= 1) nx += __shfl_xor_sync(0xffffffffu, nx, o);
-        nx = sqrt(nx);
+        for (int i = k + 1 + tid; i < m; i += nthr) nx += norm2(h(i, k));
+        nx = sqrt(bsum(nx));
         if (nx == T(0)) continue;
         const cx<T> x0 = h(k + 1, k);
         const T a0 = hypot(x0.re, x0.im);
         const cx<T> ph = a0 > 0 ? mk<T>(x0.re / a0, x0.im / a0) : mk<T>(1, 0);
         // v = x + ph*|x| e1, reflector I - 2 v v^H / (v^H v)
-        for (int i = k + 1 + lane; i < m; i += 32) v[i] = h(i, k);
-        __syncwarp();
-        if (lane == 0) v[k + 1] = v[k + 1] + nx * ph;
-        __syncwarp();
+        for (int i = k + 1 + tid; i < m; i += nthr) v[i] = h(i, k);
+        sync();
+        if (tid == 0) v[k + 1] = v[k + 1] + nx * ph;
+        sync();
         T vv = 0;
-        for (int i = k + 1 + lane; i < m; i += 32) vv += norm2(v[i]);
-        for (int o = 16; o > 0; o >>= 1) vv += __shfl_xor_sync(0xffffffffu, vv, o);
-        const T sc = T(2) / vv;
-        // left: rows k+1.., columns k..m-1 (lanes over columns)
-        for (int j = k + lane; j < m; j += 32) {
+        for (int i = k + 1 + tid; i < m; i += nthr) vv += norm2(v[i]);
+        const T sc = T(2) / bsum(vv);
+        // left: rows k+1.., columns k..m-1 (threads over columns)
+        for (int j = k + tid; j < m; j += nthr) {
             cx<T> s = mk<T>(0, 0);
             for (int i = k + 1; i < m; ++i) s = fmac(s, v[i], h(i, j));
             s = sc * s;
             for (int i = k + 1; i < m; ++i) h(i, j) = fms(h(i, j), v[i], s);
         }
-        __syncwarp();
-        // right: columns k+1.., all rows (lanes over rows), also Z
-        for (int i = lane; i < m; i += 32) {
-            cx<T> s = mk<T>(0, 0), sz = mk<T>(0, 0);
-            for (int j = k + 1; j < m; ++j) {
-                s = fma_(s, h(i, j), v[j]);
-                sz = fma_(sz, z(i, j), v[j]);
-            }
+        sync();
+        // right: columns k+1.., all rows (threads over rows), and Z
+        for (int i = tid; i < m; i += nthr) {
+            cx<T> s = mk<T>(0, 0);
+            for (int j = k + 1; j < m; ++j) s = fma_(s, h(i, j), v[j]);
             s = sc * s;
-            sz = sc * sz;
-            for (int j = k + 1; j < m; ++j) {
-                h(i, j) = fms(h(i, j), s, conj(v[j]));
-                z(i, j) = fms(z(i, j), sz, conj(v[j]));
-            }
+            for (int j = k + 1; j < m; ++j) h(i, j) = fms(h(i, j), s, conj(v[j]));
         }
-        __syncwarp();
-        for (int i = k + 2 + lane; i < m; i += 32) h(i, k) = mk<T>(0, 0);
-        __syncwarp();
+        for (int i = tz; i < m; i += nthr) {
+            cx<T> sz = mk<T>(0, 0);
+            for (int j = k + 1; j < m; ++j) sz = fma_(sz, z(i, j), v[j]);
+            sz = sc * sz;
+            for (int j = k + 1; j < m; ++j) z(i, j) = fms(z(i, j), sz, conj(v[j]));
+        }
+        sync();
+        for (int i = k + 2 + tid; i < m; i += nthr) h(i, k) = mk<T>(0, 0);
+        sync();
     }
     // shifted QR
     int ihi = m - 1, iter = 0, since = 0, fail = 0;
@@ -870,10 +930,10 @@ __device__ int schur_form(int m, cx<T>* H, cx<T>* Z, cx<T>* v, int ld) {
             if (abs1(sub) <= eps * (ref > 0 ? ref : T(1))) break;
             --l;
         }
-        __syncwarp();
+        sync();
         if (l > 0) {
-            if (lane == 0) h(l, l - 1) = mk<T>(0, 0);
-            __syncwarp();
+            if (tid == 0) h(l, l - 1) = mk<T>(0, 0);
+            sync();
         }
         if (l == ihi) {
             --ihi;
@@ -898,32 +958,32 @@ __device__ int schur_form(int m, cx<T>* H, cx<T>* Z, cx<T>* v, int ld) {
             cx<T> sn;
             givens(x, y, &cs, &sn);
             // rows k, k+1 from column max(l, k-1) to m-1
-            for (int j = max(l, k - 1) + lane; j < m; j += 32) {
+            for (int j = max(l, k - 1) + tid; j < m; j += nthr) {
                 const cx<T> p = h(k, j), q = h(k + 1, j);
                 h(k, j) = cs * p + sn * q;
                 h(k + 1, j) = cs * q - conj(sn) * p;
             }
-            __syncwarp();
+            sync();
             // columns k, k+1 for rows 0..min(k+2, ihi); Z all rows
             const int rlim = min(k + 2, ihi);
-            for (int i = lane; i <= rlim; i += 32) {
+            for (int i = tid; i <= rlim; i += nthr) {
                 const cx<T> p = h(i, k), q = h(i, k + 1);
                 h(i, k) = cs * p + conj(sn) * q;
                 h(i, k + 1) = cs * q - sn * p;
             }
-            for (int i = lane; i < m; i += 32) {
+            for (int i = tz; i < m; i += nthr) {
                 const cx<T> p = z(i, k), q = z(i, k + 1);
                 z(i, k) = cs * p + conj(sn) * q;
                 z(i, k + 1) = cs * q - sn * p;
             }
-            __syncwarp();
+            sync();
             if (k + 1 < ihi) {
                 x = h(k + 1, k);
                 y = h(k + 2, k);
             }
         }
     }
-    __syncwarp();
+    sync();
     return fail;
 }
 
@@ -945,7 +1005,7 @@ __global__ void schur_eig_kernel(int m, const zd* __restrict__ Ain, zd* __restri
         z(i, j) = mk<T>(i == j ? T(1) : T(0), T(0));
     }
     __syncwarp();
-    const int fail = schur_form<T>(m, H, Z, v, ld);
+    const int fail = schur_form<T>(m, H, Z, v, ld, (T*)nullptr);
     __syncwarp();
     for (int i = lane; i < m; i += 32) eval[i] = cvt<double>(h(i, i));
     if (lane == 0 && status) *status = fail;
@@ -997,30 +1057,33 @@ template int small_eig<float>(int, const zd*, zd*, zd*, int*, void*, cudaStream_
 template int small_eig<double>(int, const zd*, zd*, zd*, int*, void*, cudaStream_t);
 
 // ------------------------------------------------------------------ Krylov-Schur restart
-// The FP64 Schur form H = Z T Z^H of an m x m matrix (one warp): eval = diag(T), T (upper
-// triangular) and Z written with leading dimension m. gbuf (2 m (m+1) + m complex128) is used when
-// shared memory is too small.
-__global__ void ks_schur_kernel(int m, const zd* __restrict__ A, zd* __restrict__ eval, zd* __restrict__ Tout,
-                                zd* __restrict__ Zout, int* __restrict__ status, zd* gbuf, int use_smem) {
+// The FP64 Schur form H = Z T Z^H of an m x m matrix (one CTA of kKsSchurThreads): eval = diag(T),
+// T (upper triangular) and Z written with leading dimension m. gbuf (2 m (m+1) + m complex128) is
+// used when shared memory is too small.
+constexpr int kKsSchurThreads = 128;
+__global__ void __launch_bounds__(kKsSchurThreads) ks_schur_kernel(int m, const zd* __restrict__ A, zd* __restrict__ eval,
+                                                                  zd* __restrict__ Tout, zd* __restrict__ Zout,
+                                                                  int* __restrict__ status, zd* gbuf, int use_smem) {
     extern __shared__ unsigned char sraw[];
-    const int ld = m + 1, lane = threadIdx.x;
+    __shared__ double red[kKsSchurThreads / 32];
+    const int ld = m + 1, tid = threadIdx.x, nthr = blockDim.x;
     zd* H = use_smem ? reinterpret_cast<zd*>(sraw) : gbuf;
     zd* Z = H + (int64_t)m * ld;
     zd* v = Z + (int64_t)m * ld;
-    for (int t = lane; t < m * m; t += 32) {
+    for (int t = tid; t < m * m; t += nthr) {
         const int i = t % m, j = t / m;
         H[i + (int64_t)ld * j] = A[t];
         Z[i + (int64_t)ld * j] = mk(i == j ? 1.0 : 0.0, 0.0);
     }
-    __syncwarp();
-    const int fail = schur_form<double>(m, H, Z, v, ld);
-    for (int t = lane; t < m * m; t += 32) {
+    __syncthreads();
+    const int fail = schur_form<double>(m, H, Z, v, ld, red);
+    for (int t = tid; t < m * m; t += nthr) {
         const int i = t % m, j = t / m;
         Tout[t] = i <= j ? H[i + (int64_t)ld * j] : mk(0.0, 0.0);
         Zout[t] = Z[i + (int64_t)ld * j];
     }
-    for (int i = lane; i < m; i += 32) eval[i] = H[i + (int64_t)ld * i];
-    if (lane == 0 && status) *status = fail;
+    for (int i = tid; i < m; i += nthr) eval[i] = H[i + (int64_t)ld * i];
+    if (tid == 0 && status) *status = fail;
 }
 
 // Reorders the Schur form (T, Z, leading dimension m) so that the diagonal entries that stood at
@@ -1087,7 +1150,7 @@ int launch_ks_schur(int m, const zd* A, zd* eval, zd* T, zd* Z, int* status, zd*
     const int use_smem = bytes <= 200 * 1024;
     if (use_smem) NEP_CUDA(allow_max_dynamic_smem(ks_schur_kernel));
     else if (!gbuf) return NEP_ERR_INTERNAL;
-    ks_schur_kernel<<<1, 32, use_smem ? bytes : 0, st>>>(m, A, eval, T, Z, status, gbuf, use_smem);
+    ks_schur_kernel<<<1, kKsSchurThreads, use_smem ? bytes : 0, st>>>(m, A, eval, T, Z, status, gbuf, use_smem);
     NEP_CHECK_LAUNCH();
     return NEP_OK;
 }

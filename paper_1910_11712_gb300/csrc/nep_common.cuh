@@ -350,6 +350,10 @@ int small_eig_fast(int m, const zd* A, zd* eval, zd* evec, int* status, void* gb
 // at positions sel[0 .. p) to the front in that order
 int launch_ks_schur(int m, const zd* A, zd* eval, zd* T, zd* Z, int* status, zd* gbuf, cudaStream_t st);
 int launch_ks_reorder(int m, int p, const int* sel, zd* T, zd* Z, cudaStream_t st);
+// an orthonormal basis Q (rows x r) of the range of A (rows x cols, overwritten) by QR with column
+// pivoting, stopped at a relative Frobenius mass trunc; r <= rmax
+int qr_range_basis(int rows, int cols, zd* A, zd* Q, int rmax, double trunc, zd* tau, int* perm, double* nrm2,
+                   int* steps_dev, unsigned* bar, int* err, int* r_out, cudaStream_t st);
 // complex128-sized elements of one Newton candidate's work area (FP32 Jacobian + FP64 iterate)
 size_t newton_scratch_bytes(int k, int nterms);
 int launch_pchol(int m, const zd* G, double tol2, int* rank_out, zd* Z, zd* gwork, cudaStream_t st);

@@ -1183,46 +1183,37 @@ static int krylov_lin_run(const SplitDev& s, const KrylovLin& lin, int kmax, con
         }
         return NEP_OK;
     };
-    // the compact basis after a restart to p + 1 vectors: U <- U W_r and the coefficients <- W_r^H
-    // (coefficients), W_r the leading left singular vectors of the m_cur x d (p+1) matrix of all
-    // coefficient blocks (one-sided Jacobi on its conjugate transpose); singular values below
-    // rows * eps * sigma_1 are dropped, and at most d + p kept (the blocks of p + 1 vectors of a Krylov
-    // subspace span at most d + p directions, Sec. 4.5.3)
-    zd *Ah = nullptr, *Wj = nullptr, *Vmj = nullptr;
-    double* sgj = nullptr;
-    int *jflags = nullptr, *jsweeps = nullptr, *jerr = nullptr;
-    unsigned* jbar = nullptr;
+    // the compact basis after a restart to p + 1 vectors: U <- U Q_r and the coefficients <- Q_r^H
+    // (coefficients), Q_r an orthonormal basis of the range of the m_cur x d (p+1) matrix of all
+    // coefficient blocks, from QR with column pivoting stopped at a relative Frobenius mass of 1e-13;
+    // at most d + p columns are kept (the blocks of p + 1 vectors of a Krylov subspace span at most
+    // d + p directions, Sec. 4.5.3)
+    zd *Ac = nullptr, *Gt = nullptr, *Qr = nullptr, *qtau = nullptr;
+    double* qn2 = nullptr;
+    int *qperm = nullptr, *qsteps = nullptr, *qerr = nullptr;
+    unsigned* qbar = nullptr;
     auto compress = [&](int p) -> int {
-        const int ncols = d * (p + 1), rows = std::max(ncols, m_cur);
-        if (!Ah) {
-            const size_t rmax = (size_t)std::max(d * (kmax + 1), Mx);
-            NEP_TRY(w.get(&Ah, rmax * Mx));
-            NEP_TRY(w.get(&Wj, (size_t)Mx * Mx));
-            NEP_TRY(w.get(&Vmj, (size_t)Mx * Mx));
-            NEP_TRY(w.get(&sgj, (size_t)Mx));
-            NEP_TRY(w.get(&jflags, 2));
-            NEP_TRY(w.get(&jsweeps, 1));
-            NEP_TRY(w.get(&jerr, 1));
-            NEP_TRY(w.get(&jbar, 2));
+        const int ncols = d * (p + 1);
+        if (!Ac) {
+            const size_t cmax = (size_t)d * (kmax + 1);
+            NEP_TRY(w.get(&Ac, (size_t)Mx * cmax));
+            NEP_TRY(w.get(&Gt, (size_t)Mx * cmax));
+            NEP_TRY(w.get(&Qr, (size_t)Mx * Mx));
+            NEP_TRY(w.get(&qtau, (size_t)Mx));
+            NEP_TRY(w.get(&qn2, cmax));
+            NEP_TRY(w.get(&qperm, cmax));
+            NEP_TRY(w.get(&qsteps, 1));
+            NEP_TRY(w.get(&qerr, 1));
+            NEP_TRY(w.get(&qbar, 2));
         }
-        NEP_CUDA(cudaMemsetAsync(jerr, 0, sizeof(int), st));
-        ks_blocks_h_kernel<<<ceil_div((int64_t)rows * m_cur, 256), 256, 0, st>>>(m_cur, Mx, ncols, rows, Gc, Ah);
-        NEP_CHECK_LAUNCH();
-        JacobiWork jw{Vmj, jflags, jsweeps, jbar, jerr};
-        NEP_TRY(jacobi_svd(rows, m_cur, Ah, nullptr, Wj, sgj, jw, st));
-        std::vector<double> sg(m_cur);
-        int jerr_h = 0;
-        NEP_CUDA(cudaMemcpyAsync(sg.data(), sgj, sizeof(double) * m_cur, cudaMemcpyDeviceToHost, st));
-        NEP_CUDA(cudaMemcpyAsync(&jerr_h, jerr, sizeof(int), cudaMemcpyDeviceToHost, st));
-        NEP_CUDA(cudaStreamSynchronize(st));
-        if (jerr_h) { set_error("nleigs: a bounded grid barrier timed out in the restart's SVD"); return NEP_ERR_INTERNAL; }
+        NEP_CUDA(cudaMemcpy2DAsync(Ac, sizeof(zd) * m_cur, Gc, sizeof(zd) * Mx, sizeof(zd) * m_cur, ncols,
+                                   cudaMemcpyDeviceToDevice, st));
         int r = 0;
-        while (r < m_cur && sg[r] > rows * 2.220446049250313e-16 * sg[0]) ++r;
-        r = std::max(1, std::min(r, d + p));
-        NEP_TRY(right_mul(U, n, n, m_cur, Wj, r));
-        NEP_TRY(zgemm(r, ncols, m_cur, 1, Wj, m_cur, Gc, Mx, Ah, r, nullptr, 0, st));
+        NEP_TRY(qr_range_basis(m_cur, ncols, Ac, Qr, d + p, 1e-13, qtau, qperm, qn2, qsteps, qbar, qerr, &r, st));
+        NEP_TRY(right_mul(U, n, n, m_cur, Qr, r));
+        NEP_TRY(zgemm(r, ncols, m_cur, 1, Qr, m_cur, Gc, Mx, Gt, r, nullptr, 0, st));
         NEP_CUDA(cudaMemsetAsync(Gc, 0, sizeof(zd) * (size_t)ncols * Mx, st));
-        NEP_CUDA(cudaMemcpy2DAsync(Gc, sizeof(zd) * Mx, Ah, sizeof(zd) * r, sizeof(zd) * r, ncols,
+        NEP_CUDA(cudaMemcpy2DAsync(Gc, sizeof(zd) * Mx, Gt, sizeof(zd) * r, sizeof(zd) * r, ncols,
                                    cudaMemcpyDeviceToDevice, st));
         m_cur = r;
         return NEP_OK;

@@ -620,6 +620,8 @@ struct nep_plan {
     int* info = nullptr;  // N
     double* tnorm = nullptr;
     zd* tval = nullptr;   // N x nnz
+    zdf* tval_df = nullptr;  // N x nnz, complex64 plans: the double-float copy of tval
+    zdf* V_df = nullptr;     // n x L, complex64 plans
     zd* V = nullptr;      // n x L
     zd* Y = nullptr;      // N x n x L
     zd* R = nullptr;      // N x n x L
@@ -676,7 +678,12 @@ static int plan_alloc(nep_plan* p) {
     NEP_TRY(dalloc(&p->tval, (size_t)N * h->nnz, st));
     NEP_TRY(dalloc(&p->V, (size_t)n * L, st));
     NEP_TRY(dalloc(&p->Y, (size_t)N * n * L, st));
-    NEP_TRY(dalloc(&p->R, (size_t)N * n * L, st));
+    if (p->mixed) {  // double-float refinement: no FP64 residual, split copies of T's values and V
+        NEP_TRY(dalloc_raw(reinterpret_cast<void**>(&p->tval_df), sizeof(zdf) * (size_t)N * h->nnz, st));
+        NEP_TRY(dalloc_raw(reinterpret_cast<void**>(&p->V_df), sizeof(zdf) * (size_t)n * L, st));
+    } else {
+        NEP_TRY(dalloc(&p->R, (size_t)N * n * L, st));
+    }
     NEP_TRY(dalloc_raw(&p->D, esz * (size_t)N * n * L, st));
     NEP_TRY(dalloc(&p->nrm, (size_t)N * L * 3, st));
     NEP_TRY(dalloc(&p->dmax, N, st));
@@ -745,7 +752,7 @@ static int plan_alloc(nep_plan* p) {
 
 static void plan_free(nep_plan* p) {
     cudaStream_t st = p->alloc_stream;
-    void* bufs[] = {p->F, p->coef, p->ab, p->ut, p->ipiv, p->info, p->tnorm, p->tval, p->V, p->Y, p->R, p->D, p->nrm,
+    void* bufs[] = {p->F, p->coef, p->ab, p->ut, p->ipiv, p->info, p->tnorm, p->tval, p->tval_df, p->V_df, p->V, p->Y, p->R, p->D, p->nrm,
                     p->dmax, p->ymax, p->prev, p->beta, p->active, p->sweeps, p->nactive, p->S, p->mu, p->vpart,
                     p->H, p->Hs, p->Hw, p->U, p->W, p->sigma, p->T1, p->Bred, p->theta, p->Tv, p->Z, p->cand,
                     p->XH, p->G, p->Gw, p->Wg, p->lamg, p->Q, p->Y0, p->AQ, p->Bs, p->lamn, p->Yn, p->Xc, p->Gx,
@@ -941,24 +948,38 @@ static int run_solves(nep_plan* p, cudaStream_t st) {
     cx<T>* ut = reinterpret_cast<cx<T>*>(p->ut);
     if (ut) NEP_TRY(band_transpose_u<T>(s, N, ab, ut, st));
     NEP_CUDA(cudaEventRecord(p->ev[2], st));
+    constexpr bool df = sizeof(T) == 4;  // complex64 factors: double-float refinement
+    zdf* Ydf = reinterpret_cast<zdf*>(p->Y);
     NEP_TRY(launch_convert_rhs<T>(N, n, L, p->V, D, st));
     NEP_TRY(launch_band_solve<T>(s, N, ab, ut, p->ipiv, L, D, nullptr, st, p->solve_rh));
-    NEP_TRY(launch_widen<T>(N, n, L, D, p->Y, st));
+    if constexpr (df) {
+        NEP_TRY(launch_split_df((int64_t)N * s.nnz, p->tval, p->tval_df, st));
+        NEP_TRY(launch_split_df((int64_t)n * L, p->V, p->V_df, st));
+        NEP_TRY(launch_widen_df(N, n, L, D, Ydf, st));
+    } else {
+        NEP_TRY(launch_widen<T>(N, n, L, D, p->Y, st));
+    }
     NEP_TRY(launch_fill_int(N, p->active, 1, st));
     NEP_CUDA(cudaMemsetAsync(p->prev, 0, sizeof(double) * N, st));
     NEP_CUDA(cudaMemsetAsync(p->sweeps, 0, sizeof(int) * N, st));
-    NEP_TRY(launch_drop_singular(N, n, L, p->info, p->Y, p->active, p->beta, st));
+    NEP_TRY(launch_drop_singular(N, n, L, p->info, p->Y, p->active, p->beta, st));  // zero bytes either way
     for (int sweep = 0; sweep < p->o.refine_max; ++sweep) {
-        NEP_TRY(launch_split_residual(s, N, p->tval, L, p->V, p->Y, p->R, p->nrm, p->active, st));
-        NEP_TRY(launch_refine_prepare<T>(N, n, L, p->R, D, p->active, st));
+        if constexpr (df) {
+            NEP_TRY(launch_split_residual_df(s, N, p->tval_df, L, p->V_df, Ydf, D, p->nrm, p->active, st));
+        } else {
+            NEP_TRY(launch_split_residual(s, N, p->tval, L, p->V, p->Y, p->R, p->nrm, p->active, st));
+            NEP_TRY(launch_refine_prepare<T>(N, n, L, p->R, D, p->active, st));
+        }
         NEP_TRY(launch_band_solve<T>(s, N, ab, ut, p->ipiv, L, D, p->active, st, p->solve_rh));
-        NEP_TRY(launch_refine_update<T>(N, n, L, D, p->Y, p->dmax, p->ymax, p->active, st));
+        if constexpr (df) NEP_TRY(launch_refine_update_df(N, n, L, D, Ydf, p->dmax, p->ymax, p->active, st));
+        else NEP_TRY(launch_refine_update<T>(N, n, L, D, p->Y, p->dmax, p->ymax, p->active, st));
         NEP_TRY(launch_refine_decide(N, L, sweep, p->o.refine_max, p->o.refine_tol, p->o.step_tol, p->o.refine_extrapolate, p->nrm, p->tnorm,
                                      p->dmax, p->ymax, p->prev, p->beta, p->active, p->sweeps, p->nactive, st));
         NEP_CUDA(cudaMemcpyAsync(p->h_pinned, p->nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
         NEP_CUDA(cudaStreamSynchronize(st));
         if (p->h_pinned[0] == 0) break;
     }
+    if constexpr (df) NEP_TRY(launch_df_to_zd(N, n, L, p->Y, st));
     NEP_CUDA(cudaEventRecord(p->ev[3], st));
     return NEP_OK;
 }
@@ -1108,9 +1129,16 @@ static int run_solves_batch(const std::vector<nep_plan*>& ps, cudaStream_t st) {
     };
     for (nep_plan* p : ps) NEP_TRY(launch_convert_rhs<T>(p->Np, p->h->n, p->L, p->V, reinterpret_cast<cx<T>*>(p->D), st));
     NEP_TRY(solve_all(ps, false));
+    constexpr bool df = sizeof(T) == 4;  // complex64 factors: double-float refinement, as run_solves
     for (nep_plan* p : ps) {
         const int N = p->Np, n = p->h->n, L = p->L;
-        NEP_TRY(launch_widen<T>(N, n, L, reinterpret_cast<cx<T>*>(p->D), p->Y, st));
+        if constexpr (df) {
+            NEP_TRY(launch_split_df((int64_t)N * p->h->nnz, p->tval, p->tval_df, st));
+            NEP_TRY(launch_split_df((int64_t)n * L, p->V, p->V_df, st));
+            NEP_TRY(launch_widen_df(N, n, L, reinterpret_cast<zf*>(p->D), reinterpret_cast<zdf*>(p->Y), st));
+        } else {
+            NEP_TRY(launch_widen<T>(N, n, L, reinterpret_cast<cx<T>*>(p->D), p->Y, st));
+        }
         NEP_TRY(launch_fill_int(N, p->active, 1, st));
         NEP_CUDA(cudaMemsetAsync(p->prev, 0, sizeof(double) * N, st));
         NEP_CUDA(cudaMemsetAsync(p->sweeps, 0, sizeof(int) * N, st));
@@ -1124,14 +1152,23 @@ static int run_solves_batch(const std::vector<nep_plan*>& ps, cudaStream_t st) {
     for (int sweep = 0; !live.empty(); ++sweep) {
         for (nep_plan* p : live) {
             const SplitDev s = p->h->dev();
-            NEP_TRY(launch_split_residual(s, p->Np, p->tval, p->L, p->V, p->Y, p->R, p->nrm, p->active, st));
-            NEP_TRY(launch_refine_prepare<T>(p->Np, s.n, p->L, p->R, reinterpret_cast<cx<T>*>(p->D), p->active, st));
+            if constexpr (df) {
+                NEP_TRY(launch_split_residual_df(s, p->Np, p->tval_df, p->L, p->V_df, reinterpret_cast<zdf*>(p->Y),
+                                                 reinterpret_cast<zf*>(p->D), p->nrm, p->active, st));
+            } else {
+                NEP_TRY(launch_split_residual(s, p->Np, p->tval, p->L, p->V, p->Y, p->R, p->nrm, p->active, st));
+                NEP_TRY(launch_refine_prepare<T>(p->Np, s.n, p->L, p->R, reinterpret_cast<cx<T>*>(p->D), p->active, st));
+            }
         }
         NEP_TRY(solve_all(live, true));
         for (nep_plan* p : live) {
             const SplitDev s = p->h->dev();
-            NEP_TRY(launch_refine_update<T>(p->Np, s.n, p->L, reinterpret_cast<cx<T>*>(p->D), p->Y, p->dmax, p->ymax,
-                                            p->active, st));
+            if constexpr (df)
+                NEP_TRY(launch_refine_update_df(p->Np, s.n, p->L, reinterpret_cast<zf*>(p->D),
+                                                reinterpret_cast<zdf*>(p->Y), p->dmax, p->ymax, p->active, st));
+            else
+                NEP_TRY(launch_refine_update<T>(p->Np, s.n, p->L, reinterpret_cast<cx<T>*>(p->D), p->Y, p->dmax,
+                                                p->ymax, p->active, st));
             NEP_TRY(launch_refine_decide(p->Np, p->L, sweep, p->o.refine_max, p->o.refine_tol, p->o.step_tol,
                                          p->o.refine_extrapolate, p->nrm, p->tnorm, p->dmax, p->ymax, p->prev, p->beta,
                                          p->active, p->sweeps, p->nactive, st));
@@ -1143,7 +1180,10 @@ static int run_solves_batch(const std::vector<nep_plan*>& ps, cudaStream_t st) {
             if (p->h_pinned[0] != 0 && sweep + 1 < p->o.refine_max) next.push_back(p);
         live.swap(next);
     }
-    for (nep_plan* p : ps) NEP_CUDA(cudaEventRecord(p->ev[3], st));
+    for (nep_plan* p : ps) {
+        if constexpr (df) NEP_TRY(launch_df_to_zd(p->Np, p->h->n, p->L, p->Y, st));
+        NEP_CUDA(cudaEventRecord(p->ev[3], st));
+    }
     return NEP_OK;
 }
 

@@ -366,6 +366,17 @@ int launch_scale_rows(int rows, int cols, zd* X, int ld, const double* s, cudaSt
 int launch_candidates(int m, const zd* theta, zd c, double a, zd* lam, cudaStream_t st);
 int launch_fill_int(int n, int* p, int v, cudaStream_t st);
 int launch_drop_singular(int npts, int n, int L, const int* info, zd* Y, int* active, double* beta, cudaStream_t st);
+// double-float refinement with complex64 factors (spmv.cu): a complex value as hi + lo FP32 pairs
+struct zdf {
+    float hr, hi, lr, li;  // (hr + lr) + i (hi + li)
+};
+int launch_split_df(int64_t count, const zd* x, zdf* out, cudaStream_t st);
+int launch_widen_df(int npts, int n, int L, const zf* B, zdf* Y, cudaStream_t st);
+int launch_split_residual_df(const SplitDev& s, int npts, const zdf* tval, int L, const zdf* V, const zdf* Y, zf* D,
+                             double* nrm, const int* active, cudaStream_t st);
+int launch_refine_update_df(int npts, int n, int L, const zf* D, zdf* Y, double* dmax, double* ymax, const int* active,
+                            cudaStream_t st);
+int launch_df_to_zd(int npts, int n, int L, void* Y, cudaStream_t st);
 int launch_rank(int n, const double* sigma, double tol, int* out, cudaStream_t st);
 int launch_normalize_columns(int rows, int cols, zd* X, int fix_phase, double* nrm, cudaStream_t st);
 int launch_term_spmm(const SplitDev& s, int k, const zd* Q, zd* out, cudaStream_t st);

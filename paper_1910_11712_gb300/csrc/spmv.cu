@@ -234,4 +234,184 @@ INST(float)
 INST(double)
 #undef INST
 
+
+// ------------------------------------------------------------------ double-float refinement
+// With complex64 factors the refinement keeps Y as an unevaluated sum hi + lo of two FP32 values per
+// real component (about 48 significant bits) and forms the residual V - T(z_j) Y in that arithmetic:
+// error-free products (p = a b, e = fma(a, b, -p)) and sums (Knuth's two-sum). The residual's
+// rounding is then about 2^-48 sum |t| |y|, far below the backward-error target of the refinement,
+// and the work runs on the FP32 pipe, about 68 times the FP64 rate of this part. The FP64 values of
+// T(z_j) and V are split once per pass; Y returns to FP64 for the moments.
+
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void df_quick_two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    e = b - (s - a);
+}
+// (h, l) -= (ah, al) (bh, bl)
+__device__ __forceinline__ void df_fms(float& h, float& l, float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    float pe = fmaf(ah, bh, -p);
+    pe = fmaf(ah, bl, fmaf(al, bh, pe));
+    float s, e;
+    df_two_sum(h, -p, s, e);
+    e += l - pe;
+    df_quick_two_sum(s, e, h, l);
+}
+// (h, l) += d
+__device__ __forceinline__ void df_add1(float& h, float& l, float d) {
+    float s, e;
+    df_two_sum(h, d, s, e);
+    e += l;
+    df_quick_two_sum(s, e, h, l);
+}
+
+__device__ __forceinline__ float block_max_f(float v, float* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+    return v;
+}
+
+// out[i] = x[i] as hi + lo FP32 pairs
+__global__ void split_df_kernel(int64_t count, const zd* __restrict__ x, zdf* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const zd v = x[i];
+    const float hr = (float)v.re, hi = (float)v.im;
+    out[i] = zdf{hr, hi, (float)(v.re - (double)hr), (float)(v.im - (double)hi)};
+}
+
+// Y = B (the first solve), lo parts zero
+__global__ void widen_df_kernel(int64_t total, const zf* __restrict__ B, zdf* __restrict__ Y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const zf b = B[i];
+    Y[i] = zdf{b.re, b.im, 0.0f, 0.0f};
+}
+
+// D_j = V - T(z_j) Y_j rounded to complex64 (the next correction's right-hand side), and the maxima
+// of |R|, |Y|, |V| per (point, column) as split_residual_kernel gives them
+__global__ void __launch_bounds__(256) split_residual_df_kernel(const int64_t* __restrict__ rowptr,
+                                                                const int32_t* __restrict__ col, int64_t nnz, int n,
+                                                                int L, const zdf* __restrict__ tval,
+                                                                const zdf* __restrict__ V, const zdf* __restrict__ Y,
+                                                                zf* __restrict__ D, double* __restrict__ nrm,
+                                                                const int* __restrict__ active) {
+    __shared__ float red[32];
+    const int jl = blockIdx.y;
+    const int j = jl / L, l = jl % L;
+    if (active && !active[j]) return;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const zdf* y = Y + (int64_t)jl * n;
+    const zdf* tv = tval + (int64_t)j * nnz;
+    float mr = 0.0f, my = 0.0f, mv = 0.0f;
+    if (r < n) {
+        const zdf v = V[(int64_t)l * n + r];
+        float rh = v.hr, rl = v.lr, ih = v.hi, il = v.li;
+        for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+            const zdf t = tv[e], x = y[col[e]];
+            df_fms(rh, rl, t.hr, t.lr, x.hr, x.lr);    // re -= t.re x.re
+            df_fms(rh, rl, -t.hi, -t.li, x.hi, x.li);  // re += t.im x.im
+            df_fms(ih, il, t.hr, t.lr, x.hi, x.li);    // im -= t.re x.im
+            df_fms(ih, il, t.hi, t.li, x.hr, x.lr);    // im -= t.im x.re
+        }
+        D[(int64_t)jl * n + r] = mk(rh + rl, ih + il);
+        const zdf yr = y[r];
+        mr = hypotf(rh, ih);
+        my = hypotf(yr.hr, yr.hi);
+        mv = hypotf(v.hr, v.hi);
+    }
+    if (!nrm) return;
+    mr = block_max_f(mr, red);
+    if (threadIdx.x == 0) atomic_max_nonneg_d(nrm + (int64_t)jl * 3 + 0, (double)mr);
+    my = block_max_f(my, red);
+    if (threadIdx.x == 0) atomic_max_nonneg_d(nrm + (int64_t)jl * 3 + 1, (double)my);
+    mv = block_max_f(mv, red);
+    if (threadIdx.x == 0) atomic_max_nonneg_d(nrm + (int64_t)jl * 3 + 2, (double)mv);
+}
+
+// Y += D in double-float; dmax[j] = max |D|, ymax[j] = max |Y| over the point's block
+__global__ void __launch_bounds__(256) update_df_kernel(int64_t per_point, const zf* __restrict__ D,
+                                                        zdf* __restrict__ Y, double* __restrict__ dmax,
+                                                        double* __restrict__ ymax, const int* __restrict__ active) {
+    __shared__ float red[32];
+    const int j = blockIdx.y;
+    if (active && !active[j]) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float md = 0.0f, my = 0.0f;
+    if (i < per_point) {
+        const int64_t g = (int64_t)j * per_point + i;
+        const zf d = D[g];
+        zdf y = Y[g];
+        df_add1(y.hr, y.lr, d.re);
+        df_add1(y.hi, y.li, d.im);
+        Y[g] = y;
+        md = hypotf(d.re, d.im);
+        my = hypotf(y.hr, y.hi);
+    }
+    md = block_max_f(md, red);
+    if (threadIdx.x == 0) atomic_max_nonneg_d(dmax + j, (double)md);
+    my = block_max_f(my, red);
+    if (threadIdx.x == 0) atomic_max_nonneg_d(ymax + j, (double)my);
+}
+
+// Y (double-float) -> FP64 in place
+__global__ void df_to_zd_kernel(int64_t total, void* __restrict__ Y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const zdf y = reinterpret_cast<const zdf*>(Y)[i];
+    reinterpret_cast<zd*>(Y)[i] = mk((double)y.hr + (double)y.lr, (double)y.hi + (double)y.li);
+}
+
+int launch_split_df(int64_t count, const zd* x, zdf* out, cudaStream_t st) {
+    if (count <= 0) return NEP_OK;
+    split_df_kernel<<<ceil_div(count, 256), 256, 0, st>>>(count, x, out);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+int launch_widen_df(int npts, int n, int L, const zf* B, zdf* Y, cudaStream_t st) {
+    const int64_t total = (int64_t)npts * n * L;
+    widen_df_kernel<<<ceil_div(total, 256), 256, 0, st>>>(total, B, Y);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+int launch_split_residual_df(const SplitDev& s, int npts, const zdf* tval, int L, const zdf* V, const zdf* Y, zf* D,
+                             double* nrm, const int* active, cudaStream_t st) {
+    if (npts <= 0 || L <= 0) return NEP_OK;
+    if (nrm) NEP_CUDA(cudaMemsetAsync(nrm, 0, sizeof(double) * 3 * npts * L, st));
+    dim3 grid(ceil_div(s.n, 256), npts * L);
+    split_residual_df_kernel<<<grid, 256, 0, st>>>(s.rowptr, s.col, s.nnz, s.n, L, tval, V, Y, D, nrm, active);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+int launch_refine_update_df(int npts, int n, int L, const zf* D, zdf* Y, double* dmax, double* ymax, const int* active,
+                            cudaStream_t st) {
+    if (npts <= 0) return NEP_OK;
+    const int64_t per_point = (int64_t)n * L;
+    NEP_CUDA(cudaMemsetAsync(dmax, 0, sizeof(double) * npts, st));
+    NEP_CUDA(cudaMemsetAsync(ymax, 0, sizeof(double) * npts, st));
+    dim3 grid(ceil_div(per_point, 256), npts);
+    update_df_kernel<<<grid, 256, 0, st>>>(per_point, D, Y, dmax, ymax, active);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+int launch_df_to_zd(int npts, int n, int L, void* Y, cudaStream_t st) {
+    const int64_t total = (int64_t)npts * n * L;
+    if (total <= 0) return NEP_OK;
+    df_to_zd_kernel<<<ceil_div(total, 256), 256, 0, st>>>(total, Y);
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+
 }  // namespace nep

@@ -778,14 +778,25 @@ def main():
                                                     max_batch=4, fp64=False)
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(p)
+            cores = max(1, min(32, os.cpu_count() or 1))
             if "c3" in wide:
                 p3 = synth.config_problem("drude2d_s128", seed=0)
-                cores = max(1, min(32, os.cpu_count() or 1))
                 v3 = cpu_sample_points(p3, 2 * cores, cores)
                 line["c3"]["cpu_baseline"] = {"value": v3, "unit": UNIT, "cores": cores, "kind": "oracle",
                                               "sample": f"quadrature solves at {2 * cores} of the 128 nodes of "
                                                         "drude2d_s128 (assembly, band LU, FP64 refinement), "
-                                                        f"{cores} threads over points"}
+                                                        f"{cores} threads over points",
+                                              "one_thread": {"value": cpu_sample_points(p3, 1, 1), "unit": UNIT,
+                                                             "sample": "the solve at 1 node, one thread"}}
+            if "c4" in wide:
+                # one node per thread: about 70 GF of band LU per node, tens of seconds each
+                p4 = synth.config_problem("sqrt3d_s24", seed=0)
+                v4 = cpu_sample_points(p4, cores, cores)
+                line["c4"]["cpu_baseline"] = {"value": v4, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                              "sample": f"quadrature solves at {cores} of the 64 nodes of "
+                                                        "sqrt3d_s24 (assembly, band LU, FP64 refinement), one node "
+                                                        f"on each of {cores} threads",
+                                              "seconds_per_node_one_thread": cores / v4}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -979,8 +979,7 @@ static int run_solves(nep_plan* p, cudaStream_t st) {
         NEP_CUDA(cudaStreamSynchronize(st));
         if (p->h_pinned[0] == 0) break;
     }
-    if constexpr (df) NEP_TRY(launch_df_to_zd(N, n, L, p->Y, st));
-    NEP_CUDA(cudaEventRecord(p->ev[3], st));
+    NEP_CUDA(cudaEventRecord(p->ev[3], st));  // complex64 factors: Y stays double-float for the moments
     return NEP_OK;
 }
 
@@ -1180,10 +1179,7 @@ static int run_solves_batch(const std::vector<nep_plan*>& ps, cudaStream_t st) {
             if (p->h_pinned[0] != 0 && sweep + 1 < p->o.refine_max) next.push_back(p);
         live.swap(next);
     }
-    for (nep_plan* p : ps) {
-        if constexpr (df) NEP_TRY(launch_df_to_zd(p->Np, p->h->n, p->L, p->Y, st));
-        NEP_CUDA(cudaEventRecord(p->ev[3], st));
-    }
+    for (nep_plan* p : ps) NEP_CUDA(cudaEventRecord(p->ev[3], st));
     return NEP_OK;
 }
 
@@ -1199,7 +1195,8 @@ static int run_extract(nep_plan* p, cudaStream_t st) {
     const int n = s.n, L = p->L, M = p->M, K = p->K, LM = p->LM, nt = s.nterms;
     // moments and Hankel matrices; under conjugate symmetry the nodes not solved contribute the
     // conjugates of the solved ones' terms: S_k = 2 Re sum_{Im z_j > 0} w_j zeta_j^k Y_j
-    NEP_TRY(launch_moments(n, L, p->Np, K, p->coef, p->Y, p->S, st));
+    if (p->mixed) NEP_TRY(launch_moments_df(n, L, p->Np, K, p->coef, p->Y, p->S, st));  // Y back to FP64 too
+    else NEP_TRY(launch_moments(n, L, p->Np, K, p->coef, p->Y, p->S, st));
     if (p->Np != p->N) NEP_TRY(launch_double_real(int64_t(K) * n * L, p->S, st));
     NEP_TRY(launch_vh_times(n, L, K, p->V, p->S, p->mu, p->vpart, st));
     NEP_TRY(launch_hankel_build(L, M, p->mu, p->H, p->Hs, st));

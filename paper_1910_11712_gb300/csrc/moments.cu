@@ -13,6 +13,7 @@
 // reduction (no atomics), so results do not depend on scheduling.
 #include <algorithm>
 
+#include "df_arith.cuh"
 #include "nep_common.cuh"
 
 namespace nep {
@@ -70,6 +71,60 @@ int launch_moments(int n, int L, int N, int K, const zd* coef, const zd* Y, zd* 
         moments_kernel<8><<<blocks, 256, sm, st>>>(nl, N, coef, Y, S);
     } else {
         moments_kernel_generic<<<blocks, 256, 0, st>>>(nl, N, K, coef, Y, S);
+    }
+    NEP_CHECK_LAUNCH();
+    return NEP_OK;
+}
+
+// The moments from Y held as double-float pairs (complex64 factors, the refinement's form): the
+// accumulation in double-float arithmetic (coefficients split once per CTA), S written in FP64,
+// and each Y element returned to FP64 in place after it is read.
+template <int K>
+__global__ void __launch_bounds__(256) moments_df_kernel(int64_t nl, int N, const zd* __restrict__ coef,
+                                                         void* __restrict__ Y, zd* __restrict__ S) {
+    extern __shared__ zdf csf[];  // N x K
+    for (int t = threadIdx.x; t < N * K; t += blockDim.x) {
+        const zd c = coef[(t / K) + (int64_t)N * (t % K)];
+        const float hr = (float)c.re, hi = (float)c.im;
+        csf[t] = zdf{hr, hi, (float)(c.re - (double)hr), (float)(c.im - (double)hi)};
+    }
+    __syncthreads();
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nl) return;
+    float rh[K], rl[K], ih[K], il[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) rh[k] = rl[k] = ih[k] = il[k] = 0.0f;
+    zdf* Yd = reinterpret_cast<zdf*>(Y);
+    zd* Yz = reinterpret_cast<zd*>(Y);
+    for (int j = 0; j < N; ++j) {
+        const zdf y = Yd[(int64_t)j * nl + e];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const zdf c = csf[j * K + k];
+            df_fma(rh[k], rl[k], c.hr, c.lr, y.hr, y.lr);    // re += c.re y.re
+            df_fms(rh[k], rl[k], c.hi, c.li, y.hi, y.li);    // re -= c.im y.im
+            df_fma(ih[k], il[k], c.hr, c.lr, y.hi, y.li);    // im += c.re y.im
+            df_fma(ih[k], il[k], c.hi, c.li, y.hr, y.lr);    // im += c.im y.re
+        }
+        Yz[(int64_t)j * nl + e] = mk((double)y.hr + (double)y.lr, (double)y.hi + (double)y.li);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) S[(int64_t)k * nl + e] = mk((double)rh[k] + (double)rl[k], (double)ih[k] + (double)il[k]);
+}
+
+int launch_moments_df(int n, int L, int N, int K, const zd* coef, void* Y, zd* S, cudaStream_t st) {
+    const int64_t nl = (int64_t)n * L;
+    const int blocks = ceil_div(nl, 256);
+    const size_t sm = sizeof(zdf) * (size_t)N * K;
+    if (K == 16 && sm <= 96 * 1024) {
+        NEP_CUDA(allow_max_dynamic_smem(moments_df_kernel<16>));
+        moments_df_kernel<16><<<blocks, 256, sm, st>>>(nl, N, coef, Y, S);
+    } else if (K == 8 && sm <= 96 * 1024) {
+        NEP_CUDA(allow_max_dynamic_smem(moments_df_kernel<8>));
+        moments_df_kernel<8><<<blocks, 256, sm, st>>>(nl, N, coef, Y, S);
+    } else {  // other moment counts: Y to FP64, then the FP64 moments
+        NEP_TRY(launch_df_to_zd(N, n, L, Y, st));
+        return launch_moments(n, L, N, K, coef, reinterpret_cast<const zd*>(Y), S, st);
     }
     NEP_CHECK_LAUNCH();
     return NEP_OK;

@@ -377,6 +377,8 @@ int launch_split_residual_df(const SplitDev& s, int npts, const zdf* tval, int L
 int launch_refine_update_df(int npts, int n, int L, const zf* D, zdf* Y, double* dmax, double* ymax, const int* active,
                             cudaStream_t st);
 int launch_df_to_zd(int npts, int n, int L, void* Y, cudaStream_t st);
+// moments.cu: the moments from double-float Y, which it returns to FP64 in place
+int launch_moments_df(int n, int L, int N, int K, const zd* coef, void* Y, zd* S, cudaStream_t st);
 int launch_rank(int n, const double* sigma, double tol, int* out, cudaStream_t st);
 int launch_normalize_columns(int rows, int cols, zd* X, int fix_phase, double* nrm, cudaStream_t st);
 int launch_term_spmm(const SplitDev& s, int k, const zd* Q, zd* out, cudaStream_t st);

@@ -13,6 +13,7 @@
 //   R = V - T Y (FP64);  beta = max_l ||R_l||_inf / (||T||_inf ||Y_l||_inf + ||V_l||_inf);
 //   D = T^{-1} R with the stored factors (complex64 or complex128);  Y += D (FP64);
 //   stop when beta <= tol and (||D||/||Y|| <= step_tol or ||D||/||Y|| stopped halving).
+#include "df_arith.cuh"
 #include "nep_common.cuh"
 
 namespace nep {
@@ -242,33 +243,6 @@ INST(double)
 // rounding is then about 2^-48 sum |t| |y|, far below the backward-error target of the refinement,
 // and the work runs on the FP32 pipe, about 68 times the FP64 rate of this part. The FP64 values of
 // T(z_j) and V are split once per pass; Y returns to FP64 for the moments.
-
-__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-__device__ __forceinline__ void df_quick_two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    e = b - (s - a);
-}
-// (h, l) -= (ah, al) (bh, bl)
-__device__ __forceinline__ void df_fms(float& h, float& l, float ah, float al, float bh, float bl) {
-    const float p = ah * bh;
-    float pe = fmaf(ah, bh, -p);
-    pe = fmaf(ah, bl, fmaf(al, bh, pe));
-    float s, e;
-    df_two_sum(h, -p, s, e);
-    e += l - pe;
-    df_quick_two_sum(s, e, h, l);
-}
-// (h, l) += d
-__device__ __forceinline__ void df_add1(float& h, float& l, float d) {
-    float s, e;
-    df_two_sum(h, d, s, e);
-    e += l;
-    df_quick_two_sum(s, e, h, l);
-}
 
 __device__ __forceinline__ float block_max_f(float v, float* red) {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));

@@ -1200,7 +1200,8 @@ __device__ __forceinline__ void givens_rsqrt(cx<T> x, cx<T> y, T* c, cx<T>* s) {
 }
 
 // ------------------------------------------------------------------ eigenvalues, then inverse iteration
-// Faster variant for the reduced Hankel matrix: (1) one warp reduces to Hessenberg form and
+// Faster variant for the reduced Hankel matrix: (1) one CTA (one warp below m = 64, four from
+// there, the rotations' row and column updates spread over them) reduces to Hessenberg form and
 // runs the shifted QR iteration updating only the active block (eigenvalues only, no Schur
 // vectors); (2) one warp per eigenvalue solves (A - theta I) v = v twice by Gaussian
 // elimination with partial pivoting (inverse iteration) for the eigenvector.
@@ -1208,53 +1209,67 @@ template <typename T>
 __global__ void hqr_eigvals_kernel(int m, const zd* __restrict__ Ain, zd* __restrict__ eval, int* __restrict__ status,
                                    cx<T>* gbuf, int use_smem) {
     extern __shared__ unsigned char sraw[];
+    __shared__ T red[32];
     const int ld = m + 1;
     cx<T>* H = use_smem ? reinterpret_cast<cx<T>*>(sraw) : gbuf;
     cx<T>* v = H + (int64_t)m * ld;
-    const int lane = threadIdx.x;
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, nw = nthr >> 5;
     const T eps = sizeof(T) == 4 ? T(6e-8) : T(1.2e-16);
     auto h = [&](int i, int j) -> cx<T>& { return H[i + (int64_t)ld * j]; };
-    for (int t = lane; t < m * m; t += 32) h(t % m, t / m) = cvt<T>(Ain[t]);
-    __syncwarp();
+    auto sync = [&]() {
+        if (nw > 1) __syncthreads();
+        else __syncwarp();
+    };
+    auto bsum = [&](T x) -> T {
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (nw == 1) return x;
+        if (lane == 0) red[tid >> 5] = x;
+        __syncthreads();
+        T t = 0;
+        for (int w = 0; w < nw; ++w) t += red[w];
+        __syncthreads();
+        return t;
+    };
+    for (int t = tid; t < m * m; t += nthr) h(t % m, t / m) = cvt<T>(Ain[t]);
+    sync();
     for (int k = 0; k + 2 < m; ++k) {
         T nx = 0;
-        for (int i = k + 1 + lane; i < m; i += 32) nx += norm2(h(i, k));
-        for (int o = 16; o > 0; o >>= 1) nx += __shfl_xor_sync(0xffffffffu, nx, o);
-        nx = sqrt(nx);
+        for (int i = k + 1 + tid; i < m; i += nthr) nx += norm2(h(i, k));
+        nx = sqrt(bsum(nx));
         if (nx == T(0)) continue;
         const cx<T> x0 = h(k + 1, k);
         const T a0 = hypot(x0.re, x0.im);
         const cx<T> ph = a0 > 0 ? mk<T>(x0.re / a0, x0.im / a0) : mk<T>(1, 0);
-        for (int i = k + 1 + lane; i < m; i += 32) v[i] = h(i, k);
-        __syncwarp();
-        if (lane == 0) v[k + 1] = v[k + 1] + nx * ph;
-        __syncwarp();
+        for (int i = k + 1 + tid; i < m; i += nthr) v[i] = h(i, k);
+        sync();
+        if (tid == 0) v[k + 1] = v[k + 1] + nx * ph;
+        sync();
         T vv = 0;
-        for (int i = k + 1 + lane; i < m; i += 32) vv += norm2(v[i]);
-        for (int o = 16; o > 0; o >>= 1) vv += __shfl_xor_sync(0xffffffffu, vv, o);
-        const T sc = T(2) / vv;
-        for (int j = k + lane; j < m; j += 32) {
+        for (int i = k + 1 + tid; i < m; i += nthr) vv += norm2(v[i]);
+        const T sc = T(2) / bsum(vv);
+        for (int j = k + tid; j < m; j += nthr) {
             cx<T> sm = mk<T>(0, 0);
             for (int i = k + 1; i < m; ++i) sm = fmac(sm, v[i], h(i, j));
             sm = sc * sm;
             for (int i = k + 1; i < m; ++i) h(i, j) = fms(h(i, j), v[i], sm);
         }
-        __syncwarp();
-        for (int i = lane; i < m; i += 32) {
+        sync();
+        for (int i = tid; i < m; i += nthr) {
             cx<T> sm = mk<T>(0, 0);
             for (int j = k + 1; j < m; ++j) sm = fma_(sm, h(i, j), v[j]);
             sm = sc * sm;
             for (int j = k + 1; j < m; ++j) h(i, j) = fms(h(i, j), sm, conj(v[j]));
         }
-        __syncwarp();
-        for (int i = k + 2 + lane; i < m; i += 32) h(i, k) = mk<T>(0, 0);
-        __syncwarp();
+        sync();
+        for (int i = k + 2 + tid; i < m; i += nthr) h(i, k) = mk<T>(0, 0);
+        sync();
     }
     int ihi = m - 1, iter = 0, since = 0, fail = 0;
     const int maxit = 60 * m + 100;
     while (ihi > 0) {
         if (iter++ > maxit) { fail = 1; break; }
-        // the largest l <= ihi with a negligible h(l, l-1) (0 if none), 32 subdiagonals per ballot
+        // the largest l <= ihi with a negligible h(l, l-1) (0 if none), 32 subdiagonals per ballot;
+        // every warp finds the same l
         int l = 0;
         for (int base = ihi; base > 0; base -= 32) {
             const int li = base - lane;
@@ -1269,9 +1284,9 @@ __global__ void hqr_eigvals_kernel(int m, const zd* __restrict__ Ain, zd* __rest
                 break;
             }
         }
-        __syncwarp();
-        if (l > 0 && lane == 0) h(l, l - 1) = mk<T>(0, 0);
-        __syncwarp();
+        sync();
+        if (l > 0 && tid == 0) h(l, l - 1) = mk<T>(0, 0);
+        sync();
         if (l == ihi) { --ihi; since = 0; continue; }
         ++since;
         const cx<T> a = h(ihi - 1, ihi - 1), b = h(ihi - 1, ihi), c2 = h(ihi, ihi - 1), d = h(ihi, ihi);
@@ -1290,28 +1305,28 @@ __global__ void hqr_eigvals_kernel(int m, const zd* __restrict__ Ain, zd* __rest
             cx<T> sn;
             givens_rsqrt(x, y, &cs, &sn);
             // active block only: rows k, k+1 over columns max(l, k-1)..ihi; columns k, k+1 over rows l..min(k+2, ihi)
-            for (int j = max(l, k - 1) + lane; j <= ihi; j += 32) {
+            for (int j = max(l, k - 1) + tid; j <= ihi; j += nthr) {
                 const cx<T> p = h(k, j), q = h(k + 1, j);
                 h(k, j) = cs * p + sn * q;
                 h(k + 1, j) = cs * q - conj(sn) * p;
             }
-            __syncwarp();
+            sync();
             const int rlim = min(k + 2, ihi);
-            for (int i = l + lane; i <= rlim; i += 32) {
+            for (int i = l + tid; i <= rlim; i += nthr) {
                 const cx<T> p = h(i, k), q = h(i, k + 1);
                 h(i, k) = cs * p + conj(sn) * q;
                 h(i, k + 1) = cs * q - sn * p;
             }
-            __syncwarp();
+            sync();
             if (k + 1 < ihi) {
                 x = h(k + 1, k);
                 y = h(k + 2, k);
             }
         }
     }
-    __syncwarp();
-    for (int i = lane; i < m; i += 32) eval[i] = cvt<double>(h(i, i));
-    if (lane == 0 && status) *status = fail;
+    sync();
+    for (int i = tid; i < m; i += nthr) eval[i] = cvt<double>(h(i, i));
+    if (tid == 0 && status) *status = fail;
 }
 
 template <typename T>
@@ -1409,7 +1424,8 @@ int small_eig_fast(int m, const zd* A, zd* eval, zd* evec, int* status, void* gb
     const int s1 = b1 <= 200 * 1024;
     if (s1) NEP_CUDA(allow_max_dynamic_smem(hqr_eigvals_kernel<T>));
     else if (!gbuf) return NEP_ERR_INTERNAL;
-    hqr_eigvals_kernel<T><<<1, 32, s1 ? b1 : 0, st>>>(m, A, eval, status, (cx<T>*)gbuf, s1);
+    // four warps once the matrix is large enough for the rotations' row and column updates to spread
+    hqr_eigvals_kernel<T><<<1, m >= 64 ? 128 : 32, s1 ? b1 : 0, st>>>(m, A, eval, status, (cx<T>*)gbuf, s1);
     NEP_CHECK_LAUNCH();
     if (!evec) return NEP_OK;
     const size_t b2 = sizeof(cx<T>) * ((size_t)m * (m + 1) + m) + sizeof(int) * m + 16;

@@ -582,6 +582,253 @@ __global__ void __launch_bounds__(32) qrcp_kernel(int rows, int cols, zd* __rest
     }
 }
 
+// The same QR with column pivoting on one thread-block cluster of CS CTAs (CS = 16 where the
+// GPU allows it): CTA r keeps the columns j = r (mod CS) in shared memory, and the cluster's
+// barriers (hardware, about a microsecond less than a grid barrier each) and distributed shared
+// memory replace the grid barrier and the global column traffic. Per step k: every CTA publishes
+// the largest remaining norm of its columns (first index on ties) and their sum, and all read the
+// CTA results in the same order, so they agree on the pivot and on the stop; the owners of columns
+// k and p exchange them through their swap buffers; the owner of column k builds the reflector;
+// every CTA copies it and applies H_k^H to its columns j > k, one warp per column with the lane
+// order of qrcp_kernel, and recomputes their remaining norms. On exit A, tau, perm and the step
+// count are as qrcp_kernel leaves them.
+constexpr int kQrcpClusterThreads = 128;
+namespace cg = cooperative_groups;
+__global__ void __launch_bounds__(kQrcpClusterThreads) qrcp_cluster_kernel(int rows, int cols, zd* __restrict__ A,
+                                                                           zd* __restrict__ tau,
+                                                                           int* __restrict__ perm, double stop2,
+                                                                           int* __restrict__ steps_out) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int CS = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int ncl = (cols + CS - 1) / CS;  // column slots of this CTA: global j = c CS + rank
+    extern __shared__ __align__(16) unsigned char sraw[];
+    zd* colm = reinterpret_cast<zd*>(sraw);      // ncl x rows
+    zd* vloc = colm + (size_t)ncl * rows;        // rows: the current reflector
+    zd* swp = vloc + rows;                       // rows: swap buffer
+    double* lnorm = reinterpret_cast<double*>(swp + rows);  // ncl
+    int* lperm = reinterpret_cast<int*>(lnorm + ncl);       // ncl
+    __shared__ double slot_best, slot_rest, b_first;
+    __shared__ int slot_idx, swp_perm, b_p, b_stop;
+    __shared__ zd tau_s, tau_b;
+    auto col = [&](int c) { return colm + (size_t)c * rows; };
+    for (int c = 0; c < ncl; ++c) {
+        const int j = c * CS + rank;
+        for (int i = tid; i < rows; i += blockDim.x) col(c)[i] = j < cols ? A[(int64_t)j * rows + i] : mk(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int c = warp; c < ncl; c += nw) {
+        const int j = c * CS + rank;
+        double s = 0.0;
+        for (int i = lane; i < rows; i += 32) s += norm2(col(c)[i]);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            lnorm[c] = j < cols ? s : -1.0;
+            lperm[c] = j;
+        }
+    }
+    const int steps = min(rows, cols);
+    int done = steps;
+    for (int k = 0; k < steps; ++k) {
+        __syncthreads();
+        if (warp == 0) {  // this CTA's best remaining column and the sum of its remaining norms
+            double best = -1.0, rest = 0.0;
+            int bi = cols;
+            for (int c = lane; c < ncl; c += 32) {
+                const int j = c * CS + rank;
+                if (j >= k && j < cols) {
+                    const double v = lnorm[c];
+                    rest += v;
+                    if (v > best) { best = v; bi = j; }
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                rest += __shfl_xor_sync(0xffffffffu, rest, o);
+            }
+            if (lane == 0) {
+                slot_best = best;
+                slot_idx = bi;
+                slot_rest = rest;
+            }
+        }
+        cluster.sync();
+        if (warp == 0) {  // the cluster's pivot and remaining mass, the same in every CTA
+            double best = -1.0, rest = 0.0;
+            int bi = cols;
+            if (lane < CS) {
+                best = *cluster.map_shared_rank(&slot_best, lane);
+                bi = *cluster.map_shared_rank(&slot_idx, lane);
+                rest = *cluster.map_shared_rank(&slot_rest, lane);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                rest += __shfl_xor_sync(0xffffffffu, rest, o);
+            }
+            if (lane == 0) {
+                if (bi >= cols) bi = k;  // NaN norms match no column
+                if (k == 0) b_first = best;
+                b_p = bi;
+                b_stop = rest <= stop2 * b_first;
+            }
+        }
+        cluster.sync();  // every CTA has read the slots before they are written again
+        if (b_stop) {
+            done = k;
+            break;
+        }
+        const int p = b_p;
+        const int ok = k % CS, op = p % CS, ck = k / CS, cp = p / CS;
+        if (p != k) {
+            if (ok == op) {
+                if (rank == ok) {
+                    for (int i = tid; i < rows; i += blockDim.x) {
+                        const zd t = col(ck)[i];
+                        col(ck)[i] = col(cp)[i];
+                        col(cp)[i] = t;
+                    }
+                    if (tid == 0) {
+                        const int t = lperm[ck];
+                        lperm[ck] = lperm[cp];
+                        lperm[cp] = t;
+                    }
+                }
+            } else {
+                if (rank == ok || rank == op) {
+                    const int c = rank == ok ? ck : cp;
+                    for (int i = tid; i < rows; i += blockDim.x) swp[i] = col(c)[i];
+                    if (tid == 0) swp_perm = lperm[c];
+                }
+                cluster.sync();
+                if (rank == ok || rank == op) {
+                    const int c = rank == ok ? ck : cp, other = rank == ok ? op : ok;
+                    const zd* rs = cluster.map_shared_rank(swp, other);
+                    for (int i = tid; i < rows; i += blockDim.x) col(c)[i] = rs[i];
+                    if (tid == 0) lperm[c] = *cluster.map_shared_rank(&swp_perm, other);
+                }
+            }
+        }
+        __syncthreads();
+        if (rank == ok && warp == 0) {  // reflector of column k, rows k .. rows-1
+            zd* ak = col(ck);
+            double xs = 0.0;
+            for (int i = k + 1 + lane; i < rows; i += 32) xs += norm2(ak[i]);
+            for (int o = 16; o > 0; o >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, o);
+            const zd alpha = ak[k];
+            zd t = mk(0.0, 0.0);
+            if (xs > 0.0 || alpha.im != 0.0) {
+                const double an = hypot(alpha.re, alpha.im);
+                const double bnorm = sqrt(an * an + xs);
+                const double beta = alpha.re >= 0 ? -bnorm : bnorm;  // beta real, sign opposite Re(alpha)
+                t = mk((beta - alpha.re) / beta, -alpha.im / beta);
+                const zd scale = cdiv(mk(1.0, 0.0), alpha - mk(beta, 0.0));
+                __syncwarp();
+                for (int i = k + 1 + lane; i < rows; i += 32) ak[i] = ak[i] * scale;
+                __syncwarp();
+                if (lane == 0) ak[k] = mk(beta, 0.0);
+            }
+            if (lane == 0) {
+                tau_s = t;
+                tau[k] = t;
+            }
+        }
+        cluster.sync();  // the reflector is published; the swap buffers have been read
+        {
+            const zd* rv = cluster.map_shared_rank(colm + (size_t)ck * rows, ok);
+            for (int i = k + 1 + tid; i < rows; i += blockDim.x) vloc[i] = rv[i];
+            if (tid == 0) tau_b = *cluster.map_shared_rank(&tau_s, ok);
+        }
+        __syncthreads();
+        const zd tk = tau_b;
+        for (int c = warp; c < ncl; c += nw) {  // apply H_k^H = I - conj(tau) v v^H to columns j > k
+            const int j = c * CS + rank;
+            if (j <= k || j >= cols) continue;
+            zd* a = col(c);
+            zd sm = lane == 0 ? a[k] : mk(0.0, 0.0);
+            for (int i = k + 1 + lane; i < rows; i += 32) sm = fmac(sm, vloc[i], a[i]);
+            for (int o = 16; o > 0; o >>= 1) {
+                sm.re += __shfl_xor_sync(0xffffffffu, sm.re, o);
+                sm.im += __shfl_xor_sync(0xffffffffu, sm.im, o);
+            }
+            const zd f = conj(tk) * sm;
+            double rest = 0.0;
+            __syncwarp();
+            if (lane == 0) a[k] = a[k] - f;
+            for (int i = k + 1 + lane; i < rows; i += 32) {
+                a[i] = fms(a[i], vloc[i], f);
+                rest += norm2(a[i]);
+            }
+            for (int o = 16; o > 0; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
+            if (lane == 0) lnorm[c] = rest;
+        }
+    }
+    __syncthreads();
+    for (int c = 0; c < ncl; ++c) {
+        const int j = c * CS + rank;
+        if (j >= cols) continue;
+        for (int i = tid; i < rows; i += blockDim.x) A[(int64_t)j * rows + i] = col(c)[i];
+        if (tid == 0) perm[j] = lperm[c];
+    }
+    if (rank == 0) {
+        for (int k = done + tid; k < steps; k += blockDim.x) tau[k] = mk(0.0, 0.0);  // H_k = I beyond the stop
+        if (tid == 0) *steps_out = done;
+    }
+    cluster.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// Launches qrcp_cluster_kernel on the largest cluster the GPU takes (16 or 8 CTAs) whose columns
+// fit in shared memory; returns false (nothing launched) when none does.
+static bool launch_qrcp_cluster(int rows, int cols, zd* A, zd* tau, int* perm, double stop2, int* steps_dev,
+                                cudaStream_t st) {
+    static int allowed = -1;  // 16 if non-portable cluster sizes are accepted, else 8
+    if (allowed < 0)
+        allowed = cudaFuncSetAttribute(qrcp_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                          cudaSuccess
+                      ? 16
+                      : 8;
+    cudaGetLastError();
+    for (int CS = allowed; CS >= 8; CS /= 2) {
+        const int ncl = (cols + CS - 1) / CS;
+        if (ncl > 32) continue;
+        const size_t smem = sizeof(zd) * ((size_t)ncl * rows + 2 * (size_t)rows) + (sizeof(double) + sizeof(int)) * ncl;
+        if (smem > 200 * 1024) continue;
+        if (cudaFuncSetAttribute(qrcp_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(CS);
+        cfg.blockDim = dim3(kQrcpClusterThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, qrcp_cluster_kernel, &cfg) != cudaSuccess || nclusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        if (cudaLaunchKernelEx(&cfg, qrcp_cluster_kernel, rows, cols, A, tau, perm, stop2, steps_dev) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        count_launch();
+        return true;
+    }
+    return false;
+}
+
 // R^H of the upper triangle of A (n x n): Rh(i, j) = conj(A(j, i)) for i >= j, 0 above.
 __global__ void rh_from_qr_kernel(int n, int ncols, const zd* __restrict__ A, zd* __restrict__ Rh) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -666,9 +913,12 @@ int qrcp_jacobi_svd(int n, zd* A, zd* U, zd* W, double* sigma, zd* work1, zd* wo
     GridBar gb{w.bar, w.bar + 1, w.err, wait_limit()};
     int rows = n, cols = n;
     double stop2 = trunc * trunc;
-    void* args[] = {&rows, &cols, &A, &tau, &perm, &nrm2, &stop2, &steps_dev, &gb};
-    NEP_CUDA(cudaLaunchCooperativeKernel((const void*)qrcp_kernel, dim3(blocks), dim3(32), args, 0, st));
-    count_launch();
+    // one cluster with distributed shared memory where it fits, else the cooperative grid
+    if (!launch_qrcp_cluster(rows, cols, A, tau, perm, stop2, steps_dev, st)) {
+        void* args[] = {&rows, &cols, &A, &tau, &perm, &nrm2, &stop2, &steps_dev, &gb};
+        NEP_CUDA(cudaLaunchCooperativeKernel((const void*)qrcp_kernel, dim3(blocks), dim3(32), args, 0, st));
+        count_launch();
+    }
     NEP_CUDA(cudaMemcpyAsync(steps_host, steps_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
     NEP_CUDA(cudaStreamSynchronize(st));
     const int mq = std::max(0, std::min(n, *steps_host));

@@ -217,25 +217,20 @@ static int flatten_fn(nep_split* h, const nep_fn* f, int depth) {
 }
 
 static void free_split_device(nep_split* h) {
-    cudaFree(h->d_rowptr);
-    cudaFree(h->d_col);
-    cudaFree(h->d_val);
-    cudaFree(h->d_val_im);
-    cudaFree(h->d_norms);
-    cudaFree(h->d_norms1);
-    cudaFree(h->d_colptr);
-    cudaFree(h->d_cidx);
-    cudaFree(h->d_crow);
-    cudaFree(h->d_nodes);
-    cudaFree(h->d_coef);
-    cudaFree(h->d_roots);
+    void* bufs[] = {h->d_rowptr, h->d_col, h->d_val, h->d_val_im, h->d_norms, h->d_norms1,
+                    h->d_colptr, h->d_cidx, h->d_crow, h->d_nodes, h->d_coef, h->d_roots};
+    for (void* b : bufs)
+        if (b) cudaFreeAsync(b, 0);
 }
 
+// the split's arrays come from the stream-ordered pool on the legacy stream (the caller synchronises
+// it once after all uploads), so that destroying a split frees them without the device-wide
+// synchronisation of cudaFree
 template <typename T>
 static int upload(T** d, const std::vector<T>& v) {
     const size_t bytes = sizeof(T) * (v.size() ? v.size() : 1);
-    NEP_CUDA(cudaMalloc((void**)d, bytes));
-    if (!v.empty()) NEP_CUDA(cudaMemcpy(*d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    NEP_CUDA(cudaMallocAsync((void**)d, bytes, 0));
+    if (!v.empty()) NEP_CUDA(cudaMemcpyAsync(*d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, 0));
     return NEP_OK;
 }
 
@@ -355,7 +350,8 @@ extern "C" int nep_create_split(int32_t n, int32_t nterms, const nep_csr* A, con
         (rc = upload(&h->d_val_im, h->val_im)) || (rc = upload(&h->d_norms, h->norms)) ||
         (rc = upload(&h->d_norms1, h->norms1)) || (rc = upload(&h->d_colptr, h->colptr)) ||
         (rc = upload(&h->d_cidx, h->cidx)) || (rc = upload(&h->d_crow, h->crow)) ||
-        (rc = upload(&h->d_nodes, h->nodes)) || (rc = upload(&h->d_coef, h->coef)) || (rc = upload(&h->d_roots, h->roots))) {
+        (rc = upload(&h->d_nodes, h->nodes)) || (rc = upload(&h->d_coef, h->coef)) || (rc = upload(&h->d_roots, h->roots)) ||
+        (rc = cudaStreamSynchronize(0) == cudaSuccess ? NEP_OK : NEP_ERR_CUDA)) {
         free_split_device(h);
         delete h;
         return rc;
@@ -663,6 +659,32 @@ struct nep_plan {
     cudaEvent_t ev[6] = {};
 };
 
+// Pinned host scalars of the plans, handed out from chunks that live as long as the process: a
+// plan's cudaHostAlloc / cudaFreeHost pair would cost a pinning per plan and, at the free, a
+// synchronisation of the whole device, stalling every other plan's stream (the request server
+// creates and destroys a plan per request).
+namespace nep {
+static std::mutex g_pin_mu;
+static std::vector<int*> g_pin_free;
+int* pinned_slot_get() {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_free.empty()) {
+        constexpr int kSlots = 64, kInts = 64;
+        int* chunk = nullptr;
+        if (cudaHostAlloc((void**)&chunk, sizeof(int) * kSlots * kInts, cudaHostAllocDefault) != cudaSuccess)
+            return nullptr;
+        for (int i = kSlots - 1; i >= 0; --i) g_pin_free.push_back(chunk + (size_t)kInts * i);
+    }
+    int* slot = g_pin_free.back();
+    g_pin_free.pop_back();
+    return slot;
+}
+void pinned_slot_put(int* slot) {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(slot);
+}
+}  // namespace nep
+
 static int plan_alloc(nep_plan* p) {
     const nep_split* h = p->h;
     const int n = h->n, N = p->Np, L = p->L, K = p->K, LM = p->LM, nt = h->nterms;
@@ -745,7 +767,8 @@ static int plan_alloc(nep_plan* p) {
     NEP_TRY(dalloc(&p->jw.err, 1, st));
     if (g_dry) return NEP_OK;
     NEP_CUDA(cudaMemsetAsync(p->jw.err, 0, sizeof(int), st));
-    NEP_CUDA(cudaHostAlloc((void**)&p->h_pinned, 64 * sizeof(int), cudaHostAllocDefault));
+    p->h_pinned = pinned_slot_get();
+    if (!p->h_pinned) { set_error("no pinned host memory for the plan's scalars"); return NEP_ERR_NOMEM; }
     for (auto& e : p->ev) NEP_CUDA(cudaEventCreate(&e));
     return NEP_OK;
 }
@@ -761,7 +784,7 @@ static void plan_free(nep_plan* p) {
     for (void* b : bufs)
         if (b) cudaFreeAsync(b, st);
     cudaStreamSynchronize(st);
-    if (p->h_pinned) cudaFreeHost(p->h_pinned);
+    if (p->h_pinned) pinned_slot_put(p->h_pinned);
     for (auto& e : p->ev)
         if (e) cudaEventDestroy(e);
 }

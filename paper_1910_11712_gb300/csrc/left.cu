@@ -535,7 +535,8 @@ static int left_route(const SplitDev& s, bool adjoint, int P, const zd* lam, con
     NEP_CHECK_LAUNCH();
     NEP_CUDA(cudaMemcpyAsync(Y, X, sizeof(zd) * (size_t)n * P, cudaMemcpyDeviceToDevice, st));
     int* host = nullptr;
-    NEP_CUDA(cudaHostAlloc((void**)&host, sizeof(int), cudaHostAllocDefault));
+    host = pinned_slot_get();
+    if (!host) { set_error("no pinned host memory"); return NEP_ERR_NOMEM; }
     int rc = NEP_OK, k = 0;
     const int64_t total = (int64_t)P * n;
     for (; k < max_it; ++k) {
@@ -589,7 +590,7 @@ static int left_route(const SplitDev& s, bool adjoint, int P, const zd* lam, con
                 cudaStreamSynchronize(st) != cudaSuccess))
         rc = NEP_ERR_CUDA;
     if (!rc) *nonfinite = *host;
-    cudaFreeHost(host);
+    pinned_slot_put(host);
     return rc;
 }
 

@@ -407,6 +407,11 @@ int left_eigvecs(const SplitDev& s, int P, const zd* lam, const zd* X, zd* Y, do
                  int max_it, int* steps_host, cudaStream_t st);
 // Stream-ordered work arrays of one call (cudaMallocAsync on st), freed in stream order on every
 // return path.
+// pinned host scalars (64 ints a slot) from a process-wide pool: no per-call pinning, and no
+// device-wide synchronisation when a slot is given back (host_api.cu)
+int* pinned_slot_get();
+void pinned_slot_put(int* slot);
+
 struct StreamScratch {
     std::vector<void*> bufs;
     cudaStream_t st;

@@ -194,7 +194,8 @@ int rii_polish(const SplitDev& s, int P, zd* lam, zd* X, double* eta, int* its, 
     NEP_CHECK_LAUNCH();
     const double inner_tol = 1.4901161193847656e-08;  // sqrt(eps) of FP64
     int* host = nullptr;
-    NEP_CUDA(cudaHostAlloc((void**)&host, sizeof(int), cudaHostAllocDefault));
+    host = pinned_slot_get();
+    if (!host) { set_error("no pinned host memory"); return NEP_ERR_NOMEM; }
     int rc = NEP_OK, k = 0;
     for (; k <= max_it; ++k) {
         rii_coeffs_kernel<<<ceil_div(P * nt, 128), 128, 0, st>>>(s, P, lam, Fk);
@@ -221,7 +222,7 @@ int rii_polish(const SplitDev& s, int P, zd* lam, zd* X, double* eta, int* its, 
         }
         if (*host == 0) break;
     }
-    cudaFreeHost(host);
+    pinned_slot_put(host);
     if (rc) return rc;
     if (max_its_host) *max_its_host = std::min(k, max_it) + 1;  // outer iterations run
     // unit 2-norm, first entry of largest modulus real positive (the pipeline's convention)

@@ -2,11 +2,12 @@
 
 A step is one whole contour-integral pass over the n = 4096 (64 x 64 grid, bandwidth 64)
 delay problem with N = 64 quadrature points, L = 16 probe columns and M = 8 moments:
-assembly, banded LU, solves with FP64 refinement to backward error <= 1e-10, moments,
-block-Hankel SVD, reduced eigenproblem, Rayleigh-Ritz with Newton, scaled residuals.
-`value` counts quadrature solves (one (problem, z_j) pair with all L columns refined)
-per second with the operator and V resident in HBM; `e2e` is the same metric through
-nep_create_split + nep_ciss_solve with host buffers (copies included).
+assembly, banded LU, solves refined to backward error <= 1e-10 (a double-float residual with
+complex64 factors), moments, block-Hankel SVD, reduced eigenproblem, Rayleigh-Ritz with
+Newton, scaled residuals. `value` counts quadrature solves (one (problem, z_j) pair with all
+L columns refined) per second with the operator and V resident in HBM; `e2e` is the same
+metric through the request server (nep_create_split, nep_submit with the host probe block,
+nep_server_wait returning the pairs on the host), copies included.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
                   [--impl ours|reference] [--workload delay2d_s64]
@@ -25,6 +26,11 @@ import threading
 import time
 
 import numpy as np
+
+# 32 hardware work queues instead of CUDA's default 8, set before the first CUDA call: the
+# pipelines' and server workers' streams then do not share queues, and a request's short result
+# copies do not wait behind another pipeline's pass.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)

@@ -484,7 +484,13 @@ int nep_interpol_solve(nep_split_t h, const nep_region *r, const nep_interpol_op
  * the device. Each request runs exactly the computation of nep_ciss_solve on its inputs
  * (same kernels, same launch shapes, no state shared between requests), so its result does
  * not depend on what else is in flight. The split handle passed to nep_submit must stay
- * alive until the request's result has been taken. */
+ * alive until the request's result has been taken.
+ * Hardware queues: CUDA gives a context 8 work queues unless the environment variable
+ * CUDA_DEVICE_MAX_CONNECTIONS (read when the process creates its context) says otherwise.
+ * With more busy streams than queues, streams share a queue and a request's short result copy
+ * can wait behind another worker's whole pass. Set it to at least workers + 2 (32 at most)
+ * before the first CUDA call; the Python binding sets 32 when it is imported, unless the
+ * variable is already set. */
 typedef struct nep_server *nep_server_t;
 #define NEP_PENDING 1 /* nep_poll: the request has not finished yet */
 /* workers >= 1 concurrent requests; hbm_budget_bytes == 0: 80% of the free device memory. */

@@ -13,6 +13,12 @@ import numpy as np
 
 from . import build as _build
 
+# Hardware work queues of the CUDA context (read once, when the process creates it; 8 by default).
+# Streams beyond that count share queues, so with a server's worker streams busy a short copy on
+# one stream can wait behind another stream's whole pass. 32 is the largest value; a process that
+# set it, or created its context before this import, keeps what it has.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 c_int32, c_int64, c_double, c_void_p, c_size_t = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
 P_double = ctypes.POINTER(c_double)
 

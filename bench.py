@@ -489,7 +489,7 @@ def main():
             torch.cuda.current_stream().wait_event(ev)
         e1.record()
         barrier()
-    launches = (binding.kernel_launches() - launches0) // max(1, args.steps)
+    launches = binding.kernel_launches() - launches0  # all steps of the timed region
     ms = e0.elapsed_time(e1) / args.steps
     # one pipeline alone: the latency of a step
     torch.cuda.synchronize()
@@ -757,6 +757,7 @@ def main():
                        "peak_tflops": alu_peak,
                        "frac": lu_flops(p.n, split.kl, split.ku, p.N) / (lu * 1e-3) / 1e12 / alu_peak},
             "stages_ms": stage, "clocks": cs, "gpu_launches": int(launches),
+            "gpu_launches_per_step": int(launches) // max(1, args.steps),
             "result": {"nconv": int(len(res["lam"])), "hankel_rank": res["m"], "max_eta": float(res["eta"].max())
                        if len(res["eta"]) else None, "max_backward": res["info"]["max_backward"],
                        "max_sweeps": res["info"]["max_sweeps"], "svd_sweeps": res["info"]["svd_sweeps"],

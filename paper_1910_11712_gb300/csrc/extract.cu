@@ -15,6 +15,7 @@
 //   * residual/select   scaled residual eta (Sec. 2 Eq. (sressplit), infinity norms of the A_i
 //                       as in Sec. 6), inside test, duplicate removal and ordering.
 #include <cooperative_groups.h>
+#include <cstdlib>
 
 #include "nep_common.cuh"
 
@@ -429,6 +430,199 @@ __global__ void svd_finish_kernel(int rows, int cols, const zd* __restrict__ A, 
     }
 }
 
+// The same Jacobi SVD on one thread-block cluster of CS CTAs (CS = 16 where the GPU allows it):
+// CTA r keeps the columns j = r (mod CS) of A and of V in shared memory for the whole run, and each
+// warp of the cluster takes one column pair per round (pair pi on warp pi mod (CS x warps per CTA)),
+// reading and writing the pair's columns where they live through distributed shared memory. The
+// pairs of a round are disjoint, so a round needs no barrier inside it; the cluster's hardware
+// barrier between rounds replaces the grid barrier. The rotations, their order and the stopping
+// rule are those of jacobi_kernel with one warp per pair (its lane order for the dot products).
+// A sweep that rotated nothing ends the run: each CTA records a rotation in its own flag (one per
+// sweep parity), every CTA reads all flags after the last round and so all take the same decision,
+// and a cluster barrier follows the reads, so no CTA leaves while another still reads its flag.
+namespace cgj = cooperative_groups;
+// Sum of R values by pairwise halving (R a power of two): independent additions instead of one chain.
+template <int R, typename V>
+__device__ __forceinline__ V tree_sum(V (&v)[R]) {
+#pragma unroll
+    for (int h = R / 2; h > 0; h /= 2)
+#pragma unroll
+        for (int u = 0; u < h; ++u) v[u] = v[u] + v[u + h];
+    return v[0];
+}
+
+// R: elements per lane of a column of A and of V (rows, cols <= 32 R); each warp holds its pair's
+// four columns in registers for the round: one load and one store of every element.
+template <int R>
+__global__ void __launch_bounds__(256) jacobi_cluster_kernel(int rows, int cols, zd* __restrict__ A,
+                                                             zd* __restrict__ Vm, int max_sweeps, double tol,
+                                                             int* __restrict__ sweeps_out) {
+    cgj::cluster_group cluster = cgj::this_cluster();
+    const int CS = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int ncl = (cols + CS - 1) / CS;  // column slots of this CTA: global j = c CS + rank
+    extern __shared__ __align__(16) unsigned char sraw[];
+    zd* acol = reinterpret_cast<zd*>(sraw);  // ncl x rows
+    zd* vcol = acol + (size_t)ncl * rows;    // ncl x cols
+    __shared__ int rotated[2];
+    for (int c = 0; c < ncl; ++c) {
+        const int j = c * CS + rank;
+        for (int i = tid; i < rows; i += blockDim.x) acol[(size_t)c * rows + i] = j < cols ? A[(int64_t)j * rows + i] : mk(0.0, 0.0);
+        for (int i = tid; i < cols; i += blockDim.x) vcol[(size_t)c * cols + i] = mk(i == j ? 1.0 : 0.0, 0.0);
+    }
+    if (tid == 0) rotated[0] = rotated[1] = 0;
+    cluster.sync();
+    auto acol_of = [&](int j) { return cluster.map_shared_rank(acol + (size_t)(j / CS) * rows, j % CS); };
+    auto vcol_of = [&](int j) { return cluster.map_shared_rank(vcol + (size_t)(j / CS) * cols, j % CS); };
+    const int P = cols + (cols & 1);
+    const int gwarp = rank * nw + warp, nwarps = CS * nw;
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        const int par = sweep & 1;
+        // this flag was last read before the barrier that closed sweep - 2; the rounds of sweep - 1
+        // have passed cluster barriers since
+        if (tid == 0) rotated[par] = 0;
+        __syncthreads();
+        for (int round = 0; round < P - 1; ++round) {
+            for (int pi = gwarp; pi < P / 2; pi += nwarps) {
+                auto pos = [&](int k) { return k == 0 ? 0 : ((k - 1 + round) % (P - 1)) + 1; };
+                int p = pos(pi), q = pos(P - 1 - pi);
+                if (p >= cols || q >= cols) continue;
+                if (p > q) { const int t = p; p = q; q = t; }
+                zd* ap = acol_of(p);
+                zd* aq = acol_of(q);
+                zd* vp = vcol_of(p);
+                zd* vq = vcol_of(q);
+                zd x[R], y[R], vx[R], vy[R];
+#pragma unroll
+                for (int u = 0; u < R; ++u) {
+                    const int i = lane + 32 * u;
+                    x[u] = i < rows ? ap[i] : mk(0.0, 0.0);
+                    y[u] = i < rows ? aq[i] : mk(0.0, 0.0);
+                }
+#pragma unroll
+                for (int u = 0; u < R; ++u) {  // in flight while the rotation is computed
+                    const int i = lane + 32 * u;
+                    vx[u] = i < cols ? vp[i] : mk(0.0, 0.0);
+                    vy[u] = i < cols ? vq[i] : mk(0.0, 0.0);
+                }
+                double pa[R], pb[R];
+                zd pg[R];
+#pragma unroll
+                for (int u = 0; u < R; ++u) {
+                    pa[u] = norm2(x[u]);
+                    pb[u] = norm2(y[u]);
+                    pg[u] = fmac(mk(0.0, 0.0), x[u], y[u]);
+                }
+                double al = tree_sum<R>(pa), be = tree_sum<R>(pb);
+                const zd ga = tree_sum<R>(pg);
+                const double ws = warp_reduce_scatter4(al, be, ga.re, ga.im, lane);
+                al = __shfl_sync(0xffffffffu, ws, 0);
+                be = __shfl_sync(0xffffffffu, ws, 8);
+                const double gr = __shfl_sync(0xffffffffu, ws, 16), gi = __shfl_sync(0xffffffffu, ws, 24);
+                double c, sr, si;
+                if (!jacobi_rotation(al, be, gr, gi, tol, c, sr, si)) continue;
+#pragma unroll
+                for (int u = 0; u < R; ++u) {
+                    const int i = lane + 32 * u;
+                    if (i < rows) {
+                        jacobi_apply(c, sr, si, x[u], y[u]);
+                        ap[i] = x[u];
+                        aq[i] = y[u];
+                    }
+                    if (i < cols) {
+                        jacobi_apply(c, sr, si, vx[u], vy[u]);
+                        vp[i] = vx[u];
+                        vq[i] = vy[u];
+                    }
+                }
+                if (lane == 0) rotated[par] = 1;
+            }
+            cluster.sync();
+        }
+        int any = 0;
+        for (int r = 0; r < CS; ++r) any |= *cluster.map_shared_rank(&rotated[par], r);
+        cluster.sync();
+        if (!any) break;
+    }
+    for (int c = 0; c < ncl; ++c) {
+        const int j = c * CS + rank;
+        if (j >= cols) break;
+        for (int i = tid; i < rows; i += blockDim.x) A[(int64_t)j * rows + i] = acol[(size_t)c * rows + i];
+        for (int i = tid; i < cols; i += blockDim.x) Vm[(int64_t)j * cols + i] = vcol[(size_t)c * cols + i];
+    }
+    if (rank == 0 && tid == 0) *sweeps_out = sweep + 1;
+}
+
+// Launches jacobi_cluster_kernel<R> (R the smallest of 1, 2, 4, 8 with rows, cols <= 32 R) on the
+// largest cluster the GPU takes (16 or 8 CTAs) whose column slots fit in shared memory; false when
+// none does, when rows or cols exceed 256, or when NEP_JACOBI_GRID=1 asks for the cooperative grid
+// kernel (read at every call), and the caller runs jacobi_kernel instead.
+template <int R>
+static bool launch_jacobi_cluster_r(int rows, int cols, zd* A, zd* Vm, int max_sweeps, double tol, int* sweeps_out,
+                                    cudaStream_t st) {
+    // 16 if non-portable cluster sizes are accepted, else 8 (set once, thread-safe), and the dynamic
+    // shared memory limit raised once to the opt-in maximum: a per-call limit races between host
+    // threads launching different sizes
+    static const int allowed = [] {
+        const int a = cudaFuncSetAttribute(jacobi_cluster_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess
+                          ? 16
+                          : 8;
+        cudaGetLastError();
+        return a;
+    }();
+    if (allow_max_dynamic_smem(jacobi_cluster_kernel<R>) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int P = cols + (cols & 1);
+    for (int CS = allowed; CS >= 8; CS /= 2) {
+        const int ncl = (cols + CS - 1) / CS;
+        const size_t smem = sizeof(zd) * (size_t)ncl * ((size_t)rows + cols);
+        if (smem > 200 * 1024) continue;
+        // one pair per warp and round where the pairs allow it, at most eight warps per CTA
+        const int nw = std::max(1, std::min(8, (P / 2 + CS - 1) / CS));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(CS);
+        cfg.blockDim = dim3(32 * nw);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, jacobi_cluster_kernel<R>, &cfg) != cudaSuccess || nclusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        if (cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel<R>, rows, cols, A, Vm, max_sweeps, tol, sweeps_out) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        count_launch();
+        return true;
+    }
+    return false;
+}
+
+static bool launch_jacobi_cluster(int rows, int cols, zd* A, zd* Vm, int max_sweeps, double tol, int* sweeps_out,
+                                  cudaStream_t st) {
+    const char* e = std::getenv("NEP_JACOBI_GRID");
+    if (e && e[0] == '1') return false;
+    const int need = (std::max(rows, cols) + 31) / 32;
+    if (need <= 1) return launch_jacobi_cluster_r<1>(rows, cols, A, Vm, max_sweeps, tol, sweeps_out, st);
+    if (need <= 2) return launch_jacobi_cluster_r<2>(rows, cols, A, Vm, max_sweeps, tol, sweeps_out, st);
+    if (need <= 4) return launch_jacobi_cluster_r<4>(rows, cols, A, Vm, max_sweeps, tol, sweeps_out, st);
+    if (need <= 8) return launch_jacobi_cluster_r<8>(rows, cols, A, Vm, max_sweeps, tol, sweeps_out, st);
+    return false;
+}
+
 // A is destroyed; U (rows x cols) may be nullptr; W (cols x cols); sigma (cols).
 int jacobi_svd(int rows, int cols, zd* A, zd* U, zd* W, double* sigma, JacobiWork w, cudaStream_t st) {
     if (cols <= 0) return NEP_OK;
@@ -449,9 +643,12 @@ int jacobi_svd(int rows, int cols, zd* A, zd* U, zd* W, double* sigma, JacobiWor
     // columns count as orthogonal once |a_p^H a_q| <= rows * eps * |a_p| |a_q|: below that the
     // rotation angle is rounding noise
     double tol = std::max(rows, 1) * 2.220446049250313e-16;
-    void* args[] = {&rows, &cols, &A, &w.Vm, &max_sweeps, &tol, &w.flags, &w.sweeps, &gb};
-    NEP_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(tpb), args, 0, st));
-    count_launch();
+    // one cluster with distributed shared memory where it fits, else the cooperative grid
+    if (!launch_jacobi_cluster(rows, cols, A, w.Vm, max_sweeps, tol, w.sweeps, st)) {
+        void* args[] = {&rows, &cols, &A, &w.Vm, &max_sweeps, &tol, &w.flags, &w.sweeps, &gb};
+        NEP_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(tpb), args, 0, st));
+        count_launch();
+    }
     svd_finish_kernel<<<1, 256, (sizeof(double) + sizeof(int)) * cols, st>>>(rows, cols, A, w.Vm, U, W, sigma);
     NEP_CHECK_LAUNCH();
     return NEP_OK;
@@ -785,23 +982,25 @@ __global__ void __launch_bounds__(kQrcpClusterThreads) qrcp_cluster_kernel(int r
 // fit in shared memory; returns false (nothing launched) when none does.
 static bool launch_qrcp_cluster(int rows, int cols, zd* A, zd* tau, int* perm, double stop2, int* steps_dev,
                                 cudaStream_t st) {
-    static int allowed = -1;  // 16 if non-portable cluster sizes are accepted, else 8
-    if (allowed < 0)
-        allowed = cudaFuncSetAttribute(qrcp_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-                          cudaSuccess
-                      ? 16
-                      : 8;
-    cudaGetLastError();
+    // 16 if non-portable cluster sizes are accepted, else 8 (set once, thread-safe), and the dynamic
+    // shared memory limit raised once to the opt-in maximum: a per-call limit races between host
+    // threads launching different sizes
+    static const int allowed = [] {
+        const int a = cudaFuncSetAttribute(qrcp_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess
+                          ? 16
+                          : 8;
+        cudaGetLastError();
+        return a;
+    }();
+    if (allow_max_dynamic_smem(qrcp_cluster_kernel) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
     for (int CS = allowed; CS >= 8; CS /= 2) {
         const int ncl = (cols + CS - 1) / CS;
         if (ncl > 32) continue;
         const size_t smem = sizeof(zd) * ((size_t)ncl * rows + 2 * (size_t)rows) + (sizeof(double) + sizeof(int)) * ncl;
         if (smem > 200 * 1024) continue;
-        if (cudaFuncSetAttribute(qrcp_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(CS);
         cfg.blockDim = dim3(kQrcpClusterThreads);

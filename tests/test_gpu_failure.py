@@ -67,7 +67,9 @@ def test_one_refinement_sweep_misses_the_target(bnd):
     assert not (ok["flags"] & bnd.NEP_WARN_REFINE)
 
 
-def test_wait_bound_gives_up_and_context_survives(bnd):
+def test_wait_bound_gives_up_and_context_survives(bnd, monkeypatch):
+    # the cooperative grid kernel of the Jacobi SVD, whose grid barriers are the bounded waits
+    monkeypatch.setenv("NEP_JACOBI_GRID", "1")
     torch = torch_cuda()
     lib = bnd.load()
     rows = cols = 128

@@ -257,7 +257,11 @@ def test_moments_kernel(bnd, K):
 @pytest.mark.parametrize("shape,rank", [((40, 40), None), ((128, 128), None), ((96, 96), 30), ((200, 64), None),
                                         ((17, 17), None), ((129, 65), None), ((300, 120), None), ((257, 33), 20),
                                         ((5, 1), None)])
-def test_jacobi_svd_matches_lapack(bnd, shape, rank):
+@pytest.mark.parametrize("kernel", ["cluster", "grid"])
+def test_jacobi_svd_matches_lapack(bnd, shape, rank, kernel, monkeypatch):
+    # "cluster": one thread-block cluster with the columns in distributed shared memory (the
+    # default wherever they fit); "grid": the cooperative grid kernel with bounded grid barriers
+    monkeypatch.setenv("NEP_JACOBI_GRID", "1" if kernel == "grid" else "0")
     torch = torch_cuda()
     rows, cols = shape
     rng = np.random.default_rng(rows + cols)

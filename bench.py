@@ -137,7 +137,7 @@ def solve_bytes(n, ldab, L, npts, esz):
 
 # DRAM bytes (read + write) of one solve launch from an ncu capture of the same launch,
 # keyed by (workload, precision); None where no capture of the current kernel exists.
-SOLVE_TRAFFIC = {("delay2d_s64", "mixed"): (199.5 + 25.6 + 324.9 + 30.1) * 1e6}
+SOLVE_TRAFFIC = {("delay2d_s64", "mixed"): (199.0 + 24.5 + 300.9 + 28.9) * 1e6}
 
 
 def fp32_alu_peak_tflops(sm_mhz):

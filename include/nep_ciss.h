@@ -568,11 +568,12 @@ int nep_moments(int32_t n, int32_t L, int32_t N, int32_t K, const double *coef_d
                 void *stream);
 /* One-sided Jacobi SVD (FP64, device): A (rows x cols complex, column-major, rows >= cols)
  * is overwritten by U Sigma; W_dev (cols x cols) receives W with A_in W = U Sigma; sigma
- * descending with the columns of A and W permuted to match. Runs on one thread-block cluster with
- * the columns in distributed shared memory when rows, cols <= 256 and they fit, else (or when the
- * environment variable NEP_JACOBI_GRID is "1" at the call) on a cooperative grid whose barriers
- * wait a bounded time (nep_set_wait_limit; NEP_ERR_INTERNAL when one runs out). The two differ
- * in rounding only. */
+ * descending with the columns of A and W permuted to match. Runs on a cooperative grid whose
+ * barriers wait a bounded time (nep_set_wait_limit; NEP_ERR_INTERNAL when one runs out), or, when
+ * the environment variable NEP_JACOBI_CLUSTER is "1" at the call and rows, cols <= 256 fit, on one
+ * thread-block cluster with the columns in distributed shared memory (more throughput beside
+ * other work, more latency alone). The two differ in rounding only; the contour solver's
+ * Hankel SVD takes the same choice. */
 int nep_jacobi_svd(int32_t rows, int32_t cols, double *A_dev, double *W_dev, double *sigma_dev, void *stream);
 /* The SVD of nep_jacobi_svd for callers that cannot allocate device memory (a host that
  * accounts for every device byte itself, or a loop that must not enter the CUDA allocator).

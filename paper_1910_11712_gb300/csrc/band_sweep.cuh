@@ -306,11 +306,12 @@ static int sweep_batch_dispatch(int rpl, int rh, int count, int maxL, const Poin
 }
 
 // Right-hand sides per warp of the substitution sweeps. One warp per right-hand side keeps the
-// most chains in flight when there are few (N x L below ~2 per SM sub-partition); with more
-// chains than the GPU can interleave, two or four per warp share the coefficient loads and the
-// step bookkeeping (measured: bandwidth 64 with 1024 chains is fastest with one for complex FP32
-// and two for complex FP64; bandwidth 128 with 4096 chains gains 2x from four). NEP_SOLVE_RH
-// = 1, 2 or 4 overrides the choice: a tuning knob only, the results are identical.
+// most chains in flight when there are few (N x L below 1.5 per SM sub-partition); with more,
+// two or four per warp share the coefficient loads and the step bookkeeping. Measured with the
+// producer warps: bandwidth 64 with 1024 chains (1.7 per sub-partition) takes 0.823 ms per
+// solve with two against 0.849 with one, and eight concurrent passes run 7 % faster; four give
+// another 1.6 % of throughput but 1.32 ms per solve. Bandwidth 128 with 4096 chains gains 2x from
+// four. NEP_SOLVE_RH = 1, 2 or 4 overrides the choice: a tuning knob only, the results are identical.
 template <typename T>
 static int sweep_rh(int chains) {
     static const int forced = [] {
@@ -326,7 +327,7 @@ static int sweep_rh(int chains) {
         return 4 * (sms > 0 ? sms : 152);
     }();
     // about one or two warps per sub-partition; complex FP64 (FP64-throughput-bound) takes at least two
-    const int rh = chains >= 6 * smsp ? 4 : chains >= 3 * smsp ? 2 : 1;
+    const int rh = chains >= 6 * smsp ? 4 : 2 * chains >= 3 * smsp ? 2 : 1;
     return sizeof(T) == 4 ? rh : (rh < 2 ? 2 : rh);
 }
 

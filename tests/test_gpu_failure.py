@@ -69,7 +69,7 @@ def test_one_refinement_sweep_misses_the_target(bnd):
 
 def test_wait_bound_gives_up_and_context_survives(bnd, monkeypatch):
     # the cooperative grid kernel of the Jacobi SVD, whose grid barriers are the bounded waits
-    monkeypatch.setenv("NEP_JACOBI_GRID", "1")
+    monkeypatch.setenv("NEP_JACOBI_CLUSTER", "0")
     torch = torch_cuda()
     lib = bnd.load()
     rows = cols = 128

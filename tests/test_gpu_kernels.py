@@ -259,9 +259,9 @@ def test_moments_kernel(bnd, K):
                                         ((5, 1), None)])
 @pytest.mark.parametrize("kernel", ["cluster", "grid"])
 def test_jacobi_svd_matches_lapack(bnd, shape, rank, kernel, monkeypatch):
-    # "cluster": one thread-block cluster with the columns in distributed shared memory (the
-    # default wherever they fit); "grid": the cooperative grid kernel with bounded grid barriers
-    monkeypatch.setenv("NEP_JACOBI_GRID", "1" if kernel == "grid" else "0")
+    # "grid": the cooperative grid kernel with bounded grid barriers (the default); "cluster": one
+    # thread-block cluster with the columns in distributed shared memory (NEP_JACOBI_CLUSTER=1)
+    monkeypatch.setenv("NEP_JACOBI_CLUSTER", "1" if kernel == "cluster" else "0")
     torch = torch_cuda()
     rows, cols = shape
     rng = np.random.default_rng(rows + cols)

@@ -39,6 +39,26 @@ METRIC = "CISS quadrature solves/s (mixed FP32-factor + FP64 refinement, per-sol
 UNIT = "quadrature_solves/s"
 
 
+def pattern_bandwidths(mats):
+    """(kl, ku) of the union sparsity pattern of the A_i (a property of the input, not of the method)."""
+    import scipy.sparse as sp
+    kl = ku = 0
+    for A in mats:
+        c = sp.coo_matrix(A)
+        if c.nnz:
+            d = c.row.astype(np.int64) - c.col.astype(np.int64)
+            kl, ku = max(kl, int(d.max())), max(ku, int(-d.min()))
+    return kl, ku
+
+
+def workload_config(name, p):
+    """The `config` both arms print for a workload: its sizes and the L2 statement."""
+    kl, ku = pattern_bandwidths(p.mats)
+    band_mb = p.N * p.n * (2 * kl + ku + 1) * 8 / 1e6
+    return {"workload": name, "n": p.n, "bandwidth": kl, "N": p.N, "L": p.L, "M": p.M,
+            "l2": f"inputs larger than L2 (the complex64 band alone is {band_mb:.0f} MB per step)"}
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -423,7 +443,7 @@ def main():
         line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": args.workload, "n": p.n, "N": p.N, "L": p.L, "M": p.M},
+                "data": "synthetic", "config": workload_config(args.workload, p),
                 "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                                  "sample": f"{len(times)} full passes of {args.workload}"},
                 "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -732,12 +752,11 @@ def main():
             "single_stream": {"ms_per_step": ms_single, "value": world * p.N / (ms_single * 1e-3)},
             "vs_baseline": None, "dtype": "c64+f64" if mixed else "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload + (f" with N={p.N}" if args.points > 0 else ""), "n": p.n,
-                       "bandwidth": split.kl, "N": p.N, "L": p.L, "M": p.M,
-                       "precision": args.precision, "l2": "inputs larger than L2 (band factors "
-                       f"{p.N * p.n * split.ldab * esz / 1e6:.0f} MB per step)",
-                       "streams": S, "concurrency": f"{S} independent plans on {S} non-blocking streams, one host "
-                       "thread each; every step a full pass of its own"},
+            "config": workload_config(args.workload + (f" with N={p.N}" if args.points > 0 else ""), p),
+            "execution": {"precision": args.precision,
+                          "band_mb_per_step": round(p.N * p.n * split.ldab * esz / 1e6),
+                          "streams": S, "concurrency": f"{S} independent plans on {S} non-blocking streams, one "
+                          "host thread each; every step a full pass of its own"},
             "roofline": {"kernel": ("band_sweep_kernel x2" if split.kl + 1 <= 288 and split.kl + split.ku + 1 <= 288
                                     else ("band_solve_blocked_kernel" if mixed else "band_solve_kernel")) +
                                    " (forward + backward banded substitution, "

@@ -13,11 +13,13 @@ namespace nep {
 // One substitution sweep (forward with L and the row interchanges, or backward with U) for
 // narrow bands; each warp carries RH right-hand sides. Step k handles row c = k (forward) or
 // c = n-1-k (backward); the row with step index k' lives in window slot s = k' mod RS,
-// RS = 32*RPL, held by lane s / RPL in register s % RPL. Consecutive steps therefore cycle
-// through the registers in a fixed order, so with the step loop unrolled by RPL every
-// register index is a compile-time constant. The row leaving the window at step k (row c
-// itself) is replaced in the same register by the row with step index k + RS, which needs
-// its first update only later (RS > window width).
+// RS = 32*RPL >= W (the window width below), held by lane s / RPL in register s % RPL.
+// Consecutive steps therefore cycle through the registers in a fixed order, so with the step
+// loop unrolled by RPL every register index is a compile-time constant. Once x_c is broadcast,
+// the row leaving the window at step k (row c itself) is replaced in the same register by the
+// row with step index k + RS, before the step's interchange and update: with RS = W that row is
+// c + W, whose first update (by col(k)[W], staged in that slot) is this step's and which the
+// interchange may select; with RS > W its coefficient is zero and no interchange reaches it.
 //
 // The coefficients of step k form one contiguous column col(k)[d], d in [1, W]:
 //   forward  (W = kl):    col(k)[d] = ab[c*ldab + kv + d] = L(c+d, c)
@@ -84,7 +86,8 @@ __global__ void __launch_bounds__(256)
         const int cn = min(CH, n - k0);
         cx<T>* cf = coef0 + (int64_t)bsel * CH * RSP;
         // every slot of every step has exactly one writer: the window rows d in [1, W] copy their
-        // coefficient (zero past the matrix), the other RS - W slots (d = 0 and d > W) zero
+        // coefficient (zero past the matrix), the other RS - W slots zero. d = RS lands in the
+        // leaving row's slot (that of the entering row): col(k)[W] when RS = W, else zero
         for (int cc = pw; cc < cn; cc += nwarps) {
             const int k = k0 + cc, km = k % RS;
             cx<T>* dst = cf + cc * RSP;
@@ -140,6 +143,10 @@ __global__ void __launch_bounds__(256)
                     cx<T> x[RH];
 #pragma unroll
                     for (int h = 0; h < RH; ++h) x[h] = shfl_cx(a[h][u], lane_k);
+                    if (lane == lane_k) {
+#pragma unroll
+                        for (int h = 0; h < RH; ++h) a[h][u] = nb[h * CH + cc];
+                    }
                     if constexpr (SWAPS) {
                         const int p = pv[cc] - (k0 + cc);
                         if (p != 0) {
@@ -166,10 +173,6 @@ __global__ void __launch_bounds__(256)
                         const cx<T> cq = c1[q];
 #pragma unroll
                         for (int h = 0; h < RH; ++h) a[h][q] = fms(a[h][q], cq, x[h]);
-                    }
-                    if (lane == lane_k) {
-#pragma unroll
-                        for (int h = 0; h < RH; ++h) a[h][u] = nb[h * CH + cc];
                     }
                     if (lane == 0) {
 #pragma unroll
@@ -363,8 +366,8 @@ static int sweep_dispatch(int rpl, const SplitDev& s, int npts, const cx<T>* ab,
 // batched launches.
 template <typename T>
 void sweep_key(int kl, int ku, int npts, int L, int* rplf, int* rplb, int* rh, int rh_force) {
-    *rplf = (kl + 1 + 31) / 32;
-    *rplb = (kl + ku + 1 + 31) / 32;
+    *rplf = std::max(1, (kl + 31) / 32);
+    *rplb = std::max(1, (kl + ku + 31) / 32);
     *rh = rh_force == 1 || rh_force == 2 || rh_force == 4 ? rh_force : sweep_rh<T>(npts * L);
 }
 
@@ -381,7 +384,7 @@ int band_sweeps(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* ut, c
                 const int* active, cudaStream_t st, int rh_force) {
     if (npts <= 0 || L <= 0) return NEP_OK;
     if (!band_sweeps_fit(s.kl, s.ku) || !ut) return NEP_ERR_UNSUPPORTED;
-    const int rplf = (s.kl + 1 + 31) / 32, rplb = (s.kl + s.ku + 1 + 31) / 32;
+    const int rplf = std::max(1, (s.kl + 31) / 32), rplb = std::max(1, (s.kl + s.ku + 31) / 32);
     const int rc = sweep_dispatch<T, false>(rplf, s, npts, ab, ut, ipiv, L, B, active, st, rh_force);
     if (rc != NEP_OK) return rc;
     return sweep_dispatch<T, true>(rplb, s, npts, ab, ut, ipiv, L, B, active, st, rh_force);

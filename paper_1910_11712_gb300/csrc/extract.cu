@@ -1246,8 +1246,10 @@ __global__ void __launch_bounds__(256) pchol_kernel(int m, const zd* __restrict_
         const double rkk = sqrt(A[k + (int64_t)m * k].re);
         // row k of R (stored in place): R(k, j) = A(k, j) / R(k, k), j > k
         for (int j = k + 1 + tid; j < m; j += blockDim.x) A[k + (int64_t)m * j] = (1.0 / rkk) * A[k + (int64_t)m * j];
-        if (tid == 0) A[k + (int64_t)m * k] = mk(rkk, 0.0);
         __syncthreads();
+        // R(k, k) replaces A(k, k) only now, after every thread has read A(k, k) above; the
+        // trailing update below does not read it
+        if (tid == 0) A[k + (int64_t)m * k] = mk(rkk, 0.0);
         // trailing update A(i, j) -= conj(R(k, i)) R(k, j), i, j > k
         const int nr = m - k - 1;
         for (int e = tid; e < nr * nr; e += blockDim.x) {
@@ -1313,6 +1315,8 @@ __device__ int schur_form(int m, cx<T>* H, cx<T>* Z, cx<T>* v, int ld, T* red) {
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, nw = nthr >> 5;
     const int tz = (tid + nthr / 2) % nthr;  // Z rows go to the other half of the threads
     const T eps = sizeof(T) == 4 ? T(6e-8) : T(1.2e-16);
+    // the bulge's next x, y after step k, double-buffered by step parity (as in hqr_eigvals_kernel)
+    __shared__ cx<T> xy[2][2];
     auto h = [&](int i, int j) -> cx<T>& { return H[i + (int64_t)ld * j]; };
     auto z = [&](int i, int j) -> cx<T>& { return Z[i + (int64_t)ld * j]; };
     auto sync = [&]() {
@@ -1406,6 +1410,7 @@ __device__ int schur_form(int m, cx<T>* H, cx<T>* Z, cx<T>* v, int ld, T* red) {
             mu = norm2(r1 - d) < norm2(r2 - d) ? r1 : r2;
         }
         cx<T> x = h(l, l) - mu, y = h(l + 1, l);
+        sync();  // every thread has read the shift and x, y before the first rotation rewrites them
         for (int k = l; k < ihi; ++k) {
             T cs;
             cx<T> sn;
@@ -1421,8 +1426,10 @@ __device__ int schur_form(int m, cx<T>* H, cx<T>* Z, cx<T>* v, int ld, T* red) {
             const int rlim = min(k + 2, ihi);
             for (int i = tid; i <= rlim; i += nthr) {
                 const cx<T> p = h(i, k), q = h(i, k + 1);
-                h(i, k) = cs * p + conj(sn) * q;
+                const cx<T> nk = cs * p + conj(sn) * q;
+                h(i, k) = nk;
                 h(i, k + 1) = cs * q - sn * p;
+                if (i == k + 1 || i == k + 2) xy[k & 1][i - k - 1] = nk;
             }
             for (int i = tz; i < m; i += nthr) {
                 const cx<T> p = z(i, k), q = z(i, k + 1);
@@ -1430,9 +1437,9 @@ __device__ int schur_form(int m, cx<T>* H, cx<T>* Z, cx<T>* v, int ld, T* red) {
                 z(i, k + 1) = cs * q - sn * p;
             }
             sync();
-            if (k + 1 < ihi) {
-                x = h(k + 1, k);
-                y = h(k + 2, k);
+            if (k + 1 < ihi) {  // from the copy: the next row rotation rewrites h(k+1, k), h(k+2, k)
+                x = xy[k & 1][0];
+                y = xy[k & 1][1];
             }
         }
     }
@@ -1663,6 +1670,10 @@ __global__ void hqr_eigvals_kernel(int m, const zd* __restrict__ Ain, zd* __rest
                                    cx<T>* gbuf, int use_smem) {
     extern __shared__ unsigned char sraw[];
     __shared__ T red[32];
+    // the bulge's next x, y (h(k+1, k), h(k+2, k) after step k), double-buffered by step parity: all
+    // threads read them after the step's last barrier while step k+1's row rotation, which no
+    // barrier separates from those reads, rewrites the entries in h
+    __shared__ cx<T> xy[2][2];
     const int ld = m + 1;
     cx<T>* H = use_smem ? reinterpret_cast<cx<T>*>(sraw) : gbuf;
     cx<T>* v = H + (int64_t)m * ld;
@@ -1753,6 +1764,7 @@ __global__ void hqr_eigvals_kernel(int m, const zd* __restrict__ Ain, zd* __rest
             mu = norm2(r1 - d) < norm2(r2 - d) ? r1 : r2;
         }
         cx<T> x = h(l, l) - mu, y = h(l + 1, l);
+        sync();  // every thread has read the shift and x, y before the first rotation rewrites them
         for (int k = l; k < ihi; ++k) {
             T cs;
             cx<T> sn;
@@ -1767,13 +1779,15 @@ __global__ void hqr_eigvals_kernel(int m, const zd* __restrict__ Ain, zd* __rest
             const int rlim = min(k + 2, ihi);
             for (int i = l + tid; i <= rlim; i += nthr) {
                 const cx<T> p = h(i, k), q = h(i, k + 1);
-                h(i, k) = cs * p + conj(sn) * q;
+                const cx<T> nk = cs * p + conj(sn) * q;
+                h(i, k) = nk;
                 h(i, k + 1) = cs * q - sn * p;
+                if (i == k + 1 || i == k + 2) xy[k & 1][i - k - 1] = nk;
             }
             sync();
-            if (k + 1 < ihi) {
-                x = h(k + 1, k);
-                y = h(k + 2, k);
+            if (k + 1 < ihi) {  // from the copy: the next row rotation rewrites h(k+1, k), h(k+2, k)
+                x = xy[k & 1][0];
+                y = xy[k & 1][1];
             }
         }
     }

@@ -34,17 +34,20 @@ def test_results_identical_alone_and_in_mix(bnd, workers, max_batch):
     reqs = _requests()
     splits = [bnd.Split.from_problem(p) for p, _ in reqs]
     alone = [bnd.ciss_solve(sp, p.region, p.N, p.L, p.M, V=V, precision=1) for sp, (p, V) in zip(splits, reqs)]
-    srv = bnd.Server(workers=workers, max_batch=max_batch)
-    tickets = [srv.submit(sp, p.region, p.N, p.L, p.M, V=V, precision=1) for sp, (p, V) in zip(splits, reqs)]
-    mixed = [srv.wait(t) for t in tickets]
-    srv.close()
-    for a, b in zip(alone, mixed):
-        assert a["m"] == b["m"]
-        assert np.array_equal(a["lam"], b["lam"])  # bitwise: no state is shared between requests
-        assert np.array_equal(a["eta"], b["eta"])
-        assert np.array_equal(a["X"], b["X"])
-        assert b["info"]["ms_latency"] >= b["info"]["ms_queued"] >= 0.0
-        assert b["info"]["ms_latency"] > 0.0
+    # three mixes: a race inside a kernel shows only under some interleavings with other work on
+    # the same SMs (the eigenvalue QR's bulge chase and the pivoted Cholesky once had one each)
+    for _ in range(3):
+        srv = bnd.Server(workers=workers, max_batch=max_batch)
+        tickets = [srv.submit(sp, p.region, p.N, p.L, p.M, V=V, precision=1) for sp, (p, V) in zip(splits, reqs)]
+        mixed = [srv.wait(t) for t in tickets]
+        srv.close()
+        for a, b in zip(alone, mixed):
+            assert a["m"] == b["m"]
+            assert np.array_equal(a["lam"], b["lam"])  # bitwise: no state is shared between requests
+            assert np.array_equal(a["eta"], b["eta"])
+            assert np.array_equal(a["X"], b["X"])
+            assert b["info"]["ms_latency"] >= b["info"]["ms_queued"] >= 0.0
+            assert b["info"]["ms_latency"] > 0.0
 
 
 def test_admission_respects_budget(bnd):

@@ -30,7 +30,9 @@ namespace nep {
 // all its registers without predicates:  w(row of slot) -= col(k)[d] * x_c, with x_c the row's
 // value after the interchange with row ipiv[c] (forward) or the row's value times 1/U(c,c)
 // (backward). Interchanges are rare in practice, so a chunk without any runs a loop without
-// the interchange test. Steps are RSP = RS + 1 elements apart in shared memory.
+// the interchange test. A lane's RPL coefficients sit RPLP = RPL | 1 (odd) elements after the
+// previous lane's, so the 8-byte loads of a warp step fall in distinct bank pairs (an even stride
+// conflicts: RPL = 4 took 2.8x the shared-load wavefronts); steps are RSP = 32 RPLP + 1 apart.
 // The second half of the CTA's warps are producers: they stage chunk c+1 into the other buffer
 // while the compute warps (one or more right-hand sides each) run chunk c, so the staging's index
 // work and copy issue stay off the compute warps' dependency chains. One CTA barrier per chunk:
@@ -51,7 +53,7 @@ __global__ void __launch_bounds__(256)
         if ((int)blockIdx.y * ((blockDim.x >> 5) / 2) * RH >= L) return;  // no right-hand side of this point here
     }
     if (active && !active[j]) return;
-    constexpr int RS = 32 * RPL, RSP = RS + 1;
+    constexpr int RS = 32 * RPL, RPLP = RPL | 1, RSP = 32 * RPLP + 1;
     const int kv = kl + ku;
     const int W = BWD ? kv : kl;  // window width: rows updated per step
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -95,8 +97,9 @@ __global__ void __launch_bounds__(256)
             for (int d = 1 + lane; d <= RS; d += 32) {
                 int sl = km + (d == RS ? 0 : d);
                 if (sl >= RS) sl -= RS;
-                if (d <= W && k + d < n) cp_async_cx(dst + sl, src + d);
-                else dst[sl] = mk<T>(0, 0);
+                const int at = (sl / RPL) * RPLP + sl % RPL;  // lane sl / RPL, register sl % RPL
+                if (d <= W && k + d < n) cp_async_cx(dst + at, src + d);
+                else dst[at] = mk<T>(0, 0);
             }
         }
         if (pw == 0 && lane < cn) {
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(256)
             continue;
         }
         if (any) {
-            const cx<T>* cf = coef0 + (int64_t)bsel * CH * RSP + lane * RPL;
+            const cx<T>* cf = coef0 + (int64_t)bsel * CH * RSP + lane * RPLP;
             const int* pv = piv0 + bsel * CH;
             const cx<T>* nb = nb0 + ((int64_t)bsel * nwarps + warp) * RH * CH;
             cx<T> rdl = mk<T>(0, 0);
@@ -237,7 +240,7 @@ __global__ void band_transpose_u_kernel(int n, int kv, int ldab, const cx<T>* __
 template <typename T, int RPL, bool BWD, int RH>
 static int run_sweep(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* ut, const int* ipiv, int L,
                      cx<T>* B, const int* active, cudaStream_t st) {
-    constexpr int RSP = 32 * RPL + 1;
+    constexpr int RSP = 32 * (RPL | 1) + 1;
     const int warps = (L + RH - 1) / RH;
     // four compute warps per CTA (those beyond the right-hand sides idle), and as many producer
     // warps: with fewer right-hand sides the staging of a chunk fell on one producer warp and the
@@ -263,7 +266,7 @@ static int run_sweep(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* 
 // right-hand sides of any of them): the launch shape of run_sweep, per-point arithmetic unchanged.
 template <typename T, int RPL, bool BWD, int RH>
 static int run_sweep_batch(int count, int maxL, const PointDesc* pd_dev, cudaStream_t st) {
-    constexpr int RSP = 32 * RPL + 1;
+    constexpr int RSP = 32 * (RPL | 1) + 1;
     const int warps = (maxL + RH - 1) / RH;
     const int wpb = 4;
     const int gy = (warps + wpb - 1) / wpb;
@@ -361,13 +364,20 @@ static int sweep_dispatch(int rpl, const SplitDev& s, int npts, const cx<T>* ab,
     }
 }
 
+// Registers per lane of a sweep's window for window width W. RS = 32 RPL >= W is enough (the
+// entering row takes the leaving row's slot before the step's update), but W + 1 slots are taken:
+// on bandwidth 64 (W = 64 and 128) RPL = 2 and 4 executed 7-17 % fewer instructions and still ran
+// 0.349 + 0.506 ms per solve against 0.345 + 0.476 with RPL = 3 and 5, each step being bound by its
+// dependency chain rather than by issue.
+inline int sweep_rpl_of(int W) { return (W + 1 + 31) / 32; }
+
 // Sweep launch shape of a problem: rows per lane of the forward and backward windows and right-hand
 // sides per warp (from the problem's own chain count N L). Points of problems with equal keys share
 // batched launches.
 template <typename T>
 void sweep_key(int kl, int ku, int npts, int L, int* rplf, int* rplb, int* rh, int rh_force) {
-    *rplf = std::max(1, (kl + 31) / 32);
-    *rplb = std::max(1, (kl + ku + 31) / 32);
+    *rplf = sweep_rpl_of(kl);
+    *rplb = sweep_rpl_of(kl + ku);
     *rh = rh_force == 1 || rh_force == 2 || rh_force == 4 ? rh_force : sweep_rh<T>(npts * L);
 }
 
@@ -384,7 +394,7 @@ int band_sweeps(const SplitDev& s, int npts, const cx<T>* ab, const cx<T>* ut, c
                 const int* active, cudaStream_t st, int rh_force) {
     if (npts <= 0 || L <= 0) return NEP_OK;
     if (!band_sweeps_fit(s.kl, s.ku) || !ut) return NEP_ERR_UNSUPPORTED;
-    const int rplf = std::max(1, (s.kl + 31) / 32), rplb = std::max(1, (s.kl + s.ku + 31) / 32);
+    const int rplf = sweep_rpl_of(s.kl), rplb = sweep_rpl_of(s.kl + s.ku);
     const int rc = sweep_dispatch<T, false>(rplf, s, npts, ab, ut, ipiv, L, B, active, st, rh_force);
     if (rc != NEP_OK) return rc;
     return sweep_dispatch<T, true>(rplb, s, npts, ab, ut, ipiv, L, B, active, st, rh_force);

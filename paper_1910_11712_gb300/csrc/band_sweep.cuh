@@ -13,13 +13,11 @@ namespace nep {
 // One substitution sweep (forward with L and the row interchanges, or backward with U) for
 // narrow bands; each warp carries RH right-hand sides. Step k handles row c = k (forward) or
 // c = n-1-k (backward); the row with step index k' lives in window slot s = k' mod RS,
-// RS = 32*RPL >= W (the window width below), held by lane s / RPL in register s % RPL.
-// Consecutive steps therefore cycle through the registers in a fixed order, so with the step
-// loop unrolled by RPL every register index is a compile-time constant. Once x_c is broadcast,
-// the row leaving the window at step k (row c itself) is replaced in the same register by the
-// row with step index k + RS, before the step's interchange and update: with RS = W that row is
-// c + W, whose first update (by col(k)[W], staged in that slot) is this step's and which the
-// interchange may select; with RS > W its coefficient is zero and no interchange reaches it.
+// RS = 32*RPL, held by lane s / RPL in register s % RPL. Consecutive steps therefore cycle
+// through the registers in a fixed order, so with the step loop unrolled by RPL every
+// register index is a compile-time constant. The row leaving the window at step k (row c
+// itself) is replaced in the same register by the row with step index k + RS, which needs
+// its first update only later (RS > window width).
 //
 // The coefficients of step k form one contiguous column col(k)[d], d in [1, W]:
 //   forward  (W = kl):    col(k)[d] = ab[c*ldab + kv + d] = L(c+d, c)
@@ -88,8 +86,7 @@ __global__ void __launch_bounds__(256)
         const int cn = min(CH, n - k0);
         cx<T>* cf = coef0 + (int64_t)bsel * CH * RSP;
         // every slot of every step has exactly one writer: the window rows d in [1, W] copy their
-        // coefficient (zero past the matrix), the other RS - W slots zero. d = RS lands in the
-        // leaving row's slot (that of the entering row): col(k)[W] when RS = W, else zero
+        // coefficient (zero past the matrix), the other RS - W slots (d = 0 and d > W) zero
         for (int cc = pw; cc < cn; cc += nwarps) {
             const int k = k0 + cc, km = k % RS;
             cx<T>* dst = cf + cc * RSP;
@@ -146,10 +143,6 @@ __global__ void __launch_bounds__(256)
                     cx<T> x[RH];
 #pragma unroll
                     for (int h = 0; h < RH; ++h) x[h] = shfl_cx(a[h][u], lane_k);
-                    if (lane == lane_k) {
-#pragma unroll
-                        for (int h = 0; h < RH; ++h) a[h][u] = nb[h * CH + cc];
-                    }
                     if constexpr (SWAPS) {
                         const int p = pv[cc] - (k0 + cc);
                         if (p != 0) {
@@ -176,6 +169,10 @@ __global__ void __launch_bounds__(256)
                         const cx<T> cq = c1[q];
 #pragma unroll
                         for (int h = 0; h < RH; ++h) a[h][q] = fms(a[h][q], cq, x[h]);
+                    }
+                    if (lane == lane_k) {
+#pragma unroll
+                        for (int h = 0; h < RH; ++h) a[h][u] = nb[h * CH + cc];
                     }
                     if (lane == 0) {
 #pragma unroll
@@ -364,11 +361,10 @@ static int sweep_dispatch(int rpl, const SplitDev& s, int npts, const cx<T>* ab,
     }
 }
 
-// Registers per lane of a sweep's window for window width W. RS = 32 RPL >= W is enough (the
-// entering row takes the leaving row's slot before the step's update), but W + 1 slots are taken:
-// on bandwidth 64 (W = 64 and 128) RPL = 2 and 4 executed 7-17 % fewer instructions and still ran
-// 0.349 + 0.506 ms per solve against 0.345 + 0.476 with RPL = 3 and 5, each step being bound by its
-// dependency chain rather than by issue.
+// Registers per lane of a sweep's window for window width W: RS = 32 RPL > W. (A variant with
+// RS = W, the entering row moved ahead of the step's update, executed fewer instructions on
+// bandwidth 64 but ran no faster: 0.349 + 0.506 ms per solve against 0.345 + 0.476; each step is
+// bound by its dependency chain rather than by issue.)
 inline int sweep_rpl_of(int W) { return (W + 1 + 31) / 32; }
 
 // Sweep launch shape of a problem: rows per lane of the forward and backward windows and right-hand

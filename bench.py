@@ -157,7 +157,7 @@ def solve_bytes(n, ldab, L, npts, esz):
 
 # DRAM bytes (read + write) of one solve launch from an ncu capture of the same launch,
 # keyed by (workload, precision); None where no capture of the current kernel exists.
-SOLVE_TRAFFIC = {("delay2d_s64", "mixed"): (199.0 + 24.5 + 300.9 + 28.9) * 1e6}
+SOLVE_TRAFFIC = {("delay2d_s64", "mixed"): (199.1 + 23.9 + 301.0 + 28.6) * 1e6}
 
 
 def fp32_alu_peak_tflops(sm_mhz):

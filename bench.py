@@ -35,7 +35,7 @@ os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "CISS quadrature solves/s (mixed FP32-factor + FP64 refinement, per-solve backward error <= 1e-10)"
+METRIC = "CISS quadrature solves/s & p99 latency, mixed vs FP64 on GB300 at resid\u22641e-10"
 UNIT = "quadrature_solves/s"
 
 
@@ -241,7 +241,7 @@ def arm_bench(binding, p, prec, V, streams, steps, warmup):
 
 def wide_config_bench(binding, name, peaks, streams, steps, rank=0):
     """A wide-band workload (Drude 128x128, bandwidth 128; square root 24^3, bandwidth 576): the
-    mixed path (complex64 factors with the tensor-core trailing update, FP64 refinement) over
+    mixed path (complex64 factors with the tensor-core trailing update, double-float refinement) over
     `streams` pipelines, one plain FP64 pass beside it, and the roofline of its dominant kernel,
     the banded LU: algorithmic flops 8 n kl (kl+ku) per point over the LU's device time against the
     TF32 tensor peak; the tensor work executed is 3x that (the hi/lo split's three products)."""

@@ -175,7 +175,8 @@ int nep_split_info(nep_split_t h, int32_t *n, int32_t *nterms, int32_t *kl, int3
 
 /* ------------------------------------------------------------------ whole solve */
 /* Full contour-integral pass (all steps on the device): nodes and coefficients,
- * assembly, banded LU, solves with FP64 refinement, moments, block-Hankel SVD and
+ * assembly, banded LU, solves refined to the backward-error target (residual in double-float
+ * arithmetic with complex64 factors, in FP64 with complex128), moments, block-Hankel SVD and
  * reduced eigenproblem, Rayleigh-Ritz projection (Sec. 4.2 Eq. (narnoldi-split)) with
  * Newton steps (Sec. 4.1 Eq. (newton)), scaled residuals (Sec. 2 Eq. (sressplit)).
  * V_host: n x L complex probe block (column-major) or NULL (drawn from opts->seed).

@@ -5,7 +5,7 @@
 // operations per element); only the trailing product changes arithmetic: it runs as TF32 tensor-
 // core products with FP32 accumulation, each FP32 operand split as hi + lo (hi = TF32 rounding,
 // lo = TF32 rounding of the rest) and the three products hi*hi + hi*lo + lo*hi summed (~2^-22
-// relative error per product, close to FP32; the FP64 refinement of the solves removes the rest).
+// relative error per product, close to FP32; the refinement of the solves removes the rest).
 //
 // The complex product is one real product (the 4M form): with L~21 = Lr + i Li, U12 = Ur + i Ui,
 //   row 2i   of A = [ Lr(i,:)  -Li(i,:) ],  row 2i+1 of A = [ Li(i,:)  Lr(i,:) ],

@@ -314,7 +314,7 @@ static int sweep_batch_dispatch(int rpl, int rh, int count, int maxL, const Poin
 // producer warps: bandwidth 64 with 1024 chains (1.7 per sub-partition) takes 0.823 ms per
 // solve with two against 0.849 with one, and eight concurrent passes run 7 % faster; four give
 // another 1.6 % of throughput but 1.32 ms per solve. Bandwidth 128 with 4096 chains gains 2x from
-// four. NEP_SOLVE_RH = 1, 2 or 4 overrides the choice: a tuning knob only, the results are identical.
+// four over one, and 10 % over two (70 against 76 ms of solves per pass). NEP_SOLVE_RH = 1, 2 or 4 overrides the choice: a tuning knob only, the results are identical.
 template <typename T>
 static int sweep_rh(int chains) {
     static const int forced = [] {

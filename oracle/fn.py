@@ -6,7 +6,7 @@ and combinations (sum, product, quotient, composition). Derivatives follow from
 the chain, product and quotient rules (Sec. 3.2.2 notes every function provides
 both f and f').
 
-Pinned by tests/test_oracle_fn.py against finite differences and direct values.
+Pinned by tests/test_oracle_fn_band.py against finite differences and closed-form values.
 """
 from __future__ import annotations
 

@@ -156,6 +156,8 @@ typedef struct {
     int32_t lu_kernel;  /* LU of complex64 bands with kl > 64: 0 the tuned or default choice, 1 tensor    */
                         /* core with TF32 hi/lo operands (3 products, ~FP32), 2 tensor core with TF32     */
                         /* operands (1 product), 3 FP32 SIMT kernel. Results of 1-3 differ by rounding.   */
+                        /* For 32 <= kl <= 64, 1 and 2 select the tensor-core kernel in place of the      */
+                        /* register-window one (the default, 0 or 3).                                      */
     int32_t solve_rh;   /* right-hand sides per warp of the narrow-band sweeps: 0 tuned or default, 1, 2, */
                         /* 4 (a launch shape only: results identical)                                     */
 } nep_opts;

@@ -197,6 +197,10 @@ int launch_band_lu(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info,
                    int lu_kernel) {
     if (npts <= 0) return NEP_OK;
     const int kv = s.kl + s.ku;
+    // complex64, the tensor-core kernel asked for by name on a band the register window also takes
+    if constexpr (sizeof(T) == 4)
+        if ((lu_kernel == LU_TC3 || lu_kernel == LU_TC1) && band_lu_col_fits(s.kl, s.ku) && band_lu_tc_can(s.kl))
+            return launch_band_lu_tc(s, npts, ab, ipiv, info, active, st, lu_kernel == LU_TC1 ? 1 : 3);
     // register window, one barrier per step (lu_col.cu): kl <= 64, kv <= 128
     if (band_lu_col_fits(s.kl, s.ku)) return launch_band_lu_col<T>(s, npts, ab, ipiv, info, active, st);
     // wide bands in complex64: trailing updates on the tensor core

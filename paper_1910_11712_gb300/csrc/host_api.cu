@@ -1102,7 +1102,12 @@ static int run_solves_batch(const std::vector<nep_plan*>& ps, cudaStream_t st) {
         const SplitDev s = p->h->dev();
         const bool tc_ok = sizeof(T) == 4 && p->lu_kernel != LU_SIMT && (p->lu_kernel != LU_AUTO || lu_tc_enabled()) &&
                            band_lu_tc_fits(s.kl);
-        if (band_lu_col_fits(s.kl, s.ku)) {
+        // the tensor-core kernel asked for by name on a narrow band (as launch_band_lu takes it)
+        const bool tc_named = sizeof(T) == 4 && (p->lu_kernel == LU_TC3 || p->lu_kernel == LU_TC1) &&
+                              band_lu_col_fits(s.kl, s.ku) && band_lu_tc_can(s.kl);
+        if (tc_named) {
+            for (int j = 0; j < p->Np; ++j) tc[p->lu_kernel == LU_TC1].push_back(point(p, j, nullptr, nullptr));
+        } else if (band_lu_col_fits(s.kl, s.ku)) {
             for (int j = 0; j < p->Np; ++j) col[lu_col_instance(s.kl, s.ku)].push_back(point(p, j, nullptr, nullptr));
         } else if (tc_ok) {
             for (int j = 0; j < p->Np; ++j) tc[p->lu_kernel == LU_TC1].push_back(point(p, j, nullptr, nullptr));

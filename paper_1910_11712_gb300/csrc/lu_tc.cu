@@ -547,15 +547,14 @@ bool lu_tc_enabled() {
     return on;
 }
 
-bool band_lu_tc_fits(int kl) {
-    if (kl <= 64) return false;
-    return lu_tc_smem(kl) <= 227 * 1024;
-}
+bool band_lu_tc_can(int kl) { return kl >= NB && lu_tc_smem(kl) <= 227 * 1024; }
+
+bool band_lu_tc_fits(int kl) { return kl > 64 && band_lu_tc_can(kl); }
 
 int launch_band_lu_tc(const SplitDev& s, int npts, zf* ab, int* ipiv, int* info, const int* active, cudaStream_t st,
                       int passes) {
     if (npts <= 0) return NEP_OK;
-    if (!band_lu_tc_fits(s.kl)) return NEP_ERR_UNSUPPORTED;
+    if (!band_lu_tc_can(s.kl)) return NEP_ERR_UNSUPPORTED;
     auto encode = encode_fn();
     if (!encode) {
         set_error("cuTensorMapEncodeTiled is not available from the driver");
@@ -626,7 +625,7 @@ int launch_band_lu_tc_batch(const std::vector<PointDesc>& items_in, cudaStream_t
     size_t smem = 0, win_elems = 0;
     int nmt_max = 1;
     for (auto& d : items) {
-        if (!band_lu_tc_fits(d.kl)) return NEP_ERR_UNSUPPORTED;
+        if (!band_lu_tc_can(d.kl)) return NEP_ERR_UNSUPPORTED;
         const int kv = d.kl + d.ku;
         d.RWp = (d.kl + NB + NB - 1) / NB * NB;
         d.CWp = (kv + NB + NB - 1) / NB * NB;

@@ -276,8 +276,10 @@ template <typename T>
 int launch_band_lu_wide(const SplitDev& s, int npts, cx<T>* ab, int* ipiv, int* info, const int* active,
                         cudaStream_t st);
 // The same blocked LU in complex64 with the trailing update on the tensor core (lu_tc.cu): TMA-staged
-// operand tiles, tcgen05 MMA (TF32 hi/lo split, 4M complex form) into tensor memory. kl > 64.
+// operand tiles, tcgen05 MMA (TF32 hi/lo split, 4M complex form) into tensor memory. The default for
+// kl > 64 (band_lu_tc_fits); it runs for kl >= 32 (band_lu_tc_can) when asked for explicitly.
 bool band_lu_tc_fits(int kl);
+bool band_lu_tc_can(int kl);
 // passes: 3 (TF32 hi/lo split, ~FP32 products) or 1 (TF32 operands)
 int launch_band_lu_tc(const SplitDev& s, int npts, zf* ab, int* ipiv, int* info, const int* active, cudaStream_t st,
                       int passes = 3);

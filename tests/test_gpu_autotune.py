@@ -64,3 +64,30 @@ def test_wide_band_lu_kernel_with_accuracy_gate(bnd):
         assert r["info"]["max_backward"] <= 1e-10
         err, _ = match_eigenvalues(r["lam"], ref["lam"])
         assert err <= 1e-9
+
+
+def test_narrow_band_tensor_core_lu_by_name(bnd):
+    """lu_kernel 1 or 2 on a band the register-window LU takes (32 <= kl <= 64) runs the tensor-core LU:
+    the same eigenpairs to rounding, every solve at the target, and the shared-launch path equal to the
+    plan's own pass."""
+    torch = torch_cuda()
+    p = synth.delay_2d(s=40, seed=4, center=-1.5, radius=1.5)
+    p.N, p.L, p.M = 16, 4, 4
+    split = bnd.Split.from_problem(p)
+    assert 32 <= split.kl <= 64
+    V = to_dev(np.asfortranarray(synth.random_probe_block(p.n, p.L, 6)), torch)
+    ref, _ = _run(bnd, split, p, V)  # register-window LU
+    for lu in (1, 2):
+        r, Y = _run(bnd, split, p, V, lu_kernel=lu)
+        if lu == 2 and (r["flags"] & bnd.NEP_WARN_REFINE):
+            continue  # TF32 operands that refinement cannot repair
+        assert r["info"]["max_backward"] <= 1e-10
+        err, _ = match_eigenvalues(r["lam"], ref["lam"])
+        assert err <= 1e-9
+        if lu == 1:
+            a = bnd.Plan(split, p.region, p.N, p.L, p.M, precision=1, lu_kernel=1)
+            b = bnd.Plan(split, p.region, p.N, p.L, p.M, precision=1)
+            bnd.execute_batch([a, b], [V, V])
+            torch.cuda.synchronize()
+            assert np.array_equal(gpu_buffer(a, "Y"), Y)
+            assert np.array_equal(a.result()["lam"], r["lam"])
